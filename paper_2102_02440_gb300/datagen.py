@@ -1,0 +1,282 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+This module only draws data (columns, predicates, join graphs).  It contains none of
+the method's arithmetic: no hashing, no sketch update, no estimate.  Both the CUDA path
+and the oracle are fed the arrays it returns.
+
+Distributions follow the paper's workload shape (JOB over IMDB, which is not available
+here): Zipf-skewed foreign keys, primary keys that are permutations of their domain,
+dictionary-coded string columns with point / subset predicates, integer range
+predicates with a chosen selectivity.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+RANGE, EQ, IN = 0, 1, 2
+INT64_MIN = -(1 << 63)
+
+
+@dataclass
+class Pred:
+    col: int
+    op: int
+    lo: int = 0
+    hi: int = 0
+    bitmap: np.ndarray | None = None   # uint32 words, bit v of the set
+    nbits: int = 0
+
+
+@dataclass
+class Table:
+    name: str
+    cols: list                                     # numpy int32 / int64 columns, equal length
+    preds: list = field(default_factory=list)      # conjunction
+    key_col: list = field(default_factory=list)    # per sketch: column index of its join key
+    edge_id: list = field(default_factory=list)    # per sketch: join-graph edge
+
+    @property
+    def n_rows(self) -> int:
+        return int(self.cols[0].shape[0]) if self.cols else 0
+
+
+@dataclass
+class Workload:
+    name: str
+    tables: list
+    edge_u: list
+    edge_v: list
+    d: int
+    w: int
+    hash_seed: int
+    data_seed: int
+    note: str = ""
+
+    @property
+    def n_edges(self) -> int:
+        return len(self.edge_u)
+
+    @property
+    def total_rows(self) -> int:
+        return sum(t.n_rows for t in self.tables)
+
+    def column_bytes(self) -> int:
+        return sum(c.nbytes for t in self.tables for c in t.cols)
+
+    def sketch_of(self, e: int, end: int):
+        """(table index, sketch index) holding endpoint `end` (0 = edge_u side) of edge e."""
+        t = self.edge_u[e] if end == 0 else self.edge_v[e]
+        return t, self.tables[t].edge_id.index(e)
+
+
+# ---------------------------------------------------------------- Zipf sampler
+
+def _expm1_over(t):
+    t = np.asarray(t, np.float64)
+    out = np.ones_like(t)
+    big = np.abs(t) > 1e-8
+    out[big] = np.expm1(t[big]) / t[big]
+    small = ~big
+    out[small] = 1.0 + t[small] / 2.0 + t[small] ** 2 / 6.0
+    return out
+
+
+def _log1p_over(t):
+    t = np.asarray(t, np.float64)
+    out = np.ones_like(t)
+    big = np.abs(t) > 1e-8
+    out[big] = np.log1p(t[big]) / t[big]
+    small = ~big
+    out[small] = 1.0 - t[small] / 2.0 + t[small] ** 2 / 3.0
+    return out
+
+
+def zipf_ranks(rng: np.random.Generator, n: int, N: int, s: float, chunk: int = 1 << 23) -> np.ndarray:
+    """n ranks in [1, N] with P(k) proportional to k^-s, s > 0.
+
+    Rejection-inversion (Hoermann & Derflinger, ACM TOMACS 1996): with h(x) = x^-s and
+    its antiderivative H, draw U uniformly on [H(1.5) - h(1), H(N + 1/2)], set
+    X = H^-1(U), K = nearest integer to X, and accept K iff U >= H(K + 1/2) - h(K).
+    Each integer k owns an interval of length exactly h(k), so accepted K follow the
+    Zipf law exactly.
+    """
+    one_minus_s = 1.0 - s
+
+    def H(x):
+        lx = np.log(x)
+        return lx * _expm1_over(lx * one_minus_s)
+
+    def Hinv(y):
+        return np.exp(y * _log1p_over(y * one_minus_s))
+
+    lo = float(H(np.array([1.5]))[0] - 1.0)
+    hi = float(H(np.array([N + 0.5]))[0])
+    out = np.empty(n, np.int64)
+    filled = 0
+    while filled < n:
+        m = min(chunk, n - filled)
+        need = m
+        buf = np.empty(0, np.int64)
+        while need > 0:
+            u = lo + rng.random(int(need * 1.15) + 64) * (hi - lo)
+            x = Hinv(u)
+            k = np.clip(np.floor(x + 0.5), 1, N)
+            acc = u >= H(k + 0.5) - k ** (-s)
+            kk = k[acc].astype(np.int64)[:need]
+            buf = np.concatenate([buf, kk])
+            need = m - buf.size
+        out[filled:filled + m] = buf
+        filled += m
+    return out
+
+
+def affine_perm(rng: np.random.Generator, D: int):
+    """A seeded permutation of [0, D): v -> (A v + B) mod D with gcd(A, D) = 1."""
+    while True:
+        A = int(rng.integers(1, max(D, 2)))
+        if np.gcd(A, D) == 1:
+            break
+    B = int(rng.integers(0, max(D, 1)))
+    return A, B
+
+
+def zipf_keys(rng, n: int, D: int, s: float, dtype=np.int32) -> np.ndarray:
+    """Zipf(s) foreign keys over [0, D); hot keys scattered by a seeded permutation."""
+    A, B = affine_perm(rng, D)
+    r = zipf_ranks(rng, n, D, s) - 1
+    return ((A * r + B) % D).astype(dtype)
+
+
+def pk_column(rng, n: int, dtype=np.int32) -> np.ndarray:
+    """A primary key: a seeded permutation of [0, n)."""
+    return rng.permutation(n).astype(dtype)
+
+
+def uniform_col(rng, n: int, lo: int, hi: int, dtype=np.int32) -> np.ndarray:
+    return rng.integers(lo, hi, size=n, dtype=np.int64).astype(dtype)
+
+
+def bitmap_of(values, nbits: int) -> np.ndarray:
+    words = np.zeros((nbits + 31) // 32, np.uint32)
+    for v in values:
+        words[v >> 5] |= np.uint32(1 << (v & 31))
+    return words
+
+
+# ---------------------------------------------------------------- workloads
+
+def two_way(n_r: int = 100_000, n_s: int = 1_000_000, domain: int = 100_000, s: float = 1.0, d: int = 5,
+            w: int = 1024, cut: int = 300, data_seed: int = 20210204, hash_seed: int = 0xC0FFEE) -> Workload:
+    """R(key, p) join S(key, p) on key; Zipf(s) keys over [0, domain); p uniform on
+    [0, 1000) filtered by p < cut on both sides; one edge, d x w sketches."""
+    rng = np.random.default_rng(data_seed)
+    tabs = []
+    for name, n in (("R", n_r), ("S", n_s)):
+        key = zipf_keys(rng, n, domain, s)
+        p = uniform_col(rng, n, 0, 1000)
+        tabs.append(Table(name, [key, p], [Pred(1, RANGE, INT64_MIN, cut)], [0], [0]))
+    return Workload(f"two_way R{n_r} S{n_s} d{d} w{w}", tabs, [0], [1], d, w, hash_seed, data_seed)
+
+
+def five_table(scale: float = 1.0, d: int = 11, w: int = 4096, d1_sel_pct: int = 20, s: float = 1.1,
+               data_seed: int = 20210205, hash_seed: int = 0xC0FFEE + 1) -> Workload:
+    """The 5-table cyclic join graph shaped like the paper's running example
+    (Sec. 1 query, Fig. 1): fact tables F1 (cast_info-like, 36M) and F2
+    (movie_keyword-like, 4.5M), dimensions D1 (title-like, 2.5M), D2 (keyword-like,
+    134k) and D3 (name-like, 4M).  Edges, in id order:
+      e0 D2-F2 (keyword), e1 D1-F2 (movie), e2 D1-F1 (movie), e3 F1-F2 (movie),
+      e4 D3-F1 (person);  F1-F2-D1 is the triangle.
+    Predicates: D2 point on a dictionary code, D3 subset (IN, ~1% of codes), D1 range
+    on a uniform [0,1000) column at d1_sel_pct percent; F1, F2 none."""
+    rng = np.random.default_rng(data_seed)
+    n_f1, n_f2, n_d1, n_d2, n_d3 = (max(int(round(x * scale)), 16)
+                                    for x in (36_000_000, 4_500_000, 2_500_000, 134_000, 4_000_000))
+    movie_dom, kw_dom, person_dom = n_d1, n_d2, n_d3
+    # tables: 0 F1, 1 F2, 2 D1, 3 D2, 4 D3
+    f1 = Table("F1", [zipf_keys(rng, n_f1, movie_dom, s), zipf_keys(rng, n_f1, person_dom, s)], [],
+               [0, 0, 1], [2, 3, 4])
+    f2 = Table("F2", [zipf_keys(rng, n_f2, kw_dom, s), zipf_keys(rng, n_f2, movie_dom, s)], [],
+               [0, 1, 1], [0, 1, 3])
+    d1 = Table("D1", [pk_column(rng, n_d1), uniform_col(rng, n_d1, 0, 1000)],
+               [Pred(1, RANGE, 0, 10 * d1_sel_pct)], [0, 0], [1, 2])
+    codes2 = zipf_keys(rng, n_d2, 10_000, 1.0)
+    point = int(codes2[rng.integers(0, n_d2)])
+    d2 = Table("D2", [pk_column(rng, n_d2), codes2], [Pred(1, EQ, point, 0)], [0], [0])
+    code_dom = 100_000
+    codes3 = zipf_keys(rng, n_d3, code_dom, 0.8)
+    subset = rng.choice(code_dom, size=code_dom // 100, replace=False)
+    d3 = Table("D3", [pk_column(rng, n_d3), codes3], [Pred(1, IN, 0, 0, bitmap_of(subset, code_dom), code_dom)],
+               [0], [4])
+    return Workload(f"five_table scale={scale} d{d} w{w} D1sel={d1_sel_pct}%", [f1, f2, d1, d2, d3],
+                    [3, 2, 2, 0, 4], [1, 1, 0, 1, 0], d, w, hash_seed, data_seed)
+
+
+def random_graph_workload(rng: np.random.Generator, n_tables: int, extra_edges: int, rows_lo: int, rows_hi: int,
+                          domain: int, d: int, w: int, s_range=(0.5, 1.5), int64_keys: bool = False,
+                          pred_prob: float = 0.5, hash_seed: int = 1) -> Workload:
+    """Small random connected join graph (a random tree plus `extra_edges` more, parallel
+    edges allowed); one key column per (table, edge), optional predicates."""
+    eu, ev = [], []
+    for t in range(1, n_tables):
+        u = int(rng.integers(0, t))
+        eu.append(u)
+        ev.append(t)
+    for _ in range(extra_edges):
+        a, b = rng.choice(n_tables, size=2, replace=False)
+        eu.append(int(a))
+        ev.append(int(b))
+    tabs = []
+    kdt = np.int64 if int64_keys else np.int32
+    for t in range(n_tables):
+        n = int(rng.integers(rows_lo, rows_hi + 1))
+        cols, key_col, edge_id = [], [], []
+        for e in range(len(eu)):
+            if eu[e] == t or ev[e] == t:
+                s = float(rng.uniform(*s_range))
+                cols.append(zipf_keys(rng, n, domain, s, kdt))
+                key_col.append(len(cols) - 1)
+                edge_id.append(e)
+        preds = []
+        if rng.random() < pred_prob:
+            cols.append(uniform_col(rng, n, 0, 1000))
+            kind = int(rng.integers(0, 3))
+            c = len(cols) - 1
+            if kind == 0:
+                preds.append(Pred(c, RANGE, int(rng.integers(0, 500)), int(rng.integers(500, 1001))))
+            elif kind == 1:
+                preds.append(Pred(c, EQ, int(rng.integers(0, 1000))))
+            else:
+                sub = rng.choice(1000, size=int(rng.integers(1, 400)), replace=False)
+                preds.append(Pred(c, IN, 0, 0, bitmap_of(sub, 1000), 1000))
+        tabs.append(Table(f"T{t}", cols, preds, key_col, edge_id))
+    return Workload(f"random n{n_tables}+{extra_edges}", tabs, eu, ev, d, w, hash_seed, 0)
+
+
+def connected_subplans(n_tables: int, edge_u, edge_v, min_size: int = 1) -> list:
+    """Every connected induced sub-plan (bit t = table t), ascending mask order."""
+    adj = [0] * n_tables
+    for u, v in zip(edge_u, edge_v):
+        adj[u] |= 1 << v
+        adj[v] |= 1 << u
+    out = []
+    for mask in range(1, 1 << n_tables):
+        if bin(mask).count("1") < min_size:
+            continue
+        start = mask & -mask
+        seen = start
+        frontier = start
+        while frontier:
+            nxt = 0
+            m = frontier
+            while m:
+                b = m & -m
+                nxt |= adj[b.bit_length() - 1]
+                m ^= b
+            nxt &= mask & ~seen
+            seen |= nxt
+            frontier = nxt
+        if seen == mask:
+            out.append(mask)
+    return out

@@ -1,0 +1,237 @@
+"""Pins of the oracle's estimate (Sec. 3.2: per-row inner product then median;
+Sec. 4.2: sketch merging by minimum absolute value, iterated over a table's joins;
+Sec. 4.1: the 3-table contraction sum over i, j of sk_k[i] * M[i, j] * sk_t[j])."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+from paper_2102_02440_gb300 import datagen as G
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _sk(rng, d, w, lo=-6, hi=7):
+    return rng.integers(lo, hi, size=(d, w)).astype(np.int32)
+
+
+def test_worked_merge_values(orc):
+    """Sec. 4.2 example: merge[0,0] = -2 for (3, -2) and merge[0,2] = 0 for (3, 0).
+    A chain k - mk - t whose end sketches are unit vectors reads one merged bucket."""
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "merge_worked_example.txt")) if ln[0] != "#"]
+    w = 3
+    for a, b, i, j, want in ([int(v) for v in r] for r in rows):
+        mk1 = np.zeros((1, w), np.int32)
+        mk2 = np.zeros((1, w), np.int32)
+        mk1[0, i] = a
+        mk2[0, j] = b
+        mk2[0, (j + 1) % w] = 9     # other buckets must not leak in
+        k = np.zeros((1, w), np.int32)
+        k[0, i] = 1
+        t = np.zeros((1, w), np.int32)
+        t[0, j] = 1
+        # tables: 0 = k, 1 = mk, 2 = t; e0 = k-mk (mk's first join), e1 = mk-t
+        sketches = [(k, mk1), (mk2, t)]
+        for brute in (False, True):
+            r = orc.estimate([0, 1], [1, 2], sketches, [1, 1, 1], 1, w, 0b111, brute=brute)
+            assert r.rows == [want]
+
+
+def test_merge_tie_keeps_the_first_sketch(orc):
+    """The merge equation takes sk_mk1[i] when |sk_mk1[i]| <= |sk_mk2[j]|: on a tie in
+    magnitude with opposite signs the first (lower edge id) sketch's value is kept."""
+    w = 2
+    k = np.array([[1, 0]], np.int32)
+    t = np.array([[0, 1]], np.int32)
+    for a, b in ((3, -3), (-3, 3), (0, 0), (-5, 5)):
+        mk1 = np.array([[a, 7]], np.int32)
+        mk2 = np.array([[7, b]], np.int32)
+        r = orc.estimate([0, 1], [1, 2], [(k, mk1), (mk2, t)], [1, 1, 1], 1, w, 0b111)
+        assert r.rows == [a]
+
+
+def _merge2(s1, s2):
+    """Merged 2-D sketch of Sec. 4.2: s1[i] where |s1[i]| <= |s2[j]|, else s2[j]."""
+    a = np.abs(s1)[:, None] <= np.abs(s2)[None, :]
+    return np.where(a, s1[:, None], s2[None, :]).astype(object)
+
+
+def test_three_chain_equals_explicit_double_sum(orc):
+    rng = np.random.default_rng(1)
+    d, w = 3, 17
+    k, mk1, mk2, t = (_sk(rng, d, w, -40, 41) for _ in range(4))
+    sketches = [(k, mk1), (mk2, t)]
+    r = orc.estimate([0, 1], [1, 2], sketches, [1, 1, 1], d, w, 0b111)
+    for i in range(d):
+        M = _merge2(mk1[i].astype(object), mk2[i].astype(object))
+        want = int(np.dot(k[i].astype(object), M.dot(t[i].astype(object))))
+        assert r.rows[i] == want
+
+
+def test_two_way_is_inner_product_and_median(orc):
+    rng = np.random.default_rng(2)
+    for d in (1, 2, 5, 6):
+        A, B = _sk(rng, d, 64, -1000, 1000), _sk(rng, d, 64, -1000, 1000)
+        r = orc.estimate([0], [1], [(A, B)], [10, 20], d, 64, 0b11)
+        want = [int(np.dot(A[i].astype(np.int64), B[i].astype(np.int64))) for i in range(d)]
+        assert r.rows == want
+        srt = sorted(want)
+        med = srt[d // 2] if d % 2 else (srt[d // 2 - 1] + srt[d // 2]) / 2
+        assert r.est == float(med)
+
+
+def test_single_table_is_exact_count(orc):
+    A = np.ones((3, 8), np.int32)
+    r = orc.estimate([0], [1], [(A, A)], [123, 456], 3, 8, 0b10)
+    assert r.rows == [456] * 3 and r.est == 456.0
+
+
+GRAPHS = {
+    "chain4": ([0, 1, 2], [1, 2, 3], 4),
+    "star5": ([0, 0, 0, 0], [1, 2, 3, 4], 5),
+    "triangle": ([0, 1, 0], [1, 2, 2], 3),
+    "cycle4": ([0, 1, 2, 3], [1, 2, 3, 0], 4),
+    "parallel": ([0, 0, 1], [1, 1, 2], 3),
+    "tri+tail": ([0, 1, 2, 2], [1, 2, 0, 3], 4),
+    "two_cycles": ([0, 1, 2, 0, 3], [1, 2, 0, 3, 1], 4),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_message_passing_equals_brute_force(orc, name):
+    eu, ev, nt = GRAPHS[name]
+    rng = np.random.default_rng(sum(map(ord, name)))
+    w = 3 if len(eu) >= 5 else 4
+    d = 2
+    for trial in range(3):
+        lo, hi = (-3, 4) if trial < 2 else (0, 5)       # ties and zeros are frequent
+        sketches = [(_sk(rng, d, w, lo, hi), _sk(rng, d, w, lo, hi)) for _ in eu]
+        for mask in G.connected_subplans(nt, eu, ev, 2):
+            a = orc.estimate(eu, ev, sketches, [1] * nt, d, w, mask)
+            b = orc.estimate(eu, ev, sketches, [1] * nt, d, w, mask, brute=True)
+            assert a.rows == b.rows, (mask, a.rows, b.rows)
+            assert a.est == b.est
+
+
+def test_brute_force_definition_on_a_tiny_star(orc):
+    """Independent restatement of the definition for one star sub-plan (w=2)."""
+    rng = np.random.default_rng(3)
+    w, d = 2, 1
+    c = [_sk(rng, d, w) for _ in range(3)]    # centre's sketches on e0, e1, e2
+    leaf = [_sk(rng, d, w) for _ in range(3)]
+    sketches = [(c[e], leaf[e]) for e in range(3)]
+    r = orc.estimate([0, 0, 0], [1, 2, 3], sketches, [1] * 4, d, w, 0b1111, brute=True)
+    tot = 0
+    for j in itertools.product(range(w), repeat=3):
+        vals = [int(c[e][0, j[e]]) for e in range(3)]
+        m = min(range(3), key=lambda e: (abs(vals[e]), e))
+        tot += vals[m] * int(leaf[0][0, j[0]]) * int(leaf[1][0, j[1]]) * int(leaf[2][0, j[2]])
+    assert r.rows == [tot]
+
+
+def test_big_values_promote_beyond_int128(orc):
+    """A long chain of large counters exceeds 2^127; exact result vs Python integers."""
+    n = 9
+    eu, ev = list(range(n - 1)), list(range(1, n))
+    w = 2
+    big = np.full((1, w), 2_000_000_000, np.int32)
+    sketches = [(big, big) for _ in eu]
+    r = orc.estimate(eu, ev, sketches, [1] * n, 1, w, (1 << n) - 1)
+    # all merged entries are 2e9 (ties keep the first): sum over 2^(n-1) assignments of 2e9^n
+    want = (2_000_000_000 ** n) * (w ** (n - 1))
+    assert r.rows == [want]
+    assert r.est == float(want)
+    # exact big integers round once, to nearest even
+    for v in (want, -want, want + 1, (1 << 200) + (1 << 147), (1 << 200) + (1 << 147) + 1, 3 ** 150):
+        assert orc.dec_to_double(v) == float(v)
+
+
+def test_identity_hash_two_way_is_exact_join(orc):
+    rng = np.random.default_rng(4)
+    w = 512
+    a = G.zipf_keys(rng, 3000, w, 1.0)
+    b = G.zipf_keys(rng, 5000, w, 1.3)
+    hp = np.zeros((1, 3, 6), np.uint64)
+    hp[..., 0] = 1
+    A, na = orc.build_sketch(G.Table("a", [a], [], [0], [0]), hp, 3, w)
+    B, nb = orc.build_sketch(G.Table("b", [b], [], [0], [0]), hp, 3, w)
+    r = orc.estimate([0], [1], [(A[0], B[0])], [na, nb], 3, w, 0b11)
+    exact = orc.join2(a, b)
+    assert r.rows == [exact] * 3
+    assert exact == int(np.dot(np.bincount(a, minlength=w).astype(np.int64),
+                               np.bincount(b, minlength=w).astype(np.int64)))
+
+
+def test_identity_hash_merged_estimate_overestimates(orc):
+    """Sec. 4.2 says merging is likely to overestimate; with identity hashes and
+    non-negative counts min(f1[i], f2[j]) >= joint(i, j), so it provably does."""
+    rng = np.random.default_rng(5)
+    w = 64
+    for trial in range(5):
+        n = [400, 600, 500]
+        k = G.zipf_keys(rng, n[0], w, 1.1)
+        mk_a = G.zipf_keys(rng, n[1], w, 1.1)
+        mk_b = G.zipf_keys(rng, n[1], w, 0.9)
+        t = G.zipf_keys(rng, n[2], w, 1.2)
+        hp = np.zeros((2, 1, 6), np.uint64)
+        hp[..., 0] = 1
+        K, _ = orc.build_sketch(G.Table("k", [k], [], [0], [0]), hp, 1, w)
+        MK, _ = orc.build_sketch(G.Table("mk", [mk_a, mk_b], [], [0, 1], [0, 1]), hp, 1, w)
+        T, _ = orc.build_sketch(G.Table("t", [t], [], [0], [1]), hp, 1, w)
+        r = orc.estimate([0, 1], [1, 2], [(K[0], MK[0]), (MK[1], T[0])], n, 1, w, 0b111)
+        exact = orc.join_brute([0, 1], [1, 2], n, [(k, mk_a), (mk_b, t)], 0b111)
+        assert r.rows[0] >= exact
+
+
+def test_join_brute_matches_join2(orc):
+    rng = np.random.default_rng(6)
+    a = rng.integers(0, 30, 200)
+    b = rng.integers(0, 30, 300)
+    assert orc.join_brute([0], [1], [200, 300], [(a, b)], 0b11) == orc.join2(a, b)
+    assert orc.join2(a, b) == int(sum((a == v).sum() * (b == v).sum() for v in range(30)))
+
+
+def test_unbiased_two_way_over_seeds(orc):
+    """Sec. 3.2: the per-row Fast-AGMS inner product is unbiased.  Mean over 400 seeds
+    (one row each) lies within 4 standard errors of the exact join size."""
+    rng = np.random.default_rng(7)
+    a = G.zipf_keys(rng, 2000, 5000, 1.0)
+    b = G.zipf_keys(rng, 3000, 5000, 1.0)
+    exact = orc.join2(a, b)
+    vals = []
+    M, w = 400, 64
+    for s in range(M):
+        hp = orc.hash_params(1000 + s, 1, 1)
+        A, _ = orc.build_sketch(G.Table("a", [a], [], [0], [0]), hp, 1, w)
+        B, _ = orc.build_sketch(G.Table("b", [b], [], [0], [0]), hp, 1, w)
+        vals.append(orc.estimate([0], [1], [(A[0], B[0])], [0, 0], 1, w, 0b11).rows[0])
+    vals = np.array(vals, np.float64)
+    se = vals.std(ddof=1) / np.sqrt(M)
+    assert abs(vals.mean() - exact) < 4 * se, (vals.mean(), exact, se)
+
+
+def test_w1_reduces_to_agms_product(orc):
+    """w = 1: every tuple lands in the single bucket; the estimate is the basic AGMS
+    product of two sums of signs (Sec. 3.1)."""
+    rng = np.random.default_rng(8)
+    a = rng.integers(0, 100, 500)
+    b = rng.integers(0, 100, 700)
+    hp = orc.hash_params(5, 1, 3)
+    A, _ = orc.build_sketch(G.Table("a", [a], [], [0], [0]), hp, 3, 1)
+    B, _ = orc.build_sketch(G.Table("b", [b], [], [0], [0]), hp, 3, 1)
+    r = orc.estimate([0], [1], [(A[0], B[0])], [0, 0], 3, 1, 0b11)
+    for i in range(3):
+        sa = int(orc.hash_eval(hp[0, i], 1, a)[1].sum())
+        sb = int(orc.hash_eval(hp[0, i], 1, b)[1].sum())
+        assert r.rows[i] == sa * sb
+
+
+def test_rejects_disconnected_and_bad_masks(orc):
+    A = np.ones((1, 4), np.int32)
+    with pytest.raises(ValueError):
+        orc.estimate([0], [1], [(A, A)], [1, 1, 1], 1, 4, 0b101)   # tables 0 and 2 not adjacent
+    with pytest.raises(ValueError):
+        orc.estimate([0], [1], [(A, A)], [1, 1], 1, 4, 0b100)      # bit beyond n_tables
+    with pytest.raises(ValueError):
+        orc.estimate([0], [1], [(A, A)], [1, 1], 1, 4, 0)
