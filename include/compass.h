@@ -1,0 +1,161 @@
+/*
+ * compass.h -- C ABI of libcompass: GB300 (sm_103a) Fast-AGMS sketch build with
+ * push-down selection, and the sketch-merging join-size estimate of COMPASS
+ * (Izenov, Datta, Rusu, Shin, "COMPASS: Online Sketch-based Query Optimization for
+ * In-Memory Databases", arXiv 2102.02440).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named *_dev are CUDA device memory owned by the caller; *_host are host
+ *    memory owned by the caller.  The library never allocates device memory and never
+ *    frees caller memory.  Workspaces are passed in by the caller, sized by the
+ *    matching *_bytes query.
+ *  - `stream` is a cudaStream_t (0 = legacy default stream).  Every device call is
+ *    asynchronous on it; nothing synchronises unless stated.
+ *  - Argument errors are detected on the host, before any launch, and returned as
+ *    CMP_EINVAL (nothing is enqueued).  Conditions only the device can see (an int128
+ *    estimate that overflows, a bounded wait that ran out) are written to *status_dev
+ *    (first error wins; the caller zeroes it).  A failed launch returns CMP_ECUDA.
+ *  - No call aborts the process or throws across the ABI.
+ */
+#ifndef COMPASS_H
+#define COMPASS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t cmp_status;
+#define CMP_OK 0
+#define CMP_EINVAL (-1)       /* bad argument (host-detected, nothing enqueued)       */
+#define CMP_EUNSUPPORTED (-2) /* valid input this version does not handle             */
+#define CMP_EOVERFLOW (-3)    /* an exact integer result left its representation      */
+#define CMP_ECUDA (-4)        /* a CUDA call or kernel launch failed                  */
+#define CMP_EWORKSPACE (-5)   /* workspace or plan buffer smaller than required       */
+#define CMP_ETIMEOUT (-6)     /* a bounded device-side wait ran out                   */
+
+#define CMP_MAX_COLS 16       /* columns per table descriptor     */
+#define CMP_MAX_PREDS 8       /* conjuncts per table              */
+#define CMP_MAX_SKETCHES 16   /* sketches (join edges) per table  */
+#define CMP_MAX_D 64          /* sketch rows                      */
+#define CMP_MAX_W (1 << 20)   /* buckets per sketch row           */
+#define CMP_MAX_TABLES 64     /* tables per join graph (sub-plan masks are uint64) */
+
+enum { CMP_I32 = 0, CMP_I64 = 1 };                       /* column element types */
+enum { CMP_RANGE = 0, CMP_EQ = 1, CMP_IN_BITMAP = 2 };  /* predicate operators  */
+
+/* One column: `data` is a device pointer to n_rows elements of `dtype`. */
+typedef struct {
+  const void* data;
+  int32_t dtype;
+  int32_t reserved;
+} cmp_col;
+
+/* One conjunct of a table's selection (Sec. 2, "Partitioned query execution": the
+ * selection is pushed down and only satisfying tuples update the sketches; Sec. 1 names
+ * point, subset and range predicates).  Values are compared as int64 (int32 columns are
+ * sign-extended):  CMP_RANGE keeps lo <= v < hi;  CMP_EQ keeps v == lo;  CMP_IN_BITMAP
+ * keeps 0 <= v < bitmap_nbits with bit v set in `bitmap` (device, uint32 words, bit v is
+ * bit (v & 31) of word v >> 5) -- subset and LIKE predicates resolved to codes. */
+typedef struct {
+  int32_t col;
+  int32_t op;
+  int64_t lo;
+  int64_t hi;
+  const uint32_t* bitmap;
+  int64_t bitmap_nbits;
+} cmp_pred;
+
+/* Hash parameters of one (edge, sketch row): Carter-Wegman polynomials over the prime
+ * p = 2^61 - 1 (the paper asks for a per-row bucket hash h and a 4-wise independent
+ * +-1 family xi, Sec. 3.1-3.2, without naming one).  With x = key mod p in [0, p):
+ *   h(x)  = ((a x + b) mod p) mod w,
+ *   xi(x) = +1 if (c3 x^3 + c2 x^2 + c1 x + c0) mod p is even, else -1.
+ * All fields are < p and a != 0. */
+typedef struct {
+  uint64_t a, b, c0, c1, c2, c3;
+} cmp_hash;
+
+/* A base table with its pushed-down selection and its attribute-level sketches: one
+ * sketch per join edge the table takes part in, each on the key column of that join
+ * (Sec. 2 "Workflow": two joins on the same attribute get two independent sketches).
+ * All arrays here are HOST arrays; the pointers inside cmp_col / cmp_pred are device
+ * pointers. */
+typedef struct {
+  int64_t n_rows;           /* 0 .. 2^31 - 1 (int32 counters, Sec. 6.1)          */
+  int32_t n_cols;           /* 0 .. CMP_MAX_COLS                                   */
+  int32_t n_preds;          /* 0 .. CMP_MAX_PREDS (conjunction; 0 = keep all)      */
+  int32_t n_sketches;       /* 0 .. CMP_MAX_SKETCHES                               */
+  int32_t reserved;
+  const cmp_col* cols;      /* [n_cols]                                            */
+  const cmp_pred* preds;    /* [n_preds]                                           */
+  const int32_t* key_col;   /* [n_sketches] column index holding the join key      */
+  const int32_t* edge_id;   /* [n_sketches] join-graph edge of the sketch          */
+} cmp_table;
+
+/* Build launch shape.  Zero / negative fields mean "choose automatically" (the
+ * autotuned table when one is loaded, else a size heuristic). */
+typedef struct {
+  int32_t mode;           /* 0 auto, 1 shared-memory private counters, 2 L2-resident global counters */
+  int32_t pairs_per_slab; /* (sketch, row) pairs a CTA privatises in mode 1                          */
+  int32_t threads;        /* threads per CTA (multiple of 32, <= 1024)                              */
+  int32_t tile_rows;      /* rows per tile (multiple of 128, <= 16384)                              */
+  int32_t dedupe;         /* -1 auto, 0 off, 1 aggregate equal keys of a tile before hashing        */
+  int32_t ctas_per_sm;    /* CTAs per SM the grid is sized for                                      */
+} cmp_build_cfg;
+
+/* ---------------------------------------------------------------------- general */
+
+int32_t cmp_abi_version(void);
+const char* cmp_status_str(cmp_status s);
+
+/* Draws the hash parameters of every (edge, row), host only.  SplitMix64 (Steele, Lea &
+ * Flood 2014) seeded with `seed`, consumed in the order edge ascending, row ascending,
+ * fields a, b, c0, c1, c2, c3; each field is the output's top 61 bits, p itself maps to
+ * 0, and a = 0 becomes 1.  out_host: [n_edges * d], entry e*d + i.  Both endpoint
+ * tables of an edge use that edge's parameters (Sec. 3.1: the two sketches of a join
+ * share their random functions). */
+cmp_status cmp_hash_params(uint64_t seed, int32_t n_edges, int32_t d, cmp_hash* out_host);
+
+/* ----------------------------------------------------------------- sketch build */
+
+/* Push-down selection fused with the Fast-AGMS update (Sec. 2 "Partitioned query
+ * execution"; Sec. 3.2 "Fast-AGMS Sketches": for every tuple satisfying the selection
+ * and every row i of every sketch of the table, C[s][i][h_i(key)] += xi_i(key)).
+ *   hash_dev      [n_edges * d] parameters (from cmp_hash_params, copied to the device)
+ *   counters_dev  [n_sketches][d][w] int32, overwritten (zeroed, then built)
+ *   survivors_dev one int64, overwritten with the exact number of selected tuples
+ *   status_dev    one int32 device status word (0 = OK)
+ *   cfg           NULL or a launch shape
+ * d in 1..CMP_MAX_D, w in 1..CMP_MAX_W.  Counters are int32 and wrap-exact; tables with
+ * more than 2^31 - 1 rows are rejected (CMP_EINVAL).  Results are identical for every
+ * launch shape.  Enqueues a memset and one kernel on `stream`. */
+cmp_status cmp_sketch_build(const cmp_table* table, int32_t d, int32_t w, const cmp_hash* hash_dev,
+                            int32_t n_edges, int32_t* counters_dev, int64_t* survivors_dev,
+                            int32_t* status_dev, const cmp_build_cfg* cfg, void* stream);
+
+/* Batched build (all attribute-level sketches of every table of a query, or of many
+ * queries, in ONE persistent launch; Sec. 2: every table's selection and sketches are
+ * built in the same push-down pass, and per-worker partial sketches merge by addition,
+ * Sec. 2 "Sketches").  Two host steps encode a plan, the caller copies it to the
+ * device (any H2D copy), then cmp_sketch_build_batched enqueues one zeroing kernel and
+ * one build kernel reading it.  The plan holds device pointers, so it stays valid as
+ * long as the columns and outputs do; it can be replayed and captured in a CUDA graph.
+ *   counters_dev_host  host array [n_tables] of device pointers, each [n_sketches][d][w]
+ *   survivors_dev      device [n_tables] int64
+ * cmp_build_plan_encode returns CMP_EWORKSPACE if plan_bytes is too small. */
+cmp_status cmp_build_plan_bytes(const cmp_table* tables, int32_t n_tables, int32_t d, int32_t w,
+                                const cmp_build_cfg* cfg, size_t* plan_bytes);
+cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_tables, int32_t d, int32_t w,
+                                 int32_t n_edges, int32_t* const* counters_dev_host, int64_t* survivors_dev,
+                                 const cmp_build_cfg* cfg, void* plan_host, size_t plan_bytes);
+cmp_status cmp_sketch_build_batched(const void* plan_host, const void* plan_dev, const cmp_hash* hash_dev,
+                                    int32_t* status_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COMPASS_H */

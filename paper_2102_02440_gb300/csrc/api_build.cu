@@ -1,0 +1,380 @@
+// C ABI: general entry points, hash parameters, single-table and batched builds.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace cmpk {
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return 152;  // GB300; only used to size grids when no device is visible
+  }
+  return n;
+}
+
+size_t smem_optin_bytes() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return 232448;
+  }
+  return size_t(n);
+}
+
+namespace {
+
+struct SplitMix64 {  // Steele, Lea & Flood 2014
+  uint64_t s;
+  uint64_t next() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+};
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+cmp_status check_table(const cmp_table* t, int32_t d, int32_t w, int32_t n_edges) {
+  if (!t || d < 1 || d > CMP_MAX_D || w < 1 || w > CMP_MAX_W || n_edges < 0) return CMP_EINVAL;
+  if (t->n_rows < 0 || t->n_rows > 2147483647LL) return CMP_EINVAL;
+  if (t->n_cols < 0 || t->n_cols > CMP_MAX_COLS || t->n_preds < 0 || t->n_preds > CMP_MAX_PREDS ||
+      t->n_sketches < 0 || t->n_sketches > CMP_MAX_SKETCHES)
+    return CMP_EINVAL;
+  if ((t->n_cols && !t->cols) || (t->n_preds && !t->preds) || (t->n_sketches && (!t->key_col || !t->edge_id)))
+    return CMP_EINVAL;
+  for (int c = 0; c < t->n_cols; c++) {
+    if (t->cols[c].dtype != CMP_I32 && t->cols[c].dtype != CMP_I64) return CMP_EINVAL;
+    if (t->n_rows > 0 && !t->cols[c].data) return CMP_EINVAL;
+  }
+  for (int q = 0; q < t->n_preds; q++) {
+    const cmp_pred& p = t->preds[q];
+    if (p.col < 0 || p.col >= t->n_cols || p.op < CMP_RANGE || p.op > CMP_IN_BITMAP) return CMP_EINVAL;
+    if (p.op == CMP_IN_BITMAP && (p.bitmap_nbits < 0 || (p.bitmap_nbits > 0 && !p.bitmap))) return CMP_EINVAL;
+  }
+  for (int s = 0; s < t->n_sketches; s++) {
+    if (t->key_col[s] < 0 || t->key_col[s] >= t->n_cols) return CMP_EINVAL;
+    if (t->edge_id[s] < 0 || t->edge_id[s] >= n_edges) return CMP_EINVAL;
+  }
+  return CMP_OK;
+}
+
+DevTable to_dev(const cmp_table* t, int32_t* counters, int64_t* survivors) {
+  DevTable D;
+  std::memset(&D, 0, sizeof(D));
+  D.n_rows = t->n_rows;
+  D.n_cols = t->n_cols;
+  D.n_preds = t->n_preds;
+  D.n_sketches = t->n_sketches;
+  D.vec_ok = 1;
+  for (int c = 0; c < t->n_cols; c++) {
+    D.col[c] = t->cols[c].data;
+    D.dtype[c] = t->cols[c].dtype;
+    if (!aligned16(t->cols[c].data)) D.vec_ok = 0;
+  }
+  for (int q = 0; q < t->n_preds; q++) {
+    const cmp_pred& p = t->preds[q];
+    D.pred[q].col = p.col;
+    D.pred[q].op = p.op;
+    D.pred[q].lo = p.lo;
+    D.pred[q].hi = p.hi;
+    D.pred[q].bitmap = p.bitmap;
+    D.pred[q].nbits = p.op == CMP_IN_BITMAP ? p.bitmap_nbits : 0;
+  }
+  for (int s = 0; s < t->n_sketches; s++) {
+    D.key_col[s] = t->key_col[s];
+    D.edge_id[s] = t->edge_id[s];
+  }
+  D.counters = counters;
+  D.survivors = survivors;
+  return D;
+}
+
+uint32_t next_pow2(uint32_t v) {
+  uint32_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Shape common to one launch (single or batched).  max_total_pairs = largest k*d.
+cmp_status choose_shape(const cmp_build_cfg* cfg, int32_t d, int32_t w, int32_t max_total_pairs, BuildShape* out) {
+  BuildShape s;
+  std::memset(&s, 0, sizeof(s));
+  const size_t optin = smem_optin_bytes();
+  const size_t pair_bytes = size_t(w) * 4;
+  s.threads = (cfg && cfg->threads > 0) ? cfg->threads : 512;
+  s.tile_rows = (cfg && cfg->tile_rows > 0) ? cfg->tile_rows : 2048;
+  s.dedupe = (cfg && cfg->dedupe >= 0) ? (cfg->dedupe ? 1 : 0) : 1;
+  if (s.threads < 32 || s.threads > 1024 || s.threads % 32) return CMP_EINVAL;
+  if (s.tile_rows < 128 || s.tile_rows > 16384 || s.tile_rows % 128) return CMP_EINVAL;
+  s.map_slots = s.dedupe ? int32_t(next_pow2(uint32_t(2 * s.tile_rows))) : 0;
+  if (s.dedupe && s.map_slots > 8 * s.threads) return CMP_EINVAL;  // compaction keeps <= 8 slots per thread
+  int mode = (cfg && cfg->mode > 0) ? cfg->mode : 0;
+  if (mode < 0 || mode > 2) return CMP_EINVAL;
+  const int pairs_all = std::max(max_total_pairs, 1);
+  // overhead of everything but the private counters, with the parameter area sized for all pairs
+  BuildShape probe = s;
+  probe.mode = 2;
+  probe.max_pairs = pairs_all;
+  const size_t overhead = build_smem_bytes(probe, w) + 1024;
+  if (mode == 0) mode = (pair_bytes * 1 + overhead <= optin && pair_bytes <= 96 * 1024) ? 1 : 2;
+  s.mode = mode;
+  int ctas_per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : 0;
+  if (mode == 1) {
+    if (!ctas_per_sm) ctas_per_sm = pair_bytes * std::min(pairs_all, 11) > 64 * 1024 ? 1 : 2;
+    const size_t per_cta = optin / size_t(ctas_per_sm) - (ctas_per_sm > 1 ? 1024 : 0);
+    if (per_cta <= overhead) return CMP_EINVAL;
+    int pps = int(std::min<size_t>(size_t(pairs_all), (per_cta - overhead) / pair_bytes));
+    if (cfg && cfg->pairs_per_slab > 0) pps = std::min(cfg->pairs_per_slab, pairs_all);
+    if (pps < 1) return CMP_EINVAL;
+    const int n_slabs = (pairs_all + pps - 1) / pps;
+    pps = (pairs_all + n_slabs - 1) / n_slabs;  // equal slabs
+    s.pairs_per_slab = pps;
+    s.smem_pairs = pps;
+    s.max_pairs = pps;
+  } else {
+    if (!ctas_per_sm) ctas_per_sm = 2;
+    s.pairs_per_slab = pairs_all;
+    s.smem_pairs = 0;
+    s.max_pairs = pairs_all;
+  }
+  s.ctas_per_slab = ctas_per_sm;  // temporarily: CTAs per SM
+  s.smem_bytes = build_smem_bytes(s, w);
+  if (s.smem_bytes > optin) return CMP_EINVAL;
+  *out = s;
+  return CMP_OK;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+}  // namespace cmpk
+
+using namespace cmpk;
+
+extern "C" {
+
+int32_t cmp_abi_version(void) { return 1; }
+
+const char* cmp_status_str(cmp_status s) {
+  switch (s) {
+    case CMP_OK: return "ok";
+    case CMP_EINVAL: return "invalid argument";
+    case CMP_EUNSUPPORTED: return "unsupported input";
+    case CMP_EOVERFLOW: return "exact integer overflow";
+    case CMP_ECUDA: return "CUDA error";
+    case CMP_EWORKSPACE: return "workspace or plan buffer too small";
+    case CMP_ETIMEOUT: return "bounded device wait ran out";
+    default: return "unknown status";
+  }
+}
+
+cmp_status cmp_hash_params(uint64_t seed, int32_t n_edges, int32_t d, cmp_hash* out_host) {
+  if (n_edges < 0 || d < 1 || d > CMP_MAX_D || (n_edges > 0 && !out_host)) return CMP_EINVAL;
+  SplitMix64 g{seed};
+  for (int32_t e = 0; e < n_edges; e++)
+    for (int32_t i = 0; i < d; i++) {
+      uint64_t f[6];
+      for (int k = 0; k < 6; k++) {
+        const uint64_t v = g.next() >> 3;
+        f[k] = v == kP61 ? 0 : v;
+      }
+      if (f[0] == 0) f[0] = 1;
+      cmp_hash& h = out_host[size_t(e) * d + i];
+      h.a = f[0], h.b = f[1], h.c0 = f[2], h.c1 = f[3], h.c2 = f[4], h.c3 = f[5];
+    }
+  return CMP_OK;
+}
+
+cmp_status cmp_sketch_build(const cmp_table* table, int32_t d, int32_t w, const cmp_hash* hash_dev, int32_t n_edges,
+                            int32_t* counters_dev, int64_t* survivors_dev, int32_t* status_dev,
+                            const cmp_build_cfg* cfg, void* stream) {
+  cmp_status st = check_table(table, d, w, n_edges);
+  if (st != CMP_OK) return st;
+  if (!survivors_dev || (table->n_sketches && (!counters_dev || !hash_dev))) return CMP_EINVAL;
+  const int32_t total_pairs = table->n_sketches * d;
+  BuildShape s;
+  st = choose_shape(cfg, d, w, total_pairs, &s);
+  if (st != CMP_OK) return st;
+  cudaStream_t cs = as_stream(stream);
+  const size_t cbytes = size_t(total_pairs) * w * sizeof(int32_t);
+  if (cbytes && cudaMemsetAsync(counters_dev, 0, cbytes, cs) != cudaSuccess) return CMP_ECUDA;
+  if (cudaMemsetAsync(survivors_dev, 0, sizeof(int64_t), cs) != cudaSuccess) return CMP_ECUDA;
+  if (table->n_rows == 0) return CMP_OK;
+  const int n_slabs = total_pairs ? (total_pairs + s.pairs_per_slab - 1) / s.pairs_per_slab : 1;
+  const int64_t n_tiles = (table->n_rows + s.tile_rows - 1) / s.tile_rows;
+  const int target = sm_count() * s.ctas_per_slab;
+  s.ctas_per_slab = int(std::max<int64_t>(1, std::min<int64_t>(n_tiles, (target + n_slabs - 1) / n_slabs)));
+  s.grid = n_slabs * s.ctas_per_slab;
+  BuildArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.table = to_dev(table, counters_dev, survivors_dev);
+  a.hash = hash_dev;
+  a.status = status_dev;
+  a.d = d, a.w = w, a.n_edges = n_edges;
+  a.threads = s.threads, a.tile_rows = s.tile_rows, a.map_slots = s.map_slots;
+  a.max_pairs = s.max_pairs, a.smem_pairs = s.smem_pairs;
+  a.pairs_per_slab = s.pairs_per_slab, a.ctas_per_slab = s.ctas_per_slab;
+  return launch_build(a, s, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
+}
+
+// ---------------------------------------------------------------- batched build plan
+// blob: [BuildPlanHdr][DevTable x n_tables][BuildItem x n_items][int32 cta_item x grid][ZeroSpan x n_zero]
+
+static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t d, int32_t w,
+                              const cmp_build_cfg* cfg, BuildShape* shape, std::vector<BuildItem>* items,
+                              std::vector<int32_t>* cta_item, size_t* bytes, int32_t n_edges_check) {
+  if (n_tables < 1 || !tables) return CMP_EINVAL;
+  int32_t max_pairs = 1;
+  for (int32_t t = 0; t < n_tables; t++) {
+    cmp_status st = check_table(&tables[t], d, w, n_edges_check);
+    if (st != CMP_OK) return st;
+    max_pairs = std::max(max_pairs, tables[t].n_sketches * d);
+  }
+  BuildShape s;
+  cmp_status st = choose_shape(cfg, d, w, max_pairs, &s);
+  if (st != CMP_OK) return st;
+  const int ctas_per_sm = s.ctas_per_slab;
+  // work of an item ~ tiles * (pairs + 1); CTAs proportional to work, >= 1, <= tiles
+  struct Raw {
+    int32_t t, b, e;
+    int64_t tiles;
+    double work;
+  };
+  std::vector<Raw> raw;
+  double total = 0;
+  for (int32_t t = 0; t < n_tables; t++) {
+    const int32_t tp = tables[t].n_sketches * d;
+    const int64_t tiles = (tables[t].n_rows + s.tile_rows - 1) / s.tile_rows;
+    if (tiles == 0) continue;
+    const int32_t n_slabs = tp ? (tp + s.pairs_per_slab - 1) / s.pairs_per_slab : 1;
+    for (int32_t k = 0; k < n_slabs; k++) {
+      Raw r{t, k * s.pairs_per_slab, std::min(tp, (k + 1) * s.pairs_per_slab), tiles, 0};
+      r.work = double(tiles) * double(r.e - r.b + 1);
+      total += r.work;
+      raw.push_back(r);
+    }
+  }
+  const double target = double(sm_count()) * ctas_per_sm * 4.0;
+  items->clear();
+  cta_item->clear();
+  for (size_t i = 0; i < raw.size(); i++) {
+    const Raw& r = raw[i];
+    int64_t n = int64_t(r.work / std::max(total, 1.0) * target + 0.5);
+    n = std::max<int64_t>(1, std::min<int64_t>(n, r.tiles));
+    BuildItem it;
+    it.table = r.t;
+    it.pair_begin = r.b;
+    it.pair_end = r.e;
+    it.n_ctas = int32_t(n);
+    it.first_cta = int32_t(cta_item->size());
+    it.pad = 0;
+    for (int64_t c = 0; c < n; c++) cta_item->push_back(int32_t(items->size()));
+    items->push_back(it);
+  }
+  s.grid = int32_t(cta_item->size());
+  s.ctas_per_slab = 0;
+  *shape = s;
+  size_t off = align16(sizeof(BuildPlanHdr));
+  off += align16(sizeof(DevTable) * n_tables);
+  off += align16(sizeof(BuildItem) * items->size());
+  off += align16(sizeof(int32_t) * cta_item->size());
+  off += align16(sizeof(ZeroSpan) * (n_tables + 1));
+  *bytes = off;
+  return CMP_OK;
+}
+
+}  // extern "C"
+
+extern "C" cmp_status cmp_build_plan_bytes(const cmp_table* tables, int32_t n_tables, int32_t d, int32_t w,
+                                           const cmp_build_cfg* cfg, size_t* plan_bytes) {
+  if (!plan_bytes) return CMP_EINVAL;
+  BuildShape s;
+  std::vector<BuildItem> items;
+  std::vector<int32_t> cta;
+  // edge ids are validated at encode time (n_edges unknown here): accept any non-negative id
+  return plan_layout(tables, n_tables, d, w, cfg, &s, &items, &cta, plan_bytes, 1 << 30);
+}
+
+extern "C" cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_tables, int32_t d, int32_t w,
+                                            int32_t n_edges, int32_t* const* counters_dev_host,
+                                            int64_t* survivors_dev, const cmp_build_cfg* cfg, void* plan_host,
+                                            size_t plan_bytes) {
+  if (!plan_host || !counters_dev_host || !survivors_dev) return CMP_EINVAL;
+  BuildShape s;
+  std::vector<BuildItem> items;
+  std::vector<int32_t> cta;
+  size_t need = 0;
+  cmp_status st = plan_layout(tables, n_tables, d, w, cfg, &s, &items, &cta, &need, n_edges);
+  if (st != CMP_OK) return st;
+  if (plan_bytes < need) return CMP_EWORKSPACE;
+  for (int32_t t = 0; t < n_tables; t++)
+    if (tables[t].n_sketches && !counters_dev_host[t]) return CMP_EINVAL;
+  unsigned char* base = static_cast<unsigned char*>(plan_host);
+  std::memset(base, 0, need);
+  BuildPlanHdr h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = kBuildPlanMagic;
+  h.version = 1;
+  h.n_tables = n_tables;
+  h.n_items = int32_t(items.size());
+  h.d = d, h.w = w, h.n_edges = n_edges;
+  h.shape = s;
+  size_t off = align16(sizeof(BuildPlanHdr));
+  h.off_tables = int64_t(off);
+  off += align16(sizeof(DevTable) * n_tables);
+  h.off_items = int64_t(off);
+  off += align16(sizeof(BuildItem) * items.size());
+  h.off_cta_item = int64_t(off);
+  off += align16(sizeof(int32_t) * cta.size());
+  h.off_zero = int64_t(off);
+  h.total_bytes = int64_t(need);
+  std::vector<ZeroSpan> zs;
+  for (int32_t t = 0; t < n_tables; t++) {
+    DevTable D = to_dev(&tables[t], counters_dev_host[t], survivors_dev + t);
+    std::memcpy(base + h.off_tables + sizeof(DevTable) * t, &D, sizeof(D));
+    const int64_t cb = int64_t(tables[t].n_sketches) * d * w * 4;
+    if (cb) zs.push_back(ZeroSpan{counters_dev_host[t], cb});
+  }
+  zs.push_back(ZeroSpan{survivors_dev, int64_t(n_tables) * 8});
+  h.n_zero = int64_t(zs.size());
+  std::memcpy(base + h.off_items, items.data(), sizeof(BuildItem) * items.size());
+  std::memcpy(base + h.off_cta_item, cta.data(), sizeof(int32_t) * cta.size());
+  std::memcpy(base + h.off_zero, zs.data(), sizeof(ZeroSpan) * zs.size());
+  std::memcpy(base, &h, sizeof(h));
+  return CMP_OK;
+}
+
+extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void* plan_dev,
+                                               const cmp_hash* hash_dev, int32_t* status_dev, void* stream) {
+  if (!plan_host || !plan_dev) return CMP_EINVAL;
+  BuildPlanHdr h;
+  std::memcpy(&h, plan_host, sizeof(h));
+  if (h.magic != kBuildPlanMagic || h.version != 1) return CMP_EINVAL;
+  if (h.n_edges > 0 && !hash_dev) return CMP_EINVAL;
+  const unsigned char* dev = static_cast<const unsigned char*>(plan_dev);
+  cudaStream_t cs = as_stream(stream);
+  if (launch_zero_spans(reinterpret_cast<const ZeroSpan*>(dev + h.off_zero), int32_t(h.n_zero), cs) != cudaSuccess)
+    return CMP_ECUDA;
+  if (h.shape.grid == 0) return CMP_OK;
+  BuildArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.tables = reinterpret_cast<const DevTable*>(dev + h.off_tables);
+  a.items = reinterpret_cast<const BuildItem*>(dev + h.off_items);
+  a.cta_item = reinterpret_cast<const int32_t*>(dev + h.off_cta_item);
+  a.hash = hash_dev;
+  a.status = status_dev;
+  a.d = h.d, a.w = h.w, a.n_edges = h.n_edges;
+  a.threads = h.shape.threads, a.tile_rows = h.shape.tile_rows, a.map_slots = h.shape.map_slots;
+  a.max_pairs = h.shape.max_pairs, a.smem_pairs = h.shape.smem_pairs;
+  return launch_build(a, h.shape, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
+}

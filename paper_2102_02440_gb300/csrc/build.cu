@@ -1,0 +1,359 @@
+// Push-down selection fused with the Fast-AGMS sketch update (Sec. 2 "Partitioned query
+// execution", Sec. 3.2 "Fast-AGMS Sketches").
+//
+// One CTA owns a slab: a contiguous range of (sketch, row) pairs of one table.  In
+// mode 1 the slab's counters are privatised in shared memory (int32, exact), in mode 2
+// (w too large for shared memory) updates go to the L2-resident global counters.  The
+// CTA walks tiles of the table's rows:
+//   A. predicate pass: 128-bit loads of the predicate columns, conjunction, warp-ballot
+//      compaction of the surviving row offsets into shared memory;
+//   B. per key column of the slab: optional aggregation of equal keys of the tile in a
+//      shared-memory hash map (the update is linear, so count * xi is exact), then for
+//      every distinct key and every pair of the slab on that column the CW bucket and
+//      sign, and one shared-memory (or L2) atomic add;
+//   C. after the last tile: the private counters are added into the final sketch with
+//      one global atomic per nonzero counter (partial sketches merge by addition,
+//      Sec. 2 "Sketches").
+// The kernel has no inter-CTA waits.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace cmpk {
+
+namespace {
+
+__device__ __forceinline__ int64_t load1(const void* base, int32_t dtype, int64_t row) {
+  return dtype == CMP_I32 ? int64_t(__ldg(reinterpret_cast<const int32_t*>(base) + row))
+                          : int64_t(__ldg(reinterpret_cast<const long long*>(base) + row));
+}
+
+// 4 consecutive rows starting at `row` (row % 4 == 0); nvalid in 0..4.
+__device__ __forceinline__ void load4(const void* base, int32_t dtype, int64_t row, int nvalid, bool vec,
+                                      int64_t v[4]) {
+  if (dtype == CMP_I32) {
+    const int32_t* p = reinterpret_cast<const int32_t*>(base) + row;
+    if (vec && nvalid == 4) {
+      const int4 q = __ldg(reinterpret_cast<const int4*>(p));
+      v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; k++) v[k] = k < nvalid ? int64_t(__ldg(p + k)) : 0;
+    }
+  } else {
+    const long long* p = reinterpret_cast<const long long*>(base) + row;
+    if (vec && nvalid == 4) {
+      const longlong2 a = __ldg(reinterpret_cast<const longlong2*>(p));
+      const longlong2 b = __ldg(reinterpret_cast<const longlong2*>(p + 2));
+      v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; k++) v[k] = k < nvalid ? int64_t(__ldg(p + k)) : 0;
+    }
+  }
+}
+
+__device__ __forceinline__ bool pred_holds(const DevPred& q, int64_t v) {
+  if (q.op == CMP_RANGE) return q.lo <= v && v < q.hi;
+  if (q.op == CMP_EQ) return v == q.lo;
+  if (v < 0 || v >= q.nbits) return false;
+  return (__ldg(q.bitmap + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+__device__ __forceinline__ uint32_t map_slot(uint64_t x, uint32_t mask) {
+  return uint32_t((x * 0x9E3779B97F4A7C15ull) >> 40) & mask;
+}
+
+constexpr int kMaxSlotsPerThread = 8;
+
+}  // namespace
+
+template <bool GLOBAL, bool DEDUPE, bool POW2>
+__global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ BuildArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x;
+  const int T = blockDim.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+
+  // ---- resolve the work item of this CTA
+  const DevTable* tb;
+  int pair_begin, pair_end, cta_in_slab, n_ctas;
+  if (A.items) {
+    const BuildItem it = A.items[A.cta_item[blockIdx.x]];
+    tb = A.tables + it.table;
+    pair_begin = it.pair_begin;
+    pair_end = it.pair_end;
+    cta_in_slab = int(blockIdx.x) - it.first_cta;
+    n_ctas = it.n_ctas;
+  } else {
+    tb = &A.table;
+    const int slab = int(blockIdx.x) / A.ctas_per_slab;
+    cta_in_slab = int(blockIdx.x) % A.ctas_per_slab;
+    n_ctas = A.ctas_per_slab;
+    pair_begin = slab * A.pairs_per_slab;
+    const int total_pairs = tb->n_sketches * A.d;
+    pair_end = min(pair_begin + A.pairs_per_slab, total_pairs);
+  }
+  const int npairs = pair_end - pair_begin;
+  const int w = A.w;
+  const int64_t n_rows = tb->n_rows;
+  const int n_preds = tb->n_preds;
+  const bool vec = tb->vec_ok != 0;
+  const int R = A.tile_rows;
+  const int M = A.map_slots;
+
+  // ---- shared memory carve-up
+  // (region sizes must match build_smem_bytes)
+  unsigned char* sp = smem;
+  PairParam* prm = reinterpret_cast<PairParam*>(sp);
+  sp += align16(sizeof(PairParam) * A.max_pairs);
+  int32_t* pcol = reinterpret_cast<int32_t*>(sp);  // key column of each pair
+  sp += align16(sizeof(int32_t) * A.max_pairs);
+  int32_t* cnt = reinterpret_cast<int32_t*>(sp);  // private counters (mode 1)
+  if (!GLOBAL) sp += align16(sizeof(int32_t) * size_t(A.smem_pairs) * w);
+  unsigned long long* mkey = reinterpret_cast<unsigned long long*>(sp);
+  if (DEDUPE) sp += align16(sizeof(unsigned long long) * size_t(M));
+  int32_t* mcnt = reinterpret_cast<int32_t*>(sp);
+  if (DEDUPE) sp += align16(sizeof(int32_t) * size_t(M));
+  uint16_t* surv = reinterpret_cast<uint16_t*>(sp);
+  sp += align16(sizeof(uint16_t) * R);
+  int32_t* sint = reinterpret_cast<int32_t*>(sp);  // [0] tail, [1..32] warp sums, [39] #cols, [40..] columns
+  int32_t* cols_list = sint + 40;
+
+  for (int p = tid; p < npairs; p += T) {
+    const int pair = pair_begin + p;
+    const int s = pair / A.d, i = pair % A.d;
+    const int e = tb->edge_id[s];
+    prm[p] = make_pair_param(A.hash[size_t(e) * A.d + i]);
+    pcol[p] = tb->key_col[s];
+  }
+  if (!GLOBAL)
+    for (int j = tid; j < npairs * w; j += T) cnt[j] = 0;
+  if (tid == 0) {
+    // distinct key columns of the slab, in first-use order
+    int nc = 0;
+    for (int p = 0; p < npairs; p++) {
+      const int c = tb->key_col[(pair_begin + p) / A.d];
+      bool seen = false;
+      for (int q = 0; q < nc; q++) seen |= cols_list[q] == c;
+      if (!seen) cols_list[nc++] = c;
+    }
+    sint[39] = nc;
+  }
+  __syncthreads();
+  const int n_keycols = sint[39];
+
+  int32_t* gcnt = tb->counters + size_t(pair_begin) * w;
+  const int64_t n_tiles = (n_rows + R - 1) / R;
+  int64_t my_survivors = 0;
+
+  for (int64_t tile = cta_in_slab; tile < n_tiles; tile += n_ctas) {
+    const int64_t r0 = tile * R;
+    const int rows_in_tile = int(min(int64_t(R), n_rows - r0));
+
+    // ---------------- A. predicates and survivor compaction
+    int n_surv;
+    if (n_preds == 0) {
+      n_surv = rows_in_tile;
+    } else {
+      if (tid == 0) sint[0] = 0;
+      __syncthreads();
+      const int iters = (R + 4 * T - 1) / (4 * T);
+      for (int it = 0; it < iters; it++) {
+        const int base = 4 * (tid + it * T);
+        const int nvalid = max(0, min(4, rows_in_tile - base));
+        uint32_t m = (1u << nvalid) - 1u;
+        for (int q = 0; q < n_preds && m; q++) {
+          const DevPred& pq = tb->pred[q];
+          int64_t v[4];
+          load4(tb->col[pq.col], tb->dtype[pq.col], r0 + base, nvalid, vec, v);
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            if (!pred_holds(pq, v[k])) m &= ~(1u << k);
+        }
+        const int c = __popc(m);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        int wbase = 0;
+        if (lane == 31) wbase = atomicAdd(&sint[0], incl);
+        wbase = __shfl_sync(0xffffffffu, wbase, 31);
+        int pos = wbase + incl - c;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+          if ((m >> k) & 1u) surv[pos++] = uint16_t(base + k);
+      }
+      __syncthreads();
+      n_surv = sint[0];
+    }
+    my_survivors += n_surv;
+
+    // ---------------- B. per key column: aggregate equal keys, hash, update
+    for (int kc = 0; kc < n_keycols; kc++) {
+      const int c = cols_list[kc];
+      const void* kbase = tb->col[c];
+      const int32_t kdt = tb->dtype[c];
+      int n_entries = n_surv;
+      if (DEDUPE) {
+        for (int s = tid; s < M; s += T) {
+          mkey[s] = kEmptyKey;
+          mcnt[s] = 0;
+        }
+        __syncthreads();
+        const uint32_t mmask = uint32_t(M - 1);
+        for (int e = tid; e < n_surv; e += T) {
+          const int64_t row = r0 + (n_preds ? surv[e] : e);
+          const uint64_t x = key_field(load1(kbase, kdt, row));
+          uint32_t slot = map_slot(x, mmask);
+          bool done = false;
+          for (int probe = 0; probe < M; probe++) {
+            const unsigned long long prev = atomicCAS(&mkey[slot], kEmptyKey, (unsigned long long)x);
+            if (prev == kEmptyKey || prev == x) {
+              atomicAdd(&mcnt[slot], 1);
+              done = true;
+              break;
+            }
+            slot = (slot + 1) & mmask;
+          }
+          if (!done) set_status(A.status, CMP_ETIMEOUT);  // unreachable: M > tile rows
+        }
+        __syncthreads();
+        // compact occupied slots to the front (read all, barrier, write all)
+        const int spt = M / T;  // <= kMaxSlotsPerThread, host-checked
+        unsigned long long kx[kMaxSlotsPerThread];
+        int32_t kn[kMaxSlotsPerThread];
+        uint32_t valid = 0;
+#pragma unroll
+        for (int j = 0; j < kMaxSlotsPerThread; j++) {
+          kx[j] = kEmptyKey;
+          kn[j] = 0;
+          if (j < spt) {
+            kx[j] = mkey[tid * spt + j];
+            kn[j] = mcnt[tid * spt + j];
+            if (kx[j] != kEmptyKey) valid |= 1u << j;
+          }
+        }
+        const int mine = __popc(valid);
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        if (lane == 31) sint[1 + warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+          const int nw = T >> 5;
+          int v = lane < nw ? sint[1 + lane] : 0;
+          int s2 = v;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, s2, o);
+            if (lane >= o) s2 += t;
+          }
+          if (lane < nw) sint[1 + lane] = s2 - v;  // exclusive prefix per warp
+          if (lane == nw - 1) sint[0] = s2;
+        }
+        __syncthreads();
+        int pos = sint[1 + warp] + incl - mine;
+        n_entries = sint[0];
+#pragma unroll
+        for (int j = 0; j < kMaxSlotsPerThread; j++) {
+          if ((valid >> j) & 1u) {
+            mkey[pos] = kx[j];
+            mcnt[pos] = kn[j];
+            pos++;
+          }
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < n_entries; e += T) {
+        uint64_t x;
+        int32_t mult;
+        if (DEDUPE) {
+          x = mkey[e];
+          mult = mcnt[e];
+        } else {
+          const int64_t row = r0 + (n_preds ? surv[e] : e);
+          x = key_field(load1(kbase, kdt, row));
+          mult = 1;
+        }
+        const KeyPow kp = key_powers(x);
+        for (int p = 0; p < npairs; p++) {
+          if (pcol[p] != c) continue;
+          const PairParam q = prm[p];
+          const uint32_t h = cw_bucket<POW2>(q, kp, uint32_t(w));
+          const int32_t v = cw_sign(q, kp) * mult;
+          if (GLOBAL)
+            atomicAdd(gcnt + size_t(p) * w + h, v);
+          else
+            atomicAdd(cnt + size_t(p) * w + h, v);
+        }
+      }
+      __syncthreads();  // map / survivor list reused next
+    }
+  }
+
+  // ---------------- C. flush private counters, count survivors once per table
+  if (!GLOBAL) {
+    for (int j = tid; j < npairs * w; j += T) {
+      const int32_t v = cnt[j];
+      if (v) atomicAdd(gcnt + j, v);
+    }
+  }
+  if (pair_begin == 0 && tid == 0 && my_survivors)
+    atomicAdd(reinterpret_cast<unsigned long long*>(tb->survivors), (unsigned long long)my_survivors);
+}
+
+size_t build_smem_bytes(const BuildShape& s, int w) {
+  size_t b = align16(sizeof(PairParam) * s.max_pairs) + align16(sizeof(int32_t) * s.max_pairs);
+  if (s.mode == 1) b += align16(sizeof(int32_t) * size_t(s.smem_pairs) * w);
+  if (s.dedupe) b += align16(sizeof(unsigned long long) * size_t(s.map_slots)) + align16(sizeof(int32_t) * size_t(s.map_slots));
+  b += align16(sizeof(uint16_t) * s.tile_rows);
+  b += sizeof(int32_t) * (40 + CMP_MAX_COLS);
+  return b;
+}
+
+template <bool G, bool D, bool P>
+static cudaError_t launch_one(const BuildArgs& a, const BuildShape& s, cudaStream_t st) {
+  auto k = k_sketch_build<G, D, P>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem_bytes));
+  if (e != cudaSuccess) return e;
+  k<<<s.grid, s.threads, s.smem_bytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t st) {
+  const bool pow2 = (a.w & (a.w - 1)) == 0;
+  const bool g = s.mode == 2, d = s.dedupe != 0;
+  if (g) {
+    if (d) return pow2 ? launch_one<true, true, true>(a, s, st) : launch_one<true, true, false>(a, s, st);
+    return pow2 ? launch_one<true, false, true>(a, s, st) : launch_one<true, false, false>(a, s, st);
+  }
+  if (d) return pow2 ? launch_one<false, true, true>(a, s, st) : launch_one<false, true, false>(a, s, st);
+  return pow2 ? launch_one<false, false, true>(a, s, st) : launch_one<false, false, false>(a, s, st);
+}
+
+__global__ void k_zero_spans(const ZeroSpan* __restrict__ spans, int32_t n) {
+  // one block-stride pass per span; spans are 4-byte multiples
+  for (int32_t s = blockIdx.y; s < n; s += gridDim.y) {
+    const ZeroSpan z = spans[s];
+    uint32_t* p = reinterpret_cast<uint32_t*>(z.ptr);
+    const int64_t words = z.bytes / 4;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < words; i += int64_t(gridDim.x) * blockDim.x)
+      p[i] = 0;
+  }
+}
+
+cudaError_t launch_zero_spans(const ZeroSpan* spans_dev, int32_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grid(64, unsigned(n < 1024 ? n : 1024));
+  k_zero_spans<<<grid, 256, 0, st>>>(spans_dev, n);
+  return cudaGetLastError();
+}
+
+}  // namespace cmpk

@@ -1,0 +1,195 @@
+// Internal device/host definitions of libcompass (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "compass.h"
+
+namespace cmpk {
+
+// ------------------------------------------------------------------ constants
+constexpr uint64_t kP61 = (1ull << 61) - 1;     // Mersenne prime of the CW hash family
+constexpr uint32_t kM31 = 0x7FFFFFFFu;
+constexpr uint64_t kM30 = (1ull << 30) - 1;
+constexpr unsigned long long kEmptyKey = ~0ull;  // never a field element (< 2^61)
+
+// ------------------------------------------------------- arithmetic mod 2^61-1
+// A field element v < 2^61 is held as two limbs v = hi * 2^31 + lo (lo < 2^31,
+// hi < 2^30) so that every partial product fits 62 bits and three of them can be
+// summed in one uint64 before a single Mersenne fold (2^61 = 1, 2^62 = 2 mod p).
+struct Limb {
+  uint32_t lo, hi;
+};
+
+__device__ __forceinline__ Limb limb(uint64_t v) { return {uint32_t(v) & kM31, uint32_t(v >> 31)}; }
+__device__ __forceinline__ uint64_t fold61(uint64_t v) { return (v & kP61) + (v >> 61); }
+__device__ __forceinline__ uint64_t canon61(uint64_t v) { return v >= kP61 ? v - kP61 : v; }
+
+// key -> residue of the sign-extended key mod p, in [0, p).  For k < 0 write
+// k = -1 - m with m = ~k >= 0; then k mod p = p - 1 - (m mod p).
+__device__ __forceinline__ uint64_t key_field(int64_t k) {
+  const uint64_t s = uint64_t(k >> 63);
+  const uint64_t m = uint64_t(k) ^ s;
+  const uint64_t y = canon61(fold61(m));  // m < 2^64: fold < p + 8, one subtraction
+  return s ? (kP61 - 1 - y) : y;
+}
+
+// (a * b) mod p from limbs.  t0 < 2^62, t1 < 2^62, t2 < 2^60 and
+// a*b = t2 2^62 + t1 2^31 + t0 = 2 t2 + (t1 >> 30) + (t1 & (2^30-1)) 2^31 + t0 (mod p);
+// the sum is < 2^63 + 2^32.
+__device__ __forceinline__ uint64_t mulmod61(Limb a, Limb b) {
+  const uint64_t t0 = uint64_t(a.lo) * b.lo;
+  const uint64_t t1 = uint64_t(a.lo) * b.hi + uint64_t(a.hi) * b.lo;
+  const uint64_t t2 = uint64_t(a.hi) * b.hi;
+  const uint64_t s = t0 + (t1 >> 30) + ((t1 & kM30) << 31) + 2 * t2;
+  return canon61(fold61(s));
+}
+
+// Hash parameters of one (edge, row) pre-split into limbs (48 bytes, 16-aligned).
+struct __align__(16) PairParam {
+  uint32_t a_lo, a_hi, c1_lo, c1_hi, c2_lo, c2_hi, c3_lo, c3_hi;
+  uint64_t b, c0;
+};
+
+__host__ __device__ inline PairParam make_pair_param(const cmp_hash& h) {
+  PairParam q;
+  q.a_lo = uint32_t(h.a) & kM31;
+  q.a_hi = uint32_t(h.a >> 31);
+  q.c1_lo = uint32_t(h.c1) & kM31;
+  q.c1_hi = uint32_t(h.c1 >> 31);
+  q.c2_lo = uint32_t(h.c2) & kM31;
+  q.c2_hi = uint32_t(h.c2 >> 31);
+  q.c3_lo = uint32_t(h.c3) & kM31;
+  q.c3_hi = uint32_t(h.c3 >> 31);
+  q.b = h.b;
+  q.c0 = h.c0;
+  return q;
+}
+
+// Powers of the key, shared by every (sketch, row) that hashes the same key.
+struct KeyPow {
+  Limb x, x2, x3;
+};
+
+__device__ __forceinline__ KeyPow key_powers(uint64_t x) {
+  KeyPow k;
+  k.x = limb(x);
+  const uint64_t x2 = mulmod61(k.x, k.x);
+  k.x2 = limb(x2);
+  k.x3 = limb(mulmod61(k.x2, k.x));
+  return k;
+}
+
+// Bucket: ((a x + b) mod p) mod w.  Sum bound: t0 + (t1>>30) + ((t1&M30)<<31) + 2 t2 + b
+// < 2^62 + 2^32 + 3 * 2^61 < 2^64.
+template <bool POW2>
+__device__ __forceinline__ uint32_t cw_bucket(const PairParam& q, const KeyPow& k, uint32_t w) {
+  const uint64_t t0 = uint64_t(q.a_lo) * k.x.lo;
+  const uint64_t t1 = uint64_t(q.a_lo) * k.x.hi + uint64_t(q.a_hi) * k.x.lo;
+  const uint64_t t2 = uint64_t(q.a_hi) * k.x.hi;
+  const uint64_t s = t0 + (t1 >> 30) + ((t1 & kM30) << 31) + 2 * t2 + q.b;
+  const uint64_t r = canon61(fold61(s));
+  if (POW2) return uint32_t(r) & (w - 1);
+  return uint32_t(r % w);
+}
+
+// Sign: parity of (c3 x^3 + c2 x^2 + c1 x + c0) mod p, as +1 / -1.  The three products
+// are summed by limb position: S0 < 3 * 2^62, S1 < 6 * 2^61, S2 < 3 * 2^60, and
+// fold(S0) + (S1>>30) + ((S1&M30)<<31) + 2 S2 + c0 < 6 * 2^61 + 2^35 < 2^64.
+__device__ __forceinline__ int cw_sign(const PairParam& q, const KeyPow& k) {
+  const uint64_t S0 = uint64_t(q.c1_lo) * k.x.lo + uint64_t(q.c2_lo) * k.x2.lo + uint64_t(q.c3_lo) * k.x3.lo;
+  const uint64_t S1 = uint64_t(q.c1_lo) * k.x.hi + uint64_t(q.c1_hi) * k.x.lo + uint64_t(q.c2_lo) * k.x2.hi +
+                      uint64_t(q.c2_hi) * k.x2.lo + uint64_t(q.c3_lo) * k.x3.hi + uint64_t(q.c3_hi) * k.x3.lo;
+  const uint64_t S2 = uint64_t(q.c1_hi) * k.x.hi + uint64_t(q.c2_hi) * k.x2.hi + uint64_t(q.c3_hi) * k.x3.hi;
+  const uint64_t v = fold61(S0) + (S1 >> 30) + ((S1 & kM30) << 31) + 2 * S2 + q.c0;
+  const uint64_t r = canon61(fold61(v));
+  return 1 - 2 * int(r & 1);
+}
+
+// ------------------------------------------------------------ build structures
+struct DevPred {
+  int32_t col, op;
+  int64_t lo, hi;
+  const uint32_t* bitmap;
+  int64_t nbits;
+};
+
+struct DevTable {
+  int64_t n_rows;
+  int32_t n_cols, n_preds, n_sketches;
+  int32_t vec_ok;  // every column 16-byte aligned: 128-bit loads allowed
+  const void* col[CMP_MAX_COLS];
+  int32_t dtype[CMP_MAX_COLS];
+  DevPred pred[CMP_MAX_PREDS];
+  int32_t key_col[CMP_MAX_SKETCHES];
+  int32_t edge_id[CMP_MAX_SKETCHES];
+  int32_t* counters;   // [n_sketches][d][w]
+  int64_t* survivors;  // one int64
+};
+
+// One (table, slab of (sketch,row) pairs) handled by n_ctas consecutive CTAs.
+struct BuildItem {
+  int32_t table;
+  int32_t pair_begin, pair_end;
+  int32_t n_ctas;
+  int32_t first_cta;
+  int32_t pad;
+};
+
+struct BuildShape {
+  int32_t mode;            // 1 smem, 2 global
+  int32_t dedupe;          // 0 / 1
+  int32_t threads;
+  int32_t tile_rows;
+  int32_t map_slots;       // power of two >= 2 * tile_rows (dedupe only)
+  int32_t max_pairs;       // max pairs of any item (sizes the parameter area)
+  int32_t smem_pairs;      // pairs whose counters live in shared memory (mode 1)
+  int32_t pairs_per_slab;  // single-table launches
+  int32_t ctas_per_slab;   // single-table launches
+  int32_t grid;
+  size_t smem_bytes;
+};
+
+struct BuildArgs {
+  DevTable table;             // single-table launch (items == nullptr)
+  const DevTable* tables;     // batched launch
+  const BuildItem* items;
+  const int32_t* cta_item;    // [grid] item of each CTA
+  const cmp_hash* hash;       // [n_edges * d]
+  int32_t* status;
+  int32_t d, w, n_edges;
+  int32_t threads, tile_rows, map_slots, max_pairs, smem_pairs;
+  int32_t pairs_per_slab, ctas_per_slab;
+};
+
+// Plan blob (host-encoded, device-read) for the batched build.
+struct BuildPlanHdr {
+  uint64_t magic;
+  int32_t version, n_tables, n_items, d, w, n_edges;
+  BuildShape shape;
+  int64_t off_tables, off_items, off_cta_item, off_zero, n_zero;  // byte offsets in the blob
+  int64_t total_bytes;
+};
+struct ZeroSpan {
+  void* ptr;
+  int64_t bytes;
+};
+constexpr uint64_t kBuildPlanMagic = 0x434d504255494c44ull;  // "CMPBUILD"
+
+// device status helper: first error wins
+__device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// launchers implemented in the .cu files
+size_t build_smem_bytes(const BuildShape& s, int w);
+cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t st);
+cudaError_t launch_zero_spans(const ZeroSpan* spans_dev, int32_t n, cudaStream_t st);
+
+int sm_count();
+size_t smem_optin_bytes();
+
+}  // namespace cmpk

@@ -1,0 +1,121 @@
+"""Host-side tests of the C ABI: the library loads, exports every symbol the header
+declares, and rejects bad arguments before touching the GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def K():
+    from paper_2102_02440_gb300 import build_lib, compass
+    build_lib.build()
+    return compass
+
+
+def _declared():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(cmp_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(K):
+    L = K.lib()
+    declared = _declared()
+    assert len(declared) >= 7
+    missing = [n for n in declared if getattr(L, n, None) is None]
+    assert not missing, missing
+
+
+def test_status_strings(K):
+    assert K.status_str(0) == "ok"
+    assert "invalid" in K.status_str(-1)
+    assert K.lib().cmp_abi_version() == 1
+
+
+def test_hash_params_match_oracle_generator(K, orc):
+    for seed, ne, d in ((0, 1, 1), (0xC0FFEE, 5, 11), (2**63 + 5, 3, 64)):
+        assert np.array_equal(K.hash_params_u64(seed, ne, d), orc.hash_params(seed, ne, d))
+    with pytest.raises(K.CompassError):
+        K.cmp_hash_params(1, 1, 0)
+    with pytest.raises(K.CompassError):
+        K.cmp_hash_params(1, 1, 65)
+
+
+def _desc(K, n_rows=10, ncols=1, preds=(), key_col=(0,), edge_id=(0,), dtype=0):
+    cols = (K.cmp_col * max(ncols, 1))(*[K.cmp_col(0x1000 * (i + 1), dtype, 0) for i in range(ncols)])
+    pr = (K.cmp_pred * max(len(preds), 1))(*preds)
+    kc = (C.c_int32 * max(len(key_col), 1))(*key_col)
+    ei = (C.c_int32 * max(len(edge_id), 1))(*edge_id)
+    t = K.cmp_table(n_rows, ncols, len(preds), len(key_col), 0, cols, pr, kc, ei)
+    t._keep = (cols, pr, kc, ei)
+    return t
+
+
+@pytest.mark.parametrize("case", ["d0", "d65", "w0", "rows_neg", "rows_big", "bad_keycol", "bad_edge",
+                                  "bad_dtype", "bad_pred_col", "bad_pred_op", "in_no_bitmap", "null_counters",
+                                  "too_many_sketches"])
+def test_build_rejects_bad_arguments(K, case):
+    d, w, ne = 4, 64, 2
+    t = _desc(K)
+    if case == "d0":
+        d = 0
+    elif case == "d65":
+        d = 65
+    elif case == "w0":
+        w = 0
+    elif case == "rows_neg":
+        t.n_rows = -1
+    elif case == "rows_big":
+        t.n_rows = 2 ** 31
+    elif case == "bad_keycol":
+        t = _desc(K, key_col=(3,))
+    elif case == "bad_edge":
+        t = _desc(K, edge_id=(2,))
+    elif case == "bad_dtype":
+        t = _desc(K, dtype=7)
+    elif case == "bad_pred_col":
+        t = _desc(K, preds=[K.cmp_pred(5, 0, 0, 1, None, 0)])
+    elif case == "bad_pred_op":
+        t = _desc(K, preds=[K.cmp_pred(0, 9, 0, 1, None, 0)])
+    elif case == "in_no_bitmap":
+        t = _desc(K, preds=[K.cmp_pred(0, 2, 0, 0, None, 100)])
+    elif case == "too_many_sketches":
+        t = _desc(K, key_col=tuple([0] * 17), edge_id=tuple([0] * 17))
+    counters = 0 if case == "null_counters" else 0x2000
+    st = K.lib().cmp_sketch_build(C.byref(t), d, w, 0x3000, ne, counters, 0x4000, 0x5000, None, None)
+    assert st == K.CMP_EINVAL
+
+
+def test_build_rejects_bad_cfg(K):
+    t = _desc(K)
+    for cfg in (K.cmp_build_cfg.make(threads=48), K.cmp_build_cfg.make(tile_rows=100),
+                K.cmp_build_cfg.make(mode=3), K.cmp_build_cfg.make(threads=128, tile_rows=4096, dedupe=1)):
+        st = K.lib().cmp_sketch_build(C.byref(t), 4, 64, 0x3000, 2, 0x2000, 0x4000, 0x5000, C.byref(cfg), None)
+        assert st == K.CMP_EINVAL
+
+
+def test_batched_plan_encoding_host_logic(K):
+    """Plan sizing and encoding run on the host; the blob is self-describing."""
+    tabs = [_desc(K, n_rows=n, key_col=(0, 0), edge_id=(0, 1)) for n in (0, 1, 5000, 10_000_000)]
+    nb = K.cmp_build_plan_bytes(tabs, 11, 1024, None)
+    assert nb > 0
+    buf = np.zeros(nb, np.uint8)
+    with pytest.raises(K.CompassError):
+        K.cmp_build_plan_encode(tabs, 11, 1024, 2, [0x1000] * 4, 0x2000, None, buf.ctypes.data, nb - 16)
+    with pytest.raises(K.CompassError):   # edge id 1 beyond n_edges = 1
+        K.cmp_build_plan_encode(tabs, 11, 1024, 1, [0x1000] * 4, 0x2000, None, buf.ctypes.data, nb)
+    K.cmp_build_plan_encode(tabs, 11, 1024, 2, [0x1000] * 4, 0x2000, None, buf.ctypes.data, nb)
+    hdr = buf[:8].view(np.uint64)[0]
+    assert hdr == 0x434D504255494C44
+    # cmp_sketch_build_batched rejects a blob that is not a plan
+    junk = np.zeros(nb, np.uint8)
+    assert K.lib().cmp_sketch_build_batched(junk.ctypes.data, 0x1000, 0x2000, 0x3000, None) == K.CMP_EINVAL
