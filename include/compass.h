@@ -154,6 +154,68 @@ cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_tables, int3
 cmp_status cmp_sketch_build_batched(const void* plan_host, const void* plan_dev, const cmp_hash* hash_dev,
                                     int32_t* status_dev, void* stream);
 
+/* ------------------------------------------------------------------- estimation */
+
+/* Presort of sketch rows by magnitude (prepares the merged contraction of Sec. 4.2: the
+ * merged value of a bucket tuple is the operand of minimum |.|, so every sum over a
+ * merged sketch splits into sums over buckets above / below a magnitude threshold).
+ * For each of the n_rows rows of length w in counters_dev (row-major), writes the
+ * bucket permutation that sorts the row by (|C|, bucket index) ascending into perm_dev
+ * and the sorted magnitudes into abs_sorted_dev (both [n_rows][w]).  This version
+ * sorts each row in shared memory and handles w <= 16384 (CMP_EUNSUPPORTED above);
+ * cmp_presort_ws_bytes reports the workspace it needs (0 here). */
+size_t cmp_presort_ws_bytes(int64_t n_rows, int32_t w);
+cmp_status cmp_presort(const int32_t* counters_dev, int64_t n_rows, int32_t w, uint32_t* abs_sorted_dev,
+                       int32_t* perm_dev, void* ws_dev, size_t ws_bytes, void* stream);
+
+/* A join graph whose sketches have been built and presorted.  Edge e joins tables
+ * edge_u[e] and edge_v[e]; endpoint 0 is the edge_u side, 1 the edge_v side.  All
+ * arrays are HOST arrays; entries of sketch/abs_sorted/perm are DEVICE pointers to the
+ * endpoint's [d][w] sketch (int32), sorted magnitudes (uint32) and permutation (int32). */
+typedef struct {
+  int32_t n_tables;                  /* 1 .. CMP_MAX_TABLES */
+  int32_t n_edges;
+  const int32_t* edge_u;             /* [n_edges] */
+  const int32_t* edge_v;             /* [n_edges] */
+  const int32_t* const* sketch;      /* [2 * n_edges] */
+  const uint32_t* const* abs_sorted; /* [2 * n_edges] */
+  const int32_t* const* perm;        /* [2 * n_edges] */
+  const int64_t* survivors_dev;      /* device [n_tables]: exact selected counts */
+} cmp_graph;
+
+/* Estimates of many sub-plans, possibly of many graphs, in one launch sequence
+ * (Sec. 5, Alg. 1 calls the estimate for every enumerated sub-plan; Sec. 4.2 composes the
+ * attribute-level sketches of the sub-plan's joins by merging).  Sub-plan q is table set
+ * sub_mask[q] (bit t = table t) of graph sub_graph[q]; it must be connected in the graph
+ * induced by its tables (cross products are excluded, Sec. 2 "Plan enumeration"), else
+ * CMP_EINVAL.  Its edges are every edge with both ends in the set.
+ *   |S| = 1: the estimate is the exact selected count (push-down, Sec. 2).
+ *   |S| >= 2: for every sketch row i, the exact integer
+ *       E_i = sum over all bucket assignments j of the sub-plan's edges of
+ *             prod over tables t of M_t(j restricted to t's edges),
+ *     where M_t is t's merged sketch: the value of the sketch (among t's sketches of
+ *     the sub-plan's edges, in ascending edge id) whose bucket has the minimum |value|,
+ *     the first such on ties (the merge equation of Sec. 4.2, iterated).  For one edge
+ *     this is the Fast-AGMS inner product of Sec. 3.2.  The estimate is the median of
+ *     E_0..E_{d-1} (Sec. 3.2), exact, rounded once to double (even d: mean of the two
+ *     middle values).  Sub-plans whose edges contain more than one independent cycle
+ *     return CMP_EUNSUPPORTED from the plan step.
+ * Host steps: cmp_estimate_plan_bytes sizes the plan and the device workspace, and
+ * cmp_estimate_plan_encode writes the plan; the caller copies it to the device.  Then
+ * cmp_estimate enqueues the launches.
+ *   est_dev      [n_sub] double; NaN where a row left the int128 range (and status
+ *                gets CMP_EOVERFLOW)
+ *   row_est_dev  NULL or [n_sub][d][2] int64: each exact row estimate as a little-endian
+ *                two's-complement int128 (low word first) */
+cmp_status cmp_estimate_plan_bytes(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
+                                   const int32_t* sub_graph, const uint64_t* sub_mask, size_t* plan_bytes,
+                                   size_t* ws_bytes);
+cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
+                                    const int32_t* sub_graph, const uint64_t* sub_mask, void* plan_host,
+                                    size_t plan_bytes);
+cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_dev, size_t ws_bytes, double* est_dev,
+                        int64_t* row_est_dev, int32_t* status_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

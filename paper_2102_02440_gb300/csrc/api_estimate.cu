@@ -1,0 +1,283 @@
+// C ABI: presort and the batched sub-plan estimate (host planning + launches).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "estimate.cuh"
+
+using namespace cmpk;
+
+namespace {
+
+constexpr int kCondChunk = 64;   // conditioning values per work item (cycles)
+constexpr int kEstThreads = 512;
+
+struct PlanOut {
+  std::vector<EstSub> subs;
+  std::vector<EstOp> ops;
+  std::vector<EstIn> ins;
+  std::vector<EstItem> items;
+  int32_t max_slots = 0, max_in = 1;
+};
+
+bool graph_ok(const cmp_graph& g) {
+  if (g.n_tables < 1 || g.n_tables > CMP_MAX_TABLES || g.n_edges < 0) return false;
+  if (g.n_edges && (!g.edge_u || !g.edge_v || !g.sketch || !g.abs_sorted || !g.perm)) return false;
+  if (!g.survivors_dev) return false;
+  for (int e = 0; e < g.n_edges; e++) {
+    if (g.edge_u[e] < 0 || g.edge_u[e] >= g.n_tables || g.edge_v[e] < 0 || g.edge_v[e] >= g.n_tables) return false;
+    if (g.edge_u[e] == g.edge_v[e]) return false;
+    for (int end = 0; end < 2; end++)
+      if (!g.sketch[2 * e + end] || !g.abs_sorted[2 * e + end] || !g.perm[2 * e + end]) return false;
+  }
+  return true;
+}
+
+// Plan one sub-plan: spanning tree by BFS from the lowest table id (edges in id order),
+// non-tree edges conditioned, post-order operations for every non-leaf table.
+cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int32_t sub_index, PlanOut* P) {
+  const int nt = g.n_tables;
+  if (mask == 0 || (nt < 64 && (mask >> nt) != 0)) return CMP_EINVAL;
+  std::vector<int> es;
+  for (int e = 0; e < g.n_edges; e++)
+    if (((mask >> g.edge_u[e]) & 1) && ((mask >> g.edge_v[e]) & 1)) es.push_back(e);
+  int root = 0;
+  while (!((mask >> root) & 1)) root++;
+  std::vector<int> order{root}, parent_edge(nt, -1);
+  std::vector<char> seen(nt, 0), tree(g.n_edges, 0);
+  seen[root] = 1;
+  for (size_t h = 0; h < order.size(); h++) {
+    const int t = order[h];
+    for (int e : es) {
+      const int o = g.edge_u[e] == t ? g.edge_v[e] : (g.edge_v[e] == t ? g.edge_u[e] : -1);
+      if (o < 0 || seen[o]) continue;
+      seen[o] = 1;
+      parent_edge[o] = e;
+      tree[e] = 1;
+      order.push_back(o);
+    }
+  }
+  if (int(order.size()) != __builtin_popcountll(mask)) return CMP_EINVAL;  // not connected
+  EstSub sb;
+  std::memset(&sb, 0, sizeof(sb));
+  sb.op_begin = int32_t(P->ops.size());
+  sb.item_begin = int64_t(P->items.size());
+  if (order.size() == 1) {
+    sb.single = 1;
+    sb.sv = g.survivors_dev + root;
+    P->subs.push_back(sb);
+    return CMP_OK;
+  }
+  std::vector<int> cond;
+  for (int e : es)
+    if (!tree[e]) cond.push_back(e);
+  if (cond.size() > 1) return CMP_EUNSUPPORTED;  // more than one independent cycle
+  std::vector<int> deg(nt, 0);
+  for (int e : es) deg[g.edge_u[e]]++, deg[g.edge_v[e]]++;
+  auto is_leaf = [&](int t) { return t != root && deg[t] == 1; };
+  auto end_of = [&](int e, int t) { return g.edge_u[e] == t ? 0 : 1; };
+  std::vector<int> slot_of(nt, -1);
+  std::vector<char> slot_busy;
+  for (size_t h = order.size(); h-- > 0;) {
+    const int t = order[h];
+    if (is_leaf(t)) continue;
+    EstOp op;
+    op.k = 0;
+    op.p = -1;
+    op.out_slot = -1;
+    op.in_begin = int32_t(P->ins.size());
+    std::vector<int> consumed;
+    for (int e : es) {
+      if (g.edge_u[e] != t && g.edge_v[e] != t) continue;
+      const int me = end_of(e, t);
+      EstIn x;
+      std::memset(&x, 0, sizeof(x));
+      x.s = g.sketch[2 * e + me];
+      x.abs = g.abs_sorted[2 * e + me];
+      x.perm = g.perm[2 * e + me];
+      if (e == parent_edge[t]) {
+        x.kind = kInOutput;
+        op.p = op.k;
+      } else if (tree[e]) {
+        const int child = g.edge_u[e] == t ? g.edge_v[e] : g.edge_u[e];
+        if (is_leaf(child)) {
+          x.kind = kInLeaf;
+          x.msk = g.sketch[2 * e + end_of(e, child)];
+        } else {
+          x.kind = kInSlot;
+          x.slot = slot_of[child];
+          consumed.push_back(slot_of[child]);
+        }
+      } else {
+        x.kind = kInCond;
+      }
+      P->ins.push_back(x);
+      op.k++;
+    }
+    if (op.p >= 0) {  // output slot: a free slot not read by this operation
+      int s = -1;
+      for (size_t q = 0; q < slot_busy.size(); q++)
+        if (!slot_busy[q]) {
+          s = int(q);
+          break;
+        }
+      if (s < 0) {
+        s = int(slot_busy.size());
+        slot_busy.push_back(0);
+      }
+      slot_busy[s] = 1;
+      op.out_slot = s;
+      slot_of[t] = s;
+    }
+    for (int s : consumed) slot_busy[s] = 0;
+    P->max_slots = std::max<int32_t>(P->max_slots, int32_t(slot_busy.size()));
+    P->max_in = std::max<int32_t>(P->max_in, op.k);
+    P->ops.push_back(op);
+  }
+  sb.n_ops = int32_t(P->ops.size()) - sb.op_begin;
+  sb.n_chunks = cond.empty() ? 1 : (w + kCondChunk - 1) / kCondChunk;
+  P->subs.push_back(sb);
+  for (int i = 0; i < d; i++)
+    for (int ch = 0; ch < sb.n_chunks; ch++) {
+      EstItem it;
+      it.sub = sub_index;
+      it.row = i;
+      it.c0 = cond.empty() ? 0 : ch * kCondChunk;
+      it.c1 = cond.empty() ? 1 : std::min(w, (ch + 1) * kCondChunk);
+      P->items.push_back(it);
+    }
+  return CMP_OK;
+}
+
+cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
+                    const int32_t* sub_graph, const uint64_t* sub_mask, PlanOut* P, EstPlanHdr* H) {
+  if (!graphs || n_graphs < 1 || d < 1 || d > CMP_MAX_D || w < 1 || w > CMP_MAX_W || n_sub < 0) return CMP_EINVAL;
+  if (n_sub && (!sub_graph || !sub_mask)) return CMP_EINVAL;
+  for (int32_t gi = 0; gi < n_graphs; gi++)
+    if (!graph_ok(graphs[gi])) return CMP_EINVAL;
+  for (int32_t q = 0; q < n_sub; q++) {
+    if (sub_graph[q] < 0 || sub_graph[q] >= n_graphs) return CMP_EINVAL;
+    const cmp_status st = plan_sub(graphs[sub_graph[q]], sub_mask[q], d, w, q, P);
+    if (st != CMP_OK) return st;
+  }
+  std::memset(H, 0, sizeof(*H));
+  H->magic = kEstPlanMagic;
+  H->version = 1;
+  H->d = d;
+  H->w = w;
+  H->max_slots = P->max_slots;
+  H->max_in = P->max_in;
+  H->threads = kEstThreads;
+  const int64_t cap = int64_t(sm_count()) * 2;
+  H->grid = int32_t(std::max<int64_t>(1, std::min<int64_t>(int64_t(P->items.size()), cap)));
+  H->n_sub = n_sub;
+  H->n_ops = int64_t(P->ops.size());
+  H->n_in = int64_t(P->ins.size());
+  H->n_items = int64_t(P->items.size());
+  size_t off = align16(sizeof(EstPlanHdr));
+  H->off_subs = int64_t(off);
+  off += align16(sizeof(EstSub) * P->subs.size());
+  H->off_ops = int64_t(off);
+  off += align16(sizeof(EstOp) * P->ops.size());
+  H->off_in = int64_t(off);
+  off += align16(sizeof(EstIn) * P->ins.size());
+  H->off_items = int64_t(off);
+  off += align16(sizeof(EstItem) * P->items.size());
+  H->total_bytes = int64_t(off);
+  H->scratch_per_cta = int64_t(P->max_slots) * w + 2 * int64_t(P->max_in) * (int64_t(w) + 1);
+  H->ws_bytes = int64_t(align16(sizeof(i128) * P->items.size()) + align16(sizeof(int32_t) * P->items.size()) +
+                        sizeof(i128) * size_t(H->scratch_per_cta) * size_t(H->grid));
+  return CMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t cmp_presort_ws_bytes(int64_t n_rows, int32_t w) {
+  (void)n_rows;
+  (void)w;
+  return 0;
+}
+
+cmp_status cmp_presort(const int32_t* counters_dev, int64_t n_rows, int32_t w, uint32_t* abs_sorted_dev,
+                       int32_t* perm_dev, void* ws_dev, size_t ws_bytes, void* stream) {
+  (void)ws_dev;
+  (void)ws_bytes;
+  if (n_rows < 0 || w < 1 || w > CMP_MAX_W) return CMP_EINVAL;
+  if (n_rows > 0 && (!counters_dev || !abs_sorted_dev || !perm_dev)) return CMP_EINVAL;
+  if (w > 16384) return CMP_EUNSUPPORTED;
+  return launch_presort(counters_dev, n_rows, w, abs_sorted_dev, perm_dev, reinterpret_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? CMP_OK
+             : CMP_ECUDA;
+}
+
+cmp_status cmp_estimate_plan_bytes(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
+                                   const int32_t* sub_graph, const uint64_t* sub_mask, size_t* plan_bytes,
+                                   size_t* ws_bytes) {
+  if (!plan_bytes || !ws_bytes) return CMP_EINVAL;
+  PlanOut P;
+  EstPlanHdr H;
+  const cmp_status st = plan_all(graphs, n_graphs, d, w, n_sub, sub_graph, sub_mask, &P, &H);
+  if (st != CMP_OK) return st;
+  *plan_bytes = size_t(H.total_bytes);
+  *ws_bytes = size_t(H.ws_bytes);
+  return CMP_OK;
+}
+
+cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
+                                    const int32_t* sub_graph, const uint64_t* sub_mask, void* plan_host,
+                                    size_t plan_bytes) {
+  if (!plan_host) return CMP_EINVAL;
+  PlanOut P;
+  EstPlanHdr H;
+  const cmp_status st = plan_all(graphs, n_graphs, d, w, n_sub, sub_graph, sub_mask, &P, &H);
+  if (st != CMP_OK) return st;
+  if (plan_bytes < size_t(H.total_bytes)) return CMP_EWORKSPACE;
+  unsigned char* b = static_cast<unsigned char*>(plan_host);
+  std::memset(b, 0, size_t(H.total_bytes));
+  std::memcpy(b, &H, sizeof(H));
+  if (!P.subs.empty()) std::memcpy(b + H.off_subs, P.subs.data(), sizeof(EstSub) * P.subs.size());
+  if (!P.ops.empty()) std::memcpy(b + H.off_ops, P.ops.data(), sizeof(EstOp) * P.ops.size());
+  if (!P.ins.empty()) std::memcpy(b + H.off_in, P.ins.data(), sizeof(EstIn) * P.ins.size());
+  if (!P.items.empty()) std::memcpy(b + H.off_items, P.items.data(), sizeof(EstItem) * P.items.size());
+  return CMP_OK;
+}
+
+cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_dev, size_t ws_bytes, double* est_dev,
+                        int64_t* row_est_dev, int32_t* status_dev, void* stream) {
+  if (!plan_host || !plan_dev) return CMP_EINVAL;
+  EstPlanHdr H;
+  std::memcpy(&H, plan_host, sizeof(H));
+  if (H.magic != kEstPlanMagic || H.version != 1) return CMP_EINVAL;
+  if (H.n_sub > 0 && !est_dev) return CMP_EINVAL;
+  if (ws_bytes < size_t(H.ws_bytes) || (H.ws_bytes > 0 && !ws_dev)) return CMP_EWORKSPACE;
+  const unsigned char* pd = static_cast<const unsigned char*>(plan_dev);
+  unsigned char* ws = static_cast<unsigned char*>(ws_dev);
+  EstArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.subs = reinterpret_cast<const EstSub*>(pd + H.off_subs);
+  a.ops = reinterpret_cast<const EstOp*>(pd + H.off_ops);
+  a.inputs = reinterpret_cast<const EstIn*>(pd + H.off_in);
+  a.items = reinterpret_cast<const EstItem*>(pd + H.off_items);
+  a.partial = reinterpret_cast<i128*>(ws);
+  a.partial_ovf = reinterpret_cast<int32_t*>(ws + align16(sizeof(i128) * size_t(H.n_items)));
+  a.scratch = ws + align16(sizeof(i128) * size_t(H.n_items)) + align16(sizeof(int32_t) * size_t(H.n_items));
+  a.scratch_per_cta = H.scratch_per_cta;
+  a.n_items = H.n_items;
+  a.n_sub = H.n_sub;
+  a.d = H.d;
+  a.w = H.w;
+  a.max_slots = H.max_slots;
+  a.max_in = H.max_in;
+  a.grid = H.grid;
+  a.threads = H.threads;
+  a.status = status_dev;
+  return launch_estimate(a, est_dev, row_est_dev, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? CMP_OK
+                                                                                                          : CMP_ECUDA;
+}
+
+}  // extern "C"

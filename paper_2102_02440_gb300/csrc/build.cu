@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
   unsigned char* sp = smem;
   PairParam* prm = reinterpret_cast<PairParam*>(sp);
   sp += align16(sizeof(PairParam) * A.max_pairs);
-  int32_t* pcol = reinterpret_cast<int32_t*>(sp);  // key column of each pair
+  int32_t* plist = reinterpret_cast<int32_t*>(sp);  // slab pairs grouped by key column
   sp += align16(sizeof(int32_t) * A.max_pairs);
   int32_t* cnt = reinterpret_cast<int32_t*>(sp);  // private counters (mode 1)
   if (!GLOBAL) sp += align16(sizeof(int32_t) * size_t(A.smem_pairs) * w);
@@ -119,19 +119,20 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
   uint16_t* surv = reinterpret_cast<uint16_t*>(sp);
   sp += align16(sizeof(uint16_t) * R);
   int32_t* sint = reinterpret_cast<int32_t*>(sp);  // [0] tail, [1..32] warp sums, [39] #cols, [40..] columns
-  int32_t* cols_list = sint + 40;
+  int32_t* cols_list = sint + 40;                  // [CMP_MAX_COLS]
+  int32_t* colstart = sint + 40 + CMP_MAX_COLS;    // [CMP_MAX_COLS + 1]
 
   for (int p = tid; p < npairs; p += T) {
     const int pair = pair_begin + p;
     const int s = pair / A.d, i = pair % A.d;
     const int e = tb->edge_id[s];
     prm[p] = make_pair_param(A.hash[size_t(e) * A.d + i]);
-    pcol[p] = tb->key_col[s];
   }
   if (!GLOBAL)
     for (int j = tid; j < npairs * w; j += T) cnt[j] = 0;
   if (tid == 0) {
-    // distinct key columns of the slab, in first-use order
+    // distinct key columns of the slab in first-use order, and the slab's pairs grouped
+    // by column: plist[colstart[k] .. colstart[k+1]) are the pairs hashing column k
     int nc = 0;
     for (int p = 0; p < npairs; p++) {
       const int c = tb->key_col[(pair_begin + p) / A.d];
@@ -139,6 +140,13 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
       for (int q = 0; q < nc; q++) seen |= cols_list[q] == c;
       if (!seen) cols_list[nc++] = c;
     }
+    int n = 0;
+    for (int k = 0; k < nc; k++) {
+      colstart[k] = n;
+      for (int p = 0; p < npairs; p++)
+        if (tb->key_col[(pair_begin + p) / A.d] == cols_list[k]) plist[n++] = p;
+    }
+    colstart[nc] = n;
     sint[39] = nc;
   }
   __syncthreads();
@@ -205,15 +213,20 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
         }
         __syncthreads();
         const uint32_t mmask = uint32_t(M - 1);
-        for (int e = tid; e < n_surv; e += T) {
-          const int64_t row = r0 + (n_preds ? surv[e] : e);
-          const uint64_t x = key_field(load1(kbase, kdt, row));
+        for (int base = 0; base < n_surv; base += T) {  // block-uniform trip count
+          const int e = base + tid;
+          const bool valid = e < n_surv;
+          unsigned long long x = kEmptyKey;
+          if (valid) x = key_field(load1(kbase, kdt, r0 + (n_preds ? surv[e] : e)));
+          // equal keys of the warp are inserted once, by their lowest lane, with their count
+          const unsigned peers = __match_any_sync(0xffffffffu, x);
+          if (!valid || lane != __ffs(peers) - 1) continue;
           uint32_t slot = map_slot(x, mmask);
           bool done = false;
           for (int probe = 0; probe < M; probe++) {
-            const unsigned long long prev = atomicCAS(&mkey[slot], kEmptyKey, (unsigned long long)x);
+            const unsigned long long prev = atomicCAS(&mkey[slot], kEmptyKey, x);
             if (prev == kEmptyKey || prev == x) {
-              atomicAdd(&mcnt[slot], 1);
+              atomicAdd(&mcnt[slot], __popc(peers));
               done = true;
               break;
             }
@@ -271,27 +284,33 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
         }
         __syncthreads();
       }
-      for (int e = tid; e < n_entries; e += T) {
-        uint64_t x;
-        int32_t mult;
+      // Two entries per thread share every parameter load: two independent hash chains.
+      const int pl_begin = colstart[kc], pl_end = colstart[kc + 1];
+      for (int e0 = tid; e0 < n_entries; e0 += 2 * T) {
+        const int e1 = e0 + T;
+        uint64_t x0, x1 = 0;
+        int32_t m0, m1 = 0;
         if (DEDUPE) {
-          x = mkey[e];
-          mult = mcnt[e];
+          x0 = mkey[e0];
+          m0 = mcnt[e0];
+          if (e1 < n_entries) x1 = mkey[e1], m1 = mcnt[e1];
         } else {
-          const int64_t row = r0 + (n_preds ? surv[e] : e);
-          x = key_field(load1(kbase, kdt, row));
-          mult = 1;
+          x0 = key_field(load1(kbase, kdt, r0 + (n_preds ? surv[e0] : e0)));
+          m0 = 1;
+          if (e1 < n_entries) x1 = key_field(load1(kbase, kdt, r0 + (n_preds ? surv[e1] : e1))), m1 = 1;
         }
-        const KeyPow kp = key_powers(x);
-        for (int p = 0; p < npairs; p++) {
-          if (pcol[p] != c) continue;
-          const PairParam q = prm[p];
-          const uint32_t h = cw_bucket<POW2>(q, kp, uint32_t(w));
-          const int32_t v = cw_sign(q, kp) * mult;
-          if (GLOBAL)
-            atomicAdd(gcnt + size_t(p) * w + h, v);
-          else
-            atomicAdd(cnt + size_t(p) * w + h, v);
+        const KeyPow k0 = key_powers(x0);
+        const KeyPow k1 = key_powers(x1);
+        for (int j = pl_begin; j < pl_end; j++) {
+          const int pp = plist[j];
+          const PairParam q = prm[pp];
+          const uint32_t h0 = cw_bucket<POW2>(q, k0, uint32_t(w));
+          const uint32_t h1 = cw_bucket<POW2>(q, k1, uint32_t(w));
+          const int32_t v0 = cw_sign(q, k0) * m0;
+          const int32_t v1 = cw_sign(q, k1) * m1;
+          int32_t* row = (GLOBAL ? gcnt : cnt) + size_t(pp) * w;
+          atomicAdd(row + h0, v0);
+          if (m1) atomicAdd(row + h1, v1);
         }
       }
       __syncthreads();  // map / survivor list reused next
@@ -314,7 +333,7 @@ size_t build_smem_bytes(const BuildShape& s, int w) {
   if (s.mode == 1) b += align16(sizeof(int32_t) * size_t(s.smem_pairs) * w);
   if (s.dedupe) b += align16(sizeof(unsigned long long) * size_t(s.map_slots)) + align16(sizeof(int32_t) * size_t(s.map_slots));
   b += align16(sizeof(uint16_t) * s.tile_rows);
-  b += sizeof(int32_t) * (40 + CMP_MAX_COLS);
+  b += sizeof(int32_t) * (40 + 2 * CMP_MAX_COLS + 1);
   return b;
 }
 

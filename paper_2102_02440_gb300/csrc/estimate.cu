@@ -1,0 +1,459 @@
+// Sketch-merging estimate (Sec. 4.2 merge equation, iterated over a table's joins; Sec. 3.2
+// inner product and median), exact in int128.
+//
+// Reading used for sub-plans beyond the 3-table chain of Sec. 4.1: row i of sub-plan S is
+//   E_i = sum over bucket assignments j of S's edges of  prod over t in S of M_t(j|t),
+// M_t the merged sketch of t (value of the sketch, among t's sketches of S's edges in
+// ascending edge id, whose bucket has the minimum |.|, the first on ties).
+// Evaluation: a spanning tree (BFS from the lowest table id, edges in id order) is
+// contracted leaf to root; each non-tree edge index is fixed to c and summed over c.
+// For a table with incoming messages m_l on its edges l != p (p = edge to its parent),
+// splitting the sum by which edge attains the minimum gives threshold sums
+//   G_l^>(tau) = sum_{|s_l[j]| > tau} m_l[j],  G_l^>=(tau) = sum_{|s_l[j]| >= tau} m_l[j]
+// (edge l' < l loses to l iff |s_l'| > |s_l|, edge l' > l iff |s_l'| >= |s_l|):
+//   out[jp] = s_p[jp] prod_{l != p} G_l^{l<p ? > : >=}(|s_p[jp]|)
+//           + sum_{l != p} sum_{j : |s_l[j]| (l>p ? < : <=) |s_p[jp]|}
+//                 s_l[j] m_l[j] prod_{l' != l,p} G_l'^{l'<l ? > : >=}(|s_l[j]|)
+// and at the root (no p) the scalar sum_l sum_j s_l[j] m_l[j] prod_{l' != l} G_l'(...).
+// With every sketch row presorted by (|C|, bucket), each G and each inner sum is a suffix
+// / prefix sum read at a binary-searched rank.
+#include <cuda_runtime.h>
+
+#include "estimate.cuh"
+
+namespace cmpk {
+
+// ---------------------------------------------------------------- checked int128
+__device__ __forceinline__ bool add_ovf(i128 a, i128 b, i128* r) {
+  const i128 s = i128(u128(a) + u128(b));
+  *r = s;
+  return ((a ^ s) & (b ^ s)) < 0;
+}
+
+__device__ __forceinline__ bool mul_ovf(i128 a, i128 b, i128* r) {
+  const bool neg = (a < 0) != (b < 0);
+  const u128 ua = a < 0 ? u128(0) - u128(a) : u128(a);
+  const u128 ub = b < 0 ? u128(0) - u128(b) : u128(b);
+  const uint64_t a1 = uint64_t(ua >> 64), a0 = uint64_t(ua), b1 = uint64_t(ub >> 64), b0 = uint64_t(ub);
+  bool ovf = false;
+  u128 mag;
+  if (a1 == 0 && b1 == 0) {
+    mag = u128(a0) * b0;
+  } else if (a1 && b1) {
+    ovf = true;
+    mag = 0;
+  } else {
+    const u128 cross = a1 ? u128(a1) * b0 : u128(b1) * a0;
+    const u128 low = u128(a0) * b0;
+    if (uint64_t(cross >> 64)) ovf = true;
+    const u128 hi_part = cross << 64;
+    mag = low + hi_part;
+    if (mag < low) ovf = true;
+  }
+  const u128 lim = u128(1) << 127;
+  if (neg ? mag > lim : mag >= lim) ovf = true;
+  *r = neg ? i128(u128(0) - mag) : i128(mag);
+  return ovf;
+}
+
+// Round-to-nearest-even of (neg ? -1 : 1) * (top * 2^128 + mag) to binary64, from the
+// definition: the top 53 significant bits, then half-ulp and sticky bits.
+__device__ double mag_to_double(bool neg, uint32_t top, u128 mag) {
+  if (top == 0 && mag == 0) return 0.0;
+  // bit length
+  int nb;
+  if (top) nb = 129;
+  else {
+    const uint64_t hi = uint64_t(mag >> 64);
+    nb = hi ? 128 - __clzll(hi) : 64 - __clzll(uint64_t(mag));
+  }
+  double r;
+  if (nb <= 53) {
+    r = double(uint64_t(mag));
+  } else {
+    const int sh = nb - 53;  // bits below the kept significand
+    u128 sig, rest_mask, rest, half;
+    if (top) {  // nb == 129: value = 2^128 + mag
+      sig = (u128(1) << 52) | (mag >> 76);
+      rest_mask = (u128(1) << 76) - 1;
+      rest = mag & rest_mask;
+      half = u128(1) << 75;
+    } else {
+      sig = mag >> sh;
+      rest_mask = (u128(1) << sh) - 1;
+      rest = mag & rest_mask;
+      half = u128(1) << (sh - 1);
+    }
+    uint64_t s = uint64_t(sig);
+    if (rest > half || (rest == half && (s & 1))) s++;
+    int e = sh;
+    if (s == (1ull << 53)) {
+      s >>= 1;
+      e++;
+    }
+    r = ldexp(double(s), e);
+  }
+  return neg ? -r : r;
+}
+
+__device__ double i128_to_double(i128 v) {
+  const bool neg = v < 0;
+  return mag_to_double(neg, 0, neg ? u128(0) - u128(v) : u128(v));
+}
+
+// exact (a + b) / 2 rounded once (the sum may need 129 bits)
+__device__ double mean2_to_double(i128 a, i128 b) {
+  i128 s;
+  if (!add_ovf(a, b, &s)) return i128_to_double(s) * 0.5;
+  // same signs overflowed: |a| + |b| = 2^128 * top + low
+  const bool neg = a < 0;
+  const u128 ua = neg ? u128(0) - u128(a) : u128(a);
+  const u128 ub = neg ? u128(0) - u128(b) : u128(b);
+  const u128 low = ua + ub;
+  const uint32_t top = low < ua ? 1u : 0u;
+  return mag_to_double(neg, top, low) * 0.5;
+}
+
+// ---------------------------------------------------------------- presort
+// One CTA per sketch row: keys (|C| << 32 | bucket) bitonic-sorted in shared memory.
+__global__ void __launch_bounds__(1024) k_presort(const int32_t* __restrict__ C, int64_t n_rows, int32_t w,
+                                                  int32_t wp2, uint32_t* __restrict__ abs_out,
+                                                  int32_t* __restrict__ perm_out) {
+  extern __shared__ unsigned long long key[];
+  for (int64_t row = blockIdx.x; row < n_rows; row += gridDim.x) {
+    const int32_t* src = C + row * w;
+    for (int j = threadIdx.x; j < wp2; j += blockDim.x) {
+      if (j < w) {
+        const int32_t v = src[j];
+        const uint32_t a = v < 0 ? uint32_t(-int64_t(v)) : uint32_t(v);
+        key[j] = (static_cast<unsigned long long>(a) << 32) | uint32_t(j);
+      } else {
+        key[j] = ~0ull;
+      }
+    }
+    __syncthreads();
+    for (int k = 2; k <= wp2; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < wp2; i += blockDim.x) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const unsigned long long a = key[i], b = key[ixj];
+            const bool up = (i & k) == 0;
+            if ((a > b) == up) {
+              key[i] = b;
+              key[ixj] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int j = threadIdx.x; j < w; j += blockDim.x) {
+      const unsigned long long kk = key[j];
+      abs_out[row * w + j] = uint32_t(kk >> 32);
+      perm_out[row * w + j] = int32_t(uint32_t(kk));
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_presort(const int32_t* C, int64_t n_rows, int32_t w, uint32_t* abs_out, int32_t* perm_out,
+                           cudaStream_t st) {
+  if (n_rows <= 0) return cudaSuccess;
+  int wp2 = 1;
+  while (wp2 < w) wp2 <<= 1;
+  const size_t smem = sizeof(unsigned long long) * size_t(wp2);
+  cudaError_t e = cudaFuncSetAttribute(k_presort, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const int threads = wp2 >= 1024 ? 1024 : (wp2 < 32 ? 32 : wp2);
+  const int64_t grid = n_rows < 4096 ? n_rows : 4096;
+  k_presort<<<unsigned(grid), threads, smem, st>>>(C, n_rows, w, wp2, abs_out, perm_out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- estimate helpers
+namespace {
+
+// first position q in sorted a[0..w) with a[q] > tau (strict) or a[q] >= tau
+__device__ __forceinline__ int rank_of(const uint32_t* __restrict__ a, int w, uint32_t tau, bool strict) {
+  int lo = 0, hi = w;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const uint32_t v = __ldg(a + mid);
+    if (strict ? v <= tau : v < tau) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+struct BlockScratch {
+  i128* sh_i128;    // [33]
+  int32_t* sh_flag;  // [1]
+};
+
+// block-wide sum of one int128 per thread (checked); result broadcast
+__device__ i128 block_sum(i128 v, bool* ovf, BlockScratch& bs) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  bool o = false;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const int64_t lo = __shfl_down_sync(0xffffffffu, int64_t(v), off);
+    const int64_t hi = __shfl_down_sync(0xffffffffu, int64_t(v >> 64), off);
+    const i128 other = (i128(hi) << 64) | i128(uint64_t(lo));
+    i128 r;
+    const bool ob = add_ovf(v, other, &r);
+    if (lane + off < 32) {
+      o |= ob;
+      v = r;
+    }
+  }
+  if (lane == 0) bs.sh_i128[warp] = v;
+  if (o) atomicOr(bs.sh_flag, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    i128 t = 0;
+    bool oo = false;
+    for (int i = 0; i < nw; i++) oo |= add_ovf(t, bs.sh_i128[i], &t);
+    bs.sh_i128[32] = t;
+    if (oo) atomicOr(bs.sh_flag, 1);
+  }
+  __syncthreads();
+  const i128 r = bs.sh_i128[32];
+  *ovf |= bs.sh_flag[0] != 0;
+  __syncthreads();
+  return r;
+}
+
+// In-place inclusive scan of a[0..n) (forward) or suffix scan (reverse), checked.
+__device__ void block_scan(i128* a, int n, bool reverse, bool* ovf, BlockScratch& bs) {
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int per = (n + T - 1) / T;
+  const int b = tid * per, e = min(n, b + per);
+  i128 s = 0;
+  bool o = false;
+  for (int q = b; q < e; q++) o |= add_ovf(s, a[reverse ? n - 1 - q : q], &s);
+  // exclusive scan of thread sums (thread order = scan order)
+  const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+  i128 incl = s;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int64_t lo = __shfl_up_sync(0xffffffffu, int64_t(incl), off);
+    const int64_t hi = __shfl_up_sync(0xffffffffu, int64_t(incl >> 64), off);
+    const i128 other = (i128(hi) << 64) | i128(uint64_t(lo));
+    i128 r;
+    const bool ob = add_ovf(incl, other, &r);
+    if (lane >= off) {
+      o |= ob;
+      incl = r;
+    }
+  }
+  if (lane == 31) bs.sh_i128[warp] = incl;
+  __syncthreads();
+  if (tid == 0) {
+    i128 t = 0;
+    bool oo = false;
+    for (int i = 0; i < nw; i++) {
+      const i128 v = bs.sh_i128[i];
+      bs.sh_i128[i] = t;
+      oo |= add_ovf(t, v, &t);
+    }
+    if (oo) atomicOr(bs.sh_flag, 1);
+  }
+  __syncthreads();
+  i128 run;
+  o |= add_ovf(bs.sh_i128[warp], incl - s, &run);  // incl - s cannot overflow: it is a partial sum
+  for (int q = b; q < e; q++) {
+    const int idx = reverse ? n - 1 - q : q;
+    o |= add_ovf(run, a[idx], &run);
+    a[idx] = run;
+  }
+  if (o) atomicOr(bs.sh_flag, 1);
+  __syncthreads();
+  *ovf |= bs.sh_flag[0] != 0;
+  __syncthreads();
+}
+
+__device__ __forceinline__ i128 msg_at(const EstIn& in, const i128* __restrict__ slots, int64_t slot_stride,
+                                       int row, int w, int j, int c) {
+  switch (in.kind) {
+    case kInLeaf: return i128(__ldg(in.msk + int64_t(row) * w + j));
+    case kInSlot: return slots[int64_t(in.slot) * slot_stride + j];
+    default: return j == c ? i128(1) : i128(0);
+  }
+}
+
+}  // namespace
+
+// One CTA per work item (sub-plan, sketch row, range of conditioning values), persistent
+// over the item list.  Per-CTA scratch in the workspace:
+//   slots [max_slots][w] messages, suf [max_in][w+1], pre [max_in][w+1]  (int128).
+__global__ void __launch_bounds__(512) k_estimate_items(const __grid_constant__ EstArgs A) {
+  __shared__ i128 sh_i128[33];
+  __shared__ int32_t sh_flag[1];
+  BlockScratch bs{sh_i128, sh_flag};
+  const int w = A.w;
+  const int64_t slot_stride = w;
+  const int64_t arr = int64_t(w) + 1;
+  i128* base = reinterpret_cast<i128*>(A.scratch) + int64_t(blockIdx.x) * A.scratch_per_cta;
+  i128* slots = base;
+  i128* suf = slots + int64_t(A.max_slots) * w;
+  i128* pre = suf + int64_t(A.max_in) * arr;
+
+  for (int64_t it = blockIdx.x; it < A.n_items; it += gridDim.x) {
+    const EstItem item = A.items[it];
+    const EstSub sb = A.subs[item.sub];
+    const int row = item.row;
+    if (threadIdx.x == 0) sh_flag[0] = 0;
+    __syncthreads();
+    i128 acc = 0;
+    bool ovf = false;
+    for (int c = item.c0; c < item.c1; c++) {
+      for (int o = 0; o < sb.n_ops; o++) {
+        const EstOp op = A.ops[sb.op_begin + o];
+        const EstIn* in = A.inputs + op.in_begin;
+        const int k = op.k, p = op.p;
+        // 1. suffix sums of each incoming message in its sketch's presorted order
+        for (int l = 0; l < k; l++) {
+          if (l == p) continue;
+          const EstIn x = in[l];
+          const int32_t* perm = x.perm + int64_t(row) * w;
+          i128* sl = suf + int64_t(l) * arr;
+          for (int q = threadIdx.x; q < w; q += blockDim.x) sl[q] = msg_at(x, slots, slot_stride, row, w, __ldg(perm + q), c);
+          if (threadIdx.x == 0) sl[w] = 0;
+          __syncthreads();
+          block_scan(sl, w, /*reverse=*/true, &ovf, bs);
+        }
+        // 2. per incoming edge l: s_l m_l prod_{l' != l,p} G_l'(|s_l|), in l's sorted order
+        i128 root_part = 0;
+        for (int l = 0; l < k; l++) {
+          if (l == p) continue;
+          const EstIn x = in[l];
+          const int32_t* perm = x.perm + int64_t(row) * w;
+          const uint32_t* absl = x.abs + int64_t(row) * w;
+          const int32_t* sv = x.s + int64_t(row) * w;
+          i128* pl = pre + int64_t(l) * arr;
+          bool o2 = false;
+          for (int r = threadIdx.x; r < w; r += blockDim.x) {
+            const int j = __ldg(perm + r);
+            const uint32_t tau = __ldg(absl + r);
+            i128 v;
+            o2 |= mul_ovf(i128(__ldg(sv + j)), msg_at(x, slots, slot_stride, row, w, j, c), &v);
+            for (int l2 = 0; l2 < k && v != 0; l2++) {
+              if (l2 == l || l2 == p) continue;
+              const EstIn y = in[l2];
+              const int q = rank_of(y.abs + int64_t(row) * w, w, tau, /*strict=*/l2 < l);
+              o2 |= mul_ovf(v, suf[int64_t(l2) * arr + q], &v);
+            }
+            if (p < 0) o2 |= add_ovf(root_part, v, &root_part);
+            else pl[r + 1] = v;
+          }
+          if (o2) atomicOr(sh_flag, 1);
+          if (p >= 0) {
+            if (threadIdx.x == 0) pl[0] = 0;
+            __syncthreads();
+            block_scan(pl + 1, w, /*reverse=*/false, &ovf, bs);
+          }
+        }
+        if (p < 0) {
+          const i128 scal = block_sum(root_part, &ovf, bs);
+          ovf |= add_ovf(acc, scal, &acc);
+          continue;
+        }
+        // 3. the message to the parent
+        {
+          const EstIn xp = in[p];
+          const int32_t* sp = xp.s + int64_t(row) * w;
+          i128* out = slots + int64_t(op.out_slot) * slot_stride;
+          bool o3 = false;
+          for (int jp = threadIdx.x; jp < w; jp += blockDim.x) {
+            const int32_t spv = __ldg(sp + jp);
+            const uint32_t tau = spv < 0 ? uint32_t(-int64_t(spv)) : uint32_t(spv);
+            i128 t = spv;
+            for (int l = 0; l < k && t != 0; l++) {
+              if (l == p) continue;
+              const int q = rank_of(in[l].abs + int64_t(row) * w, w, tau, /*strict=*/l < p);
+              o3 |= mul_ovf(t, suf[int64_t(l) * arr + q], &t);
+            }
+            for (int l = 0; l < k; l++) {
+              if (l == p) continue;
+              // |s_l| < tau (l > p) -> count of entries < tau = rank(>=);  <= tau (l < p) -> rank(>)
+              const int q = rank_of(in[l].abs + int64_t(row) * w, w, tau, /*strict=*/l < p);
+              o3 |= add_ovf(t, pre[int64_t(l) * arr + q], &t);
+            }
+            out[jp] = t;
+          }
+          if (o3) atomicOr(sh_flag, 1);
+          __syncthreads();
+          ovf |= sh_flag[0] != 0;
+        }
+      }
+    }
+    __syncthreads();
+    ovf |= sh_flag[0] != 0;
+    if (threadIdx.x == 0) {
+      A.partial[it] = acc;
+      A.partial_ovf[it] = ovf ? 1 : 0;
+    }
+    __syncthreads();
+  }
+}
+
+// One thread per sub-plan: row sums over conditioning chunks, exact median, one rounding.
+__global__ void k_estimate_finalize(const __grid_constant__ EstArgs A, double* __restrict__ est,
+                                    int64_t* __restrict__ row_est) {
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= A.n_sub) return;
+  const EstSub sb = A.subs[q];
+  const int d = A.d;
+  i128 rows[CMP_MAX_D];
+  bool ovf = false;
+  for (int i = 0; i < d; i++) {
+    if (sb.single) {
+      rows[i] = i128(*sb.sv);
+      continue;
+    }
+    i128 s = 0;
+    for (int ch = 0; ch < sb.n_chunks; ch++) {
+      const int64_t it = int64_t(sb.item_begin) + int64_t(i) * sb.n_chunks + ch;
+      ovf |= A.partial_ovf[it] != 0;
+      ovf |= add_ovf(s, A.partial[it], &s);
+    }
+    rows[i] = s;
+  }
+  if (row_est)
+    for (int i = 0; i < d; i++) {
+      row_est[(q * d + i) * 2] = int64_t(uint64_t(u128(rows[i])));
+      row_est[(q * d + i) * 2 + 1] = int64_t(uint64_t(u128(rows[i]) >> 64));
+    }
+  if (ovf) {
+    est[q] = __longlong_as_double(0x7ff8000000000000ll);
+    set_status(A.status, CMP_EOVERFLOW);
+    return;
+  }
+  for (int i = 1; i < d; i++) {  // insertion sort of exact integers
+    const i128 v = rows[i];
+    int j = i - 1;
+    while (j >= 0 && rows[j] > v) {
+      rows[j + 1] = rows[j];
+      j--;
+    }
+    rows[j + 1] = v;
+  }
+  est[q] = (d & 1) ? i128_to_double(rows[d / 2]) : mean2_to_double(rows[d / 2 - 1], rows[d / 2]);
+}
+
+cudaError_t launch_estimate(const EstArgs& a, double* est, int64_t* row_est, cudaStream_t st) {
+  if (a.n_items > 0) {
+    k_estimate_items<<<a.grid, a.threads, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (a.n_sub > 0) {
+    const int th = 128;
+    k_estimate_finalize<<<unsigned((a.n_sub + th - 1) / th), th, 0, st>>>(a, est, row_est);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+}  // namespace cmpk

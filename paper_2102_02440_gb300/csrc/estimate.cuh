@@ -1,0 +1,71 @@
+// Internal structures of the estimate path (plan blob and kernel arguments).
+#pragma once
+
+#include "internal.cuh"
+
+namespace cmpk {
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+enum { kInOutput = 0, kInLeaf = 1, kInSlot = 2, kInCond = 3 };
+
+// One edge of a table operation, in the table's ascending edge-id order.
+struct EstIn {
+  const int32_t* s;      // this table's sketch on the edge, [d][w]
+  const uint32_t* abs;   // its presorted magnitudes, [d][w]
+  const int32_t* perm;   // its presort permutation, [d][w]
+  const int32_t* msk;    // kInLeaf: the leaf neighbour's sketch on the edge, [d][w]
+  int32_t kind;          // kInOutput / kInLeaf / kInSlot / kInCond
+  int32_t slot;          // kInSlot: message slot written by the child's operation
+};
+
+// One non-leaf table of a sub-plan's spanning tree (post-order).
+struct EstOp {
+  int32_t k;         // number of edges (inputs incl. the output edge)
+  int32_t p;         // index of the output edge among them, -1 at the root
+  int32_t out_slot;  // message slot written (p >= 0)
+  int32_t in_begin;  // first EstIn
+};
+
+struct EstSub {
+  int32_t op_begin, n_ops;
+  int32_t single;     // 1: one table, estimate = exact survivor count
+  int32_t n_chunks;   // conditioning chunks per row (1 for trees)
+  int64_t item_begin;
+  const int64_t* sv;  // single: that table's survivor count (device)
+};
+
+struct EstItem {
+  int32_t sub, row, c0, c1;  // conditioning values [c0, c1); trees use [0, 1)
+};
+
+struct EstPlanHdr {
+  uint64_t magic;
+  int32_t version, d, w, max_slots, max_in, grid, threads, pad;
+  int64_t n_sub, n_ops, n_in, n_items;
+  int64_t off_subs, off_ops, off_in, off_items, total_bytes;
+  int64_t scratch_per_cta;  // int128 elements
+  int64_t ws_bytes;
+};
+constexpr uint64_t kEstPlanMagic = 0x434d504553544d54ull;  // "CMPESTMT"
+
+struct EstArgs {
+  const EstSub* subs;
+  const EstOp* ops;
+  const EstIn* inputs;
+  const EstItem* items;
+  i128* partial;         // [n_items]
+  int32_t* partial_ovf;  // [n_items]
+  void* scratch;
+  int64_t scratch_per_cta;
+  int64_t n_items, n_sub;
+  int32_t d, w, max_slots, max_in, grid, threads;
+  int32_t* status;
+};
+
+cudaError_t launch_presort(const int32_t* C, int64_t n_rows, int32_t w, uint32_t* abs_out, int32_t* perm_out,
+                           cudaStream_t st);
+cudaError_t launch_estimate(const EstArgs& a, double* est, int64_t* row_est, cudaStream_t st);
+
+}  // namespace cmpk

@@ -88,3 +88,67 @@ class DeviceWorkload:
     def sketch(self, e: int, end: int) -> torch.Tensor:
         t, s = self.wl.sketch_of(e, end)
         return self.tables[t].counters[s]
+
+
+class DeviceEstimator:
+    """Presorted sketches of a built DeviceWorkload plus an encoded estimate plan for a
+    list of sub-plans (bit t = table t), replayable with one cmp_estimate call."""
+
+    def __init__(self, dws, masks, graph_of=None):
+        dws = dws if isinstance(dws, (list, tuple)) else [dws]
+        self.dws = dws
+        self.d, self.w = dws[0].d, dws[0].w
+        self.device = dws[0].device
+        self.graphs = []
+        self._keep = []
+        for dw in dws:
+            t_abs, t_perm = [], []
+            for t in dw.tables:
+                t_abs.append(torch.empty(t.counters.shape, dtype=torch.int32, device=self.device))
+                t_perm.append(torch.empty(t.counters.shape, dtype=torch.int32, device=self.device))
+            dw.abs_sorted, dw.perm = t_abs, t_perm
+            eu = (C.c_int32 * max(dw.n_edges, 1))(*dw.wl.edge_u)
+            ev = (C.c_int32 * max(dw.n_edges, 1))(*dw.wl.edge_v)
+            sk, ab, pm = [], [], []
+            for e in range(dw.n_edges):
+                for end in range(2):
+                    ti, si = dw.wl.sketch_of(e, end)
+                    sk.append(dw.tables[ti].counters[si].data_ptr())
+                    ab.append(t_abs[ti][si].data_ptr())
+                    pm.append(t_perm[ti][si].data_ptr())
+            n2 = max(2 * dw.n_edges, 1)
+            skp, abp, pmp = (C.c_void_p * n2)(*sk), (C.c_void_p * n2)(*ab), (C.c_void_p * n2)(*pm)
+            g = K.cmp_graph(len(dw.tables), dw.n_edges, eu, ev, skp, abp, pmp, dw.survivors.data_ptr())
+            self.graphs.append(g)
+            self._keep += [eu, ev, skp, abp, pmp]
+        self.masks = np.ascontiguousarray(masks, np.uint64)
+        self.sub_graph = np.zeros(self.masks.size, np.int32) if graph_of is None else np.ascontiguousarray(graph_of,
+                                                                                                          np.int32)
+        pb, wb = K.cmp_estimate_plan_bytes(self.graphs, self.d, self.w, self.sub_graph, self.masks)
+        self.plan_host = np.zeros(max(pb, 16), np.uint8)
+        K.cmp_estimate_plan_encode(self.graphs, self.d, self.w, self.sub_graph, self.masks,
+                                   self.plan_host.ctypes.data, pb)
+        self.plan_dev = torch.from_numpy(self.plan_host).to(self.device)
+        self.ws = torch.empty(max(wb, 16), dtype=torch.uint8, device=self.device)
+        self.est = torch.empty(self.masks.size, dtype=torch.float64, device=self.device)
+        self.row_est = torch.empty((self.masks.size, self.d, 2), dtype=torch.int64, device=self.device)
+
+    def presort(self, stream=None):
+        s = K.stream_handle(stream)
+        for dw in self.dws:
+            for t, a, p in zip(dw.tables, dw.abs_sorted, dw.perm):
+                if t.k:
+                    K.cmp_presort(t.counters.data_ptr(), t.k * self.d, self.w, a.data_ptr(), p.data_ptr(), 0, 0, s)
+
+    def estimate(self, stream=None, row_est=True):
+        status = self.dws[0].status
+        K.cmp_estimate(self.plan_host.ctypes.data, self.plan_dev.data_ptr(), self.ws.data_ptr(), self.ws.numel(),
+                       self.est.data_ptr(), self.row_est.data_ptr() if row_est else 0, status.data_ptr(),
+                       K.stream_handle(stream))
+
+    def row_values(self):
+        """Exact row estimates as Python ints, [n_sub][d]."""
+        r = self.row_est.cpu().numpy()
+        lo = r[..., 0].astype(np.uint64).astype(object)
+        hi = r[..., 1].astype(object)
+        return (hi * (1 << 64) + lo).tolist()

@@ -119,3 +119,45 @@ def test_batched_plan_encoding_host_logic(K):
     # cmp_sketch_build_batched rejects a blob that is not a plan
     junk = np.zeros(nb, np.uint8)
     assert K.lib().cmp_sketch_build_batched(junk.ctypes.data, 0x1000, 0x2000, 0x3000, None) == K.CMP_EINVAL
+
+
+def _graph(K, eu, ev, nt):
+    ne = len(eu)
+    arr = lambda v: (C.c_int32 * max(ne, 1))(*v)
+    ptrs = (C.c_void_p * max(2 * ne, 1))(*[0x10000 + 0x100 * i for i in range(2 * ne)])
+    g = K.cmp_graph(nt, ne, arr(eu), arr(ev), ptrs, ptrs, ptrs, 0x9000)
+    g._keep = (ptrs,)
+    return g
+
+
+def test_estimate_plan_host_logic(K):
+    """Planning is host-only: connectivity, cycle rank and sizes need no GPU."""
+    tri = _graph(K, [0, 1, 0], [1, 2, 2], 3)
+    pb, wb = K.cmp_estimate_plan_bytes([tri], 11, 4096, [0, 0, 0, 0], [0b111, 0b011, 0b001, 0b110])
+    assert pb > 0 and wb > 0
+    buf = np.zeros(pb, np.uint8)
+    K.cmp_estimate_plan_encode([tri], 11, 4096, [0] * 4, [0b111, 0b011, 0b001, 0b110], buf.ctypes.data, pb)
+    assert buf[:8].view(np.uint64)[0] == 0x434D504553544D54
+    with pytest.raises(K.CompassError) as ei:     # 0 and 2 are adjacent (e2), 1 is not in the set: fine
+        K.cmp_estimate_plan_bytes([_graph(K, [0, 1], [1, 2], 3)], 11, 64, [0], [0b101])
+    assert ei.value.status == K.CMP_EINVAL        # chain 0-1-2 without 1 is disconnected
+    k4 = _graph(K, [0, 0, 0, 1, 1, 2], [1, 2, 3, 2, 3, 3], 4)
+    with pytest.raises(K.CompassError) as ei:
+        K.cmp_estimate_plan_bytes([k4], 5, 64, [0], [0b1111])
+    assert ei.value.status == K.CMP_EUNSUPPORTED  # three independent cycles
+    K.cmp_estimate_plan_bytes([k4], 5, 64, [0], [0b0111])   # one cycle
+    for bad in ([0], [1 << 4], [0b10000]):
+        with pytest.raises(K.CompassError):
+            K.cmp_estimate_plan_bytes([k4], 5, 64, [0], bad)
+    with pytest.raises(K.CompassError):
+        K.cmp_estimate_plan_bytes([k4], 5, 64, [3], [0b11])    # graph index out of range
+    with pytest.raises(K.CompassError):
+        K.cmp_estimate_plan_bytes([_graph(K, [0], [0], 2)], 5, 64, [0], [0b1])   # self-loop
+    junk = np.zeros(256, np.uint8)
+    assert K.lib().cmp_estimate(junk.ctypes.data, 0x10, 0x10, 1 << 20, 0x10, None, None, None) == K.CMP_EINVAL
+
+
+def test_presort_rejections(K):
+    assert K.lib().cmp_presort(0x10, 4, 0, 0x10, 0x10, None, 0, None) == K.CMP_EINVAL
+    assert K.lib().cmp_presort(0x10, 4, 1 << 15, 0x10, 0x10, None, 0, None) == K.CMP_EUNSUPPORTED
+    assert K.lib().cmp_presort(None, 4, 64, 0x10, 0x10, None, 0, None) == K.CMP_EINVAL

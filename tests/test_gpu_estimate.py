@@ -1,0 +1,152 @@
+"""GPU parity of presort + sketch-merging estimate against the oracle: exact int128 row
+estimates and identical doubles (one rounding of the same exact median), on chains,
+stars, cycles, parallel edges, single tables, many graphs in one plan, and the
+five-table cyclic workload."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2102_02440_gb300 import compass as K
+from paper_2102_02440_gb300 import datagen as G
+from paper_2102_02440_gb300 import pipeline as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_sketches(dw):
+    """sketches[e] = (u-side, v-side) as numpy [d, w], read back from the device build."""
+    out = []
+    for e in range(dw.n_edges):
+        out.append(tuple(dw.sketch(e, end).cpu().numpy() for end in range(2)))
+    return out
+
+
+def _check(orc, dw, est, masks, brute=False):
+    torch.cuda.synchronize()
+    dw.check_status()
+    sk = _oracle_sketches(dw)
+    surv = dw.survivors.cpu().numpy()
+    rows = est.row_values()
+    e_gpu = est.est.cpu().numpy()
+    for q, m in enumerate(masks):
+        ref = orc.estimate(dw.wl.edge_u, dw.wl.edge_v, sk, surv, dw.d, dw.w, int(m), brute=brute)
+        assert rows[q] == ref.rows, (q, bin(m), rows[q], ref.rows)
+        assert e_gpu[q] == ref.est, (q, bin(m), e_gpu[q], ref.est)
+
+
+def test_presort_orders_by_magnitude_then_bucket():
+    rng = np.random.default_rng(0)
+    for w in (1, 2, 5, 64, 1023, 4096, 16384):
+        C = torch.from_numpy(rng.integers(-7, 8, size=(3, w)).astype(np.int32)).cuda()
+        C[0, 0] = -(2 ** 31) + 1
+        a = torch.empty_like(C)
+        p = torch.empty_like(C)
+        K.cmp_presort(C.data_ptr(), 3, w, a.data_ptr(), p.data_ptr(), 0, 0, K.stream_handle())
+        torch.cuda.synchronize()
+        Cn = C.cpu().numpy().astype(np.int64)
+        for r in range(3):
+            want = sorted(range(w), key=lambda j: (abs(Cn[r, j]), j))
+            assert p[r].cpu().numpy().tolist() == want
+            assert np.array_equal(a[r].cpu().numpy().view(np.uint32), np.abs(Cn[r, want]).astype(np.uint32))
+
+
+GRAPHS = {
+    "chain5": ([0, 1, 2, 3], [1, 2, 3, 4], 5),
+    "star5": ([0, 0, 0, 0], [1, 2, 3, 4], 5),
+    "triangle": ([0, 1, 0], [1, 2, 2], 3),
+    "cycle4+tail": ([0, 1, 2, 3, 3], [1, 2, 3, 0, 4], 5),
+    "parallel": ([0, 0, 1], [1, 1, 2], 3),
+    "tree": ([0, 0, 1, 1, 2], [1, 2, 3, 4, 5], 6),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+@pytest.mark.parametrize("w", [3, 16, 257])
+def test_random_graphs_all_connected_subplans(orc, name, w):
+    eu, ev, nt = GRAPHS[name]
+    rng = np.random.default_rng(sum(map(ord, name)) + w)
+    tabs = []
+    for t in range(nt):
+        n = int(rng.integers(50, 3000))
+        cols, kc, ei = [], [], []
+        for e in range(len(eu)):
+            if eu[e] == t or ev[e] == t:
+                cols.append(G.zipf_keys(rng, n, 300, float(rng.uniform(0.6, 1.4))))
+                kc.append(len(cols) - 1)
+                ei.append(e)
+        tabs.append(G.Table(f"T{t}", cols, [], kc, ei))
+    wl = G.Workload(name, tabs, eu, ev, 3, w, 77 + w, 0)
+    dw = P.DeviceWorkload(wl)
+    dw.build()
+    masks = G.connected_subplans(nt, eu, ev)
+    est = P.DeviceEstimator(dw, masks)
+    est.presort()
+    est.estimate()
+    _check(orc, dw, est, masks, brute=(w == 3 and len(eu) <= 5))
+
+
+def test_two_way_full_size_workload(orc):
+    wl = G.two_way()
+    dw = P.DeviceWorkload(wl)
+    dw.build()
+    est = P.DeviceEstimator(dw, [0b11, 0b01, 0b10])
+    est.presort()
+    est.estimate()
+    _check(orc, dw, est, [0b11, 0b01, 0b10])
+
+
+def test_many_graphs_one_plan_and_replay(orc):
+    rng = np.random.default_rng(5)
+    dws, masks, gof = [], [], []
+    for gi in range(4):
+        wl = G.random_graph_workload(rng, 5, gi % 2, 100, 4000, 500, d=5, w=64, pred_prob=0.5, hash_seed=gi)
+        dw = P.DeviceWorkload(wl)
+        dw.build()
+        dws.append(dw)
+        ms = G.connected_subplans(5, wl.edge_u, wl.edge_v)
+        masks += ms
+        gof += [gi] * len(ms)
+    est = P.DeviceEstimator(dws, masks, gof)
+    est.presort()
+    est.estimate()
+    first = est.est.clone()
+    est.estimate()
+    assert torch.equal(first, est.est)
+    torch.cuda.synchronize()
+    off = 0
+    rows = est.row_values()
+    for gi, dw in enumerate(dws):
+        sk = _oracle_sketches(dw)
+        surv = dw.survivors.cpu().numpy()
+        for q in range(off, off + gof.count(gi)):
+            ref = orc.estimate(dw.wl.edge_u, dw.wl.edge_v, sk, surv, 5, 64, masks[q])
+            assert rows[q] == ref.rows and float(est.est[q]) == ref.est
+        off += gof.count(gi)
+
+
+def test_five_table_reduced_scale_all_subplans(orc):
+    wl = G.five_table(scale=0.005, w=256)
+    dw = P.DeviceWorkload(wl)
+    dw.build_batched()
+    masks = G.connected_subplans(5, wl.edge_u, wl.edge_v)
+    assert len(masks) == 19
+    est = P.DeviceEstimator(dw, masks)
+    est.presort()
+    est.estimate()
+    _check(orc, dw, est, masks)
+
+
+def test_rejections():
+    wl = G.two_way(n_r=100, n_s=100)
+    dw = P.DeviceWorkload(wl)
+    dw.build()
+    with pytest.raises(K.CompassError):
+        P.DeviceEstimator(dw, [0b100])      # beyond n_tables
+    with pytest.raises(K.CompassError):
+        P.DeviceEstimator(dw, [0])
+    wl2 = G.Workload("2cyc", [G.Table(f"T{t}", [np.zeros(4, np.int32)] * 4, [], [0, 1, 2, 3][:k], e)
+                              for t, (k, e) in enumerate([(2, [0, 2]), (2, [0, 1]), (2, [1, 2])])],
+                     [0, 1, 0], [1, 2, 2], 2, 16, 1, 0)
+    dw2 = P.DeviceWorkload(wl2)
+    dw2.build()
+    P.DeviceEstimator(dw2, [0b111])          # one cycle: supported
