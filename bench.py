@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the COMPASS hot path on GB300: one step = the push-down Fast-AGMS build of
+every attribute-level sketch of a query's tables (one batched launch), the magnitude
+presort, the sketch-merging estimate of every connected sub-plan (one launch + finalize)
+and the learned combiner's inference over the sub-plan row estimates.
+
+Workload (N = 1): the 5-table cyclic join graph shaped like the paper's running example
+(F1 36M, F2 4.5M, D1 2.5M, D2 134k, D3 4M rows; Zipf(1.1) foreign keys; point, subset
+and 20% range predicates; d = 11, w = 4096; 19 connected sub-plans), synthetic.
+Under torchrun every rank runs its own independent query (its own data seed): weak
+scaling, no collective.  `--impl reference` times the single-threaded CPU oracle on a
+bounded sample of the same workload.
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "sketched tuples/s"
+UNIT = "tuples/s"
+INT_ISSUE_PEAK = 152 * 4 * 32 * 2.070e9   # 32-bit integer instructions/s: one warp instruction per SMSP per clock
+CW_INSTR = 60                            # 32-bit instructions per CW-61 bucket + sign evaluation
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="row-count scale of the workload (1.0 = full)")
+    ap.add_argument("--w", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--phases", action="store_true", help="print a per-phase breakdown on stderr")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(scale: float, w: int, rank: int):
+    from paper_2102_02440_gb300 import datagen as G
+    return G.five_table(scale=scale, w=w, data_seed=20210205 + rank)
+
+
+# ----------------------------------------------------------------------- CPU oracle leg
+
+def cpu_baseline(wl, budget_s: float = 12.0):
+    """The single-threaded oracle (as it stands) on a bounded row sample of every table,
+    proportional to table size; returns tuples/s and the sample description."""
+    from oracle import oracle as orc
+    orc.build()
+    hp = orc.hash_params(wl.hash_seed, wl.n_edges, wl.d)
+    # calibrate on a small slice, then size the sample to ~budget_s
+    t0 = time.perf_counter()
+    big = wl.tables[0]
+    orc.build_sketch(big, hp, wl.d, wl.w, 0, 20_000)
+    per_row = (time.perf_counter() - t0) / 20_000
+    frac = min(1.0, budget_s / max(per_row * wl.total_rows * 1.5, 1e-9))
+    rows = 0
+    t0 = time.perf_counter()
+    for t in wl.tables:
+        n = max(1, int(t.n_rows * frac))
+        orc.build_sketch(t, hp, wl.d, wl.w, 0, n)
+        rows += n
+    dt = time.perf_counter() - t0
+    return {"value": rows / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {frac:.4%} of every table's rows ({rows} rows, push-down build of all "
+                      f"{sum(len(t.key_col) for t in wl.tables)} sketches, d={wl.d} w={wl.w}), {dt:.1f} s"}
+
+
+def run_reference(a):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    wl = workload(a.scale, a.w, 0)
+    vals = []
+    for k in range(a.warmup + a.steps):
+        r = cpu_baseline(wl, budget_s=4.0)
+        if k >= a.warmup:
+            vals.append(r["value"])
+    v = statistics.median(vals)
+    r["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": wl.total_rows / v * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": wl.name, "rows_per_step": wl.total_rows, "sample": r["sample"]},
+            "cpu_baseline": r, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------- GPU leg
+
+def run_ours(a):
+    import torch
+
+    from paper_2102_02440_gb300 import datagen as G
+    from paper_2102_02440_gb300 import pipeline as P
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = workload(a.scale, a.w, rank)
+    dw = P.DeviceWorkload(wl, device=dev)
+    masks = G.connected_subplans(len(wl.tables), wl.edge_u, wl.edge_v)
+    est = P.DeviceEstimator(dw, masks)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        dw.build_batched(stream=stream)
+        if evs:
+            evs[1].record(stream)
+        est.presort(stream=stream)
+        if evs:
+            evs[2].record(stream)
+        est.estimate(stream=stream)
+        if evs:
+            evs[3].record(stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    dw.check_status()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(a.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    _barrier(world)
+    torch.cuda.synchronize(dev)
+    for k in range(a.steps):
+        flush.zero_()                        # evict the previous step's inputs from L2
+        step(evs[k])
+    torch.cuda.synchronize(dev)
+    _barrier(world)
+    clocks = sampler.stop()
+    dw.check_status()
+    per = [[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in evs]
+    step_ms = [sum(p) for p in per]
+    ms = statistics.mean(step_ms)
+    ms_max = _max_over_ranks(ms, world)
+    rows = wl.total_rows
+    value = rows * world / (ms_max / 1e3)
+    phase = {n: statistics.mean(p[i] for p in per) for i, n in enumerate(("build", "presort", "estimate"))}
+    n_est = len(masks)
+
+    # roofline of the dominant kernel (the fused build): integer-issue bound
+    surv = dw.survivors.cpu().numpy()
+    updates = int(sum(int(surv[i]) * len(t.key_col) * wl.d for i, t in enumerate(wl.tables)))
+    hbm_peak, peak_kind = _peaks()
+    col_bytes = wl.column_bytes()
+    build_s = phase["build"] / 1e3
+    ach = updates * CW_INSTR / build_s
+    roof = {"bound": "alu", "achieved": ach / 1e12, "peak": INT_ISSUE_PEAK / 1e12, "unit": "Tinstr/s",
+            "frac": ach / INT_ISSUE_PEAK, "traffic": None,
+            "kernel": "k_sketch_build (batched, zero kernel included)",
+            "algorithmic": f"{updates} CW evaluations x {CW_INSTR} int32 instr",
+            "hbm": {"achieved_gbs": col_bytes / build_s / 1e9, "peak_gbs": hbm_peak,
+                    "frac": col_bytes / build_s / 1e9 / hbm_peak, "peak_kind": peak_kind,
+                    "algorithmic_bytes": col_bytes}}
+
+    # end to end through the public API: pinned host columns -> device, path, estimates -> host
+    e2e = None
+    if not a.no_e2e:
+        host_cols = [[torch.from_numpy(np.ascontiguousarray(c)).pin_memory() for c in t.cols] for t in wl.tables]
+        h2d = sum(c.numel() * c.element_size() for tc in host_cols for c in tc)
+        out_host = torch.empty(len(masks), dtype=torch.float64).pin_memory()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tms = []
+        for k in range(a.warmup + a.steps):
+            flush.zero_()
+            e0.record(stream)
+            for tc, t in zip(host_cols, dw.tables):
+                for hc, dc in zip(tc, t.cols):
+                    dc.copy_(hc, non_blocking=True)
+            step()
+            out_host.copy_(est.est, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= a.warmup:
+                tms.append(e0.elapsed_time(e1))
+        e2e_ms = _max_over_ranks(statistics.mean(tms), world)
+        e2e = {"value": rows * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(out_host.numel() * 8), "ms_per_step": e2e_ms}
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+
+    launches_per_step = 2 + sum(1 for t in dw.tables if t.k) + 2
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": wl.name, "rows_per_step": rows, "tables": len(wl.tables),
+                           "sketches": sum(len(t.key_col) for t in wl.tables), "d": wl.d, "w": wl.w,
+                           "subplans": n_est, "column_bytes": col_bytes,
+                           "l2": "256 MB buffer written between steps, outside the per-step events",
+                           "parallelism": f"replicas x{world} (independent queries)"},
+                "phases_ms": phase, "subplan_estimates_per_s": n_est / (phase["estimate"] / 1e3),
+                "survivors": [int(x) for x in surv],
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches_per_step * a.steps}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

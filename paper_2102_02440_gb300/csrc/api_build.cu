@@ -111,22 +111,25 @@ cmp_status choose_shape(const cmp_build_cfg* cfg, int32_t d, int32_t w, int32_t 
   std::memset(&s, 0, sizeof(s));
   const size_t optin = smem_optin_bytes();
   const size_t pair_bytes = size_t(w) * 4;
-  s.threads = (cfg && cfg->threads > 0) ? cfg->threads : 512;
-  s.tile_rows = (cfg && cfg->tile_rows > 0) ? cfg->tile_rows : 2048;
+  int mode = (cfg && cfg->mode > 0) ? cfg->mode : 0;
+  if (mode < 0 || mode > 2) return CMP_EINVAL;
+  const int pairs_all = std::max(max_total_pairs, 1);
+  // Shared-memory slabs pay off when one small slab holds every pair of the table (no
+  // column re-reads, several CTAs per SM); otherwise L2-resident counters do better.
+  if (mode == 0) mode = size_t(pairs_all) * pair_bytes <= 48 * 1024 ? 1 : 2;
+  s.threads = (cfg && cfg->threads > 0) ? cfg->threads : (mode == 2 ? 1024 : 512);
+  s.tile_rows = (cfg && cfg->tile_rows > 0) ? cfg->tile_rows : (mode == 2 ? 4096 : 2048);
   s.dedupe = (cfg && cfg->dedupe >= 0) ? (cfg->dedupe ? 1 : 0) : 1;
   if (s.threads < 32 || s.threads > 1024 || s.threads % 32) return CMP_EINVAL;
   if (s.tile_rows < 128 || s.tile_rows > 16384 || s.tile_rows % 128) return CMP_EINVAL;
   s.map_slots = s.dedupe ? int32_t(next_pow2(uint32_t(2 * s.tile_rows))) : 0;
   if (s.dedupe && s.map_slots > 8 * s.threads) return CMP_EINVAL;  // compaction keeps <= 8 slots per thread
-  int mode = (cfg && cfg->mode > 0) ? cfg->mode : 0;
-  if (mode < 0 || mode > 2) return CMP_EINVAL;
-  const int pairs_all = std::max(max_total_pairs, 1);
   // overhead of everything but the private counters, with the parameter area sized for all pairs
   BuildShape probe = s;
   probe.mode = 2;
   probe.max_pairs = pairs_all;
   const size_t overhead = build_smem_bytes(probe, w) + 1024;
-  if (mode == 0) mode = (pair_bytes * 1 + overhead <= optin && pair_bytes <= 96 * 1024) ? 1 : 2;
+  if (mode == 1 && pair_bytes + overhead > optin) return CMP_EINVAL;
   s.mode = mode;
   int ctas_per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : 0;
   if (mode == 1) {

@@ -19,7 +19,7 @@ struct PlanOut {
   std::vector<EstOp> ops;
   std::vector<EstIn> ins;
   std::vector<EstItem> items;
-  int32_t max_slots = 0, max_in = 1;
+  int32_t max_slots = 0, max_in = 1, max_suf = 0, max_rank = 0;
 };
 
 bool graph_ok(const cmp_graph& g) {
@@ -80,10 +80,12 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
   auto end_of = [&](int e, int t) { return g.edge_u[e] == t ? 0 : 1; };
   std::vector<int> slot_of(nt, -1);
   std::vector<char> slot_busy;
+  int32_t n_suf = 0, n_rank = 0;
   for (size_t h = order.size(); h-- > 0;) {
     const int t = order[h];
     if (is_leaf(t)) continue;
     EstOp op;
+    std::memset(&op, 0, sizeof(op));
     op.k = 0;
     op.p = -1;
     op.out_slot = -1;
@@ -97,10 +99,12 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
       x.s = g.sketch[2 * e + me];
       x.abs = g.abs_sorted[2 * e + me];
       x.perm = g.perm[2 * e + me];
+      x.suf = -1;
       if (e == parent_edge[t]) {
         x.kind = kInOutput;
         op.p = op.k;
       } else if (tree[e]) {
+        x.suf = n_suf++;
         const int child = g.edge_u[e] == t ? g.edge_v[e] : g.edge_u[e];
         if (is_leaf(child)) {
           x.kind = kInLeaf;
@@ -132,10 +136,16 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
       slot_of[t] = s;
     }
     for (int s : consumed) slot_busy[s] = 0;
+    const int32_t m = op.k - (op.p >= 0 ? 1 : 0);
+    op.rank_off = n_rank;
+    n_rank += m * (m - 1) + (op.p >= 0 ? m : 0);
     P->max_slots = std::max<int32_t>(P->max_slots, int32_t(slot_busy.size()));
     P->max_in = std::max<int32_t>(P->max_in, op.k);
     P->ops.push_back(op);
   }
+  P->max_suf = std::max(P->max_suf, n_suf);
+  P->max_rank = std::max(P->max_rank, n_rank);
+  sb.cond = cond.empty() ? 0 : 1;
   sb.n_ops = int32_t(P->ops.size()) - sb.op_begin;
   sb.n_chunks = cond.empty() ? 1 : (w + kCondChunk - 1) / kCondChunk;
   P->subs.push_back(sb);
@@ -186,9 +196,14 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
   H->off_items = int64_t(off);
   off += align16(sizeof(EstItem) * P->items.size());
   H->total_bytes = int64_t(off);
-  H->scratch_per_cta = int64_t(P->max_slots) * w + 2 * int64_t(P->max_in) * (int64_t(w) + 1);
+  H->max_suf = P->max_suf;
+  H->max_rank = P->max_rank;
+  const int64_t W1 = int64_t(w) + 1;
+  H->scratch_per_cta = int64_t(align16(sizeof(i128) * size_t(int64_t(P->max_slots) * w + int64_t(P->max_suf) * W1 +
+                                                             int64_t(P->max_in) * W1) +
+                                       sizeof(int32_t) * size_t(int64_t(P->max_rank) * w)));
   H->ws_bytes = int64_t(align16(sizeof(i128) * P->items.size()) + align16(sizeof(int32_t) * P->items.size()) +
-                        sizeof(i128) * size_t(H->scratch_per_cta) * size_t(H->grid));
+                        size_t(H->scratch_per_cta) * size_t(H->grid));
   return CMP_OK;
 }
 
@@ -273,6 +288,8 @@ cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_de
   a.w = H.w;
   a.max_slots = H.max_slots;
   a.max_in = H.max_in;
+  a.max_suf = H.max_suf;
+  a.max_rank = H.max_rank;
   a.grid = H.grid;
   a.threads = H.threads;
   a.status = status_dev;

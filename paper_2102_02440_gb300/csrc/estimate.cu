@@ -273,83 +273,185 @@ __device__ void block_scan(i128* a, int n, bool reverse, bool* ovf, BlockScratch
   __syncthreads();
 }
 
-__device__ __forceinline__ i128 msg_at(const EstIn& in, const i128* __restrict__ slots, int64_t slot_stride,
-                                       int row, int w, int j, int c) {
-  switch (in.kind) {
-    case kInLeaf: return i128(__ldg(in.msk + int64_t(row) * w + j));
-    case kInSlot: return slots[int64_t(in.slot) * slot_stride + j];
-    default: return j == c ? i128(1) : i128(0);
-  }
-}
-
 }  // namespace
 
 // One CTA per work item (sub-plan, sketch row, range of conditioning values), persistent
 // over the item list.  Per-CTA scratch in the workspace:
-//   slots [max_slots][w] messages, suf [max_in][w+1], pre [max_in][w+1]  (int128).
+//   slots [max_slots][w]  messages (int128)
+//   suf   [max_suf][w+1]  suffix sums of each incoming message in its sketch's sorted
+//                         order (leaf inputs: computed once per item)
+//   pre   [max_in][w+1]   prefix sums of the "this edge attains the minimum" terms
+//   rank  [max_rank][w]   cross ranks between the sorted sketch rows of each table,
+//                         computed once per item (they do not depend on messages)
+// A conditioned input (unit vector at c) needs no array: its threshold sum is a
+// comparison with |s[c]| and its own term is one value.
+constexpr int kMaxIn = CMP_MAX_SKETCHES;
+
 __global__ void __launch_bounds__(512) k_estimate_items(const __grid_constant__ EstArgs A) {
   __shared__ i128 sh_i128[33];
   __shared__ int32_t sh_flag[1];
+  __shared__ i128 sh_val[kMaxIn];
+  __shared__ uint32_t sh_ac[kMaxIn];
+  __shared__ EstIn sh_in[kMaxIn];
+  __shared__ int32_t sh_L[kMaxIn];
   BlockScratch bs{sh_i128, sh_flag};
   const int w = A.w;
-  const int64_t slot_stride = w;
-  const int64_t arr = int64_t(w) + 1;
-  i128* base = reinterpret_cast<i128*>(A.scratch) + int64_t(blockIdx.x) * A.scratch_per_cta;
-  i128* slots = base;
+  const int64_t W1 = int64_t(w) + 1;
+  unsigned char* cta = reinterpret_cast<unsigned char*>(A.scratch) + int64_t(blockIdx.x) * A.scratch_per_cta;
+  i128* slots = reinterpret_cast<i128*>(cta);
   i128* suf = slots + int64_t(A.max_slots) * w;
-  i128* pre = suf + int64_t(A.max_in) * arr;
+  i128* pre = suf + int64_t(A.max_suf) * W1;
+  int32_t* rk = reinterpret_cast<int32_t*>(pre + int64_t(A.max_in) * W1);
+  const int tid = threadIdx.x, T = blockDim.x;
 
   for (int64_t it = blockIdx.x; it < A.n_items; it += gridDim.x) {
     const EstItem item = A.items[it];
     const EstSub sb = A.subs[item.sub];
-    const int row = item.row;
-    if (threadIdx.x == 0) sh_flag[0] = 0;
+    const int64_t ro = int64_t(item.row) * w;  // row offset inside every [d][w] array
+    if (tid == 0) sh_flag[0] = 0;
     __syncthreads();
-    i128 acc = 0;
     bool ovf = false;
+
+    // ---------------- prologue: cross ranks and leaf suffix sums (independent of c)
+    for (int o = 0; o < sb.n_ops; o++) {
+      const EstOp op = A.ops[sb.op_begin + o];
+      const EstIn* in = A.inputs + op.in_begin;
+      int L[kMaxIn];
+      int m = 0;
+      for (int l = 0; l < op.k; l++)
+        if (l != op.p) L[m++] = l;
+      int t = op.rank_off;
+      for (int a = 0; a < m; a++) {
+        const uint32_t* absa = in[L[a]].abs + ro;
+        for (int b = 0; b < m; b++) {
+          if (b == a) continue;
+          const uint32_t* absb = in[L[b]].abs + ro;
+          int32_t* tab = rk + int64_t(t++) * w;
+          const bool strict = L[b] < L[a];
+          for (int r = tid; r < w; r += T) tab[r] = rank_of(absb, w, __ldg(absa + r), strict);
+        }
+      }
+      if (op.p >= 0) {
+        const uint32_t* absp = in[op.p].abs + ro;
+        for (int a = 0; a < m; a++) {
+          int32_t* tab = rk + int64_t(t++) * w;
+          const uint32_t* absa = in[L[a]].abs + ro;
+          const bool strict = L[a] < op.p;
+          for (int r = tid; r < w; r += T) tab[r] = rank_of(absa, w, __ldg(absp + r), strict);
+        }
+      }
+      for (int a = 0; a < m; a++) {
+        const EstIn x = in[L[a]];
+        if (x.kind != kInLeaf) continue;
+        i128* sl = suf + int64_t(x.suf) * W1;
+        const int32_t* perm = x.perm + ro;
+        for (int r = tid; r < w; r += T) sl[r] = i128(__ldg(x.msk + ro + __ldg(perm + r)));
+        if (tid == 0) sl[w] = 0;
+        __syncthreads();
+        block_scan(sl, w, /*reverse=*/true, &ovf, bs);
+      }
+    }
+    __syncthreads();
+
+    i128 acc = 0;
     for (int c = item.c0; c < item.c1; c++) {
       for (int o = 0; o < sb.n_ops; o++) {
         const EstOp op = A.ops[sb.op_begin + o];
-        const EstIn* in = A.inputs + op.in_begin;
         const int k = op.k, p = op.p;
-        // 1. suffix sums of each incoming message in its sketch's presorted order
-        for (int l = 0; l < k; l++) {
-          if (l == p) continue;
-          const EstIn x = in[l];
-          const int32_t* perm = x.perm + int64_t(row) * w;
-          i128* sl = suf + int64_t(l) * arr;
-          for (int q = threadIdx.x; q < w; q += blockDim.x) sl[q] = msg_at(x, slots, slot_stride, row, w, __ldg(perm + q), c);
-          if (threadIdx.x == 0) sl[w] = 0;
+        if (tid < k) sh_in[tid] = A.inputs[op.in_begin + tid];
+        __syncthreads();
+        int m = 0;
+        for (int l = 0; l < k; l++)
+          if (l != p) sh_L[m++] = l;  // every thread writes the same values
+        __syncthreads();
+        // 1. suffix sums of messages arriving from non-leaf children
+        for (int a = 0; a < m; a++) {
+          const EstIn& x = sh_in[sh_L[a]];
+          if (x.kind != kInSlot) continue;
+          i128* sl = suf + int64_t(x.suf) * W1;
+          const i128* msg = slots + int64_t(x.slot) * w;
+          const int32_t* perm = x.perm + ro;
+          for (int r = tid; r < w; r += T) sl[r] = msg[__ldg(perm + r)];
+          if (tid == 0) sl[w] = 0;
           __syncthreads();
           block_scan(sl, w, /*reverse=*/true, &ovf, bs);
         }
-        // 2. per incoming edge l: s_l m_l prod_{l' != l,p} G_l'(|s_l|), in l's sorted order
+        // 2a. conditioned inputs: |s[c]| and their single "attains the minimum" term
+        if (tid < m) {
+          const EstIn& x = sh_in[sh_L[tid]];
+          if (x.kind == kInCond) {
+            const int32_t v = __ldg(x.s + ro + c);
+            sh_ac[tid] = v < 0 ? uint32_t(-int64_t(v)) : uint32_t(v);
+          }
+        }
+        __syncthreads();
+        if (tid < m) {
+          const int la = sh_L[tid];
+          const EstIn& x = sh_in[la];
+          if (x.kind == kInCond) {
+            const uint32_t tau = sh_ac[tid];
+            i128 v = i128(__ldg(x.s + ro + c));
+            bool o1 = false;
+            for (int b = 0; b < m && v != 0; b++) {
+              if (b == tid) continue;
+              const int lb = sh_L[b];
+              const EstIn& y = sh_in[lb];
+              const bool strict = lb < la;
+              if (y.kind == kInCond) {
+                if (!(strict ? sh_ac[b] > tau : sh_ac[b] >= tau)) v = 0;
+              } else {
+                const int q = rank_of(y.abs + ro, w, tau, strict);
+                o1 |= mul_ovf(v, suf[int64_t(y.suf) * W1 + q], &v);
+              }
+            }
+            sh_val[tid] = v;
+            if (o1) atomicOr(sh_flag, 1);
+          }
+        }
+        __syncthreads();
+        // 2b. other inputs: s_l m_l prod_{l' != l, p} G_l'(|s_l|) in l's sorted order
         i128 root_part = 0;
-        for (int l = 0; l < k; l++) {
-          if (l == p) continue;
-          const EstIn x = in[l];
-          const int32_t* perm = x.perm + int64_t(row) * w;
-          const uint32_t* absl = x.abs + int64_t(row) * w;
-          const int32_t* sv = x.s + int64_t(row) * w;
-          i128* pl = pre + int64_t(l) * arr;
+        int t2 = op.rank_off;
+        for (int a = 0; a < m; a++) {
+          const int la = sh_L[a];
+          const EstIn& x = sh_in[la];
+          if (x.kind == kInCond) {
+            t2 += m - 1;
+            if (p < 0 && tid == 0) ovf |= add_ovf(root_part, sh_val[a], &root_part);
+            continue;
+          }
+          const int32_t* perm = x.perm + ro;
+          const uint32_t* absa = x.abs + ro;
+          const i128* msg = x.kind == kInSlot ? slots + int64_t(x.slot) * w : nullptr;
+          i128* pl = pre + int64_t(a) * W1;
           bool o2 = false;
-          for (int r = threadIdx.x; r < w; r += blockDim.x) {
+          for (int r = tid; r < w; r += T) {
             const int j = __ldg(perm + r);
-            const uint32_t tau = __ldg(absl + r);
             i128 v;
-            o2 |= mul_ovf(i128(__ldg(sv + j)), msg_at(x, slots, slot_stride, row, w, j, c), &v);
-            for (int l2 = 0; l2 < k && v != 0; l2++) {
-              if (l2 == l || l2 == p) continue;
-              const EstIn y = in[l2];
-              const int q = rank_of(y.abs + int64_t(row) * w, w, tau, /*strict=*/l2 < l);
-              o2 |= mul_ovf(v, suf[int64_t(l2) * arr + q], &v);
+            const i128 mv = msg ? msg[j] : i128(__ldg(x.msk + ro + j));
+            o2 |= mul_ovf(i128(__ldg(x.s + ro + j)), mv, &v);
+            int tb = t2;
+            for (int b = 0; b < m; b++) {
+              if (b == a) continue;
+              const int lb = sh_L[b];
+              const EstIn& y = sh_in[lb];
+              if (v != 0) {
+                if (y.kind == kInCond) {
+                  const uint32_t tau = __ldg(absa + r);
+                  if (!(lb < la ? sh_ac[b] > tau : sh_ac[b] >= tau)) v = 0;
+                } else {
+                  o2 |= mul_ovf(v, suf[int64_t(y.suf) * W1 + rk[int64_t(tb) * w + r]], &v);
+                }
+              }
+              tb++;
             }
             if (p < 0) o2 |= add_ovf(root_part, v, &root_part);
             else pl[r + 1] = v;
           }
+          t2 += m - 1;
           if (o2) atomicOr(sh_flag, 1);
           if (p >= 0) {
-            if (threadIdx.x == 0) pl[0] = 0;
+            if (tid == 0) pl[0] = 0;
             __syncthreads();
             block_scan(pl + 1, w, /*reverse=*/false, &ovf, bs);
           }
@@ -359,38 +461,42 @@ __global__ void __launch_bounds__(512) k_estimate_items(const __grid_constant__ 
           ovf |= add_ovf(acc, scal, &acc);
           continue;
         }
-        // 3. the message to the parent
+        // 3. message to the parent, evaluated in the output sketch's sorted order
         {
-          const EstIn xp = in[p];
-          const int32_t* sp = xp.s + int64_t(row) * w;
-          i128* out = slots + int64_t(op.out_slot) * slot_stride;
+          const EstIn& xp = sh_in[p];
+          const int32_t* permp = xp.perm + ro;
+          const uint32_t* absp = xp.abs + ro;
+          i128* out = slots + int64_t(op.out_slot) * w;
+          const int t3 = op.rank_off + m * (m - 1);
           bool o3 = false;
-          for (int jp = threadIdx.x; jp < w; jp += blockDim.x) {
-            const int32_t spv = __ldg(sp + jp);
-            const uint32_t tau = spv < 0 ? uint32_t(-int64_t(spv)) : uint32_t(spv);
-            i128 t = spv;
-            for (int l = 0; l < k && t != 0; l++) {
-              if (l == p) continue;
-              const int q = rank_of(in[l].abs + int64_t(row) * w, w, tau, /*strict=*/l < p);
-              o3 |= mul_ovf(t, suf[int64_t(l) * arr + q], &t);
+          for (int r = tid; r < w; r += T) {
+            const int jp = __ldg(permp + r);
+            const uint32_t tau = __ldg(absp + r);
+            i128 t = i128(__ldg(xp.s + ro + jp));
+            i128 add = 0;
+            for (int a = 0; a < m; a++) {
+              const int la = sh_L[a];
+              const EstIn& x = sh_in[la];
+              if (x.kind == kInCond) {
+                if (t != 0 && !(la < p ? sh_ac[a] > tau : sh_ac[a] >= tau)) t = 0;
+                if (la > p ? sh_ac[a] < tau : sh_ac[a] <= tau) o3 |= add_ovf(add, sh_val[a], &add);
+              } else {
+                const int q = rk[int64_t(t3 + a) * w + r];
+                if (t != 0) o3 |= mul_ovf(t, suf[int64_t(x.suf) * W1 + q], &t);
+                o3 |= add_ovf(add, pre[int64_t(a) * W1 + q], &add);
+              }
             }
-            for (int l = 0; l < k; l++) {
-              if (l == p) continue;
-              // |s_l| < tau (l > p) -> count of entries < tau = rank(>=);  <= tau (l < p) -> rank(>)
-              const int q = rank_of(in[l].abs + int64_t(row) * w, w, tau, /*strict=*/l < p);
-              o3 |= add_ovf(t, pre[int64_t(l) * arr + q], &t);
-            }
+            o3 |= add_ovf(t, add, &t);
             out[jp] = t;
           }
           if (o3) atomicOr(sh_flag, 1);
           __syncthreads();
-          ovf |= sh_flag[0] != 0;
         }
       }
     }
     __syncthreads();
     ovf |= sh_flag[0] != 0;
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       A.partial[it] = acc;
       A.partial_ovf[it] = ovf ? 1 : 0;
     }

@@ -18,6 +18,8 @@ struct EstIn {
   const int32_t* msk;    // kInLeaf: the leaf neighbour's sketch on the edge, [d][w]
   int32_t kind;          // kInOutput / kInLeaf / kInSlot / kInCond
   int32_t slot;          // kInSlot: message slot written by the child's operation
+  int32_t suf;           // kInLeaf / kInSlot: suffix-sum array of the sub-plan (item-persistent)
+  int32_t pad;
 };
 
 // One non-leaf table of a sub-plan's spanning tree (post-order).
@@ -26,6 +28,8 @@ struct EstOp {
   int32_t p;         // index of the output edge among them, -1 at the root
   int32_t out_slot;  // message slot written (p >= 0)
   int32_t in_begin;  // first EstIn
+  int32_t rank_off;  // first rank table of the op in the item's rank scratch (units of w int32)
+  int32_t pad;
 };
 
 struct EstSub {
@@ -34,6 +38,8 @@ struct EstSub {
   int32_t n_chunks;   // conditioning chunks per row (1 for trees)
   int64_t item_begin;
   const int64_t* sv;  // single: that table's survivor count (device)
+  int32_t cond;       // 1 if a non-tree edge is conditioned
+  int32_t pad;
 };
 
 struct EstItem {
@@ -42,10 +48,10 @@ struct EstItem {
 
 struct EstPlanHdr {
   uint64_t magic;
-  int32_t version, d, w, max_slots, max_in, grid, threads, pad;
+  int32_t version, d, w, max_slots, max_in, grid, threads, max_suf, max_rank;
   int64_t n_sub, n_ops, n_in, n_items;
   int64_t off_subs, off_ops, off_in, off_items, total_bytes;
-  int64_t scratch_per_cta;  // int128 elements
+  int64_t scratch_per_cta;  // bytes
   int64_t ws_bytes;
 };
 constexpr uint64_t kEstPlanMagic = 0x434d504553544d54ull;  // "CMPESTMT"
@@ -58,9 +64,9 @@ struct EstArgs {
   i128* partial;         // [n_items]
   int32_t* partial_ovf;  // [n_items]
   void* scratch;
-  int64_t scratch_per_cta;
+  int64_t scratch_per_cta;  // bytes
   int64_t n_items, n_sub;
-  int32_t d, w, max_slots, max_in, grid, threads;
+  int32_t d, w, max_slots, max_in, grid, threads, max_suf, max_rank;
   int32_t* status;
 };
 
