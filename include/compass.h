@@ -207,12 +207,20 @@ typedef struct {
  *                gets CMP_EOVERFLOW)
  *   row_est_dev  NULL or [n_sub][d][2] int64: each exact row estimate as a little-endian
  *                two's-complement int128 (low word first) */
+/* Estimate launch shape; zero fields choose automatically. */
+typedef struct {
+  int32_t threads;     /* threads per CTA (multiple of 32, <= 1024)                */
+  int32_t ctas_per_sm; /* resident CTAs per SM the persistent grid is sized for    */
+  int32_t cond_chunk;  /* conditioning values per work item of a cyclic sub-plan   */
+  int32_t reserved;
+} cmp_estimate_cfg;
+
 cmp_status cmp_estimate_plan_bytes(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
-                                   const int32_t* sub_graph, const uint64_t* sub_mask, size_t* plan_bytes,
-                                   size_t* ws_bytes);
+                                   const int32_t* sub_graph, const uint64_t* sub_mask, const cmp_estimate_cfg* cfg,
+                                   size_t* plan_bytes, size_t* ws_bytes);
 cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
-                                    const int32_t* sub_graph, const uint64_t* sub_mask, void* plan_host,
-                                    size_t plan_bytes);
+                                    const int32_t* sub_graph, const uint64_t* sub_mask, const cmp_estimate_cfg* cfg,
+                                    void* plan_host, size_t plan_bytes);
 cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_dev, size_t ws_bytes, double* est_dev,
                         int64_t* row_est_dev, int32_t* status_dev, void* stream);
 

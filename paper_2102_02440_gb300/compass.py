@@ -52,6 +52,15 @@ class cmp_build_cfg(C.Structure):
         return cls(mode, pairs_per_slab, threads, tile_rows, dedupe, ctas_per_sm)
 
 
+class cmp_estimate_cfg(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("cond_chunk", C.c_int32),
+                ("reserved", C.c_int32)]
+
+    @classmethod
+    def make(cls, threads=0, ctas_per_sm=0, cond_chunk=0):
+        return cls(threads, ctas_per_sm, cond_chunk, 0)
+
+
 class cmp_graph(C.Structure):
     _fields_ = [("n_tables", C.c_int32), ("n_edges", C.c_int32), ("edge_u", C.POINTER(C.c_int32)),
                 ("edge_v", C.POINTER(C.c_int32)), ("sketch", C.POINTER(C.c_void_p)),
@@ -77,10 +86,11 @@ _SIGS = {
     "cmp_presort": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                                 C.c_void_p]),
     "cmp_estimate_plan_bytes": (C.c_int32, [C.POINTER(cmp_graph), C.c_int32, C.c_int32, C.c_int32, C.c_int32,
-                                            C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t),
-                                            C.POINTER(C.c_size_t)]),
+                                            C.c_void_p, C.c_void_p, C.POINTER(cmp_estimate_cfg),
+                                            C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "cmp_estimate_plan_encode": (C.c_int32, [C.POINTER(cmp_graph), C.c_int32, C.c_int32, C.c_int32, C.c_int32,
-                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t]),
+                                             C.c_void_p, C.c_void_p, C.POINTER(cmp_estimate_cfg), C.c_void_p,
+                                             C.c_size_t]),
     "cmp_estimate": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]),
     "cmp_mlp_param_count": (C.c_int64, [C.c_int32, C.c_int32]),
@@ -193,7 +203,7 @@ def cmp_presort(counters_dev: int, n_rows: int, w: int, abs_sorted_dev: int, per
                                             stream))
 
 
-def cmp_estimate_plan_bytes(graphs, d: int, w: int, sub_graph, sub_mask):
+def cmp_estimate_plan_bytes(graphs, d: int, w: int, sub_graph, sub_mask, cfg: cmp_estimate_cfg | None = None):
     import numpy as np
     g = (cmp_graph * len(graphs))(*graphs)
     sg = np.ascontiguousarray(sub_graph, np.int32)
@@ -201,18 +211,19 @@ def cmp_estimate_plan_bytes(graphs, d: int, w: int, sub_graph, sub_mask):
     pb, wb = C.c_size_t(0), C.c_size_t(0)
     _check("cmp_estimate_plan_bytes",
            lib().cmp_estimate_plan_bytes(g, len(graphs), d, w, sg.size, sg.ctypes.data, sm.ctypes.data,
-                                         C.byref(pb), C.byref(wb)))
+                                         C.byref(cfg) if cfg is not None else None, C.byref(pb), C.byref(wb)))
     return pb.value, wb.value
 
 
-def cmp_estimate_plan_encode(graphs, d: int, w: int, sub_graph, sub_mask, plan_host: int, plan_bytes: int):
+def cmp_estimate_plan_encode(graphs, d: int, w: int, sub_graph, sub_mask, plan_host: int, plan_bytes: int,
+                             cfg: cmp_estimate_cfg | None = None):
     import numpy as np
     g = (cmp_graph * len(graphs))(*graphs)
     sg = np.ascontiguousarray(sub_graph, np.int32)
     sm = np.ascontiguousarray(sub_mask, np.uint64)
     _check("cmp_estimate_plan_encode",
-           lib().cmp_estimate_plan_encode(g, len(graphs), d, w, sg.size, sg.ctypes.data, sm.ctypes.data, plan_host,
-                                          plan_bytes))
+           lib().cmp_estimate_plan_encode(g, len(graphs), d, w, sg.size, sg.ctypes.data, sm.ctypes.data,
+                                          C.byref(cfg) if cfg is not None else None, plan_host, plan_bytes))
 
 
 def cmp_estimate(plan_host: int, plan_dev: int, ws_dev: int, ws_bytes: int, est_dev: int, row_est_dev: int,

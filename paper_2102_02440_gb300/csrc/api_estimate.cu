@@ -11,8 +11,17 @@ using namespace cmpk;
 
 namespace {
 
-constexpr int kCondChunk = 64;   // conditioning values per work item (cycles)
-constexpr int kEstThreads = 512;
+struct EstShape {
+  int32_t threads, ctas_per_sm, cond_chunk;
+};
+
+cmp_status est_shape(const cmp_estimate_cfg* cfg, EstShape* s) {
+  s->threads = (cfg && cfg->threads > 0) ? cfg->threads : 1024;
+  s->ctas_per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : 1;
+  s->cond_chunk = (cfg && cfg->cond_chunk > 0) ? cfg->cond_chunk : 64;
+  if (s->threads < 32 || s->threads > 1024 || s->threads % 32 || s->ctas_per_sm > 32) return CMP_EINVAL;
+  return CMP_OK;
+}
 
 struct PlanOut {
   std::vector<EstSub> subs;
@@ -37,7 +46,8 @@ bool graph_ok(const cmp_graph& g) {
 
 // Plan one sub-plan: spanning tree by BFS from the lowest table id (edges in id order),
 // non-tree edges conditioned, post-order operations for every non-leaf table.
-cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int32_t sub_index, PlanOut* P) {
+cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int32_t sub_index, int32_t chunk,
+                    PlanOut* P) {
   const int nt = g.n_tables;
   if (mask == 0 || (nt < 64 && (mask >> nt) != 0)) return CMP_EINVAL;
   std::vector<int> es;
@@ -137,8 +147,10 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
     }
     for (int s : consumed) slot_busy[s] = 0;
     const int32_t m = op.k - (op.p >= 0 ? 1 : 0);
+    int32_t n_cond_in = 0;
+    for (int32_t l = 0; l < op.k; l++) n_cond_in += P->ins[op.in_begin + l].kind == kInCond;
     op.rank_off = n_rank;
-    n_rank += m * (m - 1) + (op.p >= 0 ? m : 0);
+    n_rank += m * (m - 1) + (op.p >= 0 ? m : 0) + n_cond_in;
     P->max_slots = std::max<int32_t>(P->max_slots, int32_t(slot_busy.size()));
     P->max_in = std::max<int32_t>(P->max_in, op.k);
     P->ops.push_back(op);
@@ -147,29 +159,32 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
   P->max_rank = std::max(P->max_rank, n_rank);
   sb.cond = cond.empty() ? 0 : 1;
   sb.n_ops = int32_t(P->ops.size()) - sb.op_begin;
-  sb.n_chunks = cond.empty() ? 1 : (w + kCondChunk - 1) / kCondChunk;
+  sb.n_chunks = cond.empty() ? 1 : (w + chunk - 1) / chunk;
   P->subs.push_back(sb);
   for (int i = 0; i < d; i++)
     for (int ch = 0; ch < sb.n_chunks; ch++) {
       EstItem it;
       it.sub = sub_index;
       it.row = i;
-      it.c0 = cond.empty() ? 0 : ch * kCondChunk;
-      it.c1 = cond.empty() ? 1 : std::min(w, (ch + 1) * kCondChunk);
+      it.c0 = cond.empty() ? 0 : ch * chunk;
+      it.c1 = cond.empty() ? 1 : std::min(w, (ch + 1) * chunk);
       P->items.push_back(it);
     }
   return CMP_OK;
 }
 
 cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
-                    const int32_t* sub_graph, const uint64_t* sub_mask, PlanOut* P, EstPlanHdr* H) {
+                    const int32_t* sub_graph, const uint64_t* sub_mask, const cmp_estimate_cfg* cfg, PlanOut* P,
+                    EstPlanHdr* H) {
   if (!graphs || n_graphs < 1 || d < 1 || d > CMP_MAX_D || w < 1 || w > CMP_MAX_W || n_sub < 0) return CMP_EINVAL;
+  EstShape shape;
+  if (est_shape(cfg, &shape) != CMP_OK) return CMP_EINVAL;
   if (n_sub && (!sub_graph || !sub_mask)) return CMP_EINVAL;
   for (int32_t gi = 0; gi < n_graphs; gi++)
     if (!graph_ok(graphs[gi])) return CMP_EINVAL;
   for (int32_t q = 0; q < n_sub; q++) {
     if (sub_graph[q] < 0 || sub_graph[q] >= n_graphs) return CMP_EINVAL;
-    const cmp_status st = plan_sub(graphs[sub_graph[q]], sub_mask[q], d, w, q, P);
+    const cmp_status st = plan_sub(graphs[sub_graph[q]], sub_mask[q], d, w, q, shape.cond_chunk, P);
     if (st != CMP_OK) return st;
   }
   std::memset(H, 0, sizeof(*H));
@@ -179,8 +194,8 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
   H->w = w;
   H->max_slots = P->max_slots;
   H->max_in = P->max_in;
-  H->threads = kEstThreads;
-  const int64_t cap = int64_t(sm_count()) * 2;
+  H->threads = shape.threads;
+  const int64_t cap = int64_t(sm_count()) * shape.ctas_per_sm;
   H->grid = int32_t(std::max<int64_t>(1, std::min<int64_t>(int64_t(P->items.size()), cap)));
   H->n_sub = n_sub;
   H->n_ops = int64_t(P->ops.size());
@@ -231,12 +246,12 @@ cmp_status cmp_presort(const int32_t* counters_dev, int64_t n_rows, int32_t w, u
 }
 
 cmp_status cmp_estimate_plan_bytes(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
-                                   const int32_t* sub_graph, const uint64_t* sub_mask, size_t* plan_bytes,
-                                   size_t* ws_bytes) {
+                                   const int32_t* sub_graph, const uint64_t* sub_mask, const cmp_estimate_cfg* cfg,
+                                   size_t* plan_bytes, size_t* ws_bytes) {
   if (!plan_bytes || !ws_bytes) return CMP_EINVAL;
   PlanOut P;
   EstPlanHdr H;
-  const cmp_status st = plan_all(graphs, n_graphs, d, w, n_sub, sub_graph, sub_mask, &P, &H);
+  const cmp_status st = plan_all(graphs, n_graphs, d, w, n_sub, sub_graph, sub_mask, cfg, &P, &H);
   if (st != CMP_OK) return st;
   *plan_bytes = size_t(H.total_bytes);
   *ws_bytes = size_t(H.ws_bytes);
@@ -244,12 +259,12 @@ cmp_status cmp_estimate_plan_bytes(const cmp_graph* graphs, int32_t n_graphs, in
 }
 
 cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
-                                    const int32_t* sub_graph, const uint64_t* sub_mask, void* plan_host,
-                                    size_t plan_bytes) {
+                                    const int32_t* sub_graph, const uint64_t* sub_mask, const cmp_estimate_cfg* cfg,
+                                    void* plan_host, size_t plan_bytes) {
   if (!plan_host) return CMP_EINVAL;
   PlanOut P;
   EstPlanHdr H;
-  const cmp_status st = plan_all(graphs, n_graphs, d, w, n_sub, sub_graph, sub_mask, &P, &H);
+  const cmp_status st = plan_all(graphs, n_graphs, d, w, n_sub, sub_graph, sub_mask, cfg, &P, &H);
   if (st != CMP_OK) return st;
   if (plan_bytes < size_t(H.total_bytes)) return CMP_EWORKSPACE;
   unsigned char* b = static_cast<unsigned char*>(plan_host);

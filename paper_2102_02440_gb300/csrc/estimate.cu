@@ -287,7 +287,7 @@ __device__ void block_scan(i128* a, int n, bool reverse, bool* ovf, BlockScratch
 // comparison with |s[c]| and its own term is one value.
 constexpr int kMaxIn = CMP_MAX_SKETCHES;
 
-__global__ void __launch_bounds__(512) k_estimate_items(const __grid_constant__ EstArgs A) {
+__global__ void __launch_bounds__(1024) k_estimate_items(const __grid_constant__ EstArgs A) {
   __shared__ i128 sh_i128[33];
   __shared__ int32_t sh_flag[1];
   __shared__ i128 sh_val[kMaxIn];
@@ -340,6 +340,13 @@ __global__ void __launch_bounds__(512) k_estimate_items(const __grid_constant__ 
           for (int r = tid; r < w; r += T) tab[r] = rank_of(absa, w, __ldg(absp + r), strict);
         }
       }
+      for (int a = 0; a < m; a++) {  // inverse permutation of conditioned inputs
+        const EstIn x = in[L[a]];
+        if (x.kind != kInCond) continue;
+        int32_t* inv = rk + int64_t(t++) * w;
+        const int32_t* perm = x.perm + ro;
+        for (int r = tid; r < w; r += T) inv[__ldg(perm + r)] = r;
+      }
       for (int a = 0; a < m; a++) {
         const EstIn x = in[L[a]];
         if (x.kind != kInLeaf) continue;
@@ -389,20 +396,27 @@ __global__ void __launch_bounds__(512) k_estimate_items(const __grid_constant__ 
           const int la = sh_L[tid];
           const EstIn& x = sh_in[la];
           if (x.kind == kInCond) {
+            // its cross ranks are the precomputed ones at bucket c's sorted position
+            int inv_tab = op.rank_off + m * (m - 1) + (p >= 0 ? m : 0);
+            for (int b = 0; b < tid; b++) inv_tab += sh_in[sh_L[b]].kind == kInCond;
+            const int rpos = rk[int64_t(inv_tab) * w + c];
             const uint32_t tau = sh_ac[tid];
             i128 v = i128(__ldg(x.s + ro + c));
             bool o1 = false;
-            for (int b = 0; b < m && v != 0; b++) {
+            int tb = op.rank_off + tid * (m - 1);
+            for (int b = 0; b < m; b++) {
               if (b == tid) continue;
               const int lb = sh_L[b];
               const EstIn& y = sh_in[lb];
               const bool strict = lb < la;
-              if (y.kind == kInCond) {
-                if (!(strict ? sh_ac[b] > tau : sh_ac[b] >= tau)) v = 0;
-              } else {
-                const int q = rank_of(y.abs + ro, w, tau, strict);
-                o1 |= mul_ovf(v, suf[int64_t(y.suf) * W1 + q], &v);
+              if (v != 0) {
+                if (y.kind == kInCond) {
+                  if (!(strict ? sh_ac[b] > tau : sh_ac[b] >= tau)) v = 0;
+                } else {
+                  o1 |= mul_ovf(v, suf[int64_t(y.suf) * W1 + rk[int64_t(tb) * w + rpos]], &v);
+                }
               }
+              tb++;
             }
             sh_val[tid] = v;
             if (o1) atomicOr(sh_flag, 1);

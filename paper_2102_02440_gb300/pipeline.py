@@ -94,7 +94,7 @@ class DeviceEstimator:
     """Presorted sketches of a built DeviceWorkload plus an encoded estimate plan for a
     list of sub-plans (bit t = table t), replayable with one cmp_estimate call."""
 
-    def __init__(self, dws, masks, graph_of=None):
+    def __init__(self, dws, masks, graph_of=None, cfg=None):
         dws = dws if isinstance(dws, (list, tuple)) else [dws]
         self.dws = dws
         self.d, self.w = dws[0].d, dws[0].w
@@ -124,10 +124,10 @@ class DeviceEstimator:
         self.masks = np.ascontiguousarray(masks, np.uint64)
         self.sub_graph = np.zeros(self.masks.size, np.int32) if graph_of is None else np.ascontiguousarray(graph_of,
                                                                                                           np.int32)
-        pb, wb = K.cmp_estimate_plan_bytes(self.graphs, self.d, self.w, self.sub_graph, self.masks)
+        pb, wb = K.cmp_estimate_plan_bytes(self.graphs, self.d, self.w, self.sub_graph, self.masks, cfg)
         self.plan_host = np.zeros(max(pb, 16), np.uint8)
         K.cmp_estimate_plan_encode(self.graphs, self.d, self.w, self.sub_graph, self.masks,
-                                   self.plan_host.ctypes.data, pb)
+                                   self.plan_host.ctypes.data, pb, cfg)
         self.plan_dev = torch.from_numpy(self.plan_host).to(self.device)
         self.ws = torch.empty(max(wb, 16), dtype=torch.uint8, device=self.device)
         self.est = torch.empty(self.masks.size, dtype=torch.float64, device=self.device)
