@@ -224,6 +224,30 @@ cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, i
 cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_dev, size_t ws_bytes, double* est_dev,
                         int64_t* row_est_dev, int32_t* status_dev, void* stream);
 
+/* Size of the device workspace built into the library for cmp_estimate_noalloc. */
+#define CMP_NOALLOC_WS_BYTES (32u << 20)
+
+/* cmp_estimate without a caller-provided workspace.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory themselves, such as
+ * an operator running inside a host engine that owns every device allocation (a
+ * database's GPU executor, a serving process with a fixed memory pool), or a latency-
+ * critical path that must not call cudaMalloc because it can synchronise the device.
+ * Arguments and results are those of cmp_estimate for the same plan.
+ *   Workspace: a fixed array of CMP_NOALLOC_WS_BYTES bytes inside the library's device
+ *   image, held by every GPU that loads the library until the process exits.  The
+ *   library allocates and frees nothing at call time.  The plan's per-item partial sums
+ *   must fit in it together with at least one CTA's scratch, else CMP_EWORKSPACE;
+ *   the persistent grid shrinks to the number of CTA scratch areas that fit, so a large
+ *   plan runs with fewer CTAs than cmp_estimate would use.
+ *   Set-up: the first call on each device looks up the array's device address (with
+ *   that device current) and caches it; make that first call before any stream capture.
+ *   Sharing: every call, on any stream, uses the same array.  Nothing in it needs to
+ *   start at zero (each launch writes what it reads), and it keeps the last call's
+ *   contents; calls whose executions overlap on the GPU race on it, so serialise them
+ *   (one stream, or events between streams). */
+cmp_status cmp_estimate_noalloc(const void* plan_host, const void* plan_dev, double* est_dev, int64_t* row_est_dev,
+                                int32_t* status_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,6 +93,7 @@ _SIGS = {
                                              C.c_size_t]),
     "cmp_estimate": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]),
+    "cmp_estimate_noalloc": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cmp_mlp_param_count": (C.c_int64, [C.c_int32, C.c_int32]),
     "cmp_mlp_features": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
@@ -230,6 +231,15 @@ def cmp_estimate(plan_host: int, plan_dev: int, ws_dev: int, ws_bytes: int, est_
                  status_dev: int, stream: int):
     _check("cmp_estimate", lib().cmp_estimate(plan_host, plan_dev, ws_dev, ws_bytes, est_dev, row_est_dev,
                                               status_dev, stream))
+
+
+CMP_NOALLOC_WS_BYTES = 32 << 20
+
+
+def cmp_estimate_noalloc(plan_host: int, plan_dev: int, est_dev: int, row_est_dev: int, status_dev: int,
+                         stream: int):
+    _check("cmp_estimate_noalloc", lib().cmp_estimate_noalloc(plan_host, plan_dev, est_dev, row_est_dev, status_dev,
+                                                              stream))
 
 
 def cmp_mlp_param_count(nin: int, nh: int) -> int:
