@@ -224,6 +224,56 @@ cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, i
 cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_dev, size_t ws_bytes, double* est_dev,
                         int64_t* row_est_dev, int32_t* status_dev, void* stream);
 
+/* ------------------------------------------------------------- learned combiner */
+/* Not in the paper, which combines the d row estimates of a sketch by their median
+ * (Sec. 3.2).  A 2-layer perceptron over features of the row estimates replaces the
+ * median:  y = base + W2 relu(W1 x + b1) + b2,  nin -> nh -> 1, predicting ln(1 + J) / 32
+ * for join size J, where base = max(x[skip], 0) if skip >= 0 (a skip connection: with
+ * skip = the median row feature, d / 2, the network learns a correction to the median)
+ * and 0 if skip = -1.  Parameters are fp32 (the master copy the optimiser updates), laid out
+ * W1[nh][nin], b1[nh], W2[nh], b2; every forward and backward pass uses their bfloat16
+ * roundings (nearest even) and accumulates in fp32.  nin <= 66, nh <= 64. */
+
+/* Number of parameters, or -1 for unsupported sizes. */
+int64_t cmp_mlp_param_count(int32_t nin, int32_t nh);
+
+/* Self-join size estimate of each sketch: f2_dev[s] = median over rows i of
+ * sum_j C[s][i][j]^2 (the Fast-AGMS estimator of Sec. 3.2 applied to a sketch with
+ * itself), exact per row and rounded once.  counters_dev: [n_sketches][d][w]. */
+cmp_status cmp_sketch_f2(const int32_t* counters_dev, int64_t n_sketches, int32_t d, int32_t w, double* f2_dev,
+                         void* stream);
+
+/* Features of n estimates: with v the d values sign(E_i) ln(1 + |E_i|) / 32 sorted
+ * ascending and m = d / 2, feat_dev[q] (fp32, d + 2 values) = v_i - v_m for i != m, v_m at
+ * i = m (the median order statistic itself), then ln(1 + f2a[q]) / 32 and
+ * ln(1 + f2b[q]) / 32.  row_est_dev: [n][d][2] int128 row estimates as from cmp_estimate. */
+cmp_status cmp_mlp_features(const int64_t* row_est_dev, int64_t n, int32_t d, const double* f2a_dev,
+                            const double* f2b_dev, float* feat_dev, void* stream);
+
+/* Forward pass: y_dev[s] for the n rows of x_dev ([n][nin] fp32). */
+cmp_status cmp_mlp_infer(const float* params_dev, int32_t nin, int32_t nh, int32_t skip, const float* x_dev, int64_t n,
+                         float* y_dev, void* stream);
+
+/* Combined estimate of n sub-plans: est_dev[q] = median_dev[q] (the plain median of
+ * cmp_estimate) where it is at least one tuple, else max(exp(32 y_dev[q]) - 1, 0) (the
+ * network's prediction).  The median stays the estimate wherever it gives a usable join
+ * size; the network replaces it where the median row estimate is zero or negative. */
+cmp_status cmp_mlp_combine(const double* median_dev, const float* y_dev, int64_t n, double* est_dev, void* stream);
+
+/* One full-batch training step on n samples: loss = (1/n) sum (y - t)^2 when
+ * huber_delta == 0, else the mean Huber loss (0.5 e^2 for |e| <= delta, delta (|e| -
+ * delta / 2) beyond; its linear tails make the fit follow the conditional median), its
+ * gradient with respect to the bf16-rounded parameters (summed in a fixed order, so runs
+ * are reproducible), then Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected with
+ * `step` >= 1) on params/adam_m/adam_v (fp32, zero-initialised moments).  loss_dev and
+ * grad_dev (the gradient before the update) are optional outputs.  Workspace:
+ * cmp_mlp_train_ws_bytes(nin, nh, n) bytes. */
+size_t cmp_mlp_train_ws_bytes(int32_t nin, int32_t nh, int64_t n);
+cmp_status cmp_mlp_train_step(float* params_dev, float* adam_m_dev, float* adam_v_dev, int32_t nin, int32_t nh,
+                              int32_t skip, const float* x_dev, const float* y_dev, int64_t n, float huber_delta,
+                              float lr, int32_t step, float* loss_dev, float* grad_dev, void* ws_dev, size_t ws_bytes,
+                              void* stream);
+
 /* Size of the device workspace built into the library for cmp_estimate_noalloc. */
 #define CMP_NOALLOC_WS_BYTES (32u << 20)
 

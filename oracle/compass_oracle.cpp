@@ -759,13 +759,14 @@ int orc_bf16_round(int64_t n, const float* in, float* out) {
   return 0;
 }
 
-int orc_mlp_forward(int nin, int nh, const float* params, int64_t n, const float* x, double* y) {
+int orc_mlp_forward(int nin, int nh, int skip, const float* params, int64_t n, const float* x, double* y) {
   const float* W1 = params;
   const float* b1 = W1 + (size_t)nh * nin;
   const float* W2 = b1 + nh;
   const float* b2 = W2 + nh;
   for (int64_t r = 0; r < n; r++) {
     double acc = bf16_round(b2[0]);
+    if (skip >= 0) acc += std::max(0.0, (double)x[r * nin + skip]);
     for (int h = 0; h < nh; h++) {
       double z = bf16_round(b1[h]);
       for (int c = 0; c < nin; c++) z += (double)bf16_round(W1[(size_t)h * nin + c]) * (double)x[r * nin + c];
@@ -778,8 +779,11 @@ int orc_mlp_forward(int nin, int nh, const float* params, int64_t n, const float
 
 /* loss = (1/n) sum (y - t)^2 and its gradient with respect to the bf16-rounded
  * parameters (applied to the fp32 master copy). grad has the params layout. */
-int orc_mlp_loss_grad(int nin, int nh, const float* params, int64_t n, const float* x, const float* t, double* loss,
-                      double* grad) {
+/* loss_kind 0: mean of (y - t)^2.  loss_kind 1: mean Huber loss with threshold delta,
+ * 0.5 e^2 for |e| <= delta and delta (|e| - 0.5 delta) beyond (L1-like tails, so the fit
+ * follows the conditional median of the target rather than its mean). */
+int orc_mlp_loss_grad(int nin, int nh, int skip, int loss_kind, double delta, const float* params, int64_t n,
+                      const float* x, const float* t, double* loss, double* grad) {
   const float* W1 = params;
   const float* b1 = W1 + (size_t)nh * nin;
   const float* W2 = b1 + nh;
@@ -794,6 +798,7 @@ int orc_mlp_loss_grad(int nin, int nh, const float* params, int64_t n, const flo
   double L = 0;
   for (int64_t r = 0; r < n; r++) {
     double y = bf16_round(b2[0]);
+    if (skip >= 0) y += std::max(0.0, (double)x[r * nin + skip]);
     for (int h = 0; h < nh; h++) {
       double zz = bf16_round(b1[h]);
       for (int c = 0; c < nin; c++) zz += (double)bf16_round(W1[(size_t)h * nin + c]) * (double)x[r * nin + c];
@@ -801,8 +806,15 @@ int orc_mlp_loss_grad(int nin, int nh, const float* params, int64_t n, const flo
       if (zz > 0) y += (double)bf16_round(W2[h]) * zz;
     }
     const double err = y - (double)t[r];
-    L += err * err;
-    const double dy = 2.0 * err / (double)n;
+    double dy;
+    if (loss_kind == 1) {
+      const double a = std::fabs(err);
+      L += a <= delta ? 0.5 * err * err : delta * (a - 0.5 * delta);
+      dy = (a <= delta ? err : (err > 0 ? delta : -delta)) / (double)n;
+    } else {
+      L += err * err;
+      dy = 2.0 * err / (double)n;
+    }
     gb2[0] += dy;
     for (int h = 0; h < nh; h++) {
       if (z[h] <= 0) continue;

@@ -228,23 +228,25 @@ def bf16_round(a) -> np.ndarray:
     return out
 
 
-def mlp_forward(nin: int, nh: int, params, x) -> np.ndarray:
+def mlp_forward(nin: int, nh: int, params, x, skip: int = -1) -> np.ndarray:
     params = np.ascontiguousarray(params, np.float32)
     x = np.ascontiguousarray(x, np.float32)
     n = x.shape[0]
     y = np.zeros(n, np.float64)
-    lib().orc_mlp_forward(nin, nh, C.c_void_p(_p(params)), C.c_int64(n), C.c_void_p(_p(x)), C.c_void_p(_p(y)))
+    lib().orc_mlp_forward(nin, nh, skip, C.c_void_p(_p(params)), C.c_int64(n), C.c_void_p(_p(x)), C.c_void_p(_p(y)))
     return y
 
 
-def mlp_loss_grad(nin: int, nh: int, params, x, t):
+def mlp_loss_grad(nin: int, nh: int, params, x, t, skip: int = -1, huber_delta: float | None = None):
     params = np.ascontiguousarray(params, np.float32)
     x = np.ascontiguousarray(x, np.float32)
     t = np.ascontiguousarray(t, np.float32)
     g = np.zeros(params.size, np.float64)
     loss = np.zeros(1, np.float64)
-    lib().orc_mlp_loss_grad(nin, nh, C.c_void_p(_p(params)), C.c_int64(x.shape[0]), C.c_void_p(_p(x)),
-                            C.c_void_p(_p(t)), C.c_void_p(_p(loss)), C.c_void_p(_p(g)))
+    kind = 0 if huber_delta is None else 1
+    lib().orc_mlp_loss_grad(nin, nh, skip, kind, C.c_double(huber_delta or 0.0), C.c_void_p(_p(params)),
+                            C.c_int64(x.shape[0]), C.c_void_p(_p(x)), C.c_void_p(_p(t)), C.c_void_p(_p(loss)),
+                            C.c_void_p(_p(g)))
     return float(loss[0]), g
 
 

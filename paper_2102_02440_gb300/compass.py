@@ -95,13 +95,16 @@ _SIGS = {
                                  C.c_void_p, C.c_void_p]),
     "cmp_estimate_noalloc": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cmp_mlp_param_count": (C.c_int64, [C.c_int32, C.c_int32]),
+    "cmp_sketch_f2": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "cmp_mlp_features": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
-    "cmp_mlp_infer": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "cmp_mlp_infer": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p,
+                                  C.c_void_p]),
+    "cmp_mlp_combine": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "cmp_mlp_train_ws_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int64]),
-    "cmp_mlp_train_step": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
-                                       C.c_void_p, C.c_int64, C.c_float, C.c_int32, C.c_void_p, C.c_void_p,
-                                       C.c_void_p, C.c_size_t, C.c_void_p]),
+    "cmp_mlp_train_step": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                       C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_float, C.c_int32,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
 }
 
 
@@ -246,20 +249,29 @@ def cmp_mlp_param_count(nin: int, nh: int) -> int:
     return int(lib().cmp_mlp_param_count(nin, nh))
 
 
+def cmp_sketch_f2(counters_dev: int, n_sketches: int, d: int, w: int, f2_dev: int, stream: int):
+    _check("cmp_sketch_f2", lib().cmp_sketch_f2(counters_dev, n_sketches, d, w, f2_dev, stream))
+
+
 def cmp_mlp_features(row_est_dev: int, n: int, d: int, f2a_dev: int, f2b_dev: int, feat_dev: int, stream: int):
     _check("cmp_mlp_features", lib().cmp_mlp_features(row_est_dev, n, d, f2a_dev, f2b_dev, feat_dev, stream))
 
 
-def cmp_mlp_infer(params_dev: int, nin: int, nh: int, x_dev: int, n: int, y_dev: int, stream: int):
-    _check("cmp_mlp_infer", lib().cmp_mlp_infer(params_dev, nin, nh, x_dev, n, y_dev, stream))
+def cmp_mlp_infer(params_dev: int, nin: int, nh: int, skip: int, x_dev: int, n: int, y_dev: int, stream: int):
+    _check("cmp_mlp_infer", lib().cmp_mlp_infer(params_dev, nin, nh, skip, x_dev, n, y_dev, stream))
+
+
+def cmp_mlp_combine(median_dev: int, y_dev: int, n: int, est_dev: int, stream: int):
+    _check("cmp_mlp_combine", lib().cmp_mlp_combine(median_dev, y_dev, n, est_dev, stream))
 
 
 def cmp_mlp_train_ws_bytes(nin: int, nh: int, n: int) -> int:
     return int(lib().cmp_mlp_train_ws_bytes(nin, nh, n))
 
 
-def cmp_mlp_train_step(params_dev: int, m_dev: int, v_dev: int, nin: int, nh: int, x_dev: int, y_dev: int, n: int,
-                       lr: float, step: int, loss_dev: int, grad_dev: int, ws_dev: int, ws_bytes: int, stream: int):
+def cmp_mlp_train_step(params_dev: int, m_dev: int, v_dev: int, nin: int, nh: int, skip: int, x_dev: int, y_dev: int,
+                       n: int, huber_delta: float, lr: float, step: int, loss_dev: int, grad_dev: int, ws_dev: int,
+                       ws_bytes: int, stream: int):
     _check("cmp_mlp_train_step",
-           lib().cmp_mlp_train_step(params_dev, m_dev, v_dev, nin, nh, x_dev, y_dev, n, C.c_float(lr), step, loss_dev,
-                                    grad_dev, ws_dev, ws_bytes, stream))
+           lib().cmp_mlp_train_step(params_dev, m_dev, v_dev, nin, nh, skip, x_dev, y_dev, n, C.c_float(huber_delta),
+                                    C.c_float(lr), step, loss_dev, grad_dev, ws_dev, ws_bytes, stream))

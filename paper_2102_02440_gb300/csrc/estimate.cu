@@ -56,51 +56,6 @@ __device__ __forceinline__ bool mul_ovf(i128 a, i128 b, i128* r) {
   return ovf;
 }
 
-// Round-to-nearest-even of (neg ? -1 : 1) * (top * 2^128 + mag) to binary64, from the
-// definition: the top 53 significant bits, then half-ulp and sticky bits.
-__device__ double mag_to_double(bool neg, uint32_t top, u128 mag) {
-  if (top == 0 && mag == 0) return 0.0;
-  // bit length
-  int nb;
-  if (top) nb = 129;
-  else {
-    const uint64_t hi = uint64_t(mag >> 64);
-    nb = hi ? 128 - __clzll(hi) : 64 - __clzll(uint64_t(mag));
-  }
-  double r;
-  if (nb <= 53) {
-    r = double(uint64_t(mag));
-  } else {
-    const int sh = nb - 53;  // bits below the kept significand
-    u128 sig, rest_mask, rest, half;
-    if (top) {  // nb == 129: value = 2^128 + mag
-      sig = (u128(1) << 52) | (mag >> 76);
-      rest_mask = (u128(1) << 76) - 1;
-      rest = mag & rest_mask;
-      half = u128(1) << 75;
-    } else {
-      sig = mag >> sh;
-      rest_mask = (u128(1) << sh) - 1;
-      rest = mag & rest_mask;
-      half = u128(1) << (sh - 1);
-    }
-    uint64_t s = uint64_t(sig);
-    if (rest > half || (rest == half && (s & 1))) s++;
-    int e = sh;
-    if (s == (1ull << 53)) {
-      s >>= 1;
-      e++;
-    }
-    r = ldexp(double(s), e);
-  }
-  return neg ? -r : r;
-}
-
-__device__ double i128_to_double(i128 v) {
-  const bool neg = v < 0;
-  return mag_to_double(neg, 0, neg ? u128(0) - u128(v) : u128(v));
-}
-
 // exact (a + b) / 2 rounded once (the sum may need 129 bits)
 __device__ double mean2_to_double(i128 a, i128 b) {
   i128 s;

@@ -280,3 +280,90 @@ def connected_subplans(n_tables: int, edge_u, edge_v, min_size: int = 1) -> list
         if seen == mask:
             out.append(mask)
     return out
+
+
+def join_pairs(n_pairs: int, rows_lo: int = 10_000, rows_hi: int = 10_000_000, dom_lo: int = 1_000,
+               dom_hi: int = 1_000_000, s_lo: float = 0.5, s_hi: float = 1.5, seed: int = 20210208):
+    """Independent two-table joins for the learned combiner: per pair, row counts
+    log-uniform in [rows_lo, rows_hi], one domain log-uniform in [dom_lo, dom_hi], and
+    each side's keys Zipf(s) with s uniform in [s_lo, s_hi] (own permutation of the
+    domain), no predicates.  Returns a list of (keys_R, keys_S) int32 arrays."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_pairs):
+        dom = int(np.exp(rng.uniform(np.log(dom_lo), np.log(dom_hi))))
+        pair = []
+        for _side in range(2):
+            n = int(np.exp(rng.uniform(np.log(rows_lo), np.log(rows_hi))))
+            pair.append(zipf_keys(rng, n, dom, float(rng.uniform(s_lo, s_hi))))
+        out.append(tuple(pair))
+    return out
+
+
+def zipf_ranks_device(gen, s, N):
+    """Device version of zipf_ranks with one (s, N) per element: s, N are float64 torch
+    tensors of equal length on the generator's device; returns int64 ranks in [1, N].
+    Same rejection-inversion as zipf_ranks, with rejected elements redrawn."""
+    import torch
+
+    one_minus_s = 1.0 - s
+
+    def expm1_over(t):
+        small = t.abs() <= 1e-8
+        return torch.where(small, 1.0 + t / 2.0 + t * t / 6.0, torch.expm1(t) / torch.where(small, 1.0, t))
+
+    def log1p_over(t):
+        small = t.abs() <= 1e-8
+        return torch.where(small, 1.0 - t / 2.0 + t * t / 3.0, torch.log1p(t) / torch.where(small, 1.0, t))
+
+    def H(x, oms):
+        lx = torch.log(x)
+        return lx * expm1_over(lx * oms)
+
+    def Hinv(y, oms):
+        return torch.exp(y * log1p_over(y * oms))
+
+    lo = H(torch.full_like(s, 1.5), one_minus_s) - 1.0
+    hi = H(N + 0.5, one_minus_s)
+    out = torch.zeros_like(s, dtype=torch.int64)
+    todo = torch.arange(s.numel(), device=s.device)
+    while todo.numel():
+        ss, oms, l, h, NN = s[todo], one_minus_s[todo], lo[todo], hi[todo], N[todo]
+        u = l + torch.rand(todo.numel(), dtype=torch.float64, device=s.device, generator=gen) * (h - l)
+        k = torch.clamp(torch.floor(Hinv(u, oms) + 0.5), min=1.0)
+        k = torch.minimum(k, NN)
+        acc = u >= H(k + 0.5, oms) - torch.pow(k, -ss)
+        out[todo[acc]] = k[acc].to(torch.int64)
+        todo = todo[~acc]
+    return out
+
+
+def join_pairs_device(n_pairs: int, rows_lo: int, rows_hi: int, dom_lo: int = 1_000, dom_hi: int = 1_000_000,
+                      s_lo: float = 0.5, s_hi: float = 1.5, seed: int = 20210208, device="cuda"):
+    """join_pairs drawn on the device, all tables at once.  Returns (keys, offsets, meta):
+    keys int32 [total] on the device, offsets int64 [2 n_pairs + 1] (table t is
+    keys[offsets[t]:offsets[t+1]]; tables 2i and 2i+1 form pair i), meta = numpy arrays
+    (rows, domain, s) per table."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    dom = np.exp(rng.uniform(np.log(dom_lo), np.log(dom_hi), n_pairs)).astype(np.int64)
+    rows = np.exp(rng.uniform(np.log(rows_lo), np.log(rows_hi), 2 * n_pairs)).astype(np.int64)
+    sk = rng.uniform(s_lo, s_hi, 2 * n_pairs)
+    dom_t = np.repeat(dom, 2)
+    A = np.empty(2 * n_pairs, np.int64)
+    B = np.empty(2 * n_pairs, np.int64)
+    for t in range(2 * n_pairs):
+        A[t], B[t] = affine_perm(rng, int(dom_t[t]))
+    offsets = np.concatenate([[0], np.cumsum(rows)])
+    table_of = torch.repeat_interleave(torch.arange(2 * n_pairs, device=device), torch.from_numpy(rows).to(device))
+    s_el = torch.from_numpy(sk).to(device)[table_of]
+    N_el = torch.from_numpy(dom_t.astype(np.float64)).to(device)[table_of]
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    r = zipf_ranks_device(gen, s_el, N_el) - 1
+    A_el = torch.from_numpy(A).to(device)[table_of]
+    B_el = torch.from_numpy(B).to(device)[table_of]
+    D_el = torch.from_numpy(dom_t).to(device)[table_of]
+    keys = ((A_el * r + B_el) % D_el).to(torch.int32)
+    return keys, offsets, {"rows": rows, "domain": dom_t, "s": sk}

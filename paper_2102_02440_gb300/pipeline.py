@@ -41,7 +41,7 @@ class DeviceTable:
 
 
 class DeviceWorkload:
-    def __init__(self, wl, device="cuda", hash_seed: int | None = None):
+    def __init__(self, wl, device="cuda", hash_seed: int | None = None, cols_dev=None):
         self.wl = wl
         self.device = torch.device(device)
         self.d, self.w = wl.d, wl.w
@@ -51,7 +51,8 @@ class DeviceWorkload:
         hp = np.frombuffer(self.hash_host, dtype=np.uint64, count=max(self.n_edges * self.d, 1) * 6).copy()
         self.hash_u64 = hp[: self.n_edges * self.d * 6].reshape(self.n_edges, self.d, 6)
         self.hash_dev = torch.from_numpy(hp.view(np.int64)).to(self.device)
-        self.tables = [DeviceTable(t, self.d, self.w, self.device) for t in wl.tables]
+        self.tables = [DeviceTable(t, self.d, self.w, self.device, cols_dev=cols_dev[i] if cols_dev else None)
+                       for i, t in enumerate(wl.tables)]
         self.survivors = torch.zeros(len(self.tables), dtype=torch.int64, device=self.device)
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
         self._plan = None
@@ -152,3 +153,128 @@ class DeviceEstimator:
         lo = r[..., 0].astype(np.uint64).astype(object)
         hi = r[..., 1].astype(object)
         return (hi * (1 << 64) + lo).tolist()
+
+
+class PairBatch:
+    """N independent two-table joins R_i |x| S_i on a key: every sketch built in one
+    batched launch, all N two-way estimates in one plan (one graph per pair), and the
+    learned combiner's features over them."""
+
+    def __init__(self, pairs, d: int, w: int, hash_seed: int, device="cuda", cfg=None, device_keys=None, offsets=None):
+        """pairs: list of (keys_R, keys_S) host arrays; or device_keys (one int32 device
+        tensor) with offsets (table t = device_keys[offsets[t]:offsets[t+1]], tables 2i
+        and 2i+1 forming pair i)."""
+        from . import datagen as G
+        tables, eu, ev, cols_dev = [], [], [], None
+        if device_keys is not None:
+            n_pairs = (len(offsets) - 1) // 2
+            cols_dev = []
+            for t in range(2 * n_pairs):
+                n = int(offsets[t + 1] - offsets[t])
+                shape_only = np.lib.stride_tricks.as_strided(np.zeros(1, np.int32), shape=(n,), strides=(0,))
+                tables.append(G.Table(f"T{t}", [shape_only], [], [0], [t // 2]))
+                cols_dev.append([device_keys[int(offsets[t]):int(offsets[t + 1])]])
+        else:
+            n_pairs = len(pairs)
+            for i, (a, b) in enumerate(pairs):
+                tables += [G.Table(f"R{i}", [a], [], [0], [i]), G.Table(f"S{i}", [b], [], [0], [i])]
+        for i in range(n_pairs):
+            eu.append(2 * i)
+            ev.append(2 * i + 1)
+        self.n = n_pairs
+        self.d, self.w = d, w
+        self.dw = DeviceWorkload(G.Workload("pairs", tables, eu, ev, d, w, hash_seed, 0), device=device,
+                                 cols_dev=cols_dev)
+        self.device = self.dw.device
+        self.cfg = cfg
+        # one contiguous [2n][d][w] counter buffer: presort and self-join sizes in one launch each
+        self.counters = torch.zeros((2 * self.n, d, w), dtype=torch.int32, device=self.device)
+        for i, t in enumerate(self.dw.tables):
+            t.counters = self.counters[i:i + 1]
+
+    def build(self, stream=None):
+        self.dw.build_batched(self.cfg, stream)
+
+    def prepare_estimate(self):
+        dw, d, w = self.dw, self.d, self.w
+        self.abs = torch.empty((2 * self.n, d, w), dtype=torch.int32, device=self.device)
+        self.perm = torch.empty_like(self.abs)
+        self.graphs, self._keep = [], []
+        eu = (C.c_int32 * 1)(0)
+        ev = (C.c_int32 * 1)(1)
+        self._keep += [eu, ev]
+        for i in range(self.n):
+            a, b = dw.tables[2 * i].counters[0], dw.tables[2 * i + 1].counters[0]
+            skp = (C.c_void_p * 2)(a.data_ptr(), b.data_ptr())
+            abp = (C.c_void_p * 2)(self.abs[2 * i].data_ptr(), self.abs[2 * i + 1].data_ptr())
+            pmp = (C.c_void_p * 2)(self.perm[2 * i].data_ptr(), self.perm[2 * i + 1].data_ptr())
+            self._keep += [skp, abp, pmp]
+            self.graphs.append(K.cmp_graph(2, 1, eu, ev, skp, abp, pmp, dw.survivors.data_ptr() + 16 * i))
+        sub_graph = np.arange(self.n, dtype=np.int32)
+        masks = np.full(self.n, 0b11, np.uint64)
+        pb, wb = K.cmp_estimate_plan_bytes(self.graphs, d, w, sub_graph, masks)
+        self.plan_host = np.zeros(max(pb, 16), np.uint8)
+        K.cmp_estimate_plan_encode(self.graphs, d, w, sub_graph, masks, self.plan_host.ctypes.data, pb)
+        self.plan_dev = torch.from_numpy(self.plan_host).to(self.device)
+        self.ws = torch.empty(max(wb, 16), dtype=torch.uint8, device=self.device)
+        self.est = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        self.row_est = torch.empty((self.n, d, 2), dtype=torch.int64, device=self.device)
+        self.f2 = torch.empty(2 * self.n, dtype=torch.float64, device=self.device)
+        self.feat = torch.empty((self.n, d + 2), dtype=torch.float32, device=self.device)
+
+    def estimate(self, stream=None):
+        s = K.stream_handle(stream)
+        K.cmp_presort(self.counters.data_ptr(), 2 * self.n * self.d, self.w, self.abs.data_ptr(), self.perm.data_ptr(),
+                      0, 0, s)
+        K.cmp_estimate(self.plan_host.ctypes.data, self.plan_dev.data_ptr(), self.ws.data_ptr(), self.ws.numel(),
+                       self.est.data_ptr(), self.row_est.data_ptr(), self.dw.status.data_ptr(), s)
+
+    def features(self, stream=None):
+        s = K.stream_handle(stream)
+        K.cmp_sketch_f2(self.counters.data_ptr(), 2 * self.n, self.d, self.w, self.f2.data_ptr(), s)
+        f2 = self.f2.view(self.n, 2)
+        self.f2a = f2[:, 0].contiguous()
+        self.f2b = f2[:, 1].contiguous()
+        K.cmp_mlp_features(self.row_est.data_ptr(), self.n, self.d, self.f2a.data_ptr(), self.f2b.data_ptr(),
+                           self.feat.data_ptr(), s)
+        return self.feat
+
+
+class Combiner:
+    """The learned combiner's parameters and Adam state on the device."""
+
+    def __init__(self, nin: int, nh: int = 64, seed: int = 0, device="cuda", skip: int = -1, init_scale: float = 1.0):
+        self.nin, self.nh, self.skip = nin, nh, skip
+        npar = K.cmp_mlp_param_count(nin, nh)
+        rng = np.random.default_rng(seed)
+        p = np.zeros(npar, np.float32)
+        p[: nh * nin] = rng.standard_normal(nh * nin) * np.sqrt(2.0 / nin)
+        p[nh * nin + nh: nh * nin + 2 * nh] = rng.standard_normal(nh) * np.sqrt(1.0 / nh) * init_scale
+        self.params = torch.from_numpy(p).to(device)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step = 0
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.grad = torch.zeros_like(self.params)
+        self._ws = None
+
+    def train_step(self, x: torch.Tensor, t: torch.Tensor, lr: float, huber_delta: float = 0.0, stream=None):
+        n = x.shape[0]
+        need = K.cmp_mlp_train_ws_bytes(self.nin, self.nh, n)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(max(need, 16), dtype=torch.uint8, device=x.device)
+        self.step += 1
+        K.cmp_mlp_train_step(self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), self.nin, self.nh, self.skip,
+                             x.data_ptr(), t.data_ptr(), n, huber_delta, lr, self.step, self.loss.data_ptr(), self.grad.data_ptr(),
+                             self._ws.data_ptr(), self._ws.numel(), K.stream_handle(stream))
+
+    def combine(self, median: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
+        out = torch.empty_like(median)
+        K.cmp_mlp_combine(median.data_ptr(), y.data_ptr(), median.numel(), out.data_ptr(), K.stream_handle(stream))
+        return out
+
+    def infer(self, x: torch.Tensor, stream=None) -> torch.Tensor:
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        K.cmp_mlp_infer(self.params.data_ptr(), self.nin, self.nh, self.skip, x.data_ptr(), x.shape[0], y.data_ptr(),
+                        K.stream_handle(stream))
+        return y

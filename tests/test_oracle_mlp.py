@@ -39,6 +39,24 @@ def test_forward_matches_numpy(orc):
     np.testing.assert_allclose(orc.mlp_forward(NIN, NH, p, x), want, rtol=1e-12, atol=1e-12)
 
 
+def test_skip_connection_adds_the_clamped_feature(orc):
+    """y = max(x[skip], 0) + MLP(x): the difference to the no-skip output is exactly the
+    clamped feature, and the gradient (no parameter on the skip path) is unchanged."""
+    rng = np.random.default_rng(9)
+    p = _params(rng)
+    x = rng.standard_normal((30, NIN)).astype(np.float32)
+    t = rng.standard_normal(30).astype(np.float32)
+    y0 = orc.mlp_forward(NIN, NH, p, x)
+    y5 = orc.mlp_forward(NIN, NH, p, x, skip=5)
+    np.testing.assert_allclose(y5 - y0, np.maximum(x[:, 5].astype(np.float64), 0), rtol=0, atol=1e-12)
+    # loss/grad with skip equal those without skip on targets shifted by the skip term
+    l5, g5 = orc.mlp_loss_grad(NIN, NH, p, x, t, skip=5)
+    t_shift = (t.astype(np.float64) - np.maximum(x[:, 5], 0)).astype(np.float32)
+    l0, g0 = orc.mlp_loss_grad(NIN, NH, p, x, t_shift)
+    assert abs(l5 - l0) < 1e-5 * max(l0, 1e-9) + 1e-9
+    np.testing.assert_allclose(g5, g0, rtol=1e-4, atol=1e-7)
+
+
 def _pattern(p, x):
     W1 = p[:NH * NIN].reshape(NH, NIN).astype(np.float64)
     b1 = p[NH * NIN:NH * NIN + NH].astype(np.float64)
@@ -69,6 +87,36 @@ def test_gradient_by_central_differences(orc):
         fd = (lp - lm) / (2 * float(h))   # exact for a quadratic, up to rounding
         assert abs(fd - g[i]) <= 1e-9 + 1e-7 * abs(g[i]), (i, fd, g[i])
     assert checked >= 40
+
+
+def test_huber_gradient_by_central_differences(orc):
+    """Huber loss (quadratic within delta, linear beyond): gradient vs central differences,
+    with a step small enough that no residual crosses +-delta or a ReLU kink."""
+    rng = np.random.default_rng(11)
+    p = orc.bf16_round(_params(rng))
+    x = rng.standard_normal((40, NIN)).astype(np.float32)
+    t = rng.standard_normal(40).astype(np.float32)
+    delta = 0.5
+    _, g = orc.mlp_loss_grad(NIN, NH, p, x, t, skip=3, huber_delta=delta)
+    y0 = orc.mlp_forward(NIN, NH, p, x, skip=3)
+    checked = 0
+    for i in list(rng.choice(p.size, 40, replace=False)) + [p.size - 1]:
+        h = np.float32(2.0 ** (np.floor(np.log2(abs(p[i]) + 1e-3)) - 6))
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        yp, ym = orc.mlp_forward(NIN, NH, pp, x, skip=3), orc.mlp_forward(NIN, NH, pm, x, skip=3)
+        side = lambda y: np.sign(np.abs(y - t) - delta)
+        if not (np.array_equal(side(yp), side(y0)) and np.array_equal(side(ym), side(y0))):
+            continue
+        if not (np.array_equal(_pattern(pp, x), _pattern(p, x)) and np.array_equal(_pattern(pm, x), _pattern(p, x))):
+            continue
+        checked += 1
+        lp, _ = orc.mlp_loss_grad(NIN, NH, pp, x, t, skip=3, huber_delta=delta)
+        lm, _ = orc.mlp_loss_grad(NIN, NH, pm, x, t, skip=3, huber_delta=delta)
+        fd = (lp - lm) / (2 * float(h))
+        assert abs(fd - g[i]) <= 1e-9 + 1e-6 * abs(g[i]), (i, fd, g[i])
+    assert checked >= 20
 
 
 def test_adam_first_step_moves_by_lr(orc):
