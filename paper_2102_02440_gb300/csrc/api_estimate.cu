@@ -159,6 +159,8 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
   P->max_rank = std::max(P->max_rank, n_rank);
   sb.cond = cond.empty() ? 0 : 1;
   sb.n_ops = int32_t(P->ops.size()) - sb.op_begin;
+  if (sb.n_ops > kEstMaxOps || int32_t(P->ins.size()) - P->ops[sb.op_begin].in_begin > kEstMaxSubIn)
+    return CMP_EUNSUPPORTED;
   sb.n_chunks = cond.empty() ? 1 : (w + chunk - 1) / chunk;
   P->subs.push_back(sb);
   for (int i = 0; i < d; i++)

@@ -179,14 +179,21 @@ __device__ i128 block_sum(i128 v, bool* ovf, BlockScratch& bs) {
   return r;
 }
 
-// In-place inclusive scan of a[0..n) (forward) or suffix scan (reverse), checked.
-__device__ void block_scan(i128* a, int n, bool reverse, bool* ovf, BlockScratch& bs) {
+// Whether an exact value fits the storage type of the scratch arrays.
+__device__ __forceinline__ bool store_fits(i128 v, int64_t*) { return v == i128(int64_t(v)); }
+__device__ __forceinline__ bool store_fits(i128, i128*) { return true; }
+
+// In-place inclusive scan of a[0..n) (forward) or suffix scan (reverse).  Sums are exact
+// in int128 (bit 0 of the flag on overflow); a stored value that does not fit S sets
+// bit 1 (the item is then recomputed with int128 storage).
+template <typename S>
+__device__ void block_scan(S* a, int n, bool reverse, BlockScratch& bs) {
   const int T = blockDim.x, tid = threadIdx.x;
   const int per = (n + T - 1) / T;
   const int b = tid * per, e = min(n, b + per);
   i128 s = 0;
   bool o = false;
-  for (int q = b; q < e; q++) o |= add_ovf(s, a[reverse ? n - 1 - q : q], &s);
+  for (int q = b; q < e; q++) o |= add_ovf(s, i128(a[reverse ? n - 1 - q : q]), &s);
   // exclusive scan of thread sums (thread order = scan order)
   const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
   i128 incl = s;
@@ -217,130 +224,166 @@ __device__ void block_scan(i128* a, int n, bool reverse, bool* ovf, BlockScratch
   __syncthreads();
   i128 run;
   o |= add_ovf(bs.sh_i128[warp], incl - s, &run);  // incl - s cannot overflow: it is a partial sum
+  bool so = false;
   for (int q = b; q < e; q++) {
     const int idx = reverse ? n - 1 - q : q;
-    o |= add_ovf(run, a[idx], &run);
-    a[idx] = run;
+    o |= add_ovf(run, i128(a[idx]), &run);
+    so |= !store_fits(run, a);
+    a[idx] = S(run);
   }
   if (o) atomicOr(bs.sh_flag, 1);
-  __syncthreads();
-  *ovf |= bs.sh_flag[0] != 0;
+  if (so) atomicOr(bs.sh_flag, 2);
   __syncthreads();
 }
 
 }  // namespace
 
 // One CTA per work item (sub-plan, sketch row, range of conditioning values), persistent
-// over the item list.  Per-CTA scratch in the workspace:
-//   slots [max_slots][w]  messages (int128)
+// over the item list.  Per-CTA scratch in the workspace (S = int64, or int128 on retry):
+//   slots [max_slots][w]  messages
 //   suf   [max_suf][w+1]  suffix sums of each incoming message in its sketch's sorted
 //                         order (leaf inputs: computed once per item)
 //   pre   [max_in][w+1]   prefix sums of the "this edge attains the minimum" terms
 //   rank  [max_rank][w]   cross ranks between the sorted sketch rows of each table,
 //                         computed once per item (they do not depend on messages)
 // A conditioned input (unit vector at c) needs no array: its threshold sum is a
-// comparison with |s[c]| and its own term is one value.
+// comparison with |s[c]| and its own term is one value.  When some conditioned sketch
+// value s[c] is 0, every merged tensor entry at c through that table is 0 and c adds
+// nothing, so it is skipped.  Products and sums are exact int128; values stored in the
+// int64 arrays that do not fit flag the item for recomputation with int128 storage.
 constexpr int kMaxIn = CMP_MAX_SKETCHES;
 
-__global__ void __launch_bounds__(1024) k_estimate_items(const __grid_constant__ EstArgs A) {
+// kIlp elements per thread have their loads issued together (memory-level parallelism);
+// MAXT is the launch bound that sets the register budget.
+template <typename S, int kIlp, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__ EstArgs A, int retry) {
   __shared__ i128 sh_i128[33];
   __shared__ int32_t sh_flag[1];
   __shared__ i128 sh_val[kMaxIn];
   __shared__ uint32_t sh_ac[kMaxIn];
-  __shared__ EstIn sh_in[kMaxIn];
-  __shared__ int32_t sh_L[kMaxIn];
+  __shared__ EstOp sh_ops[kEstMaxOps];
+  __shared__ EstIn sh_in[kEstMaxSubIn];
+  __shared__ const int32_t* sh_cond[2];
+  __shared__ int32_t sh_ncond;
   BlockScratch bs{sh_i128, sh_flag};
   const int w = A.w;
   const int64_t W1 = int64_t(w) + 1;
   unsigned char* cta = reinterpret_cast<unsigned char*>(A.scratch) + int64_t(blockIdx.x) * A.scratch_per_cta;
-  i128* slots = reinterpret_cast<i128*>(cta);
-  i128* suf = slots + int64_t(A.max_slots) * w;
-  i128* pre = suf + int64_t(A.max_suf) * W1;
+  S* slots = reinterpret_cast<S*>(cta);
+  S* suf = slots + int64_t(A.max_slots) * w;
+  S* pre = suf + int64_t(A.max_suf) * W1;
   int32_t* rk = reinterpret_cast<int32_t*>(pre + int64_t(A.max_in) * W1);
   const int tid = threadIdx.x, T = blockDim.x;
 
   for (int64_t it = blockIdx.x; it < A.n_items; it += gridDim.x) {
+    if (retry && A.partial_ovf[it] != 2) continue;  // block-uniform
     const EstItem item = A.items[it];
     const EstSub sb = A.subs[item.sub];
     const int64_t ro = int64_t(item.row) * w;  // row offset inside every [d][w] array
+    const int in0 = A.ops[sb.op_begin].in_begin;
+    const int n_in = sb.n_ops ? A.ops[sb.op_begin + sb.n_ops - 1].in_begin + A.ops[sb.op_begin + sb.n_ops - 1].k - in0
+                              : 0;
+    for (int o = tid; o < sb.n_ops; o += T) {
+      EstOp op = A.ops[sb.op_begin + o];
+      op.in_begin -= in0;  // index into sh_in
+      sh_ops[o] = op;
+    }
+    for (int q = tid; q < n_in; q += T) sh_in[q] = A.inputs[in0 + q];
     if (tid == 0) sh_flag[0] = 0;
     __syncthreads();
-    bool ovf = false;
+    if (tid == 0) {
+      int nc = 0;
+      for (int q = 0; q < n_in && nc < 2; q++)
+        if (sh_in[q].kind == kInCond) sh_cond[nc++] = sh_in[q].s + ro;
+      sh_ncond = nc;
+    }
 
     // ---------------- prologue: cross ranks and leaf suffix sums (independent of c)
     for (int o = 0; o < sb.n_ops; o++) {
-      const EstOp op = A.ops[sb.op_begin + o];
-      const EstIn* in = A.inputs + op.in_begin;
-      int L[kMaxIn];
-      int m = 0;
-      for (int l = 0; l < op.k; l++)
-        if (l != op.p) L[m++] = l;
+      const EstOp op = sh_ops[o];
+      const EstIn* in = sh_in + op.in_begin;
+      const int p = op.p;
+      const int m = op.k - (p >= 0 ? 1 : 0);
       int t = op.rank_off;
       for (int a = 0; a < m; a++) {
-        const uint32_t* absa = in[L[a]].abs + ro;
+        const int la = a + (p >= 0 && a >= p ? 1 : 0);
+        const uint32_t* absa = in[la].abs + ro;
         for (int b = 0; b < m; b++) {
           if (b == a) continue;
-          const uint32_t* absb = in[L[b]].abs + ro;
+          const int lb = b + (p >= 0 && b >= p ? 1 : 0);
+          const uint32_t* absb = in[lb].abs + ro;
           int32_t* tab = rk + int64_t(t++) * w;
-          const bool strict = L[b] < L[a];
+          const bool strict = lb < la;
           for (int r = tid; r < w; r += T) tab[r] = rank_of(absb, w, __ldg(absa + r), strict);
         }
       }
-      if (op.p >= 0) {
-        const uint32_t* absp = in[op.p].abs + ro;
+      if (p >= 0) {
+        const uint32_t* absp = in[p].abs + ro;
         for (int a = 0; a < m; a++) {
+          const int la = a + (a >= p ? 1 : 0);
           int32_t* tab = rk + int64_t(t++) * w;
-          const uint32_t* absa = in[L[a]].abs + ro;
-          const bool strict = L[a] < op.p;
+          const uint32_t* absa = in[la].abs + ro;
+          const bool strict = la < p;
           for (int r = tid; r < w; r += T) tab[r] = rank_of(absa, w, __ldg(absp + r), strict);
         }
       }
       for (int a = 0; a < m; a++) {  // inverse permutation of conditioned inputs
-        const EstIn x = in[L[a]];
-        if (x.kind != kInCond) continue;
+        const int la = a + (p >= 0 && a >= p ? 1 : 0);
+        if (in[la].kind != kInCond) continue;
         int32_t* inv = rk + int64_t(t++) * w;
-        const int32_t* perm = x.perm + ro;
+        const int32_t* perm = in[la].perm + ro;
         for (int r = tid; r < w; r += T) inv[__ldg(perm + r)] = r;
       }
       for (int a = 0; a < m; a++) {
-        const EstIn x = in[L[a]];
+        const int la = a + (p >= 0 && a >= p ? 1 : 0);
+        const EstIn& x = in[la];
         if (x.kind != kInLeaf) continue;
-        i128* sl = suf + int64_t(x.suf) * W1;
+        S* sl = suf + int64_t(x.suf) * W1;
         const int32_t* perm = x.perm + ro;
-        for (int r = tid; r < w; r += T) sl[r] = i128(__ldg(x.msk + ro + __ldg(perm + r)));
+        for (int r = tid; r < w; r += T) sl[r] = S(__ldg(x.msk + ro + __ldg(perm + r)));
         if (tid == 0) sl[w] = 0;
         __syncthreads();
-        block_scan(sl, w, /*reverse=*/true, &ovf, bs);
+        block_scan(sl, w, /*reverse=*/true, bs);
       }
     }
     __syncthreads();
 
     i128 acc = 0;
+    bool ovf = false;
     for (int c = item.c0; c < item.c1; c++) {
+      bool zero = false;
+      for (int q = 0; q < sh_ncond; q++) zero |= __ldg(sh_cond[q] + c) == 0;
+      if (zero) continue;  // block-uniform
       for (int o = 0; o < sb.n_ops; o++) {
-        const EstOp op = A.ops[sb.op_begin + o];
+        const EstOp op = sh_ops[o];
+        const EstIn* in = sh_in + op.in_begin;
         const int k = op.k, p = op.p;
-        if (tid < k) sh_in[tid] = A.inputs[op.in_begin + tid];
-        __syncthreads();
-        int m = 0;
-        for (int l = 0; l < k; l++)
-          if (l != p) sh_L[m++] = l;  // every thread writes the same values
-        __syncthreads();
+        const int m = k - (p >= 0 ? 1 : 0);
         // 1. suffix sums of messages arriving from non-leaf children
         for (int a = 0; a < m; a++) {
-          const EstIn& x = sh_in[sh_L[a]];
+          const EstIn& x = in[a + (p >= 0 && a >= p ? 1 : 0)];
           if (x.kind != kInSlot) continue;
-          i128* sl = suf + int64_t(x.suf) * W1;
-          const i128* msg = slots + int64_t(x.slot) * w;
+          S* sl = suf + int64_t(x.suf) * W1;
+          const S* msg = slots + int64_t(x.slot) * w;
           const int32_t* perm = x.perm + ro;
-          for (int r = tid; r < w; r += T) sl[r] = msg[__ldg(perm + r)];
+          for (int r0 = tid; r0 < w; r0 += kIlp * T) {  // independent loads first, then the gathers
+            int jj[kIlp];
+#pragma unroll
+            for (int u = 0; u < kIlp; u++) jj[u] = r0 + u * T < w ? __ldg(perm + r0 + u * T) : 0;
+            S vv[kIlp];
+#pragma unroll
+            for (int u = 0; u < kIlp; u++) vv[u] = msg[jj[u]];
+#pragma unroll
+            for (int u = 0; u < kIlp; u++)
+              if (r0 + u * T < w) sl[r0 + u * T] = vv[u];
+          }
           if (tid == 0) sl[w] = 0;
           __syncthreads();
-          block_scan(sl, w, /*reverse=*/true, &ovf, bs);
+          block_scan(sl, w, /*reverse=*/true, bs);
         }
         // 2a. conditioned inputs: |s[c]| and their single "attains the minimum" term
         if (tid < m) {
-          const EstIn& x = sh_in[sh_L[tid]];
+          const EstIn& x = in[tid + (p >= 0 && tid >= p ? 1 : 0)];
           if (x.kind == kInCond) {
             const int32_t v = __ldg(x.s + ro + c);
             sh_ac[tid] = v < 0 ? uint32_t(-int64_t(v)) : uint32_t(v);
@@ -348,12 +391,12 @@ __global__ void __launch_bounds__(1024) k_estimate_items(const __grid_constant__
         }
         __syncthreads();
         if (tid < m) {
-          const int la = sh_L[tid];
-          const EstIn& x = sh_in[la];
+          const int la = tid + (p >= 0 && tid >= p ? 1 : 0);
+          const EstIn& x = in[la];
           if (x.kind == kInCond) {
             // its cross ranks are the precomputed ones at bucket c's sorted position
             int inv_tab = op.rank_off + m * (m - 1) + (p >= 0 ? m : 0);
-            for (int b = 0; b < tid; b++) inv_tab += sh_in[sh_L[b]].kind == kInCond;
+            for (int b = 0; b < tid; b++) inv_tab += in[b + (p >= 0 && b >= p ? 1 : 0)].kind == kInCond;
             const int rpos = rk[int64_t(inv_tab) * w + c];
             const uint32_t tau = sh_ac[tid];
             i128 v = i128(__ldg(x.s + ro + c));
@@ -361,14 +404,14 @@ __global__ void __launch_bounds__(1024) k_estimate_items(const __grid_constant__
             int tb = op.rank_off + tid * (m - 1);
             for (int b = 0; b < m; b++) {
               if (b == tid) continue;
-              const int lb = sh_L[b];
-              const EstIn& y = sh_in[lb];
+              const int lb = b + (p >= 0 && b >= p ? 1 : 0);
+              const EstIn& y = in[lb];
               const bool strict = lb < la;
               if (v != 0) {
                 if (y.kind == kInCond) {
                   if (!(strict ? sh_ac[b] > tau : sh_ac[b] >= tau)) v = 0;
                 } else {
-                  o1 |= mul_ovf(v, suf[int64_t(y.suf) * W1 + rk[int64_t(tb) * w + rpos]], &v);
+                  o1 |= mul_ovf(v, i128(suf[int64_t(y.suf) * W1 + rk[int64_t(tb) * w + rpos]]), &v);
                 }
               }
               tb++;
@@ -382,8 +425,8 @@ __global__ void __launch_bounds__(1024) k_estimate_items(const __grid_constant__
         i128 root_part = 0;
         int t2 = op.rank_off;
         for (int a = 0; a < m; a++) {
-          const int la = sh_L[a];
-          const EstIn& x = sh_in[la];
+          const int la = a + (p >= 0 && a >= p ? 1 : 0);
+          const EstIn& x = in[la];
           if (x.kind == kInCond) {
             t2 += m - 1;
             if (p < 0 && tid == 0) ovf |= add_ovf(root_part, sh_val[a], &root_part);
@@ -391,83 +434,150 @@ __global__ void __launch_bounds__(1024) k_estimate_items(const __grid_constant__
           }
           const int32_t* perm = x.perm + ro;
           const uint32_t* absa = x.abs + ro;
-          const i128* msg = x.kind == kInSlot ? slots + int64_t(x.slot) * w : nullptr;
-          i128* pl = pre + int64_t(a) * W1;
-          bool o2 = false;
-          for (int r = tid; r < w; r += T) {
-            const int j = __ldg(perm + r);
-            i128 v;
-            const i128 mv = msg ? msg[j] : i128(__ldg(x.msk + ro + j));
-            o2 |= mul_ovf(i128(__ldg(x.s + ro + j)), mv, &v);
+          const S* msg = x.kind == kInSlot ? slots + int64_t(x.slot) * w : nullptr;
+          S* pl = pre + int64_t(a) * W1;
+          bool o2 = false, so2 = false;
+          for (int r0 = tid; r0 < w; r0 += kIlp * T) {
+            int jj[kIlp];
+            bool ok[kIlp];
+#pragma unroll
+            for (int u = 0; u < kIlp; u++) {
+              ok[u] = r0 + u * T < w;
+              jj[u] = ok[u] ? __ldg(perm + r0 + u * T) : 0;
+            }
+            int64_t sv[kIlp], mv[kIlp];
+#pragma unroll
+            for (int u = 0; u < kIlp; u++) {
+              sv[u] = __ldg(x.s + ro + jj[u]);
+              mv[u] = msg ? int64_t(0) : int64_t(__ldg(x.msk + ro + jj[u]));
+            }
+            i128 v[kIlp];
+#pragma unroll
+            for (int u = 0; u < kIlp; u++) {
+              if (msg) o2 |= mul_ovf(i128(sv[u]), i128(msg[jj[u]]), &v[u]);
+              else v[u] = i128(sv[u]) * i128(mv[u]);  // |int32 * int32| < 2^62
+              if (!ok[u]) v[u] = 0;
+            }
             int tb = t2;
             for (int b = 0; b < m; b++) {
               if (b == a) continue;
-              const int lb = sh_L[b];
-              const EstIn& y = sh_in[lb];
-              if (v != 0) {
-                if (y.kind == kInCond) {
-                  const uint32_t tau = __ldg(absa + r);
-                  if (!(lb < la ? sh_ac[b] > tau : sh_ac[b] >= tau)) v = 0;
-                } else {
-                  o2 |= mul_ovf(v, suf[int64_t(y.suf) * W1 + rk[int64_t(tb) * w + r]], &v);
+              const int lb = b + (p >= 0 && b >= p ? 1 : 0);
+              const EstIn& y = in[lb];
+              if (y.kind == kInCond) {
+#pragma unroll
+                for (int u = 0; u < kIlp; u++) {
+                  const uint32_t tau = ok[u] ? __ldg(absa + r0 + u * T) : 0u;
+                  if (!(lb < la ? sh_ac[b] > tau : sh_ac[b] >= tau)) v[u] = 0;
                 }
+              } else {
+                int qq[kIlp];
+#pragma unroll
+                for (int u = 0; u < kIlp; u++) qq[u] = ok[u] ? rk[int64_t(tb) * w + r0 + u * T] : 0;
+                S gg[kIlp];
+#pragma unroll
+                for (int u = 0; u < kIlp; u++) gg[u] = suf[int64_t(y.suf) * W1 + qq[u]];
+#pragma unroll
+                for (int u = 0; u < kIlp; u++)
+                  if (v[u] != 0) o2 |= mul_ovf(v[u], i128(gg[u]), &v[u]);
               }
               tb++;
             }
-            if (p < 0) o2 |= add_ovf(root_part, v, &root_part);
-            else pl[r + 1] = v;
+#pragma unroll
+            for (int u = 0; u < kIlp; u++) {
+              if (!ok[u]) continue;
+              if (p < 0) {
+                o2 |= add_ovf(root_part, v[u], &root_part);
+              } else {
+                so2 |= !store_fits(v[u], pl);
+                pl[r0 + u * T + 1] = S(v[u]);
+              }
+            }
           }
           t2 += m - 1;
           if (o2) atomicOr(sh_flag, 1);
+          if (so2) atomicOr(sh_flag, 2);
           if (p >= 0) {
             if (tid == 0) pl[0] = 0;
             __syncthreads();
-            block_scan(pl + 1, w, /*reverse=*/false, &ovf, bs);
+            block_scan(pl + 1, w, /*reverse=*/false, bs);
           }
         }
         if (p < 0) {
-          const i128 scal = block_sum(root_part, &ovf, bs);
-          ovf |= add_ovf(acc, scal, &acc);
+          bool o4 = false;
+          const i128 scal = block_sum(root_part, &o4, bs);
+          ovf |= o4 | add_ovf(acc, scal, &acc);
           continue;
         }
         // 3. message to the parent, evaluated in the output sketch's sorted order
         {
-          const EstIn& xp = sh_in[p];
+          const EstIn& xp = in[p];
           const int32_t* permp = xp.perm + ro;
           const uint32_t* absp = xp.abs + ro;
-          i128* out = slots + int64_t(op.out_slot) * w;
+          S* out = slots + int64_t(op.out_slot) * w;
           const int t3 = op.rank_off + m * (m - 1);
-          bool o3 = false;
-          for (int r = tid; r < w; r += T) {
-            const int jp = __ldg(permp + r);
-            const uint32_t tau = __ldg(absp + r);
-            i128 t = i128(__ldg(xp.s + ro + jp));
-            i128 add = 0;
+          bool o3 = false, so3 = false;
+          for (int r0 = tid; r0 < w; r0 += kIlp * T) {
+            int jp[kIlp];
+            uint32_t tau[kIlp];
+            bool ok[kIlp];
+#pragma unroll
+            for (int u = 0; u < kIlp; u++) {
+              ok[u] = r0 + u * T < w;
+              jp[u] = ok[u] ? __ldg(permp + r0 + u * T) : 0;
+              tau[u] = ok[u] ? __ldg(absp + r0 + u * T) : 0u;
+            }
+            i128 t[kIlp], add[kIlp];
+#pragma unroll
+            for (int u = 0; u < kIlp; u++) {
+              t[u] = i128(__ldg(xp.s + ro + jp[u]));
+              add[u] = 0;
+            }
             for (int a = 0; a < m; a++) {
-              const int la = sh_L[a];
-              const EstIn& x = sh_in[la];
+              const int la = a + (a >= p ? 1 : 0);
+              const EstIn& x = in[la];
               if (x.kind == kInCond) {
-                if (t != 0 && !(la < p ? sh_ac[a] > tau : sh_ac[a] >= tau)) t = 0;
-                if (la > p ? sh_ac[a] < tau : sh_ac[a] <= tau) o3 |= add_ovf(add, sh_val[a], &add);
+#pragma unroll
+                for (int u = 0; u < kIlp; u++) {
+                  if (t[u] != 0 && !(la < p ? sh_ac[a] > tau[u] : sh_ac[a] >= tau[u])) t[u] = 0;
+                  if (la > p ? sh_ac[a] < tau[u] : sh_ac[a] <= tau[u]) o3 |= add_ovf(add[u], sh_val[a], &add[u]);
+                }
               } else {
-                const int q = rk[int64_t(t3 + a) * w + r];
-                if (t != 0) o3 |= mul_ovf(t, suf[int64_t(x.suf) * W1 + q], &t);
-                o3 |= add_ovf(add, pre[int64_t(a) * W1 + q], &add);
+                int qq[kIlp];
+#pragma unroll
+                for (int u = 0; u < kIlp; u++) qq[u] = ok[u] ? rk[int64_t(t3 + a) * w + r0 + u * T] : 0;
+                S gs[kIlp], gp[kIlp];
+#pragma unroll
+                for (int u = 0; u < kIlp; u++) {
+                  gs[u] = suf[int64_t(x.suf) * W1 + qq[u]];
+                  gp[u] = pre[int64_t(a) * W1 + qq[u]];
+                }
+#pragma unroll
+                for (int u = 0; u < kIlp; u++) {
+                  if (t[u] != 0) o3 |= mul_ovf(t[u], i128(gs[u]), &t[u]);
+                  o3 |= add_ovf(add[u], i128(gp[u]), &add[u]);
+                }
               }
             }
-            o3 |= add_ovf(t, add, &t);
-            out[jp] = t;
+#pragma unroll
+            for (int u = 0; u < kIlp; u++) {
+              if (!ok[u]) continue;
+              o3 |= add_ovf(t[u], add[u], &t[u]);
+              so3 |= !store_fits(t[u], out);
+              out[jp[u]] = S(t[u]);
+            }
           }
           if (o3) atomicOr(sh_flag, 1);
+          if (so3) atomicOr(sh_flag, 2);
           __syncthreads();
         }
       }
     }
     __syncthreads();
-    ovf |= sh_flag[0] != 0;
+    const int fl = sh_flag[0];
     if (tid == 0) {
       A.partial[it] = acc;
-      A.partial_ovf[it] = ovf ? 1 : 0;
+      // storage overflow: recompute with int128 storage; else arithmetic overflow is final
+      A.partial_ovf[it] = (fl & 2) ? 2 : ((ovf || (fl & 1)) ? 1 : 0);
     }
     __syncthreads();
   }
@@ -519,7 +629,14 @@ __global__ void k_estimate_finalize(const __grid_constant__ EstArgs A, double* _
 
 cudaError_t launch_estimate(const EstArgs& a, double* est, int64_t* row_est, cudaStream_t st) {
   if (a.n_items > 0) {
-    k_estimate_items<<<a.grid, a.threads, 0, st>>>(a);
+    // int64 storage first; items whose stored values left int64 are recomputed in int128
+    if (a.threads > 512) {
+      k_estimate_items<int64_t, 2, 1024><<<a.grid, a.threads, 0, st>>>(a, 0);
+      k_estimate_items<i128, 1, 1024><<<a.grid, a.threads, 0, st>>>(a, 1);
+    } else {
+      k_estimate_items<int64_t, 4, 512><<<a.grid, a.threads, 0, st>>>(a, 0);
+      k_estimate_items<i128, 2, 512><<<a.grid, a.threads, 0, st>>>(a, 1);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

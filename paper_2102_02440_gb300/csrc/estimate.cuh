@@ -9,6 +9,8 @@ typedef __int128 i128;
 typedef unsigned __int128 u128;
 
 enum { kInOutput = 0, kInLeaf = 1, kInSlot = 2, kInCond = 3 };
+constexpr int kEstMaxOps = 64;     // operations of one sub-plan (one per non-leaf table)
+constexpr int kEstMaxSubIn = 136;  // edge inputs of one sub-plan
 
 // One edge of a table operation, in the table's ascending edge-id order.
 struct EstIn {
