@@ -33,6 +33,7 @@ METRIC = "sketched tuples/s"
 UNIT = "tuples/s"
 INT_ISSUE_PEAK = 152 * 4 * 32 * 2.070e9   # 32-bit integer instructions/s: one warp instruction per SMSP per clock
 CW_INSTR = 60                            # 32-bit instructions per CW-61 bucket + sign evaluation
+OP128_INSTR = 8                          # 32-bit instructions per exact 128-bit multiply or add
 
 
 def _args():
@@ -46,7 +47,75 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phases", action="store_true", help="print a per-phase breakdown on stderr")
+    ap.add_argument("--case", default=None, choices=["estimate_small", "build_f1"],
+                    help="run one small profiling case instead of the benchmark (for ncu captures)")
     return ap.parse_args()
+
+
+def estimate_ops(n_tables, eu, ev, masks, d, w) -> int:
+    """Exact 128-bit integer operations (multiplies and adds) of the sketch-merging
+    contraction as the estimate kernel evaluates it: spanning tree from the lowest table,
+    one operation per non-leaf table, every conditioning value of a cyclic sub-plan."""
+    total = 0
+    for m in masks:
+        tabs = [t for t in range(n_tables) if (m >> t) & 1]
+        if len(tabs) < 2:
+            continue
+        es = [e for e in range(len(eu)) if (m >> eu[e]) & 1 and (m >> ev[e]) & 1]
+        root = tabs[0]
+        order, seen, parent, tree = [root], {root}, {root: -1}, set()
+        h = 0
+        while h < len(order):
+            t = order[h]
+            h += 1
+            for e in es:
+                o = ev[e] if eu[e] == t else (eu[e] if ev[e] == t else None)
+                if o is None or o in seen:
+                    continue
+                seen.add(o)
+                parent[o] = e
+                tree.add(e)
+                order.append(o)
+        cond = [e for e in es if e not in tree]
+        deg = {t: sum(1 for e in es if t in (eu[e], ev[e])) for t in tabs}
+        per_c = per_row = 0
+        for t in order:
+            if t != root and deg[t] == 1:
+                continue
+            kinds = []
+            for e in es:
+                if t not in (eu[e], ev[e]):
+                    continue
+                if e == parent[t]:
+                    kinds.append("out")
+                elif e in tree:
+                    child = ev[e] if eu[e] == t else eu[e]
+                    kinds.append("leaf" if (child != root and deg[child] == 1) else "slot")
+                else:
+                    kinds.append("cond")
+            nc = [k for k in kinds if k in ("leaf", "slot")]
+            per_row += w * kinds.count("leaf")                  # leaf suffix sums, once per item
+            per_c += w * kinds.count("slot")                    # message suffix sums
+            per_c += len(nc) * w * (len(nc) + 1)                # s*m, threshold products, prefix add
+            if "out" in kinds:
+                per_c += w * (2 * len(nc) + 1)                  # output: products, prefix adds, final add
+        total += d * (per_row + (w if cond else 1) * per_c)
+    return total
+
+
+def _kernel_traffic(name: str):
+    """DRAM bytes per launch of `name` from the committed ncu capture, or None if the
+    kernel's source changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "counters.json")) as f:
+            c = json.load(f)[name]
+        src = os.path.join(ROOT, "paper_2102_02440_gb300", "csrc", c["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != c["source_sha256"]:
+            return None
+        return c["dram_bytes_per_launch"]
+    except Exception:
+        return None
 
 
 def _peaks():
@@ -133,9 +202,17 @@ def _max_over_ranks(v: float, world: int) -> float:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, ms_local: float, world: int):
+    """Weak-scaling aggregate: every rank processes units_per_rank units; the job takes
+    as long as its slowest rank.  Returns (units per second of the whole job, max ms)."""
+    ms_max = _max_over_ranks(ms_local, world)
+    return units_per_rank * world / (ms_max / 1e3), ms_max
 
 
 def workload(scale: float, w: int, rank: int):
@@ -269,27 +346,35 @@ def run_ours(a):
     per = [[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs]
     step_ms = [sum(p) for p in per]
     ms = statistics.mean(step_ms)
-    ms_max = _max_over_ranks(ms, world)
     rows = wl.total_rows
-    value = rows * world / (ms_max / 1e3)
+    value, ms_max = whole_job_rate(rows, ms, world)
     phase = {n: statistics.mean(p[i] for p in per)
              for i, n in enumerate(("build", "presort", "estimate", "combiner"))}
     n_est = len(masks)
 
-    # roofline of the dominant kernel (the fused build): integer-issue bound
+    # roofline of the dominant kernel (the estimate, ~90% of the step): integer ALU bound
     surv = dw.survivors.cpu().numpy()
+    est_ops = estimate_ops(len(wl.tables), wl.edge_u, wl.edge_v, masks, wl.d, wl.w)
+    est_s = phase["estimate"] / 1e3
+    op_peak = INT_ISSUE_PEAK / OP128_INSTR
+    roof = {"bound": "alu", "achieved": est_ops / est_s / 1e12, "peak": op_peak / 1e12, "unit": "T int128-op/s",
+            "frac": est_ops / est_s / op_peak, "traffic": _kernel_traffic("k_estimate_items"),
+            "kernel": "k_estimate_items (int64 tier + int128 recompute) and k_estimate_finalize",
+            "algorithmic": f"{est_ops} exact 128-bit multiplies/adds of the spanning-tree contraction",
+            "peak_derivation": f"152 SMs x 4 SMSP x 32 lanes x 2.07 GHz / {OP128_INSTR} int32 instr per op"}
+    # the fused build, second kernel: integer ALU bound, with its HBM fraction
     updates = int(sum(int(surv[i]) * len(t.key_col) * wl.d for i, t in enumerate(wl.tables)))
     hbm_peak, peak_kind = _peaks()
     col_bytes = wl.column_bytes()
     build_s = phase["build"] / 1e3
     ach = updates * CW_INSTR / build_s
-    roof = {"bound": "alu", "achieved": ach / 1e12, "peak": INT_ISSUE_PEAK / 1e12, "unit": "Tinstr/s",
-            "frac": ach / INT_ISSUE_PEAK, "traffic": None,
-            "kernel": "k_sketch_build (batched, zero kernel included)",
-            "algorithmic": f"{updates} CW evaluations x {CW_INSTR} int32 instr",
-            "hbm": {"achieved_gbs": col_bytes / build_s / 1e9, "peak_gbs": hbm_peak,
-                    "frac": col_bytes / build_s / 1e9 / hbm_peak, "peak_kind": peak_kind,
-                    "algorithmic_bytes": col_bytes}}
+    roof_build = {"bound": "alu", "achieved": ach / 1e12, "peak": INT_ISSUE_PEAK / 1e12, "unit": "Tinstr/s",
+                  "frac": ach / INT_ISSUE_PEAK, "traffic": _kernel_traffic("k_sketch_build"),
+                  "kernel": "k_sketch_build (batched) + k_zero_spans",
+                  "algorithmic": f"{updates} CW evaluations x {CW_INSTR} int32 instr",
+                  "hbm": {"achieved_gbs": col_bytes / build_s / 1e9, "peak_gbs": hbm_peak,
+                          "frac": col_bytes / build_s / 1e9 / hbm_peak, "peak_kind": peak_kind,
+                          "algorithmic_bytes": col_bytes}}
 
     # end to end through the public API: pinned host columns -> device, path, estimates -> host
     e2e = None
@@ -332,7 +417,7 @@ def run_ours(a):
                 "phases_ms": phase, "subplan_estimates_per_s": n_est / (phase["estimate"] / 1e3),
                 "build_only_tuples_per_s": rows / (phase["build"] / 1e3),
                 "survivors": [int(x) for x in surv],
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "roofline": roof, "roofline_build": roof_build, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_step * a.steps}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -340,9 +425,42 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_case(a):
+    """Small profiling cases (one GPU): the estimate of all 19 sub-plans of the five-table
+    graph at w = 4096 (tables at 5% scale; the estimate's cost depends on w and the sketch
+    values), or the fused build of the 36M-row F1 table alone (3 sketches, d = 11,
+    w = 4096)."""
+    import torch
+
+    from paper_2102_02440_gb300 import datagen as G
+    from paper_2102_02440_gb300 import pipeline as P
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if a.case == "estimate_small":
+        wl = G.five_table(scale=0.05, w=4096)
+        dw = P.DeviceWorkload(wl)
+        dw.build_batched()
+        est = P.DeviceEstimator(dw, G.connected_subplans(5, wl.edge_u, wl.edge_v))
+        est.presort()
+        fn = est.estimate
+    else:
+        full = G.five_table(scale=1.0, w=4096)
+        wl = G.Workload("F1 only", [full.tables[0]], [0] * 5, [0] * 5, 11, 4096, full.hash_seed, 0)
+        dw = P.DeviceWorkload(wl)
+        fn = dw.build
+    for r in range(2):
+        s.record()
+        fn()
+        e.record()
+        torch.cuda.synchronize()
+        print(f"{a.case} rep {r}: {s.elapsed_time(e):.3f} ms", flush=True)
+    dw.check_status()
+
+
 def main():
     a = _args()
-    if a.impl == "reference":
+    if a.case:
+        run_case(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)
