@@ -404,7 +404,9 @@ def run_ours(a):
     if rank == 0 and not a.no_cpu_baseline:
         cpu = cpu_baseline(wl)
 
-    launches_per_step = 2 + sum(1 for t in dw.tables if t.k) + 2 + 2 * len(two) + 3
+    # zero + build, presort + cross ranks per table, estimate (int64, int128 recompute, finalize),
+    # two self-join sizes per two-table sub-plan, features, infer, combine
+    launches_per_step = 2 + 2 * sum(1 for t in dw.tables if t.k) + 3 + 2 * len(two) + 3
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",

@@ -36,7 +36,7 @@ typedef int32_t cmp_status;
 #define CMP_EWORKSPACE (-5)   /* workspace or plan buffer smaller than required       */
 #define CMP_ETIMEOUT (-6)     /* a bounded device-side wait ran out                   */
 
-#define CMP_MAX_COLS 16       /* columns per table descriptor     */
+#define CMP_MAX_COLS 32       /* columns per table descriptor     */
 #define CMP_MAX_PREDS 8       /* conjuncts per table              */
 #define CMP_MAX_SKETCHES 16   /* sketches (join edges) per table  */
 #define CMP_MAX_D 64          /* sketch rows                      */
@@ -168,10 +168,24 @@ size_t cmp_presort_ws_bytes(int64_t n_rows, int32_t w);
 cmp_status cmp_presort(const int32_t* counters_dev, int64_t n_rows, int32_t w, uint32_t* abs_sorted_dev,
                        int32_t* perm_dev, void* ws_dev, size_t ws_bytes, void* stream);
 
+/* Cross ranks between the sorted rows of one table's sketches (prepares the merged
+ * contraction, like cmp_presort; independent of any sub-plan, so every sub-plan that
+ * contains the table reuses them -- the paper caches merged sketches and products for
+ * the same reason, Sec. 5).  For a table with k sketches on edges edge_id_host[0..k),
+ * with abs_sorted_dev / perm_dev its [k][d][w] presort outputs, writes ranks_dev
+ * [k][k][d][w] int32:  for x != y, ranks[x][y][i][r] = the number of buckets j of row i
+ * of sketch y whose |C_y[i][j]| is < abs_x[i][r], or <= it when edge_id[y] < edge_id[x];
+ * on the diagonal, ranks[x][x][i][j] = the sorted position of bucket j (the inverse of
+ * perm).  d counts rows only (k * k * d < 2^31): with k = 1, the rows of many one-sketch
+ * tables stored back to back can be processed in one call. */
+cmp_status cmp_cross_ranks(const uint32_t* abs_sorted_dev, const int32_t* perm_dev, int32_t k, int32_t d, int32_t w,
+                           const int32_t* edge_id_host, int32_t* ranks_dev, void* stream);
+
 /* A join graph whose sketches have been built and presorted.  Edge e joins tables
  * edge_u[e] and edge_v[e]; endpoint 0 is the edge_u side, 1 the edge_v side.  All
  * arrays are HOST arrays; entries of sketch/abs_sorted/perm are DEVICE pointers to the
- * endpoint's [d][w] sketch (int32), sorted magnitudes (uint32) and permutation (int32). */
+ * endpoint's [d][w] sketch (int32), sorted magnitudes (uint32) and permutation (int32),
+ * and ranks points into its table's cross-rank array. */
 typedef struct {
   int32_t n_tables;                  /* 1 .. CMP_MAX_TABLES */
   int32_t n_edges;
@@ -180,6 +194,9 @@ typedef struct {
   const int32_t* const* sketch;      /* [2 * n_edges] */
   const uint32_t* const* abs_sorted; /* [2 * n_edges] */
   const int32_t* const* perm;        /* [2 * n_edges] */
+  const int32_t* const* ranks;       /* [2 * n_edges]: the endpoint table's cmp_cross_ranks block of this sketch,
+                                        ranks_dev + x * d * w for the endpoint's sketch index x */
+  const int32_t* slot;               /* [2 * n_edges]: the endpoint's sketch index x within its table (host) */
   const int64_t* survivors_dev;      /* device [n_tables]: exact selected counts */
 } cmp_graph;
 

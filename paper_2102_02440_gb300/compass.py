@@ -15,7 +15,7 @@ from . import build_lib
 CMP_OK, CMP_EINVAL, CMP_EUNSUPPORTED, CMP_EOVERFLOW, CMP_ECUDA, CMP_EWORKSPACE, CMP_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 CMP_I32, CMP_I64 = 0, 1
 CMP_RANGE, CMP_EQ, CMP_IN_BITMAP = 0, 1, 2
-CMP_MAX_COLS, CMP_MAX_PREDS, CMP_MAX_SKETCHES, CMP_MAX_D = 16, 8, 16, 64
+CMP_MAX_COLS, CMP_MAX_PREDS, CMP_MAX_SKETCHES, CMP_MAX_D = 32, 8, 16, 64
 
 
 class CompassError(RuntimeError):
@@ -65,7 +65,7 @@ class cmp_graph(C.Structure):
     _fields_ = [("n_tables", C.c_int32), ("n_edges", C.c_int32), ("edge_u", C.POINTER(C.c_int32)),
                 ("edge_v", C.POINTER(C.c_int32)), ("sketch", C.POINTER(C.c_void_p)),
                 ("abs_sorted", C.POINTER(C.c_void_p)), ("perm", C.POINTER(C.c_void_p)),
-                ("survivors_dev", C.c_void_p)]
+                ("ranks", C.POINTER(C.c_void_p)), ("slot", C.POINTER(C.c_int32)), ("survivors_dev", C.c_void_p)]
 
 
 _lib = None
@@ -85,6 +85,8 @@ _SIGS = {
     "cmp_presort_ws_bytes": (C.c_size_t, [C.c_int64, C.c_int32]),
     "cmp_presort": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                                 C.c_void_p]),
+    "cmp_cross_ranks": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                    C.POINTER(C.c_int32), C.c_void_p, C.c_void_p]),
     "cmp_estimate_plan_bytes": (C.c_int32, [C.POINTER(cmp_graph), C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                             C.c_void_p, C.c_void_p, C.POINTER(cmp_estimate_cfg),
                                             C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
@@ -205,6 +207,11 @@ def cmp_presort(counters_dev: int, n_rows: int, w: int, abs_sorted_dev: int, per
                 ws_bytes: int, stream: int):
     _check("cmp_presort", lib().cmp_presort(counters_dev, n_rows, w, abs_sorted_dev, perm_dev, ws_dev, ws_bytes,
                                             stream))
+
+
+def cmp_cross_ranks(abs_dev: int, perm_dev: int, k: int, d: int, w: int, edge_ids, ranks_dev: int, stream: int):
+    e = (C.c_int32 * max(k, 1))(*edge_ids)
+    _check("cmp_cross_ranks", lib().cmp_cross_ranks(abs_dev, perm_dev, k, d, w, e, ranks_dev, stream))
 
 
 def cmp_estimate_plan_bytes(graphs, d: int, w: int, sub_graph, sub_mask, cfg: cmp_estimate_cfg | None = None):

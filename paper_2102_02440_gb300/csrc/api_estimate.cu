@@ -33,13 +33,16 @@ struct PlanOut {
 
 bool graph_ok(const cmp_graph& g) {
   if (g.n_tables < 1 || g.n_tables > CMP_MAX_TABLES || g.n_edges < 0) return false;
-  if (g.n_edges && (!g.edge_u || !g.edge_v || !g.sketch || !g.abs_sorted || !g.perm)) return false;
+  if (g.n_edges && (!g.edge_u || !g.edge_v || !g.sketch || !g.abs_sorted || !g.perm || !g.ranks || !g.slot))
+    return false;
   if (!g.survivors_dev) return false;
   for (int e = 0; e < g.n_edges; e++) {
     if (g.edge_u[e] < 0 || g.edge_u[e] >= g.n_tables || g.edge_v[e] < 0 || g.edge_v[e] >= g.n_tables) return false;
     if (g.edge_u[e] == g.edge_v[e]) return false;
     for (int end = 0; end < 2; end++)
-      if (!g.sketch[2 * e + end] || !g.abs_sorted[2 * e + end] || !g.perm[2 * e + end]) return false;
+      if (!g.sketch[2 * e + end] || !g.abs_sorted[2 * e + end] || !g.perm[2 * e + end] || !g.ranks[2 * e + end] ||
+          g.slot[2 * e + end] < 0 || g.slot[2 * e + end] >= CMP_MAX_SKETCHES)
+        return false;
   }
   return true;
 }
@@ -90,7 +93,7 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
   auto end_of = [&](int e, int t) { return g.edge_u[e] == t ? 0 : 1; };
   std::vector<int> slot_of(nt, -1);
   std::vector<char> slot_busy;
-  int32_t n_suf = 0, n_rank = 0;
+  int32_t n_suf = 0;
   for (size_t h = order.size(); h-- > 0;) {
     const int t = order[h];
     if (is_leaf(t)) continue;
@@ -109,6 +112,8 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
       x.s = g.sketch[2 * e + me];
       x.abs = g.abs_sorted[2 * e + me];
       x.perm = g.perm[2 * e + me];
+      x.rk = g.ranks[2 * e + me];
+      x.tslot = g.slot[2 * e + me];
       x.suf = -1;
       if (e == parent_edge[t]) {
         x.kind = kInOutput;
@@ -146,17 +151,12 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
       slot_of[t] = s;
     }
     for (int s : consumed) slot_busy[s] = 0;
-    const int32_t m = op.k - (op.p >= 0 ? 1 : 0);
-    int32_t n_cond_in = 0;
-    for (int32_t l = 0; l < op.k; l++) n_cond_in += P->ins[op.in_begin + l].kind == kInCond;
-    op.rank_off = n_rank;
-    n_rank += m * (m - 1) + (op.p >= 0 ? m : 0) + n_cond_in;
+    op.rank_off = 0;
     P->max_slots = std::max<int32_t>(P->max_slots, int32_t(slot_busy.size()));
     P->max_in = std::max<int32_t>(P->max_in, op.k);
     P->ops.push_back(op);
   }
   P->max_suf = std::max(P->max_suf, n_suf);
-  P->max_rank = std::max(P->max_rank, n_rank);
   sb.cond = cond.empty() ? 0 : 1;
   sb.n_ops = int32_t(P->ops.size()) - sb.op_begin;
   if (sb.n_ops > kEstMaxOps || int32_t(P->ins.size()) - P->ops[sb.op_begin].in_begin > kEstMaxSubIn)
@@ -232,6 +232,18 @@ size_t cmp_presort_ws_bytes(int64_t n_rows, int32_t w) {
   (void)n_rows;
   (void)w;
   return 0;
+}
+
+cmp_status cmp_cross_ranks(const uint32_t* abs_sorted_dev, const int32_t* perm_dev, int32_t k, int32_t d, int32_t w,
+                           const int32_t* edge_id_host, int32_t* ranks_dev, void* stream) {
+  // d only counts rows here (several tables' rows may be passed as one block when k = 1)
+  if (k < 0 || k > CMP_MAX_SKETCHES || d < 1 || w < 1 || w > CMP_MAX_W) return CMP_EINVAL;
+  if (int64_t(k) * k * d >= (int64_t(1) << 31)) return CMP_EINVAL;
+  if (k > 0 && (!abs_sorted_dev || !perm_dev || !edge_id_host || !ranks_dev)) return CMP_EINVAL;
+  return launch_cross_ranks(abs_sorted_dev, perm_dev, k, d, w, edge_id_host, ranks_dev,
+                            reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? CMP_OK
+             : CMP_ECUDA;
 }
 
 cmp_status cmp_presort(const int32_t* counters_dev, int64_t n_rows, int32_t w, uint32_t* abs_sorted_dev,

@@ -126,6 +126,58 @@ cudaError_t launch_presort(const int32_t* C, int64_t n_rows, int32_t w, uint32_t
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- cross ranks
+struct CrossArgs {
+  const uint32_t* abs;
+  const int32_t* perm;
+  int32_t* ranks;
+  int32_t k, d, w;
+  int32_t edge[CMP_MAX_SKETCHES];
+};
+
+__device__ __forceinline__ int rank_in(const uint32_t* __restrict__ a, int w, uint32_t tau, bool strict) {
+  int lo = 0, hi = w;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const uint32_t v = __ldg(a + mid);
+    if (strict ? v <= tau : v < tau) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// One CTA per (x, y, row): ranks of x's sorted magnitudes in y's, or x's inverse permutation.
+__global__ void k_cross_ranks(const __grid_constant__ CrossArgs A) {
+  const int k = A.k, d = A.d, w = A.w;
+  const int64_t blk = blockIdx.x;
+  const int row = int(blk % d), y = int((blk / d) % k), x = int(blk / (int64_t(d) * k));
+  int32_t* out = A.ranks + ((int64_t(x) * k + y) * d + row) * w;
+  if (x == y) {
+    const int32_t* perm = A.perm + (int64_t(x) * d + row) * w;
+    for (int r = threadIdx.x; r < w; r += blockDim.x) out[__ldg(perm + r)] = r;
+    return;
+  }
+  const uint32_t* ax = A.abs + (int64_t(x) * d + row) * w;
+  const uint32_t* ay = A.abs + (int64_t(y) * d + row) * w;
+  const bool strict = A.edge[y] < A.edge[x];
+  for (int r = threadIdx.x; r < w; r += blockDim.x) out[r] = rank_in(ay, w, __ldg(ax + r), strict);
+}
+
+cudaError_t launch_cross_ranks(const uint32_t* abs, const int32_t* perm, int32_t k, int32_t d, int32_t w,
+                               const int32_t* edge_id, int32_t* ranks, cudaStream_t st) {
+  if (k <= 0) return cudaSuccess;
+  CrossArgs a;
+  a.abs = abs;
+  a.perm = perm;
+  a.ranks = ranks;
+  a.k = k;
+  a.d = d;
+  a.w = w;
+  for (int i = 0; i < CMP_MAX_SKETCHES; i++) a.edge[i] = i < k ? edge_id[i] : 0;
+  k_cross_ranks<<<unsigned(int64_t(k) * k * d), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- estimate helpers
 namespace {
 
@@ -139,6 +191,11 @@ __device__ __forceinline__ int rank_of(const uint32_t* __restrict__ a, int w, ui
     else hi = mid;
   }
   return lo;
+}
+
+// Row `row` of the cross ranks of sketch x against sketch y of the same table.
+__device__ __forceinline__ const int32_t* rank_row(const EstIn& x, const EstIn& y, int d, int row, int w) {
+  return x.rk + (int64_t(y.tslot) * d + row) * w;
 }
 
 struct BlockScratch {
@@ -244,8 +301,8 @@ __device__ void block_scan(S* a, int n, bool reverse, BlockScratch& bs) {
 //   suf   [max_suf][w+1]  suffix sums of each incoming message in its sketch's sorted
 //                         order (leaf inputs: computed once per item)
 //   pre   [max_in][w+1]   prefix sums of the "this edge attains the minimum" terms
-//   rank  [max_rank][w]   cross ranks between the sorted sketch rows of each table,
-//                         computed once per item (they do not depend on messages)
+// Cross ranks between the sorted rows of a table's sketches come from the cache written
+// by cmp_cross_ranks (they depend on no message and no sub-plan).
 // A conditioned input (unit vector at c) needs no array: its threshold sum is a
 // comparison with |s[c]| and its own term is one value.  When some conditioned sketch
 // value s[c] is 0, every merged tensor entry at c through that table is 0 and c adds
@@ -272,7 +329,6 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
   S* slots = reinterpret_cast<S*>(cta);
   S* suf = slots + int64_t(A.max_slots) * w;
   S* pre = suf + int64_t(A.max_suf) * W1;
-  int32_t* rk = reinterpret_cast<int32_t*>(pre + int64_t(A.max_in) * W1);
   const int tid = threadIdx.x, T = blockDim.x;
 
   for (int64_t it = blockIdx.x; it < A.n_items; it += gridDim.x) {
@@ -304,36 +360,6 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
       const EstIn* in = sh_in + op.in_begin;
       const int p = op.p;
       const int m = op.k - (p >= 0 ? 1 : 0);
-      int t = op.rank_off;
-      for (int a = 0; a < m; a++) {
-        const int la = a + (p >= 0 && a >= p ? 1 : 0);
-        const uint32_t* absa = in[la].abs + ro;
-        for (int b = 0; b < m; b++) {
-          if (b == a) continue;
-          const int lb = b + (p >= 0 && b >= p ? 1 : 0);
-          const uint32_t* absb = in[lb].abs + ro;
-          int32_t* tab = rk + int64_t(t++) * w;
-          const bool strict = lb < la;
-          for (int r = tid; r < w; r += T) tab[r] = rank_of(absb, w, __ldg(absa + r), strict);
-        }
-      }
-      if (p >= 0) {
-        const uint32_t* absp = in[p].abs + ro;
-        for (int a = 0; a < m; a++) {
-          const int la = a + (a >= p ? 1 : 0);
-          int32_t* tab = rk + int64_t(t++) * w;
-          const uint32_t* absa = in[la].abs + ro;
-          const bool strict = la < p;
-          for (int r = tid; r < w; r += T) tab[r] = rank_of(absa, w, __ldg(absp + r), strict);
-        }
-      }
-      for (int a = 0; a < m; a++) {  // inverse permutation of conditioned inputs
-        const int la = a + (p >= 0 && a >= p ? 1 : 0);
-        if (in[la].kind != kInCond) continue;
-        int32_t* inv = rk + int64_t(t++) * w;
-        const int32_t* perm = in[la].perm + ro;
-        for (int r = tid; r < w; r += T) inv[__ldg(perm + r)] = r;
-      }
       for (int a = 0; a < m; a++) {
         const int la = a + (p >= 0 && a >= p ? 1 : 0);
         const EstIn& x = in[la];
@@ -394,14 +420,11 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
           const int la = tid + (p >= 0 && tid >= p ? 1 : 0);
           const EstIn& x = in[la];
           if (x.kind == kInCond) {
-            // its cross ranks are the precomputed ones at bucket c's sorted position
-            int inv_tab = op.rank_off + m * (m - 1) + (p >= 0 ? m : 0);
-            for (int b = 0; b < tid; b++) inv_tab += in[b + (p >= 0 && b >= p ? 1 : 0)].kind == kInCond;
-            const int rpos = rk[int64_t(inv_tab) * w + c];
+            // its cross ranks are the cached ones at bucket c's sorted position
+            const int rpos = __ldg(rank_row(x, x, A.d, item.row, w) + c);
             const uint32_t tau = sh_ac[tid];
             i128 v = i128(__ldg(x.s + ro + c));
             bool o1 = false;
-            int tb = op.rank_off + tid * (m - 1);
             for (int b = 0; b < m; b++) {
               if (b == tid) continue;
               const int lb = b + (p >= 0 && b >= p ? 1 : 0);
@@ -411,10 +434,10 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
                 if (y.kind == kInCond) {
                   if (!(strict ? sh_ac[b] > tau : sh_ac[b] >= tau)) v = 0;
                 } else {
-                  o1 |= mul_ovf(v, i128(suf[int64_t(y.suf) * W1 + rk[int64_t(tb) * w + rpos]]), &v);
+                  const int q = __ldg(rank_row(x, y, A.d, item.row, w) + rpos);
+                  o1 |= mul_ovf(v, i128(suf[int64_t(y.suf) * W1 + q]), &v);
                 }
               }
-              tb++;
             }
             sh_val[tid] = v;
             if (o1) atomicOr(sh_flag, 1);
@@ -423,12 +446,10 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
         __syncthreads();
         // 2b. other inputs: s_l m_l prod_{l' != l, p} G_l'(|s_l|) in l's sorted order
         i128 root_part = 0;
-        int t2 = op.rank_off;
         for (int a = 0; a < m; a++) {
           const int la = a + (p >= 0 && a >= p ? 1 : 0);
           const EstIn& x = in[la];
           if (x.kind == kInCond) {
-            t2 += m - 1;
             if (p < 0 && tid == 0) ovf |= add_ovf(root_part, sh_val[a], &root_part);
             continue;
           }
@@ -458,7 +479,6 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
               else v[u] = i128(sv[u]) * i128(mv[u]);  // |int32 * int32| < 2^62
               if (!ok[u]) v[u] = 0;
             }
-            int tb = t2;
             for (int b = 0; b < m; b++) {
               if (b == a) continue;
               const int lb = b + (p >= 0 && b >= p ? 1 : 0);
@@ -470,9 +490,10 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
                   if (!(lb < la ? sh_ac[b] > tau : sh_ac[b] >= tau)) v[u] = 0;
                 }
               } else {
+                const int32_t* rrow = rank_row(x, y, A.d, item.row, w);
                 int qq[kIlp];
 #pragma unroll
-                for (int u = 0; u < kIlp; u++) qq[u] = ok[u] ? rk[int64_t(tb) * w + r0 + u * T] : 0;
+                for (int u = 0; u < kIlp; u++) qq[u] = ok[u] ? __ldg(rrow + r0 + u * T) : 0;
                 S gg[kIlp];
 #pragma unroll
                 for (int u = 0; u < kIlp; u++) gg[u] = suf[int64_t(y.suf) * W1 + qq[u]];
@@ -480,7 +501,6 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
                 for (int u = 0; u < kIlp; u++)
                   if (v[u] != 0) o2 |= mul_ovf(v[u], i128(gg[u]), &v[u]);
               }
-              tb++;
             }
 #pragma unroll
             for (int u = 0; u < kIlp; u++) {
@@ -493,7 +513,6 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
               }
             }
           }
-          t2 += m - 1;
           if (o2) atomicOr(sh_flag, 1);
           if (so2) atomicOr(sh_flag, 2);
           if (p >= 0) {
@@ -514,7 +533,6 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
           const int32_t* permp = xp.perm + ro;
           const uint32_t* absp = xp.abs + ro;
           S* out = slots + int64_t(op.out_slot) * w;
-          const int t3 = op.rank_off + m * (m - 1);
           bool o3 = false, so3 = false;
           for (int r0 = tid; r0 < w; r0 += kIlp * T) {
             int jp[kIlp];
@@ -542,9 +560,10 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
                   if (la > p ? sh_ac[a] < tau[u] : sh_ac[a] <= tau[u]) o3 |= add_ovf(add[u], sh_val[a], &add[u]);
                 }
               } else {
+                const int32_t* rrow = rank_row(xp, x, A.d, item.row, w);
                 int qq[kIlp];
 #pragma unroll
-                for (int u = 0; u < kIlp; u++) qq[u] = ok[u] ? rk[int64_t(t3 + a) * w + r0 + u * T] : 0;
+                for (int u = 0; u < kIlp; u++) qq[u] = ok[u] ? __ldg(rrow + r0 + u * T) : 0;
                 S gs[kIlp], gp[kIlp];
 #pragma unroll
                 for (int u = 0; u < kIlp; u++) {

@@ -18,10 +18,11 @@ struct EstIn {
   const uint32_t* abs;   // its presorted magnitudes, [d][w]
   const int32_t* perm;   // its presort permutation, [d][w]
   const int32_t* msk;    // kInLeaf: the leaf neighbour's sketch on the edge, [d][w]
+  const int32_t* rk;     // this table's cross ranks from this sketch: [k][d][w], indexed by the other sketch
   int32_t kind;          // kInOutput / kInLeaf / kInSlot / kInCond
   int32_t slot;          // kInSlot: message slot written by the child's operation
   int32_t suf;           // kInLeaf / kInSlot: suffix-sum array of the sub-plan (item-persistent)
-  int32_t pad;
+  int32_t tslot;         // this sketch's index within its table (selects rows of another input's rk)
 };
 
 // One non-leaf table of a sub-plan's spanning tree (post-order).
@@ -120,5 +121,7 @@ __device__ inline double i128_to_double(i128 v) {
 cudaError_t launch_presort(const int32_t* C, int64_t n_rows, int32_t w, uint32_t* abs_out, int32_t* perm_out,
                            cudaStream_t st);
 cudaError_t launch_estimate(const EstArgs& a, double* est, int64_t* row_est, cudaStream_t st);
+cudaError_t launch_cross_ranks(const uint32_t* abs, const int32_t* perm, int32_t k, int32_t d, int32_t w,
+                               const int32_t* edge_id, int32_t* ranks, cudaStream_t st);
 
 }  // namespace cmpk

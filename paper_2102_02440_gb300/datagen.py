@@ -367,3 +367,47 @@ def join_pairs_device(n_pairs: int, rows_lo: int, rows_hi: int, dom_lo: int = 1_
     D_el = torch.from_numpy(dom_t).to(device)[table_of]
     keys = ((A_el * r + B_el) % D_el).to(torch.int32)
     return keys, offsets, {"rows": rows, "domain": dom_t, "s": sk}
+
+
+def graph_batch(n_graphs: int = 64, n_lo: int = 4, n_hi: int = 17, rows_lo: int = 10_000, rows_hi: int = 100_000_000,
+                domain: int = 100_000, d: int = 11, w: int = 1024, pred_prob: float = 0.5, seed: int = 20210206,
+                kinds=("chain", "star", "cycle"), hash_seed: int = 0xC0FFEE + 2) -> list:
+    """Synthetic join graphs for batched enumeration: type uniform over `kinds`, n tables
+    uniform in [n_lo, n_hi], rows log-uniform in [rows_lo, rows_hi].  Every (table, edge)
+    has its own key column, Zipf(s) over [0, domain) with s uniform in [0.5, 1.5]; with
+    probability pred_prob a table gets a predicate: EQ on a Zipf(1.0) code over 1000 codes,
+    or a RANGE on a uniform [0, 1000) column with selectivity uniform in [1%, 50%].
+    Returns one Workload per graph (edges: chain i-(i+1); star 0-i; cycle = chain + (n-1)-0)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for gi in range(n_graphs):
+        kind = kinds[int(rng.integers(0, len(kinds)))]
+        n = int(rng.integers(n_lo, n_hi + 1))
+        if kind == "chain":
+            edges = [(i, i + 1) for i in range(n - 1)]
+        elif kind == "star":
+            edges = [(0, i) for i in range(1, n)]
+        else:
+            edges = [(i, i + 1) for i in range(n - 1)] + [(0, n - 1)]
+        tabs = []
+        for t in range(n):
+            rows = int(np.exp(rng.uniform(np.log(rows_lo), np.log(rows_hi))))
+            cols, kc, ei = [], [], []
+            for e, (u, v) in enumerate(edges):
+                if t in (u, v):
+                    cols.append(zipf_keys(rng, rows, domain, float(rng.uniform(0.5, 1.5))))
+                    kc.append(len(cols) - 1)
+                    ei.append(e)
+            preds = []
+            if rng.random() < pred_prob:
+                if rng.random() < 0.5:
+                    codes = zipf_keys(rng, rows, 1000, 1.0)
+                    cols.append(codes)
+                    preds.append(Pred(len(cols) - 1, EQ, int(codes[int(rng.integers(0, rows))])))
+                else:
+                    cols.append(uniform_col(rng, rows, 0, 1000))
+                    preds.append(Pred(len(cols) - 1, RANGE, 0, int(1000 * rng.uniform(0.01, 0.5))))
+            tabs.append(Table(f"G{gi}T{t}", cols, preds, kc, ei))
+        out.append(Workload(f"{kind}{n}", tabs, [u for u, _ in edges], [v for _, v in edges], d, w,
+                            hash_seed + gi, seed))
+    return out

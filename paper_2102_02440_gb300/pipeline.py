@@ -91,6 +91,45 @@ class DeviceWorkload:
         return self.tables[t].counters[s]
 
 
+def _prep_tables(dw):
+    """Presort and cross-rank buffers for every table of a DeviceWorkload (once)."""
+    if getattr(dw, "ranks", None) is None:
+        dev = dw.device
+        dw.abs_sorted = [torch.empty(t.counters.shape, dtype=torch.int32, device=dev) for t in dw.tables]
+        dw.perm = [torch.empty(t.counters.shape, dtype=torch.int32, device=dev) for t in dw.tables]
+        dw.ranks = [torch.empty((t.counters.shape[0],) + tuple(t.counters.shape), dtype=torch.int32, device=dev)
+                    for t in dw.tables]
+
+
+def _presort_tables(dw, s):
+    """cmp_presort then cmp_cross_ranks for every table with sketches."""
+    for t, a, p, r in zip(dw.tables, dw.abs_sorted, dw.perm, dw.ranks):
+        if t.k:
+            K.cmp_presort(t.counters.data_ptr(), t.k * dw.d, dw.w, a.data_ptr(), p.data_ptr(), 0, 0, s)
+            K.cmp_cross_ranks(a.data_ptr(), p.data_ptr(), t.k, dw.d, dw.w, t.edge_id, r.data_ptr(), s)
+
+
+def _graph_struct(dw, g_tables, g_eu, g_ev, sketch_of, survivors_ptr, keep):
+    """cmp_graph over tables of `dw`; sketch_of(e, end) -> (table index in dw, sketch index)."""
+    ne = len(g_eu)
+    eu = (C.c_int32 * max(ne, 1))(*g_eu)
+    ev = (C.c_int32 * max(ne, 1))(*g_ev)
+    sk, ab, pm, rk, sl = [], [], [], [], []
+    for e in range(ne):
+        for end in range(2):
+            ti, si = sketch_of(e, end)
+            sk.append(dw.tables[ti].counters[si].data_ptr())
+            ab.append(dw.abs_sorted[ti][si].data_ptr())
+            pm.append(dw.perm[ti][si].data_ptr())
+            rk.append(dw.ranks[ti][si].data_ptr())
+            sl.append(si)
+    n2 = max(2 * ne, 1)
+    arrs = [(C.c_void_p * n2)(*sk), (C.c_void_p * n2)(*ab), (C.c_void_p * n2)(*pm), (C.c_void_p * n2)(*rk),
+            (C.c_int32 * n2)(*sl)]
+    keep += [eu, ev] + arrs
+    return K.cmp_graph(g_tables, ne, eu, ev, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4], survivors_ptr)
+
+
 class DeviceEstimator:
     """Presorted sketches of a built DeviceWorkload plus an encoded estimate plan for a
     list of sub-plans (bit t = table t), replayable with one cmp_estimate call."""
@@ -103,25 +142,9 @@ class DeviceEstimator:
         self.graphs = []
         self._keep = []
         for dw in dws:
-            t_abs, t_perm = [], []
-            for t in dw.tables:
-                t_abs.append(torch.empty(t.counters.shape, dtype=torch.int32, device=self.device))
-                t_perm.append(torch.empty(t.counters.shape, dtype=torch.int32, device=self.device))
-            dw.abs_sorted, dw.perm = t_abs, t_perm
-            eu = (C.c_int32 * max(dw.n_edges, 1))(*dw.wl.edge_u)
-            ev = (C.c_int32 * max(dw.n_edges, 1))(*dw.wl.edge_v)
-            sk, ab, pm = [], [], []
-            for e in range(dw.n_edges):
-                for end in range(2):
-                    ti, si = dw.wl.sketch_of(e, end)
-                    sk.append(dw.tables[ti].counters[si].data_ptr())
-                    ab.append(t_abs[ti][si].data_ptr())
-                    pm.append(t_perm[ti][si].data_ptr())
-            n2 = max(2 * dw.n_edges, 1)
-            skp, abp, pmp = (C.c_void_p * n2)(*sk), (C.c_void_p * n2)(*ab), (C.c_void_p * n2)(*pm)
-            g = K.cmp_graph(len(dw.tables), dw.n_edges, eu, ev, skp, abp, pmp, dw.survivors.data_ptr())
-            self.graphs.append(g)
-            self._keep += [eu, ev, skp, abp, pmp]
+            _prep_tables(dw)
+            self.graphs.append(_graph_struct(dw, len(dw.tables), dw.wl.edge_u, dw.wl.edge_v, dw.wl.sketch_of,
+                                             dw.survivors.data_ptr(), self._keep))
         self.masks = np.ascontiguousarray(masks, np.uint64)
         self.sub_graph = np.zeros(self.masks.size, np.int32) if graph_of is None else np.ascontiguousarray(graph_of,
                                                                                                           np.int32)
@@ -137,9 +160,7 @@ class DeviceEstimator:
     def presort(self, stream=None):
         s = K.stream_handle(stream)
         for dw in self.dws:
-            for t, a, p in zip(dw.tables, dw.abs_sorted, dw.perm):
-                if t.k:
-                    K.cmp_presort(t.counters.data_ptr(), t.k * self.d, self.w, a.data_ptr(), p.data_ptr(), 0, 0, s)
+            _presort_tables(dw, s)
 
     def estimate(self, stream=None, row_est=True):
         status = self.dws[0].status
@@ -199,17 +220,14 @@ class PairBatch:
         dw, d, w = self.dw, self.d, self.w
         self.abs = torch.empty((2 * self.n, d, w), dtype=torch.int32, device=self.device)
         self.perm = torch.empty_like(self.abs)
+        self.ranks = torch.empty_like(self.abs)   # one sketch per table: the inverse permutations
+        dw.abs_sorted = [self.abs[i:i + 1] for i in range(2 * self.n)]
+        dw.perm = [self.perm[i:i + 1] for i in range(2 * self.n)]
+        dw.ranks = [self.ranks[i:i + 1].unsqueeze(0) for i in range(2 * self.n)]
         self.graphs, self._keep = [], []
-        eu = (C.c_int32 * 1)(0)
-        ev = (C.c_int32 * 1)(1)
-        self._keep += [eu, ev]
         for i in range(self.n):
-            a, b = dw.tables[2 * i].counters[0], dw.tables[2 * i + 1].counters[0]
-            skp = (C.c_void_p * 2)(a.data_ptr(), b.data_ptr())
-            abp = (C.c_void_p * 2)(self.abs[2 * i].data_ptr(), self.abs[2 * i + 1].data_ptr())
-            pmp = (C.c_void_p * 2)(self.perm[2 * i].data_ptr(), self.perm[2 * i + 1].data_ptr())
-            self._keep += [skp, abp, pmp]
-            self.graphs.append(K.cmp_graph(2, 1, eu, ev, skp, abp, pmp, dw.survivors.data_ptr() + 16 * i))
+            self.graphs.append(_graph_struct(dw, 2, [0], [1], lambda e, end, i=i: (2 * i + end, 0),
+                                             dw.survivors.data_ptr() + 16 * i, self._keep))
         sub_graph = np.arange(self.n, dtype=np.int32)
         masks = np.full(self.n, 0b11, np.uint64)
         pb, wb = K.cmp_estimate_plan_bytes(self.graphs, d, w, sub_graph, masks)
@@ -226,6 +244,9 @@ class PairBatch:
         s = K.stream_handle(stream)
         K.cmp_presort(self.counters.data_ptr(), 2 * self.n * self.d, self.w, self.abs.data_ptr(), self.perm.data_ptr(),
                       0, 0, s)
+        # k = 1 per table: the cross ranks are the inverse permutations, one call for all tables
+        K.cmp_cross_ranks(self.abs.data_ptr(), self.perm.data_ptr(), 1, 2 * self.n * self.d, self.w, [0],
+                          self.ranks.data_ptr(), s)
         K.cmp_estimate(self.plan_host.ctypes.data, self.plan_dev.data_ptr(), self.ws.data_ptr(), self.ws.numel(),
                        self.est.data_ptr(), self.row_est.data_ptr(), self.dw.status.data_ptr(), s)
 
@@ -278,3 +299,78 @@ class Combiner:
         K.cmp_mlp_infer(self.params.data_ptr(), self.nin, self.nh, self.skip, x.data_ptr(), x.shape[0], y.data_ptr(),
                         K.stream_handle(stream))
         return y
+
+
+class GraphBatch:
+    """Many join graphs handled together: every table of every graph in one batched build
+    (edges renumbered globally, one hash-parameter array), and the estimates of any set of
+    (graph, sub-plan) pairs in one plan."""
+
+    def __init__(self, graphs, device="cuda", hash_seed: int = 0xC0FFEE + 2):
+        from . import datagen as G
+        self.graphs = graphs
+        self.d, self.w = graphs[0].d, graphs[0].w
+        tables, eu, ev = [], [], []
+        self.table_off, self.edge_off = [], []
+        for g in graphs:
+            assert g.d == self.d and g.w == self.w
+            toff, eoff = len(tables), len(eu)
+            self.table_off.append(toff)
+            self.edge_off.append(eoff)
+            for t in g.tables:
+                tables.append(G.Table(t.name, t.cols, t.preds, t.key_col, [e + eoff for e in t.edge_id]))
+            eu += [u + toff for u in g.edge_u]
+            ev += [v + toff for v in g.edge_v]
+        self.wl = G.Workload("graph batch", tables, eu, ev, self.d, self.w, hash_seed, 0)
+        self.dw = DeviceWorkload(self.wl, device=device)
+        self.device = self.dw.device
+        self.total_rows = self.wl.total_rows
+
+    def build_batched(self, cfg=None, stream=None):
+        self.dw.build_batched(cfg, stream)
+
+    def build_per_table(self, cfg=None, stream=None):
+        self.dw.build(cfg, stream)
+
+    def graph_structs(self):
+        """cmp_graph per graph over the batch's device sketches (presort arrays allocated)."""
+        dw = self.dw
+        if not hasattr(self, "_graphs"):
+            _prep_tables(dw)
+            self._graphs, self._keep = [], []
+            for gi, g in enumerate(self.graphs):
+                toff, eoff = self.table_off[gi], self.edge_off[gi]
+                self._graphs.append(_graph_struct(dw, len(g.tables), g.edge_u, g.edge_v,
+                                                  lambda e, end, eoff=eoff: self.wl.sketch_of(e + eoff, end),
+                                                  dw.survivors.data_ptr() + 8 * toff, self._keep))
+        return self._graphs
+
+    def presort(self, stream=None):
+        s = K.stream_handle(stream)
+        self.graph_structs()
+        _presort_tables(self.dw, s)
+
+    def plan(self, sub_graph, sub_mask, cfg=None):
+        """An encoded estimate plan (host blob, device copy, workspace, outputs)."""
+        graphs = self.graph_structs()
+        sg = np.ascontiguousarray(sub_graph, np.int32)
+        sm = np.ascontiguousarray(sub_mask, np.uint64)
+        pb, wb = K.cmp_estimate_plan_bytes(graphs, self.d, self.w, sg, sm, cfg)
+        host = np.zeros(max(pb, 16), np.uint8)
+        K.cmp_estimate_plan_encode(graphs, self.d, self.w, sg, sm, host.ctypes.data, pb, cfg)
+        return EstimatePlan(host, self.device, wb, sm.size, self.d, self.dw.status)
+
+
+class EstimatePlan:
+    def __init__(self, host, device, ws_bytes, n_sub, d, status):
+        self.host = host
+        self.dev = torch.from_numpy(host).to(device)
+        self.ws = torch.empty(max(ws_bytes, 16), dtype=torch.uint8, device=device)
+        self.est = torch.empty(n_sub, dtype=torch.float64, device=device)
+        self.row_est = torch.empty((n_sub, d, 2), dtype=torch.int64, device=device)
+        self.status = status
+
+    def run(self, stream=None, row_est=True):
+        K.cmp_estimate(self.host.ctypes.data, self.dev.data_ptr(), self.ws.data_ptr(), self.ws.numel(),
+                       self.est.data_ptr(), self.row_est.data_ptr() if row_est else 0, self.status.data_ptr(),
+                       K.stream_handle(stream))

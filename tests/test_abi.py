@@ -125,8 +125,9 @@ def _graph(K, eu, ev, nt):
     ne = len(eu)
     arr = lambda v: (C.c_int32 * max(ne, 1))(*v)
     ptrs = (C.c_void_p * max(2 * ne, 1))(*[0x10000 + 0x100 * i for i in range(2 * ne)])
-    g = K.cmp_graph(nt, ne, arr(eu), arr(ev), ptrs, ptrs, ptrs, 0x9000)
-    g._keep = (ptrs,)
+    slots = (C.c_int32 * max(2 * ne, 1))(*([0] * (2 * ne)))
+    g = K.cmp_graph(nt, ne, arr(eu), arr(ev), ptrs, ptrs, ptrs, ptrs, slots, 0x9000)
+    g._keep = (ptrs, slots)
     return g
 
 
