@@ -30,7 +30,16 @@ __device__ __forceinline__ bool add_ovf(i128 a, i128 b, i128* r) {
   return ((a ^ s) & (b ^ s)) < 0;
 }
 
+__device__ __forceinline__ bool fits64(i128 v) { return v == i128(int64_t(v)); }
+
 __device__ __forceinline__ bool mul_ovf(i128 a, i128 b, i128* r) {
+  if (fits64(a) && fits64(b)) {  // |a|, |b| <= 2^63: the product fits int128 exactly
+    const int64_t x = int64_t(a), y = int64_t(b);
+    const uint64_t lo = uint64_t(x) * uint64_t(y);
+    const int64_t hi = __mul64hi(x, y);
+    *r = i128((u128(uint64_t(hi)) << 64) | lo);
+    return false;
+  }
   const bool neg = (a < 0) != (b < 0);
   const u128 ua = a < 0 ? u128(0) - u128(a) : u128(a);
   const u128 ub = b < 0 ? u128(0) - u128(b) : u128(b);
