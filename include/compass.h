@@ -161,9 +161,10 @@ cmp_status cmp_sketch_build_batched(const void* plan_host, const void* plan_dev,
  * merged sketch splits into sums over buckets above / below a magnitude threshold).
  * For each of the n_rows rows of length w in counters_dev (row-major), writes the
  * bucket permutation that sorts the row by (|C|, bucket index) ascending into perm_dev
- * and the sorted magnitudes into abs_sorted_dev (both [n_rows][w]).  This version
- * sorts each row in shared memory and handles w <= 16384 (CMP_EUNSUPPORTED above);
- * cmp_presort_ws_bytes reports the workspace it needs (0 here). */
+ * and the sorted magnitudes into abs_sorted_dev (both [n_rows][w]).  Rows with
+ * w <= 16384 are sorted in shared memory and need no workspace; longer rows are sorted
+ * in chunks and merged in global memory, 64 rows at a time, in ws_dev of
+ * cmp_presort_ws_bytes(n_rows, w) bytes (CMP_EWORKSPACE if smaller). */
 size_t cmp_presort_ws_bytes(int64_t n_rows, int32_t w);
 cmp_status cmp_presort(const int32_t* counters_dev, int64_t n_rows, int32_t w, uint32_t* abs_sorted_dev,
                        int32_t* perm_dev, void* ws_dev, size_t ws_bytes, void* stream);

@@ -228,10 +228,13 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
 
 extern "C" {
 
+// Rows sorted per pass by the large-w path (bounds its workspace).
+constexpr int64_t kPresortRowsPerPass = 64;
+
 size_t cmp_presort_ws_bytes(int64_t n_rows, int32_t w) {
-  (void)n_rows;
-  (void)w;
-  return 0;
+  if (n_rows <= 0 || w <= kPresortSmemMaxW || w > CMP_MAX_W) return 0;
+  const int64_t rows = n_rows < kPresortRowsPerPass ? n_rows : kPresortRowsPerPass;
+  return size_t(2 * rows * presort_padded(w) * int64_t(sizeof(unsigned long long)));
 }
 
 cmp_status cmp_cross_ranks(const uint32_t* abs_sorted_dev, const int32_t* perm_dev, int32_t k, int32_t d, int32_t w,
@@ -248,13 +251,15 @@ cmp_status cmp_cross_ranks(const uint32_t* abs_sorted_dev, const int32_t* perm_d
 
 cmp_status cmp_presort(const int32_t* counters_dev, int64_t n_rows, int32_t w, uint32_t* abs_sorted_dev,
                        int32_t* perm_dev, void* ws_dev, size_t ws_bytes, void* stream) {
-  (void)ws_dev;
-  (void)ws_bytes;
   if (n_rows < 0 || w < 1 || w > CMP_MAX_W) return CMP_EINVAL;
   if (n_rows > 0 && (!counters_dev || !abs_sorted_dev || !perm_dev)) return CMP_EINVAL;
-  if (w > 16384) return CMP_EUNSUPPORTED;
-  return launch_presort(counters_dev, n_rows, w, abs_sorted_dev, perm_dev, reinterpret_cast<cudaStream_t>(stream)) ==
-                 cudaSuccess
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (w <= kPresortSmemMaxW)
+    return launch_presort(counters_dev, n_rows, w, abs_sorted_dev, perm_dev, st) == cudaSuccess ? CMP_OK : CMP_ECUDA;
+  if (n_rows == 0) return CMP_OK;
+  if (!ws_dev || ws_bytes < cmp_presort_ws_bytes(n_rows, w)) return CMP_EWORKSPACE;
+  const int64_t rows = n_rows < kPresortRowsPerPass ? n_rows : kPresortRowsPerPass;
+  return launch_presort_large(counters_dev, n_rows, w, abs_sorted_dev, perm_dev, ws_dev, rows, st) == cudaSuccess
              ? CMP_OK
              : CMP_ECUDA;
 }

@@ -121,6 +121,127 @@ __global__ void __launch_bounds__(1024) k_presort(const int32_t* __restrict__ C,
   }
 }
 
+// Rows longer than one shared-memory sort: chunks of kChunk keys are bitonic-sorted in
+// shared memory, then runs are merged pairwise in global memory.  Each key's place in the
+// merged run is its index in its own run plus the number of partner-run keys placed
+// before it.
+constexpr int kChunk = 8192;
+
+// Rows of C are w long; key rows are L long (L a multiple of kChunk, keys beyond w are
+// padding that sorts last).
+__global__ void __launch_bounds__(1024) k_presort_chunks(const int32_t* __restrict__ C, int64_t n_rows, int32_t w,
+                                                         int64_t L, unsigned long long* __restrict__ keys) {
+  extern __shared__ unsigned long long key[];  // kChunk keys
+  const int chunks = int(L / kChunk);
+  for (int64_t blk = blockIdx.x; blk < n_rows * chunks; blk += gridDim.x) {
+    const int64_t row = blk / chunks;
+    const int c0 = int(blk % chunks) * kChunk;
+    const int32_t* src = C + row * w;
+    for (int j = threadIdx.x; j < kChunk; j += blockDim.x) {
+      const int g = c0 + j;
+      if (g < w) {
+        const int32_t v = src[g];
+        const uint32_t a = v < 0 ? uint32_t(-int64_t(v)) : uint32_t(v);
+        key[j] = (static_cast<unsigned long long>(a) << 32) | uint32_t(g);
+      } else {
+        key[j] = ~0ull;
+      }
+    }
+    __syncthreads();
+    for (int k = 2; k <= kChunk; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < kChunk; i += blockDim.x) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const unsigned long long a = key[i], b = key[ixj];
+            if ((a > b) == ((i & k) == 0)) {
+              key[i] = b;
+              key[ixj] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    unsigned long long* dst = keys + row * L + c0;
+    for (int j = threadIdx.x; j < kChunk; j += blockDim.x) dst[j] = key[j];
+    __syncthreads();
+  }
+}
+
+// One merge level: runs of length `run` (padded row length L, a power of two times kChunk).
+__global__ void k_presort_merge(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out,
+                                int64_t n_rows, int64_t L, int64_t run) {
+  const int64_t total = n_rows * L;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t row = t / L, i = t % L;
+    const int64_t base = row * L + (i / (2 * run)) * (2 * run);
+    const int64_t off = i % (2 * run);
+    const bool left = off < run;
+    const int64_t idx = left ? off : off - run;
+    const unsigned long long v = in[t];
+    const unsigned long long* other = in + base + (left ? run : 0);
+    // partner keys placed before v: below it, and for the right run also equal to it
+    // (equal keys are the padding; the left run's copies go first, so positions are a
+    // permutation of the output run)
+    int64_t lo = 0, hi = run;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (left ? other[mid] < v : other[mid] <= v) lo = mid + 1;
+      else hi = mid;
+    }
+    out[base + idx + lo] = v;
+  }
+}
+
+__global__ void k_presort_split(const unsigned long long* __restrict__ keys, int64_t n_rows, int32_t w, int64_t L,
+                                uint32_t* __restrict__ abs_out, int32_t* __restrict__ perm_out) {
+  const int64_t total = n_rows * int64_t(w);
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t row = t / w, j = t % w;
+    const unsigned long long k = keys[row * L + j];
+    abs_out[t] = uint32_t(k >> 32);
+    perm_out[t] = int32_t(uint32_t(k));
+  }
+}
+
+int64_t presort_padded(int32_t w) {
+  int64_t L = kChunk;
+  while (L < w) L <<= 1;
+  return L;
+}
+
+cudaError_t launch_presort_large(const int32_t* C, int64_t n_rows, int32_t w, uint32_t* abs_out, int32_t* perm_out,
+                                 void* ws, int64_t rows_per_pass, cudaStream_t st) {
+  const int64_t L = presort_padded(w);
+  unsigned long long* a = static_cast<unsigned long long*>(ws);
+  unsigned long long* b = a + rows_per_pass * L;
+  for (int64_t r0 = 0; r0 < n_rows; r0 += rows_per_pass) {
+    const int64_t nr = n_rows - r0 < rows_per_pass ? n_rows - r0 : rows_per_pass;
+    const int64_t nblk = nr * (L / kChunk);
+    const int smem = int(sizeof(unsigned long long)) * kChunk;
+    cudaError_t e = cudaFuncSetAttribute(k_presort_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_presort_chunks<<<unsigned(nblk < 4096 ? nblk : 4096), 1024, smem, st>>>(C + r0 * w, nr, w, L, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int64_t run = kChunk; run < L; run <<= 1) {
+      k_presort_merge<<<4096, 256, 0, st>>>(a, b, nr, L, run);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      unsigned long long* t = a;
+      a = b;
+      b = t;
+    }
+    k_presort_split<<<4096, 256, 0, st>>>(a, nr, w, L, abs_out + r0 * w, perm_out + r0 * w);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    a = static_cast<unsigned long long*>(ws);
+    b = a + rows_per_pass * L;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_presort(const int32_t* C, int64_t n_rows, int32_t w, uint32_t* abs_out, int32_t* perm_out,
                            cudaStream_t st) {
   if (n_rows <= 0) return cudaSuccess;

@@ -120,6 +120,10 @@ __device__ inline double i128_to_double(i128 v) {
 
 cudaError_t launch_presort(const int32_t* C, int64_t n_rows, int32_t w, uint32_t* abs_out, int32_t* perm_out,
                            cudaStream_t st);
+cudaError_t launch_presort_large(const int32_t* C, int64_t n_rows, int32_t w, uint32_t* abs_out, int32_t* perm_out,
+                                 void* ws, int64_t rows_per_pass, cudaStream_t st);
+int64_t presort_padded(int32_t w);
+constexpr int32_t kPresortSmemMaxW = 16384;
 cudaError_t launch_estimate(const EstArgs& a, double* est, int64_t* row_est, cudaStream_t st);
 cudaError_t launch_cross_ranks(const uint32_t* abs, const int32_t* perm, int32_t k, int32_t d, int32_t w,
                                const int32_t* edge_id, int32_t* ranks, cudaStream_t st);

@@ -160,5 +160,8 @@ def test_estimate_plan_host_logic(K):
 
 def test_presort_rejections(K):
     assert K.lib().cmp_presort(0x10, 4, 0, 0x10, 0x10, None, 0, None) == K.CMP_EINVAL
-    assert K.lib().cmp_presort(0x10, 4, 1 << 15, 0x10, 0x10, None, 0, None) == K.CMP_EUNSUPPORTED
+    assert K.lib().cmp_presort(0x10, 4, 1 << 15, 0x10, 0x10, None, 0, None) == K.CMP_EWORKSPACE
+    assert K.cmp_presort_ws_bytes(4, 1 << 15) == 2 * 4 * (1 << 15) * 8
+    assert K.cmp_presort_ws_bytes(1000, 65536) == 2 * 64 * 65536 * 8
+    assert K.cmp_presort_ws_bytes(1000, 4096) == 0
     assert K.lib().cmp_presort(None, 4, 64, 0x10, 0x10, None, 0, None) == K.CMP_EINVAL

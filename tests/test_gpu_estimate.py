@@ -36,12 +36,14 @@ def _check(orc, dw, est, masks, brute=False):
 
 def test_presort_orders_by_magnitude_then_bucket():
     rng = np.random.default_rng(0)
-    for w in (1, 2, 5, 64, 1023, 4096, 16384):
+    for w in (1, 2, 5, 64, 1023, 4096, 16384, 16385, 40000, 65536):
         C = torch.from_numpy(rng.integers(-7, 8, size=(3, w)).astype(np.int32)).cuda()
         C[0, 0] = -(2 ** 31) + 1
         a = torch.empty_like(C)
         p = torch.empty_like(C)
-        K.cmp_presort(C.data_ptr(), 3, w, a.data_ptr(), p.data_ptr(), 0, 0, K.stream_handle())
+        nb = K.cmp_presort_ws_bytes(3, w)
+        ws = torch.empty(max(nb, 16), dtype=torch.uint8, device="cuda")
+        K.cmp_presort(C.data_ptr(), 3, w, a.data_ptr(), p.data_ptr(), ws.data_ptr(), nb, K.stream_handle())
         torch.cuda.synchronize()
         Cn = C.cpu().numpy().astype(np.int64)
         for r in range(3):
