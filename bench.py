@@ -47,7 +47,7 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phases", action="store_true", help="print a per-phase breakdown on stderr")
-    ap.add_argument("--case", default=None, choices=["estimate_small", "build_f1", "batched"],
+    ap.add_argument("--case", default=None, choices=["estimate_small", "build_f1", "batched", "scale"],
                     help="run one small profiling case instead of the benchmark (for ncu captures)")
     return ap.parse_args()
 
@@ -538,10 +538,54 @@ def run_batched(a):
     print(json.dumps(line), flush=True)
 
 
+def run_scale(a):
+    """The scale configuration (1e9-row fact, int64 keys, d = 15, w = 65536, drawn on the
+    device): batched build of the three tables, presort + cross ranks, estimates of every
+    connected sub-plan; per-phase CUDA-event times over 3 timed repetitions."""
+    import torch
+
+    from paper_2102_02440_gb300 import datagen as G
+    from paper_2102_02440_gb300 import pipeline as P
+    wl = G.scale_workload_device()
+    dw = P.DeviceWorkload(wl)
+    masks = G.connected_subplans(3, wl.edge_u, wl.edge_v)
+    est = P.DeviceEstimator(dw, masks)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ts = []
+    for k in range(4):
+        ev[0].record()
+        dw.build_batched()
+        ev[1].record()
+        est.presort()
+        ev[2].record()
+        est.estimate()
+        ev[3].record()
+        torch.cuda.synchronize()
+        if k:
+            ts.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
+    dw.check_status()
+    ph = {n: statistics.median(t[i] for t in ts) for i, n in enumerate(("build", "presort", "estimate"))}
+    surv = dw.survivors.cpu().numpy()
+    rows, col_bytes = wl.total_rows, wl.column_bytes()
+    evals = int(sum(int(surv[i]) * len(t.key_col) * wl.d for i, t in enumerate(wl.tables)))
+    hbm_peak, kind = _peaks()
+    step = sum(ph.values())
+    print(json.dumps({"case": "scale", "workload": wl.name, "rows": rows, "column_bytes": col_bytes,
+                      "survivors": [int(x) for x in surv], "phases_ms": ph,
+                      "tuples_per_s_step": rows / (step / 1e3), "build_tuples_per_s": rows / (ph["build"] / 1e3),
+                      "build_hbm": {"achieved_gbs": col_bytes / (ph["build"] / 1e3) / 1e9, "peak_gbs": hbm_peak,
+                                    "frac": col_bytes / (ph["build"] / 1e3) / 1e9 / hbm_peak, "peak_kind": kind},
+                      "build_alu": {"cw_evaluations": evals,
+                                    "frac": evals * CW_INSTR / (ph["build"] / 1e3) / INT_ISSUE_PEAK},
+                      "estimates": est.est.cpu().numpy().tolist()}), flush=True)
+
+
 def main():
     a = _args()
     if a.case == "batched":
         run_batched(a)
+    elif a.case == "scale":
+        run_scale(a)
     elif a.case:
         run_case(a)
     elif a.impl == "reference":

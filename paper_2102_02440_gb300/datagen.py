@@ -411,3 +411,50 @@ def graph_batch(n_graphs: int = 64, n_lo: int = 4, n_hi: int = 17, rows_lo: int 
         out.append(Workload(f"{kind}{n}", tabs, [u for u, _ in edges], [v for _, v in edges], d, w,
                             hash_seed + gi, seed))
     return out
+
+
+def zipf_keys_device(gen, n: int, D: int, s: float, dtype=None, chunk: int = 1 << 26):
+    """n Zipf(s) keys over [0, D) drawn on the generator's device (chunked), hot keys
+    scattered by a seeded affine permutation; int64 unless dtype is given."""
+    import torch
+    dev = gen.device
+    dtype = dtype or torch.int64
+    lo = int(torch.randint(1, max(D, 2), (1,), generator=gen, device=dev).item())
+    A = lo
+    while np.gcd(A, D) != 1:
+        A = A % (D - 1) + 1 if D > 2 else 1
+    B = int(torch.randint(0, max(D, 1), (1,), generator=gen, device=dev).item())
+    out = torch.empty(n, dtype=dtype, device=dev)
+    for c0 in range(0, n, chunk):
+        m = min(chunk, n - c0)
+        s_t = torch.full((m,), float(s), dtype=torch.float64, device=dev)
+        N_t = torch.full((m,), float(D), dtype=torch.float64, device=dev)
+        r = zipf_ranks_device(gen, s_t, N_t) - 1
+        out[c0:c0 + m] = ((A * r + B) % D).to(dtype)
+    return out
+
+
+def scale_workload_device(n_fact: int = 1_000_000_000, n_d1: int = 100_000_000, n_d2: int = 1_000_000,
+                          d: int = 15, w: int = 65536, seed: int = 20210209, device="cuda",
+                          hash_seed: int = 0xC0FFEE + 4) -> Workload:
+    """The scale configuration, drawn on the device: fact F (n_fact rows) with fk1 int64
+    Zipf(1.2) over [0, n_d1), fk2 int64 Zipf(1.2) over [0, n_d2), p1 and p2 int32 uniform
+    on [0, 1000) filtered by p1 < 250 and p2 < 400 (10% combined); dimensions D1 (n_d1)
+    and D2 (n_d2) with int64 primary keys that are permutations.  Edges e0 D1-F, e1 D2-F.
+    Columns are device tensors."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    fk1 = zipf_keys_device(gen, n_fact, n_d1, 1.2)
+    fk2 = zipf_keys_device(gen, n_fact, n_d2, 1.2)
+    p1 = torch.randint(0, 1000, (n_fact,), generator=gen, device=device, dtype=torch.int32)
+    p2 = torch.randint(0, 1000, (n_fact,), generator=gen, device=device, dtype=torch.int32)
+    pk1 = torch.randperm(n_d1, generator=gen, device=device, dtype=torch.int64)
+    pk2 = torch.randperm(n_d2, generator=gen, device=device, dtype=torch.int64)
+    F = Table("F", [fk1, fk2, p1, p2], [Pred(2, RANGE, INT64_MIN, 250), Pred(3, RANGE, INT64_MIN, 400)], [0, 1],
+              [0, 1])
+    D1 = Table("D1", [pk1], [], [0], [0])
+    D2 = Table("D2", [pk2], [], [0], [1])
+    # tables: 0 F, 1 D1, 2 D2
+    return Workload(f"scale F{n_fact} D1 {n_d1} D2 {n_d2} d{d} w{w}", [F, D1, D2], [1, 2], [0, 0], d, w,
+                    hash_seed, seed)

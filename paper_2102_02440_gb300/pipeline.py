@@ -12,7 +12,9 @@ import torch
 from . import compass as K
 
 
-def _dev(a: np.ndarray, device) -> torch.Tensor:
+def _dev(a, device) -> torch.Tensor:
+    if isinstance(a, torch.Tensor):
+        return a.to(device).contiguous()
     return torch.from_numpy(np.ascontiguousarray(a)).to(device)
 
 
@@ -103,9 +105,14 @@ def _prep_tables(dw):
 
 def _presort_tables(dw, s):
     """cmp_presort then cmp_cross_ranks for every table with sketches."""
+    need = max((K.cmp_presort_ws_bytes(t.k * dw.d, dw.w) for t in dw.tables), default=0)
+    ws = getattr(dw, "presort_ws", None)
+    if need and (ws is None or ws.numel() < need):
+        ws = dw.presort_ws = torch.empty(need, dtype=torch.uint8, device=dw.device)
     for t, a, p, r in zip(dw.tables, dw.abs_sorted, dw.perm, dw.ranks):
         if t.k:
-            K.cmp_presort(t.counters.data_ptr(), t.k * dw.d, dw.w, a.data_ptr(), p.data_ptr(), 0, 0, s)
+            K.cmp_presort(t.counters.data_ptr(), t.k * dw.d, dw.w, a.data_ptr(), p.data_ptr(),
+                          ws.data_ptr() if need else 0, need, s)
             K.cmp_cross_ranks(a.data_ptr(), p.data_ptr(), t.k, dw.d, dw.w, t.edge_id, r.data_ptr(), s)
 
 
