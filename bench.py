@@ -281,7 +281,11 @@ def run_ours(a):
     wl = workload(a.scale, a.w, rank)
     dw = P.DeviceWorkload(wl, device=dev)
     masks = G.connected_subplans(len(wl.tables), wl.edge_u, wl.edge_v)
-    est = P.DeviceEstimator(dw, masks)
+    # launch shapes picked by the autotuner on this workload (outside the timed region)
+    from paper_2102_02440_gb300 import autotune as AT
+    cfg_build, tuned_build = AT.tune_build(dw, reps=2)
+    cfg_est, tuned_est = AT.tune_estimate(lambda c: P.DeviceEstimator(dw, masks, cfg=c), reps=1)
+    est = P.DeviceEstimator(dw, masks, cfg=cfg_est)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     # learned combiner over every sub-plan's row estimates; self-join sizes of the two
@@ -312,7 +316,7 @@ def run_ours(a):
         s = K.stream_handle(stream)
         if evs:
             evs[0].record(stream)
-        dw.build_batched(stream=stream)
+        dw.build_batched(cfg_build, stream=stream)
         if evs:
             evs[1].record(stream)
         est.presort(stream=stream)
@@ -417,6 +421,7 @@ def run_ours(a):
                            "l2": "256 MB buffer written between steps, outside the per-step events",
                            "parallelism": f"replicas x{world} (independent queries)"},
                 "phases_ms": phase, "subplan_estimates_per_s": n_est / (phase["estimate"] / 1e3),
+                "autotuned": {"build": tuned_build["cfg"], "estimate": tuned_est["cfg"]},
                 "build_only_tuples_per_s": rows / (phase["build"] / 1e3),
                 "survivors": [int(x) for x in surv],
                 "roofline": roof, "roofline_build": roof_build, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
