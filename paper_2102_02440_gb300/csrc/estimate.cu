@@ -32,6 +32,33 @@ __device__ __forceinline__ bool add_ovf(i128 a, i128 b, i128* r) {
 
 __device__ __forceinline__ bool fits64(i128 v) { return v == i128(int64_t(v)); }
 
+// a * b for |b| <= 2^63 (b from a stored int64 or int32 value), overflow-checked.
+__device__ __forceinline__ bool mul_ovf_64(i128 a, int64_t b, i128* r) {
+  if (fits64(a)) {
+    const int64_t x = int64_t(a);
+    const uint64_t lo = uint64_t(x) * uint64_t(b);
+    const int64_t hi = __mul64hi(x, b);
+    *r = i128((u128(uint64_t(hi)) << 64) | lo);
+    return false;
+  }
+  // |a| * |b| = (ah * |b|) 2^64 + al * |b| with ah = |a| >> 64 < 2^63
+  const bool neg = (a < 0) != (b < 0);
+  const u128 ua = a < 0 ? u128(0) - u128(a) : u128(a);
+  const uint64_t ub = b < 0 ? uint64_t(0) - uint64_t(b) : uint64_t(b);
+  const uint64_t ah = uint64_t(ua >> 64), al = uint64_t(ua);
+  const u128 hi = u128(ah) * ub;          // must stay below 2^63 after the carry
+  const u128 lo = u128(al) * ub;
+  const u128 top = hi + (lo >> 64);
+  const bool ovf = (top >> 63) != 0 && !(neg && top == (u128(1) << 63) && uint64_t(lo) == 0);
+  const u128 mag = (top << 64) | uint64_t(lo);
+  *r = neg ? i128(u128(0) - mag) : i128(mag);
+  return ovf;
+}
+
+__device__ __forceinline__ bool mul_ovf(i128 a, i128 b, i128* r);
+__device__ __forceinline__ bool mul_s(i128 a, int64_t b, i128* r) { return mul_ovf_64(a, b, r); }
+__device__ __forceinline__ bool mul_s(i128 a, i128 b, i128* r) { return mul_ovf(a, b, r); }
+
 __device__ __forceinline__ bool mul_ovf(i128 a, i128 b, i128* r) {
   if (fits64(a) && fits64(b)) {  // |a|, |b| <= 2^63: the product fits int128 exactly
     const int64_t x = int64_t(a), y = int64_t(b);
@@ -373,6 +400,68 @@ __device__ __forceinline__ bool store_fits(i128, i128*) { return true; }
 // In-place inclusive scan of a[0..n) (forward) or suffix scan (reverse).  Sums are exact
 // in int128 (bit 0 of the flag on overflow); a stored value that does not fit S sets
 // bit 1 (the item is then recomputed with int128 storage).
+// int64 storage: partial sums stay in int64 (overflow only flags bit 1: the item is then
+// recomputed with int128 storage, so no int128 work is needed here).
+__device__ __forceinline__ bool add64_ovf(int64_t a, int64_t b, int64_t* r) {
+  const int64_t s = int64_t(uint64_t(a) + uint64_t(b));
+  *r = s;
+  return ((a ^ s) & (b ^ s)) < 0;
+}
+
+__device__ void block_scan(int64_t* a, int n, bool reverse, BlockScratch& bs) {
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int per = (n + T - 1) / T;
+  const int b = tid * per, e = min(n, b + per);
+  int64_t s = 0;
+  bool o = false;
+  if (reverse) {
+    for (int q = b; q < e; q++) o |= add64_ovf(s, a[n - 1 - q], &s);
+  } else {
+    for (int q = b; q < e; q++) o |= add64_ovf(s, a[q], &s);
+  }
+  const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+  int64_t incl = s;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int64_t other = __shfl_up_sync(0xffffffffu, incl, off);
+    int64_t r;
+    const bool ob = add64_ovf(incl, other, &r);
+    if (lane >= off) {
+      o |= ob;
+      incl = r;
+    }
+  }
+  int64_t* sh = reinterpret_cast<int64_t*>(bs.sh_i128);
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  if (tid == 0) {
+    int64_t t = 0;
+    bool oo = false;
+    for (int i = 0; i < nw; i++) {
+      const int64_t v = sh[i];
+      sh[i] = t;
+      oo |= add64_ovf(t, v, &t);
+    }
+    if (oo) atomicOr(bs.sh_flag, 2);
+  }
+  __syncthreads();
+  int64_t run;
+  o |= add64_ovf(sh[warp], incl - s, &run);
+  if (reverse) {
+    for (int q = b; q < e; q++) {
+      o |= add64_ovf(run, a[n - 1 - q], &run);
+      a[n - 1 - q] = run;
+    }
+  } else {
+    for (int q = b; q < e; q++) {
+      o |= add64_ovf(run, a[q], &run);
+      a[q] = run;
+    }
+  }
+  if (o) atomicOr(bs.sh_flag, 2);
+  __syncthreads();
+}
+
 template <typename S>
 __device__ void block_scan(S* a, int n, bool reverse, BlockScratch& bs) {
   const int T = blockDim.x, tid = threadIdx.x;
@@ -439,6 +528,7 @@ __device__ void block_scan(S* a, int n, bool reverse, BlockScratch& bs) {
 // nothing, so it is skipped.  Products and sums are exact int128; values stored in the
 // int64 arrays that do not fit flag the item for recomputation with int128 storage.
 constexpr int kMaxIn = CMP_MAX_SKETCHES;
+constexpr int kMaxPreChunk = 256;  // conditioning values per item whose scalars the prologue precomputes
 
 // kIlp elements per thread have their loads issued together (memory-level parallelism);
 // MAXT is the launch bound that sets the register budget.
@@ -452,6 +542,12 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
   __shared__ EstIn sh_in[kEstMaxSubIn];
   __shared__ const int32_t* sh_cond[2];
   __shared__ int32_t sh_ncond;
+  // per conditioned operation (at most two per sub-plan), for every c of the chunk when
+  // its other inputs are leaves: |s[c]| and the "attains the minimum" value
+  __shared__ int32_t sh_pop[2], sh_pa[2];
+  __shared__ uint32_t sh_cac[2][kMaxPreChunk];
+  __shared__ i128 sh_cval[2][kMaxPreChunk];
+  __shared__ uint8_t sh_skip[kMaxPreChunk];
   BlockScratch bs{sh_i128, sh_flag};
   const int w = A.w;
   const int64_t W1 = int64_t(w) + 1;
@@ -482,6 +578,26 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
       for (int q = 0; q < n_in && nc < 2; q++)
         if (sh_in[q].kind == kInCond) sh_cond[nc++] = sh_in[q].s + ro;
       sh_ncond = nc;
+      // conditioned operations whose other inputs are all leaves: precomputable per c
+      int np = 0;
+      for (int o = 0; o < sb.n_ops && np < 2; o++) {
+        const EstOp& op = sh_ops[o];
+        int ca = -1;
+        bool leaves = true;
+        for (int a = 0, l = 0; l < op.k; l++) {
+          if (l == op.p) continue;
+          const int kind = sh_in[op.in_begin + l].kind;
+          if (kind == kInCond) ca = a;
+          else leaves &= kind == kInLeaf;
+          a++;
+        }
+        if (ca >= 0 && leaves) {
+          sh_pop[np] = o;
+          sh_pa[np] = ca;
+          np++;
+        }
+      }
+      for (int q = np; q < 2; q++) sh_pop[q] = -1;
     }
 
     // ---------------- prologue: cross ranks and leaf suffix sums (independent of c)
@@ -503,13 +619,49 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
       }
     }
     __syncthreads();
+    const int nchunk = item.c1 - item.c0;
+    const bool pre_ok = sb.cond && nchunk <= kMaxPreChunk;
+    if (pre_ok) {
+      for (int c = item.c0 + tid; c < item.c1; c += T) {
+        bool zero = false;
+        for (int q = 0; q < sh_ncond; q++) zero |= __ldg(sh_cond[q] + c) == 0;
+        sh_skip[c - item.c0] = zero;
+      }
+      for (int t = tid; t < 2 * nchunk; t += T) {
+        const int k = t / nchunk, c = item.c0 + t % nchunk;
+        if (sh_pop[k] < 0) continue;
+        const EstOp op = sh_ops[sh_pop[k]];
+        const EstIn* in = sh_in + op.in_begin;
+        const int p = op.p, m = op.k - (p >= 0 ? 1 : 0), a = sh_pa[k];
+        const int la = a + (p >= 0 && a >= p ? 1 : 0);
+        const EstIn& x = in[la];
+        const int32_t sv = __ldg(x.s + ro + c);
+        sh_cac[k][t % nchunk] = sv < 0 ? uint32_t(-int64_t(sv)) : uint32_t(sv);
+        const int rpos = __ldg(rank_row(x, x, A.d, item.row, w) + c);
+        i128 v = i128(sv);
+        bool o1 = false;
+        for (int b = 0; b < m && v != 0; b++) {  // the others are leaves: G is a cached suffix sum
+          if (b == a) continue;
+          const EstIn& y = in[b + (p >= 0 && b >= p ? 1 : 0)];
+          const int q = __ldg(rank_row(x, y, A.d, item.row, w) + rpos);
+          o1 |= mul_s(v, suf[int64_t(y.suf) * W1 + q], &v);
+        }
+        sh_cval[k][t % nchunk] = v;
+        if (o1) atomicOr(sh_flag, 1);
+      }
+      __syncthreads();
+    }
 
     i128 acc = 0;
     bool ovf = false;
     for (int c = item.c0; c < item.c1; c++) {
-      bool zero = false;
-      for (int q = 0; q < sh_ncond; q++) zero |= __ldg(sh_cond[q] + c) == 0;
-      if (zero) continue;  // block-uniform
+      if (pre_ok) {
+        if (sh_skip[c - item.c0]) continue;  // block-uniform
+      } else {
+        bool zero = false;
+        for (int q = 0; q < sh_ncond; q++) zero |= __ldg(sh_cond[q] + c) == 0;
+        if (zero) continue;  // block-uniform
+      }
       for (int o = 0; o < sb.n_ops; o++) {
         const EstOp op = sh_ops[o];
         const EstIn* in = sh_in + op.in_begin;
@@ -538,15 +690,24 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
           block_scan(sl, w, /*reverse=*/true, bs);
         }
         // 2a. conditioned inputs: |s[c]| and their single "attains the minimum" term
-        if (tid < m) {
-          const EstIn& x = in[tid + (p >= 0 && tid >= p ? 1 : 0)];
-          if (x.kind == kInCond) {
-            const int32_t v = __ldg(x.s + ro + c);
-            sh_ac[tid] = v < 0 ? uint32_t(-int64_t(v)) : uint32_t(v);
+        const int pk = pre_ok ? (sh_pop[0] == o ? 0 : (sh_pop[1] == o ? 1 : -1)) : -1;
+        if (pk >= 0) {  // precomputed in the prologue
+          if (tid == 0) {
+            sh_ac[sh_pa[pk]] = sh_cac[pk][c - item.c0];
+            sh_val[sh_pa[pk]] = sh_cval[pk][c - item.c0];
           }
+          __syncthreads();
+        } else {
+          if (tid < m) {
+            const EstIn& x = in[tid + (p >= 0 && tid >= p ? 1 : 0)];
+            if (x.kind == kInCond) {
+              const int32_t v = __ldg(x.s + ro + c);
+              sh_ac[tid] = v < 0 ? uint32_t(-int64_t(v)) : uint32_t(v);
+            }
+          }
+          __syncthreads();
         }
-        __syncthreads();
-        if (tid < m) {
+        if (pk < 0 && tid < m) {
           const int la = tid + (p >= 0 && tid >= p ? 1 : 0);
           const EstIn& x = in[la];
           if (x.kind == kInCond) {
@@ -565,7 +726,7 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
                   if (!(strict ? sh_ac[b] > tau : sh_ac[b] >= tau)) v = 0;
                 } else {
                   const int q = __ldg(rank_row(x, y, A.d, item.row, w) + rpos);
-                  o1 |= mul_ovf(v, i128(suf[int64_t(y.suf) * W1 + q]), &v);
+                  o1 |= mul_s(v, suf[int64_t(y.suf) * W1 + q], &v);
                 }
               }
             }
@@ -605,7 +766,7 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
             i128 v[kIlp];
 #pragma unroll
             for (int u = 0; u < kIlp; u++) {
-              if (msg) o2 |= mul_ovf(i128(sv[u]), i128(msg[jj[u]]), &v[u]);
+              if (msg) o2 |= mul_s(i128(sv[u]), msg[jj[u]], &v[u]);
               else v[u] = i128(sv[u]) * i128(mv[u]);  // |int32 * int32| < 2^62
               if (!ok[u]) v[u] = 0;
             }
@@ -629,7 +790,7 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
                 for (int u = 0; u < kIlp; u++) gg[u] = suf[int64_t(y.suf) * W1 + qq[u]];
 #pragma unroll
                 for (int u = 0; u < kIlp; u++)
-                  if (v[u] != 0) o2 |= mul_ovf(v[u], i128(gg[u]), &v[u]);
+                  if (v[u] != 0) o2 |= mul_s(v[u], gg[u], &v[u]);
               }
             }
 #pragma unroll
@@ -702,7 +863,7 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
                 }
 #pragma unroll
                 for (int u = 0; u < kIlp; u++) {
-                  if (t[u] != 0) o3 |= mul_ovf(t[u], i128(gs[u]), &t[u]);
+                  if (t[u] != 0) o3 |= mul_s(t[u], gs[u], &t[u]);
                   o3 |= add_ovf(add[u], i128(gp[u]), &add[u]);
                 }
               }
