@@ -225,12 +225,18 @@ typedef struct {
  *                gets CMP_EOVERFLOW)
  *   row_est_dev  NULL or [n_sub][d][2] int64: each exact row estimate as a little-endian
  *                two's-complement int128 (low word first) */
-/* Estimate launch shape; zero fields choose automatically. */
+/* Estimate launch shape; zero fields choose automatically.
+ * Sub-plans whose only cycle is a triangle, with every other table a leaf of one of its
+ * three tables, are evaluated by the triangle path: the conditioned sum regrouped as
+ * batched dominance sums, O(w G log w) per sketch row for G distinct clamp ranks, instead
+ * of one tree contraction per conditioning value (O(w^2)).  Both give the same exact
+ * integers.  It needs w <= 16384; flag CMP_EST_GENERIC_ONLY turns it off. */
+#define CMP_EST_GENERIC_ONLY 1
 typedef struct {
   int32_t threads;     /* threads per CTA (multiple of 32, <= 1024)                */
   int32_t ctas_per_sm; /* resident CTAs per SM the persistent grid is sized for    */
   int32_t cond_chunk;  /* conditioning values per work item of a cyclic sub-plan   */
-  int32_t reserved;
+  int32_t flags;       /* 0, or CMP_EST_GENERIC_ONLY; other bits: CMP_EINVAL       */
 } cmp_estimate_cfg;
 
 cmp_status cmp_estimate_plan_bytes(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,

@@ -15,6 +15,7 @@ from . import build_lib
 CMP_OK, CMP_EINVAL, CMP_EUNSUPPORTED, CMP_EOVERFLOW, CMP_ECUDA, CMP_EWORKSPACE, CMP_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 CMP_I32, CMP_I64 = 0, 1
 CMP_RANGE, CMP_EQ, CMP_IN_BITMAP = 0, 1, 2
+CMP_EST_GENERIC_ONLY = 1
 CMP_MAX_COLS, CMP_MAX_PREDS, CMP_MAX_SKETCHES, CMP_MAX_D = 32, 8, 16, 64
 
 
@@ -54,11 +55,11 @@ class cmp_build_cfg(C.Structure):
 
 class cmp_estimate_cfg(C.Structure):
     _fields_ = [("threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("cond_chunk", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("flags", C.c_int32)]
 
     @classmethod
-    def make(cls, threads=0, ctas_per_sm=0, cond_chunk=0):
-        return cls(threads, ctas_per_sm, cond_chunk, 0)
+    def make(cls, threads=0, ctas_per_sm=0, cond_chunk=0, flags=0):
+        return cls(threads, ctas_per_sm, cond_chunk, flags)
 
 
 class cmp_graph(C.Structure):

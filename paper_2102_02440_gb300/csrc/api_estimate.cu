@@ -12,13 +12,15 @@ using namespace cmpk;
 namespace {
 
 struct EstShape {
-  int32_t threads, ctas_per_sm, cond_chunk;
+  int32_t threads, ctas_per_sm, cond_chunk, flags;
 };
 
 cmp_status est_shape(const cmp_estimate_cfg* cfg, EstShape* s) {
   s->threads = (cfg && cfg->threads > 0) ? cfg->threads : 1024;
   s->ctas_per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : 1;
   s->cond_chunk = (cfg && cfg->cond_chunk > 0) ? cfg->cond_chunk : 64;
+  s->flags = cfg ? cfg->flags : 0;
+  if (s->flags & ~int32_t(CMP_EST_GENERIC_ONLY)) return CMP_EINVAL;
   if (s->threads < 32 || s->threads > 1024 || s->threads % 32 || s->ctas_per_sm > 32) return CMP_EINVAL;
   return CMP_OK;
 }
@@ -29,6 +31,9 @@ struct PlanOut {
   std::vector<EstIn> ins;
   std::vector<EstItem> items;
   int32_t max_slots = 0, max_in = 1, max_suf = 0, max_rank = 0;
+  std::vector<TriSub> tris;
+  std::vector<EstItem> tri_items;  // appended after the generic items
+  int32_t tri_max_leaves = 0;
 };
 
 bool graph_ok(const cmp_graph& g) {
@@ -47,10 +52,103 @@ bool graph_ok(const cmp_graph& g) {
   return true;
 }
 
+// Triangle evaluation (estimate_tri.cu): the only cycle is a-W-b, closed by the
+// conditioned edge a-b, and every other table is a leaf joined to a, b or W.  Returns
+// false, leaving P unchanged, for any other shape.
+bool plan_triangle(const cmp_graph& g, const std::vector<int>& es, const std::vector<char>& tree, int e_star,
+                   uint64_t mask, int32_t d, int32_t w, int32_t sub_index, PlanOut* P, EstSub* sb) {
+  const int nt = g.n_tables;
+  const int a = g.edge_u[e_star], b = g.edge_v[e_star];
+  auto touches = [&](int e, int t) { return g.edge_u[e] == t || g.edge_v[e] == t; };
+  auto other = [&](int e, int t) { return g.edge_u[e] == t ? g.edge_v[e] : g.edge_u[e]; };
+  auto end_of = [&](int e, int t) { return g.edge_u[e] == t ? 0 : 1; };
+  int W = -1, eaW = -1, ebW = -1;
+  for (int t = 0; t < nt && W < 0; t++) {
+    if (!((mask >> t) & 1) || t == a || t == b) continue;
+    int ea = -1, eb = -1;
+    for (int e : es) {
+      if (!tree[e] || !touches(e, t)) continue;
+      if (other(e, t) == a) ea = e;
+      if (other(e, t) == b) eb = e;
+    }
+    if (ea >= 0 && eb >= 0) {
+      W = t;
+      eaW = ea;
+      ebW = eb;
+    }
+  }
+  if (W < 0) return false;
+  std::vector<int> deg(nt, 0);
+  for (int e : es) deg[g.edge_u[e]]++, deg[g.edge_v[e]]++;
+  for (int t = 0; t < nt; t++) {
+    if (!((mask >> t) & 1) || t == a || t == b || t == W) continue;
+    if (deg[t] != 1) return false;
+    for (int e : es)
+      if (touches(e, t) && other(e, t) != a && other(e, t) != b && other(e, t) != W) return false;
+  }
+  const int nodes[3] = {a, b, W};
+  for (int n = 0; n < 3; n++)
+    if (deg[nodes[n]] - 2 > kTriMaxLeaves) return false;
+  TriSub ts;
+  std::memset(&ts, 0, sizeof(ts));
+  ts.sub = sub_index;
+  int32_t leaves = 0;
+  for (int n = 0; n < 3; n++) {
+    const int t = nodes[n];
+    TriNode& nd = ts.node[n];
+    nd.in_begin = int32_t(P->ins.size());
+    nd.k = 0;
+    nd.ia = nd.ib = -1;
+    for (int e : es) {  // ascending edge id
+      if (!touches(e, t)) continue;
+      const int me = end_of(e, t);
+      EstIn x;
+      std::memset(&x, 0, sizeof(x));
+      x.s = g.sketch[2 * e + me];
+      x.abs = g.abs_sorted[2 * e + me];
+      x.perm = g.perm[2 * e + me];
+      x.rk = g.ranks[2 * e + me];
+      x.tslot = g.slot[2 * e + me];
+      x.slot = x.suf = -1;
+      if (e == e_star) {
+        x.kind = kInCond;
+      } else if (e == eaW || e == ebW) {
+        x.kind = kInSlot;
+      } else {
+        x.kind = kInLeaf;
+        x.msk = g.sketch[2 * e + end_of(e, other(e, t))];
+      }
+      if (e == (n == 1 ? ebW : eaW)) nd.ia = nd.k;
+      if (e == (n == 2 ? ebW : e_star)) nd.ib = nd.k;
+      P->ins.push_back(x);
+      nd.k++;
+    }
+    leaves = std::max(leaves, nd.k - 2);
+  }
+  P->tri_max_leaves = std::max(P->tri_max_leaves, leaves);
+  const int32_t nch = (w + kTriCols - 1) / kTriCols;
+  sb->tri = int32_t(P->tris.size());
+  sb->cond = 1;
+  sb->n_ops = 0;
+  sb->n_chunks = nch;
+  sb->item_begin = int64_t(P->tri_items.size());  // offset by the generic items in plan_all
+  P->tris.push_back(ts);
+  for (int i = 0; i < d; i++)
+    for (int ch = 0; ch < nch; ch++) {
+      EstItem it;
+      it.sub = sub_index;
+      it.row = i;
+      it.c0 = ch * kTriCols;
+      it.c1 = std::min(w, (ch + 1) * kTriCols);
+      P->tri_items.push_back(it);
+    }
+  return true;
+}
+
 // Plan one sub-plan: spanning tree by BFS from the lowest table id (edges in id order),
 // non-tree edges conditioned, post-order operations for every non-leaf table.
 cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int32_t sub_index, int32_t chunk,
-                    PlanOut* P) {
+                    int32_t flags, PlanOut* P) {
   const int nt = g.n_tables;
   if (mask == 0 || (nt < 64 && (mask >> nt) != 0)) return CMP_EINVAL;
   std::vector<int> es;
@@ -77,6 +175,7 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
   std::memset(&sb, 0, sizeof(sb));
   sb.op_begin = int32_t(P->ops.size());
   sb.item_begin = int64_t(P->items.size());
+  sb.tri = -1;
   if (order.size() == 1) {
     sb.single = 1;
     sb.sv = g.survivors_dev + root;
@@ -87,6 +186,11 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
   for (int e : es)
     if (!tree[e]) cond.push_back(e);
   if (cond.size() > 1) return CMP_EUNSUPPORTED;  // more than one independent cycle
+  if (cond.size() == 1 && !(flags & CMP_EST_GENERIC_ONLY) && w <= kTriMaxW &&
+      plan_triangle(g, es, tree, cond[0], mask, d, w, sub_index, P, &sb)) {
+    P->subs.push_back(sb);
+    return CMP_OK;
+  }
   std::vector<int> deg(nt, 0);
   for (int e : es) deg[g.edge_u[e]]++, deg[g.edge_v[e]]++;
   auto is_leaf = [&](int t) { return t != root && deg[t] == 1; };
@@ -186,19 +290,29 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
     if (!graph_ok(graphs[gi])) return CMP_EINVAL;
   for (int32_t q = 0; q < n_sub; q++) {
     if (sub_graph[q] < 0 || sub_graph[q] >= n_graphs) return CMP_EINVAL;
-    const cmp_status st = plan_sub(graphs[sub_graph[q]], sub_mask[q], d, w, q, shape.cond_chunk, P);
+    const cmp_status st = plan_sub(graphs[sub_graph[q]], sub_mask[q], d, w, q, shape.cond_chunk, shape.flags, P);
     if (st != CMP_OK) return st;
   }
+  // triangle items after the generic ones (the generic kernel runs [0, n_gen_items))
+  const int64_t n_gen = int64_t(P->items.size());
+  for (EstSub& sb : P->subs)
+    if (sb.tri >= 0) sb.item_begin += n_gen;
+  P->items.insert(P->items.end(), P->tri_items.begin(), P->tri_items.end());
   std::memset(H, 0, sizeof(*H));
   H->magic = kEstPlanMagic;
-  H->version = 1;
+  H->version = kEstPlanVersion;
   H->d = d;
   H->w = w;
   H->max_slots = P->max_slots;
   H->max_in = P->max_in;
   H->threads = shape.threads;
   const int64_t cap = int64_t(sm_count()) * shape.ctas_per_sm;
-  H->grid = int32_t(std::max<int64_t>(1, std::min<int64_t>(int64_t(P->items.size()), cap)));
+  H->grid = int32_t(std::max<int64_t>(1, std::min<int64_t>(n_gen, cap)));
+  H->n_gen_items = n_gen;
+  H->n_tri = int64_t(P->tris.size());
+  H->tri_max_leaves = P->tri_max_leaves;
+  H->tri_nch = (w + kTriCols - 1) / kTriCols;
+  H->tri_row_bytes = H->n_tri ? tri_layout(w, P->tri_max_leaves).bytes : 0;
   H->n_sub = n_sub;
   H->n_ops = int64_t(P->ops.size());
   H->n_in = int64_t(P->ins.size());
@@ -212,6 +326,8 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
   off += align16(sizeof(EstIn) * P->ins.size());
   H->off_items = int64_t(off);
   off += align16(sizeof(EstItem) * P->items.size());
+  H->off_tri = int64_t(off);
+  off += align16(sizeof(TriSub) * P->tris.size());
   H->total_bytes = int64_t(off);
   H->max_suf = P->max_suf;
   H->max_rank = P->max_rank;
@@ -219,8 +335,7 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
   H->scratch_per_cta = int64_t(align16(sizeof(i128) * size_t(int64_t(P->max_slots) * w + int64_t(P->max_suf) * W1 +
                                                              int64_t(P->max_in) * W1) +
                                        sizeof(int32_t) * size_t(int64_t(P->max_rank) * w)));
-  H->ws_bytes = int64_t(align16(sizeof(i128) * P->items.size()) + align16(sizeof(int32_t) * P->items.size()) +
-                        size_t(H->scratch_per_cta) * size_t(H->grid));
+  H->ws_bytes = int64_t(est_ws_bytes(*H, H->grid, H->n_tri * d));
   return CMP_OK;
 }
 
@@ -293,6 +408,7 @@ cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, i
   if (!P.ops.empty()) std::memcpy(b + H.off_ops, P.ops.data(), sizeof(EstOp) * P.ops.size());
   if (!P.ins.empty()) std::memcpy(b + H.off_in, P.ins.data(), sizeof(EstIn) * P.ins.size());
   if (!P.items.empty()) std::memcpy(b + H.off_items, P.items.data(), sizeof(EstItem) * P.items.size());
+  if (!P.tris.empty()) std::memcpy(b + H.off_tri, P.tris.data(), sizeof(TriSub) * P.tris.size());
   return CMP_OK;
 }
 
@@ -301,32 +417,11 @@ cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_de
   if (!plan_host || !plan_dev) return CMP_EINVAL;
   EstPlanHdr H;
   std::memcpy(&H, plan_host, sizeof(H));
-  if (H.magic != kEstPlanMagic || H.version != 1) return CMP_EINVAL;
+  if (H.magic != kEstPlanMagic || H.version != kEstPlanVersion) return CMP_EINVAL;
   if (H.n_sub > 0 && !est_dev) return CMP_EINVAL;
   if (ws_bytes < size_t(H.ws_bytes) || (H.ws_bytes > 0 && !ws_dev)) return CMP_EWORKSPACE;
-  const unsigned char* pd = static_cast<const unsigned char*>(plan_dev);
-  unsigned char* ws = static_cast<unsigned char*>(ws_dev);
-  EstArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.subs = reinterpret_cast<const EstSub*>(pd + H.off_subs);
-  a.ops = reinterpret_cast<const EstOp*>(pd + H.off_ops);
-  a.inputs = reinterpret_cast<const EstIn*>(pd + H.off_in);
-  a.items = reinterpret_cast<const EstItem*>(pd + H.off_items);
-  a.partial = reinterpret_cast<i128*>(ws);
-  a.partial_ovf = reinterpret_cast<int32_t*>(ws + align16(sizeof(i128) * size_t(H.n_items)));
-  a.scratch = ws + align16(sizeof(i128) * size_t(H.n_items)) + align16(sizeof(int32_t) * size_t(H.n_items));
-  a.scratch_per_cta = H.scratch_per_cta;
-  a.n_items = H.n_items;
-  a.n_sub = H.n_sub;
-  a.d = H.d;
-  a.w = H.w;
-  a.max_slots = H.max_slots;
-  a.max_in = H.max_in;
-  a.max_suf = H.max_suf;
-  a.max_rank = H.max_rank;
-  a.grid = H.grid;
-  a.threads = H.threads;
-  a.status = status_dev;
+  const EstArgs a = est_args(H, static_cast<const unsigned char*>(plan_dev), static_cast<unsigned char*>(ws_dev),
+                             H.grid, H.n_tri * H.d, status_dev);
   return launch_estimate(a, est_dev, row_est_dev, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? CMP_OK
                                                                                                           : CMP_ECUDA;
 }

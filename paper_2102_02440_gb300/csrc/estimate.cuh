@@ -42,12 +42,53 @@ struct EstSub {
   int64_t item_begin;
   const int64_t* sv;  // single: that table's survivor count (device)
   int32_t cond;       // 1 if a non-tree edge is conditioned
-  int32_t pad;
+  int32_t tri;        // index of its TriSub (triangle evaluation), else -1
 };
 
 struct EstItem {
-  int32_t sub, row, c0, c1;  // conditioning values [c0, c1); trees use [0, 1)
+  int32_t sub, row, c0, c1;  // conditioning values [c0, c1); trees use [0, 1); triangle: columns [c0, c1)
 };
+
+// Triangle sub-plans: the only cycle is U-W-V with the conditioned edge U-V, and every
+// other table is a leaf joined to U, V or W.  Each node lists its edges (EstIn, ascending
+// edge id; kInCond = the conditioned edge, kInSlot = a triangle edge, kInLeaf = a leaf).
+struct TriNode {
+  int32_t in_begin, k;  // first EstIn, number of edges
+  int32_t ia, ib;       // U, V: edge to W, conditioned edge.  W: edge to U, edge to V
+};
+struct TriSub {
+  TriNode node[3];  // U, V, W
+  int32_t sub, pad;
+};
+constexpr int32_t kTriMaxW = 16384;   // queries and rows are sorted in shared memory
+constexpr int32_t kTriMaxLeaves = 16; // leaves per triangle node
+constexpr int32_t kTriCols = 256;     // columns per sweep item (one per thread)
+
+// Per triangle row (sub-plan, sketch row) scratch, in bytes, and its regions.
+struct TriLayout {
+  int64_t hdr, vec, sg, pre, rkx, rpre, cky, ccol, qs, qr, qpre, gr, gqb, bytes;
+};
+__host__ __device__ inline int64_t tri_al(int64_t x) { return (x + 255) & ~int64_t(255); }
+__host__ __device__ inline TriLayout tri_layout(int32_t w, int32_t max_leaves) {
+  const int64_t W1 = int64_t(w) + 1, nl = 3 * int64_t(max_leaves);
+  TriLayout L;
+  int64_t o = 0;
+  L.hdr = o;  o += tri_al(64);
+  L.vec = o;  o += tri_al(16 * 6 * int64_t(w));   // phiU psiU phiV psiV f g, bucket order
+  L.sg = o;   o += tri_al(8 * nl * W1);          // leaf suffix sums
+  L.pre = o;  o += tri_al(16 * nl * W1);         // leaf "attains the minimum" prefix sums
+  L.rkx = o;  o += tri_al(8 * int64_t(w));       // row keys, sorted within batches
+  L.rpre = o; o += tri_al(16 * 3 * W1);          // row prefix sums: phi*f, f, phi
+  L.cky = o;  o += tri_al(8 * int64_t(w));       // column keys
+  L.ccol = o; o += tri_al(16 * 2 * int64_t(w));  // column phi, g
+  L.qs = o;   o += tri_al(4 * int64_t(w));       // query clamp ranks on the column side, sorted
+  L.qr = o;   o += tri_al(4 * int64_t(w));       // query clamp ranks on the row side, sorted
+  L.qpre = o; o += tri_al(16 * 3 * W1);          // query prefix sums: psiR, psiC, psiR*psiC
+  L.gr = o;   o += tri_al(4 * (W1 + 1));         // distinct row-side ranks (group boundaries)
+  L.gqb = o;  o += tri_al(4 * (W1 + 1));         // first query of each group
+  L.bytes = o;
+  return L;
+}
 
 struct EstPlanHdr {
   uint64_t magic;
@@ -56,8 +97,13 @@ struct EstPlanHdr {
   int64_t off_subs, off_ops, off_in, off_items, total_bytes;
   int64_t scratch_per_cta;  // bytes
   int64_t ws_bytes;
+  int64_t n_gen_items;      // items [0, n_gen_items) run the generic kernel
+  int64_t n_tri, off_tri;   // triangle sub-plans
+  int64_t tri_row_bytes;
+  int32_t tri_max_leaves, tri_nch;  // leaves per node (scratch layout), sweep items per row
 };
 constexpr uint64_t kEstPlanMagic = 0x434d504553544d54ull;  // "CMPESTMT"
+constexpr int32_t kEstPlanVersion = 2;
 
 struct EstArgs {
   const EstSub* subs;
@@ -71,6 +117,12 @@ struct EstArgs {
   int64_t n_items, n_sub;
   int32_t d, w, max_slots, max_in, grid, threads, max_suf, max_rank;
   int32_t* status;
+  int64_t n_gen_items;
+  const TriSub* tri;
+  int64_t n_tri;
+  unsigned char* tri_scratch;  // tri_slots rows of tri_row_bytes
+  int64_t tri_row_bytes, tri_slots;
+  int32_t tri_max_leaves, tri_nch;
 };
 
 // Round-to-nearest-even of (neg ? -1 : 1) * (top * 2^128 + mag) to binary64, from the
@@ -124,7 +176,49 @@ cudaError_t launch_presort_large(const int32_t* C, int64_t n_rows, int32_t w, ui
                                  void* ws, int64_t rows_per_pass, cudaStream_t st);
 int64_t presort_padded(int32_t w);
 constexpr int32_t kPresortSmemMaxW = 16384;
+// Workspace of an encoded plan: per-item partial sums and flags, `grid` per-CTA scratch
+// areas of the generic kernel, then `tri_slots` triangle rows.
+inline size_t est_fixed_bytes(const EstPlanHdr& H) {
+  return align16(sizeof(i128) * size_t(H.n_items)) + align16(sizeof(int32_t) * size_t(H.n_items));
+}
+inline size_t est_ws_bytes(const EstPlanHdr& H, int64_t grid, int64_t tri_slots) {
+  return est_fixed_bytes(H) + size_t(H.scratch_per_cta) * size_t(grid) + size_t(H.tri_row_bytes) * size_t(tri_slots);
+}
+inline EstArgs est_args(const EstPlanHdr& H, const unsigned char* pd, unsigned char* ws, int32_t grid,
+                        int64_t tri_slots, int32_t* status) {
+  EstArgs a;
+  a.subs = reinterpret_cast<const EstSub*>(pd + H.off_subs);
+  a.ops = reinterpret_cast<const EstOp*>(pd + H.off_ops);
+  a.inputs = reinterpret_cast<const EstIn*>(pd + H.off_in);
+  a.items = reinterpret_cast<const EstItem*>(pd + H.off_items);
+  a.partial = reinterpret_cast<i128*>(ws);
+  a.partial_ovf = reinterpret_cast<int32_t*>(ws + align16(sizeof(i128) * size_t(H.n_items)));
+  a.scratch = ws + est_fixed_bytes(H);
+  a.scratch_per_cta = H.scratch_per_cta;
+  a.n_items = H.n_items;
+  a.n_sub = H.n_sub;
+  a.d = H.d;
+  a.w = H.w;
+  a.max_slots = H.max_slots;
+  a.max_in = H.max_in;
+  a.grid = grid;
+  a.threads = H.threads;
+  a.max_suf = H.max_suf;
+  a.max_rank = H.max_rank;
+  a.status = status;
+  a.n_gen_items = H.n_gen_items;
+  a.tri = reinterpret_cast<const TriSub*>(pd + H.off_tri);
+  a.n_tri = H.n_tri;
+  a.tri_scratch = ws + est_fixed_bytes(H) + size_t(H.scratch_per_cta) * size_t(grid);
+  a.tri_row_bytes = H.tri_row_bytes;
+  a.tri_slots = tri_slots;
+  a.tri_max_leaves = H.tri_max_leaves;
+  a.tri_nch = H.tri_nch;
+  return a;
+}
+
 cudaError_t launch_estimate(const EstArgs& a, double* est, int64_t* row_est, cudaStream_t st);
+cudaError_t launch_estimate_tri(const EstArgs& a, cudaStream_t st);
 cudaError_t launch_cross_ranks(const uint32_t* abs, const int32_t* perm, int32_t k, int32_t d, int32_t w,
                                const int32_t* edge_id, int32_t* ranks, cudaStream_t st);
 

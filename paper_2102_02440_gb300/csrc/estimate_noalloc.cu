@@ -3,6 +3,7 @@
 // not allocate device memory themselves.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -42,40 +43,23 @@ extern "C" cmp_status cmp_estimate_noalloc(const void* plan_host, const void* pl
   if (!plan_host || !plan_dev) return CMP_EINVAL;
   EstPlanHdr H;
   std::memcpy(&H, plan_host, sizeof(H));
-  if (H.magic != kEstPlanMagic || H.version != 1) return CMP_EINVAL;
+  if (H.magic != kEstPlanMagic || H.version != kEstPlanVersion) return CMP_EINVAL;
   if (H.n_sub > 0 && !est_dev) return CMP_EINVAL;
-  // per-item partial sums, then as many per-CTA scratch areas as fit (at least one)
-  const size_t fixed = align16(sizeof(i128) * size_t(H.n_items)) + align16(sizeof(int32_t) * size_t(H.n_items));
-  const size_t per_cta = size_t(H.scratch_per_cta);
-  if (fixed + per_cta > size_t(CMP_NOALLOC_WS_BYTES)) return CMP_EWORKSPACE;
-  size_t fit = per_cta ? (size_t(CMP_NOALLOC_WS_BYTES) - fixed) / per_cta : size_t(H.grid);
-  const int32_t grid = int32_t(fit < size_t(H.grid) ? fit : size_t(H.grid));
+  // per-item partial sums, then as many generic per-CTA scratch areas and triangle rows
+  // as fit (at least one of each that the plan uses); triangle rows beyond that run in waves
+  const size_t cap = size_t(CMP_NOALLOC_WS_BYTES), fixed = est_fixed_bytes(H);
+  const size_t per_cta = H.n_gen_items > 0 ? size_t(H.scratch_per_cta) : 0;
+  const size_t per_tri = H.n_tri > 0 ? size_t(H.tri_row_bytes) : 0;
+  if (fixed + per_cta + per_tri > cap) return CMP_EWORKSPACE;
+  int64_t grid = H.grid;
+  if (per_cta) grid = std::min<int64_t>(grid, int64_t((cap - fixed - per_tri) / per_cta));
+  int64_t slots = 0;
+  if (per_tri) slots = std::min<int64_t>(H.n_tri * H.d, int64_t((cap - fixed - per_cta * size_t(grid)) / per_tri));
   void* ws_v = nullptr;
   const cmp_status st = workspace_address(&ws_v);
   if (st != CMP_OK) return st;
-  unsigned char* ws = static_cast<unsigned char*>(ws_v);
-  const unsigned char* pd = static_cast<const unsigned char*>(plan_dev);
-  EstArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.subs = reinterpret_cast<const EstSub*>(pd + H.off_subs);
-  a.ops = reinterpret_cast<const EstOp*>(pd + H.off_ops);
-  a.inputs = reinterpret_cast<const EstIn*>(pd + H.off_in);
-  a.items = reinterpret_cast<const EstItem*>(pd + H.off_items);
-  a.partial = reinterpret_cast<i128*>(ws);
-  a.partial_ovf = reinterpret_cast<int32_t*>(ws + align16(sizeof(i128) * size_t(H.n_items)));
-  a.scratch = ws + fixed;
-  a.scratch_per_cta = H.scratch_per_cta;
-  a.n_items = H.n_items;
-  a.n_sub = H.n_sub;
-  a.d = H.d;
-  a.w = H.w;
-  a.max_slots = H.max_slots;
-  a.max_in = H.max_in;
-  a.max_suf = H.max_suf;
-  a.max_rank = H.max_rank;
-  a.grid = grid > 0 ? grid : 1;
-  a.threads = H.threads;
-  a.status = status_dev;
+  const EstArgs a = est_args(H, static_cast<const unsigned char*>(plan_dev), static_cast<unsigned char*>(ws_v),
+                             int32_t(grid > 0 ? grid : 1), slots, status_dev);
   return launch_estimate(a, est_dev, row_est_dev, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? CMP_OK
                                                                                                           : CMP_ECUDA;
 }

@@ -1,0 +1,506 @@
+// Triangle sub-plans: the conditioned sum of a sub-plan whose only cycle is a triangle,
+// evaluated as batched dominance sums instead of one tree contraction per conditioning
+// value (the estimate itself is the contraction of the sketch-merging estimate, Sec. 4.2
+// merge equation iterated over a table's joins, Sec. 3.2 per-row sums and median).
+//
+// Setting.  Tables U, V, W form the cycle; e* = U-V is the conditioned edge (bucket c),
+// eU = U-W (bucket k) and eV = V-W (bucket i).  Every other table is a leaf joined to one
+// of the three.  "x beats y" is the merge order on (|value|, edge id): smaller magnitude
+// first, the lower edge id first on ties.  It is a total order, so it is transitive.
+//
+//  * Fix c.  U's message to W over eU is then a clamp.  At buckets k whose U-sketch value
+//    on eU beats s_U*(c) it equals phiU[k], U's message with e* left out.  At the other
+//    buckets it is the scalar psiU(c), U's message along e* with eU left out, read at c.
+//    (The losing fixed input never attains the minimum, and a leaf value that beats the
+//    winner beats the loser too.)  The first kind is a prefix of U's presorted order of its
+//    eU sketch, of length rU(c).  The same holds for V.
+//  * For fixed (k, i), W's merged value summed over W's leaves is f[k] (W's message along eU
+//    with eV left out) when W's eU value at k beats its eV value at i, and g[i] otherwise.
+//
+// Let u and v be the positions of k and i in U's and V's presorted orders.  Then
+//   E_row = sum_c sum_{u,v} mU_c(u) mV_c(v) Cell(u,v),   Cell(u,v) = sel(u,v) ? f_u : g_v.
+// For one c, sum_u mU_c(u) Cell(u,v) = A_v(rU) + psiU(c) (Tot_v - B_v(rU)).  Here
+//   A_v(r) = sum_{u<r} phiU_u Cell(u,v),   B_v(r) = sum_{u<r} Cell(u,v),   Tot_v = B_v(w).
+// Conditioning values with equal rU form a group.  A group adds A_v H1_v - B_v H2_v to
+// column v, and Tot_v H2_v after all rows, where
+//   H1_v = sum_c mV_c(v),   H2_v = sum_c psiU(c) mV_c(v),
+//   mV_c(v) = phiV_v if v < rV(c), else psiV(c).
+// So H1 and H2 are prefix sums over the group's values sorted by rV.
+//
+// Rows between consecutive group ranks form a batch.  Sorted by W's eU key within the batch,
+// the batch's share of A_v and B_v is a prefix sum read at one binary-searched position.
+// The cost per sketch row is O(w G log w) for G distinct row-side ranks, against O(w^2)
+// for one contraction per c.  Per sketch row, the row side is whichever of U, V has
+// fewer distinct magnitudes in its conditioned sketch; G is at most that count.
+//
+// Leaves at a node.  With the fixed input a at value x, the node's message is
+//   x * prod_l G_l(x) + sum_l PRE_l[q_l(x)].
+//   - G_l(x) is the sum of leaf l's message over the buckets that x beats: a suffix of l's
+//     sorted order starting at q_l(x), the number of l's values that beat x.
+//   - PRE_l holds prefix sums of the "leaf l attains the minimum" terms: value times leaf
+//     message times the other leaves' G at that value.
+// All arithmetic is exact int128 with overflow checks; an overflow makes the row
+// estimate NaN with CMP_EOVERFLOW, as on the generic path.
+#include <cuda_runtime.h>
+
+#include "est_arith.cuh"
+
+namespace cmpk {
+namespace {
+
+__device__ __forceinline__ bool sub_ovf(i128 a, i128 b, i128* r) {
+  const i128 s = i128(u128(a) - u128(b));
+  *r = s;
+  return ((a ^ b) & (a ^ s)) < 0;
+}
+
+__device__ __forceinline__ uint32_t mag32(int32_t v) { return v < 0 ? uint32_t(-int64_t(v)) : uint32_t(v); }
+
+// Regions of one triangle row's scratch (see tri_layout).
+struct TriPtrs {
+  int32_t* hdr;  // [0] groups G, [1] queries, [2] overflow in the preparation
+  i128* vec;     // [6][w]: phiU psiU phiV psiV f g, in bucket order
+  int64_t* sg;   // [3 * max_leaves][w+1]
+  i128* pre;     // [3 * max_leaves][w+1]
+  uint64_t* rkx;
+  i128* rpre;  // [3][w+1]: phi*f, f, phi of the row side, exclusive prefix sums
+  uint64_t* cky;
+  i128* ccol;  // [2][w]: phi, g of the column side
+  int32_t* qs;
+  int32_t* qr;
+  i128* qpre;  // [3][w+1]: psiR, psiC, psiR*psiC, exclusive prefix sums
+  int32_t* gr;
+  int32_t* gqb;
+};
+
+__device__ TriPtrs tri_ptrs(unsigned char* base, int w, int max_leaves) {
+  const TriLayout L = tri_layout(w, max_leaves);
+  TriPtrs p;
+  p.hdr = reinterpret_cast<int32_t*>(base + L.hdr);
+  p.vec = reinterpret_cast<i128*>(base + L.vec);
+  p.sg = reinterpret_cast<int64_t*>(base + L.sg);
+  p.pre = reinterpret_cast<i128*>(base + L.pre);
+  p.rkx = reinterpret_cast<uint64_t*>(base + L.rkx);
+  p.rpre = reinterpret_cast<i128*>(base + L.rpre);
+  p.cky = reinterpret_cast<uint64_t*>(base + L.cky);
+  p.ccol = reinterpret_cast<i128*>(base + L.ccol);
+  p.qs = reinterpret_cast<int32_t*>(base + L.qs);
+  p.qr = reinterpret_cast<int32_t*>(base + L.qr);
+  p.qpre = reinterpret_cast<i128*>(base + L.qpre);
+  p.gr = reinterpret_cast<int32_t*>(base + L.gr);
+  p.gqb = reinterpret_cast<int32_t*>(base + L.gqb);
+  return p;
+}
+
+__device__ void bitonic_sort(unsigned long long* key, int n2) {
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = key[i], b = key[ixj];
+          if ((a > b) == ((i & k) == 0)) {
+            key[i] = b;
+            key[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// Message of triangle node n with the fixed input a (every input but ia, ib is a leaf),
+// for every bucket of a's edge.
+__device__ void node_msg(const EstArgs& A, const TriNode& nd, int n, int a, const TriPtrs& P, int64_t ro, i128* out,
+                         int32_t* flag) {
+  const int w = A.w;
+  const int64_t W1 = int64_t(w) + 1;
+  const EstIn* in = A.inputs + nd.in_begin;
+  const int32_t* sa = in[a].s + ro;
+  bool o = false;
+  for (int j = threadIdx.x; j < w; j += blockDim.x) {
+    const int32_t x = __ldg(sa + j);
+    const uint32_t tau = mag32(x);
+    i128 v = i128(x), acc = 0;
+    for (int l = 0, li = 0; l < nd.k; l++) {
+      if (l == nd.ia || l == nd.ib) continue;
+      // leaf values that beat x: |y| < |x|, or |y| == |x| with l before a
+      const int q = rank_of(in[l].abs + ro, w, tau, l < a);
+      const int64_t slot = (int64_t(n) * A.tri_max_leaves + li) * W1;
+      if (v != 0) o |= mul_ovf_64(v, P.sg[slot + q], &v);
+      o |= add_ovf(acc, P.pre[slot + q], &acc);
+      li++;
+    }
+    o |= add_ovf(v, acc, &v);
+    out[j] = v;
+  }
+  if (o) atomicOr(flag, 1);
+}
+
+// Exclusive scan of the 0/1 flags at[0..n) (thread-contiguous ranges).  Returns this
+// thread's first output index and writes the total to *total.
+__device__ int block_count_base(const int32_t* at, int n, int32_t* sh_w, int32_t* total) {
+  const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+  const int per = (n + T - 1) / T;
+  const int b = min(n, tid * per), e = min(n, b + per);
+  int cnt = 0;
+  for (int q = b; q < e; q++) cnt += at[q] != 0;
+  int incl = cnt;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int o = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += o;
+  }
+  if (lane == 31) sh_w[warp] = incl;
+  __syncthreads();
+  if (tid == 0) {
+    int t = 0;
+    for (int i = 0; i < nw; i++) {
+      const int v = sh_w[i];
+      sh_w[i] = t;
+      t += v;
+    }
+    *total = t;
+  }
+  __syncthreads();
+  const int base = sh_w[warp] + incl - cnt;
+  __syncthreads();
+  return base;
+}
+
+}  // namespace
+
+// One CTA per triangle row (sub-plan, sketch row) of the wave starting at tr0.
+__global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstArgs A, int64_t tr0) {
+  extern __shared__ unsigned long long key[];
+  __shared__ i128 sh_i128[33];
+  __shared__ int32_t sh_flag[1];
+  __shared__ int32_t sh_cnt[4];
+  __shared__ int32_t sh_w[32];
+  BlockScratch bs{sh_i128, sh_flag};
+  const int w = A.w, d = A.d, tid = threadIdx.x, T = blockDim.x;
+  if (w > kTriMaxW || T != 1024) {  // the planner never sends these; sorts and group starts assume them
+    if (tid == 0) set_status(A.status, CMP_EINVAL);
+    return;
+  }
+  const int64_t W1 = int64_t(w) + 1;
+  const int64_t tr = tr0 + blockIdx.x;
+  const TriSub ts = A.tri[tr / d];
+  const int64_t ro = (tr % d) * int64_t(w);
+  const TriPtrs P = tri_ptrs(A.tri_scratch + int64_t(blockIdx.x) * A.tri_row_bytes, w, A.tri_max_leaves);
+  const EstIn* inputs = A.inputs;
+  int wp2 = 1;
+  while (wp2 < w) wp2 <<= 1;
+  if (tid == 0) {
+    sh_flag[0] = 0;
+    sh_cnt[0] = sh_cnt[1] = sh_cnt[2] = sh_cnt[3] = 0;
+  }
+  __syncthreads();
+
+  // ---- leaves: suffix sums of each leaf's message in its sketch's sorted order
+  for (int n = 0; n < 3; n++) {
+    const TriNode nd = ts.node[n];
+    for (int l = 0, li = 0; l < nd.k; l++) {
+      if (l == nd.ia || l == nd.ib) continue;
+      const EstIn& x = inputs[nd.in_begin + l];
+      int64_t* sg = P.sg + (int64_t(n) * A.tri_max_leaves + li) * W1;
+      const int32_t* perm = x.perm + ro;
+      for (int r = tid; r < w; r += T) sg[r] = __ldg(x.msk + ro + __ldg(perm + r));
+      if (tid == 0) sg[w] = 0;
+      __syncthreads();
+      block_scan(sg, w, /*reverse=*/true, bs);
+      li++;
+    }
+  }
+  // ---- leaves: prefix sums of the terms in which leaf l attains the minimum
+  for (int n = 0; n < 3; n++) {
+    const TriNode nd = ts.node[n];
+    for (int l = 0, li = 0; l < nd.k; l++) {
+      if (l == nd.ia || l == nd.ib) continue;
+      const EstIn& x = inputs[nd.in_begin + l];
+      i128* pre = P.pre + (int64_t(n) * A.tri_max_leaves + li) * W1;
+      const int32_t* perm = x.perm + ro;
+      bool o = false;
+      for (int r = tid; r < w; r += T) {
+        const int j = __ldg(perm + r);
+        const int32_t y = __ldg(x.s + ro + j);
+        i128 v = i128(int64_t(y) * int64_t(__ldg(x.msk + ro + j)));  // |int32 * int32| < 2^62
+        const uint32_t tau = mag32(y);
+        for (int l2 = 0, li2 = 0; l2 < nd.k && v != 0; l2++) {
+          if (l2 == nd.ia || l2 == nd.ib) continue;
+          if (l2 != l) {
+            const int q = rank_of(inputs[nd.in_begin + l2].abs + ro, w, tau, l2 < l);
+            o |= mul_ovf_64(v, P.sg[(int64_t(n) * A.tri_max_leaves + li2) * W1 + q], &v);
+          }
+          li2++;
+        }
+        pre[r + 1] = v;
+      }
+      if (o) atomicOr(sh_flag, 1);
+      if (tid == 0) pre[0] = 0;
+      __syncthreads();
+      block_scan(pre + 1, w, /*reverse=*/false, bs);
+      li++;
+    }
+  }
+  // ---- the six node messages, in bucket order
+  for (int n = 0; n < 3; n++) {
+    const TriNode nd = ts.node[n];
+    node_msg(A, nd, n, nd.ia, P, ro, P.vec + int64_t(2 * n) * w, sh_flag);
+    node_msg(A, nd, n, nd.ib, P, ro, P.vec + int64_t(2 * n + 1) * w, sh_flag);
+  }
+  // ---- row side: U or V, whichever conditioned sketch has fewer distinct magnitudes
+  for (int n = 0; n < 2; n++) {
+    const uint32_t* ab = inputs[ts.node[n].in_begin + ts.node[n].ib].abs + ro;
+    int cnt = 0;
+    for (int r = tid + 1; r < w; r += T) cnt += __ldg(ab + r) != __ldg(ab + r - 1);
+    if (cnt) atomicAdd(&sh_cnt[n], cnt);
+  }
+  __syncthreads();  // also orders the node messages before their reads below
+  const bool swap = sh_cnt[1] < sh_cnt[0];
+  const TriNode NR = ts.node[swap ? 1 : 0], NC = ts.node[swap ? 0 : 1], NW = ts.node[2];
+  const int wR = swap ? NW.ib : NW.ia, wC = swap ? NW.ia : NW.ib;  // W's edges to R and C
+  const i128* phiR = P.vec + int64_t(swap ? 2 : 0) * w;
+  const i128* psiR = P.vec + int64_t(swap ? 3 : 1) * w;
+  const i128* phiC = P.vec + int64_t(swap ? 0 : 2) * w;
+  const i128* psiC = P.vec + int64_t(swap ? 1 : 3) * w;
+  const i128* fR = P.vec + int64_t(swap ? 5 : 4) * w;
+  const i128* gC = P.vec + int64_t(swap ? 4 : 5) * w;
+  const bool tieR = NR.ia < NR.ib, tieC = NC.ia < NC.ib, tieW = wR < wC;
+  const EstIn& Rpar = inputs[NR.in_begin + NR.ia];
+  const EstIn& Rcond = inputs[NR.in_begin + NR.ib];
+  const EstIn& Cpar = inputs[NC.in_begin + NC.ia];
+  const EstIn& Ccond = inputs[NC.in_begin + NC.ib];
+  const EstIn& Wr = inputs[NW.in_begin + wR];
+  const EstIn& Wc = inputs[NW.in_begin + wC];
+
+  // ---- queries: conditioning values with both conditioned sketch values nonzero (a zero
+  // makes every merged entry at c through that table 0), sorted by (rR, rC, c)
+  {
+    int cnt = 0;
+    for (int c = tid; c < wp2; c += T) {
+      unsigned long long kk = ~0ull;
+      if (c < w) {
+        const int32_t sr = __ldg(Rcond.s + ro + c), sc = __ldg(Ccond.s + ro + c);
+        if (sr != 0 && sc != 0) {
+          // number of parent-sketch values that beat the conditioned value
+          const int r = rank_of(Rpar.abs + ro, w, mag32(sr), tieR);
+          const int s = rank_of(Cpar.abs + ro, w, mag32(sc), tieC);
+          kk = (static_cast<unsigned long long>(r) << 42) | (static_cast<unsigned long long>(s) << 21) |
+               static_cast<unsigned long long>(c);
+          cnt++;
+        }
+      }
+      key[c] = kk;
+    }
+    if (cnt) atomicAdd(&sh_cnt[2], cnt);
+  }
+  __syncthreads();
+  bitonic_sort(key, wp2);
+  const int nq = sh_cnt[2];
+  {
+    bool o = false;
+    for (int q = tid; q < nq; q += T) {
+      const unsigned long long kk = key[q];
+      const int c = int(kk & 0x1FFFFFull);
+      P.qs[q] = int((kk >> 21) & 0x1FFFFFull);
+      P.qr[q] = int(kk >> 42);
+      const i128 pr = psiR[c], pc = psiC[c];
+      i128 prc;
+      o |= mul_ovf(pr, pc, &prc);
+      P.qpre[q + 1] = pr;
+      P.qpre[W1 + q + 1] = pc;
+      P.qpre[2 * W1 + q + 1] = prc;
+    }
+    if (o) atomicOr(sh_flag, 1);
+    if (tid == 0) P.qpre[0] = P.qpre[W1] = P.qpre[2 * W1] = 0;
+  }
+  __syncthreads();
+  for (int m = 0; m < 3; m++) block_scan(P.qpre + m * W1 + 1, nq, /*reverse=*/false, bs);
+  // groups: first query of each distinct row-side rank (flags staged in gqb)
+  for (int q = tid; q < nq; q += T) P.gqb[q] = (q == 0 || P.qr[q] != P.qr[q - 1]) ? 1 : 0;
+  __syncthreads();
+  {
+    // launched with 1024 threads: at most kTriMaxW / 1024 queries per thread
+    const int per = (nq + T - 1) / T;
+    const int b = min(nq, tid * per), e = min(nq, b + per);
+    int starts[kTriMaxW / 1024];
+    int ns = 0;
+    for (int q = b; q < e; q++)
+      if (P.gqb[q]) starts[ns++] = q;
+    const int base = block_count_base(P.gqb, nq, sh_w, &sh_cnt[3]);  // every flag read before it returns
+    for (int i = 0; i < ns; i++) {
+      P.gr[base + i] = P.qr[starts[i]];
+      P.gqb[base + i] = starts[i];
+    }
+  }
+  __syncthreads();
+  const int G = sh_cnt[3];
+  if (tid == 0) P.gqb[G] = nq;
+
+  // ---- rows of the row side: batch (number of group ranks <= u), then W's key, then u
+  for (int u = tid; u < wp2; u += T) {
+    unsigned long long kk = ~0ull;
+    if (u < w) {
+      const int k = __ldg(Rpar.perm + ro + u);
+      const uint64_t kx = 2ull * mag32(__ldg(Wr.s + ro + k)) + (tieW ? 0ull : 1ull);
+      int lo = 0, hi = G;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (P.gr[mid] <= u) lo = mid + 1;
+        else hi = mid;
+      }
+      kk = (static_cast<unsigned long long>(lo) << 48) | (kx << 14) | static_cast<unsigned long long>(u);
+    }
+    key[u] = kk;
+  }
+  __syncthreads();
+  bitonic_sort(key, wp2);
+  {
+    bool o = false;
+    for (int q = tid; q < w; q += T) {
+      const unsigned long long kk = key[q];
+      const int u = int(kk & 0x3FFFull);
+      const int k = __ldg(Rpar.perm + ro + u);
+      P.rkx[q] = (kk >> 14) & ((1ull << 33) - 1);
+      const i128 phi = phiR[k], f = fR[k];
+      i128 pf;
+      o |= mul_ovf(phi, f, &pf);
+      P.rpre[q + 1] = pf;
+      P.rpre[W1 + q + 1] = f;
+      P.rpre[2 * W1 + q + 1] = phi;
+    }
+    if (o) atomicOr(sh_flag, 1);
+    if (tid == 0) P.rpre[0] = P.rpre[W1] = P.rpre[2 * W1] = 0;
+  }
+  __syncthreads();
+  for (int m = 0; m < 3; m++) block_scan(P.rpre + m * W1 + 1, w, /*reverse=*/false, bs);
+  // ---- columns of the column side, in its presorted order
+  for (int v = tid; v < w; v += T) {
+    const int i = __ldg(Cpar.perm + ro + v);
+    P.cky[v] = 2ull * mag32(__ldg(Wc.s + ro + i)) + (tieW ? 1ull : 0ull);
+    P.ccol[v] = phiC[i];
+    P.ccol[w + v] = gC[i];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    P.hdr[0] = G;
+    P.hdr[1] = nq;
+    P.hdr[2] = sh_flag[0] != 0;
+  }
+}
+
+// One thread per column; kTriCols columns per CTA, tri_nch CTAs per triangle row.
+__global__ void __launch_bounds__(kTriCols) k_tri_sweep(const __grid_constant__ EstArgs A, int64_t tr0) {
+  __shared__ i128 sh_i128[33];
+  __shared__ int32_t sh_flag[1];
+  BlockScratch bs{sh_i128, sh_flag};
+  const int w = A.w, tid = threadIdx.x;
+  const int64_t W1 = int64_t(w) + 1;
+  const int64_t slot = blockIdx.x / A.tri_nch;
+  const int ch = int(blockIdx.x % A.tri_nch);
+  const int64_t it = A.n_gen_items + (tr0 + slot) * A.tri_nch + ch;
+  const TriPtrs P = tri_ptrs(A.tri_scratch + slot * A.tri_row_bytes, w, A.tri_max_leaves);
+  if (tid == 0) sh_flag[0] = 0;
+  __syncthreads();
+  const int G = P.hdr[0];
+  const int prep_ovf = P.hdr[2];
+  const int v = ch * kTriCols + tid;
+  i128 E = 0;
+  bool o = false;
+  if (v < w) {
+    const uint64_t ky = P.cky[v];
+    const i128 phi = P.ccol[v], g = P.ccol[w + v];
+    const i128* prePF = P.rpre;
+    const i128* preF = P.rpre + W1;
+    const i128* prePhi = P.rpre + 2 * W1;
+    const i128* qR = P.qpre;
+    const i128* qC = P.qpre + W1;
+    const i128* qRC = P.qpre + 2 * W1;
+    i128 SA = 0, SB = 0, SC = 0, H2t = 0, t1, t2;
+    int SD = 0, lo = 0;
+    for (int b = 0; b <= G; b++) {
+      const int hi = b < G ? P.gr[b] : w;
+      // rows of the batch whose W key is below the column's: Cell = f_u there
+      int a0 = lo, a1 = hi;
+      while (a0 < a1) {
+        const int mid = (a0 + a1) >> 1;
+        if (P.rkx[mid] < ky) a0 = mid + 1;
+        else a1 = mid;
+      }
+      if (a0 > lo) {
+        o |= sub_ovf(prePF[a0], prePF[lo], &t1);
+        o |= add_ovf(SA, t1, &SA);
+        o |= sub_ovf(preF[a0], preF[lo], &t1);
+        o |= add_ovf(SB, t1, &SB);
+        o |= sub_ovf(prePhi[a0], prePhi[lo], &t1);
+        o |= add_ovf(SC, t1, &SC);
+        SD += a0 - lo;
+      }
+      if (b < G) {
+        // group b: its conditioning values have row-side rank r = hi
+        const int qb = P.gqb[b], qe = P.gqb[b + 1];
+        int c0 = qb, c1 = qe;  // first value whose column-side rank exceeds v
+        while (c0 < c1) {
+          const int mid = (c0 + c1) >> 1;
+          if (P.qs[mid] <= v) c0 = mid + 1;
+          else c1 = mid;
+        }
+        i128 Av, Bv, H1, H2;
+        // A = SA + g (sum_{u<r} phi_u - SC),  B = SB + g (r - SD)
+        o |= sub_ovf(prePhi[hi], SC, &t1);
+        o |= mul_ovf(g, t1, &t1);
+        o |= add_ovf(SA, t1, &Av);
+        o |= mul_ovf_64(g, int64_t(hi - SD), &t1);
+        o |= add_ovf(SB, t1, &Bv);
+        // H1 = phi * #{rC > v} + sum_{rC <= v} psiC,  H2 = phi * sum_{rC > v} psiR + sum_{rC <= v} psiR psiC
+        o |= mul_ovf_64(phi, int64_t(qe - c0), &H1);
+        o |= sub_ovf(qC[c0], qC[qb], &t1);
+        o |= add_ovf(H1, t1, &H1);
+        o |= sub_ovf(qR[qe], qR[c0], &t1);
+        o |= mul_ovf(phi, t1, &H2);
+        o |= sub_ovf(qRC[c0], qRC[qb], &t1);
+        o |= add_ovf(H2, t1, &H2);
+        o |= mul_ovf(Av, H1, &t1);
+        o |= mul_ovf(Bv, H2, &t2);
+        o |= sub_ovf(t1, t2, &t1);
+        o |= add_ovf(E, t1, &E);
+        o |= add_ovf(H2t, H2, &H2t);
+      }
+      lo = hi;
+    }
+    // Tot = SB + g (w - SD) after every row
+    o |= mul_ovf_64(g, int64_t(w - SD), &t1);
+    o |= add_ovf(SB, t1, &t1);
+    o |= mul_ovf(t1, H2t, &t1);
+    o |= add_ovf(E, t1, &E);
+  }
+  if (o) atomicOr(sh_flag, 1);
+  __syncthreads();
+  bool o2 = false;
+  const i128 sum = block_sum(E, &o2, bs);
+  if (tid == 0) {
+    A.partial[it] = sum;
+    A.partial_ovf[it] = (o2 || prep_ovf) ? 1 : 0;
+  }
+}
+
+cudaError_t launch_estimate_tri(const EstArgs& a, cudaStream_t st) {
+  if (a.n_tri <= 0 || a.tri_slots <= 0) return cudaSuccess;
+  const int64_t rows = a.n_tri * a.d;
+  int wp2 = 1;
+  while (wp2 < a.w) wp2 <<= 1;
+  const int smem = int(sizeof(unsigned long long)) * wp2;
+  cudaError_t e = cudaFuncSetAttribute(k_tri_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  for (int64_t r0 = 0; r0 < rows; r0 += a.tri_slots) {
+    const int64_t n = rows - r0 < a.tri_slots ? rows - r0 : a.tri_slots;
+    k_tri_prep<<<unsigned(n), 1024, smem, st>>>(a, r0);
+    k_tri_sweep<<<unsigned(n * a.tri_nch), kTriCols, 0, st>>>(a, r0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace cmpk

@@ -158,6 +158,30 @@ def test_estimate_plan_host_logic(K):
     assert K.lib().cmp_estimate(junk.ctypes.data, 0x10, 0x10, 1 << 20, 0x10, None, None, None) == K.CMP_EINVAL
 
 
+def test_estimate_plan_triangle_path_host_logic(K):
+    """Sub-plans whose only cycle is a triangle (other tables leaves of it) are planned on
+    the triangle path, which changes the workspace; trees, longer cycles and rows wider
+    than 16384 are not; CMP_EST_GENERIC_ONLY turns it off; other flag bits are rejected."""
+    g = _graph(K, [0, 1, 0, 0, 1, 3], [1, 2, 2, 3, 4, 5], 6)   # triangle 0-1-2, leaves 3, 4; 5 hangs off 3
+    gen = K.cmp_estimate_cfg.make(flags=K.CMP_EST_GENERIC_ONLY)
+
+    def ws(mask, w=4096, cfg=None):
+        return K.cmp_estimate_plan_bytes([g], 11, w, [0], [mask], cfg)[1]
+
+    for m in (0b000111, 0b001111, 0b011111):          # triangle plus leaves
+        assert ws(m) != ws(m, cfg=gen)
+    for m in (0b000011, 0b011011, 0b111011):          # trees
+        assert ws(m) == ws(m, cfg=gen)
+    assert ws(0b111111) == ws(0b111111, cfg=gen)      # table 5 is not a leaf of the triangle
+    assert ws(0b000111, w=16385) == ws(0b000111, w=16385, cfg=gen)
+    c4 = _graph(K, [0, 1, 2, 3], [1, 2, 3, 0], 4)
+    assert (K.cmp_estimate_plan_bytes([c4], 5, 64, [0], [0b1111])[1] ==
+            K.cmp_estimate_plan_bytes([c4], 5, 64, [0], [0b1111], gen)[1])
+    with pytest.raises(K.CompassError) as ei:
+        K.cmp_estimate_plan_bytes([g], 11, 64, [0], [0b111], K.cmp_estimate_cfg.make(flags=2))
+    assert ei.value.status == K.CMP_EINVAL
+
+
 def test_presort_rejections(K):
     assert K.lib().cmp_presort(0x10, 4, 0, 0x10, 0x10, None, 0, None) == K.CMP_EINVAL
     assert K.lib().cmp_presort(0x10, 4, 1 << 15, 0x10, 0x10, None, 0, None) == K.CMP_EWORKSPACE
