@@ -32,8 +32,11 @@ import numpy as np  # noqa: E402
 METRIC = "sketched tuples/s"
 UNIT = "tuples/s"
 INT_ISSUE_PEAK = 152 * 4 * 32 * 2.070e9   # 32-bit integer instructions/s: one warp instruction per SMSP per clock
-CW_INSTR = 60                            # 32-bit instructions per CW-61 bucket + sign evaluation
-OP128_INSTR = 8                          # 32-bit instructions per exact 128-bit multiply or add
+# Algorithmic cost of one CW-61 bucket + sign evaluation: 4 products of 61-bit field elements
+# (16 32x32->64-bit partial products) plus folds, reductions and the counter atomic.
+CW_INSTR = 60
+# Algorithmic cost of one exact 128-bit add or multiply-by-64-bit: 4 limbs, carries included.
+OP128_INSTR = 8
 
 
 def _args():
@@ -47,6 +50,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phases", action="store_true", help="print a per-phase breakdown on stderr")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of autotuned launch shapes: read if it has this workload's, else written")
     ap.add_argument("--case", default=None, choices=["estimate_small", "build_f1", "batched", "scale"],
                     help="run one small profiling case instead of the benchmark (for ncu captures)")
     return ap.parse_args()
@@ -101,6 +106,90 @@ def estimate_ops(n_tables, eu, ev, masks, d, w) -> int:
                 per_c += w * (2 * len(nc) + 1)                  # output: products, prefix adds, final add
         total += d * (per_row + (w if cond else 1) * per_c)
     return total
+
+
+def triangle_plan(n_tables, eu, ev, mask):
+    """(U, V, W, e*, eU, eV) when the sub-plan's only cycle is a triangle U-W-V closed by
+    the conditioned edge e* = U-V (BFS spanning tree from the lowest table, edges in id
+    order) and every other table is a leaf of U, V or W; else None.  Same rule as the
+    estimate planner."""
+    es = [e for e in range(len(eu)) if (mask >> eu[e]) & 1 and (mask >> ev[e]) & 1]
+    tabs = [t for t in range(n_tables) if (mask >> t) & 1]
+    order, seen, tree = [tabs[0]], {tabs[0]}, set()
+    h = 0
+    while h < len(order):
+        t = order[h]
+        h += 1
+        for e in es:
+            o = ev[e] if eu[e] == t else (eu[e] if ev[e] == t else None)
+            if o is None or o in seen:
+                continue
+            seen.add(o)
+            tree.add(e)
+            order.append(o)
+    cond = [e for e in es if e not in tree]
+    if len(cond) != 1:
+        return None
+    es_ = cond[0]
+    a, b = eu[es_], ev[es_]
+    other = lambda e, t: ev[e] if eu[e] == t else eu[e]
+    for w_ in tabs:
+        if w_ in (a, b):
+            continue
+        ea = [e for e in tree if w_ in (eu[e], ev[e]) and other(e, w_) == a]
+        eb = [e for e in tree if w_ in (eu[e], ev[e]) and other(e, w_) == b]
+        if ea and eb:
+            for t in tabs:
+                if t in (a, b, w_):
+                    continue
+                inc = [e for e in es if t in (eu[e], ev[e])]
+                if len(inc) != 1 or other(inc[0], t) not in (a, b, w_):
+                    return None
+            return a, b, w_, es_, ea[0], eb[0]
+    return None
+
+
+def triangle_ops(dw, masks):
+    """Exact 128-bit operations of the triangle path for the triangle sub-plans of `masks`,
+    and of the generic path for the others.  Per triangle sketch row, with G distinct
+    row-side clamp ranks, L_n leaves at node n and nq conditioning values:
+      preparation  sum_leaves 3w + 6 messages x w (1 + 2 L_n) + 4 nq + 4 w
+      sweep        w (6 (G + 1) + 16 G + 4)   (per column: batch sums, group terms, total)
+    G is computed here from the sketches with the kernel's rules (row side = the endpoint
+    whose conditioned sketch row has fewer distinct magnitudes)."""
+    wl = dw.wl
+    nt, eu, ev, d, w = len(wl.tables), wl.edge_u, wl.edge_v, wl.d, wl.w
+    generic = [m for m in masks if triangle_plan(nt, eu, ev, m) is None]
+    ops = estimate_ops(nt, eu, ev, generic, d, w)
+    sk = {}
+
+    def sketch(e, t):
+        key = (e, t)
+        if key not in sk:
+            sk[key] = dw.sketch(e, 0 if eu[e] == t else 1).cpu().numpy().astype(np.int64)
+        return sk[key]
+
+    n_tri = 0
+    for m in masks:
+        tp = triangle_plan(nt, eu, ev, m)
+        if tp is None:
+            continue
+        n_tri += 1
+        a, b, W, es_, ea, eb = tp
+        es = [e for e in range(len(eu)) if (m >> eu[e]) & 1 and (m >> ev[e]) & 1]
+        leaves = [sum(1 for e in es if t in (eu[e], ev[e])) - 2 for t in (a, b, W)]
+        for r in range(d):
+            cu, cv = np.abs(sketch(es_, a)[r]), np.abs(sketch(es_, b)[r])
+            distinct = lambda x: int(np.count_nonzero(np.diff(np.sort(x))))
+            R, par, tie = (b, eb, eb < es_) if distinct(cv) < distinct(cu) else (a, ea, ea < es_)
+            sr, sc = sketch(es_, R)[r], sketch(es_, a if R == b else b)[r]
+            live = (sr != 0) & (sc != 0)
+            srt = np.sort(np.abs(sketch(par, R)[r]))
+            ranks = np.searchsorted(srt, np.abs(sr[live]), side="right" if tie else "left")
+            G, nq = int(np.unique(ranks).size), int(live.sum())
+            prep = sum(3 * w * L for L in leaves) + sum(2 * w * (1 + 2 * L) for L in leaves) + 4 * nq + 4 * w
+            ops += prep + w * (6 * (G + 1) + 16 * G + 4)
+    return ops, n_tri, len(generic)
 
 
 def _kernel_traffic(name: str):
@@ -283,8 +372,10 @@ def run_ours(a):
     masks = G.connected_subplans(len(wl.tables), wl.edge_u, wl.edge_v)
     # launch shapes picked by the autotuner on this workload (outside the timed region)
     from paper_2102_02440_gb300 import autotune as AT
-    cfg_build, tuned_build = AT.tune_build(dw, reps=2)
-    cfg_est, tuned_est = AT.tune_estimate(lambda c: P.DeviceEstimator(dw, masks, cfg=c), reps=1)
+    cfg_build, tuned_build = AT.tune_build(dw, reps=2, cache_path=a.tune_cache)
+    sig = f"estimate d{wl.d} w{wl.w} tables{len(wl.tables)} masks{','.join(str(m) for m in masks)}"
+    cfg_est, tuned_est = AT.tune_estimate(lambda c: P.DeviceEstimator(dw, masks, cfg=c), reps=1,
+                                          cache_path=a.tune_cache, signature=sig)
     est = P.DeviceEstimator(dw, masks, cfg=cfg_est)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
@@ -356,29 +447,33 @@ def run_ours(a):
              for i, n in enumerate(("build", "presort", "estimate", "combiner"))}
     n_est = len(masks)
 
-    # roofline of the dominant kernel (the estimate, ~90% of the step): integer ALU bound
+    # roofline of the dominant kernel: the fused build (~80% of the step), integer ALU bound,
+    # with its HBM fraction beside it
     surv = dw.survivors.cpu().numpy()
-    est_ops = estimate_ops(len(wl.tables), wl.edge_u, wl.edge_v, masks, wl.d, wl.w)
-    est_s = phase["estimate"] / 1e3
-    op_peak = INT_ISSUE_PEAK / OP128_INSTR
-    roof = {"bound": "alu", "achieved": est_ops / est_s / 1e12, "peak": op_peak / 1e12, "unit": "T int128-op/s",
-            "frac": est_ops / est_s / op_peak, "traffic": _kernel_traffic("k_estimate_items"),
-            "kernel": "k_estimate_items (int64 tier + int128 recompute) and k_estimate_finalize",
-            "algorithmic": f"{est_ops} exact 128-bit multiplies/adds of the spanning-tree contraction",
-            "peak_derivation": f"152 SMs x 4 SMSP x 32 lanes x 2.07 GHz / {OP128_INSTR} int32 instr per op"}
-    # the fused build, second kernel: integer ALU bound, with its HBM fraction
     updates = int(sum(int(surv[i]) * len(t.key_col) * wl.d for i, t in enumerate(wl.tables)))
     hbm_peak, peak_kind = _peaks()
     col_bytes = wl.column_bytes()
     build_s = phase["build"] / 1e3
     ach = updates * CW_INSTR / build_s
-    roof_build = {"bound": "alu", "achieved": ach / 1e12, "peak": INT_ISSUE_PEAK / 1e12, "unit": "Tinstr/s",
-                  "frac": ach / INT_ISSUE_PEAK, "traffic": _kernel_traffic("k_sketch_build"),
-                  "kernel": "k_sketch_build (batched) + k_zero_spans",
-                  "algorithmic": f"{updates} CW evaluations x {CW_INSTR} int32 instr",
-                  "hbm": {"achieved_gbs": col_bytes / build_s / 1e9, "peak_gbs": hbm_peak,
-                          "frac": col_bytes / build_s / 1e9 / hbm_peak, "peak_kind": peak_kind,
-                          "algorithmic_bytes": col_bytes}}
+    roof = {"bound": "alu", "achieved": ach / 1e12, "peak": INT_ISSUE_PEAK / 1e12, "unit": "Tinstr/s",
+            "frac": ach / INT_ISSUE_PEAK, "traffic": _kernel_traffic("k_sketch_build"),
+            "kernel": "k_sketch_build (batched) + k_zero_spans",
+            "algorithmic": f"{updates} CW evaluations x {CW_INSTR} int32 instr",
+            "peak_derivation": "152 SMs x 4 SMSP x 32 lanes x 2.07 GHz (one int32 warp instruction per SMSP-clock)",
+            "hbm": {"achieved_gbs": col_bytes / build_s / 1e9, "peak_gbs": hbm_peak,
+                    "frac": col_bytes / build_s / 1e9 / hbm_peak, "peak_kind": peak_kind,
+                    "algorithmic_bytes": col_bytes}}
+    # the estimate: triangle path (preparation + sweep) for the cyclic sub-plans, generic
+    # contraction for the trees; exact 128-bit operations of those algorithms
+    est_ops, n_tri_sub, n_gen_sub = triangle_ops(dw, masks)
+    est_s = phase["estimate"] / 1e3
+    op_peak = INT_ISSUE_PEAK / OP128_INSTR
+    roof_est = {"bound": "alu", "achieved": est_ops / est_s / 1e12, "peak": op_peak / 1e12,
+                "unit": "T int128-op/s", "frac": est_ops / est_s / op_peak,
+                "traffic": _kernel_traffic("k_tri_sweep"),
+                "kernel": "k_estimate_items (trees), k_tri_prep + k_tri_sweep (triangles), k_estimate_finalize",
+                "algorithmic": f"{est_ops} exact 128-bit operations ({n_tri_sub} triangle, {n_gen_sub} other sub-plans)",
+                "peak_derivation": f"152 SMs x 4 SMSP x 32 lanes x 2.07 GHz / {OP128_INSTR} int32 instr per op"}
 
     # end to end through the public API: pinned host columns -> device, path, estimates -> host
     e2e = None
@@ -408,9 +503,15 @@ def run_ours(a):
     if rank == 0 and not a.no_cpu_baseline:
         cpu = cpu_baseline(wl)
 
-    # zero + build, presort + cross ranks per table, estimate (int64, int128 recompute, finalize),
+    # zero + build, presort + cross ranks per table, estimate (generic int64 + int128 recompute
+    # when trees are planned, triangle preparation + sweep when triangles are, finalize),
     # two self-join sizes per two-table sub-plan, features, infer, combine
-    launches_per_step = 2 + 2 * sum(1 for t in dw.tables if t.k) + 3 + 2 * len(two) + 3
+    est_launches = (2 if n_gen_sub > sum(1 for m in masks if bin(m).count("1") == 1) else 0) + \
+        (2 if n_tri_sub else 0) + 1
+    # build: zero spans + build kernel, plus key range, clearing and counting when the plan
+    # aggregates key columns (it then has a workspace)
+    build_launches = 2 + (3 if dw._plan[2] else 0)
+    launches_per_step = build_launches + 2 * sum(1 for t in dw.tables if t.k) + est_launches + 2 * len(two) + 3
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -424,7 +525,7 @@ def run_ours(a):
                 "autotuned": {"build": tuned_build["cfg"], "estimate": tuned_est["cfg"]},
                 "build_only_tuples_per_s": rows / (phase["build"] / 1e3),
                 "survivors": [int(x) for x in surv],
-                "roofline": roof, "roofline_build": roof_build, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "roofline": roof, "roofline_estimate": roof_est, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_step * a.steps}
         print(json.dumps(line), flush=True)
     if world > 1:

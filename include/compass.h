@@ -104,10 +104,16 @@ typedef struct {
   int32_t tile_rows;      /* rows per tile (multiple of 128, <= 16384)                              */
   int32_t dedupe;         /* -1 auto, 0 off, 1 aggregate equal keys of a tile before hashing        */
   int32_t ctas_per_sm;    /* CTAs per SM the grid is sized for                                      */
+  int32_t aggregate;      /* batched build only: -1 auto (tables of >= 2^18 rows), 0 off, 1 every
+                             table: aggregate each key column's survivors per distinct key before
+                             hashing (needs dedupe; same counters)                                  */
+  int32_t reserved;
 } cmp_build_cfg;
 
 /* ---------------------------------------------------------------------- general */
 
+/* Version of this interface (CMP_ABI_VERSION); bindings refuse a library that differs. */
+#define CMP_ABI_VERSION 2
 int32_t cmp_abi_version(void);
 const char* cmp_status_str(cmp_status s);
 
@@ -137,22 +143,33 @@ cmp_status cmp_sketch_build(const cmp_table* table, int32_t d, int32_t w, const 
                             int32_t* status_dev, const cmp_build_cfg* cfg, void* stream);
 
 /* Batched build (all attribute-level sketches of every table of a query, or of many
- * queries, in ONE persistent launch; Sec. 2: every table's selection and sketches are
- * built in the same push-down pass, and per-worker partial sketches merge by addition,
+ * queries, in ONE persistent build launch; Sec. 2: every table's selection and sketches
+ * are built in the same push-down pass, and per-worker partial sketches merge by addition,
  * Sec. 2 "Sketches").  Two host steps encode a plan, the caller copies it to the
- * device (any H2D copy), then cmp_sketch_build_batched enqueues one zeroing kernel and
- * one build kernel reading it.  The plan holds device pointers, so it stays valid as
- * long as the columns and outputs do; it can be replayed and captured in a CUDA graph.
+ * device (any H2D copy), then cmp_sketch_build_batched enqueues a zeroing kernel and the
+ * build kernel reading it.  The plan holds device pointers, so it stays valid as long as
+ * the columns and outputs do; it can be replayed and captured in a CUDA graph.
  *   counters_dev_host  host array [n_tables] of device pointers, each [n_sketches][d][w]
  *   survivors_dev      device [n_tables] int64
- * cmp_build_plan_encode returns CMP_EWORKSPACE if plan_bytes is too small. */
+ *   ws_dev, ws_bytes   device workspace of at least the *ws_bytes cmp_build_plan_bytes
+ *                      reports (0 when no key column is aggregated; NULL allowed then),
+ *                      caller-owned, contents irrelevant between calls
+ * Key aggregation (cfg->aggregate): the survivors of each key column of a large table
+ * are first counted per distinct key (dense count array over [min key, max key], found
+ * on the device), then each distinct key is hashed once per (sketch, row) with its count
+ * as the multiplier.  The update is linear and the counters wrap exactly, so the result
+ * is bit-identical to one update per tuple; a column whose key range exceeds
+ * min(rows, 2^27) falls back to the per-row path at run time.  This adds three small
+ * launches (key range, clearing, counting) before the build kernel.
+ * cmp_build_plan_encode returns CMP_EWORKSPACE if plan_bytes is too small;
+ * cmp_sketch_build_batched returns CMP_EWORKSPACE if ws_bytes is. */
 cmp_status cmp_build_plan_bytes(const cmp_table* tables, int32_t n_tables, int32_t d, int32_t w,
-                                const cmp_build_cfg* cfg, size_t* plan_bytes);
+                                const cmp_build_cfg* cfg, size_t* plan_bytes, size_t* ws_bytes);
 cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_tables, int32_t d, int32_t w,
                                  int32_t n_edges, int32_t* const* counters_dev_host, int64_t* survivors_dev,
                                  const cmp_build_cfg* cfg, void* plan_host, size_t plan_bytes);
 cmp_status cmp_sketch_build_batched(const void* plan_host, const void* plan_dev, const cmp_hash* hash_dev,
-                                    int32_t* status_dev, void* stream);
+                                    void* ws_dev, size_t ws_bytes, int32_t* status_dev, void* stream);
 
 /* ------------------------------------------------------------------- estimation */
 

@@ -106,9 +106,15 @@ def tune_build(dw, candidates=None, reps: int = 3, cache_path: str | None = None
     return K.cmp_build_cfg.make(**best[0]), entry
 
 
-def tune_estimate(make_estimator, candidates=None, reps: int = 3):
+def tune_estimate(make_estimator, candidates=None, reps: int = 3, cache_path: str | None = None,
+                  signature: str | None = None):
     """Fastest estimate shape; make_estimator(cfg) must return an object with presort()
-    (called once), estimate() and est / row_est tensors.  Returns (cmp_estimate_cfg, report)."""
+    (called once), estimate() and est / row_est tensors.  Returns (cmp_estimate_cfg, report).
+    With cache_path and signature (a description of the plan's sizes), a cached choice is
+    reused without timing."""
+    cache = _load(cache_path) if signature else {}
+    if signature and signature in cache:
+        return K.cmp_estimate_cfg.make(**cache[signature]["cfg"]), cache[signature]
     report, ref, best = [], None, None
     for cand in candidates or ESTIMATE_CANDIDATES:
         cfg = K.cmp_estimate_cfg.make(**cand)
@@ -125,4 +131,9 @@ def tune_estimate(make_estimator, candidates=None, reps: int = 3):
         if best is None or ms < best[1]:
             best = (cand, ms)
         del est
-    return K.cmp_estimate_cfg.make(**best[0]), {"cfg": best[0], "ms": best[1], "tried": report}
+    entry = {"cfg": best[0], "ms": best[1], "tried": report}
+    if signature:
+        entry["signature"] = signature
+        cache[signature] = entry
+        _save(cache_path, cache)
+    return K.cmp_estimate_cfg.make(**best[0]), entry

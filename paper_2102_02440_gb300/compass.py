@@ -16,6 +16,7 @@ CMP_OK, CMP_EINVAL, CMP_EUNSUPPORTED, CMP_EOVERFLOW, CMP_ECUDA, CMP_EWORKSPACE, 
 CMP_I32, CMP_I64 = 0, 1
 CMP_RANGE, CMP_EQ, CMP_IN_BITMAP = 0, 1, 2
 CMP_EST_GENERIC_ONLY = 1
+CMP_ABI_VERSION = 2
 CMP_MAX_COLS, CMP_MAX_PREDS, CMP_MAX_SKETCHES, CMP_MAX_D = 32, 8, 16, 64
 
 
@@ -46,11 +47,12 @@ class cmp_table(C.Structure):
 
 class cmp_build_cfg(C.Structure):
     _fields_ = [("mode", C.c_int32), ("pairs_per_slab", C.c_int32), ("threads", C.c_int32),
-                ("tile_rows", C.c_int32), ("dedupe", C.c_int32), ("ctas_per_sm", C.c_int32)]
+                ("tile_rows", C.c_int32), ("dedupe", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("aggregate", C.c_int32), ("reserved", C.c_int32)]
 
     @classmethod
-    def make(cls, mode=0, pairs_per_slab=0, threads=0, tile_rows=0, dedupe=-1, ctas_per_sm=0):
-        return cls(mode, pairs_per_slab, threads, tile_rows, dedupe, ctas_per_sm)
+    def make(cls, mode=0, pairs_per_slab=0, threads=0, tile_rows=0, dedupe=-1, ctas_per_sm=0, aggregate=-1):
+        return cls(mode, pairs_per_slab, threads, tile_rows, dedupe, ctas_per_sm, aggregate, 0)
 
 
 class cmp_estimate_cfg(C.Structure):
@@ -78,11 +80,12 @@ _SIGS = {
     "cmp_sketch_build": (C.c_int32, [C.POINTER(cmp_table), C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.POINTER(cmp_build_cfg), C.c_void_p]),
     "cmp_build_plan_bytes": (C.c_int32, [C.POINTER(cmp_table), C.c_int32, C.c_int32, C.c_int32,
-                                         C.POINTER(cmp_build_cfg), C.POINTER(C.c_size_t)]),
+                                         C.POINTER(cmp_build_cfg), C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "cmp_build_plan_encode": (C.c_int32, [C.POINTER(cmp_table), C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                           C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(cmp_build_cfg), C.c_void_p,
                                           C.c_size_t]),
-    "cmp_sketch_build_batched": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cmp_sketch_build_batched": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                             C.c_void_p, C.c_void_p]),
     "cmp_presort_ws_bytes": (C.c_size_t, [C.c_int64, C.c_int32]),
     "cmp_presort": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                                 C.c_void_p]),
@@ -131,6 +134,9 @@ def lib(build_if_missing: bool = True):
                 continue
             fn.restype = res
             fn.argtypes = args
+        if L.cmp_abi_version() != CMP_ABI_VERSION:
+            raise RuntimeError(f"libcompass at {path} has interface version {L.cmp_abi_version()}, "
+                               f"this binding needs {CMP_ABI_VERSION}: rebuild it")
         _lib = L
     return _lib
 
@@ -178,12 +184,14 @@ def cmp_sketch_build(table: cmp_table, d: int, w: int, hash_dev: int, n_edges: i
                                   C.byref(cfg) if cfg is not None else None, stream))
 
 
-def cmp_build_plan_bytes(tables, d: int, w: int, cfg: cmp_build_cfg | None) -> int:
+def cmp_build_plan_bytes(tables, d: int, w: int, cfg: cmp_build_cfg | None) -> tuple[int, int]:
+    """(plan bytes, workspace bytes) of a batched build."""
     arr = (cmp_table * len(tables))(*tables)
-    n = C.c_size_t(0)
+    n, ws = C.c_size_t(0), C.c_size_t(0)
     _check("cmp_build_plan_bytes", lib().cmp_build_plan_bytes(arr, len(tables), d, w,
-                                                              C.byref(cfg) if cfg is not None else None, C.byref(n)))
-    return n.value
+                                                              C.byref(cfg) if cfg is not None else None, C.byref(n),
+                                                              C.byref(ws)))
+    return n.value, ws.value
 
 
 def cmp_build_plan_encode(tables, d: int, w: int, n_edges: int, counters_ptrs, survivors_dev: int,
@@ -195,9 +203,10 @@ def cmp_build_plan_encode(tables, d: int, w: int, n_edges: int, counters_ptrs, s
                                        C.byref(cfg) if cfg is not None else None, plan_host, plan_bytes))
 
 
-def cmp_sketch_build_batched(plan_host: int, plan_dev: int, hash_dev: int, status_dev: int, stream: int):
-    _check("cmp_sketch_build_batched", lib().cmp_sketch_build_batched(plan_host, plan_dev, hash_dev, status_dev,
-                                                                      stream))
+def cmp_sketch_build_batched(plan_host: int, plan_dev: int, hash_dev: int, ws_dev: int, ws_bytes: int,
+                             status_dev: int, stream: int):
+    _check("cmp_sketch_build_batched", lib().cmp_sketch_build_batched(plan_host, plan_dev, hash_dev, ws_dev, ws_bytes,
+                                                                      status_dev, stream))
 
 
 def cmp_presort_ws_bytes(n_rows: int, w: int) -> int:

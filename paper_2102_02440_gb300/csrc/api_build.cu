@@ -96,6 +96,7 @@ DevTable to_dev(const cmp_table* t, int32_t* counters, int64_t* survivors) {
   }
   D.counters = counters;
   D.survivors = survivors;
+  for (int c = 0; c < CMP_MAX_COLS; c++) D.agg[c] = -1;
   return D;
 }
 
@@ -166,7 +167,7 @@ using namespace cmpk;
 
 extern "C" {
 
-int32_t cmp_abi_version(void) { return 1; }
+int32_t cmp_abi_version(void) { return CMP_ABI_VERSION; }
 
 const char* cmp_status_str(cmp_status s) {
   switch (s) {
@@ -231,11 +232,29 @@ cmp_status cmp_sketch_build(const cmp_table* table, int32_t d, int32_t w, const 
 }
 
 // ---------------------------------------------------------------- batched build plan
-// blob: [BuildPlanHdr][DevTable x n_tables][BuildItem x n_items][int32 cta_item x grid][ZeroSpan x n_zero]
+// blob: [BuildPlanHdr][DevTable x n_tables][BuildItem x n_items][int32 cta_item x grid]
+//       [ZeroSpan x n_zero][AggCol x n_agg][CountItem x n_cnt_items][int32 cnt_cta x cnt_grid]
+
+// Key aggregation: tables with at least this many rows (auto mode), count arrays of at
+// most this many slots (a column whose key range is wider keeps the per-row path).
+constexpr int64_t kAggMinRows = int64_t(1) << 18;
+constexpr int64_t kAggMaxCap = int64_t(1) << 27;
+
+struct BuildPlanParts {
+  BuildShape shape;
+  std::vector<BuildItem> items;
+  std::vector<int32_t> cta_item;
+  std::vector<AggCol> aggs;
+  std::vector<CountItem> cnt_items;
+  std::vector<int32_t> cnt_cta;
+  std::vector<std::vector<int32_t>> col_agg;  // [table][col] AggCol index or -1
+  size_t bytes = 0, ws_bytes = 0;
+};
+
+static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
 static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t d, int32_t w,
-                              const cmp_build_cfg* cfg, BuildShape* shape, std::vector<BuildItem>* items,
-                              std::vector<int32_t>* cta_item, size_t* bytes, int32_t n_edges_check) {
+                              const cmp_build_cfg* cfg, int32_t n_edges_check, BuildPlanParts* P) {
   if (n_tables < 1 || !tables) return CMP_EINVAL;
   int32_t max_pairs = 1;
   for (int32_t t = 0; t < n_tables; t++) {
@@ -246,66 +265,143 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
   BuildShape s;
   cmp_status st = choose_shape(cfg, d, w, max_pairs, &s);
   if (st != CMP_OK) return st;
+  const int agg_mode = cfg ? cfg->aggregate : -1;
+  if (agg_mode < -1 || agg_mode > 1) return CMP_EINVAL;
+  if (agg_mode == 1 && !s.dedupe) return CMP_EINVAL;  // aggregated items use the tile map's entry lists
   const int ctas_per_sm = s.ctas_per_slab;
-  // work of an item ~ tiles * (pairs + 1); CTAs proportional to work, >= 1, <= tiles
+  const int R = s.tile_rows;
+  // aggregated key columns: every distinct key column of a selected table
+  P->col_agg.assign(n_tables, std::vector<int32_t>(CMP_MAX_COLS, -1));
+  P->aggs.clear();
+  size_t ws = al256(16 * size_t(n_tables) * CMP_MAX_SKETCHES);  // stats area (upper bound, fixed)
+  for (int32_t t = 0; t < n_tables; t++) {
+    const cmp_table& tb = tables[t];
+    const bool on = tb.n_sketches > 0 && tb.n_rows > 0 && s.dedupe &&
+                    (agg_mode == 1 || (agg_mode == -1 && tb.n_rows >= kAggMinRows));
+    if (!on) continue;
+    for (int k = 0; k < tb.n_sketches; k++) {
+      const int c = tb.key_col[k];
+      if (P->col_agg[t][c] >= 0) continue;
+      AggCol a;
+      a.table = t;
+      a.col = c;
+      a.cap = std::min<int64_t>(tb.n_rows, kAggMaxCap);
+      a.off = 0;
+      P->col_agg[t][c] = int32_t(P->aggs.size());
+      P->aggs.push_back(a);
+    }
+  }
+  if (P->aggs.size() > size_t(n_tables) * CMP_MAX_SKETCHES) return CMP_EINVAL;
+  for (AggCol& a : P->aggs) {
+    a.off = int64_t(ws);
+    ws += al256(16 * size_t((a.cap + 3) / 4));  // whole int4 words: the zeroing kernel writes them
+  }
+  P->ws_bytes = P->aggs.empty() ? 0 : ws;
+  // work of an item ~ units (tiles or count chunks) * (pairs hashed per unit + 1); CTAs
+  // proportional to work, >= 1, <= units.  Aggregated items hash distinct keys only
+  // (counted as a quarter of their chunk's slots).
   struct Raw {
-    int32_t t, b, e;
-    int64_t tiles;
+    int32_t t, b, e, agg;
+    int64_t units;
     double work;
   };
   std::vector<Raw> raw;
   double total = 0;
   for (int32_t t = 0; t < n_tables; t++) {
-    const int32_t tp = tables[t].n_sketches * d;
-    const int64_t tiles = (tables[t].n_rows + s.tile_rows - 1) / s.tile_rows;
+    const cmp_table& tb = tables[t];
+    const int32_t tp = tb.n_sketches * d;
+    const int64_t tiles = (tb.n_rows + R - 1) / R;
     if (tiles == 0) continue;
     const int32_t n_slabs = tp ? (tp + s.pairs_per_slab - 1) / s.pairs_per_slab : 1;
     for (int32_t k = 0; k < n_slabs; k++) {
-      Raw r{t, k * s.pairs_per_slab, std::min(tp, (k + 1) * s.pairs_per_slab), tiles, 0};
-      r.work = double(tiles) * double(r.e - r.b + 1);
+      const int32_t b = k * s.pairs_per_slab, e = std::min(tp, (k + 1) * s.pairs_per_slab);
+      int32_t row_pairs = 0;
+      for (int32_t p = b; p < e; p++)
+        if (P->col_agg[t][tb.key_col[p / d]] < 0) row_pairs++;
+      Raw r{t, b, e, -1, tiles, double(tiles) * double(row_pairs + 1)};
       total += r.work;
       raw.push_back(r);
+      for (int32_t c = 0; c < tb.n_cols; c++) {
+        const int32_t ai = P->col_agg[t][c];
+        if (ai < 0) continue;
+        int32_t np = 0;
+        for (int32_t p = b; p < e; p++) np += tb.key_col[p / d] == c;
+        if (!np) continue;
+        const int64_t chunks = (P->aggs[ai].cap + R - 1) / R;
+        Raw ra{t, b, e, ai, chunks, double(chunks) * (1.0 + 0.25 * np)};
+        total += ra.work;
+        raw.push_back(ra);
+      }
     }
   }
   const double target = double(sm_count()) * ctas_per_sm * 4.0;
-  items->clear();
-  cta_item->clear();
-  for (size_t i = 0; i < raw.size(); i++) {
-    const Raw& r = raw[i];
+  P->items.clear();
+  P->cta_item.clear();
+  for (const Raw& r : raw) {
     int64_t n = int64_t(r.work / std::max(total, 1.0) * target + 0.5);
-    n = std::max<int64_t>(1, std::min<int64_t>(n, r.tiles));
+    n = std::max<int64_t>(1, std::min<int64_t>(n, r.units));
     BuildItem it;
     it.table = r.t;
     it.pair_begin = r.b;
     it.pair_end = r.e;
     it.n_ctas = int32_t(n);
-    it.first_cta = int32_t(cta_item->size());
-    it.pad = 0;
-    for (int64_t c = 0; c < n; c++) cta_item->push_back(int32_t(items->size()));
-    items->push_back(it);
+    it.first_cta = int32_t(P->cta_item.size());
+    it.agg = r.agg;
+    for (int64_t c = 0; c < n; c++) P->cta_item.push_back(int32_t(P->items.size()));
+    P->items.push_back(it);
   }
-  s.grid = int32_t(cta_item->size());
+  // counting pass: one item per table with aggregated columns, CTAs by tiles x columns
+  P->cnt_items.clear();
+  P->cnt_cta.clear();
+  double cnt_total = 0;
+  for (int32_t t = 0; t < n_tables; t++) {
+    int ncol = 0;
+    for (int32_t c = 0; c < CMP_MAX_COLS; c++) ncol += P->col_agg[t][c] >= 0;
+    if (ncol) cnt_total += double((tables[t].n_rows + R - 1) / R) * (ncol + 1);
+  }
+  const double cnt_target = double(sm_count()) * std::max(1, 2048 / s.threads) * 4.0;
+  for (int32_t t = 0; t < n_tables; t++) {
+    int ncol = 0;
+    for (int32_t c = 0; c < CMP_MAX_COLS; c++) ncol += P->col_agg[t][c] >= 0;
+    if (!ncol) continue;
+    const int64_t tiles = (tables[t].n_rows + R - 1) / R;
+    int64_t n = int64_t(double(tiles) * (ncol + 1) / std::max(cnt_total, 1.0) * cnt_target + 0.5);
+    n = std::max<int64_t>(1, std::min<int64_t>(n, tiles));
+    CountItem ci;
+    ci.table = t;
+    ci.n_ctas = int32_t(n);
+    ci.first_cta = int32_t(P->cnt_cta.size());
+    ci.pad = 0;
+    for (int64_t c = 0; c < n; c++) P->cnt_cta.push_back(int32_t(P->cnt_items.size()));
+    P->cnt_items.push_back(ci);
+  }
+  s.grid = int32_t(P->cta_item.size());
   s.ctas_per_slab = 0;
-  *shape = s;
+  P->shape = s;
   size_t off = align16(sizeof(BuildPlanHdr));
   off += align16(sizeof(DevTable) * n_tables);
-  off += align16(sizeof(BuildItem) * items->size());
-  off += align16(sizeof(int32_t) * cta_item->size());
+  off += align16(sizeof(BuildItem) * P->items.size());
+  off += align16(sizeof(int32_t) * P->cta_item.size());
   off += align16(sizeof(ZeroSpan) * (n_tables + 1));
-  *bytes = off;
+  off += align16(sizeof(AggCol) * P->aggs.size());
+  off += align16(sizeof(CountItem) * P->cnt_items.size());
+  off += align16(sizeof(int32_t) * P->cnt_cta.size());
+  P->bytes = off;
   return CMP_OK;
 }
 
 }  // extern "C"
 
 extern "C" cmp_status cmp_build_plan_bytes(const cmp_table* tables, int32_t n_tables, int32_t d, int32_t w,
-                                           const cmp_build_cfg* cfg, size_t* plan_bytes) {
-  if (!plan_bytes) return CMP_EINVAL;
-  BuildShape s;
-  std::vector<BuildItem> items;
-  std::vector<int32_t> cta;
+                                           const cmp_build_cfg* cfg, size_t* plan_bytes, size_t* ws_bytes) {
+  if (!plan_bytes || !ws_bytes) return CMP_EINVAL;
+  BuildPlanParts P;
   // edge ids are validated at encode time (n_edges unknown here): accept any non-negative id
-  return plan_layout(tables, n_tables, d, w, cfg, &s, &items, &cta, plan_bytes, 1 << 30);
+  const cmp_status st = plan_layout(tables, n_tables, d, w, cfg, 1 << 30, &P);
+  if (st != CMP_OK) return st;
+  *plan_bytes = P.bytes;
+  *ws_bytes = P.ws_bytes;
+  return CMP_OK;
 }
 
 extern "C" cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_tables, int32_t d, int32_t w,
@@ -313,57 +409,71 @@ extern "C" cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_t
                                             int64_t* survivors_dev, const cmp_build_cfg* cfg, void* plan_host,
                                             size_t plan_bytes) {
   if (!plan_host || !counters_dev_host || !survivors_dev) return CMP_EINVAL;
-  BuildShape s;
-  std::vector<BuildItem> items;
-  std::vector<int32_t> cta;
-  size_t need = 0;
-  cmp_status st = plan_layout(tables, n_tables, d, w, cfg, &s, &items, &cta, &need, n_edges);
+  BuildPlanParts P;
+  cmp_status st = plan_layout(tables, n_tables, d, w, cfg, n_edges, &P);
   if (st != CMP_OK) return st;
-  if (plan_bytes < need) return CMP_EWORKSPACE;
+  if (plan_bytes < P.bytes) return CMP_EWORKSPACE;
   for (int32_t t = 0; t < n_tables; t++)
     if (tables[t].n_sketches && !counters_dev_host[t]) return CMP_EINVAL;
   unsigned char* base = static_cast<unsigned char*>(plan_host);
-  std::memset(base, 0, need);
+  std::memset(base, 0, P.bytes);
   BuildPlanHdr h;
   std::memset(&h, 0, sizeof(h));
   h.magic = kBuildPlanMagic;
-  h.version = 1;
+  h.version = kBuildPlanVersion;
   h.n_tables = n_tables;
-  h.n_items = int32_t(items.size());
+  h.n_items = int32_t(P.items.size());
   h.d = d, h.w = w, h.n_edges = n_edges;
-  h.shape = s;
+  h.shape = P.shape;
   size_t off = align16(sizeof(BuildPlanHdr));
   h.off_tables = int64_t(off);
   off += align16(sizeof(DevTable) * n_tables);
   h.off_items = int64_t(off);
-  off += align16(sizeof(BuildItem) * items.size());
+  off += align16(sizeof(BuildItem) * P.items.size());
   h.off_cta_item = int64_t(off);
-  off += align16(sizeof(int32_t) * cta.size());
+  off += align16(sizeof(int32_t) * P.cta_item.size());
   h.off_zero = int64_t(off);
-  h.total_bytes = int64_t(need);
+  off += align16(sizeof(ZeroSpan) * (n_tables + 1));
+  h.n_agg = int64_t(P.aggs.size());
+  h.off_agg = int64_t(off);
+  off += align16(sizeof(AggCol) * P.aggs.size());
+  h.n_cnt_items = int64_t(P.cnt_items.size());
+  h.off_cnt_items = int64_t(off);
+  off += align16(sizeof(CountItem) * P.cnt_items.size());
+  h.off_cnt_cta = int64_t(off);
+  h.cnt_grid = int32_t(P.cnt_cta.size());
+  h.ws_bytes = int64_t(P.ws_bytes);
+  h.total_bytes = int64_t(P.bytes);
   std::vector<ZeroSpan> zs;
   for (int32_t t = 0; t < n_tables; t++) {
     DevTable D = to_dev(&tables[t], counters_dev_host[t], survivors_dev + t);
+    for (int32_t c = 0; c < CMP_MAX_COLS; c++) D.agg[c] = P.col_agg[t][c];
     std::memcpy(base + h.off_tables + sizeof(DevTable) * t, &D, sizeof(D));
     const int64_t cb = int64_t(tables[t].n_sketches) * d * w * 4;
     if (cb) zs.push_back(ZeroSpan{counters_dev_host[t], cb});
   }
   zs.push_back(ZeroSpan{survivors_dev, int64_t(n_tables) * 8});
   h.n_zero = int64_t(zs.size());
-  std::memcpy(base + h.off_items, items.data(), sizeof(BuildItem) * items.size());
-  std::memcpy(base + h.off_cta_item, cta.data(), sizeof(int32_t) * cta.size());
+  std::memcpy(base + h.off_items, P.items.data(), sizeof(BuildItem) * P.items.size());
+  std::memcpy(base + h.off_cta_item, P.cta_item.data(), sizeof(int32_t) * P.cta_item.size());
   std::memcpy(base + h.off_zero, zs.data(), sizeof(ZeroSpan) * zs.size());
+  if (!P.aggs.empty()) std::memcpy(base + h.off_agg, P.aggs.data(), sizeof(AggCol) * P.aggs.size());
+  if (!P.cnt_items.empty())
+    std::memcpy(base + h.off_cnt_items, P.cnt_items.data(), sizeof(CountItem) * P.cnt_items.size());
+  if (!P.cnt_cta.empty()) std::memcpy(base + h.off_cnt_cta, P.cnt_cta.data(), sizeof(int32_t) * P.cnt_cta.size());
   std::memcpy(base, &h, sizeof(h));
   return CMP_OK;
 }
 
 extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void* plan_dev,
-                                               const cmp_hash* hash_dev, int32_t* status_dev, void* stream) {
+                                               const cmp_hash* hash_dev, void* ws_dev, size_t ws_bytes,
+                                               int32_t* status_dev, void* stream) {
   if (!plan_host || !plan_dev) return CMP_EINVAL;
   BuildPlanHdr h;
   std::memcpy(&h, plan_host, sizeof(h));
-  if (h.magic != kBuildPlanMagic || h.version != 1) return CMP_EINVAL;
+  if (h.magic != kBuildPlanMagic || h.version != kBuildPlanVersion) return CMP_EINVAL;
   if (h.n_edges > 0 && !hash_dev) return CMP_EINVAL;
+  if (h.ws_bytes > 0 && (!ws_dev || ws_bytes < size_t(h.ws_bytes))) return CMP_EWORKSPACE;
   const unsigned char* dev = static_cast<const unsigned char*>(plan_dev);
   cudaStream_t cs = as_stream(stream);
   if (launch_zero_spans(reinterpret_cast<const ZeroSpan*>(dev + h.off_zero), int32_t(h.n_zero), cs) != cudaSuccess)
@@ -379,5 +489,16 @@ extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void
   a.d = h.d, a.w = h.w, a.n_edges = h.n_edges;
   a.threads = h.shape.threads, a.tile_rows = h.shape.tile_rows, a.map_slots = h.shape.map_slots;
   a.max_pairs = h.shape.max_pairs, a.smem_pairs = h.shape.smem_pairs;
+  if (h.n_agg > 0) {
+    a.agg = reinterpret_cast<const AggCol*>(dev + h.off_agg);
+    a.n_agg = int32_t(h.n_agg);
+    a.ws = static_cast<unsigned char*>(ws_dev);
+    a.cnt_items = reinterpret_cast<const CountItem*>(dev + h.off_cnt_items);
+    a.cnt_cta_item = reinterpret_cast<const int32_t*>(dev + h.off_cnt_cta);
+    // the (max, min) stats start from zero (decoding as an empty column)
+    if (cudaMemsetAsync(ws_dev, 0, 16 * size_t(h.n_agg), cs) != cudaSuccess) return CMP_ECUDA;
+    if (launch_agg(a, h.shape, h.cnt_grid, cs) != cudaSuccess) return CMP_ECUDA;
+  }
   return launch_build(a, h.shape, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
 }
+

@@ -15,7 +15,16 @@
 //      one global atomic per nonzero counter (partial sketches merge by addition,
 //      Sec. 2 "Sketches").
 // The kernel has no inter-CTA waits.
+//
+// Key aggregation (batched build, large tables): before the build kernel, k_agg_stats
+// finds each aggregated key column's smallest and largest key, k_agg_zero clears the
+// used part of its count array, and k_agg_count adds every tile's survivors to it (tile
+// keys reduced in a shared-memory map first, one global atomic per distinct key of the
+// tile).  The build kernel's aggregated items then hash each nonzero (key, count) entry
+// once per pair instead of once per tuple, and its row items skip those columns.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "internal.cuh"
 
@@ -66,6 +75,48 @@ __device__ __forceinline__ uint32_t map_slot(uint64_t x, uint32_t mask) {
 
 constexpr int kMaxSlotsPerThread = 8;
 
+// Phase A of one tile: the predicate conjunction over rows [r0, r0 + rows_in_tile), the
+// survivors' offsets compacted into surv[] (warp scan, one shared atomic per warp).
+// Returns the survivor count.  Block-wide: every thread calls it; sint[0] is the tail.
+__device__ int tile_survivors(const DevTable* tb, int64_t r0, int rows_in_tile, int R, bool vec, uint16_t* surv,
+                              int32_t* sint) {
+  const int n_preds = tb->n_preds;
+  if (n_preds == 0) return rows_in_tile;
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
+  if (tid == 0) sint[0] = 0;
+  __syncthreads();
+  const int iters = (R + 4 * T - 1) / (4 * T);
+  for (int it = 0; it < iters; it++) {
+    const int base = 4 * (tid + it * T);
+    const int nvalid = max(0, min(4, rows_in_tile - base));
+    uint32_t m = (1u << nvalid) - 1u;
+    for (int q = 0; q < n_preds && m; q++) {
+      const DevPred& pq = tb->pred[q];
+      int64_t v[4];
+      load4(tb->col[pq.col], tb->dtype[pq.col], r0 + base, nvalid, vec, v);
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if (!pred_holds(pq, v[k])) m &= ~(1u << k);
+    }
+    const int c = __popc(m);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    int wbase = 0;
+    if (lane == 31) wbase = atomicAdd(&sint[0], incl);
+    wbase = __shfl_sync(0xffffffffu, wbase, 31);
+    int pos = wbase + incl - c;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      if ((m >> k) & 1u) surv[pos++] = uint16_t(base + k);
+  }
+  __syncthreads();
+  return sint[0];
+}
+
 }  // namespace
 
 template <bool GLOBAL, bool DEDUPE, bool POW2>
@@ -78,7 +129,7 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
 
   // ---- resolve the work item of this CTA
   const DevTable* tb;
-  int pair_begin, pair_end, cta_in_slab, n_ctas;
+  int pair_begin, pair_end, cta_in_slab, n_ctas, agg_item = -1;
   if (A.items) {
     const BuildItem it = A.items[A.cta_item[blockIdx.x]];
     tb = A.tables + it.table;
@@ -86,6 +137,7 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
     pair_end = it.pair_end;
     cta_in_slab = int(blockIdx.x) - it.first_cta;
     n_ctas = it.n_ctas;
+    agg_item = it.agg;
   } else {
     tb = &A.table;
     const int slab = int(blockIdx.x) / A.ctas_per_slab;
@@ -153,167 +205,178 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
   const int n_keycols = sint[39];
 
   int32_t* gcnt = tb->counters + size_t(pair_begin) * w;
-  const int64_t n_tiles = (n_rows + R - 1) / R;
   int64_t my_survivors = 0;
 
-  for (int64_t tile = cta_in_slab; tile < n_tiles; tile += n_ctas) {
-    const int64_t r0 = tile * R;
-    const int rows_in_tile = int(min(int64_t(R), n_rows - r0));
-
-    // ---------------- A. predicates and survivor compaction
-    int n_surv;
-    if (n_preds == 0) {
-      n_surv = rows_in_tile;
-    } else {
-      if (tid == 0) sint[0] = 0;
-      __syncthreads();
-      const int iters = (R + 4 * T - 1) / (4 * T);
-      for (int it = 0; it < iters; it++) {
-        const int base = 4 * (tid + it * T);
-        const int nvalid = max(0, min(4, rows_in_tile - base));
-        uint32_t m = (1u << nvalid) - 1u;
-        for (int q = 0; q < n_preds && m; q++) {
-          const DevPred& pq = tb->pred[q];
-          int64_t v[4];
-          load4(tb->col[pq.col], tb->dtype[pq.col], r0 + base, nvalid, vec, v);
-#pragma unroll
-          for (int k = 0; k < 4; k++)
-            if (!pred_holds(pq, v[k])) m &= ~(1u << k);
-        }
-        const int c = __popc(m);
-        int incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int t = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += t;
-        }
-        int wbase = 0;
-        if (lane == 31) wbase = atomicAdd(&sint[0], incl);
-        wbase = __shfl_sync(0xffffffffu, wbase, 31);
-        int pos = wbase + incl - c;
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-          if ((m >> k) & 1u) surv[pos++] = uint16_t(base + k);
+  // Hash the first n_entries (field element, count) entries of mkey / mcnt for the pairs
+  // of key column kc, or (no map) the keys of the tile's first n_entries survivors.  Two
+  // entries per thread share every parameter load: two independent hash chains.
+  auto hash_entries = [&](int kc, int n_entries, const void* kbase, int32_t kdt, int64_t r0, bool from_map) {
+    const int pl_begin = colstart[kc], pl_end = colstart[kc + 1];
+    for (int e0 = tid; e0 < n_entries; e0 += 2 * T) {
+      const int e1 = e0 + T;
+      uint64_t x0, x1 = 0;
+      int32_t m0, m1 = 0;
+      if (from_map) {
+        x0 = mkey[e0];
+        m0 = mcnt[e0];
+        if (e1 < n_entries) x1 = mkey[e1], m1 = mcnt[e1];
+      } else {
+        x0 = key_field(load1(kbase, kdt, r0 + (n_preds ? surv[e0] : e0)));
+        m0 = 1;
+        if (e1 < n_entries) x1 = key_field(load1(kbase, kdt, r0 + (n_preds ? surv[e1] : e1))), m1 = 1;
       }
-      __syncthreads();
-      n_surv = sint[0];
+      const KeyPow k0 = key_powers(x0);
+      const KeyPow k1 = key_powers(x1);
+      for (int j = pl_begin; j < pl_end; j++) {
+        const int pp = plist[j];
+        const PairParam q = prm[pp];
+        const uint32_t h0 = cw_bucket<POW2>(q, k0, uint32_t(w));
+        const uint32_t h1 = cw_bucket<POW2>(q, k1, uint32_t(w));
+        const int32_t v0 = cw_sign(q, k0) * m0;
+        const int32_t v1 = cw_sign(q, k1) * m1;
+        int32_t* row = (GLOBAL ? gcnt : cnt) + size_t(pp) * w;
+        atomicAdd(row + h0, v0);
+        if (m1) atomicAdd(row + h1, v1);
+      }
     }
-    my_survivors += n_surv;
+  };
 
-    // ---------------- B. per key column: aggregate equal keys, hash, update
-    for (int kc = 0; kc < n_keycols; kc++) {
-      const int c = cols_list[kc];
-      const void* kbase = tb->col[c];
-      const int32_t kdt = tb->dtype[c];
-      int n_entries = n_surv;
-      if (DEDUPE) {
-        for (int s = tid; s < M; s += T) {
-          mkey[s] = kEmptyKey;
-          mcnt[s] = 0;
-        }
-        __syncthreads();
-        const uint32_t mmask = uint32_t(M - 1);
-        for (int base = 0; base < n_surv; base += T) {  // block-uniform trip count
-          const int e = base + tid;
-          const bool valid = e < n_surv;
-          unsigned long long x = kEmptyKey;
-          if (valid) x = key_field(load1(kbase, kdt, r0 + (n_preds ? surv[e] : e)));
-          // equal keys of the warp are inserted once, by their lowest lane, with their count
-          const unsigned peers = __match_any_sync(0xffffffffu, x);
-          if (!valid || lane != __ffs(peers) - 1) continue;
-          uint32_t slot = map_slot(x, mmask);
-          bool done = false;
-          for (int probe = 0; probe < M; probe++) {
-            const unsigned long long prev = atomicCAS(&mkey[slot], kEmptyKey, x);
-            if (prev == kEmptyKey || prev == x) {
-              atomicAdd(&mcnt[slot], __popc(peers));
-              done = true;
-              break;
+  if (agg_item >= 0) {
+    // ---------------- aggregated column: chunks of its count array
+    if constexpr (DEDUPE) {
+      const AggCol ac = A.agg[agg_item];
+      int64_t kmin = 0, range = 0;
+      int kc = -1;
+      for (int k = 0; k < n_keycols; k++)
+        if (cols_list[k] == ac.col) kc = k;
+      if (kc >= 0 && agg_active(ac, agg_item, A.ws, &kmin, &range)) {
+        const int32_t* cnts = reinterpret_cast<const int32_t*>(A.ws + ac.off);
+        const int64_t n_chunks = (range + R - 1) / R;
+        for (int64_t chunk = cta_in_slab; chunk < n_chunks; chunk += n_ctas) {
+          const int64_t i0 = chunk * R;
+          const int nin = int(min(int64_t(R), range - i0));
+          if (tid == 0) sint[0] = 0;
+          __syncthreads();
+          for (int base = 0; base < nin; base += T) {  // block-uniform trip count
+            const int j = base + tid;
+            const int32_t c = j < nin ? __ldg(cnts + i0 + j) : 0;
+            const unsigned nz = __ballot_sync(0xffffffffu, c != 0);
+            int wbase = 0;
+            if (lane == 0 && nz) wbase = atomicAdd(&sint[0], __popc(nz));
+            wbase = __shfl_sync(0xffffffffu, wbase, 0);
+            if (c != 0) {
+              const int pos = wbase + __popc(nz & ((1u << lane) - 1u));
+              mkey[pos] = key_field(kmin + i0 + j);
+              mcnt[pos] = c;
             }
-            slot = (slot + 1) & mmask;
           }
-          if (!done) set_status(A.status, CMP_ETIMEOUT);  // unreachable: M > tile rows
+          __syncthreads();
+          hash_entries(kc, sint[0], nullptr, 0, 0, true);
+          __syncthreads();  // entry lists reused next
         }
-        __syncthreads();
-        // compact occupied slots to the front (read all, barrier, write all)
-        const int spt = M / T;  // <= kMaxSlotsPerThread, host-checked
-        unsigned long long kx[kMaxSlotsPerThread];
-        int32_t kn[kMaxSlotsPerThread];
-        uint32_t valid = 0;
-#pragma unroll
-        for (int j = 0; j < kMaxSlotsPerThread; j++) {
-          kx[j] = kEmptyKey;
-          kn[j] = 0;
-          if (j < spt) {
-            kx[j] = mkey[tid * spt + j];
-            kn[j] = mcnt[tid * spt + j];
-            if (kx[j] != kEmptyKey) valid |= 1u << j;
+      }
+    }
+  } else {
+    const int64_t n_tiles = (n_rows + R - 1) / R;
+    for (int64_t tile = cta_in_slab; tile < n_tiles; tile += n_ctas) {
+      const int64_t r0 = tile * R;
+      const int rows_in_tile = int(min(int64_t(R), n_rows - r0));
+
+      // ---------------- A. predicates and survivor compaction
+      const int n_surv = tile_survivors(tb, r0, rows_in_tile, R, vec, surv, sint);
+      my_survivors += n_surv;
+
+      // ---------------- B. per key column: aggregate equal keys, hash, update
+      for (int kc = 0; kc < n_keycols; kc++) {
+        const int c = cols_list[kc];
+        if (A.agg && tb->agg[c] >= 0) {  // hashed by the column's aggregated items when active
+          int64_t kmin, range;
+          if (agg_active(A.agg[tb->agg[c]], tb->agg[c], A.ws, &kmin, &range)) continue;
+        }
+        const void* kbase = tb->col[c];
+        const int32_t kdt = tb->dtype[c];
+        int n_entries = n_surv;
+        if (DEDUPE) {
+          for (int s = tid; s < M; s += T) {
+            mkey[s] = kEmptyKey;
+            mcnt[s] = 0;
           }
-        }
-        const int mine = __popc(valid);
-        int incl = mine;
+          __syncthreads();
+          const uint32_t mmask = uint32_t(M - 1);
+          for (int base = 0; base < n_surv; base += T) {  // block-uniform trip count
+            const int e = base + tid;
+            const bool valid = e < n_surv;
+            unsigned long long x = kEmptyKey;
+            if (valid) x = key_field(load1(kbase, kdt, r0 + (n_preds ? surv[e] : e)));
+            // equal keys of the warp are inserted once, by their lowest lane, with their count
+            const unsigned peers = __match_any_sync(0xffffffffu, x);
+            if (!valid || lane != __ffs(peers) - 1) continue;
+            uint32_t slot = map_slot(x, mmask);
+            bool done = false;
+            for (int probe = 0; probe < M; probe++) {
+              const unsigned long long prev = atomicCAS(&mkey[slot], kEmptyKey, x);
+              if (prev == kEmptyKey || prev == x) {
+                atomicAdd(&mcnt[slot], __popc(peers));
+                done = true;
+                break;
+              }
+              slot = (slot + 1) & mmask;
+            }
+            if (!done) set_status(A.status, CMP_ETIMEOUT);  // unreachable: M > tile rows
+          }
+          __syncthreads();
+          // compact occupied slots to the front (read all, barrier, write all)
+          const int spt = M / T;  // <= kMaxSlotsPerThread, host-checked
+          unsigned long long kx[kMaxSlotsPerThread];
+          int32_t kn[kMaxSlotsPerThread];
+          uint32_t valid = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int t = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += t;
-        }
-        if (lane == 31) sint[1 + warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-          const int nw = T >> 5;
-          int v = lane < nw ? sint[1 + lane] : 0;
-          int s2 = v;
+          for (int j = 0; j < kMaxSlotsPerThread; j++) {
+            kx[j] = kEmptyKey;
+            kn[j] = 0;
+            if (j < spt) {
+              kx[j] = mkey[tid * spt + j];
+              kn[j] = mcnt[tid * spt + j];
+              if (kx[j] != kEmptyKey) valid |= 1u << j;
+            }
+          }
+          const int mine = __popc(valid);
+          int incl = mine;
 #pragma unroll
           for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, s2, o);
-            if (lane >= o) s2 += t;
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
           }
-          if (lane < nw) sint[1 + lane] = s2 - v;  // exclusive prefix per warp
-          if (lane == nw - 1) sint[0] = s2;
-        }
-        __syncthreads();
-        int pos = sint[1 + warp] + incl - mine;
-        n_entries = sint[0];
+          if (lane == 31) sint[1 + warp] = incl;
+          __syncthreads();
+          if (warp == 0) {
+            const int nw = T >> 5;
+            int v = lane < nw ? sint[1 + lane] : 0;
+            int s2 = v;
 #pragma unroll
-        for (int j = 0; j < kMaxSlotsPerThread; j++) {
-          if ((valid >> j) & 1u) {
-            mkey[pos] = kx[j];
-            mcnt[pos] = kn[j];
-            pos++;
+            for (int o = 1; o < 32; o <<= 1) {
+              const int t = __shfl_up_sync(0xffffffffu, s2, o);
+              if (lane >= o) s2 += t;
+            }
+            if (lane < nw) sint[1 + lane] = s2 - v;  // exclusive prefix per warp
+            if (lane == nw - 1) sint[0] = s2;
           }
+          __syncthreads();
+          int pos = sint[1 + warp] + incl - mine;
+          n_entries = sint[0];
+#pragma unroll
+          for (int j = 0; j < kMaxSlotsPerThread; j++) {
+            if ((valid >> j) & 1u) {
+              mkey[pos] = kx[j];
+              mcnt[pos] = kn[j];
+              pos++;
+            }
+          }
+          __syncthreads();
         }
-        __syncthreads();
+        hash_entries(kc, n_entries, kbase, kdt, r0, DEDUPE);
+        __syncthreads();  // map / survivor list reused next
       }
-      // Two entries per thread share every parameter load: two independent hash chains.
-      const int pl_begin = colstart[kc], pl_end = colstart[kc + 1];
-      for (int e0 = tid; e0 < n_entries; e0 += 2 * T) {
-        const int e1 = e0 + T;
-        uint64_t x0, x1 = 0;
-        int32_t m0, m1 = 0;
-        if (DEDUPE) {
-          x0 = mkey[e0];
-          m0 = mcnt[e0];
-          if (e1 < n_entries) x1 = mkey[e1], m1 = mcnt[e1];
-        } else {
-          x0 = key_field(load1(kbase, kdt, r0 + (n_preds ? surv[e0] : e0)));
-          m0 = 1;
-          if (e1 < n_entries) x1 = key_field(load1(kbase, kdt, r0 + (n_preds ? surv[e1] : e1))), m1 = 1;
-        }
-        const KeyPow k0 = key_powers(x0);
-        const KeyPow k1 = key_powers(x1);
-        for (int j = pl_begin; j < pl_end; j++) {
-          const int pp = plist[j];
-          const PairParam q = prm[pp];
-          const uint32_t h0 = cw_bucket<POW2>(q, k0, uint32_t(w));
-          const uint32_t h1 = cw_bucket<POW2>(q, k1, uint32_t(w));
-          const int32_t v0 = cw_sign(q, k0) * m0;
-          const int32_t v1 = cw_sign(q, k1) * m1;
-          int32_t* row = (GLOBAL ? gcnt : cnt) + size_t(pp) * w;
-          atomicAdd(row + h0, v0);
-          if (m1) atomicAdd(row + h1, v1);
-        }
-      }
-      __syncthreads();  // map / survivor list reused next
     }
   }
 
@@ -355,6 +418,142 @@ cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t s
   }
   if (d) return pow2 ? launch_one<false, true, true>(a, s, st) : launch_one<false, true, false>(a, s, st);
   return pow2 ? launch_one<false, false, true>(a, s, st) : launch_one<false, false, false>(a, s, st);
+}
+
+// ---------------------------------------------------------------- key aggregation
+// Smallest and largest key of every aggregated column over all its rows (a bound on the
+// survivors' keys); grid.y = column.
+__global__ void __launch_bounds__(256) k_agg_stats(const __grid_constant__ BuildArgs A) {
+  const int ai = int(blockIdx.y);
+  const AggCol ac = A.agg[ai];
+  const DevTable* tb = A.tables + ac.table;
+  const void* base = tb->col[ac.col];
+  const int32_t dt = tb->dtype[ac.col];
+  const bool vec = tb->vec_ok != 0;
+  const int64_t n = tb->n_rows;
+  int64_t mn = INT64_MAX, mx = INT64_MIN;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x * 4;
+  for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4; r < n; r += stride) {
+    int64_t v[4];
+    const int nvalid = int(min(int64_t(4), n - r));
+    load4(base, dt, r, nvalid, vec, v);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      if (k < nvalid) {
+        mn = min(mn, v[k]);
+        mx = max(mx, v[k]);
+      }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    mn = min(mn, (int64_t)__shfl_down_sync(0xffffffffu, (long long)mn, off));
+    mx = max(mx, (int64_t)__shfl_down_sync(0xffffffffu, (long long)mx, off));
+  }
+  if ((threadIdx.x & 31) == 0 && mx >= mn) {
+    unsigned long long* st = reinterpret_cast<unsigned long long*>(A.ws) + 2 * int64_t(ai);
+    atomicMax(st, (unsigned long long)enc_max(mx));
+    atomicMax(st + 1, (unsigned long long)enc_min(mn));
+  }
+}
+
+// Clears the used part [0, range) of every active column's count array; grid.y = column.
+__global__ void __launch_bounds__(256) k_agg_zero(const __grid_constant__ BuildArgs A) {
+  const int ai = int(blockIdx.y);
+  const AggCol ac = A.agg[ai];
+  int64_t kmin, range;
+  if (!agg_active(ac, ai, A.ws, &kmin, &range)) return;
+  int4* c4 = reinterpret_cast<int4*>(A.ws + ac.off);  // 256-byte aligned
+  const int64_t n4 = (range + 3) / 4;                 // within cap rounded up to 64 entries
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x)
+    c4[i] = make_int4(0, 0, 0, 0);
+}
+
+// Per tile of a table with aggregated columns: survivors (phase A), then for every active
+// column the tile's keys reduced in a shared-memory map (key - min -> count; equal keys of
+// a warp inserted once by __match_any_sync) and one global atomic per occupied slot.
+__global__ void __launch_bounds__(1024) k_agg_count(const __grid_constant__ BuildArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const CountItem it = A.cnt_items[A.cnt_cta_item[blockIdx.x]];
+  const DevTable* tb = A.tables + it.table;
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
+  const int R = A.tile_rows, M = A.map_slots;
+  unsigned char* sp = smem;
+  uint32_t* mkey = reinterpret_cast<uint32_t*>(sp);
+  sp += align16(sizeof(uint32_t) * size_t(M));
+  int32_t* mcnt = reinterpret_cast<int32_t*>(sp);
+  sp += align16(sizeof(int32_t) * size_t(M));
+  uint16_t* surv = reinterpret_cast<uint16_t*>(sp);
+  sp += align16(sizeof(uint16_t) * R);
+  int32_t* sint = reinterpret_cast<int32_t*>(sp);
+  constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // never an index: cap <= 2^31 - 1
+  const int64_t n_rows = tb->n_rows;
+  const int64_t n_tiles = (n_rows + R - 1) / R;
+  const int n_preds = tb->n_preds;
+  const bool vec = tb->vec_ok != 0;
+  const int cta = int(blockIdx.x) - it.first_cta;
+  for (int64_t tile = cta; tile < n_tiles; tile += it.n_ctas) {
+    const int64_t r0 = tile * R;
+    const int rows_in_tile = int(min(int64_t(R), n_rows - r0));
+    const int n_surv = tile_survivors(tb, r0, rows_in_tile, R, vec, surv, sint);
+    for (int c = 0; c < tb->n_cols; c++) {
+      const int ai = tb->agg[c];
+      if (ai < 0) continue;
+      int64_t kmin, range;
+      if (!agg_active(A.agg[ai], ai, A.ws, &kmin, &range)) continue;  // block-uniform
+      int32_t* cnts = reinterpret_cast<int32_t*>(A.ws + A.agg[ai].off);
+      const void* kbase = tb->col[c];
+      const int32_t kdt = tb->dtype[c];
+      for (int s = tid; s < M; s += T) {
+        mkey[s] = kEmpty;
+        mcnt[s] = 0;
+      }
+      __syncthreads();
+      const uint32_t mmask = uint32_t(M - 1);
+      for (int base = 0; base < n_surv; base += T) {  // block-uniform trip count
+        const int e = base + tid;
+        const bool valid = e < n_surv;
+        uint32_t x = kEmpty;
+        if (valid) x = uint32_t(load1(kbase, kdt, r0 + (n_preds ? surv[e] : e)) - kmin);  // < range <= cap
+        const unsigned peers = __match_any_sync(0xffffffffu, x);
+        if (!valid || lane != __ffs(peers) - 1) continue;
+        uint32_t slot = map_slot(x, mmask);
+        bool done = false;
+        for (int probe = 0; probe < M; probe++) {
+          const uint32_t prev = atomicCAS(&mkey[slot], kEmpty, x);
+          if (prev == kEmpty || prev == x) {
+            atomicAdd(&mcnt[slot], __popc(peers));
+            done = true;
+            break;
+          }
+          slot = (slot + 1) & mmask;
+        }
+        if (!done) set_status(A.status, CMP_ETIMEOUT);  // unreachable: M > tile rows
+      }
+      __syncthreads();
+      for (int s = tid; s < M; s += T)
+        if (mkey[s] != kEmpty) atomicAdd(cnts + mkey[s], mcnt[s]);
+      __syncthreads();  // map reused next
+    }
+  }
+}
+
+size_t agg_count_smem_bytes(const BuildShape& s) {
+  return align16(sizeof(uint32_t) * size_t(s.map_slots)) + align16(sizeof(int32_t) * size_t(s.map_slots)) +
+         align16(sizeof(uint16_t) * s.tile_rows) + sizeof(int32_t) * 40;
+}
+
+cudaError_t launch_agg(const BuildArgs& a, const BuildShape& s, int32_t cnt_grid, cudaStream_t st) {
+  if (a.n_agg <= 0) return cudaSuccess;
+  const dim3 g(unsigned(std::max(1, 2 * sm_count() / std::max(1, a.n_agg))), unsigned(a.n_agg));
+  k_agg_stats<<<g, 256, 0, st>>>(a);
+  k_agg_zero<<<g, 256, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || cnt_grid <= 0) return e;
+  const size_t smem = agg_count_smem_bytes(s);
+  e = cudaFuncSetAttribute(k_agg_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  k_agg_count<<<unsigned(cnt_grid), s.threads, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 __global__ void k_zero_spans(const ZeroSpan* __restrict__ spans, int32_t n) {

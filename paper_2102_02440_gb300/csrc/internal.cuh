@@ -126,15 +126,57 @@ struct DevTable {
   int32_t edge_id[CMP_MAX_SKETCHES];
   int32_t* counters;   // [n_sketches][d][w]
   int64_t* survivors;  // one int64
+  int32_t agg[CMP_MAX_COLS];  // batched build: AggCol index of each aggregated key column, else -1
 };
 
+// Key aggregation of the batched build.  A key column of a large table is reduced to one
+// (key, survivor count) entry per distinct key before hashing: the Fast-AGMS update is
+// linear and the int32 counters wrap exactly, so count * xi(key) added once per entry
+// gives the counters of one update per tuple.  Keys are counted in a dense array indexed
+// by key - min; a column whose key range exceeds the array (cap) at run time keeps the
+// per-row path.  Workspace: [n_agg] x (max, min) encoded as uint64 pairs (256-aligned),
+// then each column's int32 count array at byte offset `off`.
+struct AggCol {
+  int32_t table, col;
+  int64_t cap;  // count slots
+  int64_t off;  // byte offset of the count array in the workspace
+};
+
+// Order-preserving maps of an int64 to uint64, for atomicMax on the stats pairs (both
+// zero-initialised: an empty column decodes as max < min).
+__host__ __device__ inline uint64_t enc_max(int64_t v) { return uint64_t(v) ^ (1ull << 63); }
+__host__ __device__ inline uint64_t enc_min(int64_t v) { return ~(uint64_t(v) ^ (1ull << 63)); }
+__host__ __device__ inline int64_t dec_max(uint64_t e) { return int64_t(e ^ (1ull << 63)); }
+__host__ __device__ inline int64_t dec_min(uint64_t e) { return int64_t(~e ^ (1ull << 63)); }
+
+// Whether aggregated column `a` (index ai) takes the aggregated path in this run, with its
+// smallest key and key range.
+__device__ __forceinline__ bool agg_active(const AggCol& a, int ai, const unsigned char* ws, int64_t* kmin,
+                                           int64_t* range) {
+  const unsigned long long* st = reinterpret_cast<const unsigned long long*>(ws) + 2 * int64_t(ai);
+  const int64_t mx = dec_max(st[0]), mn = dec_min(st[1]);
+  if (mx < mn) return false;
+  const uint64_t r = uint64_t(mx) - uint64_t(mn);
+  if (r >= uint64_t(a.cap)) return false;
+  *kmin = mn;
+  *range = int64_t(r) + 1;
+  return true;
+}
+
 // One (table, slab of (sketch,row) pairs) handled by n_ctas consecutive CTAs.
+// Row items walk tiles of the table's rows; aggregated items (agg >= 0) walk chunks of one
+// aggregated column's count array and hash that column's pairs of the slab.
 struct BuildItem {
   int32_t table;
   int32_t pair_begin, pair_end;
   int32_t n_ctas;
   int32_t first_cta;
-  int32_t pad;
+  int32_t agg;  // AggCol index, or -1
+};
+
+// Counting pass of key aggregation: n_ctas CTAs walk the tiles of one table.
+struct CountItem {
+  int32_t table, n_ctas, first_cta, pad;
 };
 
 struct BuildShape {
@@ -161,6 +203,11 @@ struct BuildArgs {
   int32_t d, w, n_edges;
   int32_t threads, tile_rows, map_slots, max_pairs, smem_pairs;
   int32_t pairs_per_slab, ctas_per_slab;
+  const AggCol* agg;  // key aggregation (batched build only)
+  int32_t n_agg;
+  unsigned char* ws;
+  const CountItem* cnt_items;
+  const int32_t* cnt_cta_item;
 };
 
 // Plan blob (host-encoded, device-read) for the batched build.
@@ -170,7 +217,12 @@ struct BuildPlanHdr {
   BuildShape shape;
   int64_t off_tables, off_items, off_cta_item, off_zero, n_zero;  // byte offsets in the blob
   int64_t total_bytes;
+  int64_t n_agg, off_agg;                            // aggregated key columns
+  int64_t n_cnt_items, off_cnt_items, off_cnt_cta;  // counting pass
+  int32_t cnt_grid, pad;
+  int64_t ws_bytes;
 };
+constexpr int32_t kBuildPlanVersion = 2;
 struct ZeroSpan {
   void* ptr;
   int64_t bytes;
@@ -187,6 +239,8 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 // launchers implemented in the .cu files
 size_t build_smem_bytes(const BuildShape& s, int w);
 cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t st);
+size_t agg_count_smem_bytes(const BuildShape& s);
+cudaError_t launch_agg(const BuildArgs& a, const BuildShape& s, int32_t cnt_grid, cudaStream_t st);
 cudaError_t launch_zero_spans(const ZeroSpan* spans_dev, int32_t n, cudaStream_t st);
 
 int sm_count();

@@ -22,36 +22,61 @@ __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__floa
 
 // ---------------------------------------------------------------- self-join sizes
 // f2[s] = median over rows i of sum_j C[s][i][j]^2 (the Fast-AGMS self-join estimate of
-// Sec. 3.2 applied to one sketch), exact per row, rounded once.
-__global__ void k_sketch_f2(const int32_t* __restrict__ C, int64_t n_sketches, int32_t d, int32_t w,
-                            double* __restrict__ f2) {
-  __shared__ i128 rows[CMP_MAX_D];
+// Sec. 3.2 applied to one sketch), exact per row, rounded once.  One CTA per sketch; its
+// warps split the d rows into d * split contiguous parts (split = warps / d, at least 1),
+// each lane streaming its part with four independent accumulators.
+constexpr int kF2Threads = 1024;
+
+__global__ void __launch_bounds__(kF2Threads) k_sketch_f2(const int32_t* __restrict__ C, int64_t n_sketches,
+                                                          int32_t d, int32_t w, double* __restrict__ f2) {
   __shared__ u128 part[32];
+  __shared__ i128 rows[CMP_MAX_D];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int split = nw / d > 0 ? nw / d : 1;
+  const int units = d * split;
+  const int64_t len = (int64_t(w) + split - 1) / split;
   for (int64_t s = blockIdx.x; s < n_sketches; s += gridDim.x) {
-    for (int i = 0; i < d; i++) {
-      const int32_t* src = C + (s * d + i) * int64_t(w);
-      u128 acc = 0;
-      for (int j = threadIdx.x; j < w; j += blockDim.x) {
-        const int64_t v = src[j];
-        acc += u128(uint64_t(v * v));
-      }
+    for (int u0 = 0; u0 < units; u0 += nw) {  // rounds of at most nw parts (one round unless d > warps)
+      const int u = u0 + warp;
+      if (u < units) {
+        const int i = u / split, p = u % split;
+        const int64_t b = int64_t(p) * len, e = b + len < w ? b + len : int64_t(w);
+        const int32_t* src = C + (s * d + i) * int64_t(w);
+        u128 a0 = 0, a1 = 0, a2 = 0, a3 = 0;  // each term < 2^62
+        int64_t j = b + lane;
+        for (; j + 96 < e; j += 128) {
+          const int64_t v0 = __ldg(src + j), v1 = __ldg(src + j + 32), v2 = __ldg(src + j + 64),
+                        v3 = __ldg(src + j + 96);
+          a0 += u128(uint64_t(v0 * v0));
+          a1 += u128(uint64_t(v1 * v1));
+          a2 += u128(uint64_t(v2 * v2));
+          a3 += u128(uint64_t(v3 * v3));
+        }
+        for (; j < e; j += 32) {
+          const int64_t v = __ldg(src + j);
+          a0 += u128(uint64_t(v * v));
+        }
+        u128 acc = a0 + a1 + a2 + a3;
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const uint64_t lo = __shfl_down_sync(0xffffffffu, uint64_t(acc), off);
-        const uint64_t hi = __shfl_down_sync(0xffffffffu, uint64_t(acc >> 64), off);
-        acc += (u128(hi) << 64) | lo;
+        for (int off = 16; off > 0; off >>= 1) {
+          const uint64_t lo = __shfl_down_sync(0xffffffffu, uint64_t(acc), off);
+          const uint64_t hi = __shfl_down_sync(0xffffffffu, uint64_t(acc >> 64), off);
+          acc += (u128(hi) << 64) | lo;
+        }
+        if (lane == 0) part[warp] = acc;
       }
-      if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
       __syncthreads();
       if (threadIdx.x == 0) {
-        u128 t = 0;
-        for (int k = 0; k < int(blockDim.x >> 5); k++) t += part[k];
-        rows[i] = i128(t);
+        for (int q = 0; q < nw && u0 + q < units; q++) {
+          const int uu = u0 + q, i = uu / split;
+          if (uu % split == 0) rows[i] = 0;
+          rows[i] = i128(u128(rows[i]) + part[q]);
+        }
       }
       __syncthreads();
     }
     if (threadIdx.x == 0) {
-      for (int i = 1; i < d; i++) {
+      for (int i = 1; i < d; i++) {  // insertion sort of exact integers
         const i128 v = rows[i];
         int j = i - 1;
         while (j >= 0 && rows[j] > v) {
@@ -241,7 +266,7 @@ cudaError_t launch_sketch_f2(const int32_t* C, int64_t n_sketches, int32_t d, in
                              cudaStream_t st) {
   if (n_sketches <= 0) return cudaSuccess;
   const int64_t grid = n_sketches < 8192 ? n_sketches : 8192;
-  k_sketch_f2<<<unsigned(grid), 256, 0, st>>>(C, n_sketches, d, w, f2);
+  k_sketch_f2<<<unsigned(grid), kF2Threads, 0, st>>>(C, n_sketches, d, w, f2);
   return cudaGetLastError();
 }
 

@@ -69,19 +69,23 @@ class DeviceWorkload:
 
     def encode_batched(self, cfg=None):
         descs = [t.desc for t in self.tables]
-        nb = K.cmp_build_plan_bytes(descs, self.d, self.w, cfg)
+        nb, wb = K.cmp_build_plan_bytes(descs, self.d, self.w, cfg)
         host = np.zeros(nb, np.uint8)
         K.cmp_build_plan_encode(descs, self.d, self.w, self.n_edges, [t.counters.data_ptr() for t in self.tables],
                                 self.survivors.data_ptr(), cfg, host.ctypes.data, nb)
-        self._plan = (host, torch.from_numpy(host).to(self.device))
+        ws = getattr(self, "build_ws", None)
+        if wb and (ws is None or ws.numel() < wb):
+            self.build_ws = torch.empty(wb, dtype=torch.uint8, device=self.device)
+        self._plan = (host, torch.from_numpy(host).to(self.device), wb)
         return nb
 
     def build_batched(self, cfg=None, stream=None):
         if self._plan is None:
             self.encode_batched(cfg)
-        host, dev = self._plan
-        K.cmp_sketch_build_batched(host.ctypes.data, dev.data_ptr(), self.hash_dev.data_ptr(), self.status.data_ptr(),
-                                   K.stream_handle(stream))
+        host, dev, wb = self._plan
+        ws = self.build_ws.data_ptr() if wb else 0
+        K.cmp_sketch_build_batched(host.ctypes.data, dev.data_ptr(), self.hash_dev.data_ptr(), ws, wb,
+                                   self.status.data_ptr(), K.stream_handle(stream))
 
     def check_status(self):
         st = int(self.status.item())

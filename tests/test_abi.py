@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(K):
 def test_status_strings(K):
     assert K.status_str(0) == "ok"
     assert "invalid" in K.status_str(-1)
-    assert K.lib().cmp_abi_version() == 1
+    assert K.lib().cmp_abi_version() == K.CMP_ABI_VERSION == 2
 
 
 def test_hash_params_match_oracle_generator(K, orc):
@@ -106,8 +106,16 @@ def test_build_rejects_bad_cfg(K):
 def test_batched_plan_encoding_host_logic(K):
     """Plan sizing and encoding run on the host; the blob is self-describing."""
     tabs = [_desc(K, n_rows=n, key_col=(0, 0), edge_id=(0, 1)) for n in (0, 1, 5000, 10_000_000)]
-    nb = K.cmp_build_plan_bytes(tabs, 11, 1024, None)
+    nb, wb = K.cmp_build_plan_bytes(tabs, 11, 1024, None)
     assert nb > 0
+    # key aggregation (auto: tables of >= 2^18 rows): one count array for the 10M-row table
+    assert wb >= 10_000_000 * 4
+    assert K.cmp_build_plan_bytes(tabs, 11, 1024, K.cmp_build_cfg.make(aggregate=0))[1] == 0
+    assert K.cmp_build_plan_bytes(tabs, 11, 1024, K.cmp_build_cfg.make(aggregate=1))[1] > wb  # also the 5000-row table
+    for bad in (K.cmp_build_cfg.make(aggregate=1, dedupe=0), K.cmp_build_cfg.make(aggregate=2)):
+        with pytest.raises(K.CompassError) as ei:
+            K.cmp_build_plan_bytes(tabs, 11, 1024, bad)
+        assert ei.value.status == K.CMP_EINVAL
     buf = np.zeros(nb, np.uint8)
     with pytest.raises(K.CompassError):
         K.cmp_build_plan_encode(tabs, 11, 1024, 2, [0x1000] * 4, 0x2000, None, buf.ctypes.data, nb - 16)
@@ -116,9 +124,15 @@ def test_batched_plan_encoding_host_logic(K):
     K.cmp_build_plan_encode(tabs, 11, 1024, 2, [0x1000] * 4, 0x2000, None, buf.ctypes.data, nb)
     hdr = buf[:8].view(np.uint64)[0]
     assert hdr == 0x434D504255494C44
+    # a workspace below the plan's requirement is rejected before anything is enqueued
+    assert K.lib().cmp_sketch_build_batched(buf.ctypes.data, 0x1000, 0x2000, 0x4000, wb - 1, 0x3000,
+                                            None) == K.CMP_EWORKSPACE
+    assert K.lib().cmp_sketch_build_batched(buf.ctypes.data, 0x1000, 0x2000, None, 0, 0x3000,
+                                            None) == K.CMP_EWORKSPACE
     # cmp_sketch_build_batched rejects a blob that is not a plan
     junk = np.zeros(nb, np.uint8)
-    assert K.lib().cmp_sketch_build_batched(junk.ctypes.data, 0x1000, 0x2000, 0x3000, None) == K.CMP_EINVAL
+    assert K.lib().cmp_sketch_build_batched(junk.ctypes.data, 0x1000, 0x2000, None, 0, 0x3000,
+                                            None) == K.CMP_EINVAL
 
 
 def _graph(K, eu, ev, nt):
