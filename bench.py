@@ -48,11 +48,13 @@ def _args():
     ap.add_argument("--scale", type=float, default=1.0, help="row-count scale of the workload (1.0 = full)")
     ap.add_argument("--w", type=int, default=4096)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch every step eagerly instead of replaying it as one captured CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phases", action="store_true", help="print a per-phase breakdown on stderr")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of autotuned launch shapes: read if it has this workload's, else written")
-    ap.add_argument("--case", default=None, choices=["estimate_small", "build_f1", "batched", "scale"],
+    ap.add_argument("--case", default=None, choices=["estimate_small", "build_f1", "build_five", "batched", "scale"],
                     help="run one small profiling case instead of the benchmark (for ncu captures)")
     return ap.parse_args()
 
@@ -190,6 +192,44 @@ def triangle_ops(dw, masks):
             prep = sum(3 * w * L for L in leaves) + sum(2 * w * (1 + 2 * L) for L in leaves) + 4 * nq + 4 * w
             ops += prep + w * (6 * (G + 1) + 16 * G + 4)
     return ops, n_tri, len(generic)
+
+
+def build_work(wl, dw, dedupe: bool):
+    """CW evaluations the batched build must do.  A key column of a table with >= 2^18
+    rows whose key range fits min(rows, 2^27) is aggregated (dedupe on): one evaluation
+    per distinct surviving key per sketch row of that column; other columns one per
+    surviving row per sketch row.  Survivors and distinct keys are counted on the device
+    (torch, outside any timed region)."""
+    import torch
+    total, distinct = 0, {}
+    for ti, (t, dt) in enumerate(zip(wl.tables, dw.tables)):
+        if not t.key_col:
+            continue
+        keep = torch.ones(t.n_rows, dtype=torch.bool, device=dw.device)
+        for q in t.preds:
+            v = dt.cols[q.col].to(torch.int64)
+            if q.op == 0:
+                keep &= (v >= q.lo) & (v < q.hi)
+            elif q.op == 1:
+                keep &= v == q.lo
+            else:
+                bm = dt.bitmaps[t.preds.index(q)].to(torch.int64)
+                inb = (v >= 0) & (v < q.nbits)
+                vv = torch.where(inb, v, torch.zeros_like(v))
+                keep &= inb & (((bm[vv >> 5] >> (vv & 31)) & 1) == 1)
+        n_surv = int(keep.sum().item())
+        for c in sorted(set(t.key_col)):
+            pairs = t.key_col.count(c) * wl.d
+            col = dt.cols[c]
+            agg = dedupe and t.n_rows >= (1 << 18) and t.n_rows > 0 and \
+                int(col.max().item()) - int(col.min().item()) < min(t.n_rows, 1 << 27)
+            if agg:
+                nd = int(torch.unique(col[keep]).numel())
+                distinct[f"{t.name}.col{c}"] = nd
+                total += nd * pairs
+            else:
+                total += n_surv * pairs
+    return total, distinct
 
 
 def _kernel_traffic(name: str):
@@ -377,7 +417,7 @@ def run_ours(a):
     cfg_est, tuned_est = AT.tune_estimate(lambda c: P.DeviceEstimator(dw, masks, cfg=c), reps=1,
                                           cache_path=a.tune_cache, signature=sig)
     est = P.DeviceEstimator(dw, masks, cfg=cfg_est)
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)  # a side stream: CUDA graphs cannot capture the legacy default stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     # learned combiner over every sub-plan's row estimates; self-join sizes of the two
     # sketches of each two-table sub-plan (its training domain), zero elsewhere
@@ -420,45 +460,85 @@ def run_ours(a):
         if evs:
             evs[4].record(stream)
 
-    for _ in range(a.warmup):
-        step()
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        for _ in range(a.warmup):
+            step()
     torch.cuda.synchronize(dev)
     dw.check_status()
+    # the whole step captured once as a CUDA graph (the same launches, replayed without
+    # per-launch host overhead); its outputs must equal the eager step's bit for bit
+    graph = None
+    if not a.no_graph:
+        eager_out = (est.row_est.clone(), est.est.clone(), est_comb.clone())
+        with torch.cuda.stream(stream):
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                step()
+            for _ in range(a.warmup):
+                graph.replay()
+        torch.cuda.synchronize(dev)
+        dw.check_status()
+        if not (torch.equal(eager_out[0], est.row_est) and torch.equal(eager_out[1].nan_to_num(-1.0),
+                                                                     est.est.nan_to_num(-1.0))
+                and torch.equal(eager_out[2].nan_to_num(-1.0), est_comb.nan_to_num(-1.0))):
+            raise RuntimeError("graph replay of the step differs from the eager step")
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(a.steps)]
+    def timed_step(ev0, ev1):
+        ev0.record(stream)
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+        ev1.record(stream)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(a.steps)]
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     _barrier(world)
     torch.cuda.synchronize(dev)
-    for k in range(a.steps):
-        flush.zero_()                        # evict the previous step's inputs from L2
-        step(evs[k])
+    with torch.cuda.stream(stream):
+        for k in range(a.steps):
+            flush.zero_()                        # evict the previous step's inputs from L2
+            timed_step(*evs[k])
     torch.cuda.synchronize(dev)
     _barrier(world)
     clocks = sampler.stop()
     dw.check_status()
-    per = [[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs]
-    step_ms = [sum(p) for p in per]
+    step_ms = [e[0].elapsed_time(e[1]) for e in evs]
     ms = statistics.mean(step_ms)
+    # per-phase split from eager steps with events between the phases (outside the timing)
+    pevs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(a.steps)]
+    with torch.cuda.stream(stream):
+        for k in range(a.steps):
+            flush.zero_()
+            step(pevs[k])
+    torch.cuda.synchronize(dev)
+    per = [[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in pevs]
     rows = wl.total_rows
     value, ms_max = whole_job_rate(rows, ms, world)
     phase = {n: statistics.mean(p[i] for p in per)
              for i, n in enumerate(("build", "presort", "estimate", "combiner"))}
     n_est = len(masks)
 
-    # roofline of the dominant kernel: the fused build (~80% of the step), integer ALU bound,
-    # with its HBM fraction beside it
+    # roofline of the dominant phase: the batched build (zero spans, key range, clearing,
+    # counting, build kernel; ~60% of the step), integer ALU bound on the hash evaluations
+    # it must do, with its HBM fraction beside it
     surv = dw.survivors.cpu().numpy()
     updates = int(sum(int(surv[i]) * len(t.key_col) * wl.d for i, t in enumerate(wl.tables)))
+    cw_evals, distinct = build_work(wl, dw, dedupe=bool(tuned_build["cfg"].get("dedupe", 1)))
     hbm_peak, peak_kind = _peaks()
     col_bytes = wl.column_bytes()
     build_s = phase["build"] / 1e3
-    ach = updates * CW_INSTR / build_s
+    ach = cw_evals * CW_INSTR / build_s
     roof = {"bound": "alu", "achieved": ach / 1e12, "peak": INT_ISSUE_PEAK / 1e12, "unit": "Tinstr/s",
             "frac": ach / INT_ISSUE_PEAK, "traffic": _kernel_traffic("k_sketch_build"),
-            "kernel": "k_sketch_build (batched) + k_zero_spans",
-            "algorithmic": f"{updates} CW evaluations x {CW_INSTR} int32 instr",
+            "kernel": "batched build: k_zero_spans, k_agg_stats, k_agg_zero, k_agg_count, k_sketch_build",
+            "algorithmic": f"{cw_evals} CW evaluations x {CW_INSTR} int32 instr (one per distinct surviving key "
+                           f"and sketch row on aggregated columns, one per surviving tuple and sketch row elsewhere; "
+                           f"{updates} tuple updates)",
+            "distinct_keys": distinct,
             "peak_derivation": "152 SMs x 4 SMSP x 32 lanes x 2.07 GHz (one int32 warp instruction per SMSP-clock)",
             "hbm": {"achieved_gbs": col_bytes / build_s / 1e9, "peak_gbs": hbm_peak,
                     "frac": col_bytes / build_s / 1e9 / hbm_peak, "peak_kind": peak_kind,
@@ -483,18 +563,22 @@ def run_ours(a):
         out_host = torch.empty(n_sub, dtype=torch.float64).pin_memory()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         tms = []
-        for k in range(a.warmup + a.steps):
-            flush.zero_()
-            e0.record(stream)
-            for tc, t in zip(host_cols, dw.tables):
-                for hc, dc in zip(tc, t.cols):
-                    dc.copy_(hc, non_blocking=True)
-            step()
-            out_host.copy_(est_comb, non_blocking=True)
-            e1.record(stream)
-            e1.synchronize()
-            if k >= a.warmup:
-                tms.append(e0.elapsed_time(e1))
+        with torch.cuda.stream(stream):
+            for k in range(a.warmup + a.steps):
+                flush.zero_()
+                e0.record(stream)
+                for tc, t in zip(host_cols, dw.tables):
+                    for hc, dc in zip(tc, t.cols):
+                        dc.copy_(hc, non_blocking=True)
+                if graph is not None:
+                    graph.replay()
+                else:
+                    step()
+                out_host.copy_(est_comb, non_blocking=True)
+                e1.record(stream)
+                e1.synchronize()
+                if k >= a.warmup:
+                    tms.append(e0.elapsed_time(e1))
         e2e_ms = _max_over_ranks(statistics.mean(tms), world)
         e2e = {"value": rows * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(out_host.numel() * 8), "ms_per_step": e2e_ms}
@@ -520,6 +604,8 @@ def run_ours(a):
                            "sketches": sum(len(t.key_col) for t in wl.tables), "d": wl.d, "w": wl.w,
                            "subplans": n_est, "column_bytes": col_bytes,
                            "l2": "256 MB buffer written between steps, outside the per-step events",
+                           "step": "one captured CUDA graph replayed per step" if graph is not None else "eager launches",
+                           "phases": "from eager steps with events between phases",
                            "parallelism": f"replicas x{world} (independent queries)"},
                 "phases_ms": phase, "subplan_estimates_per_s": n_est / (phase["estimate"] / 1e3),
                 "autotuned": {"build": tuned_build["cfg"], "estimate": tuned_est["cfg"]},
@@ -536,8 +622,8 @@ def run_ours(a):
 def run_case(a):
     """Small profiling cases (one GPU): the estimate of all 19 sub-plans of the five-table
     graph at w = 4096 (tables at 5% scale; the estimate's cost depends on w and the sketch
-    values), or the fused build of the 36M-row F1 table alone (3 sketches, d = 11,
-    w = 4096)."""
+    values); the single-table fused build of the 36M-row F1 table alone (3 sketches, d = 11,
+    w = 4096, per-tuple path); or the benchmark's batched build of all five tables."""
     import torch
 
     from paper_2102_02440_gb300 import datagen as G
@@ -550,11 +636,15 @@ def run_case(a):
         est = P.DeviceEstimator(dw, G.connected_subplans(5, wl.edge_u, wl.edge_v))
         est.presort()
         fn = est.estimate
-    else:
+    elif a.case == "build_f1":
         full = G.five_table(scale=1.0, w=4096)
         wl = G.Workload("F1 only", [full.tables[0]], [0] * 5, [0] * 5, 11, 4096, full.hash_seed, 0)
         dw = P.DeviceWorkload(wl)
         fn = dw.build
+    else:  # build_five: the benchmark's batched build (key aggregation on F1, F2, D1, D3)
+        wl = G.five_table(scale=1.0, w=4096)
+        dw = P.DeviceWorkload(wl)
+        fn = dw.build_batched
     for r in range(2):
         s.record()
         fn()

@@ -249,6 +249,7 @@ struct BuildPlanParts {
   std::vector<int32_t> cnt_cta;
   std::vector<std::vector<int32_t>> col_agg;  // [table][col] AggCol index or -1
   size_t bytes = 0, ws_bytes = 0;
+  int32_t stat_grid = 0;
 };
 
 static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -287,6 +288,7 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
       a.col = c;
       a.cap = std::min<int64_t>(tb.n_rows, kAggMaxCap);
       a.off = 0;
+      a.stat_cta0 = a.stat_ncta = 0;
       P->col_agg[t][c] = int32_t(P->aggs.size());
       P->aggs.push_back(a);
     }
@@ -327,7 +329,7 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
         int32_t np = 0;
         for (int32_t p = b; p < e; p++) np += tb.key_col[p / d] == c;
         if (!np) continue;
-        const int64_t chunks = (P->aggs[ai].cap + R - 1) / R;
+        const int64_t chunks = (P->aggs[ai].cap + s.map_slots - 1) / s.map_slots;
         Raw ra{t, b, e, ai, chunks, double(chunks) * (1.0 + 0.25 * np)};
         total += ra.work;
         raw.push_back(ra);
@@ -374,6 +376,21 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
     ci.pad = 0;
     for (int64_t c = 0; c < n; c++) P->cnt_cta.push_back(int32_t(P->cnt_items.size()));
     P->cnt_items.push_back(ci);
+  }
+  // key-range pass: CTAs per column in proportion to its rows (about 8 per SM in all)
+  {
+    double rows_total = 0;
+    for (const AggCol& a : P->aggs) rows_total += double(tables[a.table].n_rows);
+    int32_t next = 0;
+    for (AggCol& a : P->aggs) {
+      const int64_t n = tables[a.table].n_rows;
+      int64_t k = int64_t(double(n) / std::max(rows_total, 1.0) * sm_count() * 8 + 0.5);
+      k = std::max<int64_t>(1, std::min<int64_t>(k, (n + 4095) / 4096));
+      a.stat_cta0 = next;
+      a.stat_ncta = int32_t(k);
+      next += int32_t(k);
+    }
+    P->stat_grid = next;
   }
   s.grid = int32_t(P->cta_item.size());
   s.ctas_per_slab = 0;
@@ -442,6 +459,7 @@ extern "C" cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_t
   off += align16(sizeof(CountItem) * P.cnt_items.size());
   h.off_cnt_cta = int64_t(off);
   h.cnt_grid = int32_t(P.cnt_cta.size());
+  h.stat_grid = P.stat_grid;
   h.ws_bytes = int64_t(P.ws_bytes);
   h.total_bytes = int64_t(P.bytes);
   std::vector<ZeroSpan> zs;
@@ -497,7 +515,7 @@ extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void
     a.cnt_cta_item = reinterpret_cast<const int32_t*>(dev + h.off_cnt_cta);
     // the (max, min) stats start from zero (decoding as an empty column)
     if (cudaMemsetAsync(ws_dev, 0, 16 * size_t(h.n_agg), cs) != cudaSuccess) return CMP_ECUDA;
-    if (launch_agg(a, h.shape, h.cnt_grid, cs) != cudaSuccess) return CMP_ECUDA;
+    if (launch_agg(a, h.shape, h.stat_grid, h.cnt_grid, cs) != cudaSuccess) return CMP_ECUDA;
   }
   return launch_build(a, h.shape, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
 }

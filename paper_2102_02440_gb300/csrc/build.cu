@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -210,6 +211,21 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
   // Hash the first n_entries (field element, count) entries of mkey / mcnt for the pairs
   // of key column kc, or (no map) the keys of the tile's first n_entries survivors.  Two
   // entries per thread share every parameter load: two independent hash chains.
+  auto hash_pairs = [&](auto smallx, const KeyPow& k0, const KeyPow& k1, int32_t m0, int32_t m1, int pl_begin,
+                        int pl_end) {
+    constexpr bool SMALLX = decltype(smallx)::value;
+    for (int j = pl_begin; j < pl_end; j++) {
+      const int pp = plist[j];
+      const PairParam q = prm[pp];
+      const uint32_t h0 = cw_bucket<POW2, SMALLX>(q, k0, uint32_t(w));
+      const uint32_t h1 = cw_bucket<POW2, SMALLX>(q, k1, uint32_t(w));
+      const int32_t v0 = cw_sign<SMALLX>(q, k0) * m0;
+      const int32_t v1 = cw_sign<SMALLX>(q, k1) * m1;
+      int32_t* row = (GLOBAL ? gcnt : cnt) + size_t(pp) * w;
+      atomicAdd(row + h0, v0);
+      if (m1) atomicAdd(row + h1, v1);
+    }
+  };
   auto hash_entries = [&](int kc, int n_entries, const void* kbase, int32_t kdt, int64_t r0, bool from_map) {
     const int pl_begin = colstart[kc], pl_end = colstart[kc + 1];
     for (int e0 = tid; e0 < n_entries; e0 += 2 * T) {
@@ -227,17 +243,11 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
       }
       const KeyPow k0 = key_powers(x0);
       const KeyPow k1 = key_powers(x1);
-      for (int j = pl_begin; j < pl_end; j++) {
-        const int pp = plist[j];
-        const PairParam q = prm[pp];
-        const uint32_t h0 = cw_bucket<POW2>(q, k0, uint32_t(w));
-        const uint32_t h1 = cw_bucket<POW2>(q, k1, uint32_t(w));
-        const int32_t v0 = cw_sign(q, k0) * m0;
-        const int32_t v1 = cw_sign(q, k1) * m1;
-        int32_t* row = (GLOBAL ? gcnt : cnt) + size_t(pp) * w;
-        atomicAdd(row + h0, v0);
-        if (m1) atomicAdd(row + h1, v1);
-      }
+      // keys below 2^31 (every non-negative int32 key) have a zero high limb
+      if (__all_sync(__activemask(), (k0.x.hi | k1.x.hi) == 0))
+        hash_pairs(std::true_type{}, k0, k1, m0, m1, pl_begin, pl_end);
+      else
+        hash_pairs(std::false_type{}, k0, k1, m0, m1, pl_begin, pl_end);
     }
   };
 
@@ -251,10 +261,10 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
         if (cols_list[k] == ac.col) kc = k;
       if (kc >= 0 && agg_active(ac, agg_item, A.ws, &kmin, &range)) {
         const int32_t* cnts = reinterpret_cast<const int32_t*>(A.ws + ac.off);
-        const int64_t n_chunks = (range + R - 1) / R;
+        const int64_t n_chunks = (range + M - 1) / M;  // chunks of the entry lists' capacity
         for (int64_t chunk = cta_in_slab; chunk < n_chunks; chunk += n_ctas) {
-          const int64_t i0 = chunk * R;
-          const int nin = int(min(int64_t(R), range - i0));
+          const int64_t i0 = chunk * M;
+          const int nin = int(min(int64_t(M), range - i0));
           if (tid == 0) sint[0] = 0;
           __syncthreads();
           for (int base = 0; base < nin; base += T) {  // block-uniform trip count
@@ -422,26 +432,39 @@ cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t s
 
 // ---------------------------------------------------------------- key aggregation
 // Smallest and largest key of every aggregated column over all its rows (a bound on the
-// survivors' keys); grid.y = column.
-__global__ void __launch_bounds__(256) k_agg_stats(const __grid_constant__ BuildArgs A) {
-  const int ai = int(blockIdx.y);
+// survivors' keys).  Column a is read by CTAs [stat_cta0, stat_cta0 + stat_ncta), each
+// one contiguous slice, four 4-row loads in flight per thread.
+constexpr int kStatThreads = 256;
+
+__global__ void __launch_bounds__(kStatThreads) k_agg_stats(const __grid_constant__ BuildArgs A) {
+  __shared__ long long red[2][kStatThreads / 32];
+  int ai = 0;
+  while (ai + 1 < A.n_agg && A.agg[ai + 1].stat_cta0 <= int(blockIdx.x)) ai++;
   const AggCol ac = A.agg[ai];
   const DevTable* tb = A.tables + ac.table;
   const void* base = tb->col[ac.col];
   const int32_t dt = tb->dtype[ac.col];
   const bool vec = tb->vec_ok != 0;
   const int64_t n = tb->n_rows;
+  const int64_t per = ((n + ac.stat_ncta - 1) / ac.stat_ncta + 15) & ~int64_t(15);  // rows per CTA, x16
+  const int64_t r_begin = min(n, per * (int64_t(blockIdx.x) - ac.stat_cta0)), r_end = min(n, r_begin + per);
   int64_t mn = INT64_MAX, mx = INT64_MIN;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x * 4;
-  for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4; r < n; r += stride) {
-    int64_t v[4];
-    const int nvalid = int(min(int64_t(4), n - r));
-    load4(base, dt, r, nvalid, vec, v);
+  for (int64_t r = r_begin + 16 * int64_t(threadIdx.x); r < r_end; r += 16 * int64_t(blockDim.x)) {
+    int64_t v[4][4];
 #pragma unroll
-    for (int k = 0; k < 4; k++)
-      if (k < nvalid) {
-        mn = min(mn, v[k]);
-        mx = max(mx, v[k]);
+    for (int u = 0; u < 4; u++) {
+      const int nvalid = int(max(int64_t(0), min(int64_t(4), r_end - (r + 4 * u))));
+      load4(base, dt, r + 4 * u, nvalid, vec, v[u]);
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if (k >= nvalid) v[u][k] = v[0][0];  // padding repeats row r, valid inside the loop
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        mn = min(mn, v[u][k]);
+        mx = max(mx, v[u][k]);
       }
   }
 #pragma unroll
@@ -449,10 +472,22 @@ __global__ void __launch_bounds__(256) k_agg_stats(const __grid_constant__ Build
     mn = min(mn, (int64_t)__shfl_down_sync(0xffffffffu, (long long)mn, off));
     mx = max(mx, (int64_t)__shfl_down_sync(0xffffffffu, (long long)mx, off));
   }
-  if ((threadIdx.x & 31) == 0 && mx >= mn) {
-    unsigned long long* st = reinterpret_cast<unsigned long long*>(A.ws) + 2 * int64_t(ai);
-    atomicMax(st, (unsigned long long)enc_max(mx));
-    atomicMax(st + 1, (unsigned long long)enc_min(mn));
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][warp] = mn;
+    red[1][warp] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < int(blockDim.x >> 5); q++) {
+      mn = min(mn, int64_t(red[0][q]));
+      mx = max(mx, int64_t(red[1][q]));
+    }
+    if (mx >= mn) {
+      unsigned long long* st = reinterpret_cast<unsigned long long*>(A.ws) + 2 * int64_t(ai);
+      atomicMax(st, (unsigned long long)enc_max(mx));
+      atomicMax(st + 1, (unsigned long long)enc_min(mn));
+    }
   }
 }
 
@@ -469,8 +504,12 @@ __global__ void __launch_bounds__(256) k_agg_zero(const __grid_constant__ BuildA
 }
 
 // Per tile of a table with aggregated columns: survivors (phase A), then for every active
-// column the tile's keys reduced in a shared-memory map (key - min -> count; equal keys of
-// a warp inserted once by __match_any_sync) and one global atomic per occupied slot.
+// column the tile's keys reduced in a shared-memory map and one global atomic per
+// occupied slot.  A slot packs (key - min) in its high 32 bits and the tile count in its
+// low 32 bits (a count never exceeds the tile's rows), so an insert is one atomic: a CAS
+// that claims an empty slot with the count, or an add to a slot holding the key.  Equal
+// keys of a warp are inserted once, by their lowest lane (__match_any_sync).  The flush
+// also empties the slots, so the map is cleared once per CTA.
 __global__ void __launch_bounds__(1024) k_agg_count(const __grid_constant__ BuildArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const CountItem it = A.cnt_items[A.cnt_cta_item[blockIdx.x]];
@@ -478,19 +517,20 @@ __global__ void __launch_bounds__(1024) k_agg_count(const __grid_constant__ Buil
   const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
   const int R = A.tile_rows, M = A.map_slots;
   unsigned char* sp = smem;
-  uint32_t* mkey = reinterpret_cast<uint32_t*>(sp);
-  sp += align16(sizeof(uint32_t) * size_t(M));
-  int32_t* mcnt = reinterpret_cast<int32_t*>(sp);
-  sp += align16(sizeof(int32_t) * size_t(M));
+  unsigned long long* slot64 = reinterpret_cast<unsigned long long*>(sp);
+  sp += align16(sizeof(unsigned long long) * size_t(M));
   uint16_t* surv = reinterpret_cast<uint16_t*>(sp);
   sp += align16(sizeof(uint16_t) * R);
   int32_t* sint = reinterpret_cast<int32_t*>(sp);
-  constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // never an index: cap <= 2^31 - 1
+  constexpr unsigned long long kEmpty = ~0ull;  // key part 0xFFFFFFFF is never an index: cap <= 2^31 - 1
   const int64_t n_rows = tb->n_rows;
   const int64_t n_tiles = (n_rows + R - 1) / R;
   const int n_preds = tb->n_preds;
   const bool vec = tb->vec_ok != 0;
   const int cta = int(blockIdx.x) - it.first_cta;
+  const uint32_t mmask = uint32_t(M - 1);
+  for (int s = tid; s < M; s += T) slot64[s] = kEmpty;
+  __syncthreads();
   for (int64_t tile = cta; tile < n_tiles; tile += it.n_ctas) {
     const int64_t r0 = tile * R;
     const int rows_in_tile = int(min(int64_t(R), n_rows - r0));
@@ -503,49 +543,57 @@ __global__ void __launch_bounds__(1024) k_agg_count(const __grid_constant__ Buil
       int32_t* cnts = reinterpret_cast<int32_t*>(A.ws + A.agg[ai].off);
       const void* kbase = tb->col[c];
       const int32_t kdt = tb->dtype[c];
-      for (int s = tid; s < M; s += T) {
-        mkey[s] = kEmpty;
-        mcnt[s] = 0;
-      }
-      __syncthreads();
-      const uint32_t mmask = uint32_t(M - 1);
       for (int base = 0; base < n_surv; base += T) {  // block-uniform trip count
         const int e = base + tid;
         const bool valid = e < n_surv;
-        uint32_t x = kEmpty;
+        uint32_t x = 0xFFFFFFFFu;
         if (valid) x = uint32_t(load1(kbase, kdt, r0 + (n_preds ? surv[e] : e)) - kmin);  // < range <= cap
         const unsigned peers = __match_any_sync(0xffffffffu, x);
         if (!valid || lane != __ffs(peers) - 1) continue;
+        const unsigned long long cnt = (unsigned long long)__popc(peers);
         uint32_t slot = map_slot(x, mmask);
         bool done = false;
-        for (int probe = 0; probe < M; probe++) {
-          const uint32_t prev = atomicCAS(&mkey[slot], kEmpty, x);
-          if (prev == kEmpty || prev == x) {
-            atomicAdd(&mcnt[slot], __popc(peers));
+        for (int probe = 0; probe < M && !done; probe++) {
+          const unsigned long long cur = slot64[slot];
+          if (uint32_t(cur >> 32) == x) {
+            atomicAdd(&slot64[slot], cnt);
             done = true;
-            break;
+          } else if (cur == kEmpty) {
+            const unsigned long long prev = atomicCAS(&slot64[slot], kEmpty, ((unsigned long long)x << 32) | cnt);
+            if (prev == kEmpty) {
+              done = true;
+            } else if (uint32_t(prev >> 32) == x) {
+              atomicAdd(&slot64[slot], cnt);
+              done = true;
+            }
           }
-          slot = (slot + 1) & mmask;
+          if (!done) slot = (slot + 1) & mmask;
         }
         if (!done) set_status(A.status, CMP_ETIMEOUT);  // unreachable: M > tile rows
       }
       __syncthreads();
-      for (int s = tid; s < M; s += T)
-        if (mkey[s] != kEmpty) atomicAdd(cnts + mkey[s], mcnt[s]);
+      for (int s = tid; s < M; s += T) {
+        const unsigned long long v = slot64[s];
+        if (v != kEmpty) {
+          atomicAdd(cnts + uint32_t(v >> 32), int32_t(uint32_t(v)));
+          slot64[s] = kEmpty;
+        }
+      }
       __syncthreads();  // map reused next
     }
   }
 }
 
 size_t agg_count_smem_bytes(const BuildShape& s) {
-  return align16(sizeof(uint32_t) * size_t(s.map_slots)) + align16(sizeof(int32_t) * size_t(s.map_slots)) +
-         align16(sizeof(uint16_t) * s.tile_rows) + sizeof(int32_t) * 40;
+  return align16(sizeof(unsigned long long) * size_t(s.map_slots)) + align16(sizeof(uint16_t) * s.tile_rows) +
+         sizeof(int32_t) * 40;
 }
 
-cudaError_t launch_agg(const BuildArgs& a, const BuildShape& s, int32_t cnt_grid, cudaStream_t st) {
+cudaError_t launch_agg(const BuildArgs& a, const BuildShape& s, int32_t stat_grid, int32_t cnt_grid,
+                       cudaStream_t st) {
   if (a.n_agg <= 0) return cudaSuccess;
-  const dim3 g(unsigned(std::max(1, 2 * sm_count() / std::max(1, a.n_agg))), unsigned(a.n_agg));
-  k_agg_stats<<<g, 256, 0, st>>>(a);
+  k_agg_stats<<<unsigned(stat_grid), kStatThreads, 0, st>>>(a);
+  const dim3 g(unsigned(std::max(1, 4 * sm_count() / std::max(1, a.n_agg))), unsigned(a.n_agg));
   k_agg_zero<<<g, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || cnt_grid <= 0) return e;

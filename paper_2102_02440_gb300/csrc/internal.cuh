@@ -83,11 +83,13 @@ __device__ __forceinline__ KeyPow key_powers(uint64_t x) {
 
 // Bucket: ((a x + b) mod p) mod w.  Sum bound: t0 + (t1>>30) + ((t1&M30)<<31) + 2 t2 + b
 // < 2^62 + 2^32 + 3 * 2^61 < 2^64.
-template <bool POW2>
+// SMALLX: the caller guarantees x < 2^31 (k.x.hi == 0), so the products with x.hi, which
+// are zero, are left out (same value, fewer multiplies).
+template <bool POW2, bool SMALLX = false>
 __device__ __forceinline__ uint32_t cw_bucket(const PairParam& q, const KeyPow& k, uint32_t w) {
   const uint64_t t0 = uint64_t(q.a_lo) * k.x.lo;
-  const uint64_t t1 = uint64_t(q.a_lo) * k.x.hi + uint64_t(q.a_hi) * k.x.lo;
-  const uint64_t t2 = uint64_t(q.a_hi) * k.x.hi;
+  const uint64_t t1 = SMALLX ? uint64_t(q.a_hi) * k.x.lo : uint64_t(q.a_lo) * k.x.hi + uint64_t(q.a_hi) * k.x.lo;
+  const uint64_t t2 = SMALLX ? 0 : uint64_t(q.a_hi) * k.x.hi;
   const uint64_t s = t0 + (t1 >> 30) + ((t1 & kM30) << 31) + 2 * t2 + q.b;
   const uint64_t r = canon61(fold61(s));
   if (POW2) return uint32_t(r) & (w - 1);
@@ -97,11 +99,14 @@ __device__ __forceinline__ uint32_t cw_bucket(const PairParam& q, const KeyPow& 
 // Sign: parity of (c3 x^3 + c2 x^2 + c1 x + c0) mod p, as +1 / -1.  The three products
 // are summed by limb position: S0 < 3 * 2^62, S1 < 6 * 2^61, S2 < 3 * 2^60, and
 // fold(S0) + (S1>>30) + ((S1&M30)<<31) + 2 S2 + c0 < 6 * 2^61 + 2^35 < 2^64.
+template <bool SMALLX = false>
 __device__ __forceinline__ int cw_sign(const PairParam& q, const KeyPow& k) {
   const uint64_t S0 = uint64_t(q.c1_lo) * k.x.lo + uint64_t(q.c2_lo) * k.x2.lo + uint64_t(q.c3_lo) * k.x3.lo;
-  const uint64_t S1 = uint64_t(q.c1_lo) * k.x.hi + uint64_t(q.c1_hi) * k.x.lo + uint64_t(q.c2_lo) * k.x2.hi +
-                      uint64_t(q.c2_hi) * k.x2.lo + uint64_t(q.c3_lo) * k.x3.hi + uint64_t(q.c3_hi) * k.x3.lo;
-  const uint64_t S2 = uint64_t(q.c1_hi) * k.x.hi + uint64_t(q.c2_hi) * k.x2.hi + uint64_t(q.c3_hi) * k.x3.hi;
+  const uint64_t S1 = (SMALLX ? 0 : uint64_t(q.c1_lo) * k.x.hi) + uint64_t(q.c1_hi) * k.x.lo +
+                      uint64_t(q.c2_lo) * k.x2.hi + uint64_t(q.c2_hi) * k.x2.lo + uint64_t(q.c3_lo) * k.x3.hi +
+                      uint64_t(q.c3_hi) * k.x3.lo;
+  const uint64_t S2 = (SMALLX ? 0 : uint64_t(q.c1_hi) * k.x.hi) + uint64_t(q.c2_hi) * k.x2.hi +
+                      uint64_t(q.c3_hi) * k.x3.hi;
   const uint64_t v = fold61(S0) + (S1 >> 30) + ((S1 & kM30) << 31) + 2 * S2 + q.c0;
   const uint64_t r = canon61(fold61(v));
   return 1 - 2 * int(r & 1);
@@ -140,6 +145,7 @@ struct AggCol {
   int32_t table, col;
   int64_t cap;  // count slots
   int64_t off;  // byte offset of the count array in the workspace
+  int32_t stat_cta0, stat_ncta;  // CTAs of the key-range pass reading this column
 };
 
 // Order-preserving maps of an int64 to uint64, for atomicMax on the stats pairs (both
@@ -219,7 +225,7 @@ struct BuildPlanHdr {
   int64_t total_bytes;
   int64_t n_agg, off_agg;                            // aggregated key columns
   int64_t n_cnt_items, off_cnt_items, off_cnt_cta;  // counting pass
-  int32_t cnt_grid, pad;
+  int32_t cnt_grid, stat_grid;
   int64_t ws_bytes;
 };
 constexpr int32_t kBuildPlanVersion = 2;
@@ -240,7 +246,7 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 size_t build_smem_bytes(const BuildShape& s, int w);
 cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t st);
 size_t agg_count_smem_bytes(const BuildShape& s);
-cudaError_t launch_agg(const BuildArgs& a, const BuildShape& s, int32_t cnt_grid, cudaStream_t st);
+cudaError_t launch_agg(const BuildArgs& a, const BuildShape& s, int32_t stat_grid, int32_t cnt_grid, cudaStream_t st);
 cudaError_t launch_zero_spans(const ZeroSpan* spans_dev, int32_t n, cudaStream_t st);
 
 int sm_count();
