@@ -199,6 +199,15 @@ cmp_status cmp_presort(const int32_t* counters_dev, int64_t n_rows, int32_t w, u
 cmp_status cmp_cross_ranks(const uint32_t* abs_sorted_dev, const int32_t* perm_dev, int32_t k, int32_t d, int32_t w,
                            const int32_t* edge_id_host, int32_t* ranks_dev, void* stream);
 
+/* cmp_cross_ranks of n_tables tables in one launch.  Table t has k_host[t] sketches (0 to
+ * CMP_MAX_SKETCHES) and owns, in order, the next k_t * d presorted rows of abs_sorted_dev /
+ * perm_dev and the next k_t * k_t * d * w int32 of ranks_dev; edge_ids_host holds the
+ * tables' edge ids back to back (sum of k_t entries).  Results equal one cmp_cross_ranks
+ * call per table.  CMP_EINVAL for bad sizes or a total of CTAs (sum k_t^2 d) >= 2^31. */
+cmp_status cmp_cross_ranks_multi(const uint32_t* abs_sorted_dev, const int32_t* perm_dev, int32_t n_tables,
+                                 const int32_t* k_host, const int32_t* edge_ids_host, int32_t d, int32_t w,
+                                 int32_t* ranks_dev, void* stream);
+
 /* A join graph whose sketches have been built and presorted.  Edge e joins tables
  * edge_u[e] and edge_v[e]; endpoint 0 is the edge_u side, 1 the edge_v side.  All
  * arrays are HOST arrays; entries of sketch/abs_sorted/perm are DEVICE pointers to the
@@ -213,7 +222,8 @@ typedef struct {
   const uint32_t* const* abs_sorted; /* [2 * n_edges] */
   const int32_t* const* perm;        /* [2 * n_edges] */
   const int32_t* const* ranks;       /* [2 * n_edges]: the endpoint table's cmp_cross_ranks block of this sketch,
-                                        ranks_dev + x * d * w for the endpoint's sketch index x */
+                                        ranks_dev + x * k * d * w for the endpoint's sketch index x of its
+                                        table's k sketches */
   const int32_t* slot;               /* [2 * n_edges]: the endpoint's sketch index x within its table (host) */
   const int64_t* survivors_dev;      /* device [n_tables]: exact selected counts */
 } cmp_graph;

@@ -91,6 +91,8 @@ _SIGS = {
                                 C.c_void_p]),
     "cmp_cross_ranks": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                     C.POINTER(C.c_int32), C.c_void_p, C.c_void_p]),
+    "cmp_cross_ranks_multi": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "cmp_estimate_plan_bytes": (C.c_int32, [C.POINTER(cmp_graph), C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                             C.c_void_p, C.c_void_p, C.POINTER(cmp_estimate_cfg),
                                             C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
@@ -222,6 +224,13 @@ def cmp_presort(counters_dev: int, n_rows: int, w: int, abs_sorted_dev: int, per
 def cmp_cross_ranks(abs_dev: int, perm_dev: int, k: int, d: int, w: int, edge_ids, ranks_dev: int, stream: int):
     e = (C.c_int32 * max(k, 1))(*edge_ids)
     _check("cmp_cross_ranks", lib().cmp_cross_ranks(abs_dev, perm_dev, k, d, w, e, ranks_dev, stream))
+
+
+def cmp_cross_ranks_multi(abs_dev: int, perm_dev: int, ks, edge_ids, d: int, w: int, ranks_dev: int, stream: int):
+    kk = (C.c_int32 * max(len(ks), 1))(*ks)
+    ee = (C.c_int32 * max(len(edge_ids), 1))(*edge_ids)
+    _check("cmp_cross_ranks_multi",
+           lib().cmp_cross_ranks_multi(abs_dev, perm_dev, len(ks), kk, ee, d, w, ranks_dev, stream))
 
 
 def cmp_estimate_plan_bytes(graphs, d: int, w: int, sub_graph, sub_mask, cfg: cmp_estimate_cfg | None = None):

@@ -364,6 +364,24 @@ cmp_status cmp_cross_ranks(const uint32_t* abs_sorted_dev, const int32_t* perm_d
              : CMP_ECUDA;
 }
 
+cmp_status cmp_cross_ranks_multi(const uint32_t* abs_sorted_dev, const int32_t* perm_dev, int32_t n_tables,
+                                 const int32_t* k_host, const int32_t* edge_ids_host, int32_t d, int32_t w,
+                                 int32_t* ranks_dev, void* stream) {
+  if (n_tables < 0 || d < 1 || w < 1 || w > CMP_MAX_W || (n_tables > 0 && !k_host)) return CMP_EINVAL;
+  int64_t blocks = 0, nk = 0;
+  for (int32_t t = 0; t < n_tables; t++) {
+    if (k_host[t] < 0 || k_host[t] > CMP_MAX_SKETCHES) return CMP_EINVAL;
+    blocks += int64_t(k_host[t]) * k_host[t] * d;
+    nk += k_host[t];
+  }
+  if (blocks >= (int64_t(1) << 31)) return CMP_EINVAL;
+  if (nk > 0 && (!abs_sorted_dev || !perm_dev || !edge_ids_host || !ranks_dev)) return CMP_EINVAL;
+  return launch_cross_ranks_multi(abs_sorted_dev, perm_dev, n_tables, k_host, edge_ids_host, d, w, ranks_dev,
+                                  reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? CMP_OK
+             : CMP_ECUDA;
+}
+
 cmp_status cmp_presort(const int32_t* counters_dev, int64_t n_rows, int32_t w, uint32_t* abs_sorted_dev,
                        int32_t* perm_dev, void* ws_dev, size_t ws_bytes, void* stream) {
   if (n_rows < 0 || w < 1 || w > CMP_MAX_W) return CMP_EINVAL;

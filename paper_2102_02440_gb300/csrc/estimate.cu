@@ -251,6 +251,73 @@ __global__ void k_cross_ranks(const __grid_constant__ CrossArgs A) {
   for (int r = threadIdx.x; r < w; r += blockDim.x) out[r] = rank_in(ay, w, __ldg(ax + r), strict);
 }
 
+// Several tables per launch: table t's CTAs are [blk0[t], blk0[t + 1]), its rows start at
+// row_off[t] of abs / perm and its rank block at rank_off[t] (int32 units).
+constexpr int kCrossMultiTables = 16;
+struct CrossMultiArgs {
+  const uint32_t* abs;
+  const int32_t* perm;
+  int32_t* ranks;
+  int32_t n, d, w;
+  int64_t blk0[kCrossMultiTables + 1];
+  int64_t row_off[kCrossMultiTables], rank_off[kCrossMultiTables];
+  int32_t k[kCrossMultiTables];
+  int32_t edge[kCrossMultiTables][CMP_MAX_SKETCHES];
+};
+
+__global__ void k_cross_ranks_multi(const __grid_constant__ CrossMultiArgs A) {
+  const int64_t blk = blockIdx.x;
+  int t = 0;
+  while (t + 1 < A.n && A.blk0[t + 1] <= blk) t++;
+  const int k = A.k[t], d = A.d, w = A.w;
+  const int64_t b = blk - A.blk0[t];
+  const int row = int(b % d), y = int((b / d) % k), x = int(b / (int64_t(d) * k));
+  int32_t* out = A.ranks + A.rank_off[t] + ((int64_t(x) * k + y) * d + row) * w;
+  if (x == y) {
+    const int32_t* perm = A.perm + (A.row_off[t] + int64_t(x) * d + row) * w;
+    for (int r = threadIdx.x; r < w; r += blockDim.x) out[__ldg(perm + r)] = r;
+    return;
+  }
+  const uint32_t* ax = A.abs + (A.row_off[t] + int64_t(x) * d + row) * w;
+  const uint32_t* ay = A.abs + (A.row_off[t] + int64_t(y) * d + row) * w;
+  const bool strict = A.edge[t][y] < A.edge[t][x];
+  for (int r = threadIdx.x; r < w; r += blockDim.x) out[r] = rank_in(ay, w, __ldg(ax + r), strict);
+}
+
+cudaError_t launch_cross_ranks_multi(const uint32_t* abs, const int32_t* perm, int32_t n_tables, const int32_t* k,
+                                     const int32_t* edge_ids, int32_t d, int32_t w, int32_t* ranks, cudaStream_t st) {
+  int64_t row = 0, rank = 0, e = 0;
+  for (int32_t t0 = 0; t0 < n_tables; t0 += kCrossMultiTables) {
+    CrossMultiArgs a;
+    a.abs = abs;
+    a.perm = perm;
+    a.ranks = ranks;
+    a.n = n_tables - t0 < kCrossMultiTables ? n_tables - t0 : kCrossMultiTables;
+    a.d = d;
+    a.w = w;
+    int64_t blk = 0;
+    for (int i = 0; i < a.n; i++) {
+      const int32_t kt = k[t0 + i];
+      a.blk0[i] = blk;
+      a.row_off[i] = row;
+      a.rank_off[i] = rank;
+      a.k[i] = kt;
+      for (int q = 0; q < CMP_MAX_SKETCHES; q++) a.edge[i][q] = q < kt ? edge_ids[e + q] : 0;
+      blk += int64_t(kt) * kt * d;
+      row += int64_t(kt) * d;
+      rank += int64_t(kt) * kt * d * w;
+      e += kt;
+    }
+    a.blk0[a.n] = blk;
+    if (blk > 0) {
+      k_cross_ranks_multi<<<unsigned(blk), 256, 0, st>>>(a);
+      const cudaError_t err = cudaGetLastError();
+      if (err != cudaSuccess) return err;
+    }
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_cross_ranks(const uint32_t* abs, const int32_t* perm, int32_t k, int32_t d, int32_t w,
                                const int32_t* edge_id, int32_t* ranks, cudaStream_t st) {
   if (k <= 0) return cudaSuccess;

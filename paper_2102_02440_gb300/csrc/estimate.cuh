@@ -66,7 +66,7 @@ constexpr int32_t kTriCols = 256;     // columns per sweep item (one per thread)
 
 // Per triangle row (sub-plan, sketch row) scratch, in bytes, and its regions.
 struct TriLayout {
-  int64_t hdr, vec, sg, pre, rkx, rpre, cky, ccol, qs, qr, qpre, gr, gqb, bytes;
+  int64_t hdr, vec, tmp, sg, pre, rkx, rpre, cky, ccol, qs, qr, qpre, gr, gqb, bytes;
 };
 __host__ __device__ inline int64_t tri_al(int64_t x) { return (x + 255) & ~int64_t(255); }
 __host__ __device__ inline TriLayout tri_layout(int32_t w, int32_t max_leaves) {
@@ -75,6 +75,7 @@ __host__ __device__ inline TriLayout tri_layout(int32_t w, int32_t max_leaves) {
   int64_t o = 0;
   L.hdr = o;  o += tri_al(64);
   L.vec = o;  o += tri_al(16 * 6 * int64_t(w));   // phiU psiU phiV psiV f g, bucket order
+  L.tmp = o;  o += tri_al(16 * int64_t(w));       // leaf-term sums of one node message
   L.sg = o;   o += tri_al(8 * nl * W1);          // leaf suffix sums
   L.pre = o;  o += tri_al(16 * nl * W1);         // leaf "attains the minimum" prefix sums
   L.rkx = o;  o += tri_al(8 * int64_t(w));       // row keys, sorted within batches
@@ -221,5 +222,7 @@ cudaError_t launch_estimate(const EstArgs& a, double* est, int64_t* row_est, cud
 cudaError_t launch_estimate_tri(const EstArgs& a, cudaStream_t st);
 cudaError_t launch_cross_ranks(const uint32_t* abs, const int32_t* perm, int32_t k, int32_t d, int32_t w,
                                const int32_t* edge_id, int32_t* ranks, cudaStream_t st);
+cudaError_t launch_cross_ranks_multi(const uint32_t* abs, const int32_t* perm, int32_t n_tables, const int32_t* k,
+                                     const int32_t* edge_ids, int32_t d, int32_t w, int32_t* ranks, cudaStream_t st);
 
 }  // namespace cmpk

@@ -60,6 +60,7 @@ __device__ __forceinline__ uint32_t mag32(int32_t v) { return v < 0 ? uint32_t(-
 struct TriPtrs {
   int32_t* hdr;  // [0] groups G, [1] queries, [2] overflow in the preparation
   i128* vec;     // [6][w]: phiU psiU phiV psiV f g, in bucket order
+  i128* tmp;     // [w]
   int64_t* sg;   // [3 * max_leaves][w+1]
   i128* pre;     // [3 * max_leaves][w+1]
   uint64_t* rkx;
@@ -78,6 +79,7 @@ __device__ TriPtrs tri_ptrs(unsigned char* base, int w, int max_leaves) {
   TriPtrs p;
   p.hdr = reinterpret_cast<int32_t*>(base + L.hdr);
   p.vec = reinterpret_cast<i128*>(base + L.vec);
+  p.tmp = reinterpret_cast<i128*>(base + L.tmp);
   p.sg = reinterpret_cast<int64_t*>(base + L.sg);
   p.pre = reinterpret_cast<i128*>(base + L.pre);
   p.rkx = reinterpret_cast<uint64_t*>(base + L.rkx);
@@ -109,32 +111,63 @@ __device__ void bitonic_sort(unsigned long long* key, int n2) {
     }
 }
 
+// Copies a presorted magnitude row into shared memory (block-wide, ends with a barrier).
+__device__ void stage_row(const uint32_t* __restrict__ src, uint32_t* dst, int w) {
+  for (int r = threadIdx.x; r < w; r += blockDim.x) dst[r] = __ldg(src + r);
+  __syncthreads();
+}
+
+// First position q in the sorted shared-memory row a[0..w) with a[q] > tau (strict) or
+// a[q] >= tau: the number of the row's values that beat tau.
+__device__ __forceinline__ int rank_sh(const uint32_t* a, int w, uint32_t tau, bool strict) {
+  int lo = 0, hi = w;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const uint32_t v = a[mid];
+    if (strict ? v <= tau : v < tau) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // Message of triangle node n with the fixed input a (every input but ia, ib is a leaf),
-// for every bucket of a's edge.
+// for every bucket of a's edge: out[j] = x prod_l SG_l[q_l] + sum_l PRE_l[q_l], one leaf
+// at a time with the leaf's magnitudes staged in shared memory (stage: w uint32).
 __device__ void node_msg(const EstArgs& A, const TriNode& nd, int n, int a, const TriPtrs& P, int64_t ro, i128* out,
-                         int32_t* flag) {
+                         uint32_t* stage, int32_t* flag) {
   const int w = A.w;
   const int64_t W1 = int64_t(w) + 1;
   const EstIn* in = A.inputs + nd.in_begin;
   const int32_t* sa = in[a].s + ro;
   bool o = false;
   for (int j = threadIdx.x; j < w; j += blockDim.x) {
-    const int32_t x = __ldg(sa + j);
-    const uint32_t tau = mag32(x);
-    i128 v = i128(x), acc = 0;
-    for (int l = 0, li = 0; l < nd.k; l++) {
-      if (l == nd.ia || l == nd.ib) continue;
+    out[j] = i128(__ldg(sa + j));
+    P.tmp[j] = 0;
+  }
+  for (int l = 0, li = 0; l < nd.k; l++) {
+    if (l == nd.ia || l == nd.ib) continue;
+    __syncthreads();  // the previous leaf's readers are done with the stage
+    stage_row(in[l].abs + ro, stage, w);
+    const int64_t slot = (int64_t(n) * A.tri_max_leaves + li) * W1;
+    for (int j = threadIdx.x; j < w; j += blockDim.x) {
+      const int32_t x = __ldg(sa + j);
       // leaf values that beat x: |y| < |x|, or |y| == |x| with l before a
-      const int q = rank_of(in[l].abs + ro, w, tau, l < a);
-      const int64_t slot = (int64_t(n) * A.tri_max_leaves + li) * W1;
+      const int q = rank_sh(stage, w, mag32(x), l < a);
+      i128 v = out[j], acc = P.tmp[j];
       if (v != 0) o |= mul_ovf_64(v, P.sg[slot + q], &v);
       o |= add_ovf(acc, P.pre[slot + q], &acc);
-      li++;
+      out[j] = v;
+      P.tmp[j] = acc;
     }
-    o |= add_ovf(v, acc, &v);
+    li++;
+  }
+  for (int j = threadIdx.x; j < w; j += blockDim.x) {
+    i128 v = out[j];
+    o |= add_ovf(v, P.tmp[j], &v);
     out[j] = v;
   }
   if (o) atomicOr(flag, 1);
+  __syncthreads();
 }
 
 // Exclusive scan of the 0/1 flags at[0..n) (thread-contiguous ranges).  Returns this
@@ -212,7 +245,9 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
       li++;
     }
   }
-  // ---- leaves: prefix sums of the terms in which leaf l attains the minimum
+  // ---- leaves: prefix sums of the terms in which leaf l attains the minimum: value times
+  // leaf message, times every other leaf's suffix sum at that value (other leaf staged)
+  uint32_t* stage = reinterpret_cast<uint32_t*>(key);  // 2 * wp2 uint32 before the sorts use it
   for (int n = 0; n < 3; n++) {
     const TriNode nd = ts.node[n];
     for (int l = 0, li = 0; l < nd.k; l++) {
@@ -220,21 +255,26 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
       const EstIn& x = inputs[nd.in_begin + l];
       i128* pre = P.pre + (int64_t(n) * A.tri_max_leaves + li) * W1;
       const int32_t* perm = x.perm + ro;
-      bool o = false;
       for (int r = tid; r < w; r += T) {
         const int j = __ldg(perm + r);
-        const int32_t y = __ldg(x.s + ro + j);
-        i128 v = i128(int64_t(y) * int64_t(__ldg(x.msk + ro + j)));  // |int32 * int32| < 2^62
-        const uint32_t tau = mag32(y);
-        for (int l2 = 0, li2 = 0; l2 < nd.k && v != 0; l2++) {
-          if (l2 == nd.ia || l2 == nd.ib) continue;
-          if (l2 != l) {
-            const int q = rank_of(inputs[nd.in_begin + l2].abs + ro, w, tau, l2 < l);
-            o |= mul_ovf_64(v, P.sg[(int64_t(n) * A.tri_max_leaves + li2) * W1 + q], &v);
+        pre[r + 1] = i128(int64_t(__ldg(x.s + ro + j)) * int64_t(__ldg(x.msk + ro + j)));  // |int32 * int32| < 2^62
+      }
+      bool o = false;
+      for (int l2 = 0, li2 = 0; l2 < nd.k; l2++) {
+        if (l2 == nd.ia || l2 == nd.ib) continue;
+        if (l2 != l) {
+          __syncthreads();
+          stage_row(inputs[nd.in_begin + l2].abs + ro, stage, w);
+          const int64_t* sg2 = P.sg + (int64_t(n) * A.tri_max_leaves + li2) * W1;
+          for (int r = tid; r < w; r += T) {
+            i128 v = pre[r + 1];
+            if (v == 0) continue;
+            const uint32_t tau = mag32(__ldg(x.s + ro + __ldg(perm + r)));
+            o |= mul_ovf_64(v, sg2[rank_sh(stage, w, tau, l2 < l)], &v);
+            pre[r + 1] = v;
           }
-          li2++;
         }
-        pre[r + 1] = v;
+        li2++;
       }
       if (o) atomicOr(sh_flag, 1);
       if (tid == 0) pre[0] = 0;
@@ -246,8 +286,8 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
   // ---- the six node messages, in bucket order
   for (int n = 0; n < 3; n++) {
     const TriNode nd = ts.node[n];
-    node_msg(A, nd, n, nd.ia, P, ro, P.vec + int64_t(2 * n) * w, sh_flag);
-    node_msg(A, nd, n, nd.ib, P, ro, P.vec + int64_t(2 * n + 1) * w, sh_flag);
+    node_msg(A, nd, n, nd.ia, P, ro, P.vec + int64_t(2 * n) * w, stage, sh_flag);
+    node_msg(A, nd, n, nd.ib, P, ro, P.vec + int64_t(2 * n + 1) * w, stage, sh_flag);
   }
   // ---- row side: U or V, whichever conditioned sketch has fewer distinct magnitudes
   for (int n = 0; n < 2; n++) {
@@ -275,25 +315,34 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
   const EstIn& Wc = inputs[NW.in_begin + wC];
 
   // ---- queries: conditioning values with both conditioned sketch values nonzero (a zero
-  // makes every merged entry at c through that table 0), sorted by (rR, rC, c)
+  // makes every merged entry at c through that table 0), sorted by (rR, rC, c).  The
+  // clamp ranks (number of parent-sketch values that beat the conditioned value) are
+  // searched in the staged parent rows, kept per c in qr / qs, then packed into keys.
   {
+    uint32_t* stR = stage;
+    uint32_t* stC = stage + wp2;
+    for (int r = tid; r < w; r += T) {
+      stR[r] = __ldg(Rpar.abs + ro + r);
+      stC[r] = __ldg(Cpar.abs + ro + r);
+    }
+    __syncthreads();
     int cnt = 0;
-    for (int c = tid; c < wp2; c += T) {
-      unsigned long long kk = ~0ull;
-      if (c < w) {
-        const int32_t sr = __ldg(Rcond.s + ro + c), sc = __ldg(Ccond.s + ro + c);
-        if (sr != 0 && sc != 0) {
-          // number of parent-sketch values that beat the conditioned value
-          const int r = rank_of(Rpar.abs + ro, w, mag32(sr), tieR);
-          const int s = rank_of(Cpar.abs + ro, w, mag32(sc), tieC);
-          kk = (static_cast<unsigned long long>(r) << 42) | (static_cast<unsigned long long>(s) << 21) |
-               static_cast<unsigned long long>(c);
-          cnt++;
-        }
-      }
-      key[c] = kk;
+    for (int c = tid; c < w; c += T) {
+      const int32_t sr = __ldg(Rcond.s + ro + c), sc = __ldg(Ccond.s + ro + c);
+      const bool live = sr != 0 && sc != 0;
+      P.qr[c] = live ? rank_sh(stR, w, mag32(sr), tieR) : -1;
+      P.qs[c] = live ? rank_sh(stC, w, mag32(sc), tieC) : -1;
+      cnt += live;
     }
     if (cnt) atomicAdd(&sh_cnt[2], cnt);
+    __syncthreads();  // stage no longer read: the keys overwrite it
+    for (int c = tid; c < wp2; c += T) {
+      unsigned long long kk = ~0ull;
+      if (c < w && P.qr[c] >= 0)
+        kk = (static_cast<unsigned long long>(P.qr[c]) << 42) | (static_cast<unsigned long long>(P.qs[c]) << 21) |
+             static_cast<unsigned long long>(c);
+      key[c] = kk;
+    }
   }
   __syncthreads();
   bitonic_sort(key, wp2);
@@ -339,6 +388,9 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
   if (tid == 0) P.gqb[G] = nq;
 
   // ---- rows of the row side: batch (number of group ranks <= u), then W's key, then u
+  int32_t* sgr = reinterpret_cast<int32_t*>(key + wp2);  // G <= w group ranks
+  for (int g = tid; g < G; g += T) sgr[g] = P.gr[g];
+  __syncthreads();
   for (int u = tid; u < wp2; u += T) {
     unsigned long long kk = ~0ull;
     if (u < w) {
@@ -347,7 +399,7 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
       int lo = 0, hi = G;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (P.gr[mid] <= u) lo = mid + 1;
+        if (sgr[mid] <= u) lo = mid + 1;
         else hi = mid;
       }
       kk = (static_cast<unsigned long long>(lo) << 48) | (kx << 14) | static_cast<unsigned long long>(u);
@@ -390,8 +442,16 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
   }
 }
 
-// One thread per column; kTriCols columns per CTA, tri_nch CTAs per triangle row.
+// Shared memory of the staged sweep: row keys [w] u64, column ranks [w], group ranks and
+// group starts [w + 1] each.
+__host__ __device__ inline int64_t tri_sweep_smem(int32_t w) { return 8 * int64_t(w) + 4 * (3 * int64_t(w) + 2); }
+constexpr int64_t kTriSweepSmemMax = 100 * 1024;  // staged when two CTAs per SM still fit
+
+// One thread per column; kTriCols columns per CTA, tri_nch CTAs per triangle row.  STAGED:
+// the arrays the binary searches read are first copied to shared memory.
+template <bool STAGED>
 __global__ void __launch_bounds__(kTriCols) k_tri_sweep(const __grid_constant__ EstArgs A, int64_t tr0) {
+  extern __shared__ __align__(16) unsigned char sweep_smem[];
   __shared__ i128 sh_i128[33];
   __shared__ int32_t sh_flag[1];
   BlockScratch bs{sh_i128, sh_flag};
@@ -400,11 +460,28 @@ __global__ void __launch_bounds__(kTriCols) k_tri_sweep(const __grid_constant__ 
   const int64_t slot = blockIdx.x / A.tri_nch;
   const int ch = int(blockIdx.x % A.tri_nch);
   const int64_t it = A.n_gen_items + (tr0 + slot) * A.tri_nch + ch;
-  const TriPtrs P = tri_ptrs(A.tri_scratch + slot * A.tri_row_bytes, w, A.tri_max_leaves);
+  TriPtrs P = tri_ptrs(A.tri_scratch + slot * A.tri_row_bytes, w, A.tri_max_leaves);
   if (tid == 0) sh_flag[0] = 0;
-  __syncthreads();
   const int G = P.hdr[0];
+  const int nq = P.hdr[1];
   const int prep_ovf = P.hdr[2];
+  if (STAGED) {
+    uint64_t* s_rkx = reinterpret_cast<uint64_t*>(sweep_smem);
+    int32_t* s_qs = reinterpret_cast<int32_t*>(s_rkx + w);
+    int32_t* s_gr = s_qs + w;
+    int32_t* s_gqb = s_gr + (w + 1);
+    for (int r = tid; r < w; r += kTriCols) s_rkx[r] = P.rkx[r];
+    for (int q = tid; q < nq; q += kTriCols) s_qs[q] = P.qs[q];
+    for (int g = tid; g <= G; g += kTriCols) {
+      if (g < G) s_gr[g] = P.gr[g];
+      s_gqb[g] = P.gqb[g];
+    }
+    P.rkx = s_rkx;
+    P.qs = s_qs;
+    P.gr = s_gr;
+    P.gqb = s_gqb;
+  }
+  __syncthreads();
   const int v = ch * kTriCols + tid;
   i128 E = 0;
   bool o = false;
@@ -490,13 +567,23 @@ cudaError_t launch_estimate_tri(const EstArgs& a, cudaStream_t st) {
   const int64_t rows = a.n_tri * a.d;
   int wp2 = 1;
   while (wp2 < a.w) wp2 <<= 1;
-  const int smem = int(sizeof(unsigned long long)) * wp2;
+  // sort keys (also two staged magnitude rows before the sorts), then the group ranks
+  const int smem = int(sizeof(unsigned long long)) * wp2 + int(sizeof(int32_t)) * (a.w + 1);
   cudaError_t e = cudaFuncSetAttribute(k_tri_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  const bool staged = tri_sweep_smem(a.w) <= kTriSweepSmemMax;
+  if (staged) {
+    e = cudaFuncSetAttribute(k_tri_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(tri_sweep_smem(a.w)));
+    if (e != cudaSuccess) return e;
+  }
   for (int64_t r0 = 0; r0 < rows; r0 += a.tri_slots) {
     const int64_t n = rows - r0 < a.tri_slots ? rows - r0 : a.tri_slots;
     k_tri_prep<<<unsigned(n), 1024, smem, st>>>(a, r0);
-    k_tri_sweep<<<unsigned(n * a.tri_nch), kTriCols, 0, st>>>(a, r0);
+    if (staged)
+      k_tri_sweep<true><<<unsigned(n * a.tri_nch), kTriCols, size_t(tri_sweep_smem(a.w)), st>>>(a, r0);
+    else
+      k_tri_sweep<false><<<unsigned(n * a.tri_nch), kTriCols, 0, st>>>(a, r0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

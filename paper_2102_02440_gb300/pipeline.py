@@ -55,6 +55,15 @@ class DeviceWorkload:
         self.hash_dev = torch.from_numpy(hp.view(np.int64)).to(self.device)
         self.tables = [DeviceTable(t, self.d, self.w, self.device, cols_dev=cols_dev[i] if cols_dev else None)
                        for i, t in enumerate(wl.tables)]
+        # every table's counters as consecutive blocks of one buffer (tables without sketches
+        # keep their own): presort and cross ranks then take one launch each for all tables
+        total = sum(t.k for t in self.tables)
+        self.counters_all = torch.zeros((max(total, 1), self.d, self.w), dtype=torch.int32, device=self.device)
+        off = 0
+        for t in self.tables:
+            if t.k:
+                t.counters = self.counters_all[off:off + t.k]
+                off += t.k
         self.survivors = torch.zeros(len(self.tables), dtype=torch.int64, device=self.device)
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
         self._plan = None
@@ -98,26 +107,45 @@ class DeviceWorkload:
 
 
 def _prep_tables(dw):
-    """Presort and cross-rank buffers for every table of a DeviceWorkload (once)."""
+    """Presort and cross-rank buffers for every table of a DeviceWorkload (once): one
+    buffer each for all tables, in the order of the counters, with per-table views."""
     if getattr(dw, "ranks", None) is None:
-        dev = dw.device
-        dw.abs_sorted = [torch.empty(t.counters.shape, dtype=torch.int32, device=dev) for t in dw.tables]
-        dw.perm = [torch.empty(t.counters.shape, dtype=torch.int32, device=dev) for t in dw.tables]
-        dw.ranks = [torch.empty((t.counters.shape[0],) + tuple(t.counters.shape), dtype=torch.int32, device=dev)
-                    for t in dw.tables]
+        dev, d, w = dw.device, dw.d, dw.w
+        ks = [t.k for t in dw.tables]
+        total, rtotal = sum(ks), sum(k * k for k in ks)
+        dw.abs_all = torch.empty((max(total, 1), d, w), dtype=torch.int32, device=dev)
+        dw.perm_all = torch.empty((max(total, 1), d, w), dtype=torch.int32, device=dev)
+        dw.ranks_all = torch.empty((max(rtotal, 1), d, w), dtype=torch.int32, device=dev)
+        dw.abs_sorted, dw.perm, dw.ranks = [], [], []
+        off = roff = 0
+        for k in ks:
+            if k:
+                dw.abs_sorted.append(dw.abs_all[off:off + k])
+                dw.perm.append(dw.perm_all[off:off + k])
+                dw.ranks.append(dw.ranks_all[roff:roff + k * k].view(k, k, d, w))
+                off += k
+                roff += k * k
+            else:  # no sketch: never referenced by a graph
+                dw.abs_sorted.append(dw.abs_all[:0])
+                dw.perm.append(dw.perm_all[:0])
+                dw.ranks.append(dw.ranks_all[:0])
+        dw.edge_ids_all = [e for t in dw.tables for e in t.edge_id]
 
 
 def _presort_tables(dw, s):
-    """cmp_presort then cmp_cross_ranks for every table with sketches."""
-    need = max((K.cmp_presort_ws_bytes(t.k * dw.d, dw.w) for t in dw.tables), default=0)
+    """cmp_presort of every sketch row of every table, then cmp_cross_ranks_multi: one
+    launch each (tables' counters are consecutive blocks of dw.counters_all)."""
+    total = sum(t.k for t in dw.tables)
+    if total == 0:
+        return
+    need = K.cmp_presort_ws_bytes(total * dw.d, dw.w)
     ws = getattr(dw, "presort_ws", None)
     if need and (ws is None or ws.numel() < need):
         ws = dw.presort_ws = torch.empty(need, dtype=torch.uint8, device=dw.device)
-    for t, a, p, r in zip(dw.tables, dw.abs_sorted, dw.perm, dw.ranks):
-        if t.k:
-            K.cmp_presort(t.counters.data_ptr(), t.k * dw.d, dw.w, a.data_ptr(), p.data_ptr(),
-                          ws.data_ptr() if need else 0, need, s)
-            K.cmp_cross_ranks(a.data_ptr(), p.data_ptr(), t.k, dw.d, dw.w, t.edge_id, r.data_ptr(), s)
+    K.cmp_presort(dw.counters_all.data_ptr(), total * dw.d, dw.w, dw.abs_all.data_ptr(), dw.perm_all.data_ptr(),
+                  ws.data_ptr() if need else 0, need, s)
+    K.cmp_cross_ranks_multi(dw.abs_all.data_ptr(), dw.perm_all.data_ptr(), [t.k for t in dw.tables],
+                            dw.edge_ids_all, dw.d, dw.w, dw.ranks_all.data_ptr(), s)
 
 
 def _graph_struct(dw, g_tables, g_eu, g_ev, sketch_of, survivors_ptr, keep):
@@ -219,10 +247,9 @@ class PairBatch:
                                  cols_dev=cols_dev)
         self.device = self.dw.device
         self.cfg = cfg
-        # one contiguous [2n][d][w] counter buffer: presort and self-join sizes in one launch each
-        self.counters = torch.zeros((2 * self.n, d, w), dtype=torch.int32, device=self.device)
-        for i, t in enumerate(self.dw.tables):
-            t.counters = self.counters[i:i + 1]
+        # the tables' counters are consecutive [d][w] blocks: presort and self-join sizes
+        # take one launch each
+        self.counters = self.dw.counters_all
 
     def build(self, stream=None):
         self.dw.build_batched(self.cfg, stream)

@@ -196,6 +196,17 @@ def test_estimate_plan_triangle_path_host_logic(K):
     assert ei.value.status == K.CMP_EINVAL
 
 
+def test_cross_ranks_multi_rejections(K):
+    ks = (C.c_int32 * 2)(2, 17)
+    e = (C.c_int32 * 19)(*range(19))
+    assert K.lib().cmp_cross_ranks_multi(0x10, 0x10, 2, ks, e, 3, 64, 0x10, None) == K.CMP_EINVAL  # k > 16
+    ks = (C.c_int32 * 2)(2, 1)
+    assert K.lib().cmp_cross_ranks_multi(0x10, 0x10, 2, ks, e, 0, 64, 0x10, None) == K.CMP_EINVAL  # d < 1
+    assert K.lib().cmp_cross_ranks_multi(None, 0x10, 2, ks, e, 3, 64, 0x10, None) == K.CMP_EINVAL
+    assert K.lib().cmp_cross_ranks_multi(0x10, 0x10, 2, None, e, 3, 64, 0x10, None) == K.CMP_EINVAL
+    assert K.lib().cmp_cross_ranks_multi(0x10, 0x10, 0, None, None, 3, 64, None, None) == K.CMP_OK  # nothing
+
+
 def test_presort_rejections(K):
     assert K.lib().cmp_presort(0x10, 4, 0, 0x10, 0x10, None, 0, None) == K.CMP_EINVAL
     assert K.lib().cmp_presort(0x10, 4, 1 << 15, 0x10, 0x10, None, 0, None) == K.CMP_EWORKSPACE

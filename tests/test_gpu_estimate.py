@@ -152,3 +152,28 @@ def test_rejections():
     dw2 = P.DeviceWorkload(wl2)
     dw2.build()
     P.DeviceEstimator(dw2, [0b111])          # one cycle: supported
+
+
+def test_cross_ranks_multi_equals_per_table():
+    """One launch for several tables (0 to 16 sketches each, consecutive blocks) gives the
+    ranks of one cmp_cross_ranks call per table."""
+    rng = np.random.default_rng(12)
+    d, w = 3, 300
+    ks = [2, 0, 1, 3, 16, 1]
+    total = sum(ks)
+    C = torch.from_numpy(rng.integers(-9, 10, size=(total, d, w)).astype(np.int32)).cuda()
+    a = torch.empty_like(C)
+    p = torch.empty_like(C)
+    K.cmp_presort(C.data_ptr(), total * d, w, a.data_ptr(), p.data_ptr(), 0, 0, K.stream_handle())
+    edges = [int(e) for k in ks for e in rng.permutation(40)[:k]]
+    multi = torch.full((sum(k * k for k in ks), d, w), -7, dtype=torch.int32, device="cuda")
+    K.cmp_cross_ranks_multi(a.data_ptr(), p.data_ptr(), ks, edges, d, w, multi.data_ptr(), K.stream_handle())
+    off = roff = e = 0
+    for k in ks:
+        if k:
+            one = torch.full((k * k, d, w), -9, dtype=torch.int32, device="cuda")
+            K.cmp_cross_ranks(a[off:].data_ptr(), p[off:].data_ptr(), k, d, w, edges[e:e + k], one.data_ptr(),
+                              K.stream_handle())
+            torch.cuda.synchronize()
+            assert torch.equal(one, multi[roff:roff + k * k])
+        off, roff, e = off + k, roff + k * k, e + k
