@@ -54,7 +54,8 @@ def _args():
     ap.add_argument("--phases", action="store_true", help="print a per-phase breakdown on stderr")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of autotuned launch shapes: read if it has this workload's, else written")
-    ap.add_argument("--case", default=None, choices=["estimate_small", "build_f1", "build_five", "batched", "scale"],
+    ap.add_argument("--case", default=None,
+                    choices=["estimate_small", "estimate_full", "build_f1", "build_five", "batched", "scale"],
                     help="run one small profiling case instead of the benchmark (for ncu captures)")
     return ap.parse_args()
 
@@ -233,15 +234,16 @@ def build_work(wl, dw, dedupe: bool):
 
 
 def _kernel_traffic(name: str):
-    """DRAM bytes per launch of `name` from the committed ncu capture, or None if the
-    kernel's source changed since the capture."""
+    """DRAM bytes (read + write) per launch of the kernels of `name` (a phase), summed, from
+    the committed ncu capture; None if a source file changed since the capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "counters.json")) as f:
             c = json.load(f)[name]
-        src = os.path.join(ROOT, "paper_2102_02440_gb300", "csrc", c["source"])
-        if hashlib.sha256(open(src, "rb").read()).hexdigest() != c["source_sha256"]:
-            return None
+        for src, sha in c["sources"].items():
+            path = os.path.join(ROOT, "paper_2102_02440_gb300", "csrc", src)
+            if hashlib.sha256(open(path, "rb").read()).hexdigest() != sha:
+                return None
         return c["dram_bytes_per_launch"]
     except Exception:
         return None
@@ -533,7 +535,7 @@ def run_ours(a):
     build_s = phase["build"] / 1e3
     ach = cw_evals * CW_INSTR / build_s
     roof = {"bound": "alu", "achieved": ach / 1e12, "peak": INT_ISSUE_PEAK / 1e12, "unit": "Tinstr/s",
-            "frac": ach / INT_ISSUE_PEAK, "traffic": _kernel_traffic("k_sketch_build"),
+            "frac": ach / INT_ISSUE_PEAK, "traffic": _kernel_traffic("build_phase"),
             "kernel": "batched build: k_zero_spans, k_agg_stats, k_agg_zero, k_agg_count, k_sketch_build",
             "algorithmic": f"{cw_evals} CW evaluations x {CW_INSTR} int32 instr (one per distinct surviving key "
                            f"and sketch row on aggregated columns, one per surviving tuple and sketch row elsewhere; "
@@ -550,7 +552,7 @@ def run_ours(a):
     op_peak = INT_ISSUE_PEAK / OP128_INSTR
     roof_est = {"bound": "alu", "achieved": est_ops / est_s / 1e12, "peak": op_peak / 1e12,
                 "unit": "T int128-op/s", "frac": est_ops / est_s / op_peak,
-                "traffic": _kernel_traffic("k_tri_sweep"),
+                "traffic": _kernel_traffic("estimate_phase"),
                 "kernel": "k_estimate_items (trees), k_tri_prep + k_tri_sweep (triangles), k_estimate_finalize",
                 "algorithmic": f"{est_ops} exact 128-bit operations ({n_tri_sub} triangle, {n_gen_sub} other sub-plans)",
                 "peak_derivation": f"152 SMs x 4 SMSP x 32 lanes x 2.07 GHz / {OP128_INSTR} int32 instr per op"}
@@ -620,17 +622,18 @@ def run_ours(a):
 
 
 def run_case(a):
-    """Small profiling cases (one GPU): the estimate of all 19 sub-plans of the five-table
-    graph at w = 4096 (tables at 5% scale; the estimate's cost depends on w and the sketch
-    values); the single-table fused build of the 36M-row F1 table alone (3 sketches, d = 11,
-    w = 4096, per-tuple path); or the benchmark's batched build of all five tables."""
+    """Profiling cases (one GPU, under 1 GB on the device): the estimate of all 19 sub-plans
+    of the five-table graph at w = 4096 on sketches of the tables at 5% scale (estimate_small)
+    or full scale (estimate_full, the benchmark's sketches); the single-table fused build of
+    the 36M-row F1 table alone (3 sketches, d = 11, w = 4096, per-tuple path); or the
+    benchmark's batched build of all five tables (build_five)."""
     import torch
 
     from paper_2102_02440_gb300 import datagen as G
     from paper_2102_02440_gb300 import pipeline as P
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if a.case == "estimate_small":
-        wl = G.five_table(scale=0.05, w=4096)
+    if a.case in ("estimate_small", "estimate_full"):
+        wl = G.five_table(scale=0.05 if a.case == "estimate_small" else 1.0, w=4096)
         dw = P.DeviceWorkload(wl)
         dw.build_batched()
         est = P.DeviceEstimator(dw, G.connected_subplans(5, wl.edge_u, wl.edge_v))
