@@ -422,26 +422,33 @@ def run_ours(a):
     stream = torch.cuda.Stream(dev)  # a side stream: CUDA graphs cannot capture the legacy default stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     # learned combiner over every sub-plan's row estimates; self-join sizes of the two
-    # sketches of each two-table sub-plan (its training domain), zero elsewhere
+    # sketches of each two-table sub-plan (its training domain), zero elsewhere: one
+    # cmp_sketch_f2 launch over every sketch (the tables' counters are one buffer), then the
+    # features pick each sub-plan's two sketches by index
     n_sub = len(masks)
     comb = P.Combiner(wl.d + 2, 64, seed=0, device=dev, skip=wl.d // 2)
-    f2a = torch.zeros(n_sub, dtype=torch.float64, device=dev)
-    f2b = torch.zeros(n_sub, dtype=torch.float64, device=dev)
+    n_sk = dw.counters_all.shape[0]
+    f2_all = torch.zeros(n_sk, dtype=torch.float64, device=dev)
     feat = torch.empty((n_sub, wl.d + 2), dtype=torch.float32, device=dev)
     y_mlp = torch.empty(n_sub, dtype=torch.float32, device=dev)
     est_comb = torch.empty(n_sub, dtype=torch.float64, device=dev)
+    first_sketch = np.cumsum([0] + [t.k for t in dw.tables])
+    f2_idx_host = np.full((n_sub, 2), -1, np.int32)
     two = []
     for q, m in enumerate(masks):
         if bin(m).count("1") == 2:
             tu, tv = [t for t in range(len(wl.tables)) if (m >> t) & 1]
             e = next(e for e in range(wl.n_edges) if {wl.edge_u[e], wl.edge_v[e]} == {tu, tv})
-            two.append((q, dw.sketch(e, 0), dw.sketch(e, 1)))
+            for end in range(2):
+                t, si = wl.sketch_of(e, end)
+                f2_idx_host[q, end] = first_sketch[t] + si
+            two.append(q)
+    f2_idx = torch.from_numpy(f2_idx_host).to(dev)
 
     def combiner(s):
-        for q, sa, sb in two:
-            K.cmp_sketch_f2(sa.data_ptr(), 1, wl.d, wl.w, f2a[q:].data_ptr(), s)
-            K.cmp_sketch_f2(sb.data_ptr(), 1, wl.d, wl.w, f2b[q:].data_ptr(), s)
-        K.cmp_mlp_features(est.row_est.data_ptr(), n_sub, wl.d, f2a.data_ptr(), f2b.data_ptr(), feat.data_ptr(), s)
+        K.cmp_sketch_f2(dw.counters_all.data_ptr(), n_sk, wl.d, wl.w, f2_all.data_ptr(), s)
+        K.cmp_mlp_features_indexed(est.row_est.data_ptr(), n_sub, wl.d, f2_all.data_ptr(), f2_idx.data_ptr(),
+                                   feat.data_ptr(), s)
         K.cmp_mlp_infer(comb.params.data_ptr(), wl.d + 2, 64, wl.d // 2, feat.data_ptr(), n_sub, y_mlp.data_ptr(), s)
         K.cmp_mlp_combine(est.est.data_ptr(), y_mlp.data_ptr(), n_sub, est_comb.data_ptr(), s)
 
@@ -589,15 +596,16 @@ def run_ours(a):
     if rank == 0 and not a.no_cpu_baseline:
         cpu = cpu_baseline(wl)
 
-    # zero + build, presort + cross ranks per table, estimate (generic int64 + int128 recompute
-    # when trees are planned, triangle preparation + sweep when triangles are, finalize),
-    # two self-join sizes per two-table sub-plan, features, infer, combine
+    # estimate: generic int64 + int128 recompute when trees are planned, triangle preparation +
+    # sweep when triangles are, finalize
     est_launches = (2 if n_gen_sub > sum(1 for m in masks if bin(m).count("1") == 1) else 0) + \
         (2 if n_tri_sub else 0) + 1
     # build: zero spans + build kernel, plus key range, clearing and counting when the plan
     # aggregates key columns (it then has a workspace)
     build_launches = 2 + (3 if dw._plan[2] else 0)
-    launches_per_step = build_launches + 2 * sum(1 for t in dw.tables if t.k) + est_launches + 2 * len(two) + 3
+    # presort + cross ranks of all tables: one launch each; combiner: self-join sizes, features,
+    # inference, combination
+    launches_per_step = build_launches + 2 + est_launches + 4
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",

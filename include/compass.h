@@ -301,6 +301,14 @@ cmp_status cmp_sketch_f2(const int32_t* counters_dev, int64_t n_sketches, int32_
 cmp_status cmp_mlp_features(const int64_t* row_est_dev, int64_t n, int32_t d, const double* f2a_dev,
                             const double* f2b_dev, float* feat_dev, void* stream);
 
+/* cmp_mlp_features with the self-join sizes of all sketches in one array: f2a[q] =
+ * f2_dev[f2_index_dev[2q]] and f2b[q] = f2_dev[f2_index_dev[2q + 1]], an index of -1 giving
+ * 0 (e.g. f2_dev from one cmp_sketch_f2 call over every sketch, f2_index_dev [n][2] int32 the
+ * two sketches of each two-table sub-plan, -1 elsewhere).  The indices must be below the
+ * length of f2_dev. */
+cmp_status cmp_mlp_features_indexed(const int64_t* row_est_dev, int64_t n, int32_t d, const double* f2_dev,
+                                    const int32_t* f2_index_dev, float* feat_dev, void* stream);
+
 /* Forward pass: y_dev[s] for the n rows of x_dev ([n][nin] fp32). */
 cmp_status cmp_mlp_infer(const float* params_dev, int32_t nin, int32_t nh, int32_t skip, const float* x_dev, int64_t n,
                          float* y_dev, void* stream);

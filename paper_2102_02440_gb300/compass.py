@@ -106,6 +106,8 @@ _SIGS = {
     "cmp_sketch_f2": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "cmp_mlp_features": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
+    "cmp_mlp_features_indexed": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p]),
     "cmp_mlp_infer": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p,
                                   C.c_void_p]),
     "cmp_mlp_combine": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
@@ -281,6 +283,12 @@ def cmp_sketch_f2(counters_dev: int, n_sketches: int, d: int, w: int, f2_dev: in
 
 def cmp_mlp_features(row_est_dev: int, n: int, d: int, f2a_dev: int, f2b_dev: int, feat_dev: int, stream: int):
     _check("cmp_mlp_features", lib().cmp_mlp_features(row_est_dev, n, d, f2a_dev, f2b_dev, feat_dev, stream))
+
+
+def cmp_mlp_features_indexed(row_est_dev: int, n: int, d: int, f2_dev: int, f2_index_dev: int, feat_dev: int,
+                             stream: int):
+    _check("cmp_mlp_features_indexed",
+           lib().cmp_mlp_features_indexed(row_est_dev, n, d, f2_dev, f2_index_dev, feat_dev, stream))
 
 
 def cmp_mlp_infer(params_dev: int, nin: int, nh: int, skip: int, x_dev: int, n: int, y_dev: int, stream: int):

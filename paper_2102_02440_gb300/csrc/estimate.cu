@@ -722,46 +722,54 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
   }
 }
 
-// One thread per sub-plan: row sums over conditioning chunks, exact median, one rounding.
-__global__ void k_estimate_finalize(const __grid_constant__ EstArgs A, double* __restrict__ est,
-                                    int64_t* __restrict__ row_est) {
-  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (q >= A.n_sub) return;
+// One CTA per sub-plan, one thread per sketch row: the row's sum over its items (conditioning
+// chunks or column chunks), then thread 0 takes the exact median and rounds once.
+constexpr int kFinalizeThreads = 64;  // >= CMP_MAX_D
+
+__global__ void __launch_bounds__(kFinalizeThreads) k_estimate_finalize(const __grid_constant__ EstArgs A,
+                                                                        double* __restrict__ est,
+                                                                        int64_t* __restrict__ row_est) {
+  __shared__ i128 rows[CMP_MAX_D];
+  __shared__ int32_t any_ovf;
+  const int64_t q = blockIdx.x;
   const EstSub sb = A.subs[q];
-  const int d = A.d;
-  i128 rows[CMP_MAX_D];
-  bool ovf = false;
-  for (int i = 0; i < d; i++) {
-    if (sb.single) {
-      rows[i] = i128(*sb.sv);
-      continue;
-    }
+  const int d = A.d, i = threadIdx.x;
+  if (i == 0) any_ovf = 0;
+  __syncthreads();
+  if (i < d) {
     i128 s = 0;
-    for (int ch = 0; ch < sb.n_chunks; ch++) {
-      const int64_t it = int64_t(sb.item_begin) + int64_t(i) * sb.n_chunks + ch;
-      ovf |= A.partial_ovf[it] != 0;
-      ovf |= add_ovf(s, A.partial[it], &s);
+    bool ovf = false;
+    if (sb.single) {
+      s = i128(*sb.sv);
+    } else {
+      const int64_t it0 = int64_t(sb.item_begin) + int64_t(i) * sb.n_chunks;
+      for (int ch = 0; ch < sb.n_chunks; ch++) {
+        ovf |= A.partial_ovf[it0 + ch] != 0;
+        ovf |= add_ovf(s, A.partial[it0 + ch], &s);
+      }
     }
     rows[i] = s;
-  }
-  if (row_est)
-    for (int i = 0; i < d; i++) {
-      row_est[(q * d + i) * 2] = int64_t(uint64_t(u128(rows[i])));
-      row_est[(q * d + i) * 2 + 1] = int64_t(uint64_t(u128(rows[i]) >> 64));
+    if (row_est) {
+      row_est[(q * d + i) * 2] = int64_t(uint64_t(u128(s)));
+      row_est[(q * d + i) * 2 + 1] = int64_t(uint64_t(u128(s) >> 64));
     }
-  if (ovf) {
+    if (ovf) atomicOr(&any_ovf, 1);
+  }
+  __syncthreads();
+  if (i != 0) return;
+  if (any_ovf) {
     est[q] = __longlong_as_double(0x7ff8000000000000ll);
     set_status(A.status, CMP_EOVERFLOW);
     return;
   }
-  for (int i = 1; i < d; i++) {  // insertion sort of exact integers
-    const i128 v = rows[i];
-    int j = i - 1;
-    while (j >= 0 && rows[j] > v) {
-      rows[j + 1] = rows[j];
-      j--;
+  for (int a = 1; a < d; a++) {  // insertion sort of exact integers
+    const i128 v = rows[a];
+    int b = a - 1;
+    while (b >= 0 && rows[b] > v) {
+      rows[b + 1] = rows[b];
+      b--;
     }
-    rows[j + 1] = v;
+    rows[b + 1] = v;
   }
   est[q] = (d & 1) ? i128_to_double(rows[d / 2]) : mean2_to_double(rows[d / 2 - 1], rows[d / 2]);
 }
@@ -784,8 +792,7 @@ cudaError_t launch_estimate(const EstArgs& a, double* est, int64_t* row_est, cud
     if (e != cudaSuccess) return e;
   }
   if (a.n_sub > 0) {
-    const int th = 128;
-    k_estimate_finalize<<<unsigned((a.n_sub + th - 1) / th), th, 0, st>>>(a, est, row_est);
+    k_estimate_finalize<<<unsigned(a.n_sub), kFinalizeThreads, 0, st>>>(a, est, row_est);
     return cudaGetLastError();
   }
   return cudaSuccess;

@@ -98,9 +98,11 @@ __global__ void __launch_bounds__(kF2Threads) k_sketch_f2(const int32_t* __restr
 // feat[q] = ( v_0 - v_m, ..., v_m, ..., v_{d-1} - v_m,  ln(1 + f2a[q]) / 32,  ln(1 + f2b[q]) / 32 )
 // Centring the order statistics on the median keeps the inputs of a correction to the
 // median small, so bfloat16 weights do not swamp it with rounding noise.
+// f2a / f2b per sample, or (f2_idx != nullptr) both read from one per-sketch f2 array at
+// f2_idx[2q], f2_idx[2q + 1] (-1: no sketch, feature of 0).
 __global__ void k_mlp_features(const int64_t* __restrict__ row_est, int64_t n, int32_t d,
                                const double* __restrict__ f2a, const double* __restrict__ f2b,
-                               float* __restrict__ feat) {
+                               const int32_t* __restrict__ f2_idx, float* __restrict__ feat) {
   const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= n) return;
   float v[CMP_MAX_D];
@@ -122,8 +124,17 @@ __global__ void k_mlp_features(const int64_t* __restrict__ row_est, int64_t n, i
   float* out = feat + q * (d + 2);
   const float vm = v[d / 2];
   for (int i = 0; i < d; i++) out[i] = i == d / 2 ? vm : v[i] - vm;
-  out[d] = float(log1p(fmax(f2a[q], 0.0))) * kFeatScale;
-  out[d + 1] = float(log1p(fmax(f2b[q], 0.0))) * kFeatScale;
+  double fa, fb;
+  if (f2_idx) {
+    const int32_t ia = f2_idx[2 * q], ib = f2_idx[2 * q + 1];
+    fa = ia >= 0 ? f2a[ia] : 0.0;
+    fb = ib >= 0 ? f2a[ib] : 0.0;
+  } else {
+    fa = f2a[q];
+    fb = f2b[q];
+  }
+  out[d] = float(log1p(fmax(fa, 0.0))) * kFeatScale;
+  out[d + 1] = float(log1p(fmax(fb, 0.0))) * kFeatScale;
 }
 
 // ---------------------------------------------------------------- inference
@@ -273,7 +284,14 @@ cudaError_t launch_sketch_f2(const int32_t* C, int64_t n_sketches, int32_t d, in
 cudaError_t launch_mlp_features(const int64_t* row_est, int64_t n, int32_t d, const double* f2a, const double* f2b,
                                 float* feat, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_mlp_features<<<unsigned((n + 127) / 128), 128, 0, st>>>(row_est, n, d, f2a, f2b, feat);
+  k_mlp_features<<<unsigned((n + 127) / 128), 128, 0, st>>>(row_est, n, d, f2a, f2b, nullptr, feat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_features_indexed(const int64_t* row_est, int64_t n, int32_t d, const double* f2,
+                                        const int32_t* f2_idx, float* feat, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_mlp_features<<<unsigned((n + 127) / 128), 128, 0, st>>>(row_est, n, d, f2, nullptr, f2_idx, feat);
   return cudaGetLastError();
 }
 
@@ -340,6 +358,16 @@ cmp_status cmp_mlp_features(const int64_t* row_est_dev, int64_t n, int32_t d, co
   if (n > 0 && (!row_est_dev || !f2a_dev || !f2b_dev || !feat_dev)) return CMP_EINVAL;
   return launch_mlp_features(row_est_dev, n, d, f2a_dev, f2b_dev, feat_dev, reinterpret_cast<cudaStream_t>(stream)) ==
                  cudaSuccess
+             ? CMP_OK
+             : CMP_ECUDA;
+}
+
+cmp_status cmp_mlp_features_indexed(const int64_t* row_est_dev, int64_t n, int32_t d, const double* f2_dev,
+                                    const int32_t* f2_index_dev, float* feat_dev, void* stream) {
+  if (n < 0 || d < 1 || d > CMP_MAX_D) return CMP_EINVAL;
+  if (n > 0 && (!row_est_dev || !f2_dev || !f2_index_dev || !feat_dev)) return CMP_EINVAL;
+  return launch_mlp_features_indexed(row_est_dev, n, d, f2_dev, f2_index_dev, feat_dev,
+                                     reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
              ? CMP_OK
              : CMP_ECUDA;
 }

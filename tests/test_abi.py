@@ -207,6 +207,12 @@ def test_cross_ranks_multi_rejections(K):
     assert K.lib().cmp_cross_ranks_multi(0x10, 0x10, 0, None, None, 3, 64, None, None) == K.CMP_OK  # nothing
 
 
+def test_features_indexed_rejections(K):
+    assert K.lib().cmp_mlp_features_indexed(0x10, 4, 0, 0x10, 0x10, 0x10, None) == K.CMP_EINVAL   # d < 1
+    assert K.lib().cmp_mlp_features_indexed(0x10, 4, 11, 0x10, None, 0x10, None) == K.CMP_EINVAL  # no index
+    assert K.lib().cmp_mlp_features_indexed(None, 0, 11, None, None, None, None) == K.CMP_OK       # nothing
+
+
 def test_presort_rejections(K):
     assert K.lib().cmp_presort(0x10, 4, 0, 0x10, 0x10, None, 0, None) == K.CMP_EINVAL
     assert K.lib().cmp_presort(0x10, 4, 1 << 15, 0x10, 0x10, None, 0, None) == K.CMP_EWORKSPACE

@@ -179,3 +179,23 @@ def test_learned_combiner_vs_median(orc):
           f"{np.percentile(qm, 99):.1f}")
     assert np.median(ql) <= np.median(qm)
     assert np.percentile(ql, 90) < np.percentile(qm, 90)
+
+
+def test_features_indexed_equals_gathered():
+    """cmp_mlp_features_indexed (self-join sizes of all sketches, picked by index) gives the
+    features of cmp_mlp_features on the gathered per-sample arrays, -1 reading as 0."""
+    rng = np.random.default_rng(8)
+    n, d, n_sk = 500, 11, 7
+    rows = torch.from_numpy(rng.integers(-(1 << 40), 1 << 40, size=(n, d, 2)).astype(np.int64)).cuda()
+    rows[..., 1] = torch.where(rows[..., 0] < 0, -1, 0)   # sign-extended int128 values
+    f2 = torch.from_numpy(rng.uniform(0, 1e12, n_sk)).cuda()
+    idx = torch.from_numpy(rng.integers(-1, n_sk, size=(n, 2)).astype(np.int32)).cuda()
+    a = torch.where(idx[:, 0] >= 0, f2[idx[:, 0].clamp(min=0).long()], torch.zeros((), dtype=torch.float64, device="cuda"))
+    b = torch.where(idx[:, 1] >= 0, f2[idx[:, 1].clamp(min=0).long()], torch.zeros((), dtype=torch.float64, device="cuda"))
+    ref = torch.empty((n, d + 2), dtype=torch.float32, device="cuda")
+    got = torch.full_like(ref, float("nan"))
+    K.cmp_mlp_features(rows.data_ptr(), n, d, a.contiguous().data_ptr(), b.contiguous().data_ptr(), ref.data_ptr(),
+                       K.stream_handle())
+    K.cmp_mlp_features_indexed(rows.data_ptr(), n, d, f2.data_ptr(), idx.data_ptr(), got.data_ptr(), K.stream_handle())
+    torch.cuda.synchronize()
+    assert torch.equal(ref, got)
