@@ -275,6 +275,41 @@ cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, i
 cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_dev, size_t ws_bytes, double* est_dev,
                         int64_t* row_est_dev, int32_t* status_dev, void* stream);
 
+/* ------------------------------------------------------ join-order enumeration */
+/* Algorithm 1 of Sec. 5 on the estimates of a cmp_estimate run, for every join graph of a
+ * batch at once (one thread per graph; the estimates stay on the device).  From every source
+ * table in increasing f(v) = alpha card(v) / max card + beta deg(v) / max deg (card = the
+ * graph's survivors_dev, deg = join edges at v), a depth-first search extends a left-deep
+ * prefix by its neighbours in increasing estimate of the extended sub-plan, prunes a prefix
+ * whose cost exceeds the best complete plan's, and ends the source's search after max_plans
+ * complete plans.  A plan's cost is the sum of the estimates of its join prefixes of two or
+ * more tables (the first table adds nothing).  Ties go to the lower table id; a NaN estimate
+ * counts as +inf, a negative one as 0; of equal-cost plans the first found is kept.
+ *   sub_graph / sub_mask  the sub-plan list of the cmp_estimate plan whose est_dev is passed:
+ *                         est_dev[q] is the estimate of sub_mask[q] in graph sub_graph[q].
+ *                         Every connected sub-plan of two or more tables that the search
+ *                         reaches must be in it (else +inf and CMP_EUNSUPPORTED in the status).
+ *   order_dev   [n_graphs][64] int32: the best plan's tables in join order, -1 after the last
+ *               (or everywhere when no plan was found)
+ *   cost_dev    [n_graphs] double: its cost (+inf if none)
+ *   stats_dev   [n_graphs][3] int64: complete plans reached, prefix extensions, pruned prefixes
+ *   ws_dev      the search stacks, *ws_bytes from cmp_enum_plan_bytes (one per graph)
+ * A search that exceeds max_nodes prefix extensions stops with CMP_ETIMEOUT in the status
+ * (its best plan so far is reported). */
+typedef struct {
+  double alpha, beta; /* f(v) weights; both 0: 0.5 and 0.5                                */
+  int64_t max_plans;  /* complete plans per source: 0 = 10 (the paper's default), -1 = no limit */
+  int64_t max_nodes;  /* prefix extensions per graph before the search stops; 0 = 2^26      */
+} cmp_enum_cfg;
+
+cmp_status cmp_enum_plan_bytes(const cmp_graph* graphs, int32_t n_graphs, int32_t n_sub, const int32_t* sub_graph,
+                               const uint64_t* sub_mask, size_t* plan_bytes, size_t* ws_bytes);
+cmp_status cmp_enum_plan_encode(const cmp_graph* graphs, int32_t n_graphs, int32_t n_sub, const int32_t* sub_graph,
+                                const uint64_t* sub_mask, void* plan_host, size_t plan_bytes);
+cmp_status cmp_enumerate(const void* plan_host, const void* plan_dev, const double* est_dev, const cmp_enum_cfg* cfg,
+                         void* ws_dev, size_t ws_bytes, int32_t* order_dev, double* cost_dev, int64_t* stats_dev,
+                         int32_t* status_dev, void* stream);
+
 /* ------------------------------------------------------------- learned combiner */
 /* Not in the paper, which combines the d row estimates of a sketch by their median
  * (Sec. 3.2).  A 2-layer perceptron over features of the row estimates replaces the

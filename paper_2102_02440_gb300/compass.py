@@ -71,6 +71,14 @@ class cmp_graph(C.Structure):
                 ("ranks", C.POINTER(C.c_void_p)), ("slot", C.POINTER(C.c_int32)), ("survivors_dev", C.c_void_p)]
 
 
+class cmp_enum_cfg(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("max_plans", C.c_int64), ("max_nodes", C.c_int64)]
+
+    @classmethod
+    def make(cls, alpha=0.0, beta=0.0, max_plans=0, max_nodes=0):
+        return cls(alpha, beta, max_plans, max_nodes)
+
+
 _lib = None
 
 _SIGS = {
@@ -101,6 +109,12 @@ _SIGS = {
                                              C.c_size_t]),
     "cmp_estimate": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]),
+    "cmp_enum_plan_bytes": (C.c_int32, [C.POINTER(cmp_graph), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                        C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "cmp_enum_plan_encode": (C.c_int32, [C.POINTER(cmp_graph), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_size_t]),
+    "cmp_enumerate": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(cmp_enum_cfg), C.c_void_p,
+                                  C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cmp_estimate_noalloc": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cmp_mlp_param_count": (C.c_int64, [C.c_int32, C.c_int32]),
     "cmp_sketch_f2": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
@@ -271,6 +285,32 @@ def cmp_estimate_noalloc(plan_host: int, plan_dev: int, est_dev: int, row_est_de
                          stream: int):
     _check("cmp_estimate_noalloc", lib().cmp_estimate_noalloc(plan_host, plan_dev, est_dev, row_est_dev, status_dev,
                                                               stream))
+
+
+def cmp_enum_plan_bytes(graphs, sub_graph, sub_mask) -> tuple[int, int]:
+    import numpy as np
+    g = (cmp_graph * len(graphs))(*graphs)
+    sg = np.ascontiguousarray(sub_graph, np.int32)
+    sm = np.ascontiguousarray(sub_mask, np.uint64)
+    pb, wb = C.c_size_t(0), C.c_size_t(0)
+    _check("cmp_enum_plan_bytes", lib().cmp_enum_plan_bytes(g, len(graphs), sg.size, sg.ctypes.data, sm.ctypes.data,
+                                                            C.byref(pb), C.byref(wb)))
+    return pb.value, wb.value
+
+
+def cmp_enum_plan_encode(graphs, sub_graph, sub_mask, plan_host: int, plan_bytes: int):
+    import numpy as np
+    g = (cmp_graph * len(graphs))(*graphs)
+    sg = np.ascontiguousarray(sub_graph, np.int32)
+    sm = np.ascontiguousarray(sub_mask, np.uint64)
+    _check("cmp_enum_plan_encode", lib().cmp_enum_plan_encode(g, len(graphs), sg.size, sg.ctypes.data, sm.ctypes.data,
+                                                              plan_host, plan_bytes))
+
+
+def cmp_enumerate(plan_host: int, plan_dev: int, est_dev: int, cfg: cmp_enum_cfg | None, ws_dev: int, ws_bytes: int,
+                  order_dev: int, cost_dev: int, stats_dev: int, status_dev: int, stream: int):
+    _check("cmp_enumerate", lib().cmp_enumerate(plan_host, plan_dev, est_dev, C.byref(cfg) if cfg is not None else None,
+                                                ws_dev, ws_bytes, order_dev, cost_dev, stats_dev, status_dev, stream))
 
 
 def cmp_mlp_param_count(nin: int, nh: int) -> int:

@@ -215,6 +215,40 @@ class DeviceEstimator:
         return (hi * (1 << 64) + lo).tolist()
 
 
+class Enumerator:
+    """Algorithm 1 (join-order enumeration) over an estimate plan's sub-plans, for every
+    graph of the plan in one launch: run(est) reads the estimates where cmp_estimate wrote
+    them.  graphs: cmp_graph structs (edges and survivors_dev are what it uses)."""
+
+    def __init__(self, graphs, sub_graph, sub_mask, device="cuda", cfg=None):
+        self.graphs = list(graphs)
+        self.cfg = cfg
+        self.device = torch.device(device)
+        self.sub_graph = np.ascontiguousarray(sub_graph, np.int32)
+        self.sub_mask = np.ascontiguousarray(sub_mask, np.uint64)
+        pb, wb = K.cmp_enum_plan_bytes(self.graphs, self.sub_graph, self.sub_mask)
+        self.plan_host = np.zeros(max(pb, 16), np.uint8)
+        K.cmp_enum_plan_encode(self.graphs, self.sub_graph, self.sub_mask, self.plan_host.ctypes.data, pb)
+        self.plan_dev = torch.from_numpy(self.plan_host).to(self.device)
+        self.ws = torch.empty(max(wb, 16), dtype=torch.uint8, device=self.device)
+        ng = len(self.graphs)
+        self.order = torch.empty((ng, 64), dtype=torch.int32, device=self.device)
+        self.cost = torch.empty(ng, dtype=torch.float64, device=self.device)
+        self.stats = torch.empty((ng, 3), dtype=torch.int64, device=self.device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def run(self, est, stream=None):
+        K.cmp_enumerate(self.plan_host.ctypes.data, self.plan_dev.data_ptr(), est.data_ptr(), self.cfg,
+                        self.ws.data_ptr(), self.ws.numel(), self.order.data_ptr(), self.cost.data_ptr(),
+                        self.stats.data_ptr(), self.status.data_ptr(), K.stream_handle(stream))
+
+    def plans(self):
+        """[(order tuple, cost, (plans, extensions, pruned))] per graph, on the host."""
+        o, c, st = self.order.cpu().numpy(), self.cost.cpu().numpy(), self.stats.cpu().numpy()
+        return [(tuple(int(x) for x in o[g] if x >= 0), float(c[g]), tuple(int(x) for x in st[g]))
+                for g in range(len(self.graphs))]
+
+
 class PairBatch:
     """N independent two-table joins R_i |x| S_i on a key: every sketch built in one
     batched launch, all N two-way estimates in one plan (one graph per pair), and the

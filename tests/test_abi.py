@@ -213,6 +213,29 @@ def test_features_indexed_rejections(K):
     assert K.lib().cmp_mlp_features_indexed(None, 0, 11, None, None, None, None) == K.CMP_OK       # nothing
 
 
+def test_enumeration_plan_host_logic(K):
+    """Enumeration plans are encoded on the host: edges, one estimate per sub-plan."""
+    g = _graph(K, [0, 1], [1, 2], 3)
+    pb, wb = K.cmp_enum_plan_bytes([g], [0, 0, 0], [0b011, 0b110, 0b111])
+    assert pb > 0 and wb > 0
+    buf = np.zeros(pb, np.uint8)
+    K.cmp_enum_plan_encode([g], [0, 0, 0], [0b011, 0b110, 0b111], buf.ctypes.data, pb)
+    for sg, sm in (([0, 0], [0b011, 0b011]),      # the same sub-plan twice
+                   ([1], [0b011]),                # graph index out of range
+                   ([0], [0b1000]),               # table beyond the graph
+                   ([0], [0])):                   # empty sub-plan
+        with pytest.raises(K.CompassError) as ei:
+            K.cmp_enum_plan_bytes([g], sg, sm)
+        assert ei.value.status == K.CMP_EINVAL
+    with pytest.raises(K.CompassError):
+        K.cmp_enum_plan_encode([g], [0, 0, 0], [0b011, 0b110, 0b111], buf.ctypes.data, pb - 8)
+    bad = K.cmp_enum_cfg.make(max_plans=-2)
+    assert K.lib().cmp_enumerate(buf.ctypes.data, 0x1000, 0x1000, C.byref(bad), 0x1000, wb, 0x1000, 0x1000, 0x1000,
+                                 None, None) == K.CMP_EINVAL
+    assert K.lib().cmp_enumerate(buf.ctypes.data, 0x1000, 0x1000, None, 0x1000, wb - 1, 0x1000, 0x1000, 0x1000,
+                                 None, None) == K.CMP_EWORKSPACE
+
+
 def test_presort_rejections(K):
     assert K.lib().cmp_presort(0x10, 4, 0, 0x10, 0x10, None, 0, None) == K.CMP_EINVAL
     assert K.lib().cmp_presort(0x10, 4, 1 << 15, 0x10, 0x10, None, 0, None) == K.CMP_EWORKSPACE

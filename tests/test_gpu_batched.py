@@ -65,9 +65,13 @@ def test_one_plan_equals_per_graph_plans_and_oracle(orc, batch):
         assert np.array_equal(p1.row_est.cpu().numpy(), rows_all[idx])
         g = graphs[gi]
         toff, eoff = gb.table_off[gi], gb.edge_off[gi]
-        sk = [tuple(gb.dw.tables[gb.wl.sketch_of(e + eoff, end)[0]].counters[gb.wl.sketch_of(e + eoff, end)[1]]
-                    .cpu().numpy() for end in range(2)) for e in range(g.n_edges)]
-        surv = gb.dw.survivors.cpu().numpy()[toff:toff + len(g.tables)]
+        # the oracle's own build of the graph's tables (the batch's hash parameters)
+        built = [orc.build_sketch(gb.wl.tables[toff + t], gb.dw.hash_u64, gb.d, gb.w) for t in range(len(g.tables))]
+        sk = []
+        for e in range(g.n_edges):
+            ends = [gb.wl.sketch_of(e + eoff, end) for end in range(2)]
+            sk.append(tuple(built[t - toff][0][si] for t, si in ends))
+        surv = np.array([n for _, n in built], np.int64)
         for q in rng.choice(idx, min(6, idx.size), replace=False):
             ref = orc.estimate(g.edge_u, g.edge_v, sk, surv, gb.d, gb.w, int(sm[q]))
             r = rows_all[q]

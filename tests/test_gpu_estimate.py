@@ -13,19 +13,24 @@ from paper_2102_02440_gb300 import pipeline as P
 pytestmark = pytest.mark.gpu
 
 
-def _oracle_sketches(dw):
-    """sketches[e] = (u-side, v-side) as numpy [d, w], read back from the device build."""
-    out = []
+def _oracle_inputs(orc, dw):
+    """The oracle's own build of every table: sketches[e] = (u-side, v-side) as numpy
+    [d, w], and the survivor counts.  The device build must equal it (checked here too)."""
+    wl = dw.wl
+    built = [orc.build_sketch(t, dw.hash_u64, wl.d, wl.w) for t in wl.tables]
+    for (c, n), t in zip(built, dw.tables):
+        if t.k:
+            assert np.array_equal(t.counters.cpu().numpy(), c)
+    sk = []
     for e in range(dw.n_edges):
-        out.append(tuple(dw.sketch(e, end).cpu().numpy() for end in range(2)))
-    return out
+        sk.append(tuple(built[wl.sketch_of(e, end)[0]][0][wl.sketch_of(e, end)[1]] for end in range(2)))
+    return sk, np.array([n for _, n in built], np.int64)
 
 
 def _check(orc, dw, est, masks, brute=False):
     torch.cuda.synchronize()
     dw.check_status()
-    sk = _oracle_sketches(dw)
-    surv = dw.survivors.cpu().numpy()
+    sk, surv = _oracle_inputs(orc, dw)
     rows = est.row_values()
     e_gpu = est.est.cpu().numpy()
     for q, m in enumerate(masks):
@@ -118,8 +123,7 @@ def test_many_graphs_one_plan_and_replay(orc):
     off = 0
     rows = est.row_values()
     for gi, dw in enumerate(dws):
-        sk = _oracle_sketches(dw)
-        surv = dw.survivors.cpu().numpy()
+        sk, surv = _oracle_inputs(orc, dw)
         for q in range(off, off + gof.count(gi)):
             ref = orc.estimate(dw.wl.edge_u, dw.wl.edge_v, sk, surv, 5, 64, masks[q])
             assert rows[q] == ref.rows and float(est.est[q]) == ref.est

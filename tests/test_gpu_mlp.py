@@ -35,7 +35,7 @@ def _features_ref(rows, f2a, f2b):
 
 
 @pytest.fixture(scope="module")
-def small_pairs():
+def small_pairs(orc):
     pairs = G.join_pairs(300, rows_lo=200, rows_hi=20_000, dom_lo=100, dom_hi=100_000, seed=7)
     pb = P.PairBatch(pairs, d=11, w=512, hash_seed=99)
     pb.build()
@@ -44,12 +44,27 @@ def small_pairs():
     pb.features()
     torch.cuda.synchronize()
     pb.dw.check_status()
+    # the oracle's own build of every table (one sketch each): the reference inputs
+    pb.oracle_counters = np.stack([orc.build_sketch(t, pb.dw.hash_u64, pb.d, pb.w)[0][0] for t in pb.dw.wl.tables])
     return pairs, pb
+
+
+def _host_features(rng, n, nin):
+    """Feature-like inputs drawn on the host: sorted centred log row values and two sizes."""
+    x = rng.normal(0.0, 0.05, size=(n, nin)).astype(np.float32)
+    x[:, (nin - 2) // 2] = rng.uniform(0.0, 0.8, n).astype(np.float32)
+    x[:, -2:] = rng.uniform(0.0, 0.9, size=(n, 2)).astype(np.float32)
+    return x
+
+
+def test_device_counters_equal_oracle_build(small_pairs):
+    _, pb = small_pairs
+    assert np.array_equal(pb.counters.cpu().numpy(), pb.oracle_counters)
 
 
 def test_self_join_sizes_exact(small_pairs):
     _, pb = small_pairs
-    C = pb.counters.cpu().numpy().astype(object)
+    C = pb.oracle_counters.astype(object)
     f2 = pb.f2.cpu().numpy()
     for s in range(0, 2 * pb.n, 7):
         rows = sorted(int((C[s, i] ** 2).sum()) for i in range(pb.d))
@@ -60,16 +75,27 @@ def test_two_way_estimates_match_oracle(orc, small_pairs):
     _, pb = small_pairs
     rows = _rows_as_int(pb.row_est)
     est = pb.est.cpu().numpy()
-    C = pb.counters.cpu().numpy()
+    C = pb.oracle_counters
     for q in range(0, pb.n, 13):
         ref = orc.estimate([0], [1], [(C[2 * q], C[2 * q + 1])], [0, 0], pb.d, pb.w, 0b11)
         assert list(rows[q]) == ref.rows and est[q] == ref.est
 
 
-def test_features_match_definition(small_pairs):
+def test_features_match_definition(orc, small_pairs):
+    """Features from the oracle's row estimates and self-join sizes (exact integers, one
+    rounding) against the device features."""
     _, pb = small_pairs
-    rows = _rows_as_int(pb.row_est)
-    ref = _features_ref(rows, pb.f2a.cpu().numpy(), pb.f2b.cpu().numpy())
+    C = pb.oracle_counters
+    rows = np.array([orc.estimate([0], [1], [(C[2 * q], C[2 * q + 1])], [0, 0], pb.d, pb.w, 0b11).rows
+                     for q in range(pb.n)], dtype=object)
+
+    def f2(c):
+        r = sorted(int((c[i].astype(object) ** 2).sum()) for i in range(pb.d))
+        return float(r[pb.d // 2])
+
+    f2a = np.array([f2(C[2 * q]) for q in range(pb.n)])
+    f2b = np.array([f2(C[2 * q + 1]) for q in range(pb.n)])
+    ref = _features_ref(rows, f2a, f2b)
     np.testing.assert_allclose(pb.feat.cpu().numpy(), ref, rtol=1e-6, atol=1e-7)
 
 
@@ -77,8 +103,9 @@ def test_features_match_definition(small_pairs):
 def test_forward_matches_oracle(orc, small_pairs, skip):
     _, pb = small_pairs
     comb = P.Combiner(pb.d + 2, NH, seed=3, skip=skip)
-    y = comb.infer(pb.feat).cpu().numpy()
-    ref = orc.mlp_forward(pb.d + 2, NH, comb.params.cpu().numpy(), pb.feat.cpu().numpy(), skip=skip)
+    x = _host_features(np.random.default_rng(4 + skip), pb.n, pb.d + 2)
+    y = comb.infer(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = orc.mlp_forward(pb.d + 2, NH, comb.params.cpu().numpy(), x, skip=skip)
     np.testing.assert_allclose(y, ref, rtol=1e-5, atol=1e-5)
 
 
@@ -88,12 +115,13 @@ def test_gradient_and_adam_match_oracle(orc, small_pairs, skip, huber):
     rng = np.random.default_rng(5)
     nin = pb.d + 2
     comb = P.Combiner(nin, NH, seed=4, skip=skip)
-    x = pb.feat
-    t = torch.from_numpy(rng.standard_normal(pb.n).astype(np.float32) * 0.3 + 0.5).cuda()
+    xh = _host_features(rng, pb.n, nin)
+    th = rng.standard_normal(pb.n).astype(np.float32) * 0.3 + 0.5
+    x, t = torch.from_numpy(xh).cuda(), torch.from_numpy(th).cuda()
     p0 = comb.params.cpu().numpy().copy()
     comb.train_step(x, t, lr=1e-3, huber_delta=huber or 0.0)
     torch.cuda.synchronize()
-    loss_ref, g_ref = orc.mlp_loss_grad(nin, NH, p0, x.cpu().numpy(), t.cpu().numpy(), skip=skip, huber_delta=huber)
+    loss_ref, g_ref = orc.mlp_loss_grad(nin, NH, p0, xh, th, skip=skip, huber_delta=huber)
     g = comb.grad.cpu().numpy().astype(np.float64)
     assert abs(float(comb.loss.item()) - loss_ref) <= 1e-5 * abs(loss_ref) + 1e-7
     np.testing.assert_allclose(g, g_ref, rtol=1e-4, atol=1e-6 * np.abs(g_ref).max())

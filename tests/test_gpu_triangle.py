@@ -44,10 +44,20 @@ def _raw_workload(rng, eu, ev, nt, d, w):
 
 
 def _fill(dw, rng, lo, hi, zero_p):
+    """Counters drawn on the host (kept in dw.host_counters for the oracle) and uploaded."""
+    dw.host_counters = []
     for t in dw.tables:
         a = rng.integers(lo, hi + 1, size=tuple(t.counters.shape), dtype=np.int64)
         a[rng.random(a.shape) < zero_p] = 0
-        t.counters.copy_(torch.from_numpy(a.astype(np.int32)))
+        a = a.astype(np.int32)
+        dw.host_counters.append(a)
+        t.counters.copy_(torch.from_numpy(a))
+
+
+def _set_row(dw, t, s, r, values):
+    """Overwrite one counter row on the host copy and the device."""
+    dw.host_counters[t][s, r] = values
+    dw.tables[t].counters[s, r] = torch.from_numpy(np.ascontiguousarray(dw.host_counters[t][s, r])).cuda()
 
 
 def _run(dw, masks, cfg=None):
@@ -60,9 +70,12 @@ def _run(dw, masks, cfg=None):
 
 
 def _oracle_rows(orc, dw, masks):
-    sk = [tuple(dw.sketch(e, end).cpu().numpy() for end in range(2)) for e in range(dw.n_edges)]
-    surv = dw.survivors.cpu().numpy()
-    return [orc.estimate(dw.wl.edge_u, dw.wl.edge_v, sk, surv, dw.d, dw.w, int(m)) for m in masks]
+    """Oracle estimates on the host counters the test drew (every table survivor count 1)."""
+    wl = dw.wl
+    sk = [tuple(dw.host_counters[wl.sketch_of(e, end)[0]][wl.sketch_of(e, end)[1]] for end in range(2))
+          for e in range(dw.n_edges)]
+    surv = np.ones(len(wl.tables), np.int64)
+    return [orc.estimate(wl.edge_u, wl.edge_v, sk, surv, dw.d, dw.w, int(m)) for m in masks]
 
 
 def _cyclic(masks, eu, ev):
@@ -107,8 +120,7 @@ def test_triangle_both_row_sides(orc):
     t2, s2 = dw.wl.sketch_of(1, 1)
     for r in range(4):
         narrow = (t1, s1) if r % 2 == 0 else (t2, s2)
-        dw.tables[narrow[0]].counters[narrow[1], r] = torch.from_numpy(
-            rng.integers(-1, 2, size=200).astype(np.int32)).cuda()
+        _set_row(dw, narrow[0], narrow[1], r, rng.integers(-1, 2, size=200).astype(np.int32))
     masks = [0b0111, 0b1111]
     tri, st = _run(dw, masks)
     assert st == 0
@@ -123,9 +135,10 @@ def test_triangle_without_nonzero_conditioning_values(orc):
     dw = _raw_workload(rng, eu, ev, 3, 3, 64)
     _fill(dw, rng, -5, 5, 0.2)
     t, s = dw.wl.sketch_of(1, 0)        # conditioned edge e1 = 1-2
-    dw.tables[t].counters[s, 0] = 0      # row 0: no conditioning value survives
-    dw.tables[t].counters[s, 1] = 0
-    dw.tables[t].counters[s, 1, 17] = 3  # row 1: exactly one
+    _set_row(dw, t, s, 0, 0)             # row 0: no conditioning value survives
+    row1 = np.zeros(64, np.int32)
+    row1[17] = 3                         # row 1: exactly one
+    _set_row(dw, t, s, 1, row1)
     tri, st = _run(dw, [0b111])
     assert st == 0
     ref = _oracle_rows(orc, dw, [0b111])[0]
@@ -152,8 +165,7 @@ def test_triangle_int128_overflow_is_reported(orc):
     rng = np.random.default_rng(9)
     eu, ev = [0, 1, 0, 0, 1, 2], [1, 2, 2, 3, 4, 5]
     dw = _raw_workload(rng, eu, ev, 6, 3, 32)
-    for t in dw.tables:
-        t.counters.fill_(2 ** 31 - 1)
+    _fill(dw, rng, 2 ** 31 - 1, 2 ** 31 - 1, 0.0)
     tri, st = _run(dw, [0b111111])
     assert st == K.CMP_EOVERFLOW and np.isnan(float(tri.est[0]))
     gen, st2 = _run(dw, [0b111111], GENERIC)
