@@ -1,8 +1,9 @@
 #!/usr/bin/env python
 """Benchmark of the COMPASS hot path on GB300: one step = the push-down Fast-AGMS build of
-every attribute-level sketch of a query's tables (one batched launch), the magnitude
-presort, the sketch-merging estimate of every connected sub-plan (one launch + finalize)
-and the learned combiner's inference over the sub-plan row estimates.
+every attribute-level sketch of a query's tables (one batched build), the magnitude
+presort and cross ranks, the sketch-merging estimate of every connected sub-plan, the
+learned combiner's inference over the sub-plan row estimates, and the join-order
+enumeration (Algorithm 1) over the combined estimates; replayed as one CUDA graph.
 
 Workload (N = 1): the 5-table cyclic join graph shaped like the paper's running example
 (F1 36M, F2 4.5M, D1 2.5M, D2 134k, D3 4M rows; Zipf(1.1) foreign keys; point, subset
@@ -452,6 +453,9 @@ def run_ours(a):
         K.cmp_mlp_infer(comb.params.data_ptr(), wl.d + 2, 64, wl.d // 2, feat.data_ptr(), n_sub, y_mlp.data_ptr(), s)
         K.cmp_mlp_combine(est.est.data_ptr(), y_mlp.data_ptr(), n_sub, est_comb.data_ptr(), s)
 
+    # join-order enumeration (Algorithm 1, max_plans = 10) over the combined estimates
+    enum = P.Enumerator(est.graphs, np.zeros(n_sub, np.int32), masks, device=dev)
+
     def step(evs=None):
         s = K.stream_handle(stream)
         if evs:
@@ -468,6 +472,9 @@ def run_ours(a):
         combiner(s)
         if evs:
             evs[4].record(stream)
+        enum.run(est_comb, stream=stream)
+        if evs:
+            evs[5].record(stream)
 
     torch.cuda.synchronize(dev)
     with torch.cuda.stream(stream):
@@ -479,7 +486,7 @@ def run_ours(a):
     # per-launch host overhead); its outputs must equal the eager step's bit for bit
     graph = None
     if not a.no_graph:
-        eager_out = (est.row_est.clone(), est.est.clone(), est_comb.clone())
+        eager_out = (est.row_est.clone(), est.est.clone(), est_comb.clone(), enum.order.clone())
         with torch.cuda.stream(stream):
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph, stream=stream):
@@ -488,7 +495,8 @@ def run_ours(a):
                 graph.replay()
         torch.cuda.synchronize(dev)
         dw.check_status()
-        if not (torch.equal(eager_out[0], est.row_est) and torch.equal(eager_out[1].nan_to_num(-1.0),
+        if not (torch.equal(eager_out[3], enum.order) and torch.equal(eager_out[0], est.row_est) and
+                torch.equal(eager_out[1].nan_to_num(-1.0),
                                                                      est.est.nan_to_num(-1.0))
                 and torch.equal(eager_out[2].nan_to_num(-1.0), est_comb.nan_to_num(-1.0))):
             raise RuntimeError("graph replay of the step differs from the eager step")
@@ -518,17 +526,17 @@ def run_ours(a):
     step_ms = [e[0].elapsed_time(e[1]) for e in evs]
     ms = statistics.mean(step_ms)
     # per-phase split from eager steps with events between the phases (outside the timing)
-    pevs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(a.steps)]
+    pevs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(a.steps)]
     with torch.cuda.stream(stream):
         for k in range(a.steps):
             flush.zero_()
             step(pevs[k])
     torch.cuda.synchronize(dev)
-    per = [[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in pevs]
+    per = [[e[i].elapsed_time(e[i + 1]) for i in range(5)] for e in pevs]
     rows = wl.total_rows
     value, ms_max = whole_job_rate(rows, ms, world)
     phase = {n: statistics.mean(p[i] for p in per)
-             for i, n in enumerate(("build", "presort", "estimate", "combiner"))}
+             for i, n in enumerate(("build", "presort", "estimate", "combiner", "enumerate"))}
     n_est = len(masks)
 
     # roofline of the dominant phase: the batched build (zero spans, key range, clearing,
@@ -604,8 +612,8 @@ def run_ours(a):
     # aggregates key columns (it then has a workspace)
     build_launches = 2 + (3 if dw._plan[2] else 0)
     # presort + cross ranks of all tables: one launch each; combiner: self-join sizes, features,
-    # inference, combination
-    launches_per_step = build_launches + 2 + est_launches + 4
+    # inference, combination; enumeration: one launch
+    launches_per_step = build_launches + 2 + est_launches + 4 + 1
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -618,6 +626,8 @@ def run_ours(a):
                            "phases": "from eager steps with events between phases",
                            "parallelism": f"replicas x{world} (independent queries)"},
                 "phases_ms": phase, "subplan_estimates_per_s": n_est / (phase["estimate"] / 1e3),
+                "plan": {"order": [wl.tables[t].name for t in enum.plans()[0][0]], "cost": enum.plans()[0][1],
+                         "search": dict(zip(("complete_plans", "extensions", "pruned"), enum.plans()[0][2]))},
                 "autotuned": {"build": tuned_build["cfg"], "estimate": tuned_est["cfg"]},
                 "build_only_tuples_per_s": rows / (phase["build"] / 1e3),
                 "survivors": [int(x) for x in surv],
@@ -675,6 +685,7 @@ def run_batched(a):
       the batched build + presort + estimate captured in one CUDA graph vs eager."""
     import torch
 
+    from paper_2102_02440_gb300 import compass as K
     from paper_2102_02440_gb300 import datagen as G
     from paper_2102_02440_gb300 import pipeline as P
     graphs = G.graph_batch(64, 4, 17, rows_lo=10_000, rows_hi=1_000_000, d=11, w=1024)
@@ -730,6 +741,16 @@ def run_batched(a):
     # with CMP_EOVERFLOW in the status word; count them instead of failing
     n_ovf = int(torch.isnan(plan.est).sum().item())
     gb.dw.status.zero_()
+    # join-order enumeration of every graph in one launch (Algorithm 1, max_plans = 10 and 1)
+    enum_ms, enum_stats = {}, {}
+    for mp in (10, 1):
+        en = P.Enumerator(gb.graph_structs(), sg, sm, cfg=K.cmp_enum_cfg.make(max_plans=mp, max_nodes=1 << 20))
+        enum_ms[f"max_plans_{mp}"] = timed(lambda: en.run(plan.est), 5)
+        res = en.plans()
+        enum_stats[f"max_plans_{mp}"] = {"plans_found": sum(1 for o, c, st in res if o),
+                                         "extensions": sum(st[1] for o, c, st in res),
+                                         "complete_plans": sum(st[0] for o, c, st in res),
+                                         "status": int(en.status.item())}
     n_tables = len(gb.wl.tables)
     line = {"case": "batched enumeration", "graphs": len(graphs), "tables": n_tables, "rows": gb.total_rows,
             "subplans": int(sm.size), "d": 11, "w": 1024,
@@ -741,6 +762,7 @@ def run_batched(a):
                          "speedup": (sm.size / (ms_est_b / 1e3)) / (samp.size / (ms_est_1 / 1e3))},
             "sequence_ms": {"eager": ms_eager, "cuda_graph": ms_graph},
             "subplans_beyond_int128": n_ovf,
+            "enumeration_ms": enum_ms, "enumeration": enum_stats,
             "kinds": {k: sum(1 for g in graphs if g.name.startswith(k)) for k in ("chain", "star", "cycle")}}
     print(json.dumps(line), flush=True)
 
