@@ -56,7 +56,8 @@ def _args():
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of autotuned launch shapes: read if it has this workload's, else written")
     ap.add_argument("--case", default=None,
-                    choices=["estimate_small", "estimate_full", "build_f1", "build_five", "batched", "scale"],
+                    choices=["estimate_small", "estimate_full", "build_f1", "build_five", "batched", "scale",
+                             "partition"],
                     help="run one small profiling case instead of the benchmark (for ncu captures)")
     return ap.parse_args()
 
@@ -809,12 +810,100 @@ def run_scale(a):
                       "estimates": est.est.cpu().numpy().tolist()}), flush=True)
 
 
+def chain_join_size(wl) -> int:
+    """Exact size of D2 |x| F2 |x| D1 (tables 3, 1, 2 over edges e0, e1) of the five-table
+    workload, from the columns on the host: per F2 tuple, the number of selected D2 tuples
+    with its keyword key times the number of selected D1 tuples with its movie key."""
+    def counts(t, col, dom):
+        tb = wl.tables[t]
+        keep = np.ones(tb.n_rows, bool)
+        for q in tb.preds:
+            v = tb.cols[q.col].astype(np.int64)
+            keep &= (q.lo <= v) & (v < q.hi) if q.op == 0 else (v == q.lo)
+        return np.bincount(tb.cols[col][keep].astype(np.int64), minlength=dom)
+    f2 = wl.tables[1]
+    kw = counts(3, 0, int(max(f2.cols[0].max(), wl.tables[3].cols[0].max())) + 1)
+    mv = counts(2, 0, int(max(f2.cols[1].max(), wl.tables[2].cols[0].max())) + 1)
+    return int((kw[f2.cols[0].astype(np.int64)] * mv[f2.cols[1].astype(np.int64)]).sum())
+
+
+def run_partition(a):
+    """Sketch partitioning (Sec. 4.1) on the k - mk - t chain of the five-table workload at
+    full scale: D2 |x| F2 |x| D1 over edges e0 (keyword) and e1 (movie), F2 with the 2-axis
+    tensor.  For two width configurations, equal memory (64 x 64 counters per F2 row: the
+    4096 buckets of a 1-D row rearranged, so D2 and D1 get 64 buckets) and equal width
+    (4096 x 4096: the merged sketches' width on both edges), the build of the three
+    partitioned sketches and the contraction estimate are timed with CUDA events (median of
+    10 after 3 warm-ups); the estimate is compared with the exact join size and with the
+    merged 1-D estimate of the same sub-plan (w = 4096)."""
+    import torch
+
+    from paper_2102_02440_gb300 import datagen as G
+    from paper_2102_02440_gb300 import pipeline as P
+    wl = G.five_table(scale=a.scale, w=4096)
+    dw = P.DeviceWorkload(wl)
+    dw.build_batched()
+    mask = (1 << 3) | (1 << 1) | (1 << 2)
+    est_m = P.DeviceEstimator(dw, [mask])
+    est_m.presort()
+    est_m.estimate()
+    torch.cuda.synchronize()
+    merged = float(est_m.est.item())
+    exact = chain_join_size(wl)
+    hbm_peak, kind = _peaks()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=10, warm=3):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        return statistics.median(ts)
+
+    def qerr(x):
+        return max(x, 1.0) / max(exact, 1.0) if x >= exact else max(exact, 1.0) / max(x, 1.0)
+
+    configs = {}
+    for name, widths in (("equal_memory_64x64", [64, 64]), ("equal_width_4096x4096", [4096, 4096])):
+        pj = P.PartitionedJoin(wl, [3, 1, 2], [0, 1], widths, cols_dev=[dw.tables[t].cols for t in (3, 1, 2)],
+                               hash_dev=dw.hash_dev)
+        ms_build = timed(pj.build)
+        ms_est = timed(pj.estimate)
+        if int(pj.status.item()) != 0:
+            raise RuntimeError(f"device status {int(pj.status.item())}")
+        surv = [int(x) for x in pj.survivors.cpu().numpy()]
+        est = float(pj.est.item())
+        tensor_bytes = sum(x.numel() * 4 for x in pj.tensors)
+        evals = sum(n * len(ax) * wl.d for n, ax in zip(surv, pj.axes))
+        configs[name] = {
+            "widths": widths, "tensor_bytes": tensor_bytes, "survivors": surv,
+            "build_ms": ms_build, "estimate_ms": ms_est, "estimate": est, "q_error": qerr(est),
+            "build_alu": {"cw_evaluations": evals, "frac": evals * CW_INSTR / (ms_build / 1e3) / INT_ISSUE_PEAK},
+            "estimate_hbm": {"bytes": tensor_bytes, "achieved_gbs": tensor_bytes / (ms_est / 1e3) / 1e9,
+                             "peak_gbs": hbm_peak, "frac": tensor_bytes / (ms_est / 1e3) / 1e9 / hbm_peak,
+                             "peak_kind": kind},
+        }
+        del pj
+        torch.cuda.empty_cache()
+    print(json.dumps({"case": "partition", "workload": wl.name, "join": "D2 |x| F2 |x| D1 (e0, e1)", "d": wl.d,
+                      "exact": exact, "merged_1d_w4096": {"estimate": merged, "q_error": qerr(merged)},
+                      "partitioned": configs}), flush=True)
+
+
 def main():
     a = _args()
     if a.case == "batched":
         run_batched(a)
     elif a.case == "scale":
         run_scale(a)
+    elif a.case == "partition":
+        run_partition(a)
     elif a.case:
         run_case(a)
     elif a.impl == "reference":

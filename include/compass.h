@@ -113,7 +113,7 @@ typedef struct {
 /* ---------------------------------------------------------------------- general */
 
 /* Version of this interface (CMP_ABI_VERSION); bindings refuse a library that differs. */
-#define CMP_ABI_VERSION 2
+#define CMP_ABI_VERSION 3
 int32_t cmp_abi_version(void);
 const char* cmp_status_str(cmp_status s);
 
@@ -274,6 +274,79 @@ cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, i
                                     void* plan_host, size_t plan_bytes);
 cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_dev, size_t ws_bytes, double* est_dev,
                         int64_t* row_est_dev, int32_t* status_dev, void* stream);
+
+/* ------------------------------------------------------- partitioned sketches */
+/* Sketch partitioning (Sec. 4.1): the unbiased estimator of a fixed multi-way join.  A
+ * table that joins through edges e_1..e_k gets, per sketch row i, a k-dimensional tensor
+ * of width[e_1] x ... x width[e_k] int32 counters (axis l for edge e_l, row-major: the last
+ * axis is contiguous; layout [d][prod of its widths]).  Every tuple that satisfies the
+ * table's selection adds xi_{e_1,i}(key_1) * ... * xi_{e_k,i}(key_k) to the counter at
+ * (h_{e_1,i}(key_1), ..., h_{e_k,i}(key_k)), where h and xi are the (edge, row) functions of
+ * cmp_hash with the edge's own width, which both endpoint tables of an edge use.  A one-axis
+ * tensor is the 1-D sketch of cmp_sketch_build; a zero-axis tensor holds the selected count.
+ * Unlike merged 1-D sketches, the tensors serve only the join they were built for. */
+#define CMP_PART_MAX_AXES 4
+#define CMP_PART_MAX_SIZE 2147483647LL /* counters per tensor row */
+
+/* Build launch shape; zero fields choose automatically. */
+typedef struct {
+  int32_t mode;         /* 0 auto, 1 shared-memory private tensors, 2 L2-resident global counters */
+  int32_t rows_per_cta; /* sketch rows a CTA updates (mode 1: rows whose tensors it privatises)   */
+  int32_t threads;      /* threads per CTA (multiple of 32, <= 1024)                              */
+  int32_t tile_rows;    /* rows per tile (multiple of 128, <= 16384)                              */
+  int32_t ctas_per_sm;  /* CTAs per SM the grid is sized for                                      */
+  int32_t reserved;
+} cmp_part_build_cfg;
+
+/* Builds the partitioned sketch of one table.  Its axes are the table's sketches in order:
+ * axis l joins on edge table->edge_id[l] with key column table->key_col[l] (distinct edges,
+ * 0 .. CMP_PART_MAX_AXES of them).
+ *   width_host    [n_sketches] buckets per axis, 1 .. CMP_MAX_W, product <= CMP_PART_MAX_SIZE
+ *   hash_dev      [n_edges * d] parameters (cmp_hash_params)
+ *   counters_dev  [d][prod width_host] int32, overwritten
+ *   survivors_dev one int64, overwritten with the exact selected count
+ * Counters are int32 and wrap-exact; results are identical for every launch shape.  Enqueues
+ * two memsets and one kernel on `stream`. */
+cmp_status cmp_part_build(const cmp_table* table, int32_t d, const int32_t* width_host, const cmp_hash* hash_dev,
+                          int32_t n_edges, int32_t* counters_dev, int64_t* survivors_dev,
+                          const cmp_part_build_cfg* cfg, void* stream);
+
+/* A tree-shaped join over partitioned sketches (host arrays; tensor entries are device
+ * pointers).  The edges form a spanning tree of the tables, and table t's axes are exactly
+ * its incident edges, in the order of its tensor. */
+typedef struct {
+  int32_t n_tables;               /* 1 .. CMP_MAX_TABLES                                   */
+  int32_t n_edges;                /* n_tables - 1                                          */
+  const int32_t* edge_u;          /* [n_edges]                                             */
+  const int32_t* edge_v;          /* [n_edges]                                             */
+  const int32_t* width;           /* [n_edges] buckets of each edge                        */
+  const int32_t* n_axes;          /* [n_tables]                                            */
+  const int32_t* axis_edge;       /* table 0's axes, then table 1's, ... (sum n_axes)      */
+  const int32_t* const* tensor;   /* [n_tables] device [d][prod of the table's widths]     */
+} cmp_part_join;
+
+/* Estimate of the join (Sec. 4.1): per sketch row i the exact integer
+ *   E_i = sum over all bucket assignments j of the edges of prod over tables t of T_t[i][j|t],
+ * the full contraction of the tables' tensors (for the chain k - mk - t, the sum over i, j
+ * of sk_k[i] sk_part(mk)[i, j] sk_t[j]); the estimate is the median of E_0..E_{d-1}
+ * (Sec. 3.2), rounded once to double (even d: the mean of the two middle values).
+ * Evaluation order (it fixes which rows are out of range): the tree is rooted at table 0; a
+ * table's message to its parent is its tensor with every child axis contracted, the root's
+ * value is its tensor with every axis contracted; a table contracts its child axes one at a
+ * time, last axis first, each contraction multiplying every entry by the child's message
+ * entry at its index on that axis and summing over the axis; a leaf's message is its own
+ * tensor.  Values are int128 and sums are exact; a row where a single product or a value
+ * after a contraction leaves int128 has est NaN and CMP_EOVERFLOW in the status.
+ *   ws_dev       *ws_bytes from cmp_part_estimate_ws_bytes (intermediate messages), caller-owned
+ *   est_dev      one double
+ *   row_est_dev  NULL or [d][2] int64: each row value as a little-endian two's-complement
+ *                int128 (low word first; unspecified for out-of-range rows)
+ * One launch per contracted edge plus one finalize launch (no host synchronisation; can be
+ * captured in a CUDA graph).  CMP_EINVAL for a join that is not a tree or whose axes do not
+ * match its edges; CMP_EWORKSPACE if ws_bytes is too small. */
+cmp_status cmp_part_estimate_ws_bytes(const cmp_part_join* join, int32_t d, size_t* ws_bytes);
+cmp_status cmp_part_estimate(const cmp_part_join* join, int32_t d, void* ws_dev, size_t ws_bytes, double* est_dev,
+                             int64_t* row_est_dev, int32_t* status_dev, void* stream);
 
 /* ------------------------------------------------------ join-order enumeration */
 /* Algorithm 1 of Sec. 5 on the estimates of a cmp_estimate run, for every join graph of a

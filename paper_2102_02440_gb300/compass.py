@@ -16,7 +16,8 @@ CMP_OK, CMP_EINVAL, CMP_EUNSUPPORTED, CMP_EOVERFLOW, CMP_ECUDA, CMP_EWORKSPACE, 
 CMP_I32, CMP_I64 = 0, 1
 CMP_RANGE, CMP_EQ, CMP_IN_BITMAP = 0, 1, 2
 CMP_EST_GENERIC_ONLY = 1
-CMP_ABI_VERSION = 2
+CMP_ABI_VERSION = 3
+CMP_PART_MAX_AXES = 4
 CMP_MAX_COLS, CMP_MAX_PREDS, CMP_MAX_SKETCHES, CMP_MAX_D = 32, 8, 16, 64
 
 
@@ -79,6 +80,21 @@ class cmp_enum_cfg(C.Structure):
         return cls(alpha, beta, max_plans, max_nodes)
 
 
+class cmp_part_build_cfg(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("rows_per_cta", C.c_int32), ("threads", C.c_int32), ("tile_rows", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("reserved", C.c_int32)]
+
+    @classmethod
+    def make(cls, mode=0, rows_per_cta=0, threads=0, tile_rows=0, ctas_per_sm=0):
+        return cls(mode, rows_per_cta, threads, tile_rows, ctas_per_sm, 0)
+
+
+class cmp_part_join(C.Structure):
+    _fields_ = [("n_tables", C.c_int32), ("n_edges", C.c_int32), ("edge_u", C.POINTER(C.c_int32)),
+                ("edge_v", C.POINTER(C.c_int32)), ("width", C.POINTER(C.c_int32)), ("n_axes", C.POINTER(C.c_int32)),
+                ("axis_edge", C.POINTER(C.c_int32)), ("tensor", C.POINTER(C.c_void_p))]
+
+
 _lib = None
 
 _SIGS = {
@@ -116,6 +132,11 @@ _SIGS = {
     "cmp_enumerate": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(cmp_enum_cfg), C.c_void_p,
                                   C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cmp_estimate_noalloc": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cmp_part_build": (C.c_int32, [C.POINTER(cmp_table), C.c_int32, C.POINTER(C.c_int32), C.c_void_p, C.c_int32,
+                                   C.c_void_p, C.c_void_p, C.POINTER(cmp_part_build_cfg), C.c_void_p]),
+    "cmp_part_estimate_ws_bytes": (C.c_int32, [C.POINTER(cmp_part_join), C.c_int32, C.POINTER(C.c_size_t)]),
+    "cmp_part_estimate": (C.c_int32, [C.POINTER(cmp_part_join), C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p]),
     "cmp_mlp_param_count": (C.c_int64, [C.c_int32, C.c_int32]),
     "cmp_sketch_f2": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "cmp_mlp_features": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -311,6 +332,35 @@ def cmp_enumerate(plan_host: int, plan_dev: int, est_dev: int, cfg: cmp_enum_cfg
                   order_dev: int, cost_dev: int, stats_dev: int, status_dev: int, stream: int):
     _check("cmp_enumerate", lib().cmp_enumerate(plan_host, plan_dev, est_dev, C.byref(cfg) if cfg is not None else None,
                                                 ws_dev, ws_bytes, order_dev, cost_dev, stats_dev, status_dev, stream))
+
+
+def cmp_part_build(table: cmp_table, d: int, widths, hash_dev: int, n_edges: int, counters_dev: int,
+                   survivors_dev: int, cfg: cmp_part_build_cfg | None, stream: int):
+    wa = (C.c_int32 * max(len(widths), 1))(*widths)
+    _check("cmp_part_build", lib().cmp_part_build(C.byref(table), d, wa, hash_dev, n_edges, counters_dev, survivors_dev,
+                                                  C.byref(cfg) if cfg is not None else None, stream))
+
+
+def part_join(edge_u, edge_v, width, axes, tensor_ptrs):
+    """A cmp_part_join and the ctypes arrays it points into (keep both alive)."""
+    ne, nt = len(edge_u), len(axes)
+    keep = [(C.c_int32 * max(ne, 1))(*edge_u), (C.c_int32 * max(ne, 1))(*edge_v), (C.c_int32 * max(ne, 1))(*width),
+            (C.c_int32 * max(nt, 1))(*[len(a) for a in axes]),
+            (C.c_int32 * max(sum(len(a) for a in axes), 1))(*[e for a in axes for e in a]),
+            (C.c_void_p * max(nt, 1))(*tensor_ptrs)]
+    return cmp_part_join(nt, ne, *keep), keep
+
+
+def cmp_part_estimate_ws_bytes(join: cmp_part_join, d: int) -> int:
+    n = C.c_size_t(0)
+    _check("cmp_part_estimate_ws_bytes", lib().cmp_part_estimate_ws_bytes(C.byref(join), d, C.byref(n)))
+    return n.value
+
+
+def cmp_part_estimate(join: cmp_part_join, d: int, ws_dev: int, ws_bytes: int, est_dev: int, row_est_dev: int,
+                      status_dev: int, stream: int):
+    _check("cmp_part_estimate", lib().cmp_part_estimate(C.byref(join), d, ws_dev, ws_bytes, est_dev, row_est_dev,
+                                                        status_dev, stream))
 
 
 def cmp_mlp_param_count(nin: int, nh: int) -> int:

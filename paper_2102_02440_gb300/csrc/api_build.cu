@@ -30,19 +30,9 @@ size_t smem_optin_bytes() {
 }
 
 namespace {
-
-struct SplitMix64 {  // Steele, Lea & Flood 2014
-  uint64_t s;
-  uint64_t next() {
-    s += 0x9E3779B97F4A7C15ull;
-    uint64_t z = s;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-  }
-};
-
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+}  // namespace
 
 cmp_status check_table(const cmp_table* t, int32_t d, int32_t w, int32_t n_edges) {
   if (!t || d < 1 || d > CMP_MAX_D || w < 1 || w > CMP_MAX_W || n_edges < 0) return CMP_EINVAL;
@@ -99,6 +89,19 @@ DevTable to_dev(const cmp_table* t, int32_t* counters, int64_t* survivors) {
   for (int c = 0; c < CMP_MAX_COLS; c++) D.agg[c] = -1;
   return D;
 }
+
+namespace {
+
+struct SplitMix64 {  // Steele, Lea & Flood 2014
+  uint64_t s;
+  uint64_t next() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+};
 
 uint32_t next_pow2(uint32_t v) {
   uint32_t p = 1;

@@ -28,95 +28,17 @@
 #include <type_traits>
 
 #include "internal.cuh"
+#include "tile.cuh"
 
 namespace cmpk {
 
 namespace {
-
-__device__ __forceinline__ int64_t load1(const void* base, int32_t dtype, int64_t row) {
-  return dtype == CMP_I32 ? int64_t(__ldg(reinterpret_cast<const int32_t*>(base) + row))
-                          : int64_t(__ldg(reinterpret_cast<const long long*>(base) + row));
-}
-
-// 4 consecutive rows starting at `row` (row % 4 == 0); nvalid in 0..4.
-__device__ __forceinline__ void load4(const void* base, int32_t dtype, int64_t row, int nvalid, bool vec,
-                                      int64_t v[4]) {
-  if (dtype == CMP_I32) {
-    const int32_t* p = reinterpret_cast<const int32_t*>(base) + row;
-    if (vec && nvalid == 4) {
-      const int4 q = __ldg(reinterpret_cast<const int4*>(p));
-      v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; k++) v[k] = k < nvalid ? int64_t(__ldg(p + k)) : 0;
-    }
-  } else {
-    const long long* p = reinterpret_cast<const long long*>(base) + row;
-    if (vec && nvalid == 4) {
-      const longlong2 a = __ldg(reinterpret_cast<const longlong2*>(p));
-      const longlong2 b = __ldg(reinterpret_cast<const longlong2*>(p + 2));
-      v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; k++) v[k] = k < nvalid ? int64_t(__ldg(p + k)) : 0;
-    }
-  }
-}
-
-__device__ __forceinline__ bool pred_holds(const DevPred& q, int64_t v) {
-  if (q.op == CMP_RANGE) return q.lo <= v && v < q.hi;
-  if (q.op == CMP_EQ) return v == q.lo;
-  if (v < 0 || v >= q.nbits) return false;
-  return (__ldg(q.bitmap + (v >> 5)) >> (v & 31)) & 1u;
-}
 
 __device__ __forceinline__ uint32_t map_slot(uint64_t x, uint32_t mask) {
   return uint32_t((x * 0x9E3779B97F4A7C15ull) >> 40) & mask;
 }
 
 constexpr int kMaxSlotsPerThread = 8;
-
-// Phase A of one tile: the predicate conjunction over rows [r0, r0 + rows_in_tile), the
-// survivors' offsets compacted into surv[] (warp scan, one shared atomic per warp).
-// Returns the survivor count.  Block-wide: every thread calls it; sint[0] is the tail.
-__device__ int tile_survivors(const DevTable* tb, int64_t r0, int rows_in_tile, int R, bool vec, uint16_t* surv,
-                              int32_t* sint) {
-  const int n_preds = tb->n_preds;
-  if (n_preds == 0) return rows_in_tile;
-  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
-  if (tid == 0) sint[0] = 0;
-  __syncthreads();
-  const int iters = (R + 4 * T - 1) / (4 * T);
-  for (int it = 0; it < iters; it++) {
-    const int base = 4 * (tid + it * T);
-    const int nvalid = max(0, min(4, rows_in_tile - base));
-    uint32_t m = (1u << nvalid) - 1u;
-    for (int q = 0; q < n_preds && m; q++) {
-      const DevPred& pq = tb->pred[q];
-      int64_t v[4];
-      load4(tb->col[pq.col], tb->dtype[pq.col], r0 + base, nvalid, vec, v);
-#pragma unroll
-      for (int k = 0; k < 4; k++)
-        if (!pred_holds(pq, v[k])) m &= ~(1u << k);
-    }
-    const int c = __popc(m);
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    int wbase = 0;
-    if (lane == 31) wbase = atomicAdd(&sint[0], incl);
-    wbase = __shfl_sync(0xffffffffu, wbase, 31);
-    int pos = wbase + incl - c;
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-      if ((m >> k) & 1u) surv[pos++] = uint16_t(base + k);
-  }
-  __syncthreads();
-  return sint[0];
-}
 
 }  // namespace
 

@@ -76,6 +76,19 @@ __device__ __forceinline__ bool mul_ovf(i128 a, i128 b, i128* r) {
   return ovf;
 }
 
+// exact (a + b) / 2 rounded once (the sum may need 129 bits)
+__device__ __forceinline__ double mean2_to_double(i128 a, i128 b) {
+  i128 s;
+  if (!add_ovf(a, b, &s)) return i128_to_double(s) * 0.5;
+  // same signs overflowed: |a| + |b| = 2^128 * top + low
+  const bool neg = a < 0;
+  const u128 ua = neg ? u128(0) - u128(a) : u128(a);
+  const u128 ub = neg ? u128(0) - u128(b) : u128(b);
+  const u128 low = ua + ub;
+  const uint32_t top = low < ua ? 1u : 0u;
+  return mag_to_double(neg, top, low) * 0.5;
+}
+
 // first position q in sorted a[0..w) with a[q] > tau (strict) or a[q] >= tau
 __device__ __forceinline__ int rank_of(const uint32_t* __restrict__ a, int w, uint32_t tau, bool strict) {
   int lo = 0, hi = w;

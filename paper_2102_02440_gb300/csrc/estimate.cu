@@ -23,19 +23,6 @@
 
 namespace cmpk {
 
-// exact (a + b) / 2 rounded once (the sum may need 129 bits)
-__device__ double mean2_to_double(i128 a, i128 b) {
-  i128 s;
-  if (!add_ovf(a, b, &s)) return i128_to_double(s) * 0.5;
-  // same signs overflowed: |a| + |b| = 2^128 * top + low
-  const bool neg = a < 0;
-  const u128 ua = neg ? u128(0) - u128(a) : u128(a);
-  const u128 ub = neg ? u128(0) - u128(b) : u128(b);
-  const u128 low = ua + ub;
-  const uint32_t top = low < ua ? 1u : 0u;
-  return mag_to_double(neg, top, low) * 0.5;
-}
-
 // ---------------------------------------------------------------- presort
 // One CTA per sketch row: keys (|C| << 32 | bucket) bitonic-sorted in shared memory.
 __global__ void __launch_bounds__(1024) k_presort(const int32_t* __restrict__ C, int64_t n_rows, int32_t w,

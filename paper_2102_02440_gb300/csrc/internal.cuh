@@ -251,5 +251,8 @@ cudaError_t launch_zero_spans(const ZeroSpan* spans_dev, int32_t n, cudaStream_t
 
 int sm_count();
 size_t smem_optin_bytes();
+// host checks and device descriptor of one cmp_table (api_build.cu)
+cmp_status check_table(const cmp_table* t, int32_t d, int32_t w, int32_t n_edges);
+DevTable to_dev(const cmp_table* t, int32_t* counters, int64_t* survivors);
 
 }  // namespace cmpk

@@ -249,6 +249,71 @@ class Enumerator:
                 for g in range(len(self.graphs))]
 
 
+class PartitionedJoin:
+    """Partitioned sketches (Sec. 4.1) of one tree-shaped join of a workload on the device:
+    each listed table gets one tensor over its edges of the join (cmp_part_build, hashed with
+    the workload's per-edge parameters), and estimate() contracts them (cmp_part_estimate).
+    tables: workload table indices, the first is the contraction's root; edges: workload edge
+    ids forming a spanning tree of those tables; widths: buckets per listed edge.  A table's
+    axes follow the order of its sketches in the workload.  cols_dev: optional uploaded
+    columns per listed table (e.g. a DeviceWorkload's)."""
+
+    def __init__(self, wl, tables, edges, widths, device="cuda", cols_dev=None, cfg=None, hash_dev=None):
+        from . import datagen as G
+        self.wl = wl
+        self.device = torch.device(device)
+        self.d = wl.d
+        self.cfg = cfg
+        self.table_ids = list(tables)
+        self.edge_ids = list(edges)
+        self.widths = [int(x) for x in widths]
+        if hash_dev is None:
+            hp = K.hash_params_u64(wl.hash_seed, wl.n_edges, self.d)
+            hash_dev = torch.from_numpy(np.ascontiguousarray(hp).reshape(-1).view(np.int64)).to(self.device)
+        self.hash_dev = hash_dev
+        pos = {t: i for i, t in enumerate(self.table_ids)}
+        local = {e: i for i, e in enumerate(self.edge_ids)}
+        eu = [pos[wl.edge_u[e]] for e in self.edge_ids]
+        ev = [pos[wl.edge_v[e]] for e in self.edge_ids]
+        self.tables, self.tensors, self.axes = [], [], []
+        for i, t in enumerate(self.table_ids):
+            src = wl.tables[t]
+            sel = [s for s, e in enumerate(src.edge_id) if e in local]
+            tt = G.Table(src.name, src.cols, src.preds, [src.key_col[s] for s in sel], [src.edge_id[s] for s in sel])
+            self.tables.append(DeviceTable(tt, self.d, 1, self.device, cols_dev=cols_dev[i] if cols_dev else None))
+            ax = [local[src.edge_id[s]] for s in sel]
+            self.axes.append(ax)
+            size = int(np.prod([self.widths[a] for a in ax])) if ax else 1
+            self.tensors.append(torch.zeros((self.d, size), dtype=torch.int32, device=self.device))
+        self.survivors = torch.zeros(len(self.tables), dtype=torch.int64, device=self.device)
+        self.join, self._keep = K.part_join(eu, ev, self.widths, self.axes, [x.data_ptr() for x in self.tensors])
+        nb = K.cmp_part_estimate_ws_bytes(self.join, self.d)
+        self.ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=self.device)
+        self.est = torch.empty(1, dtype=torch.float64, device=self.device)
+        self.row_est = torch.empty((self.d, 2), dtype=torch.int64, device=self.device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def table_widths(self, i: int) -> list:
+        return [self.widths[a] for a in self.axes[i]]
+
+    def build(self, stream=None):
+        s = K.stream_handle(stream)
+        for i, t in enumerate(self.tables):
+            K.cmp_part_build(t.desc, self.d, self.table_widths(i), self.hash_dev.data_ptr(), self.wl.n_edges,
+                             self.tensors[i].data_ptr(), self.survivors.data_ptr() + 8 * i, self.cfg, s)
+
+    def estimate(self, stream=None, row_est=True):
+        K.cmp_part_estimate(self.join, self.d, self.ws.data_ptr(), self.ws.numel(), self.est.data_ptr(),
+                            self.row_est.data_ptr() if row_est else 0, self.status.data_ptr(),
+                            K.stream_handle(stream))
+
+    def row_values(self):
+        r = self.row_est.cpu().numpy()
+        lo = r[:, 0].astype(np.uint64).astype(object)
+        hi = r[:, 1].astype(object)
+        return (hi * (1 << 64) + lo).tolist()
+
+
 class PairBatch:
     """N independent two-table joins R_i |x| S_i on a key: every sketch built in one
     batched launch, all N two-way estimates in one plan (one graph per pair), and the

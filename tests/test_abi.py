@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(K):
 def test_status_strings(K):
     assert K.status_str(0) == "ok"
     assert "invalid" in K.status_str(-1)
-    assert K.lib().cmp_abi_version() == K.CMP_ABI_VERSION == 2
+    assert K.lib().cmp_abi_version() == K.CMP_ABI_VERSION == 3
 
 
 def test_hash_params_match_oracle_generator(K, orc):
@@ -243,3 +243,68 @@ def test_presort_rejections(K):
     assert K.cmp_presort_ws_bytes(1000, 65536) == 2 * 64 * 65536 * 8
     assert K.cmp_presort_ws_bytes(1000, 4096) == 0
     assert K.lib().cmp_presort(None, 4, 64, 0x10, 0x10, None, 0, None) == K.CMP_EINVAL
+
+
+def test_partitioned_build_rejects_bad_arguments(K):
+    """Host checks of cmp_part_build (nothing is launched)."""
+    L = K.lib()
+
+    def call(t, widths, ne=5, counters=0x2000, cfg=None):
+        wa = (C.c_int32 * max(len(widths), 1))(*widths) if widths is not None else None
+        return L.cmp_part_build(C.byref(t), 4, wa, 0x3000, ne, counters, 0x4000, C.byref(cfg) if cfg else None, None)
+
+    two = _desc(K, ncols=2, key_col=(0, 1), edge_id=(0, 1))
+    assert call(_desc(K, key_col=(0,) * 5, edge_id=(0, 1, 2, 3, 4)), [2] * 5) == K.CMP_EINVAL   # > 4 axes
+    assert call(_desc(K, ncols=2, key_col=(0, 1), edge_id=(1, 1)), [4, 4]) == K.CMP_EINVAL      # repeated edge
+    assert call(two, [0, 4]) == K.CMP_EINVAL
+    assert call(two, [4, (1 << 20) + 1]) == K.CMP_EINVAL
+    assert call(two, [65536, 65536]) == K.CMP_EINVAL                                             # > 2^31 - 1
+    assert call(two, None) == K.CMP_EINVAL
+    assert call(two, [4, 4], counters=0) == K.CMP_EINVAL
+    assert call(two, [4, 4], ne=1) == K.CMP_EINVAL                                               # edge id >= n_edges
+    for cfg in (K.cmp_part_build_cfg.make(threads=48), K.cmp_part_build_cfg.make(tile_rows=100),
+                K.cmp_part_build_cfg.make(mode=3), K.cmp_part_build_cfg.make(rows_per_cta=-1)):
+        assert call(two, [4, 4], cfg=cfg) == K.CMP_EINVAL
+    # shared-memory mode with a tensor row larger than a CTA's shared memory
+    assert call(two, [1 << 10, 1 << 10], cfg=K.cmp_part_build_cfg.make(mode=1)) == K.CMP_EINVAL
+
+
+def test_partitioned_estimate_plan_host_logic(K):
+    """Workspace of the contraction order and the tree checks (host only)."""
+    j, keep = K.part_join([0, 1], [1, 2], [5, 7], [[0], [0, 1], [1]], [0x1000, 0x2000, 0x3000])
+    # flags (256 B), table 1 contracted on its last axis with table 2: [3][5] int128 (256 B),
+    # then the root with table 1's message: [3][1] (256 B)
+    assert K.cmp_part_estimate_ws_bytes(j, 3) == 768
+    j1, k1 = K.part_join([], [], [], [[]], [0x1000])
+    assert K.cmp_part_estimate_ws_bytes(j1, 11) == 256
+    # 4-axis centre as the root: four contractions, [d][w0 w1 w2] ... [d][1]
+    j4, k4 = K.part_join([0, 0, 0, 0], [1, 2, 3, 4], [2, 3, 4, 5], [[0, 1, 2, 3], [0], [1], [2], [3]],
+                         [0x1000 * (i + 1) for i in range(5)])
+    per = [2 * 3 * 4, 2 * 3, 2, 1]
+    assert K.cmp_part_estimate_ws_bytes(j4, 1) == 256 + sum(((16 * p + 255) // 256) * 256 for p in per)
+    bad = [
+        ([0, 1, 0], [1, 2, 2], [2, 2, 2], [[0, 2], [0, 1], [1, 2]]),    # a cycle (3 edges, 3 tables)
+        ([0, 1], [1, 0], [2, 2], [[0, 1], [0, 1], []]),                 # not connected
+        ([0, 1], [1, 2], [2, 2], [[0], [0, 0], [1]]),                   # repeated axis
+        ([0, 1], [1, 2], [2, 2], [[1], [0, 1], [0]]),                   # axis not incident
+        ([0, 1], [1, 2], [2, 2], [[0], [0], [1]]),                      # missing axis
+        ([0, 1], [1, 2], [0, 2], [[0], [0, 1], [1]]),                   # width 0
+        ([0, 1], [1, 1], [2, 2], [[0], [0, 1], [1]]),                   # self-loop
+    ]
+    for eu, ev, w, ax in bad:
+        jb, kb = K.part_join(eu, ev, w, ax, [0x1000, 0x2000, 0x3000])
+        with pytest.raises(K.CompassError):
+            K.cmp_part_estimate_ws_bytes(jb, 3)
+    jn, kn = K.part_join([0, 1], [1, 2], [5, 7], [[0], [0, 1], [1]], [0x1000, 0, 0x3000])
+    with pytest.raises(K.CompassError):
+        K.cmp_part_estimate_ws_bytes(jn, 3)
+    for d in (0, 65):
+        with pytest.raises(K.CompassError):
+            K.cmp_part_estimate_ws_bytes(j, d)
+    j5, k5 = K.part_join([0] * 5, [1, 2, 3, 4, 5], [2] * 5, [[0, 1, 2, 3, 4], [0], [1], [2], [3], [4]],
+                         [0x1000] * 6)
+    with pytest.raises(K.CompassError):
+        K.cmp_part_estimate_ws_bytes(j5, 3)                              # > 4 axes
+    # workspace too small / misaligned: rejected before any launch
+    assert K.lib().cmp_part_estimate(C.byref(j), 3, 0x10000, 512, 0x2000, None, None, None) == K.CMP_EWORKSPACE
+    assert K.lib().cmp_part_estimate(C.byref(j), 3, 0x10010, 768, 0x2000, None, None, None) == K.CMP_EINVAL
