@@ -57,7 +57,7 @@ def _args():
                     help="JSON file of autotuned launch shapes: read if it has this workload's, else written")
     ap.add_argument("--case", default=None,
                     choices=["estimate_small", "estimate_full", "build_f1", "build_five", "batched", "scale",
-                             "partition"],
+                             "partition", "offline_sample"],
                     help="run one small profiling case instead of the benchmark (for ncu captures)")
     return ap.parse_args()
 
@@ -896,6 +896,114 @@ def run_partition(a):
                       "partitioned": configs}), flush=True)
 
 
+def two_way_sizes(wl):
+    """Exact size of every single-edge join of the workload (its two-table sub-plans), from
+    the columns on the host: per edge, the dot product of the two endpoints' selected key
+    histograms."""
+    def keep(t):
+        tb = wl.tables[t]
+        m = np.ones(tb.n_rows, bool)
+        for q in tb.preds:
+            v = tb.cols[q.col].astype(np.int64)
+            if q.op == 0:
+                m &= (q.lo <= v) & (v < q.hi)
+            elif q.op == 1:
+                m &= v == q.lo
+            else:
+                inb = (v >= 0) & (v < q.nbits)
+                bits = np.zeros(tb.n_rows, bool)
+                vv = v[inb]
+                bits[inb] = ((q.bitmap[vv >> 5] >> (vv & 31).astype(np.uint32)) & 1) == 1
+                m &= bits
+        return m
+    masks = [keep(t) for t in range(len(wl.tables))]
+    out = {}
+    for e in range(wl.n_edges):
+        cols = []
+        for end in range(2):
+            t, s = wl.sketch_of(e, end)
+            cols.append(wl.tables[t].cols[wl.tables[t].key_col[s]][masks[t]].astype(np.int64))
+        n = int(max(c.max() if c.size else 0 for c in cols)) + 1
+        out[(1 << wl.edge_u[e]) | (1 << wl.edge_v[e])] = int(
+            (np.bincount(cols[0], minlength=n).astype(np.int64) * np.bincount(cols[1], minlength=n)).sum())
+    return out
+
+
+def run_offline_sample(a):
+    """Two build options of Sec. 2 "Workflow" on the five-table workload (full scale, d = 11,
+    w = 4096), each timed as build + presort + estimate of all 19 sub-plans (median of 5
+    after a warm-up, CUDA events):
+      offline: F1 and F2 have no predicates, so their sketches, presort and cross ranks are
+        built once (untimed) and plugged into every query; the per-query work is D1, D2 and
+        D3 only.  The estimates must equal the all-online ones bit for bit.
+      sample: every table's sketches over a Bernoulli row sample at rate p (1, 0.1, 0.01),
+        estimates scaled by 1 / p per table; q-errors of the five two-table sub-plans against
+        their exact sizes."""
+    import torch
+
+    from paper_2102_02440_gb300 import datagen as G
+    from paper_2102_02440_gb300 import pipeline as P
+    wl = G.five_table(scale=a.scale, w=4096)
+    masks = G.connected_subplans(5, wl.edge_u, wl.edge_v)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        return statistics.median(ts)
+
+    def query(dw, est):
+        def run():
+            dw.build_batched()
+            est.presort()
+            est.estimate()
+        return run
+
+    dw = P.DeviceWorkload(wl)
+    est = P.DeviceEstimator(dw, masks)
+    ms_online = timed(query(dw, est))
+    ref = est.est.clone()
+    cols = [t.cols for t in dw.tables]
+    dwo = P.DeviceWorkload(wl, cols_dev=cols, offline=[0, 1])
+    dwo.build_offline()
+    esto = P.DeviceEstimator(dwo, masks)
+    ms_offline = timed(query(dwo, esto))
+    same = bool(torch.equal(esto.est, ref)) or bool(torch.equal(torch.nan_to_num(esto.est), torch.nan_to_num(ref)))
+    del dwo, esto
+    exact = two_way_sizes(wl)
+    pair_q = {m: q for q, m in enumerate(masks) if int(m) in exact}
+
+    def qerr(x, t):
+        x, t = max(float(x), 1.0), max(float(t), 1.0)
+        return max(x / t, t / x)
+
+    sample = {}
+    for rate in (1.0, 0.1, 0.01):
+        dws = P.DeviceWorkload(wl, cols_dev=cols, sample_rates=[rate] * 5)
+        ests = P.DeviceEstimator(dws, masks)
+        ms = timed(query(dws, ests))
+        dws.check_status()
+        ev = ests.est.cpu().numpy()
+        qs = [qerr(ev[q], exact[int(m)]) for m, q in pair_q.items()]
+        sample[f"rate_{rate}"] = {"ms": ms, "survivors": [int(x) for x in dws.survivors.cpu().numpy()],
+                                  "two_way_q_error": {"median": float(np.median(qs)), "max": float(max(qs))},
+                                  "two_way": {bin(int(m)): [float(ev[q]), exact[int(m)]] for m, q in pair_q.items()}}
+        del dws, ests
+        torch.cuda.empty_cache()
+    print(json.dumps({"case": "offline_sample", "workload": wl.name, "subplans": len(masks),
+                      "online_ms": ms_online,
+                      "offline": {"tables": ["F1", "F2"], "per_query_ms": ms_offline,
+                                  "speedup": ms_online / ms_offline, "estimates_identical": same},
+                      "sample": sample}), flush=True)
+
+
 def main():
     a = _args()
     if a.case == "batched":
@@ -904,6 +1012,8 @@ def main():
         run_scale(a)
     elif a.case == "partition":
         run_partition(a)
+    elif a.case == "offline_sample":
+        run_offline_sample(a)
     elif a.case:
         run_case(a)
     elif a.impl == "reference":

@@ -93,7 +93,19 @@ typedef struct {
   const cmp_pred* preds;    /* [n_preds]                                           */
   const int32_t* key_col;   /* [n_sketches] column index holding the join key      */
   const int32_t* edge_id;   /* [n_sketches] join-graph edge of the sketch          */
+  uint64_t sample_seed;     /* row sample, see below                               */
+  double sample_rate;       /* 0 or 1: every row; in (0, 1): a Bernoulli sample    */
 } cmp_table;
+
+/* Row sample (Sec. 2 "Workflow": sketches may be built over a sample only, trading
+ * accuracy for time).  With sample_rate p in (0, 1), row r (0-based, of the whole table)
+ * takes part in the selection only if output r of SplitMix64 (Steele, Lea & Flood 2014)
+ * seeded with sample_seed, z = sample_seed + (r + 1) * 0x9E3779B97F4A7C15 mixed by the
+ * generator's finaliser, is below floor(p * 2^64) (at least 1): one independent trial per
+ * row, computed from r alone, so every launch shape and both builds sample the same rows.
+ * The survivor count is then the number of sampled rows that satisfy the predicates.
+ * Sample tables with different seeds; the estimates scale back with cmp_graph.sample_rate
+ * and cmp_part_join.sample_rate. */
 
 /* Build launch shape.  Zero / negative fields mean "choose automatically" (the
  * autotuned table when one is loaded, else a size heuristic). */
@@ -113,7 +125,7 @@ typedef struct {
 /* ---------------------------------------------------------------------- general */
 
 /* Version of this interface (CMP_ABI_VERSION); bindings refuse a library that differs. */
-#define CMP_ABI_VERSION 3
+#define CMP_ABI_VERSION 4
 int32_t cmp_abi_version(void);
 const char* cmp_status_str(cmp_status s);
 
@@ -226,6 +238,8 @@ typedef struct {
                                         table's k sketches */
   const int32_t* slot;               /* [2 * n_edges]: the endpoint's sketch index x within its table (host) */
   const int64_t* survivors_dev;      /* device [n_tables]: exact selected counts */
+  const double* sample_rate;         /* NULL, or [n_tables] the rate each table's sketches were built at
+                                        (cmp_table.sample_rate: 0 or 1 = unsampled, else in (0, 1)) */
 } cmp_graph;
 
 /* Estimates of many sub-plans, possibly of many graphs, in one launch sequence
@@ -245,6 +259,11 @@ typedef struct {
  *     E_0..E_{d-1} (Sec. 3.2), exact, rounded once to double (even d: mean of the two
  *     middle values).  Sub-plans whose edges contain more than one independent cycle
  *     return CMP_EUNSUPPORTED from the plan step.
+ *   Sampled tables (sample_rate): the estimate (the median, or the selected count of a
+ *     single table) is multiplied by the sub-plan's scale, the product over its tables in
+ *     ascending order of 1 / rate (double, left to right), which makes the two-way
+ *     estimate unbiased over the independent samples; row_est stays the exact integers of
+ *     the sampled sketches.
  * Host steps: cmp_estimate_plan_bytes sizes the plan and the device workspace, and
  * cmp_estimate_plan_encode writes the plan; the caller copies it to the device.  Then
  * cmp_estimate enqueues the launches.
@@ -323,6 +342,7 @@ typedef struct {
   const int32_t* n_axes;          /* [n_tables]                                            */
   const int32_t* axis_edge;       /* table 0's axes, then table 1's, ... (sum n_axes)      */
   const int32_t* const* tensor;   /* [n_tables] device [d][prod of the table's widths]     */
+  const double* sample_rate;      /* NULL, or [n_tables] build sample rates (as cmp_graph)  */
 } cmp_part_join;
 
 /* Estimate of the join (Sec. 4.1): per sketch row i the exact integer
@@ -336,7 +356,9 @@ typedef struct {
  * time, last axis first, each contraction multiplying every entry by the child's message
  * entry at its index on that axis and summing over the axis; a leaf's message is its own
  * tensor.  Values are int128 and sums are exact; a row where a single product or a value
- * after a contraction leaves int128 has est NaN and CMP_EOVERFLOW in the status.
+ * after a contraction leaves int128 has est NaN and CMP_EOVERFLOW in the status.  With
+ * sample rates, est is multiplied by the product over the tables, ascending, of 1 / rate
+ * (the contraction is linear in every tensor, so this keeps it unbiased).
  *   ws_dev       *ws_bytes from cmp_part_estimate_ws_bytes (intermediate messages), caller-owned
  *   est_dev      one double
  *   row_est_dev  NULL or [d][2] int64: each row value as a little-endian two's-complement

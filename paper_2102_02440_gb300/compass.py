@@ -16,7 +16,7 @@ CMP_OK, CMP_EINVAL, CMP_EUNSUPPORTED, CMP_EOVERFLOW, CMP_ECUDA, CMP_EWORKSPACE, 
 CMP_I32, CMP_I64 = 0, 1
 CMP_RANGE, CMP_EQ, CMP_IN_BITMAP = 0, 1, 2
 CMP_EST_GENERIC_ONLY = 1
-CMP_ABI_VERSION = 3
+CMP_ABI_VERSION = 4
 CMP_PART_MAX_AXES = 4
 CMP_MAX_COLS, CMP_MAX_PREDS, CMP_MAX_SKETCHES, CMP_MAX_D = 32, 8, 16, 64
 
@@ -43,7 +43,8 @@ class cmp_hash(C.Structure):
 class cmp_table(C.Structure):
     _fields_ = [("n_rows", C.c_int64), ("n_cols", C.c_int32), ("n_preds", C.c_int32), ("n_sketches", C.c_int32),
                 ("reserved", C.c_int32), ("cols", C.POINTER(cmp_col)), ("preds", C.POINTER(cmp_pred)),
-                ("key_col", C.POINTER(C.c_int32)), ("edge_id", C.POINTER(C.c_int32))]
+                ("key_col", C.POINTER(C.c_int32)), ("edge_id", C.POINTER(C.c_int32)),
+                ("sample_seed", C.c_uint64), ("sample_rate", C.c_double)]
 
 
 class cmp_build_cfg(C.Structure):
@@ -69,7 +70,8 @@ class cmp_graph(C.Structure):
     _fields_ = [("n_tables", C.c_int32), ("n_edges", C.c_int32), ("edge_u", C.POINTER(C.c_int32)),
                 ("edge_v", C.POINTER(C.c_int32)), ("sketch", C.POINTER(C.c_void_p)),
                 ("abs_sorted", C.POINTER(C.c_void_p)), ("perm", C.POINTER(C.c_void_p)),
-                ("ranks", C.POINTER(C.c_void_p)), ("slot", C.POINTER(C.c_int32)), ("survivors_dev", C.c_void_p)]
+                ("ranks", C.POINTER(C.c_void_p)), ("slot", C.POINTER(C.c_int32)), ("survivors_dev", C.c_void_p),
+                ("sample_rate", C.POINTER(C.c_double))]
 
 
 class cmp_enum_cfg(C.Structure):
@@ -92,7 +94,8 @@ class cmp_part_build_cfg(C.Structure):
 class cmp_part_join(C.Structure):
     _fields_ = [("n_tables", C.c_int32), ("n_edges", C.c_int32), ("edge_u", C.POINTER(C.c_int32)),
                 ("edge_v", C.POINTER(C.c_int32)), ("width", C.POINTER(C.c_int32)), ("n_axes", C.POINTER(C.c_int32)),
-                ("axis_edge", C.POINTER(C.c_int32)), ("tensor", C.POINTER(C.c_void_p))]
+                ("axis_edge", C.POINTER(C.c_int32)), ("tensor", C.POINTER(C.c_void_p)),
+                ("sample_rate", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -341,14 +344,15 @@ def cmp_part_build(table: cmp_table, d: int, widths, hash_dev: int, n_edges: int
                                                   C.byref(cfg) if cfg is not None else None, stream))
 
 
-def part_join(edge_u, edge_v, width, axes, tensor_ptrs):
+def part_join(edge_u, edge_v, width, axes, tensor_ptrs, sample_rate=None):
     """A cmp_part_join and the ctypes arrays it points into (keep both alive)."""
     ne, nt = len(edge_u), len(axes)
     keep = [(C.c_int32 * max(ne, 1))(*edge_u), (C.c_int32 * max(ne, 1))(*edge_v), (C.c_int32 * max(ne, 1))(*width),
             (C.c_int32 * max(nt, 1))(*[len(a) for a in axes]),
             (C.c_int32 * max(sum(len(a) for a in axes), 1))(*[e for a in axes for e in a]),
             (C.c_void_p * max(nt, 1))(*tensor_ptrs)]
-    return cmp_part_join(nt, ne, *keep), keep
+    rates = (C.c_double * max(nt, 1))(*sample_rate) if sample_rate is not None else None
+    return cmp_part_join(nt, ne, *keep, rates), keep + [rates]
 
 
 def cmp_part_estimate_ws_bytes(join: cmp_part_join, d: int) -> int:

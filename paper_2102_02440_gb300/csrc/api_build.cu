@@ -55,6 +55,7 @@ cmp_status check_table(const cmp_table* t, int32_t d, int32_t w, int32_t n_edges
     if (t->key_col[s] < 0 || t->key_col[s] >= t->n_cols) return CMP_EINVAL;
     if (t->edge_id[s] < 0 || t->edge_id[s] >= n_edges) return CMP_EINVAL;
   }
+  if (!(t->sample_rate >= 0.0 && t->sample_rate <= 1.0)) return CMP_EINVAL;  // NaN fails too
   return CMP_OK;
 }
 
@@ -84,6 +85,9 @@ DevTable to_dev(const cmp_table* t, int32_t* counters, int64_t* survivors) {
     D.key_col[s] = t->key_col[s];
     D.edge_id[s] = t->edge_id[s];
   }
+  D.sample_seed = t->sample_seed;
+  D.sample_keep = sample_keep_of(t->sample_rate);
+  D.filtered = (t->n_preds > 0 || D.sample_keep != 0) ? 1 : 0;
   D.counters = counters;
   D.survivors = survivors;
   for (int c = 0; c < CMP_MAX_COLS; c++) D.agg[c] = -1;

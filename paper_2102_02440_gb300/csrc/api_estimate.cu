@@ -41,6 +41,9 @@ bool graph_ok(const cmp_graph& g) {
   if (g.n_edges && (!g.edge_u || !g.edge_v || !g.sketch || !g.abs_sorted || !g.perm || !g.ranks || !g.slot))
     return false;
   if (!g.survivors_dev) return false;
+  if (g.sample_rate)
+    for (int t = 0; t < g.n_tables; t++)
+      if (!(g.sample_rate[t] >= 0.0 && g.sample_rate[t] <= 1.0)) return false;  // NaN fails too
   for (int e = 0; e < g.n_edges; e++) {
     if (g.edge_u[e] < 0 || g.edge_u[e] >= g.n_tables || g.edge_v[e] < 0 || g.edge_v[e] >= g.n_tables) return false;
     if (g.edge_u[e] == g.edge_v[e]) return false;
@@ -173,6 +176,12 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
   if (int(order.size()) != __builtin_popcountll(mask)) return CMP_EINVAL;  // not connected
   EstSub sb;
   std::memset(&sb, 0, sizeof(sb));
+  sb.scale = 1.0;  // sampled tables: prod over the sub-plan's tables, ascending, of 1 / rate
+  if (g.sample_rate)
+    for (int t = 0; t < nt; t++) {
+      const double r = g.sample_rate[t];
+      if (((mask >> t) & 1) && r > 0.0 && r < 1.0) sb.scale = sb.scale * (1.0 / r);
+    }
   sb.op_begin = int32_t(P->ops.size());
   sb.item_begin = int64_t(P->items.size());
   sb.tri = -1;

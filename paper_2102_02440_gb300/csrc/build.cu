@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
   const int npairs = pair_end - pair_begin;
   const int w = A.w;
   const int64_t n_rows = tb->n_rows;
-  const int n_preds = tb->n_preds;
+  const int filtered = tb->filtered;
   const bool vec = tb->vec_ok != 0;
   const int R = A.tile_rows;
   const int M = A.map_slots;
@@ -159,9 +159,9 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
         m0 = mcnt[e0];
         if (e1 < n_entries) x1 = mkey[e1], m1 = mcnt[e1];
       } else {
-        x0 = key_field(load1(kbase, kdt, r0 + (n_preds ? surv[e0] : e0)));
+        x0 = key_field(load1(kbase, kdt, r0 + (filtered ? surv[e0] : e0)));
         m0 = 1;
-        if (e1 < n_entries) x1 = key_field(load1(kbase, kdt, r0 + (n_preds ? surv[e1] : e1))), m1 = 1;
+        if (e1 < n_entries) x1 = key_field(load1(kbase, kdt, r0 + (filtered ? surv[e1] : e1))), m1 = 1;
       }
       const KeyPow k0 = key_powers(x0);
       const KeyPow k1 = key_powers(x1);
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
             const int e = base + tid;
             const bool valid = e < n_surv;
             unsigned long long x = kEmptyKey;
-            if (valid) x = key_field(load1(kbase, kdt, r0 + (n_preds ? surv[e] : e)));
+            if (valid) x = key_field(load1(kbase, kdt, r0 + (filtered ? surv[e] : e)));
             // equal keys of the warp are inserted once, by their lowest lane, with their count
             const unsigned peers = __match_any_sync(0xffffffffu, x);
             if (!valid || lane != __ffs(peers) - 1) continue;
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(1024) k_agg_count(const __grid_constant__ Buil
   constexpr unsigned long long kEmpty = ~0ull;  // key part 0xFFFFFFFF is never an index: cap <= 2^31 - 1
   const int64_t n_rows = tb->n_rows;
   const int64_t n_tiles = (n_rows + R - 1) / R;
-  const int n_preds = tb->n_preds;
+  const int filtered = tb->filtered;
   const bool vec = tb->vec_ok != 0;
   const int cta = int(blockIdx.x) - it.first_cta;
   const uint32_t mmask = uint32_t(M - 1);
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(1024) k_agg_count(const __grid_constant__ Buil
         const int e = base + tid;
         const bool valid = e < n_surv;
         uint32_t x = 0xFFFFFFFFu;
-        if (valid) x = uint32_t(load1(kbase, kdt, r0 + (n_preds ? surv[e] : e)) - kmin);  // < range <= cap
+        if (valid) x = uint32_t(load1(kbase, kdt, r0 + (filtered ? surv[e] : e)) - kmin);  // < range <= cap
         const unsigned peers = __match_any_sync(0xffffffffu, x);
         if (!valid || lane != __ffs(peers) - 1) continue;
         const unsigned long long cnt = (unsigned long long)__popc(peers);

@@ -758,7 +758,8 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_estimate_finalize(const __
     }
     rows[b + 1] = v;
   }
-  est[q] = (d & 1) ? i128_to_double(rows[d / 2]) : mean2_to_double(rows[d / 2 - 1], rows[d / 2]);
+  const double med = (d & 1) ? i128_to_double(rows[d / 2]) : mean2_to_double(rows[d / 2 - 1], rows[d / 2]);
+  est[q] = __dmul_rn(med, sb.scale);  // sampled tables: one rounded product (scale 1 is exact)
 }
 
 cudaError_t launch_estimate(const EstArgs& a, double* est, int64_t* row_est, cudaStream_t st) {

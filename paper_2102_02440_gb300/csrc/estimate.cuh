@@ -43,6 +43,7 @@ struct EstSub {
   const int64_t* sv;  // single: that table's survivor count (device)
   int32_t cond;       // 1 if a non-tree edge is conditioned
   int32_t tri;        // index of its TriSub (triangle evaluation), else -1
+  double scale;       // sampled tables: prod of 1 / rate over the sub-plan's tables, else 1
 };
 
 struct EstItem {
@@ -104,7 +105,7 @@ struct EstPlanHdr {
   int32_t tri_max_leaves, tri_nch;  // leaves per node (scratch layout), sweep items per row
 };
 constexpr uint64_t kEstPlanMagic = 0x434d504553544d54ull;  // "CMPESTMT"
-constexpr int32_t kEstPlanVersion = 2;
+constexpr int32_t kEstPlanVersion = 3;
 
 struct EstArgs {
   const EstSub* subs;

@@ -112,6 +112,22 @@ __device__ __forceinline__ int cw_sign(const PairParam& q, const KeyPow& k) {
   return 1 - 2 * int(r & 1);
 }
 
+// Output r (0-based) of SplitMix64 (Steele, Lea & Flood 2014) seeded with `seed`: the
+// generator's state after r + 1 steps, through its finaliser.
+__host__ __device__ inline uint64_t splitmix64_at(uint64_t seed, uint64_t r) {
+  uint64_t z = seed + (r + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Sample threshold of a rate: 0 (no sample) for 0 or 1, else floor(rate * 2^64), at least 1.
+inline uint64_t sample_keep_of(double rate) {
+  if (!(rate > 0.0 && rate < 1.0)) return 0;
+  const uint64_t k = uint64_t(rate * 18446744073709551616.0);
+  return k ? k : 1;
+}
+
 // ------------------------------------------------------------ build structures
 struct DevPred {
   int32_t col, op;
@@ -124,6 +140,8 @@ struct DevTable {
   int64_t n_rows;
   int32_t n_cols, n_preds, n_sketches;
   int32_t vec_ok;  // every column 16-byte aligned: 128-bit loads allowed
+  int32_t filtered, pad0;  // predicates or a row sample: tiles go through the survivor compaction
+  uint64_t sample_seed, sample_keep;  // row r is sampled iff splitmix64_at(seed, r) < keep (keep 0: no sample)
   const void* col[CMP_MAX_COLS];
   int32_t dtype[CMP_MAX_COLS];
   DevPred pred[CMP_MAX_PREDS];
@@ -228,7 +246,7 @@ struct BuildPlanHdr {
   int32_t cnt_grid, stat_grid;
   int64_t ws_bytes;
 };
-constexpr int32_t kBuildPlanVersion = 2;
+constexpr int32_t kBuildPlanVersion = 3;
 struct ZeroSpan {
   void* ptr;
   int64_t bytes;

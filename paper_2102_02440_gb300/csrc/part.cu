@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(1024) k_part_build(const __grid_constant__ Par
   const int64_t n_rows = tb.n_rows;
   const int64_t n_tiles = (n_rows + R - 1) / R;
   const bool vec = tb.vec_ok != 0;
-  const bool has_preds = tb.n_preds > 0;
+  const bool filtered = tb.filtered != 0;
   int g0, g1, c, C;
   if (SMEM) {
     g0 = blockIdx.x / A.ctas_per_group;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(1024) k_part_build(const __grid_constant__ Par
         if (tid < r_n && n_surv) atomicAdd(out + int64_t(tid) * A.size, n_surv);
       } else {
         for (int s = tid; s < n_surv; s += T) {
-          const int64_t row = r0 + (has_preds ? int64_t(surv[s]) : int64_t(s));
+          const int64_t row = r0 + (filtered ? int64_t(surv[s]) : int64_t(s));
           KeyPow kp[axes_or_1<K>()];
           bool small = true;
 #pragma unroll
@@ -367,8 +367,8 @@ cudaError_t launch_step(const PartStep& S, bool x_wide, bool v_wide, int sms, cu
 
 __global__ void __launch_bounds__(64) k_part_finalize(const void* root, int32_t root_wide, int64_t root_rs,
                                                       const uint32_t* __restrict__ oor, int32_t d,
-                                                      double* __restrict__ est, int64_t* __restrict__ row_est,
-                                                      int32_t* status) {
+                                                      double scale, double* __restrict__ est,
+                                                      int64_t* __restrict__ row_est, int32_t* status) {
   __shared__ i128 rows[CMP_MAX_D];
   __shared__ int32_t any_oor;
   const int i = threadIdx.x;
@@ -400,7 +400,8 @@ __global__ void __launch_bounds__(64) k_part_finalize(const void* root, int32_t 
     }
     rows[b + 1] = v;
   }
-  *est = (d & 1) ? i128_to_double(rows[d / 2]) : mean2_to_double(rows[d / 2 - 1], rows[d / 2]);
+  const double med = (d & 1) ? i128_to_double(rows[d / 2]) : mean2_to_double(rows[d / 2 - 1], rows[d / 2]);
+  *est = __dmul_rn(med, scale);  // sampled tables: one rounded product (scale 1 is exact)
 }
 
 // ------------------------------------------------------------ host plan
@@ -429,6 +430,9 @@ cmp_status check_join(const cmp_part_join* j, int32_t d, std::vector<int32_t>* a
   if (!j || d < 1 || d > CMP_MAX_D) return CMP_EINVAL;
   const int nt = j->n_tables, ne = j->n_edges;
   if (nt < 1 || nt > CMP_MAX_TABLES || ne != nt - 1 || !j->n_axes || !j->tensor) return CMP_EINVAL;
+  if (j->sample_rate)
+    for (int t = 0; t < nt; t++)
+      if (!(j->sample_rate[t] >= 0.0 && j->sample_rate[t] <= 1.0)) return CMP_EINVAL;  // NaN fails too
   if (ne > 0 && (!j->edge_u || !j->edge_v || !j->width || !j->axis_edge)) return CMP_EINVAL;
   for (int e = 0; e < ne; e++) {
     const int u = j->edge_u[e], v = j->edge_v[e];
@@ -655,8 +659,14 @@ cmp_status cmp_part_estimate(const cmp_part_join* join, int32_t d, void* ws_dev,
             (reinterpret_cast<uintptr_t>(S.x) & 15) == 0 && (reinterpret_cast<uintptr_t>(S.v) & 15) == 0;
     if (launch_step(S, xw, vw, sms, cs) != cudaSuccess) return CMP_ECUDA;
   }
-  k_part_finalize<<<1, 64, 0, cs>>>(ptr(P.root), P.root.table < 0 ? 1 : 0, P.root.rs, oor, d, est_dev, row_est_dev,
-                                     status_dev);
+  double scale = 1.0;  // sampled tables: prod over the tables, ascending, of 1 / rate
+  if (join->sample_rate)
+    for (int t = 0; t < join->n_tables; t++) {
+      const double r = join->sample_rate[t];
+      if (r > 0.0 && r < 1.0) scale = scale * (1.0 / r);
+    }
+  k_part_finalize<<<1, 64, 0, cs>>>(ptr(P.root), P.root.table < 0 ? 1 : 0, P.root.rs, oor, d, scale, est_dev,
+                                     row_est_dev, status_dev);
   return cudaGetLastError() == cudaSuccess ? CMP_OK : CMP_ECUDA;
 }
 

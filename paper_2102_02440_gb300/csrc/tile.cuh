@@ -44,13 +44,15 @@ __device__ __forceinline__ bool pred_holds(const DevPred& q, int64_t v) {
   return (__ldg(q.bitmap + (v >> 5)) >> (v & 31)) & 1u;
 }
 
-// Phase A of one tile: the predicate conjunction over rows [r0, r0 + rows_in_tile), the
-// survivors' offsets compacted into surv[] (warp scan, one shared atomic per warp).
+// Phase A of one tile: the row sample and the predicate conjunction over rows [r0, r0 +
+// rows_in_tile), the survivors' offsets compacted into surv[] (warp scan, one shared atomic
+// per warp).  An unfiltered table returns rows_in_tile without writing surv[].
 // Returns the survivor count.  Block-wide: every thread calls it; sint[0] is the tail.
 __device__ int tile_survivors(const DevTable* tb, int64_t r0, int rows_in_tile, int R, bool vec, uint16_t* surv,
                               int32_t* sint) {
   const int n_preds = tb->n_preds;
-  if (n_preds == 0) return rows_in_tile;
+  if (!tb->filtered) return rows_in_tile;
+  const uint64_t keep = tb->sample_keep, seed = tb->sample_seed;
   const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
   if (tid == 0) sint[0] = 0;
   __syncthreads();
@@ -59,6 +61,11 @@ __device__ int tile_survivors(const DevTable* tb, int64_t r0, int rows_in_tile, 
     const int base = 4 * (tid + it * T);
     const int nvalid = max(0, min(4, rows_in_tile - base));
     uint32_t m = (1u << nvalid) - 1u;
+    if (keep) {  // row sample: one SplitMix64 trial per row of the table
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if (((m >> k) & 1u) && splitmix64_at(seed, uint64_t(r0 + base + k)) >= keep) m &= ~(1u << k);
+    }
     for (int q = 0; q < n_preds && m; q++) {
       const DevPred& pq = tb->pred[q];
       int64_t v[4];

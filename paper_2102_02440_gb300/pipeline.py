@@ -21,7 +21,8 @@ def _dev(a, device) -> torch.Tensor:
 class DeviceTable:
     """One table's device columns, bitmaps, outputs and its cmp_table descriptor."""
 
-    def __init__(self, t, d: int, w: int, device, upload: bool = True, cols_dev=None):
+    def __init__(self, t, d: int, w: int, device, upload: bool = True, cols_dev=None, sample_seed: int = 0,
+                 sample_rate: float = 0.0):
         self.name = t.name
         self.n_rows = t.n_rows
         self.k = len(t.key_col)
@@ -37,13 +38,24 @@ class DeviceTable:
         self._key = (C.c_int32 * max(self.k, 1))(*t.key_col)
         self._edge = (C.c_int32 * max(self.k, 1))(*t.edge_id)
         self.desc = K.cmp_table(self.n_rows, ncols, len(t.preds), self.k, 0, self._cols, self._preds, self._key,
-                                self._edge)
+                                self._edge, sample_seed, sample_rate)
+        self.sample_rate = sample_rate
         self.key_col = list(t.key_col)
         self.edge_id = list(t.edge_id)
 
 
 class DeviceWorkload:
-    def __init__(self, wl, device="cuda", hash_seed: int | None = None, cols_dev=None):
+    """A workload's tables on the device with their sketches.
+    sample_rates: optional per-table row-sample rates (0 or 1 = every row; Sec. 2
+      "Workflow"), table t sampled with seed sample_seed + t; the estimates scale back by
+      the rates.
+    offline: tables without predicates whose sketches are built once by build_offline()
+      and plugged into every query (Sec. 2 "Workflow"): build_batched() and presort() then
+      cover only the other tables.  Counters, presort and cross-rank buffers hold the
+      online tables first, so each of those steps stays one launch over a prefix."""
+
+    def __init__(self, wl, device="cuda", hash_seed: int | None = None, cols_dev=None, sample_rates=None,
+                 sample_seed: int = 0x5A3B1E, offline=None):
         self.wl = wl
         self.device = torch.device(device)
         self.d, self.w = wl.d, wl.w
@@ -53,20 +65,34 @@ class DeviceWorkload:
         hp = np.frombuffer(self.hash_host, dtype=np.uint64, count=max(self.n_edges * self.d, 1) * 6).copy()
         self.hash_u64 = hp[: self.n_edges * self.d * 6].reshape(self.n_edges, self.d, 6)
         self.hash_dev = torch.from_numpy(hp.view(np.int64)).to(self.device)
-        self.tables = [DeviceTable(t, self.d, self.w, self.device, cols_dev=cols_dev[i] if cols_dev else None)
+        self.sample_rates = [float(r) for r in sample_rates] if sample_rates is not None else None
+        self.tables = [DeviceTable(t, self.d, self.w, self.device, cols_dev=cols_dev[i] if cols_dev else None,
+                                   sample_seed=sample_seed + i,
+                                   sample_rate=self.sample_rates[i] if self.sample_rates else 0.0)
                        for i, t in enumerate(wl.tables)]
-        # every table's counters as consecutive blocks of one buffer (tables without sketches
-        # keep their own): presort and cross ranks then take one launch each for all tables
+        self.offline = sorted(set(int(t) for t in (offline or [])))
+        for t in self.offline:
+            if wl.tables[t].preds or (self.sample_rates and 0.0 < self.sample_rates[t] < 1.0):
+                raise ValueError(f"table {t}: offline sketches serve tables without predicates or samples")
+        n = len(self.tables)
+        self.online = [t for t in range(n) if t not in self.offline]
+        self.storage_order = self.online + self.offline
+        # every table's counters as consecutive blocks of one buffer, online tables first
+        # (tables without sketches keep their own): presort and cross ranks then take one
+        # launch each for all online (or offline) tables
         total = sum(t.k for t in self.tables)
         self.counters_all = torch.zeros((max(total, 1), self.d, self.w), dtype=torch.int32, device=self.device)
         off = 0
-        for t in self.tables:
+        for i in self.storage_order:
+            t = self.tables[i]
             if t.k:
                 t.counters = self.counters_all[off:off + t.k]
                 off += t.k
-        self.survivors = torch.zeros(len(self.tables), dtype=torch.int64, device=self.device)
+        self.survivors = torch.zeros(n, dtype=torch.int64, device=self.device)
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
         self._plan = None
+        self._plans = None
+        self._offline_plans = None
 
     # --------------------------------------------------------------- build
     def build(self, cfg=None, stream=None):
@@ -76,25 +102,59 @@ class DeviceWorkload:
                                t.counters.data_ptr(), self.survivors.data_ptr() + 8 * i, self.status.data_ptr(), cfg,
                                s)
 
+    @staticmethod
+    def _runs(ids):
+        """Maximal ranges [a, b) of consecutive table ids (one batched plan each: a plan's
+        survivors are one array)."""
+        runs = []
+        for t in ids:
+            if runs and runs[-1][1] == t:
+                runs[-1][1] = t + 1
+            else:
+                runs.append([t, t + 1])
+        return runs
+
+    def _encode_runs(self, ids, cfg):
+        plans = []
+        for a, b in self._runs(ids):
+            descs = [self.tables[t].desc for t in range(a, b)]
+            nb, wb = K.cmp_build_plan_bytes(descs, self.d, self.w, cfg)
+            host = np.zeros(nb, np.uint8)
+            K.cmp_build_plan_encode(descs, self.d, self.w, self.n_edges,
+                                    [self.tables[t].counters.data_ptr() for t in range(a, b)],
+                                    self.survivors.data_ptr() + 8 * a, cfg, host.ctypes.data, nb)
+            ws = getattr(self, "build_ws", None)
+            if wb and (ws is None or ws.numel() < wb):
+                self.build_ws = torch.empty(wb, dtype=torch.uint8, device=self.device)
+            plans.append((host, torch.from_numpy(host).to(self.device), wb))
+        return plans
+
+    def _run_plans(self, plans, stream):
+        for host, dev, wb in plans:
+            ws = self.build_ws.data_ptr() if wb else 0
+            K.cmp_sketch_build_batched(host.ctypes.data, dev.data_ptr(), self.hash_dev.data_ptr(), ws, wb,
+                                       self.status.data_ptr(), K.stream_handle(stream))
+
     def encode_batched(self, cfg=None):
-        descs = [t.desc for t in self.tables]
-        nb, wb = K.cmp_build_plan_bytes(descs, self.d, self.w, cfg)
-        host = np.zeros(nb, np.uint8)
-        K.cmp_build_plan_encode(descs, self.d, self.w, self.n_edges, [t.counters.data_ptr() for t in self.tables],
-                                self.survivors.data_ptr(), cfg, host.ctypes.data, nb)
-        ws = getattr(self, "build_ws", None)
-        if wb and (ws is None or ws.numel() < wb):
-            self.build_ws = torch.empty(wb, dtype=torch.uint8, device=self.device)
-        self._plan = (host, torch.from_numpy(host).to(self.device), wb)
-        return nb
+        """Batched build plans of the online tables (one per run of consecutive ids)."""
+        self._plans = self._encode_runs(self.online, cfg)
+        self._plan = self._plans[0] if len(self._plans) == 1 else None
+        return sum(p[0].size for p in self._plans)
 
     def build_batched(self, cfg=None, stream=None):
-        if self._plan is None:
+        if self._plans is None or (self._plan is None and len(self._plans) == 1):
             self.encode_batched(cfg)
-        host, dev, wb = self._plan
-        ws = self.build_ws.data_ptr() if wb else 0
-        K.cmp_sketch_build_batched(host.ctypes.data, dev.data_ptr(), self.hash_dev.data_ptr(), ws, wb,
-                                   self.status.data_ptr(), K.stream_handle(stream))
+        self._run_plans(self._plans, stream)
+
+    def build_offline(self, cfg=None, stream=None):
+        """Sketches, presort and cross ranks of the offline tables (once, outside any query)."""
+        if not self.offline:
+            return
+        if self._offline_plans is None:
+            self._offline_plans = self._encode_runs(self.offline, cfg)
+        self._run_plans(self._offline_plans, stream)
+        _prep_tables(self)
+        _presort_tables(self, K.stream_handle(stream), offline=True)
 
     def check_status(self):
         st = int(self.status.item())
@@ -108,47 +168,54 @@ class DeviceWorkload:
 
 def _prep_tables(dw):
     """Presort and cross-rank buffers for every table of a DeviceWorkload (once): one
-    buffer each for all tables, in the order of the counters, with per-table views."""
+    buffer each for all tables, in the storage order of the counters, with per-table views."""
     if getattr(dw, "ranks", None) is None:
         dev, d, w = dw.device, dw.d, dw.w
-        ks = [t.k for t in dw.tables]
+        order = getattr(dw, "storage_order", list(range(len(dw.tables))))
+        ks = [dw.tables[i].k for i in order]
         total, rtotal = sum(ks), sum(k * k for k in ks)
         dw.abs_all = torch.empty((max(total, 1), d, w), dtype=torch.int32, device=dev)
         dw.perm_all = torch.empty((max(total, 1), d, w), dtype=torch.int32, device=dev)
         dw.ranks_all = torch.empty((max(rtotal, 1), d, w), dtype=torch.int32, device=dev)
-        dw.abs_sorted, dw.perm, dw.ranks = [], [], []
+        n = len(dw.tables)
+        dw.abs_sorted, dw.perm, dw.ranks = [None] * n, [None] * n, [None] * n
         off = roff = 0
-        for k in ks:
+        for i, k in zip(order, ks):
             if k:
-                dw.abs_sorted.append(dw.abs_all[off:off + k])
-                dw.perm.append(dw.perm_all[off:off + k])
-                dw.ranks.append(dw.ranks_all[roff:roff + k * k].view(k, k, d, w))
+                dw.abs_sorted[i] = dw.abs_all[off:off + k]
+                dw.perm[i] = dw.perm_all[off:off + k]
+                dw.ranks[i] = dw.ranks_all[roff:roff + k * k].view(k, k, d, w)
                 off += k
                 roff += k * k
             else:  # no sketch: never referenced by a graph
-                dw.abs_sorted.append(dw.abs_all[:0])
-                dw.perm.append(dw.perm_all[:0])
-                dw.ranks.append(dw.ranks_all[:0])
-        dw.edge_ids_all = [e for t in dw.tables for e in t.edge_id]
+                dw.abs_sorted[i] = dw.abs_all[:0]
+                dw.perm[i] = dw.perm_all[:0]
+                dw.ranks[i] = dw.ranks_all[:0]
 
 
-def _presort_tables(dw, s):
-    """cmp_presort of every sketch row of every table, then cmp_cross_ranks_multi: one
-    launch each (tables' counters are consecutive blocks of dw.counters_all)."""
-    total = sum(t.k for t in dw.tables)
+def _presort_tables(dw, s, offline: bool = False):
+    """cmp_presort of every sketch row of the online (or the offline) tables, then
+    cmp_cross_ranks_multi: one launch each over a contiguous range of the buffers."""
+    order = getattr(dw, "storage_order", list(range(len(dw.tables))))
+    n_on = len(getattr(dw, "online", order))
+    lo = sum(dw.tables[i].k for i in order[:n_on]) if offline else 0
+    rlo = sum(dw.tables[i].k ** 2 for i in order[:n_on]) if offline else 0
+    tabs = order[n_on:] if offline else order[:n_on]
+    total = sum(dw.tables[i].k for i in tabs)
     if total == 0:
         return
     need = K.cmp_presort_ws_bytes(total * dw.d, dw.w)
     ws = getattr(dw, "presort_ws", None)
     if need and (ws is None or ws.numel() < need):
         ws = dw.presort_ws = torch.empty(need, dtype=torch.uint8, device=dw.device)
-    K.cmp_presort(dw.counters_all.data_ptr(), total * dw.d, dw.w, dw.abs_all.data_ptr(), dw.perm_all.data_ptr(),
-                  ws.data_ptr() if need else 0, need, s)
-    K.cmp_cross_ranks_multi(dw.abs_all.data_ptr(), dw.perm_all.data_ptr(), [t.k for t in dw.tables],
-                            dw.edge_ids_all, dw.d, dw.w, dw.ranks_all.data_ptr(), s)
+    K.cmp_presort(dw.counters_all[lo:].data_ptr(), total * dw.d, dw.w, dw.abs_all[lo:].data_ptr(),
+                  dw.perm_all[lo:].data_ptr(), ws.data_ptr() if need else 0, need, s)
+    K.cmp_cross_ranks_multi(dw.abs_all[lo:].data_ptr(), dw.perm_all[lo:].data_ptr(), [dw.tables[i].k for i in tabs],
+                            [e for i in tabs for e in dw.tables[i].edge_id], dw.d, dw.w, dw.ranks_all[rlo:].data_ptr(),
+                            s)
 
 
-def _graph_struct(dw, g_tables, g_eu, g_ev, sketch_of, survivors_ptr, keep):
+def _graph_struct(dw, g_tables, g_eu, g_ev, sketch_of, survivors_ptr, keep, sample_rates=None):
     """cmp_graph over tables of `dw`; sketch_of(e, end) -> (table index in dw, sketch index)."""
     ne = len(g_eu)
     eu = (C.c_int32 * max(ne, 1))(*g_eu)
@@ -165,8 +232,9 @@ def _graph_struct(dw, g_tables, g_eu, g_ev, sketch_of, survivors_ptr, keep):
     n2 = max(2 * ne, 1)
     arrs = [(C.c_void_p * n2)(*sk), (C.c_void_p * n2)(*ab), (C.c_void_p * n2)(*pm), (C.c_void_p * n2)(*rk),
             (C.c_int32 * n2)(*sl)]
-    keep += [eu, ev] + arrs
-    return K.cmp_graph(g_tables, ne, eu, ev, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4], survivors_ptr)
+    rates = (C.c_double * max(g_tables, 1))(*sample_rates) if sample_rates is not None else None
+    keep += [eu, ev, rates] + arrs
+    return K.cmp_graph(g_tables, ne, eu, ev, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4], survivors_ptr, rates)
 
 
 class DeviceEstimator:
@@ -183,7 +251,7 @@ class DeviceEstimator:
         for dw in dws:
             _prep_tables(dw)
             self.graphs.append(_graph_struct(dw, len(dw.tables), dw.wl.edge_u, dw.wl.edge_v, dw.wl.sketch_of,
-                                             dw.survivors.data_ptr(), self._keep))
+                                             dw.survivors.data_ptr(), self._keep, dw.sample_rates))
         self.masks = np.ascontiguousarray(masks, np.uint64)
         self.sub_graph = np.zeros(self.masks.size, np.int32) if graph_of is None else np.ascontiguousarray(graph_of,
                                                                                                           np.int32)
@@ -258,7 +326,8 @@ class PartitionedJoin:
     axes follow the order of its sketches in the workload.  cols_dev: optional uploaded
     columns per listed table (e.g. a DeviceWorkload's)."""
 
-    def __init__(self, wl, tables, edges, widths, device="cuda", cols_dev=None, cfg=None, hash_dev=None):
+    def __init__(self, wl, tables, edges, widths, device="cuda", cols_dev=None, cfg=None, hash_dev=None,
+                 sample_rates=None, sample_seed: int = 0x5A3B1E):
         from . import datagen as G
         self.wl = wl
         self.device = torch.device(device)
@@ -280,13 +349,16 @@ class PartitionedJoin:
             src = wl.tables[t]
             sel = [s for s, e in enumerate(src.edge_id) if e in local]
             tt = G.Table(src.name, src.cols, src.preds, [src.key_col[s] for s in sel], [src.edge_id[s] for s in sel])
-            self.tables.append(DeviceTable(tt, self.d, 1, self.device, cols_dev=cols_dev[i] if cols_dev else None))
+            self.tables.append(DeviceTable(tt, self.d, 1, self.device, cols_dev=cols_dev[i] if cols_dev else None,
+                                           sample_seed=sample_seed + t,
+                                           sample_rate=float(sample_rates[i]) if sample_rates is not None else 0.0))
             ax = [local[src.edge_id[s]] for s in sel]
             self.axes.append(ax)
             size = int(np.prod([self.widths[a] for a in ax])) if ax else 1
             self.tensors.append(torch.zeros((self.d, size), dtype=torch.int32, device=self.device))
         self.survivors = torch.zeros(len(self.tables), dtype=torch.int64, device=self.device)
-        self.join, self._keep = K.part_join(eu, ev, self.widths, self.axes, [x.data_ptr() for x in self.tensors])
+        self.join, self._keep = K.part_join(eu, ev, self.widths, self.axes, [x.data_ptr() for x in self.tensors],
+                                            sample_rates)
         nb = K.cmp_part_estimate_ws_bytes(self.join, self.d)
         self.ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=self.device)
         self.est = torch.empty(1, dtype=torch.float64, device=self.device)

@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(K):
 def test_status_strings(K):
     assert K.status_str(0) == "ok"
     assert "invalid" in K.status_str(-1)
-    assert K.lib().cmp_abi_version() == K.CMP_ABI_VERSION == 3
+    assert K.lib().cmp_abi_version() == K.CMP_ABI_VERSION == 4
 
 
 def test_hash_params_match_oracle_generator(K, orc):
@@ -308,3 +308,34 @@ def test_partitioned_estimate_plan_host_logic(K):
     # workspace too small / misaligned: rejected before any launch
     assert K.lib().cmp_part_estimate(C.byref(j), 3, 0x10000, 512, 0x2000, None, None, None) == K.CMP_EWORKSPACE
     assert K.lib().cmp_part_estimate(C.byref(j), 3, 0x10010, 768, 0x2000, None, None, None) == K.CMP_EINVAL
+
+
+def test_sample_rate_rejections(K):
+    """Row-sample rates outside [0, 1] (or NaN) are rejected on the host by the builds, the
+    estimate plan and the partitioned estimate."""
+    L = K.lib()
+    for bad in (-0.5, 1.5, float("nan")):
+        t = _desc(K)
+        t.sample_rate = bad
+        assert L.cmp_sketch_build(C.byref(t), 4, 64, 0x3000, 2, 0x2000, 0x4000, 0x5000, None, None) == K.CMP_EINVAL
+        n, ws = C.c_size_t(0), C.c_size_t(0)
+        assert L.cmp_build_plan_bytes((K.cmp_table * 1)(t), 1, 4, 64, None, C.byref(n), C.byref(ws)) == K.CMP_EINVAL
+        wa = (C.c_int32 * 1)(8)
+        assert L.cmp_part_build(C.byref(t), 4, wa, 0x3000, 2, 0x2000, 0x4000, None, None) == K.CMP_EINVAL
+        j, keep = K.part_join([0], [1], [4], [[0], [0]], [0x1000, 0x2000], [0.5, bad])
+        with pytest.raises(K.CompassError):
+            K.cmp_part_estimate_ws_bytes(j, 3)
+    j, keep = K.part_join([0], [1], [4], [[0], [0]], [0x1000, 0x2000], [0.5, 1.0])
+    assert K.cmp_part_estimate_ws_bytes(j, 3) > 0
+
+
+def test_estimate_plan_sample_rates(K):
+    g = _graph(K, [0, 1], [1, 2], 3)
+    rates = (C.c_double * 3)(0.5, 1.0, 0.25)
+    g.sample_rate = rates
+    pb, wb = K.cmp_estimate_plan_bytes([g], 5, 64, [0, 0], [0b111, 0b001])
+    assert pb > 0
+    for bad in (-1.0, 2.0, float("nan")):
+        rates[1] = bad
+        with pytest.raises(K.CompassError):
+            K.cmp_estimate_plan_bytes([g], 5, 64, [0], [0b111])
