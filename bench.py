@@ -609,9 +609,9 @@ def run_ours(a):
     # sweep when triangles are, finalize
     est_launches = (2 if n_gen_sub > sum(1 for m in masks if bin(m).count("1") == 1) else 0) + \
         (2 if n_tri_sub else 0) + 1
-    # build: zero spans + build kernel, plus key range, clearing and counting when the plan
-    # aggregates key columns (it then has a workspace)
-    build_launches = 2 + (3 if dw._plan[2] else 0)
+    # build: zero spans + build kernel, plus key range, clearing, counting and hashing of the
+    # aggregated key columns when the plan aggregates (it then has a workspace)
+    build_launches = 2 + (4 if dw._plan[2] else 0)
     # presort + cross ranks of all tables: one launch each; combiner: self-join sizes, features,
     # inference, combination; enumeration: one launch
     launches_per_step = build_launches + 2 + est_launches + 4 + 1

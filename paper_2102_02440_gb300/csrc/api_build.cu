@@ -130,7 +130,8 @@ cmp_status choose_shape(const cmp_build_cfg* cfg, int32_t d, int32_t w, int32_t 
   s.dedupe = (cfg && cfg->dedupe >= 0) ? (cfg->dedupe ? 1 : 0) : 1;
   if (s.threads < 32 || s.threads > 1024 || s.threads % 32) return CMP_EINVAL;
   if (s.tile_rows < 128 || s.tile_rows > 16384 || s.tile_rows % 128) return CMP_EINVAL;
-  s.map_slots = s.dedupe ? int32_t(next_pow2(uint32_t(2 * s.tile_rows))) : 0;
+  // the map holds up to 2 entries per tile row; aggregated items use it as 64 entries per warp
+  s.map_slots = s.dedupe ? int32_t(next_pow2(uint32_t(std::max(2 * s.tile_rows, 2 * s.threads)))) : 0;
   if (s.dedupe && s.map_slots > 8 * s.threads) return CMP_EINVAL;  // compaction keeps <= 8 slots per thread
   // overhead of everything but the private counters, with the parameter area sized for all pairs
   BuildShape probe = s;
@@ -240,7 +241,7 @@ cmp_status cmp_sketch_build(const cmp_table* table, int32_t d, int32_t w, const 
 
 // ---------------------------------------------------------------- batched build plan
 // blob: [BuildPlanHdr][DevTable x n_tables][BuildItem x n_items][int32 cta_item x grid]
-//       [ZeroSpan x n_zero][AggCol x n_agg][CountItem x n_cnt_items][int32 cnt_cta x cnt_grid]
+//       [ZeroSpan x n_zero][AggCol x n_agg][CountItem x n_cnt_items]
 
 // Key aggregation: tables with at least this many rows (auto mode), count arrays of at
 // most this many slots (a column whose key range is wider keeps the per-row path).
@@ -253,10 +254,14 @@ struct BuildPlanParts {
   std::vector<int32_t> cta_item;
   std::vector<AggCol> aggs;
   std::vector<CountItem> cnt_items;
-  std::vector<int32_t> cnt_cta;
+  int64_t cnt_total_chunks = 0;
+  int32_t cnt_grid = 0;
+  int64_t hash_total_chunks = 0;
+  int32_t hash_max_pairs = 1, hash_grid = 0;
   std::vector<std::vector<int32_t>> col_agg;  // [table][col] AggCol index or -1
   size_t bytes = 0, ws_bytes = 0;
   int32_t stat_grid = 0;
+  int32_t cache_slots = 256, cache_cols = 0;  // counting pass
 };
 
 static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -281,7 +286,7 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
   // aggregated key columns: every distinct key column of a selected table
   P->col_agg.assign(n_tables, std::vector<int32_t>(CMP_MAX_COLS, -1));
   P->aggs.clear();
-  size_t ws = al256(16 * size_t(n_tables) * CMP_MAX_SKETCHES);  // stats area (upper bound, fixed)
+  size_t ws = al256(16 * size_t(n_tables) * CMP_MAX_SKETCHES + 16);  // stats + chunk counter (upper bound)
   for (int32_t t = 0; t < n_tables; t++) {
     const cmp_table& tb = tables[t];
     const bool on = tb.n_sketches > 0 && tb.n_rows > 0 && s.dedupe &&
@@ -330,19 +335,19 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
       Raw r{t, b, e, -1, tiles, double(tiles) * double(row_pairs + 1)};
       total += r.work;
       raw.push_back(r);
-      for (int32_t c = 0; c < tb.n_cols; c++) {
-        const int32_t ai = P->col_agg[t][c];
-        if (ai < 0) continue;
-        int32_t np = 0;
-        for (int32_t p = b; p < e; p++) np += tb.key_col[p / d] == c;
-        if (!np) continue;
-        const int64_t chunks = (P->aggs[ai].cap + s.map_slots - 1) / s.map_slots;
-        Raw ra{t, b, e, ai, chunks, double(chunks) * (1.0 + 0.25 * np)};
-        total += ra.work;
-        raw.push_back(ra);
-      }
     }
   }
+  // hashing pass of the aggregated columns: chunks of kHashChunk count-array slots
+  P->hash_total_chunks = 0;
+  P->hash_max_pairs = 1;
+  for (AggCol& ac : P->aggs) {
+    ac.hash_chunk0 = P->hash_total_chunks;
+    P->hash_total_chunks += (ac.cap + kHashChunk - 1) / kHashChunk;
+    int32_t np = 0;
+    for (int32_t k = 0; k < tables[ac.table].n_sketches; k++) np += tables[ac.table].key_col[k] == ac.col ? d : 0;
+    P->hash_max_pairs = std::max(P->hash_max_pairs, np);
+  }
+  P->hash_grid = int32_t(std::min<int64_t>(P->hash_total_chunks, int64_t(sm_count()) * 2));  // resident: 2 per SM
   const double target = double(sm_count()) * ctas_per_sm * 4.0;
   P->items.clear();
   P->cta_item.clear();
@@ -355,34 +360,40 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
     it.pair_end = r.e;
     it.n_ctas = int32_t(n);
     it.first_cta = int32_t(P->cta_item.size());
-    it.agg = r.agg;
+    it.pad = 0;
     for (int64_t c = 0; c < n; c++) P->cta_item.push_back(int32_t(P->items.size()));
     P->items.push_back(it);
   }
-  // counting pass: one item per table with aggregated columns, CTAs by tiles x columns
+  // counting pass: one item per table with aggregated columns, its rows as chunks of 4
+  // tiles; a persistent grid of about one resident wave takes the chunks in order
   P->cnt_items.clear();
-  P->cnt_cta.clear();
-  double cnt_total = 0;
-  for (int32_t t = 0; t < n_tables; t++) {
-    int ncol = 0;
-    for (int32_t c = 0; c < CMP_MAX_COLS; c++) ncol += P->col_agg[t][c] >= 0;
-    if (ncol) cnt_total += double((tables[t].n_rows + R - 1) / R) * (ncol + 1);
-  }
-  const double cnt_target = double(sm_count()) * std::max(1, 2048 / s.threads) * 4.0;
+  P->cnt_total_chunks = 0;
   for (int32_t t = 0; t < n_tables; t++) {
     int ncol = 0;
     for (int32_t c = 0; c < CMP_MAX_COLS; c++) ncol += P->col_agg[t][c] >= 0;
     if (!ncol) continue;
-    const int64_t tiles = (tables[t].n_rows + R - 1) / R;
-    int64_t n = int64_t(double(tiles) * (ncol + 1) / std::max(cnt_total, 1.0) * cnt_target + 0.5);
-    n = std::max<int64_t>(1, std::min<int64_t>(n, tiles));
     CountItem ci;
     ci.table = t;
-    ci.n_ctas = int32_t(n);
-    ci.first_cta = int32_t(P->cnt_cta.size());
     ci.pad = 0;
-    for (int64_t c = 0; c < n; c++) P->cnt_cta.push_back(int32_t(P->cnt_items.size()));
+    ci.chunk_begin = P->cnt_total_chunks;
+    ci.n_chunks = (tables[t].n_rows + 4 * int64_t(R) - 1) / (4 * int64_t(R));
+    P->cnt_total_chunks += ci.n_chunks;
     P->cnt_items.push_back(ci);
+  }
+  P->cnt_grid = int32_t(std::min<int64_t>(P->cnt_total_chunks, int64_t(sm_count()) * std::max(1, 2048 / s.threads)));
+  // hot-key caches of the counting pass: the most aggregated columns of any table (at most
+  // 4 cached), a power-of-two number of slots per column in about 112 KB
+  {
+    int max_ac = 0;
+    for (int32_t t = 0; t < n_tables; t++) {
+      int n = 0;
+      for (int32_t c = 0; c < CMP_MAX_COLS; c++) n += P->col_agg[t][c] >= 0;
+      max_ac = std::max(max_ac, n);
+    }
+    P->cache_cols = std::min(max_ac, 4);
+    int32_t h = 8192;
+    while (P->cache_cols && h > 256 && size_t(h) * 8 * size_t(P->cache_cols) > (size_t(112) << 10)) h >>= 1;
+    P->cache_slots = P->cache_cols ? h : 256;
   }
   // key-range pass: CTAs per column in proportion to its rows (about 8 per SM in all)
   {
@@ -409,7 +420,6 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
   off += align16(sizeof(ZeroSpan) * (n_tables + 1));
   off += align16(sizeof(AggCol) * P->aggs.size());
   off += align16(sizeof(CountItem) * P->cnt_items.size());
-  off += align16(sizeof(int32_t) * P->cnt_cta.size());
   P->bytes = off;
   return CMP_OK;
 }
@@ -464,9 +474,14 @@ extern "C" cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_t
   h.n_cnt_items = int64_t(P.cnt_items.size());
   h.off_cnt_items = int64_t(off);
   off += align16(sizeof(CountItem) * P.cnt_items.size());
-  h.off_cnt_cta = int64_t(off);
-  h.cnt_grid = int32_t(P.cnt_cta.size());
+  h.cnt_total_chunks = P.cnt_total_chunks;
+  h.cnt_grid = P.cnt_grid;
   h.stat_grid = P.stat_grid;
+  h.cnt_cache_slots = P.cache_slots;
+  h.cnt_cache_cols = P.cache_cols;
+  h.hash_total_chunks = P.hash_total_chunks;
+  h.hash_max_pairs = P.hash_max_pairs;
+  h.hash_grid = P.hash_grid;
   h.ws_bytes = int64_t(P.ws_bytes);
   h.total_bytes = int64_t(P.bytes);
   std::vector<ZeroSpan> zs;
@@ -485,7 +500,6 @@ extern "C" cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_t
   if (!P.aggs.empty()) std::memcpy(base + h.off_agg, P.aggs.data(), sizeof(AggCol) * P.aggs.size());
   if (!P.cnt_items.empty())
     std::memcpy(base + h.off_cnt_items, P.cnt_items.data(), sizeof(CountItem) * P.cnt_items.size());
-  if (!P.cnt_cta.empty()) std::memcpy(base + h.off_cnt_cta, P.cnt_cta.data(), sizeof(int32_t) * P.cnt_cta.size());
   std::memcpy(base, &h, sizeof(h));
   return CMP_OK;
 }
@@ -519,11 +533,18 @@ extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void
     a.n_agg = int32_t(h.n_agg);
     a.ws = static_cast<unsigned char*>(ws_dev);
     a.cnt_items = reinterpret_cast<const CountItem*>(dev + h.off_cnt_items);
-    a.cnt_cta_item = reinterpret_cast<const int32_t*>(dev + h.off_cnt_cta);
-    // the (max, min) stats start from zero (decoding as an empty column)
-    if (cudaMemsetAsync(ws_dev, 0, 16 * size_t(h.n_agg), cs) != cudaSuccess) return CMP_ECUDA;
+    a.n_cnt_items = int32_t(h.n_cnt_items);
+    a.cnt_total_chunks = h.cnt_total_chunks;
+    a.hash_total_chunks = h.hash_total_chunks;
+    a.hash_max_pairs = h.hash_max_pairs;
+    a.cnt_cache_slots = h.cnt_cache_slots;
+    a.cnt_cache_cols = h.cnt_cache_cols;
+    // the (max, min) stats start from zero (decoding as an empty column), so do the chunk
+    // counters of the counting and hashing passes after them
+    if (cudaMemsetAsync(ws_dev, 0, 16 * size_t(h.n_agg) + 16, cs) != cudaSuccess) return CMP_ECUDA;
     if (launch_agg(a, h.shape, h.stat_grid, h.cnt_grid, cs) != cudaSuccess) return CMP_ECUDA;
   }
-  return launch_build(a, h.shape, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
+  if (launch_build(a, h.shape, cs) != cudaSuccess) return CMP_ECUDA;
+  return launch_agg_hash(a, h.n_agg > 0 ? h.hash_grid : 0, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
 }
 

@@ -18,10 +18,12 @@
 //
 // Key aggregation (batched build, large tables): before the build kernel, k_agg_stats
 // finds each aggregated key column's smallest and largest key, k_agg_zero clears the
-// used part of its count array, and k_agg_count adds every tile's survivors to it (tile
-// keys reduced in a shared-memory map first, one global atomic per distinct key of the
-// tile).  The build kernel's aggregated items then hash each nonzero (key, count) entry
-// once per pair instead of once per tuple, and its row items skip those columns.
+// used part of its count array, and k_agg_count counts the survivors per key: each CTA
+// keeps a shared-memory cache of the keys it meets first (the frequent keys of a skewed
+// column settle there), counts them there and every other key with one global atomic, and
+// adds its cache to the count arrays at the end.  The build kernel's aggregated items then
+// hash each nonzero (key, count) entry once per pair instead of once per tuple, and its
+// row items skip those columns.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
 
   // ---- resolve the work item of this CTA
   const DevTable* tb;
-  int pair_begin, pair_end, cta_in_slab, n_ctas, agg_item = -1;
+  int pair_begin, pair_end, cta_in_slab, n_ctas;
   if (A.items) {
     const BuildItem it = A.items[A.cta_item[blockIdx.x]];
     tb = A.tables + it.table;
@@ -60,7 +62,6 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
     pair_end = it.pair_end;
     cta_in_slab = int(blockIdx.x) - it.first_cta;
     n_ctas = it.n_ctas;
-    agg_item = it.agg;
   } else {
     tb = &A.table;
     const int slab = int(blockIdx.x) / A.ctas_per_slab;
@@ -70,6 +71,23 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
     const int total_pairs = tb->n_sketches * A.d;
     pair_end = min(pair_begin + A.pairs_per_slab, total_pairs);
   }
+  // Key columns of the slab not hashed by the aggregated path at run time.  When a table has
+  // an active aggregated column, the counting pass scans all its tiles and counts its
+  // survivors; if every key column of the slab is aggregated, this CTA has nothing to do
+  // (block-uniform: every thread reads the same descriptors).
+  bool row_cols = false, table_agg = false;
+  if (A.agg)
+    for (int c = 0; c < tb->n_cols; c++) {
+      int64_t kmin, range;
+      if (tb->agg[c] >= 0 && agg_active(A.agg[tb->agg[c]], tb->agg[c], A.ws, &kmin, &range)) table_agg = true;
+    }
+  for (int s = pair_begin / A.d; pair_end > pair_begin && s <= (pair_end - 1) / A.d && !row_cols; s++) {
+    const int c = tb->key_col[s];
+    int64_t kmin, range;
+    if (!(A.agg && tb->agg[c] >= 0 && agg_active(A.agg[tb->agg[c]], tb->agg[c], A.ws, &kmin, &range)))
+      row_cols = true;
+  }
+  if (table_agg && !row_cols) return;
   const int npairs = pair_end - pair_begin;
   const int w = A.w;
   const int64_t n_rows = tb->n_rows;
@@ -173,42 +191,7 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
     }
   };
 
-  if (agg_item >= 0) {
-    // ---------------- aggregated column: chunks of its count array
-    if constexpr (DEDUPE) {
-      const AggCol ac = A.agg[agg_item];
-      int64_t kmin = 0, range = 0;
-      int kc = -1;
-      for (int k = 0; k < n_keycols; k++)
-        if (cols_list[k] == ac.col) kc = k;
-      if (kc >= 0 && agg_active(ac, agg_item, A.ws, &kmin, &range)) {
-        const int32_t* cnts = reinterpret_cast<const int32_t*>(A.ws + ac.off);
-        const int64_t n_chunks = (range + M - 1) / M;  // chunks of the entry lists' capacity
-        for (int64_t chunk = cta_in_slab; chunk < n_chunks; chunk += n_ctas) {
-          const int64_t i0 = chunk * M;
-          const int nin = int(min(int64_t(M), range - i0));
-          if (tid == 0) sint[0] = 0;
-          __syncthreads();
-          for (int base = 0; base < nin; base += T) {  // block-uniform trip count
-            const int j = base + tid;
-            const int32_t c = j < nin ? __ldg(cnts + i0 + j) : 0;
-            const unsigned nz = __ballot_sync(0xffffffffu, c != 0);
-            int wbase = 0;
-            if (lane == 0 && nz) wbase = atomicAdd(&sint[0], __popc(nz));
-            wbase = __shfl_sync(0xffffffffu, wbase, 0);
-            if (c != 0) {
-              const int pos = wbase + __popc(nz & ((1u << lane) - 1u));
-              mkey[pos] = key_field(kmin + i0 + j);
-              mcnt[pos] = c;
-            }
-          }
-          __syncthreads();
-          hash_entries(kc, sint[0], nullptr, 0, 0, true);
-          __syncthreads();  // entry lists reused next
-        }
-      }
-    }
-  } else {
+  {
     const int64_t n_tiles = (n_rows + R - 1) / R;
     for (int64_t tile = cta_in_slab; tile < n_tiles; tile += n_ctas) {
       const int64_t r0 = tile * R;
@@ -216,7 +199,7 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
 
       // ---------------- A. predicates and survivor compaction
       const int n_surv = tile_survivors(tb, r0, rows_in_tile, R, vec, surv, sint);
-      my_survivors += n_surv;
+      if (!table_agg) my_survivors += n_surv;
 
       // ---------------- B. per key column: aggregate equal keys, hash, update
       for (int kc = 0; kc < n_keycols; kc++) {
@@ -228,7 +211,10 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
         const void* kbase = tb->col[c];
         const int32_t kdt = tb->dtype[c];
         int n_entries = n_surv;
-        if (DEDUPE) {
+        // a tile with at most one survivor per thread is hashed directly: the map's clearing
+        // and compaction would cost more than the duplicates it merges
+        const bool use_map = DEDUPE && n_surv > T;  // block-uniform
+        if (use_map) {
           for (int s = tid; s < M; s += T) {
             mkey[s] = kEmptyKey;
             mcnt[s] = 0;
@@ -306,7 +292,7 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
           }
           __syncthreads();
         }
-        hash_entries(kc, n_entries, kbase, kdt, r0, DEDUPE);
+        hash_entries(kc, n_entries, kbase, kdt, r0, use_map);
         __syncthreads();  // map / survivor list reused next
       }
     }
@@ -314,6 +300,7 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
 
   // ---------------- C. flush private counters, count survivors once per table
   if (!GLOBAL) {
+    __syncthreads();
     for (int j = tid; j < npairs * w; j += T) {
       const int32_t v = cnt[j];
       if (v) atomicAdd(gcnt + j, v);
@@ -432,83 +419,274 @@ __global__ void __launch_bounds__(256) k_agg_zero(const __grid_constant__ BuildA
 // that claims an empty slot with the count, or an add to a slot holding the key.  Equal
 // keys of a warp are inserted once, by their lowest lane (__match_any_sync).  The flush
 // also empties the slots, so the map is cleared once per CTA.
-__global__ void __launch_bounds__(1024) k_agg_count(const __grid_constant__ BuildArgs A) {
+__global__ void __launch_bounds__(1024, 2) k_agg_count(const __grid_constant__ BuildArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const CountItem it = A.cnt_items[A.cnt_cta_item[blockIdx.x]];
-  const DevTable* tb = A.tables + it.table;
-  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
-  const int R = A.tile_rows, M = A.map_slots;
-  unsigned char* sp = smem;
-  unsigned long long* slot64 = reinterpret_cast<unsigned long long*>(sp);
-  sp += align16(sizeof(unsigned long long) * size_t(M));
+  __shared__ int32_t* acnt[CMP_MAX_SKETCHES];  // the current table's active aggregated columns
+  __shared__ int64_t amin[CMP_MAX_SKETCHES];
+  __shared__ int32_t acol[CMP_MAX_SKETCHES];
+  __shared__ int32_t n_ac;
+  __shared__ long long next_chunk;
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int R = A.tile_rows, H = A.cnt_cache_slots, n_cache = A.cnt_cache_cols;
+  const int hshift = 32 - (31 - __clz(H));  // H is a power of two >= 256
+  uint32_t* ckey = reinterpret_cast<uint32_t*>(smem);  // [n_cache][H] cached key - min
+  uint32_t* ccnt = ckey + size_t(H) * n_cache;          // [n_cache][H] its count so far
+  unsigned char* sp = smem + align16(sizeof(uint32_t) * 2 * size_t(H) * n_cache);
   uint16_t* surv = reinterpret_cast<uint16_t*>(sp);
   sp += align16(sizeof(uint16_t) * R);
   int32_t* sint = reinterpret_cast<int32_t*>(sp);
-  constexpr unsigned long long kEmpty = ~0ull;  // key part 0xFFFFFFFF is never an index: cap <= 2^31 - 1
-  const int64_t n_rows = tb->n_rows;
-  const int64_t n_tiles = (n_rows + R - 1) / R;
-  const int filtered = tb->filtered;
-  const bool vec = tb->vec_ok != 0;
-  const int cta = int(blockIdx.x) - it.first_cta;
-  const uint32_t mmask = uint32_t(M - 1);
-  for (int s = tid; s < M; s += T) slot64[s] = kEmpty;
-  __syncthreads();
-  for (int64_t tile = cta; tile < n_tiles; tile += it.n_ctas) {
-    const int64_t r0 = tile * R;
-    const int rows_in_tile = int(min(int64_t(R), n_rows - r0));
-    const int n_surv = tile_survivors(tb, r0, rows_in_tile, R, vec, surv, sint);
-    for (int c = 0; c < tb->n_cols; c++) {
-      const int ai = tb->agg[c];
-      if (ai < 0) continue;
-      int64_t kmin, range;
-      if (!agg_active(A.agg[ai], ai, A.ws, &kmin, &range)) continue;  // block-uniform
-      int32_t* cnts = reinterpret_cast<int32_t*>(A.ws + A.agg[ai].off);
-      const void* kbase = tb->col[c];
-      const int32_t kdt = tb->dtype[c];
-      for (int base = 0; base < n_surv; base += T) {  // block-uniform trip count
-        const int e = base + tid;
-        const bool valid = e < n_surv;
-        uint32_t x = 0xFFFFFFFFu;
-        if (valid) x = uint32_t(load1(kbase, kdt, r0 + (filtered ? surv[e] : e)) - kmin);  // < range <= cap
-        const unsigned peers = __match_any_sync(0xffffffffu, x);
-        if (!valid || lane != __ffs(peers) - 1) continue;
-        const unsigned long long cnt = (unsigned long long)__popc(peers);
-        uint32_t slot = map_slot(x, mmask);
-        bool done = false;
-        for (int probe = 0; probe < M && !done; probe++) {
-          const unsigned long long cur = slot64[slot];
-          if (uint32_t(cur >> 32) == x) {
-            atomicAdd(&slot64[slot], cnt);
-            done = true;
-          } else if (cur == kEmpty) {
-            const unsigned long long prev = atomicCAS(&slot64[slot], kEmpty, ((unsigned long long)x << 32) | cnt);
-            if (prev == kEmpty) {
-              done = true;
-            } else if (uint32_t(prev >> 32) == x) {
-              atomicAdd(&slot64[slot], cnt);
-              done = true;
-            }
-          }
-          if (!done) slot = (slot + 1) & mmask;
+  constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // never an index: cap <= 2^27
+  unsigned long long* work = reinterpret_cast<unsigned long long*>(A.ws) + 2 * int64_t(A.n_agg);
+  const int64_t CH = 4 * int64_t(R);  // rows per chunk
+
+  // One surviving key of active column a: its cache slot when that slot holds the key or is
+  // free, else one global atomic on its count-array entry.
+  auto count_key = [&](int a, int64_t key) {
+    const uint32_t x = uint32_t(key - amin[a]);  // < range <= cap
+    if (a < n_cache) {
+      const size_t slot = size_t(a) * H + ((x * 0x9E3779B1u) >> hshift);
+      const uint32_t cur = *reinterpret_cast<volatile uint32_t*>(ckey + slot);
+      if (cur == x) {
+        atomicAdd(ccnt + slot, 1u);
+        return;
+      }
+      if (cur == kEmpty) {
+        const uint32_t prev = atomicCAS(ckey + slot, kEmpty, x);
+        if (prev == kEmpty || prev == x) {
+          atomicAdd(ccnt + slot, 1u);
+          return;
         }
-        if (!done) set_status(A.status, CMP_ETIMEOUT);  // unreachable: M > tile rows
+      }
+    }
+    atomicAdd(acnt[a] + x, 1);
+  };
+  // adds the caches of the current table to its count arrays (block-wide)
+  auto flush = [&]() {
+    __syncthreads();
+    for (int a = 0; a < min(int(n_ac), n_cache); a++)
+      for (int s = tid; s < H; s += T) {
+        const uint32_t k = ckey[size_t(a) * H + s];
+        if (k != kEmpty) atomicAdd(acnt[a] + k, int32_t(ccnt[size_t(a) * H + s]));
+      }
+    __syncthreads();
+  };
+
+  int item = -1;  // block-uniform
+  for (;;) {
+    if (tid == 0) next_chunk = (long long)atomicAdd(work, 1ull);
+    __syncthreads();
+    const int64_t c = next_chunk;
+    if (c >= A.cnt_total_chunks) break;  // block-uniform
+    int it = 0;
+    while (it + 1 < A.n_cnt_items && A.cnt_items[it + 1].chunk_begin <= c) it++;
+    const CountItem ci = A.cnt_items[it];
+    const DevTable* tb = A.tables + ci.table;
+    if (it != item) {  // a new table: flush the caches, then set them up for its columns
+      if (item >= 0) flush();
+      if (tid == 0) {
+        int n = 0;
+        for (int col = 0; col < tb->n_cols && n < CMP_MAX_SKETCHES; col++) {
+          const int ai = tb->agg[col];
+          int64_t kmin, range;
+          if (ai < 0 || !agg_active(A.agg[ai], ai, A.ws, &kmin, &range)) continue;
+          acnt[n] = reinterpret_cast<int32_t*>(A.ws + A.agg[ai].off);
+          amin[n] = kmin;
+          acol[n] = col;
+          n++;
+        }
+        n_ac = n;
+      }
+      for (int s = tid; s < H * n_cache; s += T) {
+        ckey[s] = kEmpty;
+        ccnt[s] = 0;
+      }
+      item = it;
+      __syncthreads();
+    }
+    const int nac = n_ac;
+    const int64_t n_rows = tb->n_rows;
+    const int64_t r_begin = (c - ci.chunk_begin) * CH, r_end = min(n_rows, r_begin + CH);
+    const bool vec = tb->vec_ok != 0;
+    // a table with an active aggregated column has its survivors counted here, once per
+    // tile (the build kernel's row items then leave them out)
+    if (!tb->filtered) {
+      if (tid == 0 && nac > 0 && r_end > r_begin)
+        atomicAdd(reinterpret_cast<unsigned long long*>(tb->survivors), (unsigned long long)(r_end - r_begin));
+      // every row survives: eight consecutive rows per thread and step, two 16-byte loads
+      // for int32 keys
+      for (int a = 0; a < nac; a++) {
+        const void* kbase = tb->col[acol[a]];
+        const int32_t kdt = tb->dtype[acol[a]];
+        for (int64_t r = r_begin + 8 * int64_t(tid); r < r_end; r += 8 * int64_t(T)) {
+          if (kdt == CMP_I32 && vec && r + 8 <= r_end) {
+            const int4* p = reinterpret_cast<const int4*>(reinterpret_cast<const int32_t*>(kbase) + r);
+            const int4 u = __ldg(p), v = __ldg(p + 1);
+            count_key(a, u.x), count_key(a, u.y), count_key(a, u.z), count_key(a, u.w);
+            count_key(a, v.x), count_key(a, v.y), count_key(a, v.z), count_key(a, v.w);
+          } else {
+            const int64_t re = min(r_end, r + 8);
+            for (int64_t q = r; q < re; q++) count_key(a, load1(kbase, kdt, q));
+          }
+        }
+      }
+    } else {
+      for (int64_t r0 = r_begin; r0 < r_end; r0 += R) {
+        const int rows_in_tile = int(min(int64_t(R), r_end - r0));
+        const int n_surv = tile_survivors(tb, r0, rows_in_tile, R, vec, surv, sint);
+        if (tid == 0 && nac > 0 && n_surv)
+          atomicAdd(reinterpret_cast<unsigned long long*>(tb->survivors), (unsigned long long)n_surv);
+        for (int a = 0; a < nac; a++) {
+          const void* kbase = tb->col[acol[a]];
+          const int32_t kdt = tb->dtype[acol[a]];
+          for (int e = tid; e < n_surv; e += T) count_key(a, load1(kbase, kdt, r0 + surv[e]));
+        }
+        __syncthreads();  // surv is rewritten by the next tile
+      }
+    }
+    __syncthreads();  // next_chunk is rewritten next
+  }
+  if (item >= 0) flush();
+}
+
+// Hashing of the aggregated key columns: every nonzero (key, count) entry of a count array
+// is hashed once per (sketch, row) pair on that column, and count * xi is added to the
+// global counters.  Persistent CTAs take chunks of count-array slots in order from an
+// atomic counter; a CTA loads the pairs' parameters when its column changes.  Each warp
+// compacts the nonzero entries of its part of a chunk, 32 slots at a time, into a 96-entry
+// buffer and hashes 64 of them, two per lane, whenever it holds 64.
+constexpr int kHashThreads = 512;
+
+constexpr int kHashBuf = 96;  // entries buffered per warp: 64 hashed at a time, 31 carried over
+
+size_t agg_hash_smem_bytes(int32_t max_pairs) {
+  return align16(sizeof(PairParam) * size_t(max_pairs)) + align16(sizeof(int32_t*) * size_t(max_pairs)) +
+         (kHashThreads / 32) * kHashBuf * (sizeof(unsigned long long) + sizeof(int32_t));
+}
+
+template <bool POW2>
+__global__ void __launch_bounds__(kHashThreads) k_agg_hash(const __grid_constant__ BuildArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long next_chunk;
+  __shared__ int32_t n_pairs, active;
+  __shared__ long long s_kmin, s_range;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int mp = A.hash_max_pairs;
+  PairParam* prm = reinterpret_cast<PairParam*>(smem);
+  int32_t** prow = reinterpret_cast<int32_t**>(smem + align16(sizeof(PairParam) * size_t(mp)));
+  unsigned long long* bkey = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(prow) +
+                                                                   align16(sizeof(int32_t*) * size_t(mp))) +
+                             kHashBuf * warp;
+  int32_t* bcnt = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned long long*>(
+                      reinterpret_cast<unsigned char*>(prow) + align16(sizeof(int32_t*) * size_t(mp))) +
+                                             kHashBuf * nw) +
+                  kHashBuf * warp;
+  unsigned long long* work = reinterpret_cast<unsigned long long*>(A.ws) + 2 * int64_t(A.n_agg) + 1;
+  const uint32_t w = uint32_t(A.w);
+  int cur = -1;  // block-uniform
+  for (;;) {
+    if (tid == 0) next_chunk = (long long)atomicAdd(work, 1ull);
+    __syncthreads();
+    const int64_t c = next_chunk;
+    if (c >= A.hash_total_chunks) break;
+    int ai = 0;
+    while (ai + 1 < A.n_agg && A.agg[ai + 1].hash_chunk0 <= c) ai++;
+    const AggCol ac = A.agg[ai];
+    const DevTable* tb = A.tables + ac.table;
+    if (ai != cur) {  // a new column: its pairs' parameters and counter rows
+      if (tid == 0) {
+        int64_t kmin = 0, range = 0;
+        active = agg_active(ac, ai, A.ws, &kmin, &range) ? 1 : 0;
+        s_kmin = kmin;
+        s_range = range;
+        int n = 0;
+        for (int s = 0; s < tb->n_sketches; s++)
+          if (tb->key_col[s] == ac.col) n += A.d;
+        n_pairs = n;
       }
       __syncthreads();
-      for (int s = tid; s < M; s += T) {
-        const unsigned long long v = slot64[s];
-        if (v != kEmpty) {
-          atomicAdd(cnts + uint32_t(v >> 32), int32_t(uint32_t(v)));
-          slot64[s] = kEmpty;
+      const int np = n_pairs;
+      for (int p = tid; p < np; p += blockDim.x) {
+        int s = 0, k = p / A.d;  // the k-th sketch on this column
+        for (;; s++)
+          if (tb->key_col[s] == ac.col && k-- == 0) break;
+        const int i = p % A.d;
+        prm[p] = make_pair_param(A.hash[size_t(tb->edge_id[s]) * A.d + i]);
+        prow[p] = tb->counters + (size_t(s) * A.d + i) * w;
+      }
+      cur = ai;
+      __syncthreads();
+    }
+    const int64_t s0 = (c - ac.hash_chunk0) * kHashChunk, range = s_range;
+    if (active && s0 < range) {
+      const int32_t* cnts = reinterpret_cast<const int32_t*>(A.ws + ac.off);
+      const int64_t kmin = s_kmin;
+      const int np = n_pairs;
+      const int64_t per = kHashChunk / nw;  // a multiple of 32
+      const int64_t ws0 = min(range, s0 + warp * per), ws1 = min(range, ws0 + per);
+      // entries j0 and j1 of the warp's buffer (a negative index: nothing), two independent
+      // hash chains per lane sharing every parameter load
+      auto hash_batch = [&](int j0, int j1) {
+        const uint64_t x0 = j0 >= 0 ? bkey[j0] : 0, x1 = j1 >= 0 ? bkey[j1] : 0;
+        const int32_t m0 = j0 >= 0 ? bcnt[j0] : 0, m1 = j1 >= 0 ? bcnt[j1] : 0;
+        const KeyPow k0 = key_powers(x0), k1 = key_powers(x1);
+        auto run = [&](auto smallx) {
+          constexpr bool SX = decltype(smallx)::value;
+          for (int p = 0; p < np; p++) {
+            const PairParam q = prm[p];
+            int32_t* row = prow[p];
+            const uint32_t h0 = cw_bucket<POW2, SX>(q, k0, w), h1 = cw_bucket<POW2, SX>(q, k1, w);
+            const int32_t v0 = cw_sign<SX>(q, k0) * m0, v1 = cw_sign<SX>(q, k1) * m1;
+            if (m0) atomicAdd(row + h0, v0);
+            if (m1) atomicAdd(row + h1, v1);
+          }
+        };
+        if (__all_sync(0xffffffffu, (k0.x.hi | k1.x.hi) == 0)) run(std::true_type{});
+        else run(std::false_type{});
+      };
+      int nb = 0;  // warp-uniform
+      for (int64_t sb = ws0; sb < ws1; sb += 32) {
+        const int64_t j = sb + lane;
+        const int32_t cnt = j < ws1 ? __ldg(cnts + j) : 0;
+        const unsigned nz = __ballot_sync(0xffffffffu, cnt != 0);
+        if (cnt != 0) {
+          const int pos = nb + __popc(nz & ((1u << lane) - 1u));
+          bkey[pos] = key_field(kmin + j);
+          bcnt[pos] = cnt;
+        }
+        nb += __popc(nz);
+        __syncwarp();
+        if (nb >= 64) {
+          hash_batch(lane, 32 + lane);
+          __syncwarp();
+          if (lane < nb - 64) {  // keep the overflow at the front
+            bkey[lane] = bkey[64 + lane];
+            bcnt[lane] = bcnt[64 + lane];
+          }
+          nb -= 64;
+          __syncwarp();
         }
       }
-      __syncthreads();  // map reused next
+      if (nb > 0) hash_batch(lane < nb ? lane : -1, 32 + lane < nb ? 32 + lane : -1);
     }
+    __syncthreads();  // next_chunk and the parameters are rewritten next
   }
 }
 
-size_t agg_count_smem_bytes(const BuildShape& s) {
-  return align16(sizeof(unsigned long long) * size_t(s.map_slots)) + align16(sizeof(uint16_t) * s.tile_rows) +
-         sizeof(int32_t) * 40;
+cudaError_t launch_agg_hash(const BuildArgs& a, int32_t grid, cudaStream_t st) {
+  if (a.n_agg <= 0 || grid <= 0) return cudaSuccess;
+  const size_t smem = agg_hash_smem_bytes(a.hash_max_pairs);
+  const bool pow2 = (a.w & (a.w - 1)) == 0;
+  cudaError_t e = pow2 ? cudaFuncSetAttribute(k_agg_hash<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))
+                       : cudaFuncSetAttribute(k_agg_hash<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  if (pow2) k_agg_hash<true><<<unsigned(grid), kHashThreads, smem, st>>>(a);
+  else k_agg_hash<false><<<unsigned(grid), kHashThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+size_t agg_count_smem_bytes(const BuildShape& s, int32_t cache_slots, int32_t cache_cols) {
+  return align16(sizeof(uint32_t) * 2 * size_t(cache_slots) * size_t(cache_cols)) +
+         align16(sizeof(uint16_t) * s.tile_rows) + sizeof(int32_t) * 40;
 }
 
 cudaError_t launch_agg(const BuildArgs& a, const BuildShape& s, int32_t stat_grid, int32_t cnt_grid,
@@ -519,7 +697,7 @@ cudaError_t launch_agg(const BuildArgs& a, const BuildShape& s, int32_t stat_gri
   k_agg_zero<<<g, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || cnt_grid <= 0) return e;
-  const size_t smem = agg_count_smem_bytes(s);
+  const size_t smem = agg_count_smem_bytes(s, a.cnt_cache_slots, a.cnt_cache_cols);
   e = cudaFuncSetAttribute(k_agg_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   k_agg_count<<<unsigned(cnt_grid), s.threads, smem, st>>>(a);

@@ -94,7 +94,57 @@ __device__ TriPtrs tri_ptrs(unsigned char* base, int w, int max_leaves) {
   return p;
 }
 
-__device__ void bitonic_sort(unsigned long long* key, int n2) {
+// Merge sort of key[0..n2) ascending in shared memory, n2 = E * blockDim.x: thread t sorts
+// keys [t E, t E + E) in registers, then log2(blockDim.x) rounds each merge pairs of sorted
+// runs; a thread finds where its E outputs start on the merge path by binary search and
+// merges them sequentially.  Two barriers per round (about 20 for 4096 keys).
+template <int E>
+__device__ void merge_sort_reg(unsigned long long* key, int n2) {
+  const int t = threadIdx.x;
+  unsigned long long v[E];
+#pragma unroll
+  for (int e = 0; e < E; e++) v[e] = key[t * E + e];
+#pragma unroll
+  for (int a = 1; a < E; a++)  // insertion sort of the thread's keys
+#pragma unroll
+    for (int b = a; b > 0; b--)
+      if (v[b - 1] > v[b]) {
+        const unsigned long long x = v[b - 1];
+        v[b - 1] = v[b];
+        v[b] = x;
+      }
+  for (int width = E; width < n2; width <<= 1) {
+    __syncthreads();  // every read of the previous round is done
+#pragma unroll
+    for (int e = 0; e < E; e++) key[t * E + e] = v[e];
+    __syncthreads();
+    const int start = (t * E) & ~(2 * width - 1);  // first key of the pair of runs
+    const unsigned long long* A = key + start;
+    const unsigned long long* B = A + width;
+    const int d = t * E - start;  // outputs of this pair before this thread's
+    int lo = max(0, d - width), hi = min(d, width);
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (A[mid] <= B[d - mid - 1]) lo = mid + 1;
+      else hi = mid;
+    }
+    int i = lo, j = d - lo;
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+      const bool take_a = i < width && (j >= width || A[i] <= B[j]);
+      v[e] = take_a ? A[i] : B[j];
+      if (take_a) i++;
+      else j++;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < E; e++) key[t * E + e] = v[e];
+  __syncthreads();
+}
+
+// Plain shared-memory bitonic sort (every step with a barrier), for n2 < blockDim.x.
+__device__ void bitonic_sort_smem(unsigned long long* key, int n2) {
   for (int k = 2; k <= n2; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = threadIdx.x; i < n2; i += blockDim.x) {
@@ -109,6 +159,79 @@ __device__ void bitonic_sort(unsigned long long* key, int n2) {
       }
       __syncthreads();
     }
+}
+
+// key[0..n2) sorted ascending (n2 a power of two); block-wide, ends with a barrier.
+__device__ void sort_keys(unsigned long long* key, int n2) {
+  switch (n2 / int(blockDim.x)) {
+    case 1: merge_sort_reg<1>(key, n2); break;
+    case 2: merge_sort_reg<2>(key, n2); break;
+    case 4: merge_sort_reg<4>(key, n2); break;
+    case 8: merge_sort_reg<8>(key, n2); break;
+    case 16: merge_sort_reg<16>(key, n2); break;
+    default: bitonic_sort_smem(key, n2); break;
+  }
+}
+
+// Three in-place inclusive scans of n int128 values at once (the three arrays' loads
+// overlap): the blocking of block_scan (thread-contiguous segments, then warp and block
+// prefixes), exact sums, bit 0 of bs.sh_flag on overflow.  sh3: [3][33] shared scratch.
+__device__ void block_scan3(i128* a0, i128* a1, i128* a2, int n, BlockScratch& bs, i128 (*sh3)[33]) {
+  const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+  const int per = (n + T - 1) / T;
+  const int b = min(n, tid * per), e = min(n, b + per);
+  i128 s[3] = {0, 0, 0};
+  bool o = false;
+  for (int q = b; q < e; q++) {
+    const i128 x0 = a0[q], x1 = a1[q], x2 = a2[q];
+    o |= add_ovf(s[0], x0, &s[0]);
+    o |= add_ovf(s[1], x1, &s[1]);
+    o |= add_ovf(s[2], x2, &s[2]);
+  }
+  i128 incl[3] = {s[0], s[1], s[2]};
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+      const int64_t lo = __shfl_up_sync(0xffffffffu, int64_t(incl[m]), off);
+      const int64_t hi = __shfl_up_sync(0xffffffffu, int64_t(incl[m] >> 64), off);
+      const i128 other = (i128(hi) << 64) | i128(uint64_t(lo));
+      i128 r;
+      const bool ob = add_ovf(incl[m], other, &r);
+      if (lane >= off) {
+        o |= ob;
+        incl[m] = r;
+      }
+    }
+  }
+  if (lane == 31)
+    for (int m = 0; m < 3; m++) sh3[m][warp] = incl[m];
+  __syncthreads();
+  if (tid < 3) {
+    i128 t = 0;
+    bool oo = false;
+    for (int i = 0; i < nw; i++) {
+      const i128 v = sh3[tid][i];
+      sh3[tid][i] = t;
+      oo |= add_ovf(t, v, &t);
+    }
+    if (oo) atomicOr(bs.sh_flag, 1);
+  }
+  __syncthreads();
+  i128 run[3];
+#pragma unroll
+  for (int m = 0; m < 3; m++) o |= add_ovf(sh3[m][warp], incl[m] - s[m], &run[m]);  // incl - s: a partial sum
+  for (int q = b; q < e; q++) {
+    const i128 x0 = a0[q], x1 = a1[q], x2 = a2[q];
+    o |= add_ovf(run[0], x0, &run[0]);
+    o |= add_ovf(run[1], x1, &run[1]);
+    o |= add_ovf(run[2], x2, &run[2]);
+    a0[q] = run[0];
+    a1[q] = run[1];
+    a2[q] = run[2];
+  }
+  if (o) atomicOr(bs.sh_flag, 1);
+  __syncthreads();
 }
 
 // Copies a presorted magnitude row into shared memory (block-wide, ends with a barrier).
@@ -133,37 +256,60 @@ __device__ __forceinline__ int rank_sh(const uint32_t* a, int w, uint32_t tau, b
 // Message of triangle node n with the fixed input a (every input but ia, ib is a leaf),
 // for every bucket of a's edge: out[j] = x prod_l SG_l[q_l] + sum_l PRE_l[q_l], one leaf
 // at a time with the leaf's magnitudes staged in shared memory (stage: w uint32).
-__device__ void node_msg(const EstArgs& A, const TriNode& nd, int n, int a, const TriPtrs& P, int64_t ro, i128* out,
-                         uint32_t* stage, int32_t* flag) {
-  const int w = A.w;
+__device__ void node_msg(const EstArgs& A, const TriNode& nd, int n, int a, const TriPtrs& P, int64_t ro,
+                         i128* __restrict__ out, uint32_t* stage, int32_t* flag) {
+  const int w = A.w, T = blockDim.x;
   const int64_t W1 = int64_t(w) + 1;
   const EstIn* in = A.inputs + nd.in_begin;
-  const int32_t* sa = in[a].s + ro;
+  const int32_t* __restrict__ sa = in[a].s + ro;
+  i128* __restrict__ tmp = P.tmp;
   bool o = false;
-  for (int j = threadIdx.x; j < w; j += blockDim.x) {
+  for (int j = threadIdx.x; j < w; j += T) {
     out[j] = i128(__ldg(sa + j));
-    P.tmp[j] = 0;
+    tmp[j] = 0;
   }
+  constexpr int U = 2;  // buckets per thread in flight: their loads are issued together
   for (int l = 0, li = 0; l < nd.k; l++) {
     if (l == nd.ia || l == nd.ib) continue;
     __syncthreads();  // the previous leaf's readers are done with the stage
     stage_row(in[l].abs + ro, stage, w);
     const int64_t slot = (int64_t(n) * A.tri_max_leaves + li) * W1;
-    for (int j = threadIdx.x; j < w; j += blockDim.x) {
-      const int32_t x = __ldg(sa + j);
-      // leaf values that beat x: |y| < |x|, or |y| == |x| with l before a
-      const int q = rank_sh(stage, w, mag32(x), l < a);
-      i128 v = out[j], acc = P.tmp[j];
-      if (v != 0) o |= mul_ovf_64(v, P.sg[slot + q], &v);
-      o |= add_ovf(acc, P.pre[slot + q], &acc);
-      out[j] = v;
-      P.tmp[j] = acc;
+    const int64_t* __restrict__ sg = P.sg + slot;
+    const i128* __restrict__ pre = P.pre + slot;
+    const bool before = l < a;
+    for (int j0 = threadIdx.x; j0 < w; j0 += U * T) {
+      int q[U];
+      i128 v[U], acc[U], g[U], p[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int j = j0 + u * T;
+        // leaf values that beat x: |y| < |x|, or |y| == |x| with l before a
+        q[u] = j < w ? rank_sh(stage, w, mag32(__ldg(sa + j)), before) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int j = j0 + u * T;
+        v[u] = j < w ? out[j] : 0;
+        acc[u] = j < w ? tmp[j] : 0;
+        g[u] = sg[q[u]];
+        p[u] = pre[q[u]];
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int j = j0 + u * T;
+        if (j >= w) continue;
+        i128 x = v[u], y = acc[u];
+        if (x != 0) o |= mul_ovf_64(x, int64_t(g[u]), &x);
+        o |= add_ovf(y, p[u], &y);
+        out[j] = x;
+        tmp[j] = y;
+      }
     }
     li++;
   }
-  for (int j = threadIdx.x; j < w; j += blockDim.x) {
+  for (int j = threadIdx.x; j < w; j += T) {
     i128 v = out[j];
-    o |= add_ovf(v, P.tmp[j], &v);
+    o |= add_ovf(v, tmp[j], &v);
     out[j] = v;
   }
   if (o) atomicOr(flag, 1);
@@ -204,9 +350,11 @@ __device__ int block_count_base(const int32_t* at, int n, int32_t* sh_w, int32_t
 }  // namespace
 
 // One CTA per triangle row (sub-plan, sketch row) of the wave starting at tr0.
-__global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstArgs A, int64_t tr0) {
+// sep: the dynamic shared memory also holds two staged rows after the group ranks.
+__global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstArgs A, int64_t tr0, int sep) {
   extern __shared__ unsigned long long key[];
   __shared__ i128 sh_i128[33];
+  __shared__ i128 sh_scan3[3][33];
   __shared__ int32_t sh_flag[1];
   __shared__ int32_t sh_cnt[4];
   __shared__ int32_t sh_w[32];
@@ -318,7 +466,31 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
   // makes every merged entry at c through that table 0), sorted by (rR, rC, c).  The
   // clamp ranks (number of parent-sketch values that beat the conditioned value) are
   // searched in the staged parent rows, kept per c in qr / qs, then packed into keys.
-  {
+  if (sep) {  // the staged rows have their own region: the keys are written directly
+    uint32_t* stR = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(key + wp2) +
+                                                align16(sizeof(int32_t) * size_t(w + 1)));
+    uint32_t* stC = stR + wp2;
+    for (int r = tid; r < w; r += T) {
+      stR[r] = __ldg(Rpar.abs + ro + r);
+      stC[r] = __ldg(Cpar.abs + ro + r);
+    }
+    __syncthreads();
+    int cnt = 0;
+    for (int c = tid; c < wp2; c += T) {
+      unsigned long long kk = ~0ull;
+      if (c < w) {
+        const int32_t sr = __ldg(Rcond.s + ro + c), sc = __ldg(Ccond.s + ro + c);
+        if (sr != 0 && sc != 0) {
+          const unsigned long long qr = unsigned(rank_sh(stR, w, mag32(sr), tieR));
+          const unsigned long long qs = unsigned(rank_sh(stC, w, mag32(sc), tieC));
+          kk = (qr << 42) | (qs << 21) | static_cast<unsigned long long>(c);
+          cnt++;
+        }
+      }
+      key[c] = kk;
+    }
+    if (cnt) atomicAdd(&sh_cnt[2], cnt);
+  } else {
     uint32_t* stR = stage;
     uint32_t* stC = stage + wp2;
     for (int r = tid; r < w; r += T) {
@@ -345,7 +517,7 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
     }
   }
   __syncthreads();
-  bitonic_sort(key, wp2);
+  sort_keys(key, wp2);
   const int nq = sh_cnt[2];
   {
     bool o = false;
@@ -365,7 +537,7 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
     if (tid == 0) P.qpre[0] = P.qpre[W1] = P.qpre[2 * W1] = 0;
   }
   __syncthreads();
-  for (int m = 0; m < 3; m++) block_scan(P.qpre + m * W1 + 1, nq, /*reverse=*/false, bs);
+  block_scan3(P.qpre + 1, P.qpre + W1 + 1, P.qpre + 2 * W1 + 1, nq, bs, sh_scan3);
   // groups: first query of each distinct row-side rank (flags staged in gqb)
   for (int q = tid; q < nq; q += T) P.gqb[q] = (q == 0 || P.qr[q] != P.qr[q - 1]) ? 1 : 0;
   __syncthreads();
@@ -407,7 +579,7 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
     key[u] = kk;
   }
   __syncthreads();
-  bitonic_sort(key, wp2);
+  sort_keys(key, wp2);
   {
     bool o = false;
     for (int q = tid; q < w; q += T) {
@@ -426,7 +598,7 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
     if (tid == 0) P.rpre[0] = P.rpre[W1] = P.rpre[2 * W1] = 0;
   }
   __syncthreads();
-  for (int m = 0; m < 3; m++) block_scan(P.rpre + m * W1 + 1, w, /*reverse=*/false, bs);
+  block_scan3(P.rpre + 1, P.rpre + W1 + 1, P.rpre + 2 * W1 + 1, w, bs, sh_scan3);
   // ---- columns of the column side, in its presorted order
   for (int v = tid; v < w; v += T) {
     const int i = __ldg(Cpar.perm + ro + v);
@@ -567,8 +739,11 @@ cudaError_t launch_estimate_tri(const EstArgs& a, cudaStream_t st) {
   const int64_t rows = a.n_tri * a.d;
   int wp2 = 1;
   while (wp2 < a.w) wp2 <<= 1;
-  // sort keys (also two staged magnitude rows before the sorts), then the group ranks
-  const int smem = int(sizeof(unsigned long long)) * wp2 + int(sizeof(int32_t)) * (a.w + 1);
+  // sort keys (also two staged magnitude rows before the sorts), then the group ranks, and
+  // two staged rows of their own when that fits
+  const int smem0 = int(sizeof(unsigned long long)) * wp2 + int(align16(sizeof(int32_t) * size_t(a.w + 1)));
+  const int sep = size_t(smem0) + 2 * sizeof(uint32_t) * size_t(wp2) <= smem_optin_bytes() - 4096 ? 1 : 0;
+  const int smem = smem0 + (sep ? int(2 * sizeof(uint32_t)) * wp2 : 0);
   cudaError_t e = cudaFuncSetAttribute(k_tri_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const bool staged = tri_sweep_smem(a.w) <= kTriSweepSmemMax;
@@ -579,7 +754,7 @@ cudaError_t launch_estimate_tri(const EstArgs& a, cudaStream_t st) {
   }
   for (int64_t r0 = 0; r0 < rows; r0 += a.tri_slots) {
     const int64_t n = rows - r0 < a.tri_slots ? rows - r0 : a.tri_slots;
-    k_tri_prep<<<unsigned(n), 1024, smem, st>>>(a, r0);
+    k_tri_prep<<<unsigned(n), 1024, smem, st>>>(a, r0, sep);
     if (staged)
       k_tri_sweep<true><<<unsigned(n * a.tri_nch), kTriCols, size_t(tri_sweep_smem(a.w)), st>>>(a, r0);
     else

@@ -157,14 +157,17 @@ struct DevTable {
 // linear and the int32 counters wrap exactly, so count * xi(key) added once per entry
 // gives the counters of one update per tuple.  Keys are counted in a dense array indexed
 // by key - min; a column whose key range exceeds the array (cap) at run time keeps the
-// per-row path.  Workspace: [n_agg] x (max, min) encoded as uint64 pairs (256-aligned),
-// then each column's int32 count array at byte offset `off`.
+// per-row path.  Workspace: [n_agg] x (max, min) encoded as uint64 pairs followed by the
+// chunk counters of the counting and hashing passes (two uint64; all zeroed before each
+// build, 256-aligned area), then each column's int32 count array at byte offset `off`.
 struct AggCol {
   int32_t table, col;
   int64_t cap;  // count slots
   int64_t off;  // byte offset of the count array in the workspace
   int32_t stat_cta0, stat_ncta;  // CTAs of the key-range pass reading this column
+  int64_t hash_chunk0;  // first chunk of this column in the hashing pass (kHashChunk slots each)
 };
+constexpr int64_t kHashChunk = 16384;
 
 // Order-preserving maps of an int64 to uint64, for atomicMax on the stats pairs (both
 // zero-initialised: an empty column decodes as max < min).
@@ -187,20 +190,22 @@ __device__ __forceinline__ bool agg_active(const AggCol& a, int ai, const unsign
   return true;
 }
 
-// One (table, slab of (sketch,row) pairs) handled by n_ctas consecutive CTAs.
-// Row items walk tiles of the table's rows; aggregated items (agg >= 0) walk chunks of one
-// aggregated column's count array and hash that column's pairs of the slab.
+// One (table, slab of (sketch,row) pairs) handled by n_ctas consecutive CTAs walking tiles
+// of the table's rows (aggregated key columns are hashed by k_agg_hash instead).
 struct BuildItem {
   int32_t table;
   int32_t pair_begin, pair_end;
   int32_t n_ctas;
   int32_t first_cta;
-  int32_t agg;  // AggCol index, or -1
+  int32_t pad;
 };
 
-// Counting pass of key aggregation: n_ctas CTAs walk the tiles of one table.
+// Counting pass of key aggregation: the rows of one table as chunks [chunk_begin,
+// chunk_begin + n_chunks) of the pass's global chunk sequence (4 tiles each), handed out to
+// the persistent CTAs in order by an atomic counter.
 struct CountItem {
-  int32_t table, n_ctas, first_cta, pad;
+  int32_t table, pad;
+  int64_t chunk_begin, n_chunks;
 };
 
 struct BuildShape {
@@ -231,7 +236,11 @@ struct BuildArgs {
   int32_t n_agg;
   unsigned char* ws;
   const CountItem* cnt_items;
-  const int32_t* cnt_cta_item;
+  int32_t n_cnt_items;
+  int32_t cnt_cache_slots, cnt_cache_cols;  // counting pass: hot-key cache slots per column, columns cached
+  int64_t cnt_total_chunks;
+  int64_t hash_total_chunks;  // hashing pass of the aggregated columns
+  int32_t hash_max_pairs;     // most (sketch, row) pairs on one aggregated column
 };
 
 // Plan blob (host-encoded, device-read) for the batched build.
@@ -242,11 +251,14 @@ struct BuildPlanHdr {
   int64_t off_tables, off_items, off_cta_item, off_zero, n_zero;  // byte offsets in the blob
   int64_t total_bytes;
   int64_t n_agg, off_agg;                            // aggregated key columns
-  int64_t n_cnt_items, off_cnt_items, off_cnt_cta;  // counting pass
+  int64_t n_cnt_items, off_cnt_items, cnt_total_chunks;  // counting pass
   int32_t cnt_grid, stat_grid;
   int64_t ws_bytes;
+  int32_t cnt_cache_slots, cnt_cache_cols;
+  int64_t hash_total_chunks;
+  int32_t hash_max_pairs, hash_grid;
 };
-constexpr int32_t kBuildPlanVersion = 3;
+constexpr int32_t kBuildPlanVersion = 6;
 struct ZeroSpan {
   void* ptr;
   int64_t bytes;
@@ -263,9 +275,10 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 // launchers implemented in the .cu files
 size_t build_smem_bytes(const BuildShape& s, int w);
 cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t st);
-size_t agg_count_smem_bytes(const BuildShape& s);
+size_t agg_count_smem_bytes(const BuildShape& s, int32_t cache_slots, int32_t cache_cols);
 cudaError_t launch_agg(const BuildArgs& a, const BuildShape& s, int32_t stat_grid, int32_t cnt_grid, cudaStream_t st);
 cudaError_t launch_zero_spans(const ZeroSpan* spans_dev, int32_t n, cudaStream_t st);
+cudaError_t launch_agg_hash(const BuildArgs& a, int32_t grid, cudaStream_t st);
 
 int sm_count();
 size_t smem_optin_bytes();
