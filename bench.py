@@ -541,8 +541,8 @@ def run_ours(a):
     n_est = len(masks)
 
     # roofline of the dominant phase: the batched build (zero spans, key range, clearing,
-    # counting, build kernel; ~60% of the step), integer ALU bound on the hash evaluations
-    # it must do, with its HBM fraction beside it
+    # counting, row build kernel, hashing of the aggregated columns; ~60% of the step),
+    # integer ALU bound on the hash evaluations it must do, with its HBM fraction beside it
     surv = dw.survivors.cpu().numpy()
     updates = int(sum(int(surv[i]) * len(t.key_col) * wl.d for i, t in enumerate(wl.tables)))
     cw_evals, distinct = build_work(wl, dw, dedupe=bool(tuned_build["cfg"].get("dedupe", 1)))
@@ -552,7 +552,7 @@ def run_ours(a):
     ach = cw_evals * CW_INSTR / build_s
     roof = {"bound": "alu", "achieved": ach / 1e12, "peak": INT_ISSUE_PEAK / 1e12, "unit": "Tinstr/s",
             "frac": ach / INT_ISSUE_PEAK, "traffic": _kernel_traffic("build_phase"),
-            "kernel": "batched build: k_zero_spans, k_agg_stats, k_agg_zero, k_agg_count, k_sketch_build",
+            "kernel": "batched build: k_zero_spans, k_agg_stats, k_agg_zero, k_agg_count, k_sketch_build, k_agg_hash",
             "algorithmic": f"{cw_evals} CW evaluations x {CW_INSTR} int32 instr (one per distinct surviving key "
                            f"and sketch row on aggregated columns, one per surviving tuple and sketch row elsewhere; "
                            f"{updates} tuple updates)",

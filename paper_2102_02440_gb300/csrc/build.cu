@@ -358,6 +358,29 @@ __global__ void __launch_bounds__(kStatThreads) k_agg_stats(const __grid_constan
   const int64_t per = ((n + ac.stat_ncta - 1) / ac.stat_ncta + 15) & ~int64_t(15);  // rows per CTA, x16
   const int64_t r_begin = min(n, per * (int64_t(blockIdx.x) - ac.stat_cta0)), r_end = min(n, r_begin + per);
   int64_t mn = INT64_MAX, mx = INT64_MIN;
+  if (dt == CMP_I32 && vec) {  // int32 keys: 32-bit min / max, four 16-byte loads in flight
+    int32_t mn32 = INT32_MAX, mx32 = INT32_MIN;
+    const int32_t* p = reinterpret_cast<const int32_t*>(base);
+    int64_t r = r_begin + 16 * int64_t(threadIdx.x);
+    for (; r + 16 <= r_end; r += 16 * int64_t(blockDim.x)) {
+      int4 q[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) q[u] = __ldg(reinterpret_cast<const int4*>(p + r) + u);
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        mn32 = min(mn32, min(min(q[u].x, q[u].y), min(q[u].z, q[u].w)));
+        mx32 = max(mx32, max(max(q[u].x, q[u].y), max(q[u].z, q[u].w)));
+      }
+    }
+    if (r < r_end)  // the slice's last partial group of 16 rows (at most one per thread)
+      for (int64_t q = r; q < r_end; q++) {
+        const int32_t x = __ldg(p + q);
+        mn32 = min(mn32, x);
+        mx32 = max(mx32, x);
+      }
+    mn = mn32;
+    mx = mx32;
+  } else
   for (int64_t r = r_begin + 16 * int64_t(threadIdx.x); r < r_end; r += 16 * int64_t(blockDim.x)) {
     int64_t v[4][4];
 #pragma unroll

@@ -614,15 +614,15 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
   }
 }
 
-// Shared memory of the staged sweep: row keys [w] u64, column ranks [w], group ranks and
-// group starts [w + 1] each.
-__host__ __device__ inline int64_t tri_sweep_smem(int32_t w) { return 8 * int64_t(w) + 4 * (3 * int64_t(w) + 2); }
-constexpr int64_t kTriSweepSmemMax = 100 * 1024;  // staged when two CTAs per SM still fit
+// Shared memory of the staged sweep: row keys [w] u64, group ranks and group starts [w + 1]
+// each (the queries' column ranks stay in global memory).
+__host__ __device__ inline int64_t tri_sweep_smem(int32_t w) { return 8 * int64_t(w) + 4 * (2 * int64_t(w) + 2); }
+constexpr int64_t kTriSweepSmemMax = 72 * 1024;  // staged when three CTAs per SM still fit
 
 // One thread per column; kTriCols columns per CTA, tri_nch CTAs per triangle row.  STAGED:
 // the arrays the binary searches read are first copied to shared memory.
 template <bool STAGED>
-__global__ void __launch_bounds__(kTriCols) k_tri_sweep(const __grid_constant__ EstArgs A, int64_t tr0) {
+__global__ void __launch_bounds__(kTriCols, 3) k_tri_sweep(const __grid_constant__ EstArgs A, int64_t tr0) {
   extern __shared__ __align__(16) unsigned char sweep_smem[];
   __shared__ i128 sh_i128[33];
   __shared__ int32_t sh_flag[1];
@@ -639,17 +639,14 @@ __global__ void __launch_bounds__(kTriCols) k_tri_sweep(const __grid_constant__ 
   const int prep_ovf = P.hdr[2];
   if (STAGED) {
     uint64_t* s_rkx = reinterpret_cast<uint64_t*>(sweep_smem);
-    int32_t* s_qs = reinterpret_cast<int32_t*>(s_rkx + w);
-    int32_t* s_gr = s_qs + w;
+    int32_t* s_gr = reinterpret_cast<int32_t*>(s_rkx + w);
     int32_t* s_gqb = s_gr + (w + 1);
     for (int r = tid; r < w; r += kTriCols) s_rkx[r] = P.rkx[r];
-    for (int q = tid; q < nq; q += kTriCols) s_qs[q] = P.qs[q];
     for (int g = tid; g <= G; g += kTriCols) {
       if (g < G) s_gr[g] = P.gr[g];
       s_gqb[g] = P.gqb[g];
     }
     P.rkx = s_rkx;
-    P.qs = s_qs;
     P.gr = s_gr;
     P.gqb = s_gqb;
   }
