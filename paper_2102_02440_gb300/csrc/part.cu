@@ -47,6 +47,7 @@ struct PartStep {
   int32_t w, d;
   int32_t vec;     // int32 x and v, w, x_rs, v_rs multiples of 4 and 16-byte aligned rows
   uint32_t* oor;   // [d] out-of-range flags
+  int32_t* status; // device status word (a bounded wait that ran out)
 };
 
 namespace {
@@ -339,11 +340,152 @@ __global__ void __launch_bounds__(kContractThreads) k_part_col(const __grid_cons
   }
 }
 
+// ---- B == 1 with int32 rows streamed through shared memory by the bulk-copy engine.
+// Each warp owns a contiguous run of outputs (rows of x) and a ring of kBulkStages
+// buffers of kBulkChunk bytes: lane 0 starts the asynchronous copy of each chunk
+// (cp.async.bulk, completion counted in bytes on the buffer's mbarrier), the warp waits for
+// the chunk, multiplies it with the message (read through L1) and lets lane 0 refill the
+// buffer with the chunk kBulkStages ahead.  Every wait is bounded: when one runs out the
+// warp records CMP_ETIMEOUT, waits (bounded) for its copies still in flight and returns.
+constexpr int kBulkWarps = 16;
+constexpr int kBulkStages = 3;
+constexpr int kBulkChunk = 4096;  // bytes: 1024 int32
+constexpr int64_t kBulkSmem = int64_t(kBulkWarps) * kBulkStages * kBulkChunk + kBulkWarps * kBulkStages * 8;
+constexpr uint32_t kBulkWaitLimit = 1u << 22;  // try_wait polls per chunk before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// every lane polls; true once every lane has seen the phase complete
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity) {
+  bool done = false;
+  for (uint32_t it = 0; it < kBulkWaitLimit && !done; it++) done = mbar_try_wait(bar, parity);
+  return __all_sync(0xffffffffu, done);
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kBulkWarps * 32) k_part_dot_bulk(const __grid_constant__ PartStep S) {
+  extern __shared__ __align__(128) unsigned char bulk_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* buf = bulk_smem + size_t(warp) * kBulkStages * kBulkChunk;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(bulk_smem + size_t(kBulkWarps) * kBulkStages * kBulkChunk) +
+                  warp * kBulkStages;
+  if (lane == 0) {
+    for (int st = 0; st < kBulkStages; st++) mbar_init(bar + st, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const int64_t total = int64_t(S.d) * S.A;
+  const int64_t W = int64_t(gridDim.x) * kBulkWarps;
+  const int64_t per = (total + W - 1) / W;
+  const int64_t it0 = min(total, (int64_t(blockIdx.x) * kBulkWarps + warp) * per), it1 = min(total, it0 + per);
+  const int64_t row_bytes = int64_t(S.w) * 4;  // a multiple of 16 (vec)
+  const int64_t nch = (row_bytes + kBulkChunk - 1) / kBulkChunk;
+  const int64_t K = (it1 - it0) * nch;
+  const int32_t* X = static_cast<const int32_t*>(S.x);
+  const int32_t* V = static_cast<const int32_t*>(S.v);
+  auto chunk_bytes = [&](int64_t c) { return uint32_t(min(int64_t(kBulkChunk), row_bytes - c * kBulkChunk)); };
+  // Positions are advanced incrementally (no 64-bit divisions per chunk): the issue cursor
+  // (lane 0) runs kBulkStages chunks ahead of the consume cursor.
+  struct Cursor {
+    int64_t i, a, c;  // sketch row, output within it, chunk within the output's row
+  };
+  auto advance = [&](Cursor& u) {
+    if (++u.c == nch) {
+      u.c = 0;
+      if (++u.a == S.A) {
+        u.a = 0;
+        u.i++;
+      }
+    }
+  };
+  const Cursor start{it0 / S.A, it0 % S.A, 0};
+  Cursor iss = start;
+  auto issue = [&](int64_t k) {  // lane 0: chunk k (at the issue cursor) into buffer k % kBulkStages
+    const int32_t* src = X + iss.i * S.x_rs + iss.a * S.w + iss.c * (kBulkChunk / 4);
+    const int st = int(k % kBulkStages);
+    const uint32_t bytes = chunk_bytes(iss.c);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the generic reads of the buffer
+    mbar_expect_tx(bar + st, bytes);
+    bulk_copy_g2s(buf + size_t(st) * kBulkChunk, src, bytes, bar + st);
+    advance(iss);
+  };
+  if (lane == 0)
+    for (int64_t k = 0; k < min(K, int64_t(kBulkStages)); k++) issue(k);
+  // |product| <= 2^62 and w <= 2^20 terms: the int128 sum cannot wrap
+  i128 s0 = 0, s1 = 0;
+  Cursor cur = start;
+  int st = 0;
+  uint32_t parity = 0;
+  for (int64_t k = 0; k < K; k++) {
+    if (!mbar_wait_warp(bar + st, parity)) {
+      if (lane == 0) set_status(S.status, CMP_ETIMEOUT);
+      for (int64_t kk = k; kk < min(K, k + kBulkStages); kk++)  // copies still in flight
+        mbar_wait_warp(bar + int(kk % kBulkStages), uint32_t((kk / kBulkStages) & 1));
+      return;
+    }
+    const int n4 = int(chunk_bytes(cur.c) / 16);
+    const int4* xs = reinterpret_cast<const int4*>(buf + size_t(st) * kBulkChunk);
+    const int4* vs = reinterpret_cast<const int4*>(V + cur.i * S.v_rs + cur.c * (kBulkChunk / 4));
+    for (int j = lane; j < n4; j += 32) {
+      const int4 p = xs[j], q = __ldg(vs + j);
+      s0 += i128(int64_t(p.x) * q.x) + i128(int64_t(p.y) * q.y);
+      s1 += i128(int64_t(p.z) * q.z) + i128(int64_t(p.w) * q.w);
+    }
+    __syncwarp();  // every lane is done with the buffer
+    if (lane == 0 && k + kBulkStages < K) issue(k + kBulkStages);
+    if (cur.c == nch - 1) {  // the output's row is complete
+      Acc acc{s0 + s1, 0, 0, 0};
+      acc = warp_sum(acc);
+      if (lane == 0) S.y[cur.i * S.A + cur.a] = acc.s;  // B == 1
+      s0 = s1 = 0;
+    }
+    advance(cur);
+    if (++st == kBulkStages) {
+      st = 0;
+      parity ^= 1u;
+    }
+  }
+}
+
 template <typename TX, typename TV>
 cudaError_t launch_step_t(const PartStep& S, int sms, cudaStream_t st) {
   if (S.B == 1) {
     const int64_t items = int64_t(S.d) * S.A;
-    if (items >= int64_t(2) * sms * 8 || S.w < 1024) {
+    if (std::is_same<TX, int32_t>::value && std::is_same<TV, int32_t>::value && S.vec && S.w >= 1024 &&
+        items >= int64_t(sms) * kBulkWarps) {  // long int32 rows, enough of them: stream them in bulk
+      cudaError_t e = cudaFuncSetAttribute(k_part_dot_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBulkSmem));
+      if (e != cudaSuccess) return e;
+      const int64_t grid = std::min<int64_t>((items + kBulkWarps - 1) / kBulkWarps, int64_t(sms));
+      k_part_dot_bulk<<<unsigned(grid), kBulkWarps * 32, size_t(kBulkSmem), st>>>(S);
+    } else if (items >= int64_t(2) * sms * 8 || S.w < 1024) {
       const int64_t grid = std::min<int64_t>((items + 7) / 8, int64_t(sms) * 8);
       k_part_dot<TX, TV, 32><<<unsigned(grid), kContractThreads, 0, st>>>(S);
     } else {
@@ -654,6 +796,7 @@ cmp_status cmp_part_estimate(const cmp_part_join* join, int32_t d, void* ws_dev,
     S.w = s.w;
     S.d = d;
     S.oor = oor;
+    S.status = status_dev;
     const bool xw = s.x.table < 0, vw = s.v.table < 0;
     S.vec = !xw && !vw && s.w % 4 == 0 && s.x.rs % 4 == 0 && s.v.rs % 4 == 0 &&
             (reinterpret_cast<uintptr_t>(S.x) & 15) == 0 && (reinterpret_cast<uintptr_t>(S.v) & 15) == 0;

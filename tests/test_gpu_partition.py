@@ -209,6 +209,18 @@ def test_contraction_forms(part, shape):
     assert not any(oor)
 
 
+@pytest.mark.parametrize("rows,w,d", [(1300, 1500, 2), (2500, 1024, 1), (1220, 4100, 2)])
+def test_bulk_streamed_rows(part, rows, w, d):
+    """Long int32 rows of the middle table streamed through shared memory by bulk copies
+    (at least 16 rows per SM): row lengths that are and are not whole 4096-byte chunks, and
+    output counts that do not divide evenly among the warps."""
+    rng = np.random.default_rng(rows + w)
+    eu, ev, widths, axes = [0, 1], [1, 2], [rows, w], [[0], [0, 1], [1]]
+    tensors = [rng.integers(-2 ** 31, 2 ** 31, size=(d, rows)), rng.integers(-2 ** 31, 2 ** 31, size=(d, rows * w)),
+               rng.integers(-2 ** 31, 2 ** 31, size=(d, w))]
+    assert not any(_check(part, eu, ev, widths, axes, tensors, d))
+
+
 def test_out_of_range_rows(part):
     """The oracle's range rule on the device: a product beyond int128 with a zero sum, a sum
     beyond int128 of in-range products, and an in-range row."""
