@@ -76,7 +76,7 @@ __host__ __device__ inline TriLayout tri_layout(int32_t w, int32_t max_leaves) {
   int64_t o = 0;
   L.hdr = o;  o += tri_al(64);
   L.vec = o;  o += tri_al(16 * 6 * int64_t(w));   // phiU psiU phiV psiV f g, bucket order
-  L.tmp = o;  o += tri_al(16 * int64_t(w));       // leaf-term sums of one node message
+  L.tmp = o;  o += tri_al(16 * 3 * int64_t(w));   // leaf-term sums of a node message, one per node
   L.sg = o;   o += tri_al(8 * nl * W1);          // leaf suffix sums
   L.pre = o;  o += tri_al(16 * nl * W1);         // leaf "attains the minimum" prefix sums
   L.rkx = o;  o += tri_al(8 * int64_t(w));       // row keys, sorted within batches

@@ -60,7 +60,7 @@ __device__ __forceinline__ uint32_t mag32(int32_t v) { return v < 0 ? uint32_t(-
 struct TriPtrs {
   int32_t* hdr;  // [0] groups G, [1] queries, [2] overflow in the preparation
   i128* vec;     // [6][w]: phiU psiU phiV psiV f g, in bucket order
-  i128* tmp;     // [w]
+  i128* tmp;     // [3][w]: per node
   int64_t* sg;   // [3 * max_leaves][w+1]
   i128* pre;     // [3 * max_leaves][w+1]
   uint64_t* rkx;
@@ -257,12 +257,11 @@ __device__ __forceinline__ int rank_sh(const uint32_t* a, int w, uint32_t tau, b
 // for every bucket of a's edge: out[j] = x prod_l SG_l[q_l] + sum_l PRE_l[q_l], one leaf
 // at a time with the leaf's magnitudes staged in shared memory (stage: w uint32).
 __device__ void node_msg(const EstArgs& A, const TriNode& nd, int n, int a, const TriPtrs& P, int64_t ro,
-                         i128* __restrict__ out, uint32_t* stage, int32_t* flag) {
+                         i128* __restrict__ out, i128* __restrict__ tmp, uint32_t* stage, int32_t* flag) {
   const int w = A.w, T = blockDim.x;
   const int64_t W1 = int64_t(w) + 1;
   const EstIn* in = A.inputs + nd.in_begin;
   const int32_t* __restrict__ sa = in[a].s + ro;
-  i128* __restrict__ tmp = P.tmp;
   bool o = false;
   for (int j = threadIdx.x; j < w; j += T) {
     out[j] = i128(__ldg(sa + j));
@@ -349,38 +348,31 @@ __device__ int block_count_base(const int32_t* at, int n, int32_t* sh_w, int32_t
 
 }  // namespace
 
-// One CTA per triangle row (sub-plan, sketch row) of the wave starting at tr0.
-// sep: the dynamic shared memory also holds two staged rows after the group ranks.
-__global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstArgs A, int64_t tr0, int sep) {
-  extern __shared__ unsigned long long key[];
+// One CTA per (triangle row of the wave starting at tr0, node n of the triangle): node n's
+// leaf suffix sums, its leaves' "attains the minimum" prefix sums and its two messages.
+// The three nodes of a row are independent, so they run on three SMs; the node's overflow
+// flag goes to hdr[3 + n] (k_tri_prep folds it into the row's flag).
+__global__ void __launch_bounds__(1024) k_tri_nodes(const __grid_constant__ EstArgs A, int64_t tr0) {
+  extern __shared__ uint32_t stage[];  // [w]: one staged magnitude row
   __shared__ i128 sh_i128[33];
-  __shared__ i128 sh_scan3[3][33];
   __shared__ int32_t sh_flag[1];
-  __shared__ int32_t sh_cnt[4];
-  __shared__ int32_t sh_w[32];
   BlockScratch bs{sh_i128, sh_flag};
   const int w = A.w, d = A.d, tid = threadIdx.x, T = blockDim.x;
-  if (w > kTriMaxW || T != 1024) {  // the planner never sends these; sorts and group starts assume them
-    if (tid == 0) set_status(A.status, CMP_EINVAL);
-    return;
-  }
   const int64_t W1 = int64_t(w) + 1;
-  const int64_t tr = tr0 + blockIdx.x;
+  const int64_t slot = blockIdx.x / 3;
+  const int n = int(blockIdx.x % 3);
+  const int64_t tr = tr0 + slot;
   const TriSub ts = A.tri[tr / d];
+  const TriNode nd = ts.node[n];
   const int64_t ro = (tr % d) * int64_t(w);
-  const TriPtrs P = tri_ptrs(A.tri_scratch + int64_t(blockIdx.x) * A.tri_row_bytes, w, A.tri_max_leaves);
+  const TriPtrs P = tri_ptrs(A.tri_scratch + slot * A.tri_row_bytes, w, A.tri_max_leaves);
+  i128* tmp = P.tmp + int64_t(n) * w;
   const EstIn* inputs = A.inputs;
-  int wp2 = 1;
-  while (wp2 < w) wp2 <<= 1;
-  if (tid == 0) {
-    sh_flag[0] = 0;
-    sh_cnt[0] = sh_cnt[1] = sh_cnt[2] = sh_cnt[3] = 0;
-  }
+  if (tid == 0) sh_flag[0] = 0;
   __syncthreads();
 
   // ---- leaves: suffix sums of each leaf's message in its sketch's sorted order
-  for (int n = 0; n < 3; n++) {
-    const TriNode nd = ts.node[n];
+  {
     for (int l = 0, li = 0; l < nd.k; l++) {
       if (l == nd.ia || l == nd.ib) continue;
       const EstIn& x = inputs[nd.in_begin + l];
@@ -395,9 +387,7 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
   }
   // ---- leaves: prefix sums of the terms in which leaf l attains the minimum: value times
   // leaf message, times every other leaf's suffix sum at that value (other leaf staged)
-  uint32_t* stage = reinterpret_cast<uint32_t*>(key);  // 2 * wp2 uint32 before the sorts use it
-  for (int n = 0; n < 3; n++) {
-    const TriNode nd = ts.node[n];
+  {
     for (int l = 0, li = 0; l < nd.k; l++) {
       if (l == nd.ia || l == nd.ib) continue;
       const EstIn& x = inputs[nd.in_begin + l];
@@ -431,12 +421,45 @@ __global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstAr
       li++;
     }
   }
-  // ---- the six node messages, in bucket order
-  for (int n = 0; n < 3; n++) {
-    const TriNode nd = ts.node[n];
-    node_msg(A, nd, n, nd.ia, P, ro, P.vec + int64_t(2 * n) * w, stage, sh_flag);
-    node_msg(A, nd, n, nd.ib, P, ro, P.vec + int64_t(2 * n + 1) * w, stage, sh_flag);
+  // ---- the node's two messages, in bucket order
+  node_msg(A, nd, n, nd.ia, P, ro, P.vec + int64_t(2 * n) * w, tmp, stage, sh_flag);
+  node_msg(A, nd, n, nd.ib, P, ro, P.vec + int64_t(2 * n + 1) * w, tmp, stage, sh_flag);
+  if (tid == 0) P.hdr[3 + n] = sh_flag[0] != 0;
+}
+
+// One CTA per triangle row (sub-plan, sketch row) of the wave starting at tr0.
+// sep: the dynamic shared memory also holds two staged rows after the group ranks.
+__global__ void __launch_bounds__(1024) k_tri_prep(const __grid_constant__ EstArgs A, int64_t tr0, int sep) {
+  extern __shared__ unsigned long long key[];
+  __shared__ i128 sh_i128[33];
+  __shared__ i128 sh_scan3[3][33];
+  __shared__ int32_t sh_flag[1];
+  __shared__ int32_t sh_cnt[4];
+  __shared__ int32_t sh_w[32];
+  BlockScratch bs{sh_i128, sh_flag};
+  const int w = A.w, d = A.d, tid = threadIdx.x, T = blockDim.x;
+  if (w > kTriMaxW || T != 1024) {  // the planner never sends these; sorts and group starts assume them
+    if (tid == 0) set_status(A.status, CMP_EINVAL);
+    return;
   }
+  const int64_t W1 = int64_t(w) + 1;
+  const int64_t tr = tr0 + blockIdx.x;
+  const TriSub ts = A.tri[tr / d];
+  const int64_t ro = (tr % d) * int64_t(w);
+  const TriPtrs P = tri_ptrs(A.tri_scratch + int64_t(blockIdx.x) * A.tri_row_bytes, w, A.tri_max_leaves);
+  const EstIn* inputs = A.inputs;
+  int wp2 = 1;
+  while (wp2 < w) wp2 <<= 1;
+  if (tid == 0) {
+    sh_flag[0] = 0;
+    sh_cnt[0] = sh_cnt[1] = sh_cnt[2] = sh_cnt[3] = 0;
+  }
+  __syncthreads();
+
+  // the node kernel's overflow flags
+  if (tid == 0 && (P.hdr[3] | P.hdr[4] | P.hdr[5])) sh_flag[0] = 1;
+  uint32_t* stage = reinterpret_cast<uint32_t*>(key);  // 2 * wp2 uint32 before the sorts use it
+  __syncthreads();
   // ---- row side: U or V, whichever conditioned sketch has fewer distinct magnitudes
   for (int n = 0; n < 2; n++) {
     const uint32_t* ab = inputs[ts.node[n].in_begin + ts.node[n].ib].abs + ro;
@@ -635,7 +658,6 @@ __global__ void __launch_bounds__(kTriCols, 3) k_tri_sweep(const __grid_constant
   TriPtrs P = tri_ptrs(A.tri_scratch + slot * A.tri_row_bytes, w, A.tri_max_leaves);
   if (tid == 0) sh_flag[0] = 0;
   const int G = P.hdr[0];
-  const int nq = P.hdr[1];
   const int prep_ovf = P.hdr[2];
   if (STAGED) {
     uint64_t* s_rkx = reinterpret_cast<uint64_t*>(sweep_smem);
@@ -743,6 +765,10 @@ cudaError_t launch_estimate_tri(const EstArgs& a, cudaStream_t st) {
   const int smem = smem0 + (sep ? int(2 * sizeof(uint32_t)) * wp2 : 0);
   cudaError_t e = cudaFuncSetAttribute(k_tri_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  if (int64_t(4) * a.w > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_tri_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * a.w);
+    if (e != cudaSuccess) return e;
+  }
   const bool staged = tri_sweep_smem(a.w) <= kTriSweepSmemMax;
   if (staged) {
     e = cudaFuncSetAttribute(k_tri_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -751,6 +777,7 @@ cudaError_t launch_estimate_tri(const EstArgs& a, cudaStream_t st) {
   }
   for (int64_t r0 = 0; r0 < rows; r0 += a.tri_slots) {
     const int64_t n = rows - r0 < a.tri_slots ? rows - r0 : a.tri_slots;
+    k_tri_nodes<<<unsigned(3 * n), 1024, size_t(4) * size_t(a.w), st>>>(a, r0);
     k_tri_prep<<<unsigned(n), 1024, smem, st>>>(a, r0, sep);
     if (staged)
       k_tri_sweep<true><<<unsigned(n * a.tri_nch), kTriCols, size_t(tri_sweep_smem(a.w)), st>>>(a, r0);
