@@ -569,7 +569,7 @@ def run_ours(a):
     roof_est = {"bound": "alu", "achieved": est_ops / est_s / 1e12, "peak": op_peak / 1e12,
                 "unit": "T int128-op/s", "frac": est_ops / est_s / op_peak,
                 "traffic": _kernel_traffic("estimate_phase"),
-                "kernel": "k_estimate_items (trees), k_tri_prep + k_tri_sweep (triangles), k_estimate_finalize",
+                "kernel": "k_estimate_items (trees), k_tri_nodes + k_tri_prep + k_tri_sweep (triangles), k_estimate_finalize",
                 "algorithmic": f"{est_ops} exact 128-bit operations ({n_tri_sub} triangle, {n_gen_sub} other sub-plans)",
                 "peak_derivation": f"152 SMs x 4 SMSP x 32 lanes x 2.07 GHz / {OP128_INSTR} int32 instr per op"}
 
@@ -605,10 +605,10 @@ def run_ours(a):
     if rank == 0 and not a.no_cpu_baseline:
         cpu = cpu_baseline(wl)
 
-    # estimate: generic int64 + int128 recompute when trees are planned, triangle preparation +
-    # sweep when triangles are, finalize
+    # estimate: generic int64 + int128 recompute when trees are planned, triangle node messages +
+    # preparation + sweep when triangles are, finalize
     est_launches = (2 if n_gen_sub > sum(1 for m in masks if bin(m).count("1") == 1) else 0) + \
-        (2 if n_tri_sub else 0) + 1
+        (3 if n_tri_sub else 0) + 1
     # build: zero spans + build kernel, plus key range, clearing, counting and hashing of the
     # aggregated key columns when the plan aggregates (it then has a workspace)
     build_launches = 2 + (4 if dw._plan[2] else 0)
