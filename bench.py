@@ -57,7 +57,7 @@ def _args():
                     help="JSON file of autotuned launch shapes: read if it has this workload's, else written")
     ap.add_argument("--case", default=None,
                     choices=["estimate_small", "estimate_full", "build_f1", "build_five", "batched", "scale",
-                             "partition", "offline_sample"],
+                             "partition", "offline_sample", "cached"],
                     help="run one small profiling case instead of the benchmark (for ncu captures)")
     return ap.parse_args()
 
@@ -1004,10 +1004,69 @@ def run_offline_sample(a):
                       "sample": sample}), flush=True)
 
 
+def run_cached(a):
+    """Cached subtree messages (CMP_EST_CACHE_MESSAGES; Sec. 4.2 (n+1)-D from n-D merges,
+    Sec. 5 cache of merged sketches) on the batched-enumeration graph set (64 chains, stars
+    and cycles of 4..17 tables, d = 11, w = 1024): the estimate of every acyclic sub-plan,
+    and of every sub-plan, with and without the cache.  Plan counts (table operations,
+    cached messages, launch levels) come from cmp_estimate_plan_stats; CUDA-event times are
+    medians of 5 after one warm-up; both plans' outputs are compared bit for bit."""
+    import torch
+
+    from paper_2102_02440_gb300 import compass as K
+    from paper_2102_02440_gb300 import datagen as G
+    from paper_2102_02440_gb300 import pipeline as P
+    graphs = G.graph_batch(64, 4, 17, rows_lo=10_000, rows_hi=1_000_000, d=11, w=1024)
+    gb = P.GraphBatch(graphs)
+    sg, sm, tree = [], [], []
+    for gi, g in enumerate(graphs):
+        for m in G.connected_subplans(len(g.tables), g.edge_u, g.edge_v):
+            ne = sum(1 for u, v in zip(g.edge_u, g.edge_v) if (m >> u) & 1 and (m >> v) & 1)
+            sg.append(gi)
+            sm.append(m)
+            tree.append(ne == bin(m).count("1") - 1)
+    sg, sm, tree = np.array(sg, np.int32), np.array(sm, np.uint64), np.array(tree)
+    gb.build_batched()
+    gb.presort()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        return statistics.median(ts)
+
+    cfg = K.cmp_estimate_cfg.make(flags=K.CMP_EST_CACHE_MESSAGES)
+    out = {}
+    for name, sel, reps in (("acyclic_subplans", tree, 5), ("all_subplans", np.ones_like(tree), 3)):
+        plain, cached = gb.plan(sg[sel], sm[sel]), gb.plan(sg[sel], sm[sel], cfg)
+        ms_p, ms_c = timed(plain.run, reps), timed(cached.run, reps)
+        torch.cuda.synchronize()
+        ip, ic = (K.cmp_estimate_plan_stats(x.host.ctypes.data) for x in (plain, cached))
+        same = bool(torch.equal(plain.row_est, cached.row_est) and
+                    torch.equal(torch.nan_to_num(plain.est, nan=-1.0), torch.nan_to_num(cached.est, nan=-1.0)))
+        out[name] = {"subplans": int(sel.sum()), "plain_ms": ms_p, "cached_ms": ms_c, "speedup": ms_p / ms_c,
+                     "plain_ops": int(ip.n_ops), "cached_ops": int(ic.n_ops), "cached_messages": int(ic.n_jobs),
+                     "levels": int(ic.n_levels), "cache_bytes": int(ic.n_jobs) * 11 * 1024 * 16,
+                     "identical": same}
+        del plain, cached
+    gb.dw.status.zero_()
+    print(json.dumps({"case": "cached messages", "graphs": len(graphs), "d": 11, "w": 1024, **out}), flush=True)
+
+
 def main():
     a = _args()
     if a.case == "batched":
         run_batched(a)
+    elif a.case == "cached":
+        run_cached(a)
     elif a.case == "scale":
         run_scale(a)
     elif a.case == "partition":

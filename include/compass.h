@@ -276,13 +276,23 @@ typedef struct {
  * three tables, are evaluated by the triangle path: the conditioned sum regrouped as
  * batched dominance sums, O(w G log w) per sketch row for G distinct clamp ranks, instead
  * of one tree contraction per conditioning value (O(w^2)).  Both give the same exact
- * integers.  It needs w <= 16384; flag CMP_EST_GENERIC_ONLY turns it off. */
+ * integers.  It needs w <= 16384; flag CMP_EST_GENERIC_ONLY turns it off.
+ * Flag CMP_EST_CACHE_MESSAGES: incremental evaluation of tree sub-plans (Sec. 4.2: an
+ * (n+1)-D merged sketch extends an n-D one; Sec. 5: merged sketches cached across the
+ * enumerated sub-plans).  Each tree sub-plan is rooted at its lowest table id; a child
+ * subtree T joined to the rest by edge e sends one message over e, the contraction of T's
+ * merged sketches with its sketch on e, which depends on (graph, e, T) alone.  Messages
+ * referenced by two or more sub-plans or larger subtrees are computed once per sketch row,
+ * level by level (smaller subtrees first), into the workspace (16 bytes per bucket and
+ * row), and every user reads them there.  The estimates and row estimates are the same
+ * exact integers as without the flag. */
 #define CMP_EST_GENERIC_ONLY 1
+#define CMP_EST_CACHE_MESSAGES 2
 typedef struct {
   int32_t threads;     /* threads per CTA (multiple of 32, <= 1024)                */
   int32_t ctas_per_sm; /* resident CTAs per SM the persistent grid is sized for    */
   int32_t cond_chunk;  /* conditioning values per work item of a cyclic sub-plan   */
-  int32_t flags;       /* 0, or CMP_EST_GENERIC_ONLY; other bits: CMP_EINVAL       */
+  int32_t flags;       /* CMP_EST_GENERIC_ONLY | CMP_EST_CACHE_MESSAGES; other bits: CMP_EINVAL */
 } cmp_estimate_cfg;
 
 cmp_status cmp_estimate_plan_bytes(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
@@ -293,6 +303,17 @@ cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, i
                                     void* plan_host, size_t plan_bytes);
 cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_dev, size_t ws_bytes, double* est_dev,
                         int64_t* row_est_dev, int32_t* status_dev, void* stream);
+
+/* Counts of an encoded estimate plan (host only, no GPU): sub-plans, work items (one per
+ * sketch row and conditioning chunk), table operations over all sub-plans and cached
+ * messages (each evaluated once per item of its owner), cached subtree messages
+ * (CMP_EST_CACHE_MESSAGES) with their items and launch levels, triangle sub-plans, and the
+ * persistent grid.  CMP_EINVAL for a NULL argument or a blob that is not an estimate plan. */
+typedef struct {
+  int64_t n_sub, n_items, n_ops, n_jobs, n_job_items, n_tri;
+  int32_t n_levels, grid;
+} cmp_estimate_plan_info;
+cmp_status cmp_estimate_plan_stats(const void* plan_host, cmp_estimate_plan_info* info);
 
 /* ------------------------------------------------------- partitioned sketches */
 /* Sketch partitioning (Sec. 4.1): the unbiased estimator of a fixed multi-way join.  A

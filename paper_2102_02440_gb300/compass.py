@@ -16,6 +16,7 @@ CMP_OK, CMP_EINVAL, CMP_EUNSUPPORTED, CMP_EOVERFLOW, CMP_ECUDA, CMP_EWORKSPACE, 
 CMP_I32, CMP_I64 = 0, 1
 CMP_RANGE, CMP_EQ, CMP_IN_BITMAP = 0, 1, 2
 CMP_EST_GENERIC_ONLY = 1
+CMP_EST_CACHE_MESSAGES = 2
 CMP_ABI_VERSION = 4
 CMP_PART_MAX_AXES = 4
 CMP_MAX_COLS, CMP_MAX_PREDS, CMP_MAX_SKETCHES, CMP_MAX_D = 32, 8, 16, 64
@@ -55,6 +56,11 @@ class cmp_build_cfg(C.Structure):
     @classmethod
     def make(cls, mode=0, pairs_per_slab=0, threads=0, tile_rows=0, dedupe=-1, ctas_per_sm=0, aggregate=-1):
         return cls(mode, pairs_per_slab, threads, tile_rows, dedupe, ctas_per_sm, aggregate, 0)
+
+
+class cmp_estimate_plan_info(C.Structure):
+    _fields_ = [("n_sub", C.c_int64), ("n_items", C.c_int64), ("n_ops", C.c_int64), ("n_jobs", C.c_int64),
+                ("n_job_items", C.c_int64), ("n_tri", C.c_int64), ("n_levels", C.c_int32), ("grid", C.c_int32)]
 
 
 class cmp_estimate_cfg(C.Structure):
@@ -128,6 +134,7 @@ _SIGS = {
                                              C.c_size_t]),
     "cmp_estimate": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]),
+    "cmp_estimate_plan_stats": (C.c_int32, [C.c_void_p, C.POINTER(cmp_estimate_plan_info)]),
     "cmp_enum_plan_bytes": (C.c_int32, [C.POINTER(cmp_graph), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                         C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "cmp_enum_plan_encode": (C.c_int32, [C.POINTER(cmp_graph), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
@@ -294,6 +301,12 @@ def cmp_estimate_plan_encode(graphs, d: int, w: int, sub_graph, sub_mask, plan_h
     _check("cmp_estimate_plan_encode",
            lib().cmp_estimate_plan_encode(g, len(graphs), d, w, sg.size, sg.ctypes.data, sm.ctypes.data,
                                           C.byref(cfg) if cfg is not None else None, plan_host, plan_bytes))
+
+
+def cmp_estimate_plan_stats(plan_host: int) -> cmp_estimate_plan_info:
+    info = cmp_estimate_plan_info()
+    _check("cmp_estimate_plan_stats", lib().cmp_estimate_plan_stats(plan_host, C.byref(info)))
+    return info
 
 
 def cmp_estimate(plan_host: int, plan_dev: int, ws_dev: int, ws_bytes: int, est_dev: int, row_est_dev: int,

@@ -3,6 +3,8 @@
 
 #include <algorithm>
 #include <cstring>
+#include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "estimate.cuh"
@@ -20,7 +22,7 @@ cmp_status est_shape(const cmp_estimate_cfg* cfg, EstShape* s) {
   s->ctas_per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : 1;
   s->cond_chunk = (cfg && cfg->cond_chunk > 0) ? cfg->cond_chunk : 64;
   s->flags = cfg ? cfg->flags : 0;
-  if (s->flags & ~int32_t(CMP_EST_GENERIC_ONLY)) return CMP_EINVAL;
+  if (s->flags & ~int32_t(CMP_EST_GENERIC_ONLY | CMP_EST_CACHE_MESSAGES)) return CMP_EINVAL;
   if (s->threads < 32 || s->threads > 1024 || s->threads % 32 || s->ctas_per_sm > 32) return CMP_EINVAL;
   return CMP_OK;
 }
@@ -148,34 +150,284 @@ bool plan_triangle(const cmp_graph& g, const std::vector<int>& es, const std::ve
   return true;
 }
 
-// Plan one sub-plan: spanning tree by BFS from the lowest table id (edges in id order),
-// non-tree edges conditioned, post-order operations for every non-leaf table.
-cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int32_t sub_index, int32_t chunk,
-                    int32_t flags, PlanOut* P) {
+// ---------------------------------------------------------------- cached subtree messages
+// With CMP_EST_CACHE_MESSAGES, every tree sub-plan is rooted at its lowest table id and
+// each non-leaf child subtree T, hanging from the root side by edge e, sends the message of
+// T over e (the merged sketches of T contracted with each other and with T's sketch on e,
+// Sec. 4.2 iterated).  The message depends on (graph, e, T) only, so one computed for a
+// smaller subtree extends to every larger sub-plan that contains it (Sec. 4.2: (n+1)-D from
+// n-D; Sec. 5: merged sketches cached).  A subtree message referenced by two or more
+// parents (sub-plans or larger subtrees) is computed once, as a job, and cached; one with a
+// single parent stays inline in that parent's operations.
+struct JobNode {
+  int32_t g, edge, root;
+  uint64_t mask;
+  int32_t refs, cid, level;
+  std::vector<int32_t> kids;  // child subtree nodes (non-leaf children of root)
+};
+struct JobKeyHash {
+  size_t operator()(const std::pair<uint64_t, uint64_t>& k) const {
+    uint64_t h = k.first * 0x9E3779B97F4A7C15ull ^ (k.second + 0x632BE59BD9B4E019ull + (k.first << 6));
+    h ^= h >> 29;
+    return size_t(h * 0xBF58476D1CE4E5B9ull);
+  }
+};
+struct CacheCtx {
+  std::unordered_map<std::pair<uint64_t, uint64_t>, int32_t, JobKeyHash> key;  // (graph<<32 | edge, mask)
+  std::vector<JobNode> nodes;
+  int32_t lookup(int32_t gi, int32_t e, uint64_t m) const {
+    const auto it = key.find({(uint64_t(uint32_t(gi)) << 32) | uint32_t(e), m});
+    return it == key.end() ? -1 : it->second;
+  }
+};
+
+inline bool touches(const cmp_graph& g, int e, int t) { return g.edge_u[e] == t || g.edge_v[e] == t; }
+inline int other_end(const cmp_graph& g, int e, int t) { return g.edge_u[e] == t ? g.edge_v[e] : g.edge_u[e]; }
+
+// Tables reachable from `start` inside `mask` without passing through `banned`.
+uint64_t component(const cmp_graph& g, uint64_t mask, int start, int banned) {
+  uint64_t seen = uint64_t(1) << start;
+  int stack[CMP_MAX_TABLES], top = 0;
+  stack[top++] = start;
+  while (top) {
+    const int t = stack[--top];
+    for (int e = 0; e < g.n_edges; e++) {
+      if (!touches(g, e, t)) continue;
+      const int o = other_end(g, e, t);
+      if (o == banned || !((mask >> o) & 1) || ((seen >> o) & 1)) continue;
+      seen |= uint64_t(1) << o;
+      stack[top++] = o;
+    }
+  }
+  return seen;
+}
+
+// The node of subtree `m` sending over edge `e` (one end in m), created with its child
+// nodes on first use.
+int32_t job_node(const cmp_graph& g, int32_t gi, int32_t e, uint64_t m, CacheCtx* C) {
+  const std::pair<uint64_t, uint64_t> k{(uint64_t(uint32_t(gi)) << 32) | uint32_t(e), m};
+  const auto it = C->key.find(k);
+  if (it != C->key.end()) return it->second;
+  const int32_t id = int32_t(C->nodes.size());
+  C->key.emplace(k, id);
+  JobNode n;
+  n.g = gi;
+  n.edge = e;
+  n.root = ((m >> g.edge_u[e]) & 1) ? g.edge_u[e] : g.edge_v[e];
+  n.mask = m;
+  n.refs = 0;
+  n.cid = -1;
+  n.level = -1;
+  C->nodes.push_back(n);
+  const int r = C->nodes[id].root;
+  for (int e2 = 0; e2 < g.n_edges; e2++) {
+    if (e2 == e || !touches(g, e2, r)) continue;
+    const int o = other_end(g, e2, r);
+    if (!((m >> o) & 1)) continue;
+    const uint64_t sub = component(g, m, o, r);
+    if (__builtin_popcountll(sub) < 2) continue;  // a leaf: its sketch is the message
+    const int32_t kid = job_node(g, gi, e2, sub, C);
+    C->nodes[kid].refs++;
+    C->nodes[id].kids.push_back(kid);
+  }
+  return id;
+}
+
+// Registers the child subtrees of a tree sub-plan (rooted at its lowest table id); other
+// sub-plans (single tables, cycles, invalid masks) register nothing.
+void analyze_sub(const cmp_graph& g, int32_t gi, uint64_t mask, CacheCtx* C) {
   const int nt = g.n_tables;
-  if (mask == 0 || (nt < 64 && (mask >> nt) != 0)) return CMP_EINVAL;
-  std::vector<int> es;
+  if (mask == 0 || (nt < 64 && (mask >> nt) != 0) || __builtin_popcountll(mask) < 2) return;
+  int n_e = 0;
   for (int e = 0; e < g.n_edges; e++)
-    if (((mask >> g.edge_u[e]) & 1) && ((mask >> g.edge_v[e]) & 1)) es.push_back(e);
+    if (((mask >> g.edge_u[e]) & 1) && ((mask >> g.edge_v[e]) & 1)) n_e++;
   int root = 0;
   while (!((mask >> root) & 1)) root++;
-  std::vector<int> order{root}, parent_edge(nt, -1);
-  std::vector<char> seen(nt, 0), tree(g.n_edges, 0);
-  seen[root] = 1;
-  for (size_t h = 0; h < order.size(); h++) {
+  if (component(g, mask, root, -1) != mask || n_e != __builtin_popcountll(mask) - 1) return;
+  for (int e = 0; e < g.n_edges; e++) {
+    if (!touches(g, e, root)) continue;
+    const int o = other_end(g, e, root);
+    if (!((mask >> o) & 1)) continue;
+    const uint64_t sub = component(g, mask, o, root);
+    if (__builtin_popcountll(sub) >= 2) C->nodes[job_node(g, gi, e, sub, C)].refs++;
+  }
+}
+
+// Launch level of a cached node: 0 if it reads no cached message, else one more than the
+// deepest cached message it reads (through its inline children).
+int32_t job_level(int32_t id, CacheCtx* C) {
+  JobNode& n = C->nodes[id];
+  if (n.level >= 0) return n.level;
+  int32_t lv = 0;
+  std::vector<int32_t> st(n.kids.begin(), n.kids.end());
+  while (!st.empty()) {
+    const int32_t k = st.back();
+    st.pop_back();
+    if (C->nodes[k].cid >= 0) lv = std::max(lv, job_level(k, C) + 1);
+    else st.insert(st.end(), C->nodes[k].kids.begin(), C->nodes[k].kids.end());
+  }
+  C->nodes[id].level = lv;
+  return lv;
+}
+
+// Post-order operations of a spanning tree (BFS order `order` from `root`, tree edges
+// marked), non-tree edges conditioned.  out_edge >= 0: the root sends over out_edge (whose
+// other end is outside the tree) into the job's cached message.  With C, children whose
+// subtree message is cached are read from the cache and their subtrees emit nothing.
+cmp_status emit_ops(const cmp_graph& g, int32_t gi, const std::vector<int>& es, const std::vector<int>& order,
+                    std::vector<int> parent_edge, const std::vector<char>& tree, int root, int out_edge,
+                    const CacheCtx* C, PlanOut* P, EstSub* sb) {
+  const int nt = g.n_tables;
+  std::vector<int> ez = es;
+  if (out_edge >= 0) {
+    ez.insert(std::lower_bound(ez.begin(), ez.end(), out_edge), out_edge);
+    parent_edge[root] = out_edge;
+  }
+  std::vector<int> deg(nt, 0);
+  for (int e : es) deg[g.edge_u[e]]++, deg[g.edge_v[e]]++;
+  auto is_leaf = [&](int t) { return t != root && deg[t] == 1; };
+  auto end_of = [&](int e, int t) { return g.edge_u[e] == t ? 0 : 1; };
+  // cached[t]: t's subtree message over its parent edge comes from the cache;
+  // hidden[t]: t lies inside such a subtree
+  std::vector<int> cached(nt, -1);
+  std::vector<char> hidden(nt, 0);
+  if (C) {
+    std::vector<uint64_t> sub(nt, 0);
+    for (size_t h = order.size(); h-- > 0;) {
+      const int t = order[h];
+      sub[t] |= uint64_t(1) << t;
+      if (t != root) sub[other_end(g, parent_edge[t], t)] |= sub[t];
+    }
+    for (size_t h = 1; h < order.size(); h++) {
+      const int t = order[h], p = other_end(g, parent_edge[t], t);
+      hidden[t] = hidden[p] || (p != root && cached[p] >= 0);
+      if (!hidden[t] && !is_leaf(t)) {
+        const int32_t id = C->lookup(gi, parent_edge[t], sub[t]);
+        if (id >= 0) cached[t] = C->nodes[id].cid;
+      }
+    }
+  }
+  sb->op_begin = int32_t(P->ops.size());
+  std::vector<int> slot_of(nt, -1);
+  std::vector<char> slot_busy;
+  int32_t n_suf = 0;
+  for (size_t h = order.size(); h-- > 0;) {
     const int t = order[h];
+    if (is_leaf(t) || hidden[t] || (t != root && cached[t] >= 0)) continue;
+    EstOp op;
+    std::memset(&op, 0, sizeof(op));
+    op.k = 0;
+    op.p = -1;
+    op.out_slot = -1;
+    op.in_begin = int32_t(P->ins.size());
+    std::vector<int> consumed;
+    for (int e : ez) {
+      if (!touches(g, e, t)) continue;
+      const int me = end_of(e, t);
+      EstIn x;
+      std::memset(&x, 0, sizeof(x));
+      x.s = g.sketch[2 * e + me];
+      x.abs = g.abs_sorted[2 * e + me];
+      x.perm = g.perm[2 * e + me];
+      x.rk = g.ranks[2 * e + me];
+      x.tslot = g.slot[2 * e + me];
+      x.suf = -1;
+      if (e == parent_edge[t]) {
+        x.kind = kInOutput;
+        op.p = op.k;
+      } else if (tree[e]) {
+        x.suf = n_suf++;
+        const int child = other_end(g, e, t);
+        if (is_leaf(child)) {
+          x.kind = kInLeaf;
+          x.msk = g.sketch[2 * e + end_of(e, child)];
+        } else if (cached[child] >= 0) {
+          x.kind = kInCache;
+          x.slot = cached[child];
+        } else {
+          x.kind = kInSlot;
+          x.slot = slot_of[child];
+          consumed.push_back(slot_of[child]);
+        }
+      } else {
+        x.kind = kInCond;
+      }
+      P->ins.push_back(x);
+      op.k++;
+    }
+    if (op.p >= 0 && t != root) {  // output slot: a free slot not read by this operation
+      int s = -1;
+      for (size_t q = 0; q < slot_busy.size(); q++)
+        if (!slot_busy[q]) {
+          s = int(q);
+          break;
+        }
+      if (s < 0) {
+        s = int(slot_busy.size());
+        slot_busy.push_back(0);
+      }
+      slot_busy[s] = 1;
+      op.out_slot = s;
+      slot_of[t] = s;
+    }
+    for (int s : consumed) slot_busy[s] = 0;
+    op.rank_off = 0;
+    P->max_slots = std::max<int32_t>(P->max_slots, int32_t(slot_busy.size()));
+    P->max_in = std::max<int32_t>(P->max_in, op.k);
+    P->ops.push_back(op);
+  }
+  P->max_suf = std::max(P->max_suf, n_suf);
+  sb->n_ops = int32_t(P->ops.size()) - sb->op_begin;
+  if (sb->n_ops > kEstMaxOps || (sb->n_ops && int32_t(P->ins.size()) - P->ops[sb->op_begin].in_begin > kEstMaxSubIn))
+    return CMP_EUNSUPPORTED;
+  return CMP_OK;
+}
+
+// BFS spanning tree of `mask` from `root` over `es` (edges in id order).
+void bfs_tree(const cmp_graph& g, const std::vector<int>& es, int root, std::vector<int>* order,
+              std::vector<int>* parent_edge, std::vector<char>* tree) {
+  const int nt = g.n_tables;
+  order->assign(1, root);
+  parent_edge->assign(nt, -1);
+  tree->assign(g.n_edges, 0);
+  std::vector<char> seen(nt, 0);
+  seen[root] = 1;
+  for (size_t h = 0; h < order->size(); h++) {
+    const int t = (*order)[h];
     for (int e : es) {
       const int o = g.edge_u[e] == t ? g.edge_v[e] : (g.edge_v[e] == t ? g.edge_u[e] : -1);
       if (o < 0 || seen[o]) continue;
       seen[o] = 1;
-      parent_edge[o] = e;
-      tree[e] = 1;
-      order.push_back(o);
+      (*parent_edge)[o] = e;
+      (*tree)[e] = 1;
+      order->push_back(o);
     }
   }
+}
+
+std::vector<int> edges_within(const cmp_graph& g, uint64_t mask) {
+  std::vector<int> es;
+  for (int e = 0; e < g.n_edges; e++)
+    if (((mask >> g.edge_u[e]) & 1) && ((mask >> g.edge_v[e]) & 1)) es.push_back(e);
+  return es;
+}
+
+// Plan one sub-plan: spanning tree by BFS from the lowest table id (edges in id order),
+// non-tree edges conditioned, post-order operations for every non-leaf table.
+cmp_status plan_sub(const cmp_graph& g, int32_t gi, uint64_t mask, int32_t d, int32_t w, int32_t sub_index,
+                    int32_t chunk, int32_t flags, const CacheCtx* C, PlanOut* P) {
+  const int nt = g.n_tables;
+  if (mask == 0 || (nt < 64 && (mask >> nt) != 0)) return CMP_EINVAL;
+  const std::vector<int> es = edges_within(g, mask);
+  int root = 0;
+  while (!((mask >> root) & 1)) root++;
+  std::vector<int> order, parent_edge;
+  std::vector<char> tree;
+  bfs_tree(g, es, root, &order, &parent_edge, &tree);
   if (int(order.size()) != __builtin_popcountll(mask)) return CMP_EINVAL;  // not connected
   EstSub sb;
   std::memset(&sb, 0, sizeof(sb));
+  sb.job = -1;
   sb.scale = 1.0;  // sampled tables: prod over the sub-plan's tables, ascending, of 1 / rate
   if (g.sample_rate)
     for (int t = 0; t < nt; t++) {
@@ -200,80 +452,9 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
     P->subs.push_back(sb);
     return CMP_OK;
   }
-  std::vector<int> deg(nt, 0);
-  for (int e : es) deg[g.edge_u[e]]++, deg[g.edge_v[e]]++;
-  auto is_leaf = [&](int t) { return t != root && deg[t] == 1; };
-  auto end_of = [&](int e, int t) { return g.edge_u[e] == t ? 0 : 1; };
-  std::vector<int> slot_of(nt, -1);
-  std::vector<char> slot_busy;
-  int32_t n_suf = 0;
-  for (size_t h = order.size(); h-- > 0;) {
-    const int t = order[h];
-    if (is_leaf(t)) continue;
-    EstOp op;
-    std::memset(&op, 0, sizeof(op));
-    op.k = 0;
-    op.p = -1;
-    op.out_slot = -1;
-    op.in_begin = int32_t(P->ins.size());
-    std::vector<int> consumed;
-    for (int e : es) {
-      if (g.edge_u[e] != t && g.edge_v[e] != t) continue;
-      const int me = end_of(e, t);
-      EstIn x;
-      std::memset(&x, 0, sizeof(x));
-      x.s = g.sketch[2 * e + me];
-      x.abs = g.abs_sorted[2 * e + me];
-      x.perm = g.perm[2 * e + me];
-      x.rk = g.ranks[2 * e + me];
-      x.tslot = g.slot[2 * e + me];
-      x.suf = -1;
-      if (e == parent_edge[t]) {
-        x.kind = kInOutput;
-        op.p = op.k;
-      } else if (tree[e]) {
-        x.suf = n_suf++;
-        const int child = g.edge_u[e] == t ? g.edge_v[e] : g.edge_u[e];
-        if (is_leaf(child)) {
-          x.kind = kInLeaf;
-          x.msk = g.sketch[2 * e + end_of(e, child)];
-        } else {
-          x.kind = kInSlot;
-          x.slot = slot_of[child];
-          consumed.push_back(slot_of[child]);
-        }
-      } else {
-        x.kind = kInCond;
-      }
-      P->ins.push_back(x);
-      op.k++;
-    }
-    if (op.p >= 0) {  // output slot: a free slot not read by this operation
-      int s = -1;
-      for (size_t q = 0; q < slot_busy.size(); q++)
-        if (!slot_busy[q]) {
-          s = int(q);
-          break;
-        }
-      if (s < 0) {
-        s = int(slot_busy.size());
-        slot_busy.push_back(0);
-      }
-      slot_busy[s] = 1;
-      op.out_slot = s;
-      slot_of[t] = s;
-    }
-    for (int s : consumed) slot_busy[s] = 0;
-    op.rank_off = 0;
-    P->max_slots = std::max<int32_t>(P->max_slots, int32_t(slot_busy.size()));
-    P->max_in = std::max<int32_t>(P->max_in, op.k);
-    P->ops.push_back(op);
-  }
-  P->max_suf = std::max(P->max_suf, n_suf);
+  const cmp_status st = emit_ops(g, gi, es, order, parent_edge, tree, root, -1, cond.empty() ? C : nullptr, P, &sb);
+  if (st != CMP_OK) return st;
   sb.cond = cond.empty() ? 0 : 1;
-  sb.n_ops = int32_t(P->ops.size()) - sb.op_begin;
-  if (sb.n_ops > kEstMaxOps || int32_t(P->ins.size()) - P->ops[sb.op_begin].in_begin > kEstMaxSubIn)
-    return CMP_EUNSUPPORTED;
   sb.n_chunks = cond.empty() ? 1 : (w + chunk - 1) / chunk;
   P->subs.push_back(sb);
   for (int i = 0; i < d; i++)
@@ -288,6 +469,54 @@ cmp_status plan_sub(const cmp_graph& g, uint64_t mask, int32_t d, int32_t w, int
   return CMP_OK;
 }
 
+// The cached jobs, level by level: one EstSub each (after the n_sub sub-plans), its
+// operations, and d items (one per sketch row) placed before every sub-plan item.
+cmp_status plan_jobs(const cmp_graph* graphs, int32_t d, int32_t n_sub, CacheCtx* C, PlanOut* P, EstPlanHdr* H,
+                     std::vector<EstItem>* job_items) {
+  std::vector<int32_t> cached;  // node ids in cid order
+  for (int32_t i = 0; i < int32_t(C->nodes.size()); i++)
+    if (C->nodes[i].cid >= 0) cached.push_back(i);
+  int32_t n_levels = 0;
+  for (int32_t id : cached) n_levels = std::max(n_levels, job_level(id, C) + 1);
+  if (n_levels > kEstMaxLevels) return CMP_EUNSUPPORTED;
+  std::vector<EstSub> jsub(cached.size());
+  for (int32_t lv = 0; lv < n_levels; lv++) {
+    for (int32_t id : cached) {
+      const JobNode& n = C->nodes[id];
+      if (n.level != lv) continue;
+      const cmp_graph& g = graphs[n.g];
+      const std::vector<int> es = edges_within(g, n.mask);
+      std::vector<int> order, parent_edge;
+      std::vector<char> tree;
+      bfs_tree(g, es, n.root, &order, &parent_edge, &tree);
+      EstSub sb;
+      std::memset(&sb, 0, sizeof(sb));
+      sb.job = n.cid;
+      sb.scale = 1.0;
+      sb.tri = -1;
+      sb.n_chunks = 1;
+      sb.item_begin = int64_t(job_items->size());
+      const cmp_status st = emit_ops(g, n.g, es, order, parent_edge, tree, n.root, n.edge, C, P, &sb);
+      if (st != CMP_OK) return st;
+      jsub[n.cid] = sb;
+      for (int i = 0; i < d; i++) {
+        EstItem it;
+        it.sub = n_sub + n.cid;
+        it.row = i;
+        it.c0 = 0;
+        it.c1 = 1;
+        job_items->push_back(it);
+      }
+    }
+    H->lvl_end[lv] = int64_t(job_items->size());
+  }
+  P->subs.insert(P->subs.end(), jsub.begin(), jsub.end());
+  H->n_jobs = int64_t(cached.size());
+  H->n_job_items = int64_t(job_items->size());
+  H->n_levels = n_levels;
+  return CMP_OK;
+}
+
 cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
                     const int32_t* sub_graph, const uint64_t* sub_mask, const cmp_estimate_cfg* cfg, PlanOut* P,
                     EstPlanHdr* H) {
@@ -297,17 +526,32 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
   if (n_sub && (!sub_graph || !sub_mask)) return CMP_EINVAL;
   for (int32_t gi = 0; gi < n_graphs; gi++)
     if (!graph_ok(graphs[gi])) return CMP_EINVAL;
-  for (int32_t q = 0; q < n_sub; q++) {
+  for (int32_t q = 0; q < n_sub; q++)
     if (sub_graph[q] < 0 || sub_graph[q] >= n_graphs) return CMP_EINVAL;
-    const cmp_status st = plan_sub(graphs[sub_graph[q]], sub_mask[q], d, w, q, shape.cond_chunk, shape.flags, P);
+  std::memset(H, 0, sizeof(*H));
+  CacheCtx cache;
+  const bool use_cache = (shape.flags & CMP_EST_CACHE_MESSAGES) != 0;
+  if (use_cache) {
+    for (int32_t q = 0; q < n_sub; q++) analyze_sub(graphs[sub_graph[q]], sub_graph[q], sub_mask[q], &cache);
+    for (int32_t i = 0, c = 0; i < int32_t(cache.nodes.size()); i++)  // referenced twice or more: cached
+      if (cache.nodes[i].refs >= 2) cache.nodes[i].cid = c++;
+  }
+  for (int32_t q = 0; q < n_sub; q++) {
+    const cmp_status st = plan_sub(graphs[sub_graph[q]], sub_graph[q], sub_mask[q], d, w, q, shape.cond_chunk,
+                                   shape.flags, use_cache ? &cache : nullptr, P);
     if (st != CMP_OK) return st;
   }
-  // triangle items after the generic ones (the generic kernel runs [0, n_gen_items))
-  const int64_t n_gen = int64_t(P->items.size());
-  for (EstSub& sb : P->subs)
-    if (sb.tri >= 0) sb.item_begin += n_gen;
+  // items: cached jobs by level, then the sub-plans' generic items, then the triangle items
+  std::vector<EstItem> job_items;
+  if (use_cache) {
+    const cmp_status st = plan_jobs(graphs, d, n_sub, &cache, P, H, &job_items);
+    if (st != CMP_OK) return st;
+  }
+  const int64_t n_job = int64_t(job_items.size());
+  const int64_t n_gen = n_job + int64_t(P->items.size());
+  for (int32_t q = 0; q < n_sub; q++) P->subs[q].item_begin += P->subs[q].tri >= 0 ? n_gen : n_job;
+  P->items.insert(P->items.begin(), job_items.begin(), job_items.end());
   P->items.insert(P->items.end(), P->tri_items.begin(), P->tri_items.end());
-  std::memset(H, 0, sizeof(*H));
   H->magic = kEstPlanMagic;
   H->version = kEstPlanVersion;
   H->d = d;
@@ -439,6 +683,22 @@ cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, i
   return CMP_OK;
 }
 
+cmp_status cmp_estimate_plan_stats(const void* plan_host, cmp_estimate_plan_info* info) {
+  if (!plan_host || !info) return CMP_EINVAL;
+  EstPlanHdr H;
+  std::memcpy(&H, plan_host, sizeof(H));
+  if (H.magic != kEstPlanMagic || H.version != kEstPlanVersion) return CMP_EINVAL;
+  info->n_sub = H.n_sub;
+  info->n_items = H.n_items;
+  info->n_ops = H.n_ops;
+  info->n_jobs = H.n_jobs;
+  info->n_job_items = H.n_job_items;
+  info->n_tri = H.n_tri;
+  info->n_levels = H.n_levels;
+  info->grid = H.grid;
+  return CMP_OK;
+}
+
 cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_dev, size_t ws_bytes, double* est_dev,
                         int64_t* row_est_dev, int32_t* status_dev, void* stream) {
   if (!plan_host || !plan_dev) return CMP_EINVAL;
@@ -449,7 +709,7 @@ cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_de
   if (ws_bytes < size_t(H.ws_bytes) || (H.ws_bytes > 0 && !ws_dev)) return CMP_EWORKSPACE;
   const EstArgs a = est_args(H, static_cast<const unsigned char*>(plan_dev), static_cast<unsigned char*>(ws_dev),
                              H.grid, H.n_tri * H.d, status_dev);
-  return launch_estimate(a, est_dev, row_est_dev, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? CMP_OK
+  return launch_estimate(a, H, est_dev, row_est_dev, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? CMP_OK
                                                                                                           : CMP_ECUDA;
 }
 

@@ -338,6 +338,11 @@ __device__ __forceinline__ const int32_t* rank_row(const EstIn& x, const EstIn& 
 //   pre   [max_in][w+1]   prefix sums of the "this edge attains the minimum" terms
 // Cross ranks between the sorted rows of a table's sketches come from the cache written
 // by cmp_cross_ranks (they depend on no message and no sub-plan).
+// Cached subtree messages (Sec. 4.2: an (n+1)-D merge extends an n-D one; Sec. 5: merged
+// sketches cached across sub-plans): a job item computes the message of one subtree over
+// its connecting edge into the workspace cache, in int128; sub-plans and larger subtrees
+// read it as a kInCache input.  Launch l runs [it0, it1) and reads messages of earlier
+// launches only.
 // A conditioned input (unit vector at c) needs no array: its threshold sum is a
 // comparison with |s[c]| and its own term is one value.  When some conditioned sketch
 // value s[c] is 0, every merged tensor entry at c through that table is 0 and c adds
@@ -349,7 +354,8 @@ constexpr int kMaxPreChunk = 256;  // conditioning values per item whose scalars
 // kIlp elements per thread have their loads issued together (memory-level parallelism);
 // MAXT is the launch bound that sets the register budget.
 template <typename S, int kIlp, int MAXT>
-__global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__ EstArgs A, int retry) {
+__global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__ EstArgs A, int retry, int64_t it0,
+                                                         int64_t it1) {
   __shared__ i128 sh_i128[33];
   __shared__ int32_t sh_flag[1];
   __shared__ i128 sh_val[kMaxIn];
@@ -373,11 +379,12 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
   S* pre = suf + int64_t(A.max_suf) * W1;
   const int tid = threadIdx.x, T = blockDim.x;
 
-  for (int64_t it = blockIdx.x; it < A.n_gen_items; it += gridDim.x) {
+  for (int64_t it = it0 + blockIdx.x; it < it1; it += gridDim.x) {
     if (retry && A.partial_ovf[it] != 2) continue;  // block-uniform
     const EstItem item = A.items[it];
     const EstSub sb = A.subs[item.sub];
     const int64_t ro = int64_t(item.row) * w;  // row offset inside every [d][w] array
+    i128* const gout = sb.job >= 0 ? A.cache + (int64_t(sb.job) * A.d + item.row) * w : nullptr;
     const int in0 = A.ops[sb.op_begin].in_begin;
     const int n_in = sb.n_ops ? A.ops[sb.op_begin + sb.n_ops - 1].in_begin + A.ops[sb.op_begin + sb.n_ops - 1].k - in0
                               : 0;
@@ -390,6 +397,9 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
     if (tid == 0) sh_flag[0] = 0;
     __syncthreads();
     if (tid == 0) {
+      // a cached input that left int128 makes this row's result leave it too
+      for (int q = 0; q < n_in; q++)
+        if (sh_in[q].kind == kInCache && A.cache_ovf[int64_t(sh_in[q].slot) * A.d + item.row]) sh_flag[0] |= 1;
       int nc = 0;
       for (int q = 0; q < n_in && nc < 2; q++)
         if (sh_in[q].kind == kInCond) sh_cond[nc++] = sh_in[q].s + ro;
@@ -486,6 +496,22 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
         // 1. suffix sums of messages arriving from non-leaf children
         for (int a = 0; a < m; a++) {
           const EstIn& x = in[a + (p >= 0 && a >= p ? 1 : 0)];
+          if (x.kind == kInCache) {
+            S* sl = suf + int64_t(x.suf) * W1;
+            const i128* gm = A.cache + (int64_t(x.slot) * A.d + item.row) * w;
+            const int32_t* perm = x.perm + ro;
+            bool so1 = false;
+            for (int r = tid; r < w; r += T) {
+              const i128 v = gm[__ldg(perm + r)];
+              so1 |= !store_fits(v, sl);
+              sl[r] = S(v);
+            }
+            if (so1) atomicOr(sh_flag, 2);
+            if (tid == 0) sl[w] = 0;
+            __syncthreads();
+            block_scan(sl, w, /*reverse=*/true, bs);
+            continue;
+          }
           if (x.kind != kInSlot) continue;
           S* sl = suf + int64_t(x.suf) * W1;
           const S* msg = slots + int64_t(x.slot) * w;
@@ -563,6 +589,7 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
           const int32_t* perm = x.perm + ro;
           const uint32_t* absa = x.abs + ro;
           const S* msg = x.kind == kInSlot ? slots + int64_t(x.slot) * w : nullptr;
+          const i128* gm = x.kind == kInCache ? A.cache + (int64_t(x.slot) * A.d + item.row) * w : nullptr;
           S* pl = pre + int64_t(a) * W1;
           bool o2 = false, so2 = false;
           for (int r0 = tid; r0 < w; r0 += kIlp * T) {
@@ -577,12 +604,13 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
 #pragma unroll
             for (int u = 0; u < kIlp; u++) {
               sv[u] = __ldg(x.s + ro + jj[u]);
-              mv[u] = msg ? int64_t(0) : int64_t(__ldg(x.msk + ro + jj[u]));
+              mv[u] = (msg || gm) ? int64_t(0) : int64_t(__ldg(x.msk + ro + jj[u]));
             }
             i128 v[kIlp];
 #pragma unroll
             for (int u = 0; u < kIlp; u++) {
               if (msg) o2 |= mul_s(i128(sv[u]), msg[jj[u]], &v[u]);
+              else if (gm) o2 |= mul_s(i128(sv[u]), gm[jj[u]], &v[u]);
               else v[u] = i128(sv[u]) * i128(mv[u]);  // |int32 * int32| < 2^62
               if (!ok[u]) v[u] = 0;
             }
@@ -639,7 +667,7 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
           const EstIn& xp = in[p];
           const int32_t* permp = xp.perm + ro;
           const uint32_t* absp = xp.abs + ro;
-          S* out = slots + int64_t(op.out_slot) * w;
+          S* out = op.out_slot >= 0 ? slots + int64_t(op.out_slot) * w : nullptr;  // else gout
           bool o3 = false, so3 = false;
           for (int r0 = tid; r0 < w; r0 += kIlp * T) {
             int jp[kIlp];
@@ -688,8 +716,12 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
             for (int u = 0; u < kIlp; u++) {
               if (!ok[u]) continue;
               o3 |= add_ovf(t[u], add[u], &t[u]);
-              so3 |= !store_fits(t[u], out);
-              out[jp[u]] = S(t[u]);
+              if (out) {
+                so3 |= !store_fits(t[u], out);
+                out[jp[u]] = S(t[u]);
+              } else {
+                gout[jp[u]] = t[u];
+              }
             }
           }
           if (o3) atomicOr(sh_flag, 1);
@@ -704,6 +736,7 @@ __global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__
       A.partial[it] = acc;
       // storage overflow: recompute with int128 storage; else arithmetic overflow is final
       A.partial_ovf[it] = (fl & 2) ? 2 : ((ovf || (fl & 1)) ? 1 : 0);
+      if (gout) A.cache_ovf[int64_t(sb.job) * A.d + item.row] = (fl & 1) ? 1 : 0;
     }
     __syncthreads();
   }
@@ -762,16 +795,27 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_estimate_finalize(const __
   est[q] = __dmul_rn(med, sb.scale);  // sampled tables: one rounded product (scale 1 is exact)
 }
 
-cudaError_t launch_estimate(const EstArgs& a, double* est, int64_t* row_est, cudaStream_t st) {
-  if (a.n_gen_items > 0) {
+cudaError_t launch_estimate(const EstArgs& a, const EstPlanHdr& H, double* est, int64_t* row_est, cudaStream_t st) {
+  // cached subtree messages, one launch per level, in int128 storage
+  int64_t lo = 0;
+  for (int l = 0; l < H.n_levels; l++) {
+    const int64_t hi = H.lvl_end[l];
+    if (a.threads > 512) k_estimate_items<i128, 1, 1024><<<a.grid, a.threads, 0, st>>>(a, 0, lo, hi);
+    else k_estimate_items<i128, 2, 512><<<a.grid, a.threads, 0, st>>>(a, 0, lo, hi);
+    lo = hi;
+  }
+  if (a.n_gen_items > a.n_job_items) {
     // int64 storage first; items whose stored values left int64 are recomputed in int128
+    const int64_t b = a.n_job_items, e = a.n_gen_items;
     if (a.threads > 512) {
-      k_estimate_items<int64_t, 2, 1024><<<a.grid, a.threads, 0, st>>>(a, 0);
-      k_estimate_items<i128, 1, 1024><<<a.grid, a.threads, 0, st>>>(a, 1);
+      k_estimate_items<int64_t, 2, 1024><<<a.grid, a.threads, 0, st>>>(a, 0, b, e);
+      k_estimate_items<i128, 1, 1024><<<a.grid, a.threads, 0, st>>>(a, 1, b, e);
     } else {
-      k_estimate_items<int64_t, 4, 512><<<a.grid, a.threads, 0, st>>>(a, 0);
-      k_estimate_items<i128, 2, 512><<<a.grid, a.threads, 0, st>>>(a, 1);
+      k_estimate_items<int64_t, 4, 512><<<a.grid, a.threads, 0, st>>>(a, 0, b, e);
+      k_estimate_items<i128, 2, 512><<<a.grid, a.threads, 0, st>>>(a, 1, b, e);
     }
+  }
+  {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -8,9 +8,10 @@ namespace cmpk {
 typedef __int128 i128;
 typedef unsigned __int128 u128;
 
-enum { kInOutput = 0, kInLeaf = 1, kInSlot = 2, kInCond = 3 };
+enum { kInOutput = 0, kInLeaf = 1, kInSlot = 2, kInCond = 3, kInCache = 4 };
 constexpr int kEstMaxOps = 64;     // operations of one sub-plan (one per non-leaf table)
 constexpr int kEstMaxSubIn = 136;  // edge inputs of one sub-plan
+constexpr int kEstMaxLevels = 64;  // launch levels of cached subtree messages
 
 // One edge of a table operation, in the table's ascending edge-id order.
 struct EstIn {
@@ -20,7 +21,7 @@ struct EstIn {
   const int32_t* msk;    // kInLeaf: the leaf neighbour's sketch on the edge, [d][w]
   const int32_t* rk;     // this table's cross ranks from this sketch: [k][d][w], indexed by the other sketch
   int32_t kind;          // kInOutput / kInLeaf / kInSlot / kInCond
-  int32_t slot;          // kInSlot: message slot written by the child's operation
+  int32_t slot;          // kInSlot: message slot written by the child's operation; kInCache: cached message
   int32_t suf;           // kInLeaf / kInSlot: suffix-sum array of the sub-plan (item-persistent)
   int32_t tslot;         // this sketch's index within its table (selects rows of another input's rk)
 };
@@ -29,7 +30,7 @@ struct EstIn {
 struct EstOp {
   int32_t k;         // number of edges (inputs incl. the output edge)
   int32_t p;         // index of the output edge among them, -1 at the root
-  int32_t out_slot;  // message slot written (p >= 0)
+  int32_t out_slot;  // message slot written (p >= 0); -1 with p >= 0: the job's cached message
   int32_t in_begin;  // first EstIn
   int32_t rank_off;  // first rank table of the op in the item's rank scratch (units of w int32)
   int32_t pad;
@@ -44,6 +45,8 @@ struct EstSub {
   int32_t cond;       // 1 if a non-tree edge is conditioned
   int32_t tri;        // index of its TriSub (triangle evaluation), else -1
   double scale;       // sampled tables: prod of 1 / rate over the sub-plan's tables, else 1
+  int32_t job;        // >= 0: a cached subtree message (its index), not a sub-plan
+  int32_t pad;
 };
 
 struct EstItem {
@@ -103,9 +106,14 @@ struct EstPlanHdr {
   int64_t n_tri, off_tri;   // triangle sub-plans
   int64_t tri_row_bytes;
   int32_t tri_max_leaves, tri_nch;  // leaves per node (scratch layout), sweep items per row
+  // cached subtree messages: jobs, their items (the first of the generic items), and the
+  // end of each level's items (level l reads the messages of levels < l only)
+  int64_t n_jobs, n_job_items;
+  int32_t n_levels, pad;
+  int64_t lvl_end[kEstMaxLevels];
 };
 constexpr uint64_t kEstPlanMagic = 0x434d504553544d54ull;  // "CMPESTMT"
-constexpr int32_t kEstPlanVersion = 3;
+constexpr int32_t kEstPlanVersion = 4;
 
 struct EstArgs {
   const EstSub* subs;
@@ -125,6 +133,9 @@ struct EstArgs {
   unsigned char* tri_scratch;  // tri_slots rows of tri_row_bytes
   int64_t tri_row_bytes, tri_slots;
   int32_t tri_max_leaves, tri_nch;
+  i128* cache;          // [n_jobs][d][w] cached subtree messages, bucket order
+  int32_t* cache_ovf;   // [n_jobs][d] 1: the message left int128
+  int64_t n_job_items;
 };
 
 // Round-to-nearest-even of (neg ? -1 : 1) * (top * 2^128 + mag) to binary64, from the
@@ -178,10 +189,15 @@ cudaError_t launch_presort_large(const int32_t* C, int64_t n_rows, int32_t w, ui
                                  void* ws, int64_t rows_per_pass, cudaStream_t st);
 int64_t presort_padded(int32_t w);
 constexpr int32_t kPresortSmemMaxW = 16384;
-// Workspace of an encoded plan: per-item partial sums and flags, `grid` per-CTA scratch
-// areas of the generic kernel, then `tri_slots` triangle rows.
+// Workspace of an encoded plan: per-item partial sums and flags, the cached subtree
+// messages and their flags, `grid` per-CTA scratch areas of the generic kernel, then
+// `tri_slots` triangle rows.
+inline size_t est_cache_bytes(const EstPlanHdr& H) {
+  return align16(sizeof(i128) * size_t(H.n_jobs) * size_t(H.d) * size_t(H.w));
+}
 inline size_t est_fixed_bytes(const EstPlanHdr& H) {
-  return align16(sizeof(i128) * size_t(H.n_items)) + align16(sizeof(int32_t) * size_t(H.n_items));
+  return align16(sizeof(i128) * size_t(H.n_items)) + align16(sizeof(int32_t) * size_t(H.n_items)) +
+         est_cache_bytes(H) + align16(sizeof(int32_t) * size_t(H.n_jobs) * size_t(H.d));
 }
 inline size_t est_ws_bytes(const EstPlanHdr& H, int64_t grid, int64_t tri_slots) {
   return est_fixed_bytes(H) + size_t(H.scratch_per_cta) * size_t(grid) + size_t(H.tri_row_bytes) * size_t(tri_slots);
@@ -194,7 +210,12 @@ inline EstArgs est_args(const EstPlanHdr& H, const unsigned char* pd, unsigned c
   a.inputs = reinterpret_cast<const EstIn*>(pd + H.off_in);
   a.items = reinterpret_cast<const EstItem*>(pd + H.off_items);
   a.partial = reinterpret_cast<i128*>(ws);
-  a.partial_ovf = reinterpret_cast<int32_t*>(ws + align16(sizeof(i128) * size_t(H.n_items)));
+  const size_t o_ovf = align16(sizeof(i128) * size_t(H.n_items));
+  const size_t o_cache = o_ovf + align16(sizeof(int32_t) * size_t(H.n_items));
+  a.partial_ovf = reinterpret_cast<int32_t*>(ws + o_ovf);
+  a.cache = reinterpret_cast<i128*>(ws + o_cache);
+  a.cache_ovf = reinterpret_cast<int32_t*>(ws + o_cache + est_cache_bytes(H));
+  a.n_job_items = H.n_job_items;
   a.scratch = ws + est_fixed_bytes(H);
   a.scratch_per_cta = H.scratch_per_cta;
   a.n_items = H.n_items;
@@ -219,7 +240,7 @@ inline EstArgs est_args(const EstPlanHdr& H, const unsigned char* pd, unsigned c
   return a;
 }
 
-cudaError_t launch_estimate(const EstArgs& a, double* est, int64_t* row_est, cudaStream_t st);
+cudaError_t launch_estimate(const EstArgs& a, const EstPlanHdr& H, double* est, int64_t* row_est, cudaStream_t st);
 cudaError_t launch_estimate_tri(const EstArgs& a, cudaStream_t st);
 cudaError_t launch_cross_ranks(const uint32_t* abs, const int32_t* perm, int32_t k, int32_t d, int32_t w,
                                const int32_t* edge_id, int32_t* ranks, cudaStream_t st);

@@ -60,6 +60,6 @@ extern "C" cmp_status cmp_estimate_noalloc(const void* plan_host, const void* pl
   if (st != CMP_OK) return st;
   const EstArgs a = est_args(H, static_cast<const unsigned char*>(plan_dev), static_cast<unsigned char*>(ws_v),
                              int32_t(grid > 0 ? grid : 1), slots, status_dev);
-  return launch_estimate(a, est_dev, row_est_dev, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? CMP_OK
+  return launch_estimate(a, H, est_dev, row_est_dev, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? CMP_OK
                                                                                                           : CMP_ECUDA;
 }

@@ -192,8 +192,68 @@ def test_estimate_plan_triangle_path_host_logic(K):
     assert (K.cmp_estimate_plan_bytes([c4], 5, 64, [0], [0b1111])[1] ==
             K.cmp_estimate_plan_bytes([c4], 5, 64, [0], [0b1111], gen)[1])
     with pytest.raises(K.CompassError) as ei:
-        K.cmp_estimate_plan_bytes([g], 11, 64, [0], [0b111], K.cmp_estimate_cfg.make(flags=2))
+        K.cmp_estimate_plan_bytes([g], 11, 64, [0], [0b111], K.cmp_estimate_cfg.make(flags=4))
     assert ei.value.status == K.CMP_EINVAL
+
+
+def _plan_stats(K, graphs, d, w, sg, sm, flags=0):
+    cfg = K.cmp_estimate_cfg.make(flags=flags)
+    pb, wb = K.cmp_estimate_plan_bytes(graphs, d, w, sg, sm, cfg)
+    buf = np.zeros(pb, np.uint8)
+    K.cmp_estimate_plan_encode(graphs, d, w, sg, sm, buf.ctypes.data, pb, cfg)
+    return K.cmp_estimate_plan_stats(buf.ctypes.data), wb
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 9, 17])
+def test_estimate_plan_cached_messages_on_chains(K, n):
+    """Cached subtree messages on the chain 0-1-...-(n-1) with every connected sub-plan.
+    Each sub-path [i..j] is rooted at i and its child subtree is [i+1..j] over edge i.  The
+    message of [a..j] (a >= 2, j > a) has two users, the sub-plan [a-1..j] and the message of
+    [a-1..j], so (n-2)(n-3)/2 messages are cached, at levels j - a - 1 (n - 3 launches).  The
+    operations fall from sum_L (n-L+1)(L-1) (every non-leaf table of every sub-plan) to one per
+    sub-plan and cached message, plus one for each sub-plan [0..j] with j >= 2 (its child
+    [1..j] has a single user and stays inline)."""
+    from paper_2102_02440_gb300 import datagen as G
+    g = _graph(K, list(range(n - 1)), list(range(1, n)), n)
+    sm = G.connected_subplans(n, list(range(n - 1)), list(range(1, n)))
+    sg = [0] * len(sm)
+    d = 5
+    plain, wb0 = _plan_stats(K, [g], d, 64, sg, sm)
+    cached, wb1 = _plan_stats(K, [g], d, 64, sg, sm, K.CMP_EST_CACHE_MESSAGES)
+    n_jobs = (n - 2) * (n - 3) // 2 if n >= 3 else 0
+    assert plain.n_jobs == 0 and plain.n_levels == 0
+    assert plain.n_ops == sum((n - L + 1) * (L - 1) for L in range(2, n + 1))
+    assert cached.n_jobs == n_jobs and cached.n_job_items == n_jobs * d
+    assert cached.n_levels == max(n - 3, 0)
+    n_sub_multi = n * (n - 1) // 2
+    assert cached.n_ops == n_sub_multi + max(n - 2, 0) + n_jobs
+    assert cached.n_items == plain.n_items + n_jobs * d and cached.n_sub == plain.n_sub == len(sm)
+    assert wb1 >= 16 * n_jobs * d * 64   # the cache: 16 bytes per bucket and row of every cached message
+
+
+def test_estimate_plan_cached_messages_shapes(K):
+    """Stars rooted at their centre cache nothing (every child is a leaf); a star whose centre
+    is not the lowest id has one user per subtree and caches nothing either.  A cycle's
+    cyclic sub-plan is never cached, its paths are.  Many graphs: messages of different
+    graphs are distinct even on equal table sets."""
+    from paper_2102_02440_gb300 import datagen as G
+    for eu, ev, nt in (([0, 0, 0, 0], [1, 2, 3, 4], 5), ([2, 2, 2, 2], [0, 1, 3, 4], 5)):
+        sm = G.connected_subplans(nt, eu, ev)
+        st, _ = _plan_stats(K, [_graph(K, eu, ev, nt)], 3, 64, [0] * len(sm), sm, K.CMP_EST_CACHE_MESSAGES)
+        assert st.n_jobs == 0 and st.n_levels == 0
+    # cycle 0-1-2-3-4-0: arcs are chains whose lowest id may sit inside them
+    eu, ev = [0, 1, 2, 3, 4], [1, 2, 3, 4, 0]
+    sm = G.connected_subplans(5, eu, ev)
+    c5 = _graph(K, eu, ev, 5)
+    plain, _ = _plan_stats(K, [c5], 3, 64, [0] * len(sm), sm)
+    cached, _ = _plan_stats(K, [c5], 3, 64, [0] * len(sm), sm, K.CMP_EST_CACHE_MESSAGES)
+    assert cached.n_jobs > 0 and cached.n_ops < plain.n_ops
+    only_cycle, _ = _plan_stats(K, [c5], 3, 64, [0], [0b11111], K.CMP_EST_CACHE_MESSAGES)
+    assert only_cycle.n_jobs == 0
+    two, _ = _plan_stats(K, [c5, c5], 3, 64, [0] * len(sm) + [1] * len(sm), sm + sm, K.CMP_EST_CACHE_MESSAGES)
+    assert two.n_jobs == 2 * cached.n_jobs and two.n_ops == 2 * cached.n_ops
+    with pytest.raises(K.CompassError):
+        K.cmp_estimate_plan_stats(np.zeros(256, np.uint8).ctypes.data)
 
 
 def test_cross_ranks_multi_rejections(K):
