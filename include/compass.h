@@ -125,7 +125,7 @@ typedef struct {
 /* ---------------------------------------------------------------------- general */
 
 /* Version of this interface (CMP_ABI_VERSION); bindings refuse a library that differs. */
-#define CMP_ABI_VERSION 4
+#define CMP_ABI_VERSION 5
 int32_t cmp_abi_version(void);
 const char* cmp_status_str(cmp_status s);
 
@@ -288,11 +288,26 @@ typedef struct {
  * exact integers as without the flag. */
 #define CMP_EST_GENERIC_ONLY 1
 #define CMP_EST_CACHE_MESSAGES 2
+/* Flag CMP_EST_STAR_LATTICE: sub-plans made of one root table joined to leaves only, grouped
+ * by (graph, root) with K >= 3 leaf edges U over the family, are evaluated for all leaf
+ * subsets at once (Sec. 5: products of sketches cached across the enumeration's
+ * sub-plans).  In sketch row i a star over leaf set S has the exact row estimate
+ * sum_{a in S} T_a(S minus a), where T_a(V) = sum_r w_a(r) prod_{b in V} f_ab(r) over a's
+ * sorted order, w_a the root-times-leaf products and f_ab the leaf suffix sums at the cross
+ * ranks: the same sum as the merged contraction, regrouped.  T_a is computed for every V as
+ * an exact int128 product of two tables over r (2^(K-1) entries per edge and row, 17 bytes
+ * each, in the workspace), then each star gathers |S| entries.  A family is planned this way
+ * when K 2^(K-1) <= 2 sum_S |S|^2 over its requested stars (it is dense enough); other
+ * sub-plans are planned as without the flag.  Rows that stay in int128 are the same exact
+ * integers; a row where an intermediate value left int128 is flagged (CMP_EOVERFLOW, NaN)
+ * on either evaluation, which may differ between the two only on such rows. */
+#define CMP_EST_STAR_LATTICE 4
 typedef struct {
   int32_t threads;     /* threads per CTA (multiple of 32, <= 1024)                */
   int32_t ctas_per_sm; /* resident CTAs per SM the persistent grid is sized for    */
   int32_t cond_chunk;  /* conditioning values per work item of a cyclic sub-plan   */
-  int32_t flags;       /* CMP_EST_GENERIC_ONLY | CMP_EST_CACHE_MESSAGES; other bits: CMP_EINVAL */
+  int32_t flags;       /* CMP_EST_GENERIC_ONLY | CMP_EST_CACHE_MESSAGES | CMP_EST_STAR_LATTICE;
+                          other bits: CMP_EINVAL */
 } cmp_estimate_cfg;
 
 cmp_status cmp_estimate_plan_bytes(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
@@ -312,6 +327,7 @@ cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_de
 typedef struct {
   int64_t n_sub, n_items, n_ops, n_jobs, n_job_items, n_tri;
   int32_t n_levels, grid;
+  int64_t n_star, n_star_sub, n_star_entries; /* star families, their sub-plans, lattice entries */
 } cmp_estimate_plan_info;
 cmp_status cmp_estimate_plan_stats(const void* plan_host, cmp_estimate_plan_info* info);
 

@@ -17,7 +17,8 @@ CMP_I32, CMP_I64 = 0, 1
 CMP_RANGE, CMP_EQ, CMP_IN_BITMAP = 0, 1, 2
 CMP_EST_GENERIC_ONLY = 1
 CMP_EST_CACHE_MESSAGES = 2
-CMP_ABI_VERSION = 4
+CMP_EST_STAR_LATTICE = 4
+CMP_ABI_VERSION = 5
 CMP_PART_MAX_AXES = 4
 CMP_MAX_COLS, CMP_MAX_PREDS, CMP_MAX_SKETCHES, CMP_MAX_D = 32, 8, 16, 64
 
@@ -60,7 +61,8 @@ class cmp_build_cfg(C.Structure):
 
 class cmp_estimate_plan_info(C.Structure):
     _fields_ = [("n_sub", C.c_int64), ("n_items", C.c_int64), ("n_ops", C.c_int64), ("n_jobs", C.c_int64),
-                ("n_job_items", C.c_int64), ("n_tri", C.c_int64), ("n_levels", C.c_int32), ("grid", C.c_int32)]
+                ("n_job_items", C.c_int64), ("n_tri", C.c_int64), ("n_levels", C.c_int32), ("grid", C.c_int32),
+                ("n_star", C.c_int64), ("n_star_sub", C.c_int64), ("n_star_entries", C.c_int64)]
 
 
 class cmp_estimate_cfg(C.Structure):

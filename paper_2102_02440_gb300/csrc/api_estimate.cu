@@ -22,7 +22,7 @@ cmp_status est_shape(const cmp_estimate_cfg* cfg, EstShape* s) {
   s->ctas_per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : 1;
   s->cond_chunk = (cfg && cfg->cond_chunk > 0) ? cfg->cond_chunk : 64;
   s->flags = cfg ? cfg->flags : 0;
-  if (s->flags & ~int32_t(CMP_EST_GENERIC_ONLY | CMP_EST_CACHE_MESSAGES)) return CMP_EINVAL;
+  if (s->flags & ~int32_t(CMP_EST_GENERIC_ONLY | CMP_EST_CACHE_MESSAGES | CMP_EST_STAR_LATTICE)) return CMP_EINVAL;
   if (s->threads < 32 || s->threads > 1024 || s->threads % 32 || s->ctas_per_sm > 32) return CMP_EINVAL;
   return CMP_OK;
 }
@@ -36,6 +36,9 @@ struct PlanOut {
   std::vector<TriSub> tris;
   std::vector<EstItem> tri_items;  // appended after the generic items
   int32_t tri_max_leaves = 0;
+  std::vector<StarFam> stars;
+  std::vector<StarUnit> star_suf_units, star_lat_units;
+  int64_t star_suf_words = 0, star_t_entries = 0, n_star_sub = 0;
 };
 
 bool graph_ok(const cmp_graph& g) {
@@ -415,7 +418,7 @@ std::vector<int> edges_within(const cmp_graph& g, uint64_t mask) {
 // Plan one sub-plan: spanning tree by BFS from the lowest table id (edges in id order),
 // non-tree edges conditioned, post-order operations for every non-leaf table.
 cmp_status plan_sub(const cmp_graph& g, int32_t gi, uint64_t mask, int32_t d, int32_t w, int32_t sub_index,
-                    int32_t chunk, int32_t flags, const CacheCtx* C, PlanOut* P) {
+                    int32_t chunk, int32_t flags, const CacheCtx* C, int32_t star, uint32_t sbits, PlanOut* P) {
   const int nt = g.n_tables;
   if (mask == 0 || (nt < 64 && (mask >> nt) != 0)) return CMP_EINVAL;
   const std::vector<int> es = edges_within(g, mask);
@@ -428,6 +431,7 @@ cmp_status plan_sub(const cmp_graph& g, int32_t gi, uint64_t mask, int32_t d, in
   EstSub sb;
   std::memset(&sb, 0, sizeof(sb));
   sb.job = -1;
+  sb.star = -1;
   sb.scale = 1.0;  // sampled tables: prod over the sub-plan's tables, ascending, of 1 / rate
   if (g.sample_rate)
     for (int t = 0; t < nt; t++) {
@@ -440,6 +444,12 @@ cmp_status plan_sub(const cmp_graph& g, int32_t gi, uint64_t mask, int32_t d, in
   if (order.size() == 1) {
     sb.single = 1;
     sb.sv = g.survivors_dev + root;
+    P->subs.push_back(sb);
+    return CMP_OK;
+  }
+  if (star >= 0) {  // gathered from its family's lattice
+    sb.star = star;
+    sb.sbits = sbits;
     P->subs.push_back(sb);
     return CMP_OK;
   }
@@ -517,6 +527,109 @@ cmp_status plan_jobs(const cmp_graph* graphs, int32_t d, int32_t n_sub, CacheCtx
   return CMP_OK;
 }
 
+// Star families (CMP_EST_STAR_LATTICE): sub-plans whose edges all touch their lowest table
+// (the root) and reach every other table once, grouped by (graph, root).  A family with
+// leaf edges U (ascending id, K = |U| >= 3) is planned on the lattice when
+// K 2^(K-1) <= 2 sum_S |S|^2 over its stars: the lattice's multiply-adds per sorted position
+// against the generic contraction's products.  Its stars get star_of/sbits_of; the others
+// stay on the generic path.
+void plan_stars(const cmp_graph* graphs, int32_t n_sub, const int32_t* sub_graph, const uint64_t* sub_mask,
+                int32_t d, int32_t w, PlanOut* P, std::vector<int32_t>* star_of, std::vector<uint32_t>* sbits_of) {
+  struct Fam {
+    int32_t g, root;
+    std::vector<int32_t> qs;
+    std::vector<std::vector<int>> edges;
+  };
+  std::vector<Fam> fams;
+  std::unordered_map<uint64_t, int32_t> key;
+  for (int32_t q = 0; q < n_sub; q++) {
+    const cmp_graph& g = graphs[sub_graph[q]];
+    const uint64_t mask = sub_mask[q];
+    const int nt = g.n_tables;
+    if (mask == 0 || (nt < 64 && (mask >> nt) != 0) || __builtin_popcountll(mask) < 2) continue;
+    int root = 0;
+    while (!((mask >> root) & 1)) root++;
+    const std::vector<int> es = edges_within(g, mask);
+    if (int(es.size()) != __builtin_popcountll(mask) - 1) continue;
+    uint64_t reached = uint64_t(1) << root;
+    bool star = true;
+    for (int e : es) {
+      if (!touches(g, e, root)) {
+        star = false;
+        break;
+      }
+      reached |= uint64_t(1) << other_end(g, e, root);
+    }
+    if (!star || reached != mask) continue;
+    const uint64_t k = (uint64_t(uint32_t(sub_graph[q])) << 32) | uint32_t(root);
+    auto it = key.find(k);
+    int32_t f;
+    if (it == key.end()) {
+      f = int32_t(fams.size());
+      key.emplace(k, f);
+      fams.push_back(Fam{sub_graph[q], root, {}, {}});
+    } else {
+      f = it->second;
+    }
+    fams[f].qs.push_back(q);
+    fams[f].edges.push_back(es);
+  }
+  for (const Fam& fm : fams) {
+    std::vector<int> U;
+    double sumsq = 0;
+    for (const std::vector<int>& es : fm.edges) {
+      U.insert(U.end(), es.begin(), es.end());
+      sumsq += double(es.size()) * double(es.size());
+    }
+    std::sort(U.begin(), U.end());
+    U.erase(std::unique(U.begin(), U.end()), U.end());
+    const int K = int(U.size());
+    if (K < 3 || K > CMP_MAX_SKETCHES || double(K) * double(int64_t(1) << (K - 1)) > 2.0 * sumsq) continue;
+    const cmp_graph& g = graphs[fm.g];
+    const int32_t fi = int32_t(P->stars.size());
+    StarFam F;
+    std::memset(&F, 0, sizeof(F));
+    F.in_begin = int32_t(P->ins.size());
+    F.K = K;
+    const int k = K - 1;
+    F.k2 = std::min(k, kStarMaxK2);
+    F.k1 = k - F.k2;
+    F.m1 = std::min(F.k1, std::max(0, 12 - F.k2));  // at most 2^12 entries per unit
+    F.suf_off = P->star_suf_words;
+    F.t_off = P->star_t_entries;
+    P->star_suf_words += int64_t(d) * K * (int64_t(w) + 1);
+    P->star_t_entries += int64_t(d) * K * (int64_t(1) << k);
+    for (int e : U) {
+      const int me = g.edge_u[e] == fm.root ? 0 : 1;
+      EstIn x;
+      std::memset(&x, 0, sizeof(x));
+      x.s = g.sketch[2 * e + me];
+      x.abs = g.abs_sorted[2 * e + me];
+      x.perm = g.perm[2 * e + me];
+      x.rk = g.ranks[2 * e + me];
+      x.tslot = g.slot[2 * e + me];
+      x.msk = g.sketch[2 * e + (1 - me)];
+      x.kind = kInLeaf;
+      x.slot = x.suf = -1;
+      P->ins.push_back(x);
+    }
+    P->stars.push_back(F);
+    for (int i = 0; i < d; i++)
+      for (int b = 0; b < K; b++) P->star_suf_units.push_back(StarUnit{fi, i, b, -1});
+    const int32_t n_blk = int32_t(1) << (F.k1 - F.m1);
+    for (int i = 0; i < d; i++)
+      for (int a = 0; a < K; a++)
+        for (int32_t blk = 0; blk < n_blk; blk++) P->star_lat_units.push_back(StarUnit{fi, i, a, blk});
+    for (size_t j = 0; j < fm.qs.size(); j++) {
+      uint32_t bits = 0;
+      for (int e : fm.edges[j]) bits |= 1u << int(std::lower_bound(U.begin(), U.end(), e) - U.begin());
+      (*star_of)[fm.qs[j]] = fi;
+      (*sbits_of)[fm.qs[j]] = bits;
+      P->n_star_sub++;
+    }
+  }
+}
+
 cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
                     const int32_t* sub_graph, const uint64_t* sub_mask, const cmp_estimate_cfg* cfg, PlanOut* P,
                     EstPlanHdr* H) {
@@ -529,6 +642,9 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
   for (int32_t q = 0; q < n_sub; q++)
     if (sub_graph[q] < 0 || sub_graph[q] >= n_graphs) return CMP_EINVAL;
   std::memset(H, 0, sizeof(*H));
+  std::vector<int32_t> star_of(size_t(n_sub), -1);
+  std::vector<uint32_t> sbits_of(size_t(n_sub), 0);
+  if (shape.flags & CMP_EST_STAR_LATTICE) plan_stars(graphs, n_sub, sub_graph, sub_mask, d, w, P, &star_of, &sbits_of);
   CacheCtx cache;
   const bool use_cache = (shape.flags & CMP_EST_CACHE_MESSAGES) != 0;
   if (use_cache) {
@@ -538,7 +654,7 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
   }
   for (int32_t q = 0; q < n_sub; q++) {
     const cmp_status st = plan_sub(graphs[sub_graph[q]], sub_graph[q], sub_mask[q], d, w, q, shape.cond_chunk,
-                                   shape.flags, use_cache ? &cache : nullptr, P);
+                                   shape.flags, use_cache ? &cache : nullptr, star_of[q], sbits_of[q], P);
     if (st != CMP_OK) return st;
   }
   // items: cached jobs by level, then the sub-plans' generic items, then the triangle items
@@ -581,6 +697,15 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
   off += align16(sizeof(EstItem) * P->items.size());
   H->off_tri = int64_t(off);
   off += align16(sizeof(TriSub) * P->tris.size());
+  H->n_star = int64_t(P->stars.size());
+  H->off_star = int64_t(off);
+  off += align16(sizeof(StarFam) * P->stars.size());
+  H->n_star_suf_units = int64_t(P->star_suf_units.size());
+  H->n_star_units = H->n_star_suf_units + int64_t(P->star_lat_units.size());
+  H->off_star_units = int64_t(off);
+  off += align16(sizeof(StarUnit) * size_t(H->n_star_units));
+  H->star_suf_words = P->star_suf_words;
+  H->star_t_entries = P->star_t_entries;
   H->total_bytes = int64_t(off);
   H->max_suf = P->max_suf;
   H->max_rank = P->max_rank;
@@ -680,6 +805,12 @@ cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, i
   if (!P.ins.empty()) std::memcpy(b + H.off_in, P.ins.data(), sizeof(EstIn) * P.ins.size());
   if (!P.items.empty()) std::memcpy(b + H.off_items, P.items.data(), sizeof(EstItem) * P.items.size());
   if (!P.tris.empty()) std::memcpy(b + H.off_tri, P.tris.data(), sizeof(TriSub) * P.tris.size());
+  if (!P.stars.empty()) std::memcpy(b + H.off_star, P.stars.data(), sizeof(StarFam) * P.stars.size());
+  if (!P.star_suf_units.empty())
+    std::memcpy(b + H.off_star_units, P.star_suf_units.data(), sizeof(StarUnit) * P.star_suf_units.size());
+  if (!P.star_lat_units.empty())
+    std::memcpy(b + H.off_star_units + sizeof(StarUnit) * P.star_suf_units.size(), P.star_lat_units.data(),
+                sizeof(StarUnit) * P.star_lat_units.size());
   return CMP_OK;
 }
 
@@ -696,6 +827,11 @@ cmp_status cmp_estimate_plan_stats(const void* plan_host, cmp_estimate_plan_info
   info->n_tri = H.n_tri;
   info->n_levels = H.n_levels;
   info->grid = H.grid;
+  info->n_star = H.n_star;
+  info->n_star_sub = 0;
+  info->n_star_entries = H.star_t_entries;
+  const EstSub* subs = reinterpret_cast<const EstSub*>(static_cast<const unsigned char*>(plan_host) + H.off_subs);
+  for (int64_t q = 0; q < H.n_sub; q++) info->n_star_sub += subs[q].star >= 0 ? 1 : 0;
   return CMP_OK;
 }
 

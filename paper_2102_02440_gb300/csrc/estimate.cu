@@ -761,6 +761,16 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_estimate_finalize(const __
     bool ovf = false;
     if (sb.single) {
       s = i128(*sb.sv);
+    } else if (sb.star >= 0) {  // a star: gather T_a(S \ {a}) over its leaf edges a
+      const StarFam F = A.star[sb.star];
+      const int k = F.K - 1;
+      for (int a = 0; a < F.K; a++) {
+        if (!((sb.sbits >> a) & 1u)) continue;
+        const uint32_t V = (sb.sbits & ((1u << a) - 1u)) | ((sb.sbits >> (a + 1)) << a);
+        const int64_t idx = F.t_off + ((int64_t(i) * F.K + a) << k) + V;
+        ovf |= A.star_tf[idx] != 0;
+        ovf |= add_ovf(s, A.star_t[idx], &s);
+      }
     } else {
       const int64_t it0 = int64_t(sb.item_begin) + int64_t(i) * sb.n_chunks;
       for (int ch = 0; ch < sb.n_chunks; ch++) {
@@ -821,6 +831,10 @@ cudaError_t launch_estimate(const EstArgs& a, const EstPlanHdr& H, double* est, 
   }
   if (a.n_tri > 0) {
     const cudaError_t e = launch_estimate_tri(a, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (a.n_star_units > 0) {
+    const cudaError_t e = launch_estimate_star(a, st);
     if (e != cudaSuccess) return e;
   }
   if (a.n_sub > 0) {

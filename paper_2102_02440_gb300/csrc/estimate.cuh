@@ -46,8 +46,37 @@ struct EstSub {
   int32_t tri;        // index of its TriSub (triangle evaluation), else -1
   double scale;       // sampled tables: prod of 1 / rate over the sub-plan's tables, else 1
   int32_t job;        // >= 0: a cached subtree message (its index), not a sub-plan
+  int32_t star;       // >= 0: a star of that family, its rows gathered from the family's lattice
+  uint32_t sbits;     // star: its leaf edges, bit u = edge u of the family (ascending edge id)
   int32_t pad;
 };
+
+// Star families (sub-plans whose only operation is the root joined to leaves, grouped by
+// graph and root).  For the family's K leaf edges U (ascending id), sketch row i and the
+// edge a that attains the minimum, the lattice holds for every subset V of U \ {a}
+//   T_a(V) = sum_r w_a(r) prod_{b in V} f_ab(r),
+//   w_a(r) = s_a[pi_a(r)] m_a[pi_a(r)],  f_ab(r) = suffix sum of m_b in b's sorted order from
+//   the cross rank of a's position r,
+// so that a star over leaf set S has row estimate sum_{a in S} T_a(S \ {a}).  V's bits are
+// the positions of U \ {a}: the low k1 bits index the A side, the high k2 bits the B side.
+struct StarFam {
+  int32_t in_begin, K;      // its K leaf inputs (EstIn, kind kInLeaf)
+  int32_t k1, k2, m1, pad;  // k1 + k2 = K - 1; a lattice unit covers 2^m1 A-side subsets
+  int64_t suf_off;          // suffix sums: [d][K][w + 1] int64 at star_suf + suf_off
+  int64_t t_off;            // lattice: [d][K][2^(K-1)] at star_t + t_off (and star_tf)
+};
+struct StarUnit {
+  int32_t fam, row, a, blk;  // suffix units: a = the leaf b whose suffix sums are built, blk = -1
+};
+constexpr int kStarThreads = 256;
+constexpr int kStarR = 16;        // sorted positions per chunk
+constexpr int kStarMaxK2 = 8;     // B side: at most 256 subsets
+constexpr int kStarMaxEnt = 4096; // lattice entries per unit (16 per thread)
+inline size_t star_smem_bytes() {
+  // B[R][256] and A[R][16] int128 with byte flags, f[15][R] and w[R] int64, lane reduction
+  return size_t(kStarR) * (1 << kStarMaxK2) * 17 + size_t(kStarR) * 16 * 17 + 15 * kStarR * 8 + kStarR * 8 +
+         size_t(kStarThreads) * 17 + 64;
+}
 
 struct EstItem {
   int32_t sub, row, c0, c1;  // conditioning values [c0, c1); trees use [0, 1); triangle: columns [c0, c1)
@@ -111,9 +140,12 @@ struct EstPlanHdr {
   int64_t n_jobs, n_job_items;
   int32_t n_levels, pad;
   int64_t lvl_end[kEstMaxLevels];
+  // star families (CMP_EST_STAR_LATTICE): families, units (suffix units first)
+  int64_t n_star, off_star, n_star_units, n_star_suf_units, off_star_units;
+  int64_t star_suf_words, star_t_entries;  // workspace: int64 suffix sums, lattice entries
 };
 constexpr uint64_t kEstPlanMagic = 0x434d504553544d54ull;  // "CMPESTMT"
-constexpr int32_t kEstPlanVersion = 4;
+constexpr int32_t kEstPlanVersion = 5;
 
 struct EstArgs {
   const EstSub* subs;
@@ -136,6 +168,12 @@ struct EstArgs {
   i128* cache;          // [n_jobs][d][w] cached subtree messages, bucket order
   int32_t* cache_ovf;   // [n_jobs][d] 1: the message left int128
   int64_t n_job_items;
+  const StarFam* star;
+  const StarUnit* star_units;
+  int64_t n_star, n_star_units, n_star_suf_units;
+  int64_t* star_suf;
+  i128* star_t;
+  uint8_t* star_tf;     // 1: the lattice entry left int128
 };
 
 // Round-to-nearest-even of (neg ? -1 : 1) * (top * 2^128 + mag) to binary64, from the
@@ -195,9 +233,13 @@ constexpr int32_t kPresortSmemMaxW = 16384;
 inline size_t est_cache_bytes(const EstPlanHdr& H) {
   return align16(sizeof(i128) * size_t(H.n_jobs) * size_t(H.d) * size_t(H.w));
 }
+inline size_t est_star_bytes(const EstPlanHdr& H) {
+  return align16(sizeof(i128) * size_t(H.star_t_entries)) + align16(size_t(H.star_t_entries)) +
+         align16(sizeof(int64_t) * size_t(H.star_suf_words));
+}
 inline size_t est_fixed_bytes(const EstPlanHdr& H) {
   return align16(sizeof(i128) * size_t(H.n_items)) + align16(sizeof(int32_t) * size_t(H.n_items)) +
-         est_cache_bytes(H) + align16(sizeof(int32_t) * size_t(H.n_jobs) * size_t(H.d));
+         est_cache_bytes(H) + align16(sizeof(int32_t) * size_t(H.n_jobs) * size_t(H.d)) + est_star_bytes(H);
 }
 inline size_t est_ws_bytes(const EstPlanHdr& H, int64_t grid, int64_t tri_slots) {
   return est_fixed_bytes(H) + size_t(H.scratch_per_cta) * size_t(grid) + size_t(H.tri_row_bytes) * size_t(tri_slots);
@@ -216,6 +258,16 @@ inline EstArgs est_args(const EstPlanHdr& H, const unsigned char* pd, unsigned c
   a.cache = reinterpret_cast<i128*>(ws + o_cache);
   a.cache_ovf = reinterpret_cast<int32_t*>(ws + o_cache + est_cache_bytes(H));
   a.n_job_items = H.n_job_items;
+  const size_t o_star = o_cache + est_cache_bytes(H) + align16(sizeof(int32_t) * size_t(H.n_jobs) * size_t(H.d));
+  a.star = reinterpret_cast<const StarFam*>(pd + H.off_star);
+  a.star_units = reinterpret_cast<const StarUnit*>(pd + H.off_star_units);
+  a.n_star = H.n_star;
+  a.n_star_units = H.n_star_units;
+  a.n_star_suf_units = H.n_star_suf_units;
+  a.star_t = reinterpret_cast<i128*>(ws + o_star);
+  a.star_tf = ws + o_star + align16(sizeof(i128) * size_t(H.star_t_entries));
+  a.star_suf = reinterpret_cast<int64_t*>(ws + o_star + align16(sizeof(i128) * size_t(H.star_t_entries)) +
+                                          align16(size_t(H.star_t_entries)));
   a.scratch = ws + est_fixed_bytes(H);
   a.scratch_per_cta = H.scratch_per_cta;
   a.n_items = H.n_items;
@@ -242,6 +294,7 @@ inline EstArgs est_args(const EstPlanHdr& H, const unsigned char* pd, unsigned c
 
 cudaError_t launch_estimate(const EstArgs& a, const EstPlanHdr& H, double* est, int64_t* row_est, cudaStream_t st);
 cudaError_t launch_estimate_tri(const EstArgs& a, cudaStream_t st);
+cudaError_t launch_estimate_star(const EstArgs& a, cudaStream_t st);
 cudaError_t launch_cross_ranks(const uint32_t* abs, const int32_t* perm, int32_t k, int32_t d, int32_t w,
                                const int32_t* edge_id, int32_t* ranks, cudaStream_t st);
 cudaError_t launch_cross_ranks_multi(const uint32_t* abs, const int32_t* perm, int32_t n_tables, const int32_t* k,

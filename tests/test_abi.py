@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(K):
 def test_status_strings(K):
     assert K.status_str(0) == "ok"
     assert "invalid" in K.status_str(-1)
-    assert K.lib().cmp_abi_version() == K.CMP_ABI_VERSION == 4
+    assert K.lib().cmp_abi_version() == K.CMP_ABI_VERSION == 5
 
 
 def test_hash_params_match_oracle_generator(K, orc):
@@ -192,7 +192,7 @@ def test_estimate_plan_triangle_path_host_logic(K):
     assert (K.cmp_estimate_plan_bytes([c4], 5, 64, [0], [0b1111])[1] ==
             K.cmp_estimate_plan_bytes([c4], 5, 64, [0], [0b1111], gen)[1])
     with pytest.raises(K.CompassError) as ei:
-        K.cmp_estimate_plan_bytes([g], 11, 64, [0], [0b111], K.cmp_estimate_cfg.make(flags=4))
+        K.cmp_estimate_plan_bytes([g], 11, 64, [0], [0b111], K.cmp_estimate_cfg.make(flags=8))
     assert ei.value.status == K.CMP_EINVAL
 
 
@@ -254,6 +254,40 @@ def test_estimate_plan_cached_messages_shapes(K):
     assert two.n_jobs == 2 * cached.n_jobs and two.n_ops == 2 * cached.n_ops
     with pytest.raises(K.CompassError):
         K.cmp_estimate_plan_stats(np.zeros(256, np.uint8).ctypes.data)
+
+
+def test_estimate_plan_star_families(K):
+    """CMP_EST_STAR_LATTICE host logic.  A star with centre 0 and K leaves asked for every
+    leaf subset is one family of 2^K - 1 stars with K 2^(K-1) lattice entries per row; asked
+    for its two-table sub-plans only it is too sparse (K 2^(K-1) > 2 sum |S|^2) and stays on
+    the generic path; fewer than three leaf edges never form a family; a centre that is not
+    the lowest id roots the sub-plans with a leaf, which are then no stars; chains have none."""
+    from paper_2102_02440_gb300 import datagen as G
+    d = 3
+    for n_leaves in (3, 4, 8, 16):
+        eu, ev = [0] * n_leaves, list(range(1, n_leaves + 1))
+        g = _graph(K, eu, ev, n_leaves + 1)
+        sm = G.connected_subplans(n_leaves + 1, eu, ev)
+        st, wb = _plan_stats(K, [g], d, 64, [0] * len(sm), sm, K.CMP_EST_STAR_LATTICE)
+        assert st.n_star == 1 and st.n_star_sub == 2 ** n_leaves - 1
+        assert st.n_star_entries == d * n_leaves * 2 ** (n_leaves - 1)
+        assert wb >= 17 * st.n_star_entries + 8 * d * n_leaves * 65
+        plain, _ = _plan_stats(K, [g], d, 64, [0] * len(sm), sm)
+        assert plain.n_star == 0 and st.n_ops < plain.n_ops and st.n_items < plain.n_items
+        pairs = [m for m in sm if bin(m).count("1") == 2]
+        sp, _ = _plan_stats(K, [g], d, 64, [0] * len(pairs), pairs, K.CMP_EST_STAR_LATTICE)
+        assert sp.n_star == 0                              # K 2^(K-1) > 2 K
+    two = _graph(K, [0, 0], [1, 2], 3)
+    st, _ = _plan_stats(K, [two], d, 64, [0] * 3, [0b011, 0b101, 0b111], K.CMP_EST_STAR_LATTICE)
+    assert st.n_star == 0
+    c3 = _graph(K, [3, 3, 3, 3, 3], [0, 1, 2, 4, 5], 6)
+    sm = G.connected_subplans(6, [3, 3, 3, 3, 3], [0, 1, 2, 4, 5])
+    st, _ = _plan_stats(K, [c3], d, 64, [0] * len(sm), sm, K.CMP_EST_STAR_LATTICE)
+    assert st.n_star == 0                          # rooted at 3 only without 0, 1, 2: two leaf edges
+    ch = _graph(K, list(range(8)), list(range(1, 9)), 9)
+    sm = G.connected_subplans(9, list(range(8)), list(range(1, 9)))
+    st, _ = _plan_stats(K, [ch], d, 64, [0] * len(sm), sm, K.CMP_EST_STAR_LATTICE | K.CMP_EST_CACHE_MESSAGES)
+    assert st.n_star == 0 and st.n_jobs == 21
 
 
 def test_cross_ranks_multi_rejections(K):
