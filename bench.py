@@ -57,7 +57,7 @@ def _args():
                     help="JSON file of autotuned launch shapes: read if it has this workload's, else written")
     ap.add_argument("--case", default=None,
                     choices=["estimate_small", "estimate_full", "build_f1", "build_five", "batched", "scale",
-                             "partition", "offline_sample", "cached"],
+                             "partition", "offline_sample", "cached", "star17"],
                     help="run one small profiling case instead of the benchmark (for ncu captures)")
     return ap.parse_args()
 
@@ -644,8 +644,10 @@ def run_case(a):
     """Profiling cases (one GPU, under 1 GB on the device): the estimate of all 19 sub-plans
     of the five-table graph at w = 4096 on sketches of the tables at 5% scale (estimate_small)
     or full scale (estimate_full, the benchmark's sketches); the single-table fused build of
-    the 36M-row F1 table alone (3 sketches, d = 11, w = 4096, per-tuple path); or the
-    benchmark's batched build of all five tables (build_five)."""
+    the 36M-row F1 table alone (3 sketches, d = 11, w = 4096, per-tuple path); the
+    benchmark's batched build of all five tables (build_five); or the star lattice over all
+    65,535 sub-plans of one 17-table star (rows log-uniform in [1e4, 1e5], d = 11, w = 1024;
+    star17)."""
     import torch
 
     from paper_2102_02440_gb300 import datagen as G
@@ -656,6 +658,15 @@ def run_case(a):
         dw = P.DeviceWorkload(wl)
         dw.build_batched()
         est = P.DeviceEstimator(dw, G.connected_subplans(5, wl.edge_u, wl.edge_v))
+        est.presort()
+        fn = est.estimate
+    elif a.case == "star17":
+        from paper_2102_02440_gb300 import compass as K
+        g = G.graph_batch(1, 17, 17, rows_lo=10_000, rows_hi=100_000, d=11, w=1024, kinds=("star",))
+        dw = P.DeviceWorkload(g[0])
+        dw.build_batched()
+        est = P.DeviceEstimator(dw, G.connected_subplans(17, g[0].edge_u, g[0].edge_v),
+                                cfg=K.cmp_estimate_cfg.make(flags=K.CMP_EST_STAR_LATTICE))
         est.presort()
         fn = est.estimate
     elif a.case == "build_f1":
@@ -681,8 +692,9 @@ def run_batched(a):
     log-uniform in [1e4, 1e6], Zipf 0.5..1.5 keys over 1e5, ~50% of tables with a point or
     range predicate), d = 11, w = 1024.  Times, on one GPU:
       build: one batched launch for every table vs one launch per table;
-      estimate: one plan over every connected sub-plan vs one plan launch per sub-plan
-        (timed on a random sample of sub-plans, reported per sub-plan);
+      estimate: one plan over every connected sub-plan (cached subtree messages and the star
+        lattice on) vs one plan launch per sub-plan (timed on a random sample of sub-plans,
+        reported per sub-plan);
       the batched build + presort + estimate captured in one CUDA graph vs eager."""
     import torch
 
@@ -715,7 +727,10 @@ def run_batched(a):
     ms_build_t = timed(gb.build_per_table)
     gb.build_batched()
     gb.presort()
-    plan = gb.plan(sg, sm)
+    # one plan over every sub-plan, with the reuse across sub-plans on (cached subtree
+    # messages and the star lattice); the per-sub-plan comparison plans one sub-plan each
+    reuse = K.cmp_estimate_cfg.make(flags=K.CMP_EST_CACHE_MESSAGES | K.CMP_EST_STAR_LATTICE)
+    plan = gb.plan(sg, sm, reuse)
     ms_est_b = timed(plan.run, 3)
     rng = np.random.default_rng(0)
     samp = rng.choice(sm.size, min(2000, sm.size), replace=False)
@@ -757,7 +772,8 @@ def run_batched(a):
             "subplans": int(sm.size), "d": 11, "w": 1024,
             "build_ms": {"batched_one_launch": ms_build_b, "per_table_launches": ms_build_t,
                          "speedup": ms_build_t / ms_build_b},
-            "estimate": {"batched_one_plan_ms": ms_est_b, "batched_subplans_per_s": sm.size / (ms_est_b / 1e3),
+            "estimate": {"flags": "CMP_EST_CACHE_MESSAGES | CMP_EST_STAR_LATTICE",
+                         "batched_one_plan_ms": ms_est_b, "batched_subplans_per_s": sm.size / (ms_est_b / 1e3),
                          "per_subplan_launches_subplans_per_s": samp.size / (ms_est_1 / 1e3),
                          "per_subplan_sample": int(samp.size),
                          "speedup": (sm.size / (ms_est_b / 1e3)) / (samp.size / (ms_est_1 / 1e3))},
