@@ -81,7 +81,6 @@ __global__ void __launch_bounds__(kStarThreads) k_star_lattice(const __grid_cons
   uint8_t* Bf = reinterpret_cast<uint8_t*>(wv + R);               // [R][256]
   uint8_t* Af = Bf + R * NB;                                       // [R][16]
   uint8_t* redf = Af + R * 16;                                     // [256]
-  __shared__ int32_t sh_any;  // some table entry of the chunk left int128
   const int tid = threadIdx.x;
   const int w = A.w, d = A.d;
   for (int64_t ui = A.n_star_suf_units + blockIdx.x; ui < A.n_star_units; ui += gridDim.x) {
@@ -124,7 +123,6 @@ __global__ void __launch_bounds__(kStarThreads) k_star_lattice(const __grid_cons
       }
       __syncthreads();
       // 2. table roots: B[r][0] = 1, A[r][0] = w(r) times the factors of blk's bits
-      if (tid == 0) sh_any = 0;
       for (int rr = tid; rr < R; rr += kStarThreads) {
         Bs[rr * NB] = 1;
         Bf[rr * NB] = 0;
@@ -134,7 +132,6 @@ __global__ void __launch_bounds__(kStarThreads) k_star_lattice(const __grid_cons
           if ((u.blk >> i) & 1) star_step(v, fl, fv[(m1 + i) * R + rr]);
         As[rr * 16] = v;
         Af[rr * 16] = fl;
-        if (fl) sh_any = 1;
       }
       __syncthreads();
       // 3. doubling: entries [h, 2h) from [0, h) times the factor of bit jj
@@ -149,7 +146,6 @@ __global__ void __launch_bounds__(kStarThreads) k_star_lattice(const __grid_cons
             star_step(v, fl, fv[(k1 + jj) * R + rr]);
             Bs[rr * NB + idx] = v;
             Bf[rr * NB + idx] = fl;
-            if (fl) sh_any = 1;
           }
         if (jj < m1)
           for (int q = tid; q < h * R; q += kStarThreads) {
@@ -159,13 +155,10 @@ __global__ void __launch_bounds__(kStarThreads) k_star_lattice(const __grid_cons
             star_step(v, fl, fv[jj * R + rr]);
             As[rr * 16 + idx] = v;
             Af[rr * 16 + idx] = fl;
-            if (fl) sh_any = 1;
           }
         __syncthreads();
       }
-      // 4. multiply-add over the chunk's positions (without flag checks when no entry of the
-      //    chunk left int128: every table value is then exact)
-      const bool any = sh_any != 0;
+      // 4. multiply-add over the chunk's positions
 #pragma unroll
       for (int j = 0; j < 16; j++) {
         if (j >= J) break;
@@ -173,17 +166,6 @@ __global__ void __launch_bounds__(kStarThreads) k_star_lattice(const __grid_cons
         const int v1 = e >> k2, v2 = e & (NV2 - 1);
         i128 s = acc[j];
         bool sf = (accf >> j) & 1u;
-        if (!any) {
-          for (int rr = lane; rr < R; rr += L) {
-            const i128 a = As[rr * 16 + v1], b = Bs[rr * NB + v2];
-            i128 p;
-            sf |= mul_ovf(a, b, &p);
-            sf |= add_ovf(s, p, &s);
-          }
-          acc[j] = s;
-          accf = (accf & ~(1u << j)) | (uint32_t(sf) << j);
-          continue;
-        }
         for (int rr = lane; rr < R; rr += L) {
           const bool fa = Af[rr * 16 + v1], fb = Bf[rr * NB + v2];
           const i128 a = As[rr * 16 + v1], b = Bs[rr * NB + v2];
