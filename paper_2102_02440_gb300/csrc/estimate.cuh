@@ -73,8 +73,9 @@ constexpr int kStarR = 16;        // sorted positions per chunk
 constexpr int kStarMaxK2 = 8;     // B side: at most 256 subsets
 constexpr int kStarMaxEnt = 4096; // lattice entries per unit (16 per thread)
 inline size_t star_smem_bytes() {
-  // B[R][256] and A[R][16] int128 with byte flags, f[15][R] and w[R] int64, lane reduction
-  return size_t(kStarR) * (1 << kStarMaxK2) * 17 + size_t(kStarR) * 16 * 17 + 15 * kStarR * 8 + kStarR * 8 +
+  // B[R][256] and A[R][16] int128 with byte flags and float magnitude bounds, f[15][R] and
+  // w[R] int64, lane reduction
+  return size_t(kStarR) * (1 << kStarMaxK2) * 21 + size_t(kStarR) * 16 * 21 + 15 * kStarR * 8 + kStarR * 8 +
          size_t(kStarThreads) * 17 + 64;
 }
 

@@ -33,6 +33,15 @@ __device__ __forceinline__ const int32_t* star_rank_row(const EstIn& x, const Es
   return x.rk + (int64_t(y.tslot) * d + row) * w;
 }
 
+// An upper bound of |v| in float (+inf for an out-of-range entry): the high word plus one,
+// or the low word, rounded up.
+__device__ __forceinline__ float star_mag(i128 v, bool fl) {
+  if (fl) return __int_as_float(0x7f800000);
+  const u128 m = v < 0 ? u128(0) - u128(v) : u128(v);
+  const uint64_t hi = uint64_t(m >> 64);
+  return hi ? __ull2float_ru(hi + 1) * 0x1p64f : __ull2float_ru(uint64_t(m));
+}
+
 // v *= f with the out-of-range flag carried (see the file comment).
 __device__ __forceinline__ void star_step(i128& v, bool& fl, int64_t f) {
   if (f == 0) {
@@ -81,6 +90,8 @@ __global__ void __launch_bounds__(kStarThreads) k_star_lattice(const __grid_cons
   uint8_t* Bf = reinterpret_cast<uint8_t*>(wv + R);               // [R][256]
   uint8_t* Af = Bf + R * NB;                                       // [R][16]
   uint8_t* redf = Af + R * 16;                                     // [256]
+  float* Bm = reinterpret_cast<float*>(redf + kStarThreads);      // [R][256] magnitude bounds
+  float* Am = Bm + R * NB;                                         // [R][16]
   const int tid = threadIdx.x;
   const int w = A.w, d = A.d;
   for (int64_t ui = A.n_star_suf_units + blockIdx.x; ui < A.n_star_units; ui += gridDim.x) {
@@ -126,12 +137,14 @@ __global__ void __launch_bounds__(kStarThreads) k_star_lattice(const __grid_cons
       for (int rr = tid; rr < R; rr += kStarThreads) {
         Bs[rr * NB] = 1;
         Bf[rr * NB] = 0;
+        Bm[rr * NB] = 1.0f;
         i128 v = i128(wv[rr]);
         bool fl = false;
         for (int i = 0; i < k1 - m1; i++)
           if ((u.blk >> i) & 1) star_step(v, fl, fv[(m1 + i) * R + rr]);
         As[rr * 16] = v;
         Af[rr * 16] = fl;
+        Am[rr * 16] = star_mag(v, fl);
       }
       __syncthreads();
       // 3. doubling: entries [h, 2h) from [0, h) times the factor of bit jj
@@ -146,6 +159,7 @@ __global__ void __launch_bounds__(kStarThreads) k_star_lattice(const __grid_cons
             star_step(v, fl, fv[(k1 + jj) * R + rr]);
             Bs[rr * NB + idx] = v;
             Bf[rr * NB + idx] = fl;
+            Bm[rr * NB + idx] = star_mag(v, fl);
           }
         if (jj < m1)
           for (int q = tid; q < h * R; q += kStarThreads) {
@@ -155,10 +169,12 @@ __global__ void __launch_bounds__(kStarThreads) k_star_lattice(const __grid_cons
             star_step(v, fl, fv[jj * R + rr]);
             As[rr * 16 + idx] = v;
             Af[rr * 16 + idx] = fl;
+            Am[rr * 16 + idx] = star_mag(v, fl);
           }
         __syncthreads();
       }
-      // 4. multiply-add over the chunk's positions
+      // 4. multiply-add over the chunk's positions.  When the magnitude bounds keep the product
+      //    below 2^126 (float rounding stays far from 2^127), the product modulo 2^128 is exact.
 #pragma unroll
       for (int j = 0; j < 16; j++) {
         if (j >= J) break;
@@ -167,8 +183,12 @@ __global__ void __launch_bounds__(kStarThreads) k_star_lattice(const __grid_cons
         i128 s = acc[j];
         bool sf = (accf >> j) & 1u;
         for (int rr = lane; rr < R; rr += L) {
-          const bool fa = Af[rr * 16 + v1], fb = Bf[rr * NB + v2];
           const i128 a = As[rr * 16 + v1], b = Bs[rr * NB + v2];
+          if (Am[rr * 16 + v1] * Bm[rr * NB + v2] < 0x1p126f) {
+            sf |= add_ovf(s, i128(u128(a) * u128(b)), &s);
+            continue;
+          }
+          const bool fa = Af[rr * 16 + v1], fb = Bf[rr * NB + v2];
           if ((!fa && a == 0) || (!fb && b == 0)) continue;  // an exact zero factor
           if (fa || fb) {
             sf = true;
