@@ -10,12 +10,13 @@
 // (beyond the exact range) counts as +inf, a negative one as 0.  Pruning and the update of
 // the best plan are strict, so of equal-cost plans the first found is kept.
 //
-// One thread per graph: the search is sequential (each source's search starts from the best
-// cost found so far).  Its stack, one frame per prefix length, lives in the workspace; the
-// estimates come from the device array the estimate wrote (no host round trip), looked up
-// by binary search over the graph's sorted sub-plan masks.  f(v) and the costs are computed
-// with explicitly rounded double operations (no fused multiply-add), so every comparison
-// sees the same values as a plain IEEE evaluation.
+// One warp per graph, its first lane searching: the search is sequential (each source's
+// search starts from the best cost found so far), and graphs in separate warps do not
+// serialise each other's divergent paths.  The stack, one frame per prefix length, lives in
+// the workspace; the estimates come from the device array the estimate wrote (no host round
+// trip), found through the graph's open-addressing table of sub-plan masks.  f(v) and the
+// costs are computed with explicitly rounded double operations (no fused multiply-add), so
+// every comparison sees the same values as a plain IEEE evaluation.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,18 +32,31 @@ namespace {
 constexpr int kEnumMaxN = CMP_MAX_TABLES;  // 64
 
 struct EnumGraph {
-  int32_t n, pad;
-  int64_t mask_begin, n_masks;  // its sub-plans in the sorted mask table
+  int32_t n, h_log2;            // tables; log2 of its hash table's slots
+  int64_t h_begin, n_masks;     // its hash table in the slot array; its sub-plans
   const int64_t* card;          // device [n]: exact selected counts
   uint64_t adj[kEnumMaxN];
   int32_t deg[kEnumMaxN];
 };
+// One slot of a graph's table: a sub-plan mask (0 = empty; masks are nonzero) and the
+// index of its estimate.  Linear probing from enum_hash(mask); at most half the slots used.
+struct EnumSlot {
+  uint64_t mask;
+  int64_t sub;
+};
+__host__ __device__ inline uint64_t enum_hash(uint64_t m) {
+  m ^= m >> 31;
+  m *= 0x7fb5d329728ea185ull;
+  m ^= m >> 27;
+  m *= 0x81dadef4bc2dd44dull;
+  return m ^ (m >> 33);
+}
 
 struct EnumPlanHdr {
   uint64_t magic;
   int32_t version, n_graphs;
-  int64_t n_sub, n_masks;
-  int64_t off_graphs, off_masks, off_subs, total_bytes, ws_bytes;
+  int64_t n_sub, n_slots;
+  int64_t off_graphs, off_slots, total_bytes, ws_bytes;
 };
 constexpr uint64_t kEnumPlanMagic = 0x434d50454e554d31ull;  // "CMPENUM1"
 
@@ -60,8 +74,7 @@ constexpr size_t kEnumFrameBytes = (sizeof(EnumFrames) + 255) & ~size_t(255);
 
 struct EnumArgs {
   const EnumGraph* graphs;
-  const uint64_t* masks;
-  const int64_t* subs;
+  const EnumSlot* slots;
   const double* est;
   int32_t n_graphs;
   double alpha, beta;
@@ -74,17 +87,23 @@ struct EnumArgs {
 };
 
 __device__ double lookup(const EnumArgs& A, const EnumGraph& g, uint64_t m, bool* missing) {
-  int64_t lo = g.mask_begin, hi = g.mask_begin + g.n_masks;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (A.masks[mid] < m) lo = mid + 1;
-    else hi = mid;
+  const uint64_t size = uint64_t(1) << g.h_log2;
+  uint64_t i = enum_hash(m) & (size - 1);
+  int64_t sub = -1;
+  for (uint64_t probe = 0; probe < size; probe++) {  // the table has empty slots: ends early
+    const EnumSlot sl = A.slots[g.h_begin + int64_t(i)];
+    if (sl.mask == m) {
+      sub = sl.sub;
+      break;
+    }
+    if (sl.mask == 0) break;
+    i = (i + 1) & (size - 1);
   }
-  if (lo == g.mask_begin + g.n_masks || A.masks[lo] != m) {
+  if (sub < 0) {
     *missing = true;
     return INFINITY;
   }
-  const double v = A.est[A.subs[lo]];
+  const double v = A.est[sub];
   if (v != v) return INFINITY;  // NaN: beyond the exact range
   return v < 0.0 ? 0.0 : v;
 }
@@ -115,8 +134,8 @@ __device__ void expand(const EnumArgs& A, const EnumGraph& g, EnumFrames& F, int
 }  // namespace
 
 __global__ void k_enumerate(const __grid_constant__ EnumArgs A) {
-  const int gi = int(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (gi >= A.n_graphs) return;
+  const int gi = int(blockIdx.x);
+  if (gi >= A.n_graphs || threadIdx.x != 0) return;
   const EnumGraph& g = A.graphs[gi];
   EnumFrames& F = *reinterpret_cast<EnumFrames*>(A.ws + size_t(gi) * kEnumFrameBytes);
   const int n = g.n;
@@ -214,8 +233,7 @@ namespace {
 
 struct EnumPlanParts {
   std::vector<EnumGraph> graphs;
-  std::vector<uint64_t> masks;
-  std::vector<int64_t> subs;
+  std::vector<EnumSlot> slots;
   EnumPlanHdr hdr;
 };
 
@@ -231,8 +249,7 @@ cmp_status enum_plan(const cmp_graph* graphs, int32_t n_graphs, int32_t n_sub, c
     if (nt < 64 && (sub_mask[q] >> nt) != 0) return CMP_EINVAL;
     per[gi].push_back({sub_mask[q], q});
   }
-  P->masks.clear();
-  P->subs.clear();
+  P->slots.clear();
   for (int32_t gi = 0; gi < n_graphs; gi++) {
     const cmp_graph& cg = graphs[gi];
     if (cg.n_tables < 1 || cg.n_tables > kEnumMaxN || cg.n_edges < 0 || !cg.survivors_dev) return CMP_EINVAL;
@@ -253,27 +270,32 @@ cmp_status enum_plan(const cmp_graph* graphs, int32_t n_graphs, int32_t n_sub, c
     std::sort(list.begin(), list.end());
     for (size_t i = 1; i < list.size(); i++)
       if (list[i].first == list[i - 1].first) return CMP_EINVAL;  // one estimate per sub-plan
-    g.mask_begin = int64_t(P->masks.size());
     g.n_masks = int64_t(list.size());
+    int lg = 4;
+    while ((int64_t(1) << lg) < 2 * g.n_masks) lg++;
+    g.h_log2 = lg;
+    g.h_begin = int64_t(P->slots.size());
+    P->slots.resize(P->slots.size() + (size_t(1) << lg), EnumSlot{0, 0});
+    EnumSlot* tab = P->slots.data() + g.h_begin;
+    const uint64_t size = uint64_t(1) << lg;
     for (const auto& x : list) {
-      P->masks.push_back(x.first);
-      P->subs.push_back(x.second);
+      uint64_t i = enum_hash(x.first) & (size - 1);
+      while (tab[i].mask != 0) i = (i + 1) & (size - 1);
+      tab[i] = EnumSlot{x.first, x.second};
     }
   }
   EnumPlanHdr& H = P->hdr;
   std::memset(&H, 0, sizeof(H));
   H.magic = kEnumPlanMagic;
-  H.version = 1;
+  H.version = 2;
   H.n_graphs = n_graphs;
   H.n_sub = n_sub;
-  H.n_masks = int64_t(P->masks.size());
+  H.n_slots = int64_t(P->slots.size());
   size_t off = align16(sizeof(EnumPlanHdr));
   H.off_graphs = int64_t(off);
   off += align16(sizeof(EnumGraph) * P->graphs.size());
-  H.off_masks = int64_t(off);
-  off += align16(sizeof(uint64_t) * P->masks.size());
-  H.off_subs = int64_t(off);
-  off += align16(sizeof(int64_t) * P->subs.size());
+  H.off_slots = int64_t(off);
+  off += align16(sizeof(EnumSlot) * P->slots.size());
   H.total_bytes = int64_t(off);
   H.ws_bytes = int64_t(kEnumFrameBytes * size_t(n_graphs));
   return CMP_OK;
@@ -308,10 +330,7 @@ cmp_status cmp_enum_plan_encode(const cmp_graph* graphs, int32_t n_graphs, int32
   std::memset(b, 0, size_t(P.hdr.total_bytes));
   std::memcpy(b, &P.hdr, sizeof(P.hdr));
   std::memcpy(b + P.hdr.off_graphs, P.graphs.data(), sizeof(EnumGraph) * P.graphs.size());
-  if (!P.masks.empty()) {
-    std::memcpy(b + P.hdr.off_masks, P.masks.data(), sizeof(uint64_t) * P.masks.size());
-    std::memcpy(b + P.hdr.off_subs, P.subs.data(), sizeof(int64_t) * P.subs.size());
-  }
+  if (!P.slots.empty()) std::memcpy(b + P.hdr.off_slots, P.slots.data(), sizeof(EnumSlot) * P.slots.size());
   return CMP_OK;
 }
 
@@ -321,7 +340,7 @@ cmp_status cmp_enumerate(const void* plan_host, const void* plan_dev, const doub
   if (!plan_host || !plan_dev) return CMP_EINVAL;
   EnumPlanHdr H;
   std::memcpy(&H, plan_host, sizeof(H));
-  if (H.magic != kEnumPlanMagic || H.version != 1) return CMP_EINVAL;
+  if (H.magic != kEnumPlanMagic || H.version != 2) return CMP_EINVAL;
   if (!order_dev || !cost_dev || !stats_dev || (H.n_sub > 0 && !est_dev)) return CMP_EINVAL;
   if (!ws_dev || ws_bytes < size_t(H.ws_bytes)) return CMP_EWORKSPACE;
   double alpha = 0.5, beta = 0.5;
@@ -335,8 +354,7 @@ cmp_status cmp_enumerate(const void* plan_host, const void* plan_dev, const doub
   const unsigned char* pd = static_cast<const unsigned char*>(plan_dev);
   EnumArgs a;
   a.graphs = reinterpret_cast<const EnumGraph*>(pd + H.off_graphs);
-  a.masks = reinterpret_cast<const uint64_t*>(pd + H.off_masks);
-  a.subs = reinterpret_cast<const int64_t*>(pd + H.off_subs);
+  a.slots = reinterpret_cast<const EnumSlot*>(pd + H.off_slots);
   a.est = est_dev;
   a.n_graphs = H.n_graphs;
   a.alpha = alpha;
@@ -348,8 +366,7 @@ cmp_status cmp_enumerate(const void* plan_host, const void* plan_dev, const doub
   a.cost = cost_dev;
   a.stats = stats_dev;
   a.status = status_dev;
-  const int th = 32;
-  k_enumerate<<<unsigned((H.n_graphs + th - 1) / th), th, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
+  k_enumerate<<<unsigned(H.n_graphs), 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
   return cudaGetLastError() == cudaSuccess ? CMP_OK : CMP_ECUDA;
 }
 
