@@ -57,7 +57,7 @@ def _args():
                     help="JSON file of autotuned launch shapes: read if it has this workload's, else written")
     ap.add_argument("--case", default=None,
                     choices=["estimate_small", "estimate_full", "build_f1", "build_five", "batched", "scale",
-                             "partition", "offline_sample", "cached", "star17"],
+                             "partition", "offline_sample", "cached", "star17", "shapes"],
                     help="run one small profiling case instead of the benchmark (for ncu captures)")
     return ap.parse_args()
 
@@ -1144,12 +1144,60 @@ def run_cached(a):
           flush=True)
 
 
+def run_shapes(a):
+    """Estimate launch shapes on the batched-enumeration graph set (64 graphs, 381,253
+    sub-plans, d = 11, w = 1024), every sub-plan in one plan with both reuse flags: threads
+    per CTA, resident CTAs per SM and conditioning values per item.  CUDA-event medians of 3
+    after one warm-up; every shape's outputs compared bit for bit with the first."""
+    import torch
+
+    from paper_2102_02440_gb300 import compass as K
+    from paper_2102_02440_gb300 import datagen as G
+    from paper_2102_02440_gb300 import pipeline as P
+    graphs = G.graph_batch(64, 4, 17, rows_lo=10_000, rows_hi=1_000_000, d=11, w=1024)
+    gb = P.GraphBatch(graphs)
+    sg, sm = [], []
+    for gi, g in enumerate(graphs):
+        ms = G.connected_subplans(len(g.tables), g.edge_u, g.edge_v)
+        sg += [gi] * len(ms)
+        sm += ms
+    gb.build_batched()
+    gb.presort()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flags = K.CMP_EST_CACHE_MESSAGES | K.CMP_EST_STAR_LATTICE
+    out, ref = [], None
+    for th, cps, ch in ((1024, 1, 64), (256, 4, 64), (256, 4, 16), (512, 1, 64), (256, 2, 64)):
+        plan = gb.plan(sg, sm, K.cmp_estimate_cfg.make(threads=th, ctas_per_sm=cps, cond_chunk=ch, flags=flags))
+        plan.run()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            s.record()
+            plan.run()
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        r = {"threads": th, "ctas_per_sm": cps, "cond_chunk": ch, "ms": statistics.median(ts),
+             "subplans_per_s": len(sm) / (statistics.median(ts) / 1e3)}
+        if ref is None:
+            ref = plan
+        else:
+            ok = ~torch.isnan(ref.est)
+            r["identical"] = bool(torch.equal(torch.isnan(ref.est), torch.isnan(plan.est)) and
+                                  torch.equal(ref.est[ok], plan.est[ok]) and torch.equal(ref.row_est[ok], plan.row_est[ok]))
+        out.append(r)
+    gb.dw.status.zero_()
+    print(json.dumps({"case": "estimate launch shapes", "subplans": len(sm), "shapes": out}), flush=True)
+
+
 def main():
     a = _args()
     if a.case == "batched":
         run_batched(a)
     elif a.case == "cached":
         run_cached(a)
+    elif a.case == "shapes":
+        run_shapes(a)
     elif a.case == "scale":
         run_scale(a)
     elif a.case == "partition":

@@ -34,6 +34,8 @@ ESTIMATE_CANDIDATES = [
     dict(threads=512, ctas_per_sm=4, cond_chunk=64),
     dict(threads=1024, ctas_per_sm=1, cond_chunk=16),
     dict(threads=1024, ctas_per_sm=1, cond_chunk=256),
+    dict(threads=256, ctas_per_sm=4, cond_chunk=64),
+    dict(threads=256, ctas_per_sm=4, cond_chunk=16),
 ]
 
 

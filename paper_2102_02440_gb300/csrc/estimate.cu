@@ -352,9 +352,9 @@ constexpr int kMaxIn = CMP_MAX_SKETCHES;
 constexpr int kMaxPreChunk = 256;  // conditioning values per item whose scalars the prologue precomputes
 
 // kIlp elements per thread have their loads issued together (memory-level parallelism);
-// MAXT is the launch bound that sets the register budget.
-template <typename S, int kIlp, int MAXT>
-__global__ void __launch_bounds__(MAXT) k_estimate_items(const __grid_constant__ EstArgs A, int retry, int64_t it0,
+// MAXT and MINB (resident CTAs per SM) are the launch bounds that set the register budget.
+template <typename S, int kIlp, int MAXT, int MINB = 1>
+__global__ void __launch_bounds__(MAXT, MINB) k_estimate_items(const __grid_constant__ EstArgs A, int retry, int64_t it0,
                                                          int64_t it1) {
   __shared__ i128 sh_i128[33];
   __shared__ int32_t sh_flag[1];
@@ -807,11 +807,14 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_estimate_finalize(const __
 
 cudaError_t launch_estimate(const EstArgs& a, const EstPlanHdr& H, double* est, int64_t* row_est, cudaStream_t st) {
   // cached subtree messages, one launch per level, in int128 storage
+  // three register budgets: 1024 threads (one CTA per SM), 512 (wider ILP), 256 (four CTAs
+  // per SM: more items in flight when each is bound by its barriers, e.g. conditioned cycles)
   int64_t lo = 0;
   for (int l = 0; l < H.n_levels; l++) {
     const int64_t hi = H.lvl_end[l];
     if (a.threads > 512) k_estimate_items<i128, 1, 1024><<<a.grid, a.threads, 0, st>>>(a, 0, lo, hi);
-    else k_estimate_items<i128, 2, 512><<<a.grid, a.threads, 0, st>>>(a, 0, lo, hi);
+    else if (a.threads > 256) k_estimate_items<i128, 2, 512><<<a.grid, a.threads, 0, st>>>(a, 0, lo, hi);
+    else k_estimate_items<i128, 1, 256, 4><<<a.grid, a.threads, 0, st>>>(a, 0, lo, hi);
     lo = hi;
   }
   if (a.n_gen_items > a.n_job_items) {
@@ -820,9 +823,12 @@ cudaError_t launch_estimate(const EstArgs& a, const EstPlanHdr& H, double* est, 
     if (a.threads > 512) {
       k_estimate_items<int64_t, 2, 1024><<<a.grid, a.threads, 0, st>>>(a, 0, b, e);
       k_estimate_items<i128, 1, 1024><<<a.grid, a.threads, 0, st>>>(a, 1, b, e);
-    } else {
+    } else if (a.threads > 256) {
       k_estimate_items<int64_t, 4, 512><<<a.grid, a.threads, 0, st>>>(a, 0, b, e);
       k_estimate_items<i128, 2, 512><<<a.grid, a.threads, 0, st>>>(a, 1, b, e);
+    } else {
+      k_estimate_items<int64_t, 2, 256, 4><<<a.grid, a.threads, 0, st>>>(a, 0, b, e);
+      k_estimate_items<i128, 1, 256, 4><<<a.grid, a.threads, 0, st>>>(a, 1, b, e);
     }
   }
   {

@@ -92,6 +92,44 @@ def test_random_graphs_all_connected_subplans(orc, name, w):
     _check(orc, dw, est, masks, brute=(w == 3 and len(eu) <= 5))
 
 
+@pytest.mark.parametrize("shape", [dict(threads=256, ctas_per_sm=4), dict(threads=256, ctas_per_sm=4, cond_chunk=16),
+                                   dict(threads=128, ctas_per_sm=8, cond_chunk=7), dict(threads=512, ctas_per_sm=1),
+                                   dict(threads=1024, ctas_per_sm=2, cond_chunk=300)])
+def test_launch_shapes_give_identical_estimates(orc, shape):
+    """Every launch shape (the 1024-, 512- and 256-thread register budgets, ragged conditioning
+    chunks) gives the same exact rows on cycles of 4 to 7 tables, trees and the cached
+    messages, equal to the oracle."""
+    rng = np.random.default_rng(31)
+    wls = [G.random_graph_workload(rng, n, 1, 50, 1500, 200, d=3, w=97, pred_prob=0.3, hash_seed=n) for n in (4, 7)]
+    eu, ev = [0, 1, 2, 3, 4, 5], [1, 2, 3, 4, 5, 0]
+    tabs = []
+    for t in range(6):
+        n = int(rng.integers(50, 1500))
+        cols, kc, ei = [], [], []
+        for e in range(6):
+            if eu[e] == t or ev[e] == t:
+                cols.append(G.zipf_keys(rng, n, 200, 1.0))
+                kc.append(len(cols) - 1)
+                ei.append(e)
+        tabs.append(G.Table(f"C{t}", cols, [], kc, ei))
+    wls.append(G.Workload("cycle6", tabs, eu, ev, 3, 97, 5, 0))
+    for wl in wls:
+        dw = P.DeviceWorkload(wl)
+        dw.build()
+        masks = G.connected_subplans(len(wl.tables), wl.edge_u, wl.edge_v)
+        ref = P.DeviceEstimator(dw, masks)
+        ref.presort()
+        ref.estimate()
+        cfg = K.cmp_estimate_cfg.make(flags=K.CMP_EST_CACHE_MESSAGES, **shape)
+        est = P.DeviceEstimator(dw, masks, cfg=cfg)
+        est.presort()
+        est.estimate()
+        torch.cuda.synchronize()
+        dw.check_status()
+        assert torch.equal(est.row_est, ref.row_est) and torch.equal(est.est, ref.est)
+        _check(orc, dw, est, masks)
+
+
 def test_two_way_full_size_workload(orc):
     wl = G.two_way()
     dw = P.DeviceWorkload(wl)
