@@ -776,8 +776,11 @@ def run_batched(a):
     gb.build_batched()
     gb.presort()
     # one plan over every sub-plan, with the reuse across sub-plans on (cached subtree
-    # messages and the star lattice); the per-sub-plan comparison plans one sub-plan each
-    reuse = K.cmp_estimate_cfg.make(flags=K.CMP_EST_CACHE_MESSAGES | K.CMP_EST_STAR_LATTICE)
+    # messages and the star lattice) and the launch shape `--case shapes` measured fastest
+    # here (256 threads, four CTAs per SM, 16 conditioning values per item); the
+    # per-sub-plan comparison plans one sub-plan each
+    reuse = K.cmp_estimate_cfg.make(threads=256, ctas_per_sm=4, cond_chunk=16,
+                                    flags=K.CMP_EST_CACHE_MESSAGES | K.CMP_EST_STAR_LATTICE)
     plan = gb.plan(sg, sm, reuse)
     ms_est_b = timed(plan.run, 3)
     rng = np.random.default_rng(0)
@@ -820,7 +823,8 @@ def run_batched(a):
             "subplans": int(sm.size), "d": 11, "w": 1024,
             "build_ms": {"batched_one_launch": ms_build_b, "per_table_launches": ms_build_t,
                          "speedup": ms_build_t / ms_build_b},
-            "estimate": {"flags": "CMP_EST_CACHE_MESSAGES | CMP_EST_STAR_LATTICE",
+            "estimate": {"flags": "CMP_EST_CACHE_MESSAGES | CMP_EST_STAR_LATTICE", "threads": 256,
+                         "ctas_per_sm": 4, "cond_chunk": 16,
                          "batched_one_plan_ms": ms_est_b, "batched_subplans_per_s": sm.size / (ms_est_b / 1e3),
                          "per_subplan_launches_subplans_per_s": samp.size / (ms_est_1 / 1e3),
                          "per_subplan_sample": int(samp.size),
