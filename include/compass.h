@@ -511,8 +511,10 @@ cmp_status cmp_mlp_train_step(float* params_dev, float* adam_m_dev, float* adam_
  * Arguments and results are those of cmp_estimate for the same plan.
  *   Workspace: a fixed array of CMP_NOALLOC_WS_BYTES bytes inside the library's device
  *   image, held by every GPU that loads the library until the process exits.  The
- *   library allocates and frees nothing at call time.  The plan's per-item partial sums
- *   must fit in it together with at least one CTA's scratch, else CMP_EWORKSPACE;
+ *   library allocates and frees nothing at call time.  The plan's per-item partial sums,
+ *   and its cached messages and star lattices (CMP_EST_CACHE_MESSAGES,
+ *   CMP_EST_STAR_LATTICE), must fit in it together with at least one CTA's scratch, else
+ *   CMP_EWORKSPACE;
  *   the persistent grid shrinks to the number of CTA scratch areas that fit, so a large
  *   plan runs with fewer CTAs than cmp_estimate would use.
  *   Set-up: the first call on each device looks up the array's device address (with
