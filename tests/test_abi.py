@@ -290,6 +290,41 @@ def test_estimate_plan_star_families(K):
     assert st.n_star == 0 and st.n_jobs == 21
 
 
+def test_estimate_plan_reuse_flags_on_random_graphs(K):
+    """Both reuse flags on random graphs with parallel edges and extra cycles, every connected
+    sub-plan or a random subset of them: planning succeeds or fails exactly as without the
+    flags; with them the sub-plan count is unchanged, operations never grow, and every
+    sub-plan is a single table, a star of a family, or has its own items."""
+    from paper_2102_02440_gb300 import datagen as G
+    rng = np.random.default_rng(5)
+    both = K.CMP_EST_CACHE_MESSAGES | K.CMP_EST_STAR_LATTICE
+    for trial in range(12):
+        nt = int(rng.integers(3, 9))
+        eu, ev = [], []
+        for t in range(1, nt):
+            eu.append(int(rng.integers(0, t)))
+            ev.append(t)
+        for _ in range(int(rng.integers(0, 2))):
+            u, v = rng.choice(nt, 2, replace=False)
+            eu.append(int(u))
+            ev.append(int(v))
+        g = _graph(K, eu, ev, nt)
+        sm = G.connected_subplans(nt, eu, ev)
+        if trial % 2:
+            sm = [m for m in sm if rng.random() < 0.5] or sm[:1]
+        try:
+            plain, _ = _plan_stats(K, [g], 3, 64, [0] * len(sm), sm)
+        except K.CompassError as e:
+            with pytest.raises(K.CompassError) as ei:
+                _plan_stats(K, [g], 3, 64, [0] * len(sm), sm, both)
+            assert ei.value.status == e.status
+            continue
+        reuse, _ = _plan_stats(K, [g], 3, 64, [0] * len(sm), sm, both)
+        assert reuse.n_sub == plain.n_sub == len(sm)
+        assert reuse.n_ops <= plain.n_ops and reuse.n_star_sub <= len(sm)
+        assert reuse.n_job_items == 3 * reuse.n_jobs
+
+
 def test_cross_ranks_multi_rejections(K):
     ks = (C.c_int32 * 2)(2, 17)
     e = (C.c_int32 * 19)(*range(19))
