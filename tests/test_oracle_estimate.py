@@ -287,3 +287,39 @@ def test_star_regrouping_equals_the_merged_contraction(orc):
         if n_leaves == 4:
             assert orc.estimate(eu, ev, sketches, surv, 2, w, full, brute=True).rows == \
                 _star_regrouped(centre, leaf, list(range(n_leaves)))
+
+
+def _merge2(x, y):
+    """Merged 2-D sketch of a table with sketches x (lower edge id) and y (Sec. 4.2): the value
+    of smaller magnitude, x on ties."""
+    X, Y = np.meshgrid(x.astype(np.int64), y.astype(np.int64), indexing="ij")
+    return np.where(np.abs(X) <= np.abs(Y), X, Y).astype(object)
+
+
+def test_subtree_message_is_shared_by_the_sub_plans_containing_it(orc):
+    """The reading behind cached messages: on the chain 0-1-2-3-4 (edge i joins i and i+1), the
+    message of the subtree {2, 3, 4} over edge 1 (its merged sketches contracted with each other,
+    one value per bucket of table 2's sketch on edge 1) is the same array inside every sub-plan
+    that contains the subtree.  Built once from the definition, it gives the oracle's exact row
+    estimates of both {1, 2, 3, 4} and {0, 1, 2, 3, 4}."""
+    rng = np.random.default_rng(23)
+    w, n = 5, 5
+    eu, ev = list(range(n - 1)), list(range(1, n))
+    # sk[t][e]: table t's sketch on edge e (one row)
+    sk = {t: {} for t in range(n)}
+    for e in range(n - 1):
+        sk[e][e] = _sk(rng, 1, w, -4, 5)[0]
+        sk[e + 1][e] = _sk(rng, 1, w, -4, 5)[0]
+    sketches = [(sk[e][e][None, :], sk[e + 1][e][None, :]) for e in range(n - 1)]
+    surv = [1] * n
+    # message of {3, 4} over edge 2, then of {2, 3, 4} over edge 1, bucket by bucket
+    m34 = np.array([sum(int(v) for v in _merge2(sk[3][2], sk[3][3])[j] * sk[4][3].astype(object))
+                    for j in range(w)], dtype=object)
+    m234 = np.array([sum(_merge2(sk[2][1], sk[2][2])[j] * m34) for j in range(w)], dtype=object)
+    # {1, 2, 3, 4}: table 1 is a leaf on edge 1
+    want1 = orc.estimate(eu, ev, sketches, surv, 1, w, 0b11110).rows[0]
+    assert int(sum(sk[1][1].astype(object) * m234)) == want1
+    # {0, 1, 2, 3, 4}: table 1 merges edges 0 and 1, table 0 is a leaf on edge 0
+    m1 = _merge2(sk[1][0], sk[1][1])
+    got = sum(int(sk[0][0][i]) * int(sum(m1[i] * m234)) for i in range(w))
+    assert got == orc.estimate(eu, ev, sketches, surv, 1, w, 0b11111).rows[0]
