@@ -511,12 +511,16 @@ cmp_status cmp_mlp_train_step(float* params_dev, float* adam_m_dev, float* adam_
  * Arguments and results are those of cmp_estimate for the same plan.
  *   Workspace: a fixed array of CMP_NOALLOC_WS_BYTES bytes inside the library's device
  *   image, held by every GPU that loads the library until the process exits.  The
- *   library allocates and frees nothing at call time.  The plan's per-item partial sums,
- *   and its cached messages and star lattices (CMP_EST_CACHE_MESSAGES,
- *   CMP_EST_STAR_LATTICE), must fit in it together with at least one CTA's scratch, else
- *   CMP_EWORKSPACE;
- *   the persistent grid shrinks to the number of CTA scratch areas that fit, so a large
- *   plan runs with fewer CTAs than cmp_estimate would use.
+ *   library allocates and frees nothing at call time.  The array holds, in this order,
+ *   the plan's fixed part (per-item partial sums, and the cached messages and star
+ *   lattices of CMP_EST_CACHE_MESSAGES / CMP_EST_STAR_LATTICE), the generic kernel's
+ *   per-CTA scratch areas (always at least one), and the scratch of triangle rows (one
+ *   row = one triangle sub-plan on one sketch row).  A plan is rejected with
+ *   CMP_EWORKSPACE unless fixed part + one CTA scratch area + one triangle row (when the
+ *   plan has triangle sub-plans) fit.  Beyond that, the persistent grid shrinks to the
+ *   number of CTA scratch areas that fit next to one triangle row, so a large plan runs
+ *   with fewer CTAs than cmp_estimate would use, and the triangle rows that do not fit
+ *   in the rest run in successive waves of launches on the same stream.
  *   Set-up: the first call on each device looks up the array's device address (with
  *   that device current) and caches it; make that first call before any stream capture.
  *   Sharing: every call, on any stream, uses the same array.  Nothing in it needs to

@@ -45,21 +45,24 @@ extern "C" cmp_status cmp_estimate_noalloc(const void* plan_host, const void* pl
   std::memcpy(&H, plan_host, sizeof(H));
   if (H.magic != kEstPlanMagic || H.version != kEstPlanVersion) return CMP_EINVAL;
   if (H.n_sub > 0 && !est_dev) return CMP_EINVAL;
-  // per-item partial sums, then as many generic per-CTA scratch areas and triangle rows
-  // as fit (at least one of each that the plan uses); triangle rows beyond that run in waves
+  // Layout (est_args): per-item partial sums and caches, then `grid` generic per-CTA
+  // scratch areas, then `slots` triangle rows.  est_args places the triangle rows after
+  // grid >= 1 CTA areas whether or not the plan has generic items, so one CTA area is
+  // always reserved; triangle rows beyond what fits run in successive waves.
   const size_t cap = size_t(CMP_NOALLOC_WS_BYTES), fixed = est_fixed_bytes(H);
-  const size_t per_cta = H.n_gen_items > 0 ? size_t(H.scratch_per_cta) : 0;
+  const size_t per_cta = size_t(H.scratch_per_cta);
   const size_t per_tri = H.n_tri > 0 ? size_t(H.tri_row_bytes) : 0;
   if (fixed + per_cta + per_tri > cap) return CMP_EWORKSPACE;
-  int64_t grid = H.grid;
-  if (per_cta) grid = std::min<int64_t>(grid, int64_t((cap - fixed - per_tri) / per_cta));
+  int64_t grid = std::max<int64_t>(1, H.grid);
+  if (per_cta) grid = std::max<int64_t>(1, std::min<int64_t>(grid, int64_t((cap - fixed - per_tri) / per_cta)));
   int64_t slots = 0;
   if (per_tri) slots = std::min<int64_t>(H.n_tri * H.d, int64_t((cap - fixed - per_cta * size_t(grid)) / per_tri));
+  if (est_ws_bytes(H, grid, slots) > cap || (per_tri && slots < 1)) return CMP_EWORKSPACE;
   void* ws_v = nullptr;
   const cmp_status st = workspace_address(&ws_v);
   if (st != CMP_OK) return st;
   const EstArgs a = est_args(H, static_cast<const unsigned char*>(plan_dev), static_cast<unsigned char*>(ws_v),
-                             int32_t(grid > 0 ? grid : 1), slots, status_dev);
+                             int32_t(grid), slots, status_dev);
   return launch_estimate(a, H, est_dev, row_est_dev, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? CMP_OK
                                                                                                           : CMP_ECUDA;
 }
