@@ -844,7 +844,8 @@ def run_scale(a):
 
     from paper_2102_02440_gb300 import datagen as G
     from paper_2102_02440_gb300 import pipeline as P
-    wl = G.scale_workload_device()
+    f = a.scale
+    wl = G.scale_workload_device(n_fact=int(1e9 * f), n_d1=int(1e8 * f), n_d2=max(int(1e6 * min(f, 1.0)), 1000))
     dw = P.DeviceWorkload(wl)
     masks = G.connected_subplans(3, wl.edge_u, wl.edge_v)
     est = P.DeviceEstimator(dw, masks)

@@ -46,11 +46,24 @@ typedef int32_t cmp_status;
 enum { CMP_I32 = 0, CMP_I64 = 1 };                       /* column element types */
 enum { CMP_RANGE = 0, CMP_EQ = 1, CMP_IN_BITMAP = 2 };  /* predicate operators  */
 
-/* One column: `data` is a device pointer to n_rows elements of `dtype`. */
+/* One column: `data` is a device pointer to n_rows elements of `dtype`.  `flags`
+ * declares what the caller knows about a key column, as a catalog would; both are
+ * performance hints, and the sketches are the same whether they hold or not:
+ *   CMP_COL_UNIQUE  the values are distinct (a primary key).  The batched build hashes
+ *                   the column once per surviving row with the counters in shared memory
+ *                   (no per-key counting, which cannot merge anything here).
+ *   CMP_COL_DOMAIN  the values lie in [dom_lo, dom_hi) (e.g. a foreign key's referenced
+ *                   key range).  Key aggregation sizes its count array to that range.  If
+ *                   a surviving value lies outside it, the column is hashed per row in
+ *                   the same build. */
+#define CMP_COL_UNIQUE 1
+#define CMP_COL_DOMAIN 2
 typedef struct {
   const void* data;
   int32_t dtype;
-  int32_t reserved;
+  int32_t flags;   /* CMP_COL_UNIQUE | CMP_COL_DOMAIN, or 0 */
+  int64_t dom_lo;  /* CMP_COL_DOMAIN: first value of the declared range */
+  int64_t dom_hi;  /* CMP_COL_DOMAIN: one past its last value */
 } cmp_col;
 
 /* One conjunct of a table's selection (Sec. 2, "Partitioned query execution": the
@@ -119,13 +132,14 @@ typedef struct {
   int32_t aggregate;      /* batched build only: -1 auto (tables of >= 2^18 rows), 0 off, 1 every
                              table: aggregate each key column's survivors per distinct key before
                              hashing (needs dedupe; same counters)                                  */
-  int32_t reserved;
+  int32_t unique;         /* batched build only: 0 or 1 on, -1 off: key columns declared
+                             CMP_COL_UNIQUE are hashed once per row with shared-memory counters  */
 } cmp_build_cfg;
 
 /* ---------------------------------------------------------------------- general */
 
 /* Version of this interface (CMP_ABI_VERSION); bindings refuse a library that differs. */
-#define CMP_ABI_VERSION 5
+#define CMP_ABI_VERSION 6
 int32_t cmp_abi_version(void);
 const char* cmp_status_str(cmp_status s);
 
@@ -167,12 +181,19 @@ cmp_status cmp_sketch_build(const cmp_table* table, int32_t d, int32_t w, const 
  *                      reports (0 when no key column is aggregated; NULL allowed then),
  *                      caller-owned, contents irrelevant between calls
  * Key aggregation (cfg->aggregate): the survivors of each key column of a large table
- * are first counted per distinct key (dense count array over [min key, max key], found
- * on the device), then each distinct key is hashed once per (sketch, row) with its count
- * as the multiplier.  The update is linear and the counters wrap exactly, so the result
- * is bit-identical to one update per tuple; a column whose key range exceeds
- * min(rows, 2^27) falls back to the per-row path at run time.  This adds three small
- * launches (key range, clearing, counting) before the build kernel.
+ * that is not declared unique are first counted per distinct key, then each distinct key
+ * is hashed once per (sketch, row) with its count as the multiplier.  The count array
+ * covers the column's declared domain (CMP_COL_DOMAIN, at most 2^27 values), else the
+ * power of two at or above min(rows, 2^27), indexed by the key modulo its size; the
+ * counting pass also finds the surviving keys' range.  The update is linear and the
+ * counters wrap exactly, so the result is bit-identical to one update per tuple; a column
+ * whose surviving keys span more values than its array (or leave its declared domain)
+ * falls back to the per-row path in the same build.  Key columns declared unique
+ * (CMP_COL_UNIQUE, cfg->unique) are hashed once per surviving row by a kernel that keeps
+ * one or more (sketch, row) pairs' counters in shared memory: int32, or two 16-bit halves
+ * per word with every carry and borrow added to the global counter, so the counters stay
+ * exact.  Launches: zeroing, then (when present) clearing + counting, the unique-key
+ * kernel, the row kernel and the hashing of the counted keys.
  * cmp_build_plan_encode returns CMP_EWORKSPACE if plan_bytes is too small;
  * cmp_sketch_build_batched returns CMP_EWORKSPACE if ws_bytes is. */
 cmp_status cmp_build_plan_bytes(const cmp_table* tables, int32_t n_tables, int32_t d, int32_t w,

@@ -18,7 +18,7 @@ CMP_RANGE, CMP_EQ, CMP_IN_BITMAP = 0, 1, 2
 CMP_EST_GENERIC_ONLY = 1
 CMP_EST_CACHE_MESSAGES = 2
 CMP_EST_STAR_LATTICE = 4
-CMP_ABI_VERSION = 5
+CMP_ABI_VERSION = 6
 CMP_PART_MAX_AXES = 4
 CMP_MAX_COLS, CMP_MAX_PREDS, CMP_MAX_SKETCHES, CMP_MAX_D = 32, 8, 16, 64
 
@@ -29,8 +29,13 @@ class CompassError(RuntimeError):
         self.status = status
 
 
+CMP_COL_UNIQUE = 1
+CMP_COL_DOMAIN = 2
+
+
 class cmp_col(C.Structure):
-    _fields_ = [("data", C.c_void_p), ("dtype", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("data", C.c_void_p), ("dtype", C.c_int32), ("flags", C.c_int32), ("dom_lo", C.c_int64),
+                ("dom_hi", C.c_int64)]
 
 
 class cmp_pred(C.Structure):
@@ -52,11 +57,12 @@ class cmp_table(C.Structure):
 class cmp_build_cfg(C.Structure):
     _fields_ = [("mode", C.c_int32), ("pairs_per_slab", C.c_int32), ("threads", C.c_int32),
                 ("tile_rows", C.c_int32), ("dedupe", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("aggregate", C.c_int32), ("reserved", C.c_int32)]
+                ("aggregate", C.c_int32), ("unique", C.c_int32)]
 
     @classmethod
-    def make(cls, mode=0, pairs_per_slab=0, threads=0, tile_rows=0, dedupe=-1, ctas_per_sm=0, aggregate=-1):
-        return cls(mode, pairs_per_slab, threads, tile_rows, dedupe, ctas_per_sm, aggregate, 0)
+    def make(cls, mode=0, pairs_per_slab=0, threads=0, tile_rows=0, dedupe=-1, ctas_per_sm=0, aggregate=-1,
+             unique=0):
+        return cls(mode, pairs_per_slab, threads, tile_rows, dedupe, ctas_per_sm, aggregate, unique)
 
 
 class cmp_estimate_plan_info(C.Structure):

@@ -45,6 +45,8 @@ cmp_status check_table(const cmp_table* t, int32_t d, int32_t w, int32_t n_edges
   for (int c = 0; c < t->n_cols; c++) {
     if (t->cols[c].dtype != CMP_I32 && t->cols[c].dtype != CMP_I64) return CMP_EINVAL;
     if (t->n_rows > 0 && !t->cols[c].data) return CMP_EINVAL;
+    if (t->cols[c].flags & ~(CMP_COL_UNIQUE | CMP_COL_DOMAIN)) return CMP_EINVAL;
+    if ((t->cols[c].flags & CMP_COL_DOMAIN) && !(t->cols[c].dom_lo < t->cols[c].dom_hi)) return CMP_EINVAL;
   }
   for (int q = 0; q < t->n_preds; q++) {
     const cmp_pred& p = t->preds[q];
@@ -248,8 +250,20 @@ cmp_status cmp_sketch_build(const cmp_table* table, int32_t d, int32_t w, const 
 constexpr int64_t kAggMinRows = int64_t(1) << 18;
 constexpr int64_t kAggMaxCap = int64_t(1) << 27;
 
+// Unique-key kernel: shared-memory budget of a slab's counters (room is left on the SM for
+// a CTA of the counting pass), rows per tile.
+constexpr size_t kUniqSmemBudget = size_t(128) << 10;
+constexpr int32_t kUniqTileRows = 4096;
+constexpr int32_t kUniqThreadsHost = 512;
+
 struct BuildPlanParts {
   BuildShape shape;
+  std::vector<UniqSlab> uslabs;
+  std::vector<UniqItem> uitems;
+  std::vector<int32_t> u_cta_item;  // [u_grid + 1]
+  int32_t u_pack16 = 0, u_words = 0;
+  std::vector<uint32_t> uniq_mask;  // [table]
+  std::vector<int32_t> surv_by;     // [table]
   std::vector<BuildItem> items;
   std::vector<int32_t> cta_item;
   std::vector<AggCol> aggs;
@@ -260,9 +274,14 @@ struct BuildPlanParts {
   int32_t hash_max_pairs = 1, hash_grid = 0;
   std::vector<std::vector<int32_t>> col_agg;  // [table][col] AggCol index or -1
   size_t bytes = 0, ws_bytes = 0;
-  int32_t stat_grid = 0;
   int32_t cache_slots = 256, cache_cols = 0;  // counting pass
 };
+
+static uint64_t next_pow2_64(uint64_t v) {
+  uint64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
 
 static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -283,27 +302,49 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
   if (agg_mode == 1 && !s.dedupe) return CMP_EINVAL;  // aggregated items use the tile map's entry lists
   const int ctas_per_sm = s.ctas_per_slab;
   const int R = s.tile_rows;
-  // aggregated key columns: every distinct key column of a selected table
+  // Key columns: declared unique -> unique-key kernel (when its slab fits in shared
+  // memory); else aggregated (large tables); else the row kernel.
+  const int uniq_mode = cfg ? cfg->unique : 0;
+  if (uniq_mode < -1 || uniq_mode > 1) return CMP_EINVAL;
+  P->u_pack16 = size_t(w) * 4 > kUniqSmemBudget ? 1 : 0;
+  const bool uniq_fits = size_t(w) * (P->u_pack16 ? 2 : 4) <= kUniqSmemBudget;
+  P->uniq_mask.assign(n_tables, 0u);
+  P->surv_by.assign(n_tables, kSurvRow);
   P->col_agg.assign(n_tables, std::vector<int32_t>(CMP_MAX_COLS, -1));
   P->aggs.clear();
-  size_t ws = al256(16 * size_t(n_tables) * CMP_MAX_SKETCHES + 16);  // stats + chunk counter (upper bound)
+  size_t ws = al256(16 * size_t(n_tables) * CMP_MAX_SKETCHES + 16);  // stats + chunk counters (upper bound)
   for (int32_t t = 0; t < n_tables; t++) {
     const cmp_table& tb = tables[t];
-    const bool on = tb.n_sketches > 0 && tb.n_rows > 0 && s.dedupe &&
-                    (agg_mode == 1 || (agg_mode == -1 && tb.n_rows >= kAggMinRows));
-    if (!on) continue;
+    const bool agg_on = tb.n_sketches > 0 && tb.n_rows > 0 && s.dedupe &&
+                        (agg_mode == 1 || (agg_mode == -1 && tb.n_rows >= kAggMinRows));
     for (int k = 0; k < tb.n_sketches; k++) {
       const int c = tb.key_col[k];
-      if (P->col_agg[t][c] >= 0) continue;
+      const cmp_col& col = tb.cols[c];
+      if (uniq_mode >= 0 && uniq_fits && (col.flags & CMP_COL_UNIQUE)) {
+        P->uniq_mask[t] |= 1u << c;
+        continue;
+      }
+      if (!agg_on || P->col_agg[t][c] >= 0) continue;
       AggCol a;
+      std::memset(&a, 0, sizeof(a));
       a.table = t;
       a.col = c;
-      a.cap = std::min<int64_t>(tb.n_rows, kAggMaxCap);
-      a.off = 0;
-      a.stat_cta0 = a.stat_ncta = 0;
+      const uint64_t dom = (col.flags & CMP_COL_DOMAIN) ? uint64_t(col.dom_hi) - uint64_t(col.dom_lo) : 0;
+      if (dom > 0 && dom <= uint64_t(kAggMaxCap)) {  // the declared domain, slot = key - dom_lo
+        a.cap = int64_t(dom);
+        a.base = col.dom_lo;
+        a.mask = ~0ull;
+      } else {  // a power of two, slot = key mod cap
+        a.cap = int64_t(next_pow2_64(uint64_t(std::min<int64_t>(tb.n_rows, kAggMaxCap))));
+        a.base = 0;
+        a.mask = uint64_t(a.cap) - 1;
+      }
       P->col_agg[t][c] = int32_t(P->aggs.size());
       P->aggs.push_back(a);
     }
+    bool has_agg = false;
+    for (int c = 0; c < CMP_MAX_COLS; c++) has_agg |= P->col_agg[t][c] >= 0;
+    P->surv_by[t] = has_agg ? kSurvCount : (P->uniq_mask[t] ? kSurvUniq : kSurvRow);
   }
   if (P->aggs.size() > size_t(n_tables) * CMP_MAX_SKETCHES) return CMP_EINVAL;
   for (AggCol& a : P->aggs) {
@@ -311,6 +352,92 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
     ws += al256(16 * size_t((a.cap + 3) / 4));  // whole int4 words: the zeroing kernel writes them
   }
   P->ws_bytes = P->aggs.empty() ? 0 : ws;
+  // unique-key slabs and their items: each CTA gets about the same number of tiles; the
+  // slabs of one column (same table, same tiles) get the same row split, so CTAs reading
+  // the same rows run side by side
+  P->uslabs.clear();
+  P->uitems.clear();
+  P->u_cta_item.assign(1, 0);
+  P->u_words = 0;
+  {
+    struct Group {
+      int32_t t, c, first, n;  // slabs [first, first + n)
+      int64_t tiles;
+    };
+    std::vector<Group> groups;
+    int64_t total_tiles = 0;
+    for (int32_t t = 0; t < n_tables; t++) {
+      const cmp_table& tb = tables[t];
+      if (!P->uniq_mask[t] || tb.n_rows == 0) continue;
+      const int64_t tiles = (tb.n_rows + kUniqTileRows - 1) / kUniqTileRows;
+      for (int c = 0; c < tb.n_cols; c++) {
+        if (!((P->uniq_mask[t] >> c) & 1u)) continue;
+        std::vector<int32_t> pairs;
+        for (int k = 0; k < tb.n_sketches; k++)
+          if (tb.key_col[k] == c)
+            for (int i = 0; i < d; i++) pairs.push_back(k * d + i);
+        const int max_pps = P->u_pack16 ? 1
+                                         : int(std::max<size_t>(1, std::min<size_t>(kUniqMaxPairs,
+                                                                                    kUniqSmemBudget / (size_t(w) * 4))));
+        const int n_sl = int((pairs.size() + max_pps - 1) / max_pps);
+        const int pps = int((pairs.size() + n_sl - 1) / n_sl);
+        Group g{t, c, int32_t(P->uslabs.size()), 0, tiles};
+        for (size_t b = 0; b < pairs.size(); b += pps) {
+          UniqSlab sl;
+          std::memset(&sl, 0, sizeof(sl));
+          sl.table = t;
+          sl.col = c;
+          sl.n_pairs = int32_t(std::min(pairs.size() - b, size_t(pps)));
+          for (int q = 0; q < sl.n_pairs; q++) sl.pair[q] = pairs[b + q];
+          P->u_words = std::max<int32_t>(P->u_words, P->u_pack16 ? int32_t((w + 1) / 2) : sl.n_pairs * w);
+          P->uslabs.push_back(sl);
+          g.n++;
+        }
+        total_tiles += tiles * g.n;
+        groups.push_back(g);
+      }
+    }
+    if (!groups.empty()) {
+      const double avg = std::max(1.0, double(total_tiles) / double(sm_count()));
+      std::vector<bool> counted(n_tables, false);
+      auto add_item = [&](int32_t slab, int64_t rb, int64_t re) {
+        UniqItem it;
+        it.slab = slab;
+        it.count_surv = 0;
+        it.row_begin = rb;
+        it.row_end = re;
+        P->uitems.push_back(it);
+      };
+      for (const Group& g : groups) {
+        const int64_t rows = tables[g.t].n_rows;
+        const bool count_first = P->surv_by[g.t] == kSurvUniq && !counted[g.t];
+        if (double(g.tiles) >= 0.5 * avg) {
+          // every slab split into n equal row ranges, one CTA each
+          const int64_t n = std::max<int64_t>(1, std::min<int64_t>(g.tiles, int64_t(double(g.tiles) / avg + 0.5)));
+          for (int32_t k = 0; k < g.n; k++)
+            for (int64_t j = 0; j < n; j++) {
+              const int64_t tb0 = g.tiles * j / n, tb1 = g.tiles * (j + 1) / n;
+              add_item(g.first + k, tb0 * kUniqTileRows, std::min(rows, tb1 * kUniqTileRows));
+              P->uitems.back().count_surv = (count_first && k == 0) ? 1 : 0;
+              P->u_cta_item.push_back(int32_t(P->uitems.size()));
+            }
+        } else {
+          // whole slabs packed into CTAs of about avg tiles
+          int64_t acc = 0;
+          for (int32_t k = 0; k < g.n; k++) {
+            add_item(g.first + k, 0, rows);
+            P->uitems.back().count_surv = (count_first && k == 0) ? 1 : 0;
+            acc += g.tiles;
+            if (double(acc) >= avg || k == g.n - 1) {
+              P->u_cta_item.push_back(int32_t(P->uitems.size()));
+              acc = 0;
+            }
+          }
+        }
+        if (count_first) counted[g.t] = true;
+      }
+    }
+  }
   // work of an item ~ units (tiles or count chunks) * (pairs hashed per unit + 1); CTAs
   // proportional to work, >= 1, <= units.  Aggregated items hash distinct keys only
   // (counted as a quarter of their chunk's slots).
@@ -329,9 +456,17 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
     const int32_t n_slabs = tp ? (tp + s.pairs_per_slab - 1) / s.pairs_per_slab : 1;
     for (int32_t k = 0; k < n_slabs; k++) {
       const int32_t b = k * s.pairs_per_slab, e = std::min(tp, (k + 1) * s.pairs_per_slab);
-      int32_t row_pairs = 0;
-      for (int32_t p = b; p < e; p++)
-        if (P->col_agg[t][tb.key_col[p / d]] < 0) row_pairs++;
+      int32_t row_pairs = 0, agg_pairs = 0;
+      for (int32_t p = b; p < e; p++) {
+        const int c = tb.key_col[p / d];
+        if ((P->uniq_mask[t] >> c) & 1u) continue;
+        if (P->col_agg[t][c] < 0) row_pairs++;
+        else agg_pairs++;
+      }
+      // a slab whose pairs are all hashed by the unique-key kernel, of a table whose
+      // survivors are counted elsewhere, has no work here (aggregated pairs may fall back
+      // to this kernel at run time, so their slabs stay)
+      if (row_pairs == 0 && agg_pairs == 0 && P->surv_by[t] != kSurvRow) continue;
       Raw r{t, b, e, -1, tiles, double(tiles) * double(row_pairs + 1)};
       total += r.work;
       raw.push_back(r);
@@ -380,9 +515,9 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
     P->cnt_total_chunks += ci.n_chunks;
     P->cnt_items.push_back(ci);
   }
-  P->cnt_grid = int32_t(std::min<int64_t>(P->cnt_total_chunks, int64_t(sm_count()) * std::max(1, 2048 / s.threads)));
+  P->cnt_grid = 0;  // set below, once the unique-key items are known
   // hot-key caches of the counting pass: the most aggregated columns of any table (at most
-  // 4 cached), a power-of-two number of slots per column in about 112 KB
+  // 4 cached), a power-of-two number of slots per column in about 64 KB
   {
     int max_ac = 0;
     for (int32_t t = 0; t < n_tables; t++) {
@@ -392,24 +527,12 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
     }
     P->cache_cols = std::min(max_ac, 4);
     int32_t h = 8192;
-    while (P->cache_cols && h > 256 && size_t(h) * 8 * size_t(P->cache_cols) > (size_t(112) << 10)) h >>= 1;
+    while (P->cache_cols && h > 256 && size_t(h) * 8 * size_t(P->cache_cols) > (size_t(64) << 10)) h >>= 1;
     P->cache_slots = P->cache_cols ? h : 256;
   }
-  // key-range pass: CTAs per column in proportion to its rows (about 8 per SM in all)
-  {
-    double rows_total = 0;
-    for (const AggCol& a : P->aggs) rows_total += double(tables[a.table].n_rows);
-    int32_t next = 0;
-    for (AggCol& a : P->aggs) {
-      const int64_t n = tables[a.table].n_rows;
-      int64_t k = int64_t(double(n) / std::max(rows_total, 1.0) * sm_count() * 8 + 0.5);
-      k = std::max<int64_t>(1, std::min<int64_t>(k, (n + 4095) / 4096));
-      a.stat_cta0 = next;
-      a.stat_ncta = int32_t(k);
-      next += int32_t(k);
-    }
-    P->stat_grid = next;
-  }
+  // counting pass: 512-thread CTAs, two per SM; one per SM when the unique-key kernel runs
+  // beside it
+  P->cnt_grid = int32_t(std::min<int64_t>(P->cnt_total_chunks, int64_t(sm_count()) * (P->uitems.empty() ? 2 : 1)));
   s.grid = int32_t(P->cta_item.size());
   s.ctas_per_slab = 0;
   P->shape = s;
@@ -420,6 +543,9 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
   off += align16(sizeof(ZeroSpan) * (n_tables + 1));
   off += align16(sizeof(AggCol) * P->aggs.size());
   off += align16(sizeof(CountItem) * P->cnt_items.size());
+  off += align16(sizeof(UniqSlab) * P->uslabs.size());
+  off += align16(sizeof(UniqItem) * P->uitems.size());
+  off += align16(sizeof(int32_t) * P->u_cta_item.size());
   P->bytes = off;
   return CMP_OK;
 }
@@ -474,9 +600,21 @@ extern "C" cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_t
   h.n_cnt_items = int64_t(P.cnt_items.size());
   h.off_cnt_items = int64_t(off);
   off += align16(sizeof(CountItem) * P.cnt_items.size());
+  h.n_uslab = int64_t(P.uslabs.size());
+  h.off_uslab = int64_t(off);
+  off += align16(sizeof(UniqSlab) * P.uslabs.size());
+  h.n_uitems = int64_t(P.uitems.size());
+  h.off_uitems = int64_t(off);
+  off += align16(sizeof(UniqItem) * P.uitems.size());
+  h.off_u_cta = int64_t(off);
+  off += align16(sizeof(int32_t) * P.u_cta_item.size());
+  h.u_grid = int32_t(P.u_cta_item.size()) - 1;
+  h.u_pack16 = P.u_pack16;
+  h.u_words = P.u_words;
+  h.u_tile_rows = kUniqTileRows;
   h.cnt_total_chunks = P.cnt_total_chunks;
   h.cnt_grid = P.cnt_grid;
-  h.stat_grid = P.stat_grid;
+  h.cnt_threads = 512;
   h.cnt_cache_slots = P.cache_slots;
   h.cnt_cache_cols = P.cache_cols;
   h.hash_total_chunks = P.hash_total_chunks;
@@ -488,6 +626,8 @@ extern "C" cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_t
   for (int32_t t = 0; t < n_tables; t++) {
     DevTable D = to_dev(&tables[t], counters_dev_host[t], survivors_dev + t);
     for (int32_t c = 0; c < CMP_MAX_COLS; c++) D.agg[c] = P.col_agg[t][c];
+    D.uniq_mask = P.uniq_mask[t];
+    D.surv_by = P.surv_by[t];
     std::memcpy(base + h.off_tables + sizeof(DevTable) * t, &D, sizeof(D));
     const int64_t cb = int64_t(tables[t].n_sketches) * d * w * 4;
     if (cb) zs.push_back(ZeroSpan{counters_dev_host[t], cb});
@@ -500,6 +640,9 @@ extern "C" cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_t
   if (!P.aggs.empty()) std::memcpy(base + h.off_agg, P.aggs.data(), sizeof(AggCol) * P.aggs.size());
   if (!P.cnt_items.empty())
     std::memcpy(base + h.off_cnt_items, P.cnt_items.data(), sizeof(CountItem) * P.cnt_items.size());
+  if (!P.uslabs.empty()) std::memcpy(base + h.off_uslab, P.uslabs.data(), sizeof(UniqSlab) * P.uslabs.size());
+  if (!P.uitems.empty()) std::memcpy(base + h.off_uitems, P.uitems.data(), sizeof(UniqItem) * P.uitems.size());
+  std::memcpy(base + h.off_u_cta, P.u_cta_item.data(), sizeof(int32_t) * P.u_cta_item.size());
   std::memcpy(base, &h, sizeof(h));
   return CMP_OK;
 }
@@ -517,7 +660,6 @@ extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void
   cudaStream_t cs = as_stream(stream);
   if (launch_zero_spans(reinterpret_cast<const ZeroSpan*>(dev + h.off_zero), int32_t(h.n_zero), cs) != cudaSuccess)
     return CMP_ECUDA;
-  if (h.shape.grid == 0) return CMP_OK;
   BuildArgs a;
   std::memset(&a, 0, sizeof(a));
   a.tables = reinterpret_cast<const DevTable*>(dev + h.off_tables);
@@ -528,6 +670,12 @@ extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void
   a.d = h.d, a.w = h.w, a.n_edges = h.n_edges;
   a.threads = h.shape.threads, a.tile_rows = h.shape.tile_rows, a.map_slots = h.shape.map_slots;
   a.max_pairs = h.shape.max_pairs, a.smem_pairs = h.shape.smem_pairs;
+  a.uslab = reinterpret_cast<const UniqSlab*>(dev + h.off_uslab);
+  a.uitem = reinterpret_cast<const UniqItem*>(dev + h.off_uitems);
+  a.u_cta_item = reinterpret_cast<const int32_t*>(dev + h.off_u_cta);
+  a.n_uitems = h.n_uitems;
+  a.u_pack16 = h.u_pack16;
+  a.u_words = h.u_words;
   if (h.n_agg > 0) {
     a.agg = reinterpret_cast<const AggCol*>(dev + h.off_agg);
     a.n_agg = int32_t(h.n_agg);
@@ -539,12 +687,15 @@ extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void
     a.hash_max_pairs = h.hash_max_pairs;
     a.cnt_cache_slots = h.cnt_cache_slots;
     a.cnt_cache_cols = h.cnt_cache_cols;
-    // the (max, min) stats start from zero (decoding as an empty column), so do the chunk
-    // counters of the counting and hashing passes after them
+    // the (max, min) key ranges start from zero (decoding as an empty column), so do the
+    // chunk counters of the counting and hashing passes after them
     if (cudaMemsetAsync(ws_dev, 0, 16 * size_t(h.n_agg) + 16, cs) != cudaSuccess) return CMP_ECUDA;
-    if (launch_agg(a, h.shape, h.stat_grid, h.cnt_grid, cs) != cudaSuccess) return CMP_ECUDA;
+    if (launch_agg(a, h.shape.tile_rows, h.cnt_threads, h.cnt_grid, cs) != cudaSuccess) return CMP_ECUDA;
   }
-  if (launch_build(a, h.shape, cs) != cudaSuccess) return CMP_ECUDA;
+  // the unique-key kernel right after the counting pass, as its programmatic dependent:
+  // one CTA of each per SM, the two overlap (memory-bound scan, integer-bound hashing)
+  if (launch_uniq(a, h.u_grid, kUniqThreadsHost, h.u_tile_rows, cs) != cudaSuccess) return CMP_ECUDA;
+  if (h.shape.grid > 0 && launch_build(a, h.shape, cs) != cudaSuccess) return CMP_ECUDA;
   return launch_agg_hash(a, h.n_agg > 0 ? h.hash_grid : 0, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
 }
 

@@ -16,14 +16,14 @@
 //      Sec. 2 "Sketches").
 // The kernel has no inter-CTA waits.
 //
-// Key aggregation (batched build, large tables): before the build kernel, k_agg_stats
-// finds each aggregated key column's smallest and largest key, k_agg_zero clears the
-// used part of its count array, and k_agg_count counts the survivors per key: each CTA
-// keeps a shared-memory cache of the keys it meets first (the frequent keys of a skewed
-// column settle there), counts them there and every other key with one global atomic, and
-// adds its cache to the count arrays at the end.  The build kernel's aggregated items then
-// hash each nonzero (key, count) entry once per pair instead of once per tuple, and its
-// row items skip those columns.
+// Key aggregation (batched build, large tables): before the build kernel, k_agg_zero
+// clears each aggregated key column's count array and k_agg_count counts the survivors
+// per key: each CTA keeps a shared-memory cache of the keys it meets first (the frequent
+// keys of a skewed column settle there), counts them there and every other key with one
+// global atomic, adds its cache to the count arrays at the end, and records the range of
+// the surviving keys.  After the build kernel, k_agg_hash hashes each nonzero (key,
+// count) entry once per pair instead of once per tuple; the build kernel's row items skip
+// those columns.  Columns declared unique are hashed by k_uniq_hash (build_unique.cu).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,23 +71,20 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
     const int total_pairs = tb->n_sketches * A.d;
     pair_end = min(pair_begin + A.pairs_per_slab, total_pairs);
   }
-  // Key columns of the slab not hashed by the aggregated path at run time.  When a table has
-  // an active aggregated column, the counting pass scans all its tiles and counts its
-  // survivors; if every key column of the slab is aggregated, this CTA has nothing to do
-  // (block-uniform: every thread reads the same descriptors).
-  bool row_cols = false, table_agg = false;
-  if (A.agg)
-    for (int c = 0; c < tb->n_cols; c++) {
-      int64_t kmin, range;
-      if (tb->agg[c] >= 0 && agg_active(A.agg[tb->agg[c]], tb->agg[c], A.ws, &kmin, &range)) table_agg = true;
-    }
-  for (int s = pair_begin / A.d; pair_end > pair_begin && s <= (pair_end - 1) / A.d && !row_cols; s++) {
-    const int c = tb->key_col[s];
+  // Key columns of the slab hashed elsewhere: by the unique-key kernel (declared unique),
+  // or by the aggregated path when their counting pass found them in range.  If every key
+  // column of the slab is hashed elsewhere and the survivors are counted elsewhere, this
+  // CTA has nothing to do (block-uniform: every thread reads the same descriptors).
+  auto elsewhere = [&](int c) {
+    if ((tb->uniq_mask >> c) & 1u) return true;
     int64_t kmin, range;
-    if (!(A.agg && tb->agg[c] >= 0 && agg_active(A.agg[tb->agg[c]], tb->agg[c], A.ws, &kmin, &range)))
-      row_cols = true;
-  }
-  if (table_agg && !row_cols) return;
+    return A.agg && tb->agg[c] >= 0 && agg_active(A.agg[tb->agg[c]], tb->agg[c], A.ws, &kmin, &range);
+  };
+  const bool count_here = A.items == nullptr || tb->surv_by == kSurvRow;
+  bool row_cols = false;
+  for (int s = pair_begin / A.d; pair_end > pair_begin && s <= (pair_end - 1) / A.d && !row_cols; s++)
+    if (!elsewhere(tb->key_col[s])) row_cols = true;
+  if (!count_here && !row_cols) return;
   const int npairs = pair_end - pair_begin;
   const int w = A.w;
   const int64_t n_rows = tb->n_rows;
@@ -199,15 +196,12 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
 
       // ---------------- A. predicates and survivor compaction
       const int n_surv = tile_survivors(tb, r0, rows_in_tile, R, vec, surv, sint);
-      if (!table_agg) my_survivors += n_surv;
+      if (count_here) my_survivors += n_surv;
 
       // ---------------- B. per key column: aggregate equal keys, hash, update
       for (int kc = 0; kc < n_keycols; kc++) {
         const int c = cols_list[kc];
-        if (A.agg && tb->agg[c] >= 0) {  // hashed by the column's aggregated items when active
-          int64_t kmin, range;
-          if (agg_active(A.agg[tb->agg[c]], tb->agg[c], A.ws, &kmin, &range)) continue;
-        }
+        if (elsewhere(c)) continue;
         const void* kbase = tb->col[c];
         const int32_t kdt = tb->dtype[c];
         int n_entries = n_surv;
@@ -340,150 +334,89 @@ cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t s
 }
 
 // ---------------------------------------------------------------- key aggregation
-// Smallest and largest key of every aggregated column over all its rows (a bound on the
-// survivors' keys).  Column a is read by CTAs [stat_cta0, stat_cta0 + stat_ncta), each
-// one contiguous slice, four 4-row loads in flight per thread.
-constexpr int kStatThreads = 256;
-
-__global__ void __launch_bounds__(kStatThreads) k_agg_stats(const __grid_constant__ BuildArgs A) {
-  __shared__ long long red[2][kStatThreads / 32];
-  int ai = 0;
-  while (ai + 1 < A.n_agg && A.agg[ai + 1].stat_cta0 <= int(blockIdx.x)) ai++;
-  const AggCol ac = A.agg[ai];
-  const DevTable* tb = A.tables + ac.table;
-  const void* base = tb->col[ac.col];
-  const int32_t dt = tb->dtype[ac.col];
-  const bool vec = tb->vec_ok != 0;
-  const int64_t n = tb->n_rows;
-  const int64_t per = ((n + ac.stat_ncta - 1) / ac.stat_ncta + 15) & ~int64_t(15);  // rows per CTA, x16
-  const int64_t r_begin = min(n, per * (int64_t(blockIdx.x) - ac.stat_cta0)), r_end = min(n, r_begin + per);
-  int64_t mn = INT64_MAX, mx = INT64_MIN;
-  if (dt == CMP_I32 && vec) {  // int32 keys: 32-bit min / max, four 16-byte loads in flight
-    int32_t mn32 = INT32_MAX, mx32 = INT32_MIN;
-    const int32_t* p = reinterpret_cast<const int32_t*>(base);
-    int64_t r = r_begin + 16 * int64_t(threadIdx.x);
-    for (; r + 16 <= r_end; r += 16 * int64_t(blockDim.x)) {
-      int4 q[4];
-#pragma unroll
-      for (int u = 0; u < 4; u++) q[u] = __ldg(reinterpret_cast<const int4*>(p + r) + u);
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        mn32 = min(mn32, min(min(q[u].x, q[u].y), min(q[u].z, q[u].w)));
-        mx32 = max(mx32, max(max(q[u].x, q[u].y), max(q[u].z, q[u].w)));
-      }
-    }
-    if (r < r_end)  // the slice's last partial group of 16 rows (at most one per thread)
-      for (int64_t q = r; q < r_end; q++) {
-        const int32_t x = __ldg(p + q);
-        mn32 = min(mn32, x);
-        mx32 = max(mx32, x);
-      }
-    mn = mn32;
-    mx = mx32;
-  } else
-  for (int64_t r = r_begin + 16 * int64_t(threadIdx.x); r < r_end; r += 16 * int64_t(blockDim.x)) {
-    int64_t v[4][4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const int nvalid = int(max(int64_t(0), min(int64_t(4), r_end - (r + 4 * u))));
-      load4(base, dt, r + 4 * u, nvalid, vec, v[u]);
-#pragma unroll
-      for (int k = 0; k < 4; k++)
-        if (k >= nvalid) v[u][k] = v[0][0];  // padding repeats row r, valid inside the loop
-    }
-#pragma unroll
-    for (int u = 0; u < 4; u++)
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        mn = min(mn, v[u][k]);
-        mx = max(mx, v[u][k]);
-      }
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    mn = min(mn, (int64_t)__shfl_down_sync(0xffffffffu, (long long)mn, off));
-    mx = max(mx, (int64_t)__shfl_down_sync(0xffffffffu, (long long)mx, off));
-  }
-  const int warp = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    red[0][warp] = mn;
-    red[1][warp] = mx;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int q = 1; q < int(blockDim.x >> 5); q++) {
-      mn = min(mn, int64_t(red[0][q]));
-      mx = max(mx, int64_t(red[1][q]));
-    }
-    if (mx >= mn) {
-      unsigned long long* st = reinterpret_cast<unsigned long long*>(A.ws) + 2 * int64_t(ai);
-      atomicMax(st, (unsigned long long)enc_max(mx));
-      atomicMax(st + 1, (unsigned long long)enc_min(mn));
-    }
-  }
-}
-
-// Clears the used part [0, range) of every active column's count array; grid.y = column.
+// Clears every aggregated column's count array (all cap slots: the surviving keys' range
+// is only known after the counting pass); grid.y = column.  Arrays are 256-byte aligned
+// and padded to whole int4 words.
 __global__ void __launch_bounds__(256) k_agg_zero(const __grid_constant__ BuildArgs A) {
-  const int ai = int(blockIdx.y);
-  const AggCol ac = A.agg[ai];
-  int64_t kmin, range;
-  if (!agg_active(ac, ai, A.ws, &kmin, &range)) return;
-  int4* c4 = reinterpret_cast<int4*>(A.ws + ac.off);  // 256-byte aligned
-  const int64_t n4 = (range + 3) / 4;                 // within cap rounded up to 64 entries
+  const AggCol ac = A.agg[blockIdx.y];
+  int4* c4 = reinterpret_cast<int4*>(A.ws + ac.off);
+  const int64_t n4 = (ac.cap + 3) / 4;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x)
     c4[i] = make_int4(0, 0, 0, 0);
 }
 
-// Per tile of a table with aggregated columns: survivors (phase A), then for every active
-// column the tile's keys reduced in a shared-memory map and one global atomic per
-// occupied slot.  A slot packs (key - min) in its high 32 bits and the tile count in its
-// low 32 bits (a count never exceeds the tile's rows), so an insert is one atomic: a CAS
-// that claims an empty slot with the count, or an add to a slot holding the key.  Equal
-// keys of a warp are inserted once, by their lowest lane (__match_any_sync).  The flush
-// also empties the slots, so the map is cleared once per CTA.
-__global__ void __launch_bounds__(1024, 2) k_agg_count(const __grid_constant__ BuildArgs A) {
+// Counting pass of key aggregation.  Persistent CTAs take chunks of 4 tiles of a table's
+// rows in order from an atomic counter.  For every surviving row and every aggregated key
+// column of the table, the key's slot (key - base) & mask gets one count: in the CTA's
+// direct-mapped shared-memory cache when its cache slot holds that slot index or is free
+// (the frequent keys of a skewed column settle there), else with one global atomic on the
+// count array.  Caches are added to the count arrays when the CTA moves to another table
+// or ends.  The pass also records each column's smallest and largest surviving key
+// (thread-local, then warp and CTA reductions, then one global atomic pair per column and
+// table visit), and counts the table's survivors.
+__global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ BuildArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int32_t* acnt[CMP_MAX_SKETCHES];  // the current table's active aggregated columns
-  __shared__ int64_t amin[CMP_MAX_SKETCHES];
-  __shared__ int32_t acol[CMP_MAX_SKETCHES];
+  // The unique-key kernel, launched next as a programmatic dependent, reads nothing this
+  // pass writes: let it start now and share the SMs (this pass waits on memory, that one
+  // on integer arithmetic).
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  __shared__ int32_t* acnt[CMP_MAX_SKETCHES];  // the current table's aggregated columns
+  __shared__ int64_t abase[CMP_MAX_SKETCHES], acap[CMP_MAX_SKETCHES];
+  __shared__ uint64_t amask[CMP_MAX_SKETCHES];
+  __shared__ int32_t acol[CMP_MAX_SKETCHES], aidx[CMP_MAX_SKETCHES];
+  __shared__ unsigned long long amax[CMP_MAX_SKETCHES], amin[CMP_MAX_SKETCHES];  // encoded
   __shared__ int32_t n_ac;
   __shared__ long long next_chunk;
-  const int tid = threadIdx.x, T = blockDim.x;
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
   const int R = A.tile_rows, H = A.cnt_cache_slots, n_cache = A.cnt_cache_cols;
   const int hshift = 32 - (31 - __clz(H));  // H is a power of two >= 256
-  uint32_t* ckey = reinterpret_cast<uint32_t*>(smem);  // [n_cache][H] cached key - min
+  uint32_t* ckey = reinterpret_cast<uint32_t*>(smem);  // [n_cache][H] cached slot index
   uint32_t* ccnt = ckey + size_t(H) * n_cache;          // [n_cache][H] its count so far
   unsigned char* sp = smem + align16(sizeof(uint32_t) * 2 * size_t(H) * n_cache);
   uint16_t* surv = reinterpret_cast<uint16_t*>(sp);
   sp += align16(sizeof(uint16_t) * R);
   int32_t* sint = reinterpret_cast<int32_t*>(sp);
-  constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // never an index: cap <= 2^27
+  constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // never a slot index: cap <= 2^31 - 1
   unsigned long long* work = reinterpret_cast<unsigned long long*>(A.ws) + 2 * int64_t(A.n_agg);
   const int64_t CH = 4 * int64_t(R);  // rows per chunk
 
-  // One surviving key of active column a: its cache slot when that slot holds the key or is
-  // free, else one global atomic on its count-array entry.
+  // One surviving key of column a.  Returns false when the key lies outside the column's
+  // declared domain (its counts are then discarded: the column keeps the per-row path).
   auto count_key = [&](int a, int64_t key) {
-    const uint32_t x = uint32_t(key - amin[a]);  // < range <= cap
+    const uint64_t off = uint64_t(key) - uint64_t(abase[a]);
+    if (amask[a] == ~0ull && off >= uint64_t(acap[a])) return false;
+    const uint32_t x = uint32_t(off & amask[a]);  // < cap
     if (a < n_cache) {
       const size_t slot = size_t(a) * H + ((x * 0x9E3779B1u) >> hshift);
       const uint32_t cur = *reinterpret_cast<volatile uint32_t*>(ckey + slot);
       if (cur == x) {
         atomicAdd(ccnt + slot, 1u);
-        return;
+        return true;
       }
       if (cur == kEmpty) {
         const uint32_t prev = atomicCAS(ckey + slot, kEmpty, x);
         if (prev == kEmpty || prev == x) {
           atomicAdd(ccnt + slot, 1u);
-          return;
+          return true;
         }
       }
     }
     atomicAdd(acnt[a] + x, 1);
+    return true;
   };
-  // adds the caches of the current table to its count arrays (block-wide)
+  // thread-local key range of column a -> shared (warp-reduced first)
+  auto fold_range = [&](int a, int64_t mn, int64_t mx) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = min(mn, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)mn, o));
+      mx = max(mx, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)mx, o));
+    }
+    if (lane == 0 && mx >= mn) {
+      atomicMax(&amax[a], (unsigned long long)enc_max(mx));
+      atomicMax(&amin[a], (unsigned long long)enc_min(mn));
+    }
+  };
+  // adds the caches and key ranges of the current table to the global arrays (block-wide)
   auto flush = [&]() {
     __syncthreads();
     for (int a = 0; a < min(int(n_ac), n_cache); a++)
@@ -491,6 +424,11 @@ __global__ void __launch_bounds__(1024, 2) k_agg_count(const __grid_constant__ B
         const uint32_t k = ckey[size_t(a) * H + s];
         if (k != kEmpty) atomicAdd(acnt[a] + k, int32_t(ccnt[size_t(a) * H + s]));
       }
+    if (tid < n_ac && amax[tid] != 0) {
+      unsigned long long* st = reinterpret_cast<unsigned long long*>(A.ws) + 2 * int64_t(aidx[tid]);
+      atomicMax(st, amax[tid]);
+      atomicMax(st + 1, amin[tid]);
+    }
     __syncthreads();
   };
 
@@ -510,11 +448,16 @@ __global__ void __launch_bounds__(1024, 2) k_agg_count(const __grid_constant__ B
         int n = 0;
         for (int col = 0; col < tb->n_cols && n < CMP_MAX_SKETCHES; col++) {
           const int ai = tb->agg[col];
-          int64_t kmin, range;
-          if (ai < 0 || !agg_active(A.agg[ai], ai, A.ws, &kmin, &range)) continue;
-          acnt[n] = reinterpret_cast<int32_t*>(A.ws + A.agg[ai].off);
-          amin[n] = kmin;
+          if (ai < 0) continue;
+          const AggCol& ac = A.agg[ai];
+          acnt[n] = reinterpret_cast<int32_t*>(A.ws + ac.off);
+          abase[n] = ac.base;
+          acap[n] = ac.cap;
+          amask[n] = ac.mask;
           acol[n] = col;
+          aidx[n] = ai;
+          amax[n] = 0;
+          amin[n] = 0;
           n++;
         }
         n_ac = n;
@@ -530,38 +473,159 @@ __global__ void __launch_bounds__(1024, 2) k_agg_count(const __grid_constant__ B
     const int64_t n_rows = tb->n_rows;
     const int64_t r_begin = (c - ci.chunk_begin) * CH, r_end = min(n_rows, r_begin + CH);
     const bool vec = tb->vec_ok != 0;
-    // a table with an active aggregated column has its survivors counted here, once per
-    // tile (the build kernel's row items then leave them out)
     if (!tb->filtered) {
-      if (tid == 0 && nac > 0 && r_end > r_begin)
+      if (tid == 0 && r_end > r_begin)
         atomicAdd(reinterpret_cast<unsigned long long*>(tb->survivors), (unsigned long long)(r_end - r_begin));
       // every row survives: eight consecutive rows per thread and step, two 16-byte loads
       // for int32 keys
       for (int a = 0; a < nac; a++) {
         const void* kbase = tb->col[acol[a]];
         const int32_t kdt = tb->dtype[acol[a]];
+        int64_t mn = INT64_MAX, mx = INT64_MIN;
+        bool ok = true;
         for (int64_t r = r_begin + 8 * int64_t(tid); r < r_end; r += 8 * int64_t(T)) {
-          if (kdt == CMP_I32 && vec && r + 8 <= r_end) {
-            const int4* p = reinterpret_cast<const int4*>(reinterpret_cast<const int32_t*>(kbase) + r);
-            const int4 u = __ldg(p), v = __ldg(p + 1);
-            count_key(a, u.x), count_key(a, u.y), count_key(a, u.z), count_key(a, u.w);
-            count_key(a, v.x), count_key(a, v.y), count_key(a, v.z), count_key(a, v.w);
+          int64_t v[8];
+          int nv = int(min(int64_t(8), r_end - r));
+          if (vec && nv == 8) {
+            if (kdt == CMP_I32) {
+              const int4* p = reinterpret_cast<const int4*>(reinterpret_cast<const int32_t*>(kbase) + r);
+              const int4 u = __ldg(p), q = __ldg(p + 1);
+              v[0] = u.x, v[1] = u.y, v[2] = u.z, v[3] = u.w, v[4] = q.x, v[5] = q.y, v[6] = q.z, v[7] = q.w;
+            } else {
+              const longlong2* p = reinterpret_cast<const longlong2*>(reinterpret_cast<const long long*>(kbase) + r);
+#pragma unroll
+              for (int h = 0; h < 4; h++) {
+                const longlong2 u = __ldg(p + h);
+                v[2 * h] = u.x, v[2 * h + 1] = u.y;
+              }
+            }
           } else {
-            const int64_t re = min(r_end, r + 8);
-            for (int64_t q = r; q < re; q++) count_key(a, load1(kbase, kdt, q));
+            for (int q = 0; q < 8; q++) v[q] = q < nv ? load1(kbase, kdt, r + q) : 0;
+          }
+#pragma unroll
+          for (int q = 0; q < 8; q++)
+            if (q < nv) {
+              mn = min(mn, v[q]);
+              mx = max(mx, v[q]);
+              ok &= count_key(a, v[q]);
+            }
+        }
+        if (!ok) mn = INT64_MIN, mx = INT64_MAX;  // outside the declared domain: out of range
+        fold_range(a, mn, mx);
+      }
+    } else if (vec && !tb->sample_keep && tb->n_preds >= 1 && tb->n_preds <= 2 && nac <= 2 &&
+               tb->dtype[tb->pred[0].col] == CMP_I32 && tb->dtype[tb->pred[tb->n_preds - 1].col] == CMP_I32 &&
+               R >= 8 * T) {
+      // Warp-autonomous scan (no block barrier per tile): each warp takes 256 rows at a
+      // time, lane l the 16-byte groups at 4 l and 128 + 4 l, with both predicate columns'
+      // loads in flight together; the warp compacts its survivors' row offsets into its own
+      // 256-entry part of `surv`, then its lanes load every aggregated key of a survivor
+      // together and count them.
+      const int warp = tid >> 5, nwarps = T >> 5;
+      uint16_t* wbuf = surv + warp * 256;
+      const DevPred& q0 = tb->pred[0];
+      const DevPred& q1 = tb->pred[tb->n_preds - 1];
+      const int32_t* c0 = reinterpret_cast<const int32_t*>(tb->col[q0.col]);
+      const int32_t* c1 = reinterpret_cast<const int32_t*>(tb->col[q1.col]);
+      const void* kb0 = tb->col[acol[0]];
+      const void* kb1 = nac > 1 ? tb->col[acol[1]] : kb0;
+      const int32_t kd0 = tb->dtype[acol[0]], kd1 = nac > 1 ? tb->dtype[acol[1]] : kd0;
+      int64_t mn0 = INT64_MAX, mx0 = INT64_MIN, mn1 = INT64_MAX, mx1 = INT64_MIN;
+      bool ok0 = true, ok1 = true;
+      unsigned long long n_surv = 0;
+      // two 256-row steps per iteration (rows rb and rb + nwarps 256): the loads of both are
+      // in flight before either is evaluated
+      const int64_t step = int64_t(nwarps) * 256;
+      for (int64_t rb0 = r_begin + int64_t(warp) * 256; rb0 < r_end; rb0 += 2 * step) {
+        int4 v0[4], v1[4];
+        int nv[4];
+#pragma unroll
+        for (int g = 0; g < 4; g++) {
+          const int64_t r = rb0 + (g >> 1) * step + 128 * (g & 1) + 4 * lane;
+          nv[g] = int(max(int64_t(0), min(int64_t(4), r_end - r)));
+          if (nv[g] == 4) {
+            v0[g] = __ldg(reinterpret_cast<const int4*>(c0 + r));
+            v1[g] = __ldg(reinterpret_cast<const int4*>(c1 + r));
+          } else {
+            int t0[4], t1[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+              t0[j] = j < nv[g] ? __ldg(c0 + r + j) : 0;
+              t1[j] = j < nv[g] ? __ldg(c1 + r + j) : 0;
+            }
+            v0[g] = make_int4(t0[0], t0[1], t0[2], t0[3]);
+            v1[g] = make_int4(t1[0], t1[1], t1[2], t1[3]);
           }
         }
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+          const int64_t rb = rb0 + half * step;
+          if (rb >= r_end) break;  // warp-uniform
+          uint32_t m = 0;
+#pragma unroll
+          for (int gg = 0; gg < 2; gg++) {
+            const int g = 2 * half + gg;
+            const int a0[4] = {v0[g].x, v0[g].y, v0[g].z, v0[g].w}, a1[4] = {v1[g].x, v1[g].y, v1[g].z, v1[g].w};
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+              if (j < nv[g] && pred_holds(q0, a0[j]) && pred_holds(q1, a1[j])) m |= 1u << (4 * gg + j);
+          }
+          const int c = __popc(m);
+          int incl = c;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+          }
+          const int total = __shfl_sync(0xffffffffu, incl, 31);
+          int pos = incl - c;
+#pragma unroll
+          for (int gg = 0; gg < 2; gg++)
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+              if ((m >> (4 * gg + j)) & 1u) wbuf[pos++] = uint16_t(128 * gg + 4 * lane + j);
+          __syncwarp();
+          n_surv += unsigned(total);
+          for (int e = lane; e < total; e += 32) {
+            const int64_t row = rb + wbuf[e];
+            const int64_t k0 = load1(kb0, kd0, row);
+            const int64_t k1 = nac > 1 ? load1(kb1, kd1, row) : 0;
+            mn0 = min(mn0, k0), mx0 = max(mx0, k0);
+            ok0 &= count_key(0, k0);
+            if (nac > 1) {
+              mn1 = min(mn1, k1), mx1 = max(mx1, k1);
+              ok1 &= count_key(1, k1);
+            }
+          }
+          __syncwarp();
+        }
+      }
+      if (lane == 0 && n_surv) atomicAdd(reinterpret_cast<unsigned long long*>(tb->survivors), n_surv);
+      if (!ok0) mn0 = INT64_MIN, mx0 = INT64_MAX;
+      fold_range(0, mn0, mx0);
+      if (nac > 1) {
+        if (!ok1) mn1 = INT64_MIN, mx1 = INT64_MAX;
+        fold_range(1, mn1, mx1);
       }
     } else {
       for (int64_t r0 = r_begin; r0 < r_end; r0 += R) {
         const int rows_in_tile = int(min(int64_t(R), r_end - r0));
         const int n_surv = tile_survivors(tb, r0, rows_in_tile, R, vec, surv, sint);
-        if (tid == 0 && nac > 0 && n_surv)
+        if (tid == 0 && n_surv)
           atomicAdd(reinterpret_cast<unsigned long long*>(tb->survivors), (unsigned long long)n_surv);
         for (int a = 0; a < nac; a++) {
           const void* kbase = tb->col[acol[a]];
           const int32_t kdt = tb->dtype[acol[a]];
-          for (int e = tid; e < n_surv; e += T) count_key(a, load1(kbase, kdt, r0 + surv[e]));
+          int64_t mn = INT64_MAX, mx = INT64_MIN;
+          bool ok = true;
+          for (int e = tid; e < n_surv; e += T) {
+            const int64_t k = load1(kbase, kdt, r0 + surv[e]);
+            mn = min(mn, k);
+            mx = max(mx, k);
+            ok &= count_key(a, k);
+          }
+          if (!ok) mn = INT64_MIN, mx = INT64_MAX;  // outside the declared domain: out of range
+          fold_range(a, mn, mx);
         }
         __syncthreads();  // surv is rewritten by the next tile
       }
@@ -643,6 +707,8 @@ __global__ void __launch_bounds__(kHashThreads) k_agg_hash(const __grid_constant
     if (active && s0 < range) {
       const int32_t* cnts = reinterpret_cast<const int32_t*>(A.ws + ac.off);
       const int64_t kmin = s_kmin;
+      // key kmin + j sits in slot (kmin - base + j) & mask
+      const uint64_t off0 = uint64_t(kmin) - uint64_t(ac.base), mask = ac.mask;
       const int np = n_pairs;
       const int64_t per = kHashChunk / nw;  // a multiple of 32
       const int64_t ws0 = min(range, s0 + warp * per), ws1 = min(range, ws0 + per);
@@ -669,7 +735,7 @@ __global__ void __launch_bounds__(kHashThreads) k_agg_hash(const __grid_constant
       int nb = 0;  // warp-uniform
       for (int64_t sb = ws0; sb < ws1; sb += 32) {
         const int64_t j = sb + lane;
-        const int32_t cnt = j < ws1 ? __ldg(cnts + j) : 0;
+        const int32_t cnt = j < ws1 ? __ldg(cnts + ((off0 + uint64_t(j)) & mask)) : 0;
         const unsigned nz = __ballot_sync(0xffffffffu, cnt != 0);
         if (cnt != 0) {
           const int pos = nb + __popc(nz & ((1u << lane) - 1u));
@@ -707,34 +773,43 @@ cudaError_t launch_agg_hash(const BuildArgs& a, int32_t grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-size_t agg_count_smem_bytes(const BuildShape& s, int32_t cache_slots, int32_t cache_cols) {
+size_t agg_count_smem_bytes(int32_t tile_rows, int32_t cache_slots, int32_t cache_cols) {
   return align16(sizeof(uint32_t) * 2 * size_t(cache_slots) * size_t(cache_cols)) +
-         align16(sizeof(uint16_t) * s.tile_rows) + sizeof(int32_t) * 40;
+         align16(sizeof(uint16_t) * tile_rows) + sizeof(int32_t) * 40;
 }
 
-cudaError_t launch_agg(const BuildArgs& a, const BuildShape& s, int32_t stat_grid, int32_t cnt_grid,
+cudaError_t launch_agg(const BuildArgs& a, int32_t tile_rows, int32_t cnt_threads, int32_t cnt_grid,
                        cudaStream_t st) {
   if (a.n_agg <= 0) return cudaSuccess;
-  k_agg_stats<<<unsigned(stat_grid), kStatThreads, 0, st>>>(a);
-  const dim3 g(unsigned(std::max(1, 4 * sm_count() / std::max(1, a.n_agg))), unsigned(a.n_agg));
+  const dim3 g(unsigned(std::max(1, 8 * sm_count() / std::max(1, a.n_agg))), unsigned(a.n_agg));
   k_agg_zero<<<g, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || cnt_grid <= 0) return e;
-  const size_t smem = agg_count_smem_bytes(s, a.cnt_cache_slots, a.cnt_cache_cols);
+  const size_t smem = agg_count_smem_bytes(tile_rows, a.cnt_cache_slots, a.cnt_cache_cols);
   e = cudaFuncSetAttribute(k_agg_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  k_agg_count<<<unsigned(cnt_grid), s.threads, smem, st>>>(a);
+  // the whole shared memory of the SM, so that a CTA of the unique-key kernel (launched
+  // next, as a programmatic dependent) fits beside one of this pass
+  e = cudaFuncSetAttribute(k_agg_count, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
+  k_agg_count<<<unsigned(cnt_grid), cnt_threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 __global__ void k_zero_spans(const ZeroSpan* __restrict__ spans, int32_t n) {
-  // one block-stride pass per span; spans are 4-byte multiples
+  // one block-stride pass per span; spans are 4-byte multiples: 4-byte stores up to the
+  // first 16-byte boundary, 16-byte stores, then 4-byte stores for the tail
   for (int32_t s = blockIdx.y; s < n; s += gridDim.y) {
     const ZeroSpan z = spans[s];
     uint32_t* p = reinterpret_cast<uint32_t*>(z.ptr);
     const int64_t words = z.bytes / 4;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < words; i += int64_t(gridDim.x) * blockDim.x)
-      p[i] = 0;
+    const int64_t head = min(words, int64_t((16 - (reinterpret_cast<uintptr_t>(p) & 15)) & 15) / 4);
+    const int64_t n4 = (words - head) / 4;
+    const int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, step = int64_t(gridDim.x) * blockDim.x;
+    if (i0 < head) p[i0] = 0;
+    int4* q = reinterpret_cast<int4*>(p + head);
+    for (int64_t i = i0; i < n4; i += step) q[i] = make_int4(0, 0, 0, 0);
+    for (int64_t i = head + 4 * n4 + i0; i < words; i += step) p[i] = 0;
   }
 }
 

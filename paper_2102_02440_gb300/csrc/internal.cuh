@@ -112,6 +112,78 @@ __device__ __forceinline__ int cw_sign(const PairParam& q, const KeyPow& k) {
   return 1 - 2 * int(r & 1);
 }
 
+// ---- Horner form (one (sketch, row) pair per key: no powers to share).  The same two
+// residues, (a x + b) mod p and (c3 x^3 + c2 x^2 + c1 x + c0) mod p = ((c3 x + c2) x + c1) x
+// + c0, with intermediates kept only partly reduced: every step's result y satisfies
+// y < 2^61 + 5 and y = the exact residue (mod p).
+struct KeyX {
+  uint32_t lo, hi, hi2;  // x < p as lo + hi 2^31 (lo < 2^31, hi < 2^30), hi2 = 2 hi
+};
+__device__ __forceinline__ KeyX key_x(uint64_t x) {
+  return {uint32_t(x) & kM31, uint32_t(x >> 31), uint32_t(x >> 30) & ~1u};
+}
+
+// y x + c folded once, for y < 2^61 + 8 given as (ylo < 2^31, yhi <= 2^30), x < p, c < 2^61.
+// y x = ylo xlo + (ylo xhi + yhi xlo) 2^31 + yhi xhi 2^62 and 2^62 = 2, 2^61 = 1 (mod p), so with
+// t1 = ylo xhi + yhi xlo (< 2^62 + 2^31):
+//   y x + c = ylo xlo + yhi (2 xhi) + c + (t1 >> 30) + (t1 & (2^30-1)) 2^31   (mod p),
+// a sum below 2^62 + 2^61 + 2^61 + 2^33 + 2^61 < 2^64; one fold leaves it below 2^61 + 5.
+// SMALLX: x < 2^31 (xhi = 0), the products with xhi are zero and left out.
+template <bool SMALLX>
+__device__ __forceinline__ uint64_t mul_add_fold(uint32_t ylo, uint32_t yhi, const KeyX& x, uint64_t c) {
+  const uint64_t t1 = SMALLX ? uint64_t(yhi) * x.lo : uint64_t(ylo) * x.hi + uint64_t(yhi) * x.lo;
+  const uint64_t s = uint64_t(ylo) * x.lo + (SMALLX ? 0 : uint64_t(yhi) * x.hi2) + c + (t1 >> 30) +
+                     ((t1 & kM30) << 31);
+  return fold61(s);
+}
+
+// The same step for x < 2^31 (xhi = 0) with every product, shift and add on the multiply
+// pipe: with t1 = yhi xlo (< 2^61: yhi <= 2^30) split as t1hi 2^32 + t1lo,
+//   t1 2^31 = t1hi 2^63 + t1lo 2^31 = 4 t1hi + t1lo 2^31   (mod p, 2^63 = 4 2^61),
+// so y x + c = ylo xlo + c + t1lo 2^31 + 4 t1hi (mod p), a sum below 2^62 + 2^61 + 2^63 +
+// 2^31 < 2^64, folded once.  m31 = 2^31 and m4 = 4 come in as run-time values so that the
+// compiler keeps them as multiplications.
+__device__ __forceinline__ uint64_t mul_add_fold_sx(uint32_t ylo, uint32_t yhi, uint32_t xlo, uint64_t c,
+                                                    uint32_t m31, uint32_t m4) {
+  const uint64_t t1 = uint64_t(yhi) * xlo;
+  uint64_t s = uint64_t(ylo) * xlo + c;
+  s += uint64_t(uint32_t(t1)) * m31;
+  s += uint64_t(uint32_t(t1 >> 32)) * m4;
+  return fold61(s);
+}
+
+// For y < 2^61 + 8: 1 if y >= p (its residue is then y - p), else 0.
+__device__ __forceinline__ uint32_t ge_p(uint64_t y) { return uint32_t((y + 1) >> 61); }
+
+// Bucket ((a x + b) mod p) mod w; the same value as cw_bucket.  For w a power of two (w <=
+// 2^31 divides 2^61), y - p = y + 1 (mod w).
+template <bool POW2, bool SMALLX>
+__device__ __forceinline__ uint32_t cw_bucket_h(const PairParam& q, const KeyX& x, uint32_t w, uint32_t m31 = 0,
+                                                uint32_t m4 = 0) {
+  const uint64_t y = SMALLX ? mul_add_fold_sx(q.a_lo, q.a_hi, x.lo, q.b, m31, m4)
+                            : mul_add_fold<false>(q.a_lo, q.a_hi, x, q.b);
+  if (POW2) return (uint32_t(y) + ge_p(y)) & (w - 1);
+  return uint32_t((ge_p(y) ? y - kP61 : y) % w);
+}
+
+// Sign: parity of ((c3 x + c2) x + c1) x + c0 mod p, as +1 / -1; the same value as cw_sign.
+// The residue of the last y is y - p when y >= p, whose parity is flipped (p is odd).
+template <bool SMALLX>
+__device__ __forceinline__ int cw_sign_h(const PairParam& q, const KeyX& x, uint64_t c2, uint64_t c1,
+                                         uint32_t m31 = 0, uint32_t m4 = 0) {
+  uint64_t y;
+  if (SMALLX) {
+    y = mul_add_fold_sx(q.c3_lo, q.c3_hi, x.lo, c2, m31, m4);
+    y = mul_add_fold_sx(uint32_t(y) & kM31, uint32_t(y >> 31), x.lo, c1, m31, m4);
+    y = mul_add_fold_sx(uint32_t(y) & kM31, uint32_t(y >> 31), x.lo, q.c0, m31, m4);
+  } else {
+    y = mul_add_fold<false>(q.c3_lo, q.c3_hi, x, c2);
+    y = mul_add_fold<false>(uint32_t(y) & kM31, uint32_t(y >> 31), x, c1);
+    y = mul_add_fold<false>(uint32_t(y) & kM31, uint32_t(y >> 31), x, q.c0);
+  }
+  return 1 - 2 * int((uint32_t(y) ^ ge_p(y)) & 1u);
+}
+
 // Output r (0-based) of SplitMix64 (Steele, Lea & Flood 2014) seeded with `seed`: the
 // generator's state after r + 1 steps, through its finaliser.
 __host__ __device__ inline uint64_t splitmix64_at(uint64_t seed, uint64_t r) {
@@ -140,7 +212,8 @@ struct DevTable {
   int64_t n_rows;
   int32_t n_cols, n_preds, n_sketches;
   int32_t vec_ok;  // every column 16-byte aligned: 128-bit loads allowed
-  int32_t filtered, pad0;  // predicates or a row sample: tiles go through the survivor compaction
+  int32_t filtered;  // predicates or a row sample: tiles go through the survivor compaction
+  int32_t surv_by;   // batched build: kernel that counts the survivors (kSurvRow / kSurvCount / kSurvUniq)
   uint64_t sample_seed, sample_keep;  // row r is sampled iff splitmix64_at(seed, r) < keep (keep 0: no sample)
   const void* col[CMP_MAX_COLS];
   int32_t dtype[CMP_MAX_COLS];
@@ -150,21 +223,32 @@ struct DevTable {
   int32_t* counters;   // [n_sketches][d][w]
   int64_t* survivors;  // one int64
   int32_t agg[CMP_MAX_COLS];  // batched build: AggCol index of each aggregated key column, else -1
+  uint32_t uniq_mask;         // batched build: key columns hashed by the unique-key kernel (bit c)
+  int32_t pad1;
 };
+enum { kSurvRow = 0, kSurvCount = 1, kSurvUniq = 2 };
 
 // Key aggregation of the batched build.  A key column of a large table is reduced to one
 // (key, survivor count) entry per distinct key before hashing: the Fast-AGMS update is
 // linear and the int32 counters wrap exactly, so count * xi(key) added once per entry
-// gives the counters of one update per tuple.  Keys are counted in a dense array indexed
-// by key - min; a column whose key range exceeds the array (cap) at run time keeps the
-// per-row path.  Workspace: [n_agg] x (max, min) encoded as uint64 pairs followed by the
-// chunk counters of the counting and hashing passes (two uint64; all zeroed before each
-// build, 256-aligned area), then each column's int32 count array at byte offset `off`.
+// gives the counters of one update per tuple.  The counting pass adds each surviving key
+// to slot (key - base) & mask of the column's count array (cap slots, cleared before the
+// pass) and records the smallest and largest surviving key.  Two layouts:
+//  - declared domain [base, base + cap): mask = ~0; a key outside it marks the column as
+//    out of range (its counts are then discarded);
+//  - no declaration: cap is a power of two and mask = cap - 1, so any cap consecutive
+//    keys occupy distinct slots.
+// After the pass, a column whose surviving keys span at most cap values is "active" and
+// its entries are hashed by k_agg_hash; otherwise it keeps the per-row path.  Workspace:
+// [n_agg] x (max, min) encoded as uint64 pairs, then the chunk counters of the counting
+// and hashing passes (two uint64; all zeroed before each build, 256-aligned area), then
+// each column's int32 count array at byte offset `off`.
 struct AggCol {
   int32_t table, col;
-  int64_t cap;  // count slots
-  int64_t off;  // byte offset of the count array in the workspace
-  int32_t stat_cta0, stat_ncta;  // CTAs of the key-range pass reading this column
+  int64_t cap;   // count slots
+  int64_t off;   // byte offset of the count array in the workspace
+  int64_t base;  // key of slot 0 (declared domain) or 0
+  uint64_t mask; // ~0 (declared domain) or cap - 1 (power of two)
   int64_t hash_chunk0;  // first chunk of this column in the hashing pass (kHashChunk slots each)
 };
 constexpr int64_t kHashChunk = 16384;
@@ -176,8 +260,8 @@ __host__ __device__ inline uint64_t enc_min(int64_t v) { return ~(uint64_t(v) ^ 
 __host__ __device__ inline int64_t dec_max(uint64_t e) { return int64_t(e ^ (1ull << 63)); }
 __host__ __device__ inline int64_t dec_min(uint64_t e) { return int64_t(~e ^ (1ull << 63)); }
 
-// Whether aggregated column `a` (index ai) takes the aggregated path in this run, with its
-// smallest key and key range.
+// Whether aggregated column `a` (index ai) takes the aggregated path in this run (read
+// after the counting pass), with its smallest surviving key and key range.
 __device__ __forceinline__ bool agg_active(const AggCol& a, int ai, const unsigned char* ws, int64_t* kmin,
                                            int64_t* range) {
   const unsigned long long* st = reinterpret_cast<const unsigned long long*>(ws) + 2 * int64_t(ai);
@@ -189,6 +273,21 @@ __device__ __forceinline__ bool agg_active(const AggCol& a, int ai, const unsign
   *range = int64_t(r) + 1;
   return true;
 }
+
+// Unique key columns (declared distinct, e.g. primary keys) of the batched build: no key
+// repeats, so aggregation cannot reduce the hashing.  k_uniq_hash hashes each surviving
+// row once per (sketch, row) pair with a slab of the column's pairs held in shared
+// memory.  A slab is up to kUniqMaxPairs pairs of one column; an item is one slab over a
+// range of the table's rows.
+constexpr int32_t kUniqMaxPairs = 32;
+struct UniqSlab {
+  int32_t table, col, n_pairs, pad;
+  int32_t pair[kUniqMaxPairs];  // pair = sketch * d + row of the table
+};
+struct UniqItem {
+  int32_t slab, count_surv;  // count_surv: this item adds its range's survivors to the table's count
+  int64_t row_begin, row_end;
+};
 
 // One (table, slab of (sketch,row) pairs) handled by n_ctas consecutive CTAs walking tiles
 // of the table's rows (aggregated key columns are hashed by k_agg_hash instead).
@@ -241,6 +340,14 @@ struct BuildArgs {
   int64_t cnt_total_chunks;
   int64_t hash_total_chunks;  // hashing pass of the aggregated columns
   int32_t hash_max_pairs;     // most (sketch, row) pairs on one aggregated column
+  // unique-key kernel
+  const UniqSlab* uslab;
+  const UniqItem* uitem;
+  const int32_t* u_cta_item;  // [grid + 1] first item of each CTA
+  int64_t n_uitems;
+  int32_t u_pack16;  // 1: one pair per slab, counters as two 16-bit halves per word
+  int32_t u_words;   // shared-memory counter words of a slab
+  uint32_t m31, m4;  // 2^31 and 4 (multipliers of the Horner steps)
 };
 
 // Plan blob (host-encoded, device-read) for the batched build.
@@ -252,13 +359,15 @@ struct BuildPlanHdr {
   int64_t total_bytes;
   int64_t n_agg, off_agg;                            // aggregated key columns
   int64_t n_cnt_items, off_cnt_items, cnt_total_chunks;  // counting pass
-  int32_t cnt_grid, stat_grid;
+  int32_t cnt_grid, cnt_threads;
   int64_t ws_bytes;
   int32_t cnt_cache_slots, cnt_cache_cols;
   int64_t hash_total_chunks;
   int32_t hash_max_pairs, hash_grid;
+  int64_t n_uslab, off_uslab, n_uitems, off_uitems, off_u_cta;  // unique-key kernel
+  int32_t u_grid, u_pack16, u_words, u_tile_rows;
 };
-constexpr int32_t kBuildPlanVersion = 6;
+constexpr int32_t kBuildPlanVersion = 7;
 struct ZeroSpan {
   void* ptr;
   int64_t bytes;
@@ -275,8 +384,10 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 // launchers implemented in the .cu files
 size_t build_smem_bytes(const BuildShape& s, int w);
 cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t st);
-size_t agg_count_smem_bytes(const BuildShape& s, int32_t cache_slots, int32_t cache_cols);
-cudaError_t launch_agg(const BuildArgs& a, const BuildShape& s, int32_t stat_grid, int32_t cnt_grid, cudaStream_t st);
+size_t agg_count_smem_bytes(int32_t tile_rows, int32_t cache_slots, int32_t cache_cols);
+cudaError_t launch_agg(const BuildArgs& a, int32_t tile_rows, int32_t cnt_threads, int32_t cnt_grid, cudaStream_t st);
+size_t uniq_smem_bytes(int32_t words, int32_t tile_rows);
+cudaError_t launch_uniq(const BuildArgs& a, int32_t grid, int32_t threads, int32_t tile_rows, cudaStream_t st);
 cudaError_t launch_zero_spans(const ZeroSpan* spans_dev, int32_t n, cudaStream_t st);
 cudaError_t launch_agg_hash(const BuildArgs& a, int32_t grid, cudaStream_t st);
 

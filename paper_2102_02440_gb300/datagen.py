@@ -36,6 +36,9 @@ class Table:
     preds: list = field(default_factory=list)      # conjunction
     key_col: list = field(default_factory=list)    # per sketch: column index of its join key
     edge_id: list = field(default_factory=list)    # per sketch: join-graph edge
+    # per column: None, or what a catalog knows about it: ("unique", lo, hi) for a primary key
+    # holding distinct values in [lo, hi), ("domain", lo, hi) for a foreign key in [lo, hi)
+    col_meta: list = field(default_factory=list)
 
     @property
     def n_rows(self) -> int:
@@ -196,19 +199,19 @@ def five_table(scale: float = 1.0, d: int = 11, w: int = 4096, d1_sel_pct: int =
     movie_dom, kw_dom, person_dom = n_d1, n_d2, n_d3
     # tables: 0 F1, 1 F2, 2 D1, 3 D2, 4 D3
     f1 = Table("F1", [zipf_keys(rng, n_f1, movie_dom, s), zipf_keys(rng, n_f1, person_dom, s)], [],
-               [0, 0, 1], [2, 3, 4])
+               [0, 0, 1], [2, 3, 4], [("domain", 0, movie_dom), ("domain", 0, person_dom)])
     f2 = Table("F2", [zipf_keys(rng, n_f2, kw_dom, s), zipf_keys(rng, n_f2, movie_dom, s)], [],
-               [0, 1, 1], [0, 1, 3])
+               [0, 1, 1], [0, 1, 3], [("domain", 0, kw_dom), ("domain", 0, movie_dom)])
     d1 = Table("D1", [pk_column(rng, n_d1), uniform_col(rng, n_d1, 0, 1000)],
-               [Pred(1, RANGE, 0, 10 * d1_sel_pct)], [0, 0], [1, 2])
+               [Pred(1, RANGE, 0, 10 * d1_sel_pct)], [0, 0], [1, 2], [("unique", 0, n_d1), None])
     codes2 = zipf_keys(rng, n_d2, 10_000, 1.0)
     point = int(codes2[rng.integers(0, n_d2)])
-    d2 = Table("D2", [pk_column(rng, n_d2), codes2], [Pred(1, EQ, point, 0)], [0], [0])
+    d2 = Table("D2", [pk_column(rng, n_d2), codes2], [Pred(1, EQ, point, 0)], [0], [0], [("unique", 0, n_d2), None])
     code_dom = 100_000
     codes3 = zipf_keys(rng, n_d3, code_dom, 0.8)
     subset = rng.choice(code_dom, size=code_dom // 100, replace=False)
     d3 = Table("D3", [pk_column(rng, n_d3), codes3], [Pred(1, IN, 0, 0, bitmap_of(subset, code_dom), code_dom)],
-               [0], [4])
+               [0], [4], [("unique", 0, n_d3), None])
     return Workload(f"five_table scale={scale} d{d} w{w} D1sel={d1_sel_pct}%", [f1, f2, d1, d2, d3],
                     [3, 2, 2, 0, 4], [1, 1, 0, 1, 0], d, w, hash_seed, data_seed)
 
@@ -413,6 +416,57 @@ def graph_batch(n_graphs: int = 64, n_lo: int = 4, n_hi: int = 17, rows_lo: int 
     return out
 
 
+def graph_batch_device(n_graphs: int = 64, n_lo: int = 4, n_hi: int = 17, rows_lo: int = 10_000,
+                       rows_hi: int = 100_000_000, domain: int = 100_000, d: int = 11, w: int = 1024,
+                       pred_prob: float = 0.5, seed: int = 20210207, kinds=("chain", "star", "cycle"),
+                       hash_seed: int = 0xC0FFEE + 2, device="cuda", rows_scale: float = 1.0) -> list:
+    """graph_batch's recipe drawn on the device (columns are device tensors): graph kinds,
+    table sizes, Zipf exponents and predicates come from a host generator seeded with
+    `seed`, the columns from a device generator with the same seed.  rows_scale multiplies
+    every table's row count (at least rows_lo / 10), for runs that must fit a time or memory
+    budget.  Key columns carry their domain [0, domain) as a catalog declaration."""
+    import torch
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    out = []
+    for gi in range(n_graphs):
+        kind = kinds[int(rng.integers(0, len(kinds)))]
+        n = int(rng.integers(n_lo, n_hi + 1))
+        if kind == "chain":
+            edges = [(i, i + 1) for i in range(n - 1)]
+        elif kind == "star":
+            edges = [(0, i) for i in range(1, n)]
+        else:
+            edges = [(i, i + 1) for i in range(n - 1)] + [(0, n - 1)]
+        tabs = []
+        for t in range(n):
+            rows = int(np.exp(rng.uniform(np.log(rows_lo), np.log(rows_hi))))
+            rows = max(int(rows * rows_scale), max(rows_lo // 10, 16))
+            cols, kc, ei, meta = [], [], [], []
+            for e, (u, v) in enumerate(edges):
+                if t in (u, v):
+                    cols.append(zipf_keys_device(gen, rows, domain, float(rng.uniform(0.5, 1.5)), dtype=torch.int32))
+                    kc.append(len(cols) - 1)
+                    ei.append(e)
+                    meta.append(("domain", 0, domain))
+            preds = []
+            if rng.random() < pred_prob:
+                if rng.random() < 0.5:
+                    codes = zipf_keys_device(gen, rows, 1000, 1.0, dtype=torch.int32)
+                    cols.append(codes)
+                    meta.append(None)
+                    preds.append(Pred(len(cols) - 1, EQ, int(codes[int(rng.integers(0, rows))].item())))
+                else:
+                    cols.append(torch.randint(0, 1000, (rows,), generator=gen, device=device, dtype=torch.int32))
+                    meta.append(None)
+                    preds.append(Pred(len(cols) - 1, RANGE, 0, int(1000 * rng.uniform(0.01, 0.5))))
+            tabs.append(Table(f"G{gi}T{t}", cols, preds, kc, ei, meta))
+        out.append(Workload(f"{kind}{n}", tabs, [u for u, _ in edges], [v for _, v in edges], d, w,
+                            hash_seed + gi, seed))
+    return out
+
+
 def zipf_keys_device(gen, n: int, D: int, s: float, dtype=None, chunk: int = 1 << 26):
     """n Zipf(s) keys over [0, D) drawn on the generator's device (chunked), hot keys
     scattered by a seeded affine permutation; int64 unless dtype is given."""
@@ -452,9 +506,9 @@ def scale_workload_device(n_fact: int = 1_000_000_000, n_d1: int = 100_000_000, 
     pk1 = torch.randperm(n_d1, generator=gen, device=device, dtype=torch.int64)
     pk2 = torch.randperm(n_d2, generator=gen, device=device, dtype=torch.int64)
     F = Table("F", [fk1, fk2, p1, p2], [Pred(2, RANGE, INT64_MIN, 250), Pred(3, RANGE, INT64_MIN, 400)], [0, 1],
-              [0, 1])
-    D1 = Table("D1", [pk1], [], [0], [0])
-    D2 = Table("D2", [pk2], [], [0], [1])
+              [0, 1], [("domain", 0, n_d1), ("domain", 0, n_d2), None, None])
+    D1 = Table("D1", [pk1], [], [0], [0], [("unique", 0, n_d1)])
+    D2 = Table("D2", [pk2], [], [0], [1], [("unique", 0, n_d2)])
     # tables: 0 F, 1 D1, 2 D2
     return Workload(f"scale F{n_fact} D1 {n_d1} D2 {n_d2} d{d} w{w}", [F, D1, D2], [1, 2], [0, 0], d, w,
                     hash_seed, seed)

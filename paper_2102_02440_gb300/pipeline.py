@@ -22,7 +22,7 @@ class DeviceTable:
     """One table's device columns, bitmaps, outputs and its cmp_table descriptor."""
 
     def __init__(self, t, d: int, w: int, device, upload: bool = True, cols_dev=None, sample_seed: int = 0,
-                 sample_rate: float = 0.0):
+                 sample_rate: float = 0.0, hints: bool = True):
         self.name = t.name
         self.n_rows = t.n_rows
         self.k = len(t.key_col)
@@ -30,8 +30,16 @@ class DeviceTable:
         self.bitmaps = [(_dev(q.bitmap, device) if q.bitmap is not None else None) for q in t.preds]
         self.counters = torch.zeros((max(self.k, 1), d, w), dtype=torch.int32, device=device)
         ncols = len(self.cols)
-        self._cols = (K.cmp_col * max(ncols, 1))(*[
-            K.cmp_col(c.data_ptr(), K.CMP_I32 if c.dtype == torch.int32 else K.CMP_I64, 0) for c in self.cols])
+        meta = list(getattr(t, "col_meta", None) or []) if hints else []
+        meta += [None] * (ncols - len(meta))
+
+        def col(c, m):
+            dt = K.CMP_I32 if c.dtype == torch.int32 else K.CMP_I64
+            if m is None:
+                return K.cmp_col(c.data_ptr(), dt, 0, 0, 0)
+            flags = K.CMP_COL_DOMAIN | (K.CMP_COL_UNIQUE if m[0] == "unique" else 0)
+            return K.cmp_col(c.data_ptr(), dt, flags, int(m[1]), int(m[2]))
+        self._cols = (K.cmp_col * max(ncols, 1))(*[col(c, m) for c, m in zip(self.cols, meta)])
         self._preds = (K.cmp_pred * max(len(t.preds), 1))(*[
             K.cmp_pred(q.col, q.op, int(q.lo), int(q.hi), bm.data_ptr() if bm is not None else None, int(q.nbits))
             for q, bm in zip(t.preds, self.bitmaps)])
@@ -49,13 +57,15 @@ class DeviceWorkload:
     sample_rates: optional per-table row-sample rates (0 or 1 = every row; Sec. 2
       "Workflow"), table t sampled with seed sample_seed + t; the estimates scale back by
       the rates.
+    hints: pass the tables' column metadata (unique keys, key domains) to the build; the
+      sketches are the same either way, only the build's path changes.
     offline: tables without predicates whose sketches are built once by build_offline()
       and plugged into every query (Sec. 2 "Workflow"): build_batched() and presort() then
       cover only the other tables.  Counters, presort and cross-rank buffers hold the
       online tables first, so each of those steps stays one launch over a prefix."""
 
     def __init__(self, wl, device="cuda", hash_seed: int | None = None, cols_dev=None, sample_rates=None,
-                 sample_seed: int = 0x5A3B1E, offline=None):
+                 sample_seed: int = 0x5A3B1E, offline=None, hints: bool = True):
         self.wl = wl
         self.device = torch.device(device)
         self.d, self.w = wl.d, wl.w
@@ -68,7 +78,7 @@ class DeviceWorkload:
         self.sample_rates = [float(r) for r in sample_rates] if sample_rates is not None else None
         self.tables = [DeviceTable(t, self.d, self.w, self.device, cols_dev=cols_dev[i] if cols_dev else None,
                                    sample_seed=sample_seed + i,
-                                   sample_rate=self.sample_rates[i] if self.sample_rates else 0.0)
+                                   sample_rate=self.sample_rates[i] if self.sample_rates else 0.0, hints=hints)
                        for i, t in enumerate(wl.tables)]
         self.offline = sorted(set(int(t) for t in (offline or [])))
         for t in self.offline:

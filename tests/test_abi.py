@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(K):
 def test_status_strings(K):
     assert K.status_str(0) == "ok"
     assert "invalid" in K.status_str(-1)
-    assert K.lib().cmp_abi_version() == K.CMP_ABI_VERSION == 5
+    assert K.lib().cmp_abi_version() == K.CMP_ABI_VERSION == 6
 
 
 def test_hash_params_match_oracle_generator(K, orc):
@@ -50,8 +50,9 @@ def test_hash_params_match_oracle_generator(K, orc):
         K.cmp_hash_params(1, 1, 65)
 
 
-def _desc(K, n_rows=10, ncols=1, preds=(), key_col=(0,), edge_id=(0,), dtype=0):
-    cols = (K.cmp_col * max(ncols, 1))(*[K.cmp_col(0x1000 * (i + 1), dtype, 0) for i in range(ncols)])
+def _desc(K, n_rows=10, ncols=1, preds=(), key_col=(0,), edge_id=(0,), dtype=0, flags=0, dom=(0, 0)):
+    cols = (K.cmp_col * max(ncols, 1))(*[K.cmp_col(0x1000 * (i + 1), dtype, flags, dom[0], dom[1])
+                                         for i in range(ncols)])
     pr = (K.cmp_pred * max(len(preds), 1))(*preds)
     kc = (C.c_int32 * max(len(key_col), 1))(*key_col)
     ei = (C.c_int32 * max(len(edge_id), 1))(*edge_id)
@@ -62,7 +63,7 @@ def _desc(K, n_rows=10, ncols=1, preds=(), key_col=(0,), edge_id=(0,), dtype=0):
 
 @pytest.mark.parametrize("case", ["d0", "d65", "w0", "rows_neg", "rows_big", "bad_keycol", "bad_edge",
                                   "bad_dtype", "bad_pred_col", "bad_pred_op", "in_no_bitmap", "null_counters",
-                                  "too_many_sketches"])
+                                  "too_many_sketches", "bad_col_flags", "empty_domain"])
 def test_build_rejects_bad_arguments(K, case):
     d, w, ne = 4, 64, 2
     t = _desc(K)
@@ -90,6 +91,10 @@ def test_build_rejects_bad_arguments(K, case):
         t = _desc(K, preds=[K.cmp_pred(0, 2, 0, 0, None, 100)])
     elif case == "too_many_sketches":
         t = _desc(K, key_col=tuple([0] * 17), edge_id=tuple([0] * 17))
+    elif case == "bad_col_flags":
+        t = _desc(K, flags=4)
+    elif case == "empty_domain":
+        t = _desc(K, flags=K.CMP_COL_DOMAIN, dom=(5, 5))
     counters = 0 if case == "null_counters" else 0x2000
     st = K.lib().cmp_sketch_build(C.byref(t), d, w, 0x3000, ne, counters, 0x4000, 0x5000, None, None)
     assert st == K.CMP_EINVAL
@@ -101,6 +106,33 @@ def test_build_rejects_bad_cfg(K):
                 K.cmp_build_cfg.make(mode=3), K.cmp_build_cfg.make(threads=128, tile_rows=4096, dedupe=1)):
         st = K.lib().cmp_sketch_build(C.byref(t), 4, 64, 0x3000, 2, 0x2000, 0x4000, 0x5000, C.byref(cfg), None)
         assert st == K.CMP_EINVAL
+
+
+def test_column_declarations_plan_host_logic(K):
+    """A declared domain sizes the count array to the domain (instead of the power of two
+    at or above the row count); a unique column needs no count array at all, and the
+    unique path can be switched off; bad unique settings are rejected."""
+    n = 10_000_000
+    plain = K.cmp_build_plan_bytes([_desc(K, n_rows=n)], 11, 1024, None)[1]
+    assert plain >= (1 << 24) * 4                      # next power of two at or above 10M slots
+    dom = K.cmp_build_plan_bytes([_desc(K, n_rows=n, flags=K.CMP_COL_DOMAIN, dom=(-50, 1000))], 11, 1024,
+                                 None)[1]
+    assert 1050 * 4 <= dom < 1 << 20
+    wide = K.cmp_build_plan_bytes([_desc(K, n_rows=n, flags=K.CMP_COL_DOMAIN, dom=(0, 1 << 40))], 11, 1024,
+                                  None)[1]
+    assert wide == plain                               # a domain beyond 2^27 values is not used
+    uniq = [_desc(K, n_rows=n, flags=K.CMP_COL_UNIQUE)]
+    assert K.cmp_build_plan_bytes(uniq, 11, 1024, None)[1] == 0
+    assert K.cmp_build_plan_bytes(uniq, 11, 65536, None)[1] == 0       # packed 16-bit slabs
+    assert K.cmp_build_plan_bytes(uniq, 11, 1 << 18, None)[1] == plain  # too wide: aggregated instead
+    assert K.cmp_build_plan_bytes(uniq, 11, 1024, K.cmp_build_cfg.make(unique=-1))[1] == plain
+    for bad in (K.cmp_build_cfg.make(unique=2), K.cmp_build_cfg.make(unique=-2)):
+        with pytest.raises(K.CompassError) as ei:
+            K.cmp_build_plan_bytes(uniq, 11, 1024, bad)
+        assert ei.value.status == K.CMP_EINVAL
+    nb, _ = K.cmp_build_plan_bytes(uniq, 11, 1024, None)
+    buf = np.zeros(nb, np.uint8)
+    K.cmp_build_plan_encode(uniq, 11, 1024, 1, [0x2000], 0x4000, None, buf.ctypes.data, nb)
 
 
 def test_batched_plan_encoding_host_logic(K):
