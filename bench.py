@@ -46,12 +46,19 @@ def _args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "five_table"],
+                    help="scale: the 1e9-row fact table configuration (the headline); five_table: the paper's "
+                         "running example at full size")
     ap.add_argument("--scale", type=float, default=1.0, help="row-count scale of the workload (1.0 = full)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="measure the headline workload only (no five-table or batched-enumeration keys)")
     ap.add_argument("--w", type=int, default=4096)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every step eagerly instead of replaying it as one captured CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--c3-rows-scale", type=float, default=1.0,
+                    help="row-count factor of the batched-enumeration extra (1.0: rows in [1e4, 1e8])")
     ap.add_argument("--phases", action="store_true", help="print a per-phase breakdown on stderr")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of autotuned launch shapes: read if it has this workload's, else written")
@@ -197,12 +204,14 @@ def triangle_ops(dw, masks):
     return ops, n_tri, len(generic)
 
 
-def build_work(wl, dw, dedupe: bool):
-    """CW evaluations the batched build must do.  A key column of a table with >= 2^18
-    rows whose key range fits min(rows, 2^27) is aggregated (dedupe on): one evaluation
-    per distinct surviving key per sketch row of that column; other columns one per
-    surviving row per sketch row.  Survivors and distinct keys are counted on the device
-    (torch, outside any timed region)."""
+def build_work(wl, dw, dedupe: bool, unique: bool = True):
+    """CW evaluations the batched build must do, by the path each key column takes:
+    a column declared unique is hashed once per surviving row; a key column of a table
+    with >= 2^18 rows (dedupe on) is aggregated when its surviving keys span no more values
+    than its count array (the declared domain, else the power of two at or above
+    min(rows, 2^27)): one evaluation per distinct surviving key; every other column one per
+    surviving row.  Each per sketch row of each sketch on the column.  Survivors and
+    distinct keys are counted on the device (torch, outside any timed region)."""
     import torch
     total, distinct = 0, {}
     for ti, (t, dt) in enumerate(zip(wl.tables, dw.tables)):
@@ -221,13 +230,24 @@ def build_work(wl, dw, dedupe: bool):
                 vv = torch.where(inb, v, torch.zeros_like(v))
                 keep &= inb & (((bm[vv >> 5] >> (vv & 31)) & 1) == 1)
         n_surv = int(keep.sum().item())
+        meta = list(getattr(t, "col_meta", None) or []) + [None] * len(t.cols)
         for c in sorted(set(t.key_col)):
             pairs = t.key_col.count(c) * wl.d
-            col = dt.cols[c]
-            agg = dedupe and t.n_rows >= (1 << 18) and t.n_rows > 0 and \
-                int(col.max().item()) - int(col.min().item()) < min(t.n_rows, 1 << 27)
+            m = meta[c]
+            if unique and m is not None and m[0] == "unique" and wl.w <= 65536:
+                total += n_surv * pairs
+                continue
+            agg = False
+            if dedupe and t.n_rows >= (1 << 18) and n_surv:
+                kept = dt.cols[c][keep]
+                lo, hi = int(kept.min().item()), int(kept.max().item())
+                if m is not None and 0 < m[2] - m[1] <= (1 << 27):
+                    agg = m[1] <= lo and hi < m[2]
+                else:
+                    cap = 1 << max(0, (min(t.n_rows, 1 << 27) - 1).bit_length())
+                    agg = hi - lo < cap
             if agg:
-                nd = int(torch.unique(col[keep]).numel())
+                nd = int(torch.unique(kept).numel())
                 distinct[f"{t.name}.col{c}"] = nd
                 total += nd * pairs
             else:
@@ -348,56 +368,105 @@ def whole_job_rate(units_per_rank: int, ms_local: float, world: int):
     return units_per_rank * world / (ms_max / 1e3), ms_max
 
 
-def workload(scale: float, w: int, rank: int):
+def workload(a, rank: int, device="cuda"):
+    """The benchmark's workload, drawn on the device.  scale (the default): the scale
+    configuration, a 1e9-row fact table with int64 Zipf(1.2) keys over 1e8 and 1e6 and two
+    int32 predicates at 10% combined selectivity, joined with 1e8- and 1e6-row dimension
+    tables (int64 primary keys), d = 15, w = 65536.  five_table: the 5-table cyclic graph of
+    the paper's running example at full scale, d = 11, w = 4096.  Every rank draws its own
+    data (weak scaling)."""
     from paper_2102_02440_gb300 import datagen as G
-    return G.five_table(scale=scale, w=w, data_seed=20210205 + rank)
+    if a.workload == "scale":
+        f = a.scale
+        return G.scale_workload_device(n_fact=int(1e9 * f), n_d1=int(1e8 * f), n_d2=max(int(1e6 * min(f, 1.0)), 1000),
+                                       seed=20210209 + rank, device=device)
+    return G.five_table_device(scale=a.scale, w=a.w, data_seed=20210205 + rank, device=device)
+
+
+def host_sample(wl, frac: float):
+    """The first `frac` of every table's rows as host (numpy) columns: the same graph,
+    predicates and declarations, for the CPU oracle."""
+    from paper_2102_02440_gb300 import datagen as G
+    tabs = []
+    for t in wl.tables:
+        n = max(1, int(t.n_rows * frac))
+        cols = [c[:n].cpu().numpy() if hasattr(c, "cpu") else np.ascontiguousarray(c[:n]) for c in t.cols]
+        tabs.append(G.Table(t.name, cols, t.preds, t.key_col, t.edge_id, list(getattr(t, "col_meta", []) or [])))
+    return G.Workload(f"{wl.name} first {frac:.4%}", tabs, wl.edge_u, wl.edge_v, wl.d, wl.w, wl.hash_seed,
+                      wl.data_seed)
 
 
 # ----------------------------------------------------------------------- CPU oracle leg
 
-def cpu_baseline(wl, budget_s: float = 12.0):
-    """The single-threaded oracle (as it stands) on a bounded row sample of every table,
-    proportional to table size; returns tuples/s and the sample description."""
+def _oracle_calibrate(wl, hp):
+    """Seconds of oracle build per row of the workload (mean over its tables, by rows)."""
+    from oracle import oracle as orc
+    per = 0.0
+    for t in wl.tables:
+        n = min(t.n_rows, 20_000)
+        h = host_sample_table(t, n)
+        t0 = time.perf_counter()
+        orc.build_sketch(h, hp, wl.d, wl.w)
+        per += (time.perf_counter() - t0) / n * t.n_rows
+    return per / max(wl.total_rows, 1)
+
+
+def host_sample_table(t, n: int):
+    from paper_2102_02440_gb300 import datagen as G
+    cols = [c[:n].cpu().numpy() if hasattr(c, "cpu") else np.ascontiguousarray(c[:n]) for c in t.cols]
+    return G.Table(t.name, cols, t.preds, t.key_col, t.edge_id)
+
+
+def oracle_step(hwl, hp, masks, estimate: bool = True):
+    """The oracle (single-threaded, as it stands) on a host workload: the push-down build
+    of every sketch, then (estimate) the estimate of every sub-plan.  Returns seconds."""
+    from oracle import oracle as orc
+    t0 = time.perf_counter()
+    built = [orc.build_sketch(t, hp, hwl.d, hwl.w) for t in hwl.tables]
+    if estimate:
+        sk = [tuple(built[hwl.sketch_of(e, end)[0]][0][hwl.sketch_of(e, end)[1]] for end in range(2))
+              for e in range(hwl.n_edges)]
+        surv = np.array([n for _, n in built], np.int64)
+        for m in masks:
+            orc.estimate(hwl.edge_u, hwl.edge_v, sk, surv, hwl.d, hwl.w, int(m))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl, masks, budget_s: float = 12.0):
+    """The oracle on a bounded row sample of every table (the first rows, in proportion to
+    table size): build of every sketch and estimate of every sub-plan; tuples/s and the
+    sample description."""
     from oracle import oracle as orc
     orc.build()
     hp = orc.hash_params(wl.hash_seed, wl.n_edges, wl.d)
-    # calibrate on a small slice, then size the sample to ~budget_s
-    t0 = time.perf_counter()
-    big = wl.tables[0]
-    orc.build_sketch(big, hp, wl.d, wl.w, 0, 20_000)
-    per_row = (time.perf_counter() - t0) / 20_000
-    frac = min(1.0, budget_s / max(per_row * wl.total_rows * 1.5, 1e-9))
-    rows = 0
-    t0 = time.perf_counter()
-    for t in wl.tables:
-        n = max(1, int(t.n_rows * frac))
-        orc.build_sketch(t, hp, wl.d, wl.w, 0, n)
-        rows += n
-    dt = time.perf_counter() - t0
+    frac = min(1.0, budget_s / max(_oracle_calibrate(wl, hp) * wl.total_rows * 1.3, 1e-9))
+    hwl = host_sample(wl, frac)
+    dt = oracle_step(hwl, hp, masks)
+    rows = hwl.total_rows
     return {"value": rows / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {frac:.4%} of every table's rows ({rows} rows, push-down build of all "
-                      f"{sum(len(t.key_col) for t in wl.tables)} sketches, d={wl.d} w={wl.w}), {dt:.1f} s"}
+            "sample": f"first {frac:.4%} of every table's rows ({rows} rows): push-down build of all "
+                      f"{sum(len(t.key_col) for t in wl.tables)} sketches (d={wl.d} w={wl.w}) and the estimate "
+                      f"of all {len(masks)} sub-plans on them, {dt:.1f} s"}
 
 
 def cpu_baseline_all_cores(wl, budget_s: float = 6.0):
     """The same oracle (unchanged, single-threaded code) run as one instance per host core over
     row partitions of a bounded sample, merged by addition (sketches are linear, Sec. 2): each
     thread calls the oracle's C build on its rows (the call releases the interpreter lock), and
-    the per-thread counters are summed.  Returns tuples/s over the sample with cores = threads."""
+    the per-thread counters are summed.  Returns tuples/s over the sample with cores = threads
+    (build only)."""
     import threading as th
 
     from oracle import oracle as orc
     orc.build()
     n_thr = max(1, os.cpu_count() or 1)
     hp = orc.hash_params(wl.hash_seed, wl.n_edges, wl.d)
-    t0 = time.perf_counter()
-    orc.build_sketch(wl.tables[0], hp, wl.d, wl.w, 0, 20_000)
-    per_row = (time.perf_counter() - t0) / 20_000
-    frac = min(1.0, budget_s * n_thr / max(per_row * wl.total_rows * 1.5, 1e-9))
-    ns = [max(1, int(t.n_rows * frac)) for t in wl.tables]
-    parts = [[(t, (ns[i] * j) // n_thr, (ns[i] * (j + 1)) // n_thr) for i, t in enumerate(wl.tables)]
+    frac = min(1.0, budget_s * n_thr / max(_oracle_calibrate(wl, hp) * wl.total_rows * 1.5, 1e-9))
+    hwl = host_sample(wl, frac)
+    ns = [t.n_rows for t in hwl.tables]
+    parts = [[(t, (ns[i] * j) // n_thr, (ns[i] * (j + 1)) // n_thr) for i, t in enumerate(hwl.tables)]
              for j in range(n_thr)]
-    out = [[(np.zeros((len(t.key_col), wl.d, wl.w), np.int32), np.zeros(1, np.int64)) for t in wl.tables]
+    out = [[(np.zeros((len(t.key_col), wl.d, wl.w), np.int32), np.zeros(1, np.int64)) for t in hwl.tables]
            for _ in range(n_thr)]
 
     def work(j):
@@ -411,7 +480,7 @@ def cpu_baseline_all_cores(wl, budget_s: float = 6.0):
         x.start()
     for x in threads:
         x.join()
-    for i in range(len(wl.tables)):   # merge by addition (int32 counters wrap exactly)
+    for i in range(len(hwl.tables)):   # merge by addition (int32 counters wrap exactly)
         for j in range(1, n_thr):
             out[0][i][0][...] = (out[0][i][0].astype(np.int64) + out[j][i][0]).astype(np.int32)
             out[0][i][1][0] += out[j][i][1][0]
@@ -423,42 +492,93 @@ def cpu_baseline_all_cores(wl, budget_s: float = 6.0):
 
 
 def run_reference(a):
+    """The reference arm: the oracle (single-threaded C++, as it stands) on the host cores,
+    each step a bounded row sample of the same workload (build of every sketch + estimate of
+    every sub-plan), sized so that the whole run ends within a few minutes."""
     world, rank, _ = _dist()
     if rank != 0:
         return
-    wl = workload(a.scale, a.w, 0)
-    vals = []
+    from oracle import oracle as orc
+    from paper_2102_02440_gb300 import datagen as G
+    orc.build()
+    wl = workload(a, 0)
+    masks = G.connected_subplans(len(wl.tables), wl.edge_u, wl.edge_v)
+    hp = orc.hash_params(wl.hash_seed, wl.n_edges, wl.d)
+    budget = max(1.0, min(4.0, 150.0 / max(a.steps + a.warmup, 1)))
+    frac = min(1.0, budget / max(_oracle_calibrate(wl, hp) * wl.total_rows * 1.3, 1e-9))
+    hwl = host_sample(wl, frac)
+    del wl
+    secs = []
     for k in range(a.warmup + a.steps):
-        r = cpu_baseline(wl, budget_s=4.0)
+        dt = oracle_step(hwl, hp, masks)
         if k >= a.warmup:
-            vals.append(r["value"])
-    v = statistics.median(vals)
-    r["value"] = v
+            secs.append(dt)
+    ms = statistics.mean(secs) * 1e3
+    v = hwl.total_rows / (ms / 1e3)
+    sample = (f"first {frac:.4%} of every table's rows ({hwl.total_rows} rows): push-down build of all "
+              f"{sum(len(t.key_col) for t in hwl.tables)} sketches and the estimate of all {len(masks)} sub-plans")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": wl.total_rows / v * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": wl.name, "rows_per_step": wl.total_rows, "sample": r["sample"]},
-            "cpu_baseline": r, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": hwl.name, "sample_of": workload_name(a), "rows_per_step": hwl.total_rows,
+                       "sample": sample, "step": "one oracle pass over the sample (ms_per_step is that pass)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def workload_name(a) -> str:
+    if a.workload == "scale":
+        f = a.scale
+        return (f"scale: fact {int(1e9 * f)} rows (int64 Zipf(1.2) keys over {int(1e8 * f)} and "
+                f"{max(int(1e6 * min(f, 1.0)), 1000)}, 10% predicates), dimensions {int(1e8 * f)} and "
+                f"{max(int(1e6 * min(f, 1.0)), 1000)} rows, d15 w65536")
+    return f"five_table scale={a.scale} d11 w{a.w}"
 
 
 # ----------------------------------------------------------------------- GPU leg
 
-def run_ours(a):
+def cw_peak(dev, d: int, n_pairs: int):
+    """Measured rate of the build's hash arithmetic on this GPU (cmp_microbench_cw: no
+    memory traffic, no counter updates), evaluations/s, for both forms: shared powers and
+    Horner.  Median of 5 timed launches after a warm-up."""
     import torch
 
+    from paper_2102_02440_gb300 import compass as K
+    hp = K.hash_params_u64(0xC0FFEE, 1, min(max(n_pairs, 1), 64)).reshape(-1)
+    hd = torch.from_numpy(hp.view(np.int64)).to(dev)
+    out = torch.zeros(1, dtype=torch.int64, device=dev)
+    n_keys = 1 << 26
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for form, name in ((0, "shared_powers"), (1, "horner")):
+        np_ = min(max(n_pairs, 1), 64)
+        K.cmp_microbench_cw(hd.data_ptr(), np_, n_keys, 65536, form, out.data_ptr(), K.stream_handle())
+        ts = []
+        for _ in range(5):
+            s.record()
+            K.cmp_microbench_cw(hd.data_ptr(), np_, n_keys, 65536, form, out.data_ptr(), K.stream_handle())
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        res[name] = n_keys * np_ / (statistics.median(ts) / 1e3)
+    return res
+
+
+def measure(a, wl, dev, world: int, rank: int, headline: bool):
+    """One workload's step, timed: the batched build, presort + cross ranks, the estimate of
+    every connected sub-plan, the learned combiner and the enumeration, captured as one CUDA
+    graph and replayed.  Returns the fields of the bench line (headline) or of an extra key."""
+    import torch
+
+    from paper_2102_02440_gb300 import autotune as AT
     from paper_2102_02440_gb300 import compass as K
     from paper_2102_02440_gb300 import datagen as G
     from paper_2102_02440_gb300 import pipeline as P
 
-    world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    wl = workload(a.scale, a.w, rank)
     dw = P.DeviceWorkload(wl, device=dev)
     masks = G.connected_subplans(len(wl.tables), wl.edge_u, wl.edge_v)
     # launch shapes picked by the autotuner on this workload (outside the timed region)
-    from paper_2102_02440_gb300 import autotune as AT
     cfg_build, tuned_build = AT.tune_build(dw, reps=2, cache_path=a.tune_cache)
     sig = f"estimate d{wl.d} w{wl.w} tables{len(wl.tables)} masks{','.join(str(m) for m in masks)}"
     cfg_est, tuned_est = AT.tune_estimate(lambda c: P.DeviceEstimator(dw, masks, cfg=c), reps=1,
@@ -471,7 +591,7 @@ def run_ours(a):
     # cmp_sketch_f2 launch over every sketch (the tables' counters are one buffer), then the
     # features pick each sub-plan's two sketches by index
     n_sub = len(masks)
-    comb = P.Combiner(wl.d + 2, 64, seed=0, device=dev, skip=wl.d // 2)
+    comb, comb_src = P.Combiner.for_sketches(wl.d, wl.w, device=dev)
     n_sk = dw.counters_all.shape[0]
     f2_all = torch.zeros(n_sk, dtype=torch.float64, device=dev)
     feat = torch.empty((n_sub, wl.d + 2), dtype=torch.float32, device=dev)
@@ -479,7 +599,6 @@ def run_ours(a):
     est_comb = torch.empty(n_sub, dtype=torch.float64, device=dev)
     first_sketch = np.cumsum([0] + [t.k for t in dw.tables])
     f2_idx_host = np.full((n_sub, 2), -1, np.int32)
-    two = []
     for q, m in enumerate(masks):
         if bin(m).count("1") == 2:
             tu, tv = [t for t in range(len(wl.tables)) if (m >> t) & 1]
@@ -487,14 +606,14 @@ def run_ours(a):
             for end in range(2):
                 t, si = wl.sketch_of(e, end)
                 f2_idx_host[q, end] = first_sketch[t] + si
-            two.append(q)
     f2_idx = torch.from_numpy(f2_idx_host).to(dev)
 
     def combiner(s):
         K.cmp_sketch_f2(dw.counters_all.data_ptr(), n_sk, wl.d, wl.w, f2_all.data_ptr(), s)
         K.cmp_mlp_features_indexed(est.row_est.data_ptr(), n_sub, wl.d, f2_all.data_ptr(), f2_idx.data_ptr(),
                                    feat.data_ptr(), s)
-        K.cmp_mlp_infer(comb.params.data_ptr(), wl.d + 2, 64, wl.d // 2, feat.data_ptr(), n_sub, y_mlp.data_ptr(), s)
+        K.cmp_mlp_infer(comb.params.data_ptr(), wl.d + 2, comb.nh, comb.skip, feat.data_ptr(), n_sub,
+                        y_mlp.data_ptr(), s)
         K.cmp_mlp_combine(est.est.data_ptr(), y_mlp.data_ptr(), n_sub, est_comb.data_ptr(), s)
 
     # join-order enumeration (Algorithm 1, max_plans = 10) over the combined estimates
@@ -540,9 +659,8 @@ def run_ours(a):
         torch.cuda.synchronize(dev)
         dw.check_status()
         if not (torch.equal(eager_out[3], enum.order) and torch.equal(eager_out[0], est.row_est) and
-                torch.equal(eager_out[1].nan_to_num(-1.0),
-                                                                     est.est.nan_to_num(-1.0))
-                and torch.equal(eager_out[2].nan_to_num(-1.0), est_comb.nan_to_num(-1.0))):
+                torch.equal(eager_out[1].nan_to_num(-1.0), est.est.nan_to_num(-1.0)) and
+                torch.equal(eager_out[2].nan_to_num(-1.0), est_comb.nan_to_num(-1.0))):
             raise RuntimeError("graph replay of the step differs from the eager step")
 
     def timed_step(ev0, ev1):
@@ -554,9 +672,10 @@ def run_ours(a):
         ev1.record(stream)
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(a.steps)]
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
+    sampler = ClockSampler(dev.index if dev.index is not None else 0) if headline else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
     _barrier(world)
     torch.cuda.synchronize(dev)
     with torch.cuda.stream(stream):
@@ -565,10 +684,9 @@ def run_ours(a):
             timed_step(*evs[k])
     torch.cuda.synchronize(dev)
     _barrier(world)
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     dw.check_status()
-    step_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    ms = statistics.mean(step_ms)
+    ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     # per-phase split from eager steps with events between the phases (outside the timing)
     pevs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(a.steps)]
     with torch.cuda.stream(stream):
@@ -581,51 +699,67 @@ def run_ours(a):
     value, ms_max = whole_job_rate(rows, ms, world)
     phase = {n: statistics.mean(p[i] for p in per)
              for i, n in enumerate(("build", "presort", "estimate", "combiner", "enumerate"))}
-    n_est = len(masks)
 
-    # roofline of the dominant phase: the batched build (zero spans, key range, clearing,
-    # counting, row build kernel, hashing of the aggregated columns; ~60% of the step),
-    # integer ALU bound on the hash evaluations it must do, with its HBM fraction beside it
+    # roofline of the dominant phase, the batched build: HBM-bound on the columns it reads,
+    # with the hashing it must do against the measured rate of the same arithmetic beside it
     surv = dw.survivors.cpu().numpy()
     updates = int(sum(int(surv[i]) * len(t.key_col) * wl.d for i, t in enumerate(wl.tables)))
     cw_evals, distinct = build_work(wl, dw, dedupe=bool(tuned_build["cfg"].get("dedupe", 1)))
     hbm_peak, peak_kind = _peaks()
     col_bytes = wl.column_bytes()
     build_s = phase["build"] / 1e3
-    ach = cw_evals * CW_INSTR / build_s
-    roof = {"bound": "alu", "achieved": ach / 1e12, "peak": INT_ISSUE_PEAK / 1e12, "unit": "Tinstr/s",
-            "frac": ach / INT_ISSUE_PEAK, "traffic": _kernel_traffic("build_phase"),
-            "kernel": "batched build: k_zero_spans, k_agg_stats, k_agg_zero, k_agg_count, k_sketch_build, k_agg_hash",
-            "algorithmic": f"{cw_evals} CW evaluations x {CW_INSTR} int32 instr (one per distinct surviving key "
-                           f"and sketch row on aggregated columns, one per surviving tuple and sketch row elsewhere; "
-                           f"{updates} tuple updates)",
-            "distinct_keys": distinct,
-            "peak_derivation": "152 SMs x 4 SMSP x 32 lanes x 2.07 GHz (one int32 warp instruction per SMSP-clock)",
-            "hbm": {"achieved_gbs": col_bytes / build_s / 1e9, "peak_gbs": hbm_peak,
-                    "frac": col_bytes / build_s / 1e9 / hbm_peak, "peak_kind": peak_kind,
-                    "algorithmic_bytes": col_bytes}}
-    # the estimate: triangle path (preparation + sweep) for the cyclic sub-plans, generic
-    # contraction for the trees; exact 128-bit operations of those algorithms
+    peaks = cw_peak(dev, wl.d, max(len(t.key_col) for t in wl.tables) * wl.d)
+    alu_s = cw_evals / max(peaks.values())
+    tkey = "build_scale" if wl.d == 15 else "build_five_table"
+    roof = {"bound": "hbm", "achieved": col_bytes / build_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+            "frac": col_bytes / build_s / 1e9 / hbm_peak, "traffic": _kernel_traffic(tkey),
+            "peak_kind": peak_kind,
+            "kernel": "the batched build (one cmp_sketch_build_batched call: zeroing, key counting, unique-key "
+                      "hashing, row kernel, hashing of the counted keys)",
+            "algorithmic": f"{col_bytes} bytes: every referenced column read once ({rows} rows)",
+            "alu": {"cw_evaluations": cw_evals, "tuple_updates": updates, "distinct_keys": distinct,
+                    "achieved_evals_per_s": cw_evals / build_s,
+                    "measured_peak_evals_per_s": peaks,
+                    "frac": alu_s / build_s,
+                    "peak_source": "cmp_microbench_cw on this GPU (the same arithmetic, no memory traffic)"}}
     est_ops, n_tri_sub, n_gen_sub = triangle_ops(dw, masks)
     est_s = phase["estimate"] / 1e3
-    op_peak = INT_ISSUE_PEAK / OP128_INSTR
-    roof_est = {"bound": "alu", "achieved": est_ops / est_s / 1e12, "peak": op_peak / 1e12,
-                "unit": "T int128-op/s", "frac": est_ops / est_s / op_peak,
-                "traffic": _kernel_traffic("estimate_phase"),
-                "kernel": "k_estimate_items (trees), k_tri_nodes + k_tri_prep + k_tri_sweep (triangles), k_estimate_finalize",
-                "algorithmic": f"{est_ops} exact 128-bit operations ({n_tri_sub} triangle, {n_gen_sub} other sub-plans)",
-                "peak_derivation": f"152 SMs x 4 SMSP x 32 lanes x 2.07 GHz / {OP128_INSTR} int32 instr per op"}
+    out = {"value": value, "ms_per_step": ms_max, "rows_per_step": rows, "phases_ms": phase,
+           "subplans": len(masks), "subplan_estimates_per_s": len(masks) / est_s,
+           "build_only_tuples_per_s": rows / build_s, "roofline": roof,
+           "estimate_ops": {"exact_128bit_ops": est_ops, "ops_per_s": est_ops / est_s,
+                            "triangle_subplans": n_tri_sub, "other_subplans": n_gen_sub},
+           "plan": {"order": [wl.tables[t].name for t in enum.plans()[0][0]], "cost": enum.plans()[0][1],
+                    "search": dict(zip(("complete_plans", "extensions", "pruned"), enum.plans()[0][2]))},
+           "autotuned": {"build": tuned_build["cfg"], "estimate": tuned_est["cfg"]},
+           "combiner": comb_src, "survivors": [int(x) for x in surv],
+           "config": {"workload": wl.name, "rows_per_step": rows, "tables": len(wl.tables),
+                      "sketches": sum(len(t.key_col) for t in wl.tables), "d": wl.d, "w": wl.w,
+                      "subplans": len(masks), "column_bytes": col_bytes,
+                      "l2": "256 MB buffer written between steps, outside the per-step events; inputs "
+                            f"{col_bytes / 1e9:.2f} GB",
+                      "step": "one captured CUDA graph replayed per step" if graph is not None else "eager launches",
+                      "phases": "from eager steps with events between phases",
+                      "parallelism": f"replicas x{world} (independent queries)"}}
+    if clocks is not None:
+        out["clocks"] = clocks
 
     # end to end through the public API: pinned host columns -> device, path, estimates -> host
-    e2e = None
-    if not a.no_e2e:
-        host_cols = [[torch.from_numpy(np.ascontiguousarray(c)).pin_memory() for c in t.cols] for t in wl.tables]
+    if headline and not a.no_e2e:
+        host_cols = []
+        for t in dw.tables:
+            hc = []
+            for c in t.cols:
+                h = torch.empty(c.shape, dtype=c.dtype, pin_memory=True)
+                h.copy_(c)
+                hc.append(h)
+            host_cols.append(hc)
         h2d = sum(c.numel() * c.element_size() for tc in host_cols for c in tc)
         out_host = torch.empty(n_sub, dtype=torch.float64).pin_memory()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         tms = []
         with torch.cuda.stream(stream):
-            for k in range(a.warmup + a.steps):
+            for k in range(min(a.warmup, 2) + a.steps):
                 flush.zero_()
                 e0.record(stream)
                 for tc, t in zip(host_cols, dw.tables):
@@ -638,46 +772,134 @@ def run_ours(a):
                 out_host.copy_(est_comb, non_blocking=True)
                 e1.record(stream)
                 e1.synchronize()
-                if k >= a.warmup:
+                if k >= min(a.warmup, 2):
                     tms.append(e0.elapsed_time(e1))
         e2e_ms = _max_over_ranks(statistics.mean(tms), world)
-        e2e = {"value": rows * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(out_host.numel() * 8), "ms_per_step": e2e_ms}
+        out["e2e"] = {"value": rows * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(out_host.numel() * 8), "ms_per_step": e2e_ms}
+        del host_cols
+    if headline and rank == 0 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, masks)
+        out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(wl)
+    # our kernel launches per step: build (zeroing; clearing + counting with aggregated key
+    # columns; the unique-key kernel; the row kernel when it has items; hashing of the counted
+    # keys), presort (one launch for w <= 16384, else chunks + 3 merges + split per 64 rows)
+    # and cross ranks, estimate (int64 items + int128 recompute for tree sub-plans, 3 triangle
+    # launches, finalize), combiner (4), enumeration (1)
+    h = dw._plan[0][0] if dw._plan else None
+    info = P.build_plan_info(dw)
+    n_rows_sorted = sum(t.k for t in dw.tables) * wl.d
+    presort_l = 1 if wl.w <= 16384 else 5 * ((n_rows_sorted + 63) // 64)
+    est_l = (2 if n_gen_sub > sum(1 for m in masks if bin(m).count("1") == 1) else 0) + (3 if n_tri_sub else 0) + 1
+    out["gpu_launches_per_step"] = info["launches"] + presort_l + 1 + est_l + 4 + 1
+    return out
 
-    cpu = None
-    if rank == 0 and not a.no_cpu_baseline:
-        cpu = cpu_baseline(wl)
-        cpu["all_cores"] = cpu_baseline_all_cores(wl)
 
-    # estimate: generic int64 + int128 recompute when trees are planned, triangle node messages +
-    # preparation + sweep when triangles are, finalize
-    est_launches = (2 if n_gen_sub > sum(1 for m in masks if bin(m).count("1") == 1) else 0) + \
-        (3 if n_tri_sub else 0) + 1
-    # build: zero spans + build kernel, plus key range, clearing, counting and hashing of the
-    # aggregated key columns when the plan aggregates (it then has a workspace)
-    build_launches = 2 + (4 if dw._plan[2] else 0)
-    # presort + cross ranks of all tables: one launch each; combiner: self-join sizes, features,
-    # inference, combination; enumeration: one launch
-    launches_per_step = build_launches + 2 + est_launches + 4 + 1
+def measure_batched(a, dev):
+    """The batched-enumeration configuration on the device: 64 synthetic graphs (chains,
+    stars, cycles of 4..17 tables, rows log-uniform in [1e4, 1e8], Zipf 0.5..1.5 keys over
+    1e5, ~50% of tables with a point or range predicate), d = 11, w = 1024.  Build of every
+    table in one batched launch vs one launch per table; the estimate of every connected
+    sub-plan in one plan (cached subtree messages and the star lattice on), replayed as a
+    CUDA graph, vs one plan launch per sub-plan (timed on a sample of 2000)."""
+    import torch
+
+    from paper_2102_02440_gb300 import compass as K
+    from paper_2102_02440_gb300 import datagen as G
+    from paper_2102_02440_gb300 import pipeline as P
+    t0 = time.perf_counter()
+    graphs = G.graph_batch_device(64, 4, 17, rows_lo=10_000, rows_hi=100_000_000, d=11, w=1024, device=dev,
+                                  rows_scale=a.c3_rows_scale)
+    gen_s = time.perf_counter() - t0
+    gb = P.GraphBatch(graphs, device=dev)
+    sg, sm = [], []
+    for gi, g in enumerate(graphs):
+        ms_ = G.connected_subplans(len(g.tables), g.edge_u, g.edge_v)
+        sg += [gi] * len(ms_)
+        sm += ms_
+    sg, sm = np.array(sg, np.int32), np.array(sm, np.uint64)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        return statistics.median(ts)
+
+    ms_build_b = timed(gb.build_batched)
+    ms_build_t = timed(gb.build_per_table)
+    gb.build_batched()
+    gb.presort()
+    reuse = K.cmp_estimate_cfg.make(threads=256, ctas_per_sm=4, cond_chunk=16,
+                                    flags=K.CMP_EST_CACHE_MESSAGES | K.CMP_EST_STAR_LATTICE)
+    plan = gb.plan(sg, sm, reuse)
+    st = torch.cuda.Stream(dev)
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        plan.run(stream=st)
+        st.synchronize()
+        g_est = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_est, stream=st):
+            plan.run(stream=st)
+        ms_est_b = timed(lambda: (g_est.replay(), st.synchronize()))
+    rng = np.random.default_rng(0)
+    samp = rng.choice(sm.size, min(2000, sm.size), replace=False)
+    plans = [gb.plan(sg[q:q + 1], sm[q:q + 1]) for q in samp]
+    ms_est_1 = timed(lambda: [p.run() for p in plans], 1)
+    n_nan = int(torch.isnan(plan.est).sum().item())
+    gb.dw.status.zero_()
+    return {"workload": f"64 graphs, {len(gb.wl.tables)} tables, {gb.total_rows} rows, {int(sm.size)} sub-plans, "
+                        f"d11 w1024 (rows log-uniform in [1e4, 1e8] x {a.c3_rows_scale})",
+            "generation_s": gen_s, "column_bytes": gb.wl.column_bytes(),
+            "build_ms": {"batched_one_launch": ms_build_b, "per_table_launches": ms_build_t,
+                         "speedup": ms_build_t / ms_build_b, "tuples_per_s": gb.total_rows / (ms_build_b / 1e3)},
+            "estimate": {"one_plan_graph_replayed_ms": ms_est_b, "subplan_estimates_per_s": sm.size / (ms_est_b / 1e3),
+                         "per_subplan_launches_per_s": samp.size / (ms_est_1 / 1e3),
+                         "speedup": (sm.size / (ms_est_b / 1e3)) / (samp.size / (ms_est_1 / 1e3)),
+                         "flags": "CMP_EST_CACHE_MESSAGES | CMP_EST_STAR_LATTICE, 256 threads x 4 CTAs/SM, chunk 16",
+                         "subplans_beyond_int128": n_nan}}
+
+
+def run_ours(a):
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = workload(a, rank, device=dev)
+    r = measure(a, wl, dev, world, rank, headline=True)
+    del wl
+    torch.cuda.empty_cache()
+    extras = {}
+    if not a.no_extras and world == 1:
+        from paper_2102_02440_gb300 import datagen as G
+        a5 = argparse.Namespace(**vars(a))
+        a5.workload, a5.scale, a5.w = "five_table", 1.0, 4096
+        wl5 = G.five_table_device(scale=1.0, w=4096, data_seed=20210205 + rank, device=dev)
+        m5 = measure(a5, wl5, dev, world, rank, headline=False)
+        extras["five_table"] = {k: m5[k] for k in ("value", "ms_per_step", "phases_ms", "subplan_estimates_per_s",
+                                                    "build_only_tuples_per_s", "roofline", "plan", "config",
+                                                    "estimate_ops", "gpu_launches_per_step")}
+        del wl5, m5
+        torch.cuda.empty_cache()
+        extras["batched_enumeration"] = measure_batched(a, dev)
+        torch.cuda.empty_cache()
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-                "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": {"workload": wl.name, "rows_per_step": rows, "tables": len(wl.tables),
-                           "sketches": sum(len(t.key_col) for t in wl.tables), "d": wl.d, "w": wl.w,
-                           "subplans": n_est, "column_bytes": col_bytes,
-                           "l2": "256 MB buffer written between steps, outside the per-step events",
-                           "step": "one captured CUDA graph replayed per step" if graph is not None else "eager launches",
-                           "phases": "from eager steps with events between phases",
-                           "parallelism": f"replicas x{world} (independent queries)"},
-                "phases_ms": phase, "subplan_estimates_per_s": n_est / (phase["estimate"] / 1e3),
-                "plan": {"order": [wl.tables[t].name for t in enum.plans()[0][0]], "cost": enum.plans()[0][1],
-                         "search": dict(zip(("complete_plans", "extensions", "pruned"), enum.plans()[0][2]))},
-                "autotuned": {"build": tuned_build["cfg"], "estimate": tuned_est["cfg"]},
-                "build_only_tuples_per_s": rows / (phase["build"] / 1e3),
-                "survivors": [int(x) for x in surv],
-                "roofline": roof, "roofline_estimate": roof_est, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": launches_per_step * a.steps}
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": r["config"],
+                "roofline": r["roofline"], "cpu_baseline": r.get("cpu_baseline"), "e2e": r.get("e2e"),
+                "clocks": r.get("clocks"), "gpu_launches": r["gpu_launches_per_step"] * a.steps,
+                "phases_ms": r["phases_ms"], "subplan_estimates_per_s": r["subplan_estimates_per_s"],
+                "build_only_tuples_per_s": r["build_only_tuples_per_s"], "estimate_ops": r["estimate_ops"],
+                "plan": r["plan"], "autotuned": r["autotuned"], "combiner": r["combiner"],
+                "survivors": r["survivors"], **extras}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -204,6 +204,17 @@ cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_tables, int3
 cmp_status cmp_sketch_build_batched(const void* plan_host, const void* plan_dev, const cmp_hash* hash_dev,
                                     void* ws_dev, size_t ws_bytes, int32_t* status_dev, void* stream);
 
+/* Counts of an encoded batched-build plan (host only, no GPU): tables, aggregated key
+ * columns, unique-key slabs and items and that kernel's grid, the row kernel's grid, the
+ * workspace, and the number of kernels one cmp_sketch_build_batched call enqueues.
+ * CMP_EINVAL for a NULL argument or a blob that is not a build plan. */
+typedef struct {
+  int32_t n_tables, n_agg, n_unique_slabs, unique_grid;
+  int64_t n_unique_items, row_grid, ws_bytes;
+  int32_t launches, reserved;
+} cmp_build_plan_info;
+cmp_status cmp_build_plan_stats(const void* plan_host, cmp_build_plan_info* info);
+
 /* ------------------------------------------------------------------- estimation */
 
 /* Presort of sketch rows by magnitude (prepares the merged contraction of Sec. 4.2: the
@@ -428,6 +439,21 @@ cmp_status cmp_part_estimate_ws_bytes(const cmp_part_join* join, int32_t d, size
 cmp_status cmp_part_estimate(const cmp_part_join* join, int32_t d, void* ws_dev, size_t ws_bytes, double* est_dev,
                              int64_t* row_est_dev, int32_t* status_dev, void* stream);
 
+/* cmp_part_estimate with options.  The contraction of long int32 rows streams them through
+ * shared memory with bulk copies, each waited for on an mbarrier; a wait that does not see
+ * its copy complete within wait_polls polls gives up: the warp writes CMP_ETIMEOUT to the
+ * status word, waits (with the default bound) for its copies still in flight, and returns,
+ * leaving that launch's outputs incomplete.  wait_polls: -1 the default (2^22 polls, which
+ * no healthy copy comes near), 0 .. 2^31-1 a smaller budget (0 gives up at the first wait,
+ * to exercise the timeout path).  cfg NULL: as cmp_part_estimate. */
+typedef struct {
+  int32_t wait_polls;
+  int32_t reserved;
+} cmp_part_estimate_cfg;
+cmp_status cmp_part_estimate_ex(const cmp_part_join* join, int32_t d, void* ws_dev, size_t ws_bytes, double* est_dev,
+                                int64_t* row_est_dev, int32_t* status_dev, const cmp_part_estimate_cfg* cfg,
+                                void* stream);
+
 /* ------------------------------------------------------ join-order enumeration */
 /* Algorithm 1 of Sec. 5 on the estimates of a cmp_estimate run, for every join graph of a
  * batch at once (one thread per graph; the estimates stay on the device).  From every source
@@ -520,6 +546,18 @@ cmp_status cmp_mlp_train_step(float* params_dev, float* adam_m_dev, float* adam_
                               int32_t skip, const float* x_dev, const float* y_dev, int64_t n, float huber_delta,
                               float lr, int32_t step, float* loss_dev, float* grad_dev, void* ws_dev, size_t ws_bytes,
                               void* stream);
+
+/* ------------------------------------------------------------ microbenchmark */
+/* The integer roofline of the build's hashing on the GPU at hand: the Carter-Wegman
+ * bucket and sign (cmp_hash; Sec. 3.1-3.2 ask for a per-row bucket hash and a 4-wise sign
+ * family) of keys 0 .. n_keys-1 for each of the n_pairs parameter sets hash_dev[0..n_pairs)
+ * (1..64), with no memory traffic and no counter updates, in the two forms the build uses:
+ * form 0 shares the key's powers x^2, x^3 among the pairs (aggregated and int32-slab
+ * paths), form 1 evaluates each pair by Horner's rule (packed-slab path).  w: a power of
+ * two (the bucket mask).  XORs a checksum of every evaluation into *out_dev (one uint64,
+ * device) so that none can be skipped.  n_keys <= 2^31.  Asynchronous on `stream`. */
+cmp_status cmp_microbench_cw(const cmp_hash* hash_dev, int32_t n_pairs, int64_t n_keys, int32_t w, int32_t form,
+                             uint64_t* out_dev, void* stream);
 
 /* Size of the device workspace built into the library for cmp_estimate_noalloc. */
 #define CMP_NOALLOC_WS_BYTES (32u << 20)

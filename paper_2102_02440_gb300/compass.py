@@ -65,6 +65,16 @@ class cmp_build_cfg(C.Structure):
         return cls(mode, pairs_per_slab, threads, tile_rows, dedupe, ctas_per_sm, aggregate, unique)
 
 
+class cmp_build_plan_info(C.Structure):
+    _fields_ = [("n_tables", C.c_int32), ("n_agg", C.c_int32), ("n_unique_slabs", C.c_int32),
+                ("unique_grid", C.c_int32), ("n_unique_items", C.c_int64), ("row_grid", C.c_int64),
+                ("ws_bytes", C.c_int64), ("launches", C.c_int32), ("reserved", C.c_int32)]
+
+
+class cmp_part_estimate_cfg(C.Structure):
+    _fields_ = [("wait_polls", C.c_int32), ("reserved", C.c_int32)]
+
+
 class cmp_estimate_plan_info(C.Structure):
     _fields_ = [("n_sub", C.c_int64), ("n_items", C.c_int64), ("n_ops", C.c_int64), ("n_jobs", C.c_int64),
                 ("n_job_items", C.c_int64), ("n_tri", C.c_int64), ("n_levels", C.c_int32), ("grid", C.c_int32),
@@ -150,6 +160,10 @@ _SIGS = {
     "cmp_enumerate": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(cmp_enum_cfg), C.c_void_p,
                                   C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cmp_estimate_noalloc": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cmp_build_plan_stats": (C.c_int32, [C.c_void_p, C.POINTER(cmp_build_plan_info)]),
+    "cmp_part_estimate_ex": (C.c_int32, [C.POINTER(cmp_part_join), C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.POINTER(cmp_part_estimate_cfg), C.c_void_p]),
+    "cmp_microbench_cw": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "cmp_part_build": (C.c_int32, [C.POINTER(cmp_table), C.c_int32, C.POINTER(C.c_int32), C.c_void_p, C.c_int32,
                                    C.c_void_p, C.c_void_p, C.POINTER(cmp_part_build_cfg), C.c_void_p]),
     "cmp_part_estimate_ws_bytes": (C.c_int32, [C.POINTER(cmp_part_join), C.c_int32, C.POINTER(C.c_size_t)]),
@@ -332,6 +346,16 @@ def cmp_estimate_noalloc(plan_host: int, plan_dev: int, est_dev: int, row_est_de
                                                               stream))
 
 
+def cmp_build_plan_stats(plan_host: int) -> cmp_build_plan_info:
+    info = cmp_build_plan_info()
+    _check("cmp_build_plan_stats", lib().cmp_build_plan_stats(plan_host, C.byref(info)))
+    return info
+
+
+def cmp_microbench_cw(hash_dev: int, n_pairs: int, n_keys: int, w: int, form: int, out_dev: int, stream: int):
+    _check("cmp_microbench_cw", lib().cmp_microbench_cw(hash_dev, n_pairs, n_keys, w, form, out_dev, stream))
+
+
 def cmp_enum_plan_bytes(graphs, sub_graph, sub_mask) -> tuple[int, int]:
     import numpy as np
     g = (cmp_graph * len(graphs))(*graphs)
@@ -386,6 +410,13 @@ def cmp_part_estimate(join: cmp_part_join, d: int, ws_dev: int, ws_bytes: int, e
                       status_dev: int, stream: int):
     _check("cmp_part_estimate", lib().cmp_part_estimate(C.byref(join), d, ws_dev, ws_bytes, est_dev, row_est_dev,
                                                         status_dev, stream))
+
+
+def cmp_part_estimate_ex(join: cmp_part_join, d: int, ws_dev: int, ws_bytes: int, est_dev: int, row_est_dev: int,
+                         status_dev: int, wait_polls: int, stream: int):
+    cfg = cmp_part_estimate_cfg(wait_polls, 0)
+    _check("cmp_part_estimate_ex", lib().cmp_part_estimate_ex(C.byref(join), d, ws_dev, ws_bytes, est_dev, row_est_dev,
+                                                              status_dev, C.byref(cfg), stream))
 
 
 def cmp_mlp_param_count(nin: int, nh: int) -> int:

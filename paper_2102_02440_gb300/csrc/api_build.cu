@@ -699,3 +699,23 @@ extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void
   return launch_agg_hash(a, h.n_agg > 0 ? h.hash_grid : 0, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
 }
 
+
+extern "C" cmp_status cmp_build_plan_stats(const void* plan_host, cmp_build_plan_info* info) {
+  if (!plan_host || !info) return CMP_EINVAL;
+  BuildPlanHdr h;
+  std::memcpy(&h, plan_host, sizeof(h));
+  if (h.magic != kBuildPlanMagic || h.version != kBuildPlanVersion) return CMP_EINVAL;
+  info->n_tables = h.n_tables;
+  info->n_agg = int32_t(h.n_agg);
+  info->n_unique_slabs = int32_t(h.n_uslab);
+  info->unique_grid = h.n_uitems > 0 ? h.u_grid : 0;
+  info->n_unique_items = h.n_uitems;
+  info->row_grid = h.shape.grid;
+  info->ws_bytes = h.ws_bytes;
+  // zeroing; clearing (+ counting when it has chunks) and hashing of the counted keys; the
+  // unique-key kernel; the row kernel
+  info->launches = 1 + (h.n_agg > 0 ? 1 + (h.cnt_grid > 0 ? 1 : 0) + (h.hash_grid > 0 ? 1 : 0) : 0) +
+                   (h.n_uitems > 0 && h.u_grid > 0 ? 1 : 0) + (h.shape.grid > 0 ? 1 : 0);
+  info->reserved = 0;
+  return CMP_OK;
+}

@@ -48,6 +48,7 @@ struct PartStep {
   int32_t vec;     // int32 x and v, w, x_rs, v_rs multiples of 4 and 16-byte aligned rows
   uint32_t* oor;   // [d] out-of-range flags
   int32_t* status; // device status word (a bounded wait that ran out)
+  uint32_t wait_polls;  // bulk kernel: polls of each chunk's wait before it gives up
 };
 
 namespace {
@@ -377,10 +378,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// every lane polls; true once every lane has seen the phase complete
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity) {
+// every lane polls, at most `limit` times; true once every lane has seen the phase complete
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, uint32_t limit) {
   bool done = false;
-  for (uint32_t it = 0; it < kBulkWaitLimit && !done; it++) done = mbar_try_wait(bar, parity);
+  for (uint32_t it = 0; it < limit && !done; it++) done = mbar_try_wait(bar, parity);
   return __all_sync(0xffffffffu, done);
 }
 
@@ -445,10 +446,12 @@ __global__ void __launch_bounds__(kBulkWarps * 32) k_part_dot_bulk(const __grid_
   int st = 0;
   uint32_t parity = 0;
   for (int64_t k = 0; k < K; k++) {
-    if (!mbar_wait_warp(bar + st, parity)) {
+    if (!mbar_wait_warp(bar + st, parity, S.wait_polls)) {
       if (lane == 0) set_status(S.status, CMP_ETIMEOUT);
-      for (int64_t kk = k; kk < min(K, k + kBulkStages); kk++)  // copies still in flight
-        mbar_wait_warp(bar + int(kk % kBulkStages), uint32_t((kk / kBulkStages) & 1));
+      // the copies still in flight, each waited for with the full bound, so that none is
+      // left writing this CTA's shared memory after it exits
+      for (int64_t kk = k; kk < min(K, k + kBulkStages); kk++)
+        mbar_wait_warp(bar + int(kk % kBulkStages), uint32_t((kk / kBulkStages) & 1), kBulkWaitLimit);
       return;
     }
     const int n4 = int(chunk_bytes(cur.c) / 16);
@@ -769,7 +772,15 @@ cmp_status cmp_part_estimate_ws_bytes(const cmp_part_join* join, int32_t d, size
 
 cmp_status cmp_part_estimate(const cmp_part_join* join, int32_t d, void* ws_dev, size_t ws_bytes, double* est_dev,
                              int64_t* row_est_dev, int32_t* status_dev, void* stream) {
+  return cmp_part_estimate_ex(join, d, ws_dev, ws_bytes, est_dev, row_est_dev, status_dev, nullptr, stream);
+}
+
+cmp_status cmp_part_estimate_ex(const cmp_part_join* join, int32_t d, void* ws_dev, size_t ws_bytes, double* est_dev,
+                                int64_t* row_est_dev, int32_t* status_dev, const cmp_part_estimate_cfg* cfg,
+                                void* stream) {
   if (!est_dev) return CMP_EINVAL;
+  if (cfg && cfg->wait_polls < -1) return CMP_EINVAL;
+  const uint32_t polls = (cfg && cfg->wait_polls >= 0) ? uint32_t(cfg->wait_polls) : kBulkWaitLimit;
   PartPlan P;
   const cmp_status st = make_plan(join, d, &P);
   if (st != CMP_OK) return st;
@@ -797,6 +808,7 @@ cmp_status cmp_part_estimate(const cmp_part_join* join, int32_t d, void* ws_dev,
     S.d = d;
     S.oor = oor;
     S.status = status_dev;
+    S.wait_polls = polls;
     const bool xw = s.x.table < 0, vw = s.v.table < 0;
     S.vec = !xw && !vw && s.w % 4 == 0 && s.x.rs % 4 == 0 && s.v.rs % 4 == 0 &&
             (reinterpret_cast<uintptr_t>(S.x) & 15) == 0 && (reinterpret_cast<uintptr_t>(S.v) & 15) == 0;

@@ -216,6 +216,40 @@ def five_table(scale: float = 1.0, d: int = 11, w: int = 4096, d1_sel_pct: int =
                     [3, 2, 2, 0, 4], [1, 1, 0, 1, 0], d, w, hash_seed, data_seed)
 
 
+def five_table_device(scale: float = 1.0, d: int = 11, w: int = 4096, d1_sel_pct: int = 20, s: float = 1.1,
+                      data_seed: int = 20210205, hash_seed: int = 0xC0FFEE + 1, device="cuda") -> Workload:
+    """five_table's recipe drawn on the device (columns are device tensors; same tables,
+    sizes, key distributions, predicates and edges; another random stream)."""
+    import torch
+    rng = np.random.default_rng(data_seed)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(data_seed)
+    n_f1, n_f2, n_d1, n_d2, n_d3 = (max(int(round(x * scale)), 16)
+                                    for x in (36_000_000, 4_500_000, 2_500_000, 134_000, 4_000_000))
+    movie_dom, kw_dom, person_dom = n_d1, n_d2, n_d3
+    i32 = torch.int32
+
+    def pk(n):
+        return torch.randperm(n, generator=gen, device=device, dtype=torch.int64).to(i32)
+
+    f1 = Table("F1", [zipf_keys_device(gen, n_f1, movie_dom, s, i32), zipf_keys_device(gen, n_f1, person_dom, s, i32)],
+               [], [0, 0, 1], [2, 3, 4], [("domain", 0, movie_dom), ("domain", 0, person_dom)])
+    f2 = Table("F2", [zipf_keys_device(gen, n_f2, kw_dom, s, i32), zipf_keys_device(gen, n_f2, movie_dom, s, i32)],
+               [], [0, 1, 1], [0, 1, 3], [("domain", 0, kw_dom), ("domain", 0, movie_dom)])
+    d1 = Table("D1", [pk(n_d1), torch.randint(0, 1000, (n_d1,), generator=gen, device=device, dtype=i32)],
+               [Pred(1, RANGE, 0, 10 * d1_sel_pct)], [0, 0], [1, 2], [("unique", 0, n_d1), None])
+    codes2 = zipf_keys_device(gen, n_d2, 10_000, 1.0, i32)
+    point = int(codes2[int(rng.integers(0, n_d2))].item())
+    d2 = Table("D2", [pk(n_d2), codes2], [Pred(1, EQ, point, 0)], [0], [0], [("unique", 0, n_d2), None])
+    code_dom = 100_000
+    codes3 = zipf_keys_device(gen, n_d3, code_dom, 0.8, i32)
+    subset = rng.choice(code_dom, size=code_dom // 100, replace=False)
+    d3 = Table("D3", [pk(n_d3), codes3], [Pred(1, IN, 0, 0, bitmap_of(subset, code_dom), code_dom)],
+               [0], [4], [("unique", 0, n_d3), None])
+    return Workload(f"five_table scale={scale} d{d} w{w} D1sel={d1_sel_pct}%", [f1, f2, d1, d2, d3],
+                    [3, 2, 2, 0, 4], [1, 1, 0, 1, 0], d, w, hash_seed, data_seed)
+
+
 def random_graph_workload(rng: np.random.Generator, n_tables: int, extra_edges: int, rows_lo: int, rows_hi: int,
                           domain: int, d: int, w: int, s_range=(0.5, 1.5), int64_keys: bool = False,
                           pred_prob: float = 0.5, hash_seed: int = 1) -> Workload:

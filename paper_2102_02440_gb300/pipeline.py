@@ -480,8 +480,35 @@ class PairBatch:
         return self.feat
 
 
+def build_plan_info(dw) -> dict:
+    """Totals of cmp_build_plan_stats over a DeviceWorkload's encoded batched-build plans."""
+    out = {"launches": 0, "n_agg": 0, "n_unique_slabs": 0}
+    for host, _dev, _wb in (dw._plans or []):
+        info = K.cmp_build_plan_stats(host.ctypes.data)
+        out["launches"] += int(info.launches)
+        out["n_agg"] += int(info.n_agg)
+        out["n_unique_slabs"] += int(info.n_unique_slabs)
+    return out
+
+
+CHECKPOINT_DIR = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.abspath(__file__)),
+                                            "checkpoints")
+
+
 class Combiner:
     """The learned combiner's parameters and Adam state on the device."""
+
+    @classmethod
+    def for_sketches(cls, d: int, w: int, device="cuda"):
+        """The trained combiner for d-row sketches (checkpoints/combiner_d{d}.bin, written
+        by Combiner.save after training on the GPU), else an untrained one with seed-0
+        weights.  Returns (combiner, description)."""
+        import os
+        path = os.path.join(CHECKPOINT_DIR, f"combiner_d{d}.bin")
+        if os.path.exists(path):
+            c, hdr = cls.load(path, device=device)
+            return c, {"weights": f"checkpoints/combiner_d{d}.bin", **hdr}
+        return cls(d + 2, 64, seed=0, device=device, skip=d // 2), {"weights": "untrained (seed 0)"}
 
     def __init__(self, nin: int, nh: int = 64, seed: int = 0, device="cuda", skip: int = -1, init_scale: float = 1.0):
         self.nin, self.nh, self.skip = nin, nh, skip
@@ -497,6 +524,41 @@ class Combiner:
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
         self.grad = torch.zeros_like(self.params)
         self._ws = None
+
+    _MAGIC = b"CMPMLP1\0"
+
+    def save(self, path: str, meta: dict | None = None, seed: int = 0):
+        """Checkpoint: magic, int32 nin, nh, skip, step, int64 seed, parameter count, uint32
+        length of a JSON description, the JSON, then fp32 parameters, Adam m and Adam v."""
+        import json
+        import struct
+        js = json.dumps(meta or {}, sort_keys=True).encode()
+        p, m, v = (t.detach().cpu().numpy().astype(np.float32) for t in (self.params, self.m, self.v))
+        with open(path, "wb") as f:
+            f.write(self._MAGIC)
+            f.write(struct.pack("<iiiiqqI", self.nin, self.nh, self.skip, self.step, seed, p.size, len(js)))
+            f.write(js)
+            for a in (p, m, v):
+                f.write(a.tobytes())
+
+    @classmethod
+    def load(cls, path: str, device="cuda"):
+        import json
+        import struct
+        with open(path, "rb") as f:
+            if f.read(8) != cls._MAGIC:
+                raise ValueError(f"{path}: not a combiner checkpoint")
+            nin, nh, skip, step, seed, n, jl = struct.unpack("<iiiiqqI", f.read(36))
+            meta = json.loads(f.read(jl).decode())
+            arrs = [np.frombuffer(f.read(4 * n), np.float32).copy() for _ in range(3)]
+        if n != K.cmp_mlp_param_count(nin, nh):
+            raise ValueError(f"{path}: {n} parameters for a {nin}->{nh}->1 network")
+        c = cls(nin, nh, seed=seed, device=device, skip=skip)
+        c.params.copy_(torch.from_numpy(arrs[0]))
+        c.m.copy_(torch.from_numpy(arrs[1]))
+        c.v.copy_(torch.from_numpy(arrs[2]))
+        c.step = step
+        return c, {"nin": nin, "nh": nh, "skip": skip, "step": step, **meta}
 
     def train_step(self, x: torch.Tensor, t: torch.Tensor, lr: float, huber_delta: float = 0.0, stream=None):
         n = x.shape[0]
@@ -537,7 +599,8 @@ class GraphBatch:
             self.table_off.append(toff)
             self.edge_off.append(eoff)
             for t in g.tables:
-                tables.append(G.Table(t.name, t.cols, t.preds, t.key_col, [e + eoff for e in t.edge_id]))
+                tables.append(G.Table(t.name, t.cols, t.preds, t.key_col, [e + eoff for e in t.edge_id],
+                                      list(getattr(t, "col_meta", None) or [])))
             eu += [u + toff for u in g.edge_u]
             ev += [v + toff for v in g.edge_v]
         self.wl = G.Workload("graph batch", tables, eu, ev, self.d, self.w, hash_seed, 0)

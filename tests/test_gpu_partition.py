@@ -294,3 +294,31 @@ def test_five_table_chain_full_width_sampled_row(orc, part):
         assert int(pj.survivors[i].item()) == n
     rows, oor = part.contract_seq([0, 1], [1, 2], widths, pj.axes, [x for x, _ in ref], 1)
     assert not oor[0] and pj.row_values()[5] == rows[0]
+
+
+def test_bulk_wait_that_runs_out_reports_timeout(part):
+    """The bounded mbarrier wait of the bulk-streamed contraction, given a budget of 0 polls:
+    every warp's first wait gives up, the launch writes CMP_ETIMEOUT to the status word and
+    returns (each warp first drains its copies in flight); the context stays usable and the
+    same join estimated next with the default bound gives the oracle's rows."""
+    rng = np.random.default_rng(77)
+    rows, w, d = 2500, 1024, 1   # int32 rows of >= 1024 entries, >= 16 per SM: the bulk path
+    eu, ev, widths, axes = [0, 1], [1, 2], [rows, w], [[0], [0, 1], [1]]
+    tensors = [rng.integers(-2 ** 20, 2 ** 20, size=(d, rows)), rng.integers(-2 ** 20, 2 ** 20, size=(d, rows * w)),
+               rng.integers(-2 ** 20, 2 ** 20, size=(d, w))]
+    dev = [torch.from_numpy(np.ascontiguousarray(x, np.int32)).cuda() for x in tensors]
+    j, keep = K.part_join(eu, ev, widths, axes, [x.data_ptr() for x in dev])
+    nb = K.cmp_part_estimate_ws_bytes(j, d)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    est = torch.empty(1, dtype=torch.float64, device="cuda")
+    row = torch.empty((d, 2), dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    K.cmp_part_estimate_ex(j, d, ws.data_ptr(), nb, est.data_ptr(), row.data_ptr(), st.data_ptr(), 0,
+                           K.stream_handle())
+    torch.cuda.synchronize()
+    assert int(st.item()) == K.CMP_ETIMEOUT
+    assert not any(_check(part, eu, ev, widths, axes, tensors, d))   # a fresh, default-bound run
+    with pytest.raises(K.CompassError) as ei:                      # a budget below -1 is refused
+        K.cmp_part_estimate_ex(j, d, ws.data_ptr(), nb, est.data_ptr(), row.data_ptr(), st.data_ptr(), -2,
+                               K.stream_handle())
+    assert ei.value.status == K.CMP_EINVAL

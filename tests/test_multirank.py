@@ -25,8 +25,10 @@ def _rank_main(rank, world, port, out):
                       LOCAL_RANK=str(rank))
     import torch.distributed as dist
     dist.init_process_group("gloo", rank=rank, world_size=world)
+    import argparse
+
     import bench
-    wl = bench.workload(0.0005, 256, rank)
+    wl = bench.workload(argparse.Namespace(workload="scale", scale=2e-6, w=65536), rank, device="cpu")
     ms_local = 10.0 + 5.0 * rank                       # rank 1 is the slow one
     rate, ms_max = bench.whole_job_rate(wl.total_rows, ms_local, world)
     first_keys = wl.tables[0].cols[0][:16].tolist()
