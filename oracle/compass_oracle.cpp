@@ -633,7 +633,8 @@ int orc_build(int64_t n_rows, int n_cols, const void* const* cols, const int32_t
  * count (push-down gives exact selectivities).  |S| >= 2: per sketch row, the full
  * contraction of the merged tensors over the induced edges (method 0: spanning-tree
  * message passing with cycle conditioning; method 1: brute-force enumeration), then the
- * median over rows.  row_dec: d * 192 chars of decimal row estimates; row_dbl: [d].
+ * median over rows.  row_dec: d * 2048 chars of decimal row estimates (each NUL-terminated;
+ * a row that needs more digits makes the call fail with -3); row_dbl: [d].
  * Returns 0, -1 invalid / not connected, -2 too large for method 1. */
 int orc_estimate(int n_tables, int n_edges, const int32_t* edge_u, const int32_t* edge_v,
                  const int32_t* const* sketches, const int64_t* survivors, int d, int w, uint64_t mask, int method,
@@ -656,8 +657,9 @@ int orc_estimate(int n_tables, int n_edges, const int32_t* edge_u, const int32_t
     if (row_dbl) row_dbl[i] = num_to_double(rows[i]);
     if (row_dec) {
       std::string s = big_to_dec(num_big(rows[i]));
-      std::strncpy(row_dec + (size_t)i * 192, s.c_str(), 191);
-      row_dec[(size_t)i * 192 + 191] = 0;
+      if (s.size() > 2047) return -3;
+      std::strncpy(row_dec + (size_t)i * 2048, s.c_str(), 2047);
+      row_dec[(size_t)i * 2048 + 2047] = 0;
     }
   }
   *est = median_of(rows);

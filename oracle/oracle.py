@@ -171,7 +171,7 @@ def estimate(edge_u, edge_v, sketches, survivors, d: int, w: int, mask: int, bru
             sk.append(a)
     skp = (C.c_void_p * max(2 * ne, 1))(*[_p(a) for a in sk])
     sv = np.ascontiguousarray(survivors, np.int64)
-    dec = C.create_string_buffer(d * 192)
+    dec = C.create_string_buffer(d * 2048)
     dbl = np.zeros(d, np.float64)
     est = np.zeros(1, np.float64)
     rc = lib().orc_estimate(nt, ne, _p(eu) if ne else None, _p(ev) if ne else None, C.cast(skp, C.c_void_p),
@@ -181,7 +181,7 @@ def estimate(edge_u, edge_v, sketches, survivors, d: int, w: int, mask: int, bru
     if rc != 0:
         raise ValueError(f"orc_estimate rejected the sub-plan (rc={rc})")
     raw = dec.raw
-    rows = [int(raw[i * 192:(i + 1) * 192].split(b"\0", 1)[0].decode()) for i in range(d)]
+    rows = [int(raw[i * 2048:(i + 1) * 2048].split(b"\0", 1)[0].decode()) for i in range(d)]
     return Estimate(float(est[0]), rows, dbl)
 
 

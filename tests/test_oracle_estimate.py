@@ -323,3 +323,28 @@ def test_subtree_message_is_shared_by_the_sub_plans_containing_it(orc):
     m1 = _merge2(sk[1][0], sk[1][1])
     got = sum(int(sk[0][0][i]) * int(sum(m1[i] * m234)) for i in range(w))
     assert got == orc.estimate(eu, ev, sketches, surv, 1, w, 0b11111).rows[0]
+
+
+@pytest.mark.parametrize("n,c,w", [(3, 2 ** 31 - 1, 2), (20, 2 ** 31 - 1, 2), (34, 2 ** 31 - 1, 2), (40, -(2 ** 31), 3),
+                                   (12, 7, 5)])
+def test_constant_chains_have_their_closed_form(orc, n, c, w):
+    """A chain of n tables whose every counter is c: every merged value is c (ties keep it),
+    so each of the w^(n-1) bucket assignments contributes c^n and E = c^n w^(n-1) exactly;
+    the values reach 2^1300, far beyond int128 (and beyond a double), and the median of equal
+    rows is that value rounded once."""
+    eu, ev = list(range(n - 1)), list(range(1, n))
+    sk = [tuple(np.full((2, w), c, np.int32) for _ in range(2)) for _ in range(n - 1)]
+    r = orc.estimate(eu, ev, sk, np.ones(n, np.int64), 2, w, (1 << n) - 1)
+    want = c ** n * w ** (n - 1)
+    assert r.rows == [want, want]
+    # one rounding to double; beyond the largest finite double that is an infinity
+    assert r.est == (float(want) if abs(want) < 2 ** 1024 - 2 ** 970 else float("inf") * (1 if want > 0 else -1))
+
+
+def test_constant_star_has_its_closed_form(orc):
+    """A root with 12 leaves, every counter -(2^31 - 1): E = c^13 w^12."""
+    k, c, w = 12, -(2 ** 31 - 1), 3
+    eu, ev = [0] * k, list(range(1, k + 1))
+    sk = [tuple(np.full((1, w), c, np.int32) for _ in range(2)) for _ in range(k)]
+    r = orc.estimate(eu, ev, sk, np.ones(k + 1, np.int64), 1, w, (1 << (k + 1)) - 1)
+    assert r.rows == [c ** (k + 1) * w ** k]
