@@ -592,6 +592,12 @@ def measure(a, wl, dev, world: int, rank: int, headline: bool):
     # features pick each sub-plan's two sketches by index
     n_sub = len(masks)
     comb, comb_src = P.Combiner.for_sketches(wl.d, wl.w, device=dev)
+    # the network serves two-table sub-plans (its training domain) with its stored rule; the
+    # others keep the median, and so does every sub-plan when no trained weights exist for d
+    # (the untrained network still runs, its output unused)
+    use_median_at = float(comb_src.get("use_median_at", 1.0))
+    trained = not str(comb_src.get("weights", "")).startswith("untrained")
+    eligible = torch.from_numpy(np.array([trained and bin(int(m)).count("1") == 2 for m in masks], np.uint8)).to(dev)
     n_sk = dw.counters_all.shape[0]
     f2_all = torch.zeros(n_sk, dtype=torch.float64, device=dev)
     feat = torch.empty((n_sub, wl.d + 2), dtype=torch.float32, device=dev)
@@ -614,7 +620,8 @@ def measure(a, wl, dev, world: int, rank: int, headline: bool):
                                    feat.data_ptr(), s)
         K.cmp_mlp_infer(comb.params.data_ptr(), wl.d + 2, comb.nh, comb.skip, feat.data_ptr(), n_sub,
                         y_mlp.data_ptr(), s)
-        K.cmp_mlp_combine(est.est.data_ptr(), y_mlp.data_ptr(), n_sub, est_comb.data_ptr(), s)
+        K.cmp_mlp_combine_ex(est.est.data_ptr(), y_mlp.data_ptr(), eligible.data_ptr(), n_sub, use_median_at,
+                             est_comb.data_ptr(), s)
 
     # join-order enumeration (Algorithm 1, max_plans = 10) over the combined estimates
     enum = P.Enumerator(est.graphs, np.zeros(n_sub, np.int32), masks, device=dev)

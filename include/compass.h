@@ -299,10 +299,19 @@ typedef struct {
  * Host steps: cmp_estimate_plan_bytes sizes the plan and the device workspace, and
  * cmp_estimate_plan_encode writes the plan; the caller copies it to the device.  Then
  * cmp_estimate enqueues the launches.
- *   est_dev      [n_sub] double; NaN where a row left the int128 range (and status
- *                gets CMP_EOVERFLOW)
+ *   est_dev      [n_sub] double
  *   row_est_dev  NULL or [n_sub][d][2] int64: each exact row estimate as a little-endian
- *                two's-complement int128 (low word first) */
+ *                two's-complement int128 (low word first); unspecified for the rows of a
+ *                sub-plan that has a row beyond int128 (see below)
+ * Exact range.  Rows are evaluated in int128 (int64 storage where it suffices).  When a
+ * row, or an intermediate value of its evaluation, leaves int128, every row of that
+ * sub-plan is evaluated again, exactly, by a second tier: on the generic path, modulo 16
+ * primes p_j = 2^62 - c_j, and in double on magnitudes rounded upwards (a bound B on |E|);
+ * when B < 2^990 (below half the primes' product) the row is the unique integer with those
+ * residues (Garner's algorithm), and est is its exact median rounded once.  est is NaN and
+ * the status gets CMP_EOVERFLOW only when B >= 2^990, or when more than min(n_sub d, 2^19)
+ * rows of one call need the tier.  Flag CMP_EST_NO_WIDE turns the tier off (rows beyond
+ * int128 are then NaN with CMP_EOVERFLOW). */
 /* Estimate launch shape; zero fields choose automatically.
  * Sub-plans whose only cycle is a triangle, with every other table a leaf of one of its
  * three tables, are evaluated by the triangle path: the conditioned sum regrouped as
@@ -331,15 +340,16 @@ typedef struct {
  * each, in the workspace), then each star gathers |S| entries.  A family is planned this way
  * when K 2^(K-1) <= 2 sum_S |S|^2 over its requested stars (it is dense enough); other
  * sub-plans are planned as without the flag.  Rows that stay in int128 are the same exact
- * integers; a row where an intermediate value left int128 is flagged (CMP_EOVERFLOW, NaN)
- * on either evaluation, which may differ between the two only on such rows. */
+ * integers; a row where an intermediate value left int128 is passed to the exact tier
+ * (cmp_estimate, "Exact range"), which evaluates it on the generic path. */
 #define CMP_EST_STAR_LATTICE 4
+#define CMP_EST_NO_WIDE 8
 typedef struct {
   int32_t threads;     /* threads per CTA (multiple of 32, <= 1024)                */
   int32_t ctas_per_sm; /* resident CTAs per SM the persistent grid is sized for    */
   int32_t cond_chunk;  /* conditioning values per work item of a cyclic sub-plan   */
-  int32_t flags;       /* CMP_EST_GENERIC_ONLY | CMP_EST_CACHE_MESSAGES | CMP_EST_STAR_LATTICE;
-                          other bits: CMP_EINVAL */
+  int32_t flags;       /* CMP_EST_GENERIC_ONLY | CMP_EST_CACHE_MESSAGES | CMP_EST_STAR_LATTICE |
+                          CMP_EST_NO_WIDE; other bits: CMP_EINVAL */
 } cmp_estimate_cfg;
 
 cmp_status cmp_estimate_plan_bytes(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
@@ -350,6 +360,12 @@ cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, i
                                     void* plan_host, size_t plan_bytes);
 cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_dev, size_t ws_bytes, double* est_dev,
                         int64_t* row_est_dev, int32_t* status_dev, void* stream);
+/* cmp_estimate with every exact row as a wide integer: wide_rows_dev NULL or
+ * [n_sub][d][16] int64, each row a little-endian two's-complement 1024-bit integer (16
+ * limbs), including the rows the exact tier computed (unspecified for a sub-plan whose
+ * estimate is NaN). */
+cmp_status cmp_estimate_ex(const void* plan_host, const void* plan_dev, void* ws_dev, size_t ws_bytes, double* est_dev,
+                           int64_t* row_est_dev, int64_t* wide_rows_dev, int32_t* status_dev, void* stream);
 
 /* Counts of an encoded estimate plan (host only, no GPU): sub-plans, work items (one per
  * sketch row and conditioning chunk), table operations over all sub-plans and cached
@@ -532,6 +548,16 @@ cmp_status cmp_mlp_infer(const float* params_dev, int32_t nin, int32_t nh, int32
  * network's prediction).  The median stays the estimate wherever it gives a usable join
  * size; the network replaces it where the median row estimate is zero or negative. */
 cmp_status cmp_mlp_combine(const double* median_dev, const float* y_dev, int64_t n, double* est_dev, void* stream);
+
+/* The combination with its rule spelled out: est_dev[q] = the network's prediction
+ * max(exp(32 y_dev[q]) - 1, 0) where sub-plan q is eligible (eligible_dev NULL: all, else
+ * [n] uint8, nonzero = eligible) and its median is below use_median_at, else median_dev[q].
+ * use_median_at = 1 is cmp_mlp_combine; +infinity lets the network replace the median on
+ * every eligible sub-plan (a NaN median then gives the network's value too); NaN: CMP_EINVAL.
+ * Sub-plans the network was not trained on (e.g. of three or more tables) stay on the
+ * median by leaving them ineligible. */
+cmp_status cmp_mlp_combine_ex(const double* median_dev, const float* y_dev, const uint8_t* eligible_dev, int64_t n,
+                              double use_median_at, double* est_dev, void* stream);
 
 /* One full-batch training step on n samples: loss = (1/n) sum (y - t)^2 when
  * huber_delta == 0, else the mean Huber loss (0.5 e^2 for |e| <= delta, delta (|e| -

@@ -708,6 +708,28 @@ int orc_join2(int64_t na, const int64_t* a, int64_t nb, const int64_t* b, char* 
   return 0;
 }
 
+/* Exact two-way join size of two key multisets with every key in [0, domain): the dot
+ * product of the two key histograms, O(na + nb + domain).  Returns -1 for a key outside the
+ * domain.  *out = the size (below 2^128 for any na, nb < 2^63). */
+int orc_join2_dense(int64_t na, const int32_t* a, int64_t nb, const int32_t* b, int64_t domain, uint64_t* out_lo,
+                    uint64_t* out_hi) {
+  if (domain < 1) return -1;
+  std::vector<uint64_t> ha((size_t)domain, 0), hb((size_t)domain, 0);
+  for (int64_t i = 0; i < na; i++) {
+    if (a[i] < 0 || a[i] >= domain) return -1;
+    ha[(size_t)a[i]]++;
+  }
+  for (int64_t i = 0; i < nb; i++) {
+    if (b[i] < 0 || b[i] >= domain) return -1;
+    hb[(size_t)b[i]]++;
+  }
+  u128 total = 0;
+  for (int64_t k = 0; k < domain; k++) total += (u128)ha[(size_t)k] * hb[(size_t)k];
+  *out_lo = (uint64_t)total;
+  *out_hi = (uint64_t)(total >> 64);
+  return 0;
+}
+
 /* Exact multi-way join size by nested loops (tiny tables only).  Table t has n_rows[t]
  * tuples; keys[2*e + end] is the join-key column of endpoint `end` of edge e, aligned
  * with that table's tuples.  A tuple combination counts iff every edge's two keys match. */

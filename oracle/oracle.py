@@ -200,6 +200,21 @@ def join2(a, b) -> int:
     return int(buf.value.decode())
 
 
+def join2_dense(a, b, domain: int) -> int:
+    """Exact two-way join size of int32 key arrays with every key in [0, domain): the dot
+    product of the key histograms (O(n + domain)).  The C call releases the interpreter
+    lock, so threads can label many joins at once."""
+    a = np.ascontiguousarray(a, np.int32)
+    b = np.ascontiguousarray(b, np.int32)
+    lo = np.zeros(1, np.uint64)
+    hi = np.zeros(1, np.uint64)
+    rc = lib().orc_join2_dense(C.c_int64(a.size), C.c_void_p(_p(a)), C.c_int64(b.size), C.c_void_p(_p(b)),
+                               C.c_int64(domain), C.c_void_p(_p(lo)), C.c_void_p(_p(hi)))
+    if rc != 0:
+        raise ValueError("a key lies outside [0, domain)")
+    return (int(hi[0]) << 64) | int(lo[0])
+
+
 def join_brute(edge_u, edge_v, n_rows, keys, mask: int) -> int:
     """keys[e] = (key column of endpoint u, key column of endpoint v), aligned with that table's tuples."""
     eu = np.ascontiguousarray(edge_u, np.int32)

@@ -18,6 +18,7 @@ CMP_RANGE, CMP_EQ, CMP_IN_BITMAP = 0, 1, 2
 CMP_EST_GENERIC_ONLY = 1
 CMP_EST_CACHE_MESSAGES = 2
 CMP_EST_STAR_LATTICE = 4
+CMP_EST_NO_WIDE = 8
 CMP_ABI_VERSION = 6
 CMP_PART_MAX_AXES = 4
 CMP_MAX_COLS, CMP_MAX_PREDS, CMP_MAX_SKETCHES, CMP_MAX_D = 32, 8, 16, 64
@@ -163,6 +164,10 @@ _SIGS = {
     "cmp_build_plan_stats": (C.c_int32, [C.c_void_p, C.POINTER(cmp_build_plan_info)]),
     "cmp_part_estimate_ex": (C.c_int32, [C.POINTER(cmp_part_join), C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.POINTER(cmp_part_estimate_cfg), C.c_void_p]),
+    "cmp_estimate_ex": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cmp_mlp_combine_ex": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
+                                       C.c_void_p]),
     "cmp_microbench_cw": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "cmp_part_build": (C.c_int32, [C.POINTER(cmp_table), C.c_int32, C.POINTER(C.c_int32), C.c_void_p, C.c_int32,
                                    C.c_void_p, C.c_void_p, C.POINTER(cmp_part_build_cfg), C.c_void_p]),
@@ -350,6 +355,18 @@ def cmp_build_plan_stats(plan_host: int) -> cmp_build_plan_info:
     info = cmp_build_plan_info()
     _check("cmp_build_plan_stats", lib().cmp_build_plan_stats(plan_host, C.byref(info)))
     return info
+
+
+def cmp_estimate_ex(plan_host: int, plan_dev: int, ws_dev: int, ws_bytes: int, est_dev: int, row_est_dev: int,
+                    wide_rows_dev: int, status_dev: int, stream: int):
+    _check("cmp_estimate_ex", lib().cmp_estimate_ex(plan_host, plan_dev, ws_dev, ws_bytes, est_dev, row_est_dev,
+                                                    wide_rows_dev, status_dev, stream))
+
+
+def cmp_mlp_combine_ex(median_dev: int, y_dev: int, eligible_dev: int, n: int, use_median_at: float, est_dev: int,
+                       stream: int):
+    _check("cmp_mlp_combine_ex", lib().cmp_mlp_combine_ex(median_dev, y_dev, eligible_dev, n, use_median_at, est_dev,
+                                                          stream))
 
 
 def cmp_microbench_cw(hash_dev: int, n_pairs: int, n_keys: int, w: int, form: int, out_dev: int, stream: int):

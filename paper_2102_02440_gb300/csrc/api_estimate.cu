@@ -22,7 +22,8 @@ cmp_status est_shape(const cmp_estimate_cfg* cfg, EstShape* s) {
   s->ctas_per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : 1;
   s->cond_chunk = (cfg && cfg->cond_chunk > 0) ? cfg->cond_chunk : 64;
   s->flags = cfg ? cfg->flags : 0;
-  if (s->flags & ~int32_t(CMP_EST_GENERIC_ONLY | CMP_EST_CACHE_MESSAGES | CMP_EST_STAR_LATTICE)) return CMP_EINVAL;
+  if (s->flags & ~int32_t(CMP_EST_GENERIC_ONLY | CMP_EST_CACHE_MESSAGES | CMP_EST_STAR_LATTICE | CMP_EST_NO_WIDE))
+    return CMP_EINVAL;
   if (s->threads < 32 || s->threads > 1024 || s->threads % 32 || s->ctas_per_sm > 32) return CMP_EINVAL;
   return CMP_OK;
 }
@@ -632,7 +633,7 @@ void plan_stars(const cmp_graph* graphs, int32_t n_sub, const int32_t* sub_graph
 
 cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_t w, int32_t n_sub,
                     const int32_t* sub_graph, const uint64_t* sub_mask, const cmp_estimate_cfg* cfg, PlanOut* P,
-                    EstPlanHdr* H) {
+                    EstPlanHdr* H, PlanOut* F) {
   if (!graphs || n_graphs < 1 || d < 1 || d > CMP_MAX_D || w < 1 || w > CMP_MAX_W || n_sub < 0) return CMP_EINVAL;
   EstShape shape;
   if (est_shape(cfg, &shape) != CMP_OK) return CMP_EINVAL;
@@ -706,6 +707,44 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
   off += align16(sizeof(StarUnit) * size_t(H->n_star_units));
   H->star_suf_words = P->star_suf_words;
   H->star_t_entries = P->star_t_entries;
+  // exact tier beyond int128: the sub-plans on the generic path alone (the main arrays when
+  // they already are), evaluated again modulo the primes for the rows found out of range
+  H->wide = (shape.flags & CMP_EST_NO_WIDE) ? 0 : 1;
+  F->subs.clear();
+  if (H->wide) {
+    const bool own = !P->stars.empty() || !P->tris.empty() || n_job > 0;
+    if (own) {
+      for (int32_t q = 0; q < n_sub; q++) {
+        const cmp_status st = plan_sub(graphs[sub_graph[q]], sub_graph[q], sub_mask[q], d, w, q, shape.cond_chunk,
+                                       CMP_EST_GENERIC_ONLY, nullptr, -1, 0, F);
+        if (st != CMP_OK) return st;
+      }
+      H->wide_off_subs = int64_t(off);
+      off += align16(sizeof(EstSub) * F->subs.size());
+      H->wide_off_ops = int64_t(off);
+      off += align16(sizeof(EstOp) * F->ops.size());
+      H->wide_off_in = int64_t(off);
+      off += align16(sizeof(EstIn) * F->ins.size());
+      H->wide_off_items = int64_t(off);
+      off += align16(sizeof(EstItem) * F->items.size());
+      H->wide_n_items = int64_t(F->items.size());
+    } else {
+      H->wide_off_subs = H->off_subs;
+      H->wide_off_ops = H->off_ops;
+      H->wide_off_in = H->off_in;
+      H->wide_off_items = H->off_items;
+      H->wide_n_items = n_gen;
+    }
+    const PlanOut& G = own ? *F : *P;
+    H->wide_max_slots = G.max_slots;
+    H->wide_max_in = G.max_in;
+    H->wide_max_suf = G.max_suf;
+    H->wide_grid = int32_t(sm_count()) * 4;
+    H->wide_qcap = int32_t(std::min<int64_t>(int64_t(n_sub) * d, kWideQueueMax));
+    H->wide_scratch_per_cta = int64_t(align16(
+        sizeof(uint64_t) * size_t(int64_t(G.max_slots) * w + int64_t(G.max_suf) * (int64_t(w) + 1) +
+                                  int64_t(std::max(G.max_in, 1)) * (int64_t(w) + 1))));
+  }
   H->total_bytes = int64_t(off);
   H->max_suf = P->max_suf;
   H->max_rank = P->max_rank;
@@ -779,9 +818,9 @@ cmp_status cmp_estimate_plan_bytes(const cmp_graph* graphs, int32_t n_graphs, in
                                    const int32_t* sub_graph, const uint64_t* sub_mask, const cmp_estimate_cfg* cfg,
                                    size_t* plan_bytes, size_t* ws_bytes) {
   if (!plan_bytes || !ws_bytes) return CMP_EINVAL;
-  PlanOut P;
+  PlanOut P, F;
   EstPlanHdr H;
-  const cmp_status st = plan_all(graphs, n_graphs, d, w, n_sub, sub_graph, sub_mask, cfg, &P, &H);
+  const cmp_status st = plan_all(graphs, n_graphs, d, w, n_sub, sub_graph, sub_mask, cfg, &P, &H, &F);
   if (st != CMP_OK) return st;
   *plan_bytes = size_t(H.total_bytes);
   *ws_bytes = size_t(H.ws_bytes);
@@ -792,9 +831,9 @@ cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, i
                                     const int32_t* sub_graph, const uint64_t* sub_mask, const cmp_estimate_cfg* cfg,
                                     void* plan_host, size_t plan_bytes) {
   if (!plan_host) return CMP_EINVAL;
-  PlanOut P;
+  PlanOut P, F;
   EstPlanHdr H;
-  const cmp_status st = plan_all(graphs, n_graphs, d, w, n_sub, sub_graph, sub_mask, cfg, &P, &H);
+  const cmp_status st = plan_all(graphs, n_graphs, d, w, n_sub, sub_graph, sub_mask, cfg, &P, &H, &F);
   if (st != CMP_OK) return st;
   if (plan_bytes < size_t(H.total_bytes)) return CMP_EWORKSPACE;
   unsigned char* b = static_cast<unsigned char*>(plan_host);
@@ -811,6 +850,12 @@ cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, i
   if (!P.star_lat_units.empty())
     std::memcpy(b + H.off_star_units + sizeof(StarUnit) * P.star_suf_units.size(), P.star_lat_units.data(),
                 sizeof(StarUnit) * P.star_lat_units.size());
+  if (!F.subs.empty()) {  // the exact tier's own generic plan
+    std::memcpy(b + H.wide_off_subs, F.subs.data(), sizeof(EstSub) * F.subs.size());
+    if (!F.ops.empty()) std::memcpy(b + H.wide_off_ops, F.ops.data(), sizeof(EstOp) * F.ops.size());
+    if (!F.ins.empty()) std::memcpy(b + H.wide_off_in, F.ins.data(), sizeof(EstIn) * F.ins.size());
+    if (!F.items.empty()) std::memcpy(b + H.wide_off_items, F.items.data(), sizeof(EstItem) * F.items.size());
+  }
   return CMP_OK;
 }
 
@@ -837,6 +882,11 @@ cmp_status cmp_estimate_plan_stats(const void* plan_host, cmp_estimate_plan_info
 
 cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_dev, size_t ws_bytes, double* est_dev,
                         int64_t* row_est_dev, int32_t* status_dev, void* stream) {
+  return cmp_estimate_ex(plan_host, plan_dev, ws_dev, ws_bytes, est_dev, row_est_dev, nullptr, status_dev, stream);
+}
+
+cmp_status cmp_estimate_ex(const void* plan_host, const void* plan_dev, void* ws_dev, size_t ws_bytes, double* est_dev,
+                           int64_t* row_est_dev, int64_t* wide_rows_dev, int32_t* status_dev, void* stream) {
   if (!plan_host || !plan_dev) return CMP_EINVAL;
   EstPlanHdr H;
   std::memcpy(&H, plan_host, sizeof(H));
@@ -845,8 +895,10 @@ cmp_status cmp_estimate(const void* plan_host, const void* plan_dev, void* ws_de
   if (ws_bytes < size_t(H.ws_bytes) || (H.ws_bytes > 0 && !ws_dev)) return CMP_EWORKSPACE;
   const EstArgs a = est_args(H, static_cast<const unsigned char*>(plan_dev), static_cast<unsigned char*>(ws_dev),
                              H.grid, H.n_tri * H.d, status_dev);
-  return launch_estimate(a, H, est_dev, row_est_dev, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? CMP_OK
-                                                                                                          : CMP_ECUDA;
+  return launch_estimate(a, H, est_dev, row_est_dev, reinterpret_cast<cudaStream_t>(stream), wide_rows_dev) ==
+                 cudaSuccess
+             ? CMP_OK
+             : CMP_ECUDA;
 }
 
 }  // extern "C"

@@ -748,17 +748,18 @@ constexpr int kFinalizeThreads = 64;  // >= CMP_MAX_D
 
 __global__ void __launch_bounds__(kFinalizeThreads) k_estimate_finalize(const __grid_constant__ EstArgs A,
                                                                         double* __restrict__ est,
-                                                                        int64_t* __restrict__ row_est) {
+                                                                        int64_t* __restrict__ row_est,
+                                                                        int64_t* __restrict__ wide_rows) {
   __shared__ i128 rows[CMP_MAX_D];
-  __shared__ int32_t any_ovf;
+  __shared__ int32_t any_ovf, lost;
   const int64_t q = blockIdx.x;
   const EstSub sb = A.subs[q];
   const int d = A.d, i = threadIdx.x;
-  if (i == 0) any_ovf = 0;
+  if (i == 0) any_ovf = lost = 0;
   __syncthreads();
+  bool ovf = false;
   if (i < d) {
     i128 s = 0;
-    bool ovf = false;
     if (sb.single) {
       s = i128(*sb.sv);
     } else if (sb.star >= 0) {  // a star: gather T_a(S \ {a}) over its leaf edges a
@@ -783,11 +784,37 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_estimate_finalize(const __
       row_est[(q * d + i) * 2] = int64_t(uint64_t(u128(s)));
       row_est[(q * d + i) * 2 + 1] = int64_t(uint64_t(u128(s) >> 64));
     }
+    if (wide_rows)  // sign-extended; rows beyond int128 are overwritten by the exact tier
+      for (int l = 0; l < kWideLimbs; l++)
+        wide_rows[(q * d + i) * kWideLimbs + l] = l == 0 ? int64_t(uint64_t(u128(s)))
+                                                  : l == 1 ? int64_t(uint64_t(u128(s) >> 64)) : (s < 0 ? -1 : 0);
     if (ovf) atomicOr(&any_ovf, 1);
+  }
+  __syncthreads();
+  // Exact tier: the rows beyond int128 of a sub-plan are queued and evaluated again modulo
+  // the primes; its other rows are kept as they are for the median.
+  if (A.wide && i < d && any_ovf) {
+    int32_t slot = -1;
+    if (ovf) {
+      const uint32_t k = atomicAdd(A.wide_queue, 1u);
+      if (k < uint32_t(A.wide_qcap)) {
+        A.wide_queue[4 + k] = uint32_t(q * d + i);
+        slot = int32_t(k);
+      } else {
+        atomicOr(&lost, 1);
+      }
+    }
+    A.wide_slot[q * d + i] = slot;
+    A.wide_in[q * d + i] = rows[i];
   }
   __syncthreads();
   if (i != 0) return;
   if (any_ovf) {
+    if (A.wide && !lost) {  // the exact tier writes est[q]
+      const uint32_t k = atomicAdd(A.wide_queue + 1, 1u);
+      A.wide_queue[4 + A.wide_qcap + k] = uint32_t(q);
+      return;
+    }
     est[q] = __longlong_as_double(0x7ff8000000000000ll);
     set_status(A.status, CMP_EOVERFLOW);
     return;
@@ -805,7 +832,8 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_estimate_finalize(const __
   est[q] = __dmul_rn(med, sb.scale);  // sampled tables: one rounded product (scale 1 is exact)
 }
 
-cudaError_t launch_estimate(const EstArgs& a, const EstPlanHdr& H, double* est, int64_t* row_est, cudaStream_t st) {
+cudaError_t launch_estimate(const EstArgs& a, const EstPlanHdr& H, double* est, int64_t* row_est, cudaStream_t st,
+                            int64_t* wide_rows) {
   // cached subtree messages, one launch per level, in int128 storage
   // three register budgets: 1024 threads (one CTA per SM), 512 (wider ILP), 256 (four CTAs
   // per SM: more items in flight when each is bound by its barriers, e.g. conditioned cycles)
@@ -844,8 +872,11 @@ cudaError_t launch_estimate(const EstArgs& a, const EstPlanHdr& H, double* est, 
     if (e != cudaSuccess) return e;
   }
   if (a.n_sub > 0) {
-    k_estimate_finalize<<<unsigned(a.n_sub), kFinalizeThreads, 0, st>>>(a, est, row_est);
-    return cudaGetLastError();
+    if (a.wide && cudaMemsetAsync(a.wide_queue, 0, 4 * sizeof(uint32_t), st) != cudaSuccess) return cudaGetLastError();
+    k_estimate_finalize<<<unsigned(a.n_sub), kFinalizeThreads, 0, st>>>(a, est, row_est, wide_rows);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_estimate_wide(a, est, wide_rows, st);
   }
   return cudaSuccess;
 }

@@ -144,9 +144,34 @@ struct EstPlanHdr {
   // star families (CMP_EST_STAR_LATTICE): families, units (suffix units first)
   int64_t n_star, off_star, n_star_units, n_star_suf_units, off_star_units;
   int64_t star_suf_words, star_t_entries;  // workspace: int64 suffix sums, lattice entries
+  // exact tier beyond int128 (wide = 1): every sub-plan planned on the generic path alone
+  // (its own arrays when the main plan uses other paths, else the main plan's), evaluated
+  // modulo kWideMods primes for the rows found beyond int128, with a magnitude bound
+  int32_t wide, wide_qcap;  // wide_qcap: rows the tier can take per call (more stay out of range)
+  int64_t wide_off_subs, wide_off_ops, wide_off_in, wide_off_items, wide_n_items;
+  int32_t wide_max_slots, wide_max_in, wide_max_suf, wide_grid;
+  int64_t wide_scratch_per_cta;
 };
+constexpr int32_t kWideQueueMax = 1 << 19;
 constexpr uint64_t kEstPlanMagic = 0x434d504553544d54ull;  // "CMPESTMT"
-constexpr int32_t kEstPlanVersion = 5;
+constexpr int32_t kEstPlanVersion = 6;
+
+// Exact tier beyond int128: a row is evaluated modulo kWideMods primes p_j = 2^62 - c_j
+// (exact ring arithmetic: the contraction is sums of products of the counters, and the
+// min-abs selections depend only on the presorted magnitudes), and once more in double
+// rounded upwards on absolute values, a bound on |E|.  When the bound is below 2^kWideBits
+// (< P/2, P the product of the primes), E is the unique integer of (-P/2, P/2) with those
+// residues (Garner's algorithm).  Rows are reported as kWideLimbs 64-bit two's-complement
+// limbs.
+constexpr int kWideMods = 16;
+constexpr int kWideLimbs = 16;
+constexpr int kWideBits = 990;
+__host__ __device__ constexpr uint64_t wide_c(int j) {
+  return j == 0 ? 57 : j == 1 ? 87 : j == 2 ? 117 : j == 3 ? 143 : j == 4 ? 153 : j == 5 ? 167 : j == 6 ? 171
+       : j == 7 ? 195 : j == 8 ? 203 : j == 9 ? 273 : j == 10 ? 287 : j == 11 ? 317 : j == 12 ? 443
+       : j == 13 ? 483 : j == 14 ? 495 : 575;
+}
+__host__ __device__ constexpr uint64_t wide_p(int j) { return (uint64_t(1) << 62) - wide_c(j); }
 
 struct EstArgs {
   const EstSub* subs;
@@ -175,6 +200,20 @@ struct EstArgs {
   int64_t* star_suf;
   i128* star_t;
   uint8_t* star_tf;     // 1: the lattice entry left int128
+  // exact tier beyond int128
+  int32_t wide;
+  const EstSub* wsubs;
+  const EstOp* wops;
+  const EstIn* winputs;
+  const EstItem* witems;
+  int64_t wide_n_items;
+  int32_t wide_max_slots, wide_max_in, wide_max_suf, wide_grid, wide_qcap;
+  int64_t wide_scratch_per_cta;
+  uint32_t* wide_queue;   // [0] rows queued, [1] sub-plans queued, [4..4+qcap) rows, then sub-plans
+  int32_t* wide_slot;     // [n_sub * d] queue slot of each row, -1 when it stays in int128
+  i128* wide_in;          // [n_sub * d] the int128 rows of sub-plans in the queue
+  uint64_t* wide_res;     // [qcap][kWideMods + 1]: the row's residues, then its bound (double bits)
+  void* wide_scratch;     // wide_grid areas of wide_scratch_per_cta bytes
 };
 
 // Round-to-nearest-even of (neg ? -1 : 1) * (top * 2^128 + mag) to binary64, from the
@@ -238,12 +277,29 @@ inline size_t est_star_bytes(const EstPlanHdr& H) {
   return align16(sizeof(i128) * size_t(H.star_t_entries)) + align16(size_t(H.star_t_entries)) +
          align16(sizeof(int64_t) * size_t(H.star_suf_words));
 }
+// exact tier: queue counters ([0] rows, [1] sub-plans), the queued rows (sub * d + row) and
+// sub-plans, each row's queue slot (-1: it stays in int128), the int128 rows of the queued
+// sub-plans, per queued row its residues and bound.  Its kernels run after the others and
+// reuse their per-CTA and triangle scratch.
+inline size_t est_wide_bytes(const EstPlanHdr& H) {
+  if (!H.wide) return 0;
+  const size_t rows = size_t(H.n_sub) * size_t(H.d);
+  return align16(sizeof(uint32_t) * (4 + size_t(H.wide_qcap) + size_t(H.n_sub))) + align16(sizeof(int32_t) * rows) +
+         align16(sizeof(i128) * rows) + align16(sizeof(uint64_t) * size_t(H.wide_qcap) * (kWideMods + 1));
+}
 inline size_t est_fixed_bytes(const EstPlanHdr& H) {
   return align16(sizeof(i128) * size_t(H.n_items)) + align16(sizeof(int32_t) * size_t(H.n_items)) +
-         est_cache_bytes(H) + align16(sizeof(int32_t) * size_t(H.n_jobs) * size_t(H.d)) + est_star_bytes(H);
+         est_cache_bytes(H) + align16(sizeof(int32_t) * size_t(H.n_jobs) * size_t(H.d)) + est_star_bytes(H) +
+         est_wide_bytes(H);
+}
+// The scratch region after the fixed part: `grid` per-CTA areas, then `tri_slots` triangle
+// rows; at least one CTA area of the exact tier's kernel.
+inline size_t est_scratch_bytes(const EstPlanHdr& H, int64_t grid, int64_t tri_slots) {
+  const size_t main = size_t(H.scratch_per_cta) * size_t(grid) + size_t(H.tri_row_bytes) * size_t(tri_slots);
+  return H.wide && main < size_t(H.wide_scratch_per_cta) ? size_t(H.wide_scratch_per_cta) : main;
 }
 inline size_t est_ws_bytes(const EstPlanHdr& H, int64_t grid, int64_t tri_slots) {
-  return est_fixed_bytes(H) + size_t(H.scratch_per_cta) * size_t(grid) + size_t(H.tri_row_bytes) * size_t(tri_slots);
+  return est_fixed_bytes(H) + est_scratch_bytes(H, grid, tri_slots);
 }
 inline EstArgs est_args(const EstPlanHdr& H, const unsigned char* pd, unsigned char* ws, int32_t grid,
                         int64_t tri_slots, int32_t* status) {
@@ -269,6 +325,35 @@ inline EstArgs est_args(const EstPlanHdr& H, const unsigned char* pd, unsigned c
   a.star_tf = ws + o_star + align16(sizeof(i128) * size_t(H.star_t_entries));
   a.star_suf = reinterpret_cast<int64_t*>(ws + o_star + align16(sizeof(i128) * size_t(H.star_t_entries)) +
                                           align16(size_t(H.star_t_entries)));
+  a.wide = H.wide;
+  a.wsubs = reinterpret_cast<const EstSub*>(pd + H.wide_off_subs);
+  a.wops = reinterpret_cast<const EstOp*>(pd + H.wide_off_ops);
+  a.winputs = reinterpret_cast<const EstIn*>(pd + H.wide_off_in);
+  a.witems = reinterpret_cast<const EstItem*>(pd + H.wide_off_items);
+  a.wide_n_items = H.wide_n_items;
+  a.wide_max_slots = H.wide_max_slots;
+  a.wide_max_in = H.wide_max_in;
+  a.wide_max_suf = H.wide_max_suf;
+  a.wide_grid = 0;  // set below from the scratch region it shares
+  a.wide_qcap = H.wide_qcap;
+  a.wide_scratch_per_cta = H.wide_scratch_per_cta;
+  {
+    const size_t o_wide = est_fixed_bytes(H) - est_wide_bytes(H);
+    const size_t rows = size_t(H.n_sub) * size_t(H.d);
+    const size_t o_slot = o_wide + align16(sizeof(uint32_t) * (4 + size_t(H.wide_qcap) + size_t(H.n_sub)));
+    const size_t o_in = o_slot + align16(sizeof(int32_t) * rows);
+    const size_t o_res = o_in + align16(sizeof(i128) * rows);
+    a.wide_queue = H.wide ? reinterpret_cast<uint32_t*>(ws + o_wide) : nullptr;
+    a.wide_slot = H.wide ? reinterpret_cast<int32_t*>(ws + o_slot) : nullptr;
+    a.wide_in = H.wide ? reinterpret_cast<i128*>(ws + o_in) : nullptr;
+    a.wide_res = H.wide ? reinterpret_cast<uint64_t*>(ws + o_res) : nullptr;
+    // the exact tier's kernel runs after every other one and reuses their scratch
+    a.wide_scratch = H.wide ? ws + est_fixed_bytes(H) : nullptr;
+    if (H.wide && H.wide_scratch_per_cta > 0) {
+      const int64_t fit = int64_t(est_scratch_bytes(H, grid, tri_slots) / size_t(H.wide_scratch_per_cta));
+      a.wide_grid = int32_t(fit < 1 ? 1 : (fit < H.wide_grid ? fit : H.wide_grid));
+    }
+  }
   a.scratch = ws + est_fixed_bytes(H);
   a.scratch_per_cta = H.scratch_per_cta;
   a.n_items = H.n_items;
@@ -293,7 +378,9 @@ inline EstArgs est_args(const EstPlanHdr& H, const unsigned char* pd, unsigned c
   return a;
 }
 
-cudaError_t launch_estimate(const EstArgs& a, const EstPlanHdr& H, double* est, int64_t* row_est, cudaStream_t st);
+cudaError_t launch_estimate(const EstArgs& a, const EstPlanHdr& H, double* est, int64_t* row_est, cudaStream_t st,
+                            int64_t* wide_rows = nullptr);
+cudaError_t launch_estimate_wide(const EstArgs& a, double* est, int64_t* wide_rows, cudaStream_t st);
 cudaError_t launch_estimate_tri(const EstArgs& a, cudaStream_t st);
 cudaError_t launch_estimate_star(const EstArgs& a, cudaStream_t st);
 cudaError_t launch_cross_ranks(const uint32_t* abs, const int32_t* perm, int32_t k, int32_t d, int32_t w,

@@ -58,6 +58,7 @@ extern "C" cmp_status cmp_estimate_noalloc(const void* plan_host, const void* pl
   int64_t slots = 0;
   if (per_tri) slots = std::min<int64_t>(H.n_tri * H.d, int64_t((cap - fixed - per_cta * size_t(grid)) / per_tri));
   if (est_ws_bytes(H, grid, slots) > cap || (per_tri && slots < 1)) return CMP_EWORKSPACE;
+  // (est_ws_bytes includes one CTA area of the exact tier's kernel, which shares the scratch)
   void* ws_v = nullptr;
   const cmp_status st = workspace_address(&ws_v);
   if (st != CMP_OK) return st;

@@ -1,0 +1,595 @@
+// Exact tier beyond int128 of the sketch-merging estimate (Sec. 4.2 merge equation, Sec. 3.2
+// median): rows whose value, or an intermediate of their evaluation, left int128 are
+// evaluated again on the generic path with modular arithmetic.
+//
+// The contraction of a row is a polynomial in the counters: sums of products, with the
+// min-abs selections of the merge decided by comparisons of presorted magnitudes only.  So
+// its value E is determined exactly by E mod p_j for primes p_j whose product P exceeds 2|E|,
+// and the same evaluation with absolute values in double, rounded upwards at every step, is
+// an upper bound on |E|.  A CTA evaluates one (queued row, modulus) unit over all of the row's
+// conditioning chunks; the finalize rebuilds E from its residues by Garner's algorithm when
+// the bound is below 2^kWideBits (< P / 2), takes the exact median over the d rows and rounds
+// it once to double.
+#include <cuda_runtime.h>
+
+#include "est_arith.cuh"
+
+namespace cmpk {
+
+namespace {
+
+// ---------------------------------------------------------------- arithmetic policies
+// Residues modulo p = 2^62 - c (c < 2^10): a b = H 2^62 + L = L + c H (mod p), twice, then
+// one conditional subtraction (the second sum is below 2^62 + 2^21 < 2p).
+struct ModArith {
+  uint64_t p, c;
+  using V = uint64_t;
+  __device__ __forceinline__ V zero() const { return 0; }
+  __device__ __forceinline__ V reduce63(uint64_t u) const {  // u < 2^63
+    uint64_t r = (u & ((1ull << 62) - 1)) + (u >> 62) * c;
+    return r >= p ? r - p : r;
+  }
+  __device__ __forceinline__ V from(int64_t v) const {
+    if (v >= 0) return reduce63(uint64_t(v));
+    const V m = reduce63(uint64_t(0) - uint64_t(v));  // |v| <= 2^63: below 2^63 + 1, reduce63 holds
+    return m ? p - m : 0;
+  }
+  __device__ __forceinline__ V add(V a, V b) const {
+    const uint64_t s = a + b;
+    return s >= p ? s - p : s;
+  }
+  __device__ __forceinline__ V mul(V a, V b) const {
+    const uint64_t lo = a * b, hi = __umul64hi(a, b);
+    const uint64_t L = lo & ((1ull << 62) - 1), H = (hi << 2) | (lo >> 62);  // < 2^62 each
+    const u128 y = u128(H) * c + L;                                          // < 2^72 + 2^62
+    const uint64_t z = (uint64_t(y) & ((1ull << 62) - 1)) + uint64_t(y >> 62) * c;
+    return z >= p ? z - p : z;
+  }
+};
+
+// Upper bounds of magnitudes: |sum| <= sum of |terms|, |product| = product of |factors|,
+// each rounded towards +infinity.
+struct BoundArith {
+  using V = double;
+  __device__ __forceinline__ V zero() const { return 0.0; }
+  __device__ __forceinline__ V from(int64_t v) const { return fabs(double(v)); }  // int32 counters: exact
+  __device__ __forceinline__ V add(V a, V b) const { return __dadd_ru(a, b); }
+  __device__ __forceinline__ V mul(V a, V b) const { return __dmul_ru(a, b); }
+};
+
+template <class M>
+__device__ __forceinline__ typename M::V shfl_up_v(typename M::V v, int off) {
+  return __shfl_up_sync(0xffffffffu, v, off);
+}
+
+// Block-wide sum (result broadcast) and in-place scans of V values.
+template <class M>
+__device__ typename M::V block_sum_v(const M& ar, typename M::V v, typename M::V* sh) {
+  using V = typename M::V;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const V o = __shfl_down_sync(0xffffffffu, v, off);
+    if (lane + off < 32) v = ar.add(v, o);
+  }
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    V t = ar.zero();
+    for (int i = 0; i < nw; i++) t = ar.add(t, sh[i]);
+    sh[32] = t;
+  }
+  __syncthreads();
+  const V r = sh[32];
+  __syncthreads();
+  return r;
+}
+
+template <class M>
+__device__ void block_scan_v(const M& ar, typename M::V* a, int n, bool reverse, typename M::V* sh) {
+  using V = typename M::V;
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int per = (n + T - 1) / T;
+  const int b = tid * per, e = min(n, b + per);
+  V s = ar.zero();
+  for (int q = b; q < e; q++) s = ar.add(s, a[reverse ? n - 1 - q : q]);
+  const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+  V incl = s;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const V o = shfl_up_v<M>(incl, off);
+    if (lane >= off) incl = ar.add(incl, o);
+  }
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  if (tid == 0) {
+    V t = ar.zero();
+    for (int i = 0; i < nw; i++) {
+      const V v = sh[i];
+      sh[i] = t;
+      t = ar.add(t, v);
+    }
+  }
+  __syncthreads();
+  // exclusive prefix of this thread: the warp's base plus the lanes before it
+  V run = sh[warp];
+  {
+    const V before = shfl_up_v<M>(incl, 1);
+    if (lane > 0) run = ar.add(run, before);
+  }
+  for (int q = b; q < e; q++) {
+    const int idx = reverse ? n - 1 - q : q;
+    run = ar.add(run, a[idx]);
+    a[idx] = run;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ const int32_t* wrank_row(const EstIn& x, const EstIn& y, int d, int row, int w) {
+  return x.rk + (int64_t(y.tslot) * d + row) * w;
+}
+
+constexpr int kWideThreads = 256;
+
+// One row of sub-plan sb (its items [it0, it0 + n_chunks)) in arithmetic ar.
+template <class M>
+__device__ typename M::V wide_row(const M& ar, const EstArgs& A, const EstSub& sb, int row, EstOp* sh_ops,
+                                  EstIn* sh_in, typename M::V* sh, typename M::V* sh_val, uint32_t* sh_ac,
+                                  unsigned char* cta) {
+  using V = typename M::V;
+  const int w = A.w, tid = threadIdx.x, T = blockDim.x;
+  const int64_t W1 = int64_t(w) + 1, ro = int64_t(row) * w;
+  V* slots = reinterpret_cast<V*>(cta);
+  V* suf = slots + int64_t(A.wide_max_slots) * w;
+  V* pre = suf + int64_t(A.wide_max_suf) * W1;
+  // leaf suffix sums (independent of the conditioning value)
+  for (int o = 0; o < sb.n_ops; o++) {
+    const EstOp op = sh_ops[o];
+    const EstIn* in = sh_in + op.in_begin;
+    const int p = op.p, m = op.k - (p >= 0 ? 1 : 0);
+    for (int a = 0; a < m; a++) {
+      const EstIn& x = in[a + (p >= 0 && a >= p ? 1 : 0)];
+      if (x.kind != kInLeaf) continue;
+      V* sl = suf + int64_t(x.suf) * W1;
+      const int32_t* perm = x.perm + ro;
+      for (int r = tid; r < w; r += T) sl[r] = ar.from(__ldg(x.msk + ro + __ldg(perm + r)));
+      if (tid == 0) sl[w] = ar.zero();
+      __syncthreads();
+      block_scan_v(ar, sl, w, /*reverse=*/true, sh);
+    }
+  }
+  // conditioned edge: at most one (sub-plans with one independent cycle)
+  const int32_t* cond_s[2] = {nullptr, nullptr};
+  int n_cond = 0;
+  {
+    const EstOp last = sh_ops[sb.n_ops - 1];
+    const int n_in = last.in_begin + last.k;
+    for (int q = 0; q < n_in && n_cond < 2; q++)
+      if (sh_in[q].kind == kInCond) cond_s[n_cond++] = sh_in[q].s + ro;
+  }
+  V total = ar.zero();
+  const int64_t it0 = sb.item_begin + int64_t(row) * sb.n_chunks;
+  for (int ch = 0; ch < sb.n_chunks; ch++) {
+    const EstItem item = A.witems[it0 + ch];
+    for (int c = item.c0; c < item.c1; c++) {
+      bool zero = false;
+      for (int q = 0; q < n_cond; q++) zero |= __ldg(cond_s[q] + c) == 0;
+      if (zero) continue;  // block-uniform: every merged entry through that table is 0
+      for (int o = 0; o < sb.n_ops; o++) {
+        const EstOp op = sh_ops[o];
+        const EstIn* in = sh_in + op.in_begin;
+        const int p = op.p, m = op.k - (p >= 0 ? 1 : 0);
+        // 1. suffix sums of messages from non-leaf children, in this table's sorted order
+        for (int a = 0; a < m; a++) {
+          const EstIn& x = in[a + (p >= 0 && a >= p ? 1 : 0)];
+          if (x.kind != kInSlot) continue;
+          V* sl = suf + int64_t(x.suf) * W1;
+          const V* msg = slots + int64_t(x.slot) * w;
+          const int32_t* perm = x.perm + ro;
+          for (int r = tid; r < w; r += T) sl[r] = msg[__ldg(perm + r)];
+          if (tid == 0) sl[w] = ar.zero();
+          __syncthreads();
+          block_scan_v(ar, sl, w, /*reverse=*/true, sh);
+        }
+        // 2a. the conditioned input: |s[c]| and its "attains the minimum" term
+        if (tid < m) {
+          const EstIn& x = in[tid + (p >= 0 && tid >= p ? 1 : 0)];
+          if (x.kind == kInCond) {
+            const int32_t v = __ldg(x.s + ro + c);
+            sh_ac[tid] = v < 0 ? uint32_t(-int64_t(v)) : uint32_t(v);
+          }
+        }
+        __syncthreads();
+        if (tid < m) {
+          const int la = tid + (p >= 0 && tid >= p ? 1 : 0);
+          const EstIn& x = in[la];
+          if (x.kind == kInCond) {
+            const int rpos = __ldg(wrank_row(x, x, A.d, row, w) + c);
+            const uint32_t tau = sh_ac[tid];
+            V v = ar.from(__ldg(x.s + ro + c));
+            for (int b = 0; b < m; b++) {
+              if (b == tid) continue;
+              const int lb = b + (p >= 0 && b >= p ? 1 : 0);
+              const EstIn& y = in[lb];
+              if (y.kind == kInCond) {
+                if (!(lb < la ? sh_ac[b] > tau : sh_ac[b] >= tau)) v = ar.zero();
+              } else {
+                const int q = __ldg(wrank_row(x, y, A.d, row, w) + rpos);
+                v = ar.mul(v, suf[int64_t(y.suf) * W1 + q]);
+              }
+            }
+            sh_val[tid] = v;
+          }
+        }
+        __syncthreads();
+        // 2b. the other inputs: s_l m_l prod_{l' != l, p} G_l'(|s_l|), in l's sorted order
+        V root_part = ar.zero();
+        for (int a = 0; a < m; a++) {
+          const int la = a + (p >= 0 && a >= p ? 1 : 0);
+          const EstIn& x = in[la];
+          if (x.kind == kInCond) {
+            if (p < 0 && tid == 0) root_part = ar.add(root_part, sh_val[a]);
+            continue;
+          }
+          const int32_t* perm = x.perm + ro;
+          const uint32_t* absa = x.abs + ro;
+          const V* msg = x.kind == kInSlot ? slots + int64_t(x.slot) * w : nullptr;
+          V* pl = pre + int64_t(a) * W1;
+          for (int r = tid; r < w; r += T) {
+            const int j = __ldg(perm + r);
+            V v = ar.mul(ar.from(__ldg(x.s + ro + j)), msg ? msg[j] : ar.from(__ldg(x.msk + ro + j)));
+            for (int b = 0; b < m; b++) {
+              if (b == a) continue;
+              const int lb = b + (p >= 0 && b >= p ? 1 : 0);
+              const EstIn& y = in[lb];
+              if (y.kind == kInCond) {
+                const uint32_t tau = __ldg(absa + r);
+                if (!(lb < la ? sh_ac[b] > tau : sh_ac[b] >= tau)) v = ar.zero();
+              } else {
+                v = ar.mul(v, suf[int64_t(y.suf) * W1 + __ldg(wrank_row(x, y, A.d, row, w) + r)]);
+              }
+            }
+            if (p < 0) root_part = ar.add(root_part, v);
+            else pl[r + 1] = v;
+          }
+          if (p >= 0) {
+            if (tid == 0) pl[0] = ar.zero();
+            __syncthreads();
+            block_scan_v(ar, pl + 1, w, /*reverse=*/false, sh);
+          }
+        }
+        if (p < 0) {
+          total = ar.add(total, block_sum_v(ar, root_part, sh));
+          continue;
+        }
+        // 3. the message to the parent, in the output sketch's sorted order
+        const EstIn& xp = in[p];
+        const int32_t* permp = xp.perm + ro;
+        const uint32_t* absp = xp.abs + ro;
+        V* out = slots + int64_t(op.out_slot) * w;
+        for (int r = tid; r < w; r += T) {
+          const int jp = __ldg(permp + r);
+          const uint32_t tau = __ldg(absp + r);
+          V t = ar.from(__ldg(xp.s + ro + jp)), add = ar.zero();
+          for (int a = 0; a < m; a++) {
+            const int la = a + (a >= p ? 1 : 0);
+            const EstIn& x = in[la];
+            if (x.kind == kInCond) {
+              if (!(la < p ? sh_ac[a] > tau : sh_ac[a] >= tau)) t = ar.zero();
+              if (la > p ? sh_ac[a] < tau : sh_ac[a] <= tau) add = ar.add(add, sh_val[a]);
+            } else {
+              const int q = __ldg(wrank_row(xp, x, A.d, row, w) + r);
+              t = ar.mul(t, suf[int64_t(x.suf) * W1 + q]);
+              add = ar.add(add, pre[int64_t(a) * W1 + q]);
+            }
+          }
+          out[jp] = ar.add(t, add);
+        }
+        __syncthreads();
+      }
+    }
+  }
+  return total;
+}
+
+// Moduli a row needs: the fewest k with B < 2^(62 k - 2) <= P_k / 2 (P_k, the product of the
+// first k primes, exceeds 2^(62 k - 1)); 0 when the bound reaches 2^kWideBits or is not finite.
+__device__ __forceinline__ int wide_mods_for(double B) {
+  if (!(B < ldexp(1.0, kWideBits))) return 0;
+  if (B < 1.0) return 1;
+  int e;
+  frexp(B, &e);  // B < 2^e
+  const int k = (e + 2 + 61) / 62;
+  return k < 1 ? 1 : (k > kWideMods ? 0 : k);
+}
+
+// Persistent over units of the queued rows: pass 0 computes every row's bound, pass 1 its
+// residues modulo the primes it needs (the others are skipped).
+__global__ void __launch_bounds__(kWideThreads) k_estimate_wide(const __grid_constant__ EstArgs A, int pass) {
+  __shared__ EstOp sh_ops[kEstMaxOps];
+  __shared__ EstIn sh_in[kEstMaxSubIn];
+  __shared__ uint64_t sh_u[33];
+  __shared__ double sh_d[33];
+  __shared__ uint64_t sh_valu[CMP_MAX_SKETCHES];
+  __shared__ double sh_vald[CMP_MAX_SKETCHES];
+  __shared__ uint32_t sh_ac[CMP_MAX_SKETCHES];
+  const uint32_t n_rows = min(A.wide_queue[0], uint32_t(A.wide_qcap));
+  const int per_row = pass == 0 ? 1 : kWideMods;
+  const int64_t units = int64_t(n_rows) * per_row;
+  unsigned char* cta = static_cast<unsigned char*>(A.wide_scratch) + int64_t(blockIdx.x) * A.wide_scratch_per_cta;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t e = u / per_row;
+    const int j = pass == 0 ? kWideMods : int(u % per_row);
+    if (pass == 1 &&
+        j >= wide_mods_for(__longlong_as_double((long long)A.wide_res[e * (kWideMods + 1) + kWideMods])))
+      continue;  // block-uniform
+    const uint32_t qr = A.wide_queue[4 + e];
+    const int64_t q = qr / uint32_t(A.d);
+    const int row = int(qr % uint32_t(A.d));
+    const EstSub sb = A.wsubs[q];
+    uint64_t result = 0;
+    if (sb.single) {  // never queued (an exact count); kept for completeness
+      const int64_t n = *sb.sv;
+      result = j < kWideMods ? ModArith{wide_p(j), wide_c(j)}.from(n)
+                             : uint64_t(__double_as_longlong(fabs(double(n))));
+    } else if (sb.n_ops > 0) {
+      const int in0 = A.wops[sb.op_begin].in_begin;
+      const EstOp last = A.wops[sb.op_begin + sb.n_ops - 1];
+      const int n_in = last.in_begin + last.k - in0;
+      for (int o = threadIdx.x; o < sb.n_ops; o += blockDim.x) {
+        EstOp op = A.wops[sb.op_begin + o];
+        op.in_begin -= in0;
+        sh_ops[o] = op;
+      }
+      for (int k = threadIdx.x; k < n_in; k += blockDim.x) sh_in[k] = A.winputs[in0 + k];
+      __syncthreads();
+      if (j < kWideMods) {
+        const ModArith ar{wide_p(j), wide_c(j)};
+        result = wide_row(ar, A, sb, row, sh_ops, sh_in, sh_u, sh_valu, sh_ac, cta);
+      } else {
+        const BoundArith ar{};
+        result = uint64_t(__double_as_longlong(wide_row(ar, A, sb, row, sh_ops, sh_in, sh_d, sh_vald, sh_ac, cta)));
+      }
+    }
+    if (threadIdx.x == 0) A.wide_res[e * (kWideMods + 1) + j] = result;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- wide integers
+// Signed values as sign + kWideLimbs little-endian 64-bit limbs of the magnitude.
+struct Wide {
+  uint64_t m[kWideLimbs];
+  int neg;
+};
+
+__device__ __forceinline__ int wide_cmp_mag(const uint64_t* a, const uint64_t* b) {
+  for (int k = kWideLimbs - 1; k >= 0; k--)
+    if (a[k] != b[k]) return a[k] < b[k] ? -1 : 1;
+  return 0;
+}
+__device__ __forceinline__ bool wide_less(const Wide& a, const Wide& b) {
+  const bool az = wide_cmp_mag(a.m, b.m) == 0 && a.neg == b.neg;
+  if (az) return false;
+  if (a.neg != b.neg) return a.neg;  // a negative, b not (zero is never negative here)
+  const int c = wide_cmp_mag(a.m, b.m);
+  return a.neg ? c > 0 : c < 0;
+}
+
+// Round-to-nearest-even of (neg ? -1 : 1) * (top 2^(64 kWideLimbs) + mag) to double, from
+// the definition: the leading 53 bits, then the half-ulp and sticky bits.
+__device__ double wide_mag_to_double(bool neg, uint32_t top, const uint64_t* mag) {
+  int hi = kWideLimbs - 1;
+  while (hi >= 0 && mag[hi] == 0) hi--;
+  if (top == 0 && hi < 0) return 0.0;
+  // bit length of the value
+  const int nb = top ? 64 * kWideLimbs + 1 : 64 * hi + (64 - __clzll(mag[hi]));
+  auto bit = [&](int k) -> uint64_t {  // bit k of the value
+    if (k >= 64 * kWideLimbs) return top;
+    return (mag[k >> 6] >> (k & 63)) & 1ull;
+  };
+  double r;
+  if (nb <= 53) {
+    r = double(mag[0]);
+  } else {
+    const int sh = nb - 53;
+    uint64_t s = 0;
+    for (int k = nb - 1; k >= sh; k--) s = (s << 1) | bit(k);
+    const uint64_t half = bit(sh - 1);
+    bool sticky = false;
+    for (int k = 0; k < sh - 1 && !sticky; k++) sticky = bit(k) != 0;
+    if (half && (sticky || (s & 1))) s++;
+    int e = sh;
+    if (s == (1ull << 53)) {
+      s >>= 1;
+      e++;
+    }
+    r = ldexp(double(s), e);
+  }
+  return neg ? -r : r;
+}
+
+__device__ __forceinline__ uint64_t mulmod_p(uint64_t a, uint64_t b, int j) {
+  const ModArith ar{wide_p(j), wide_c(j)};
+  return ar.mul(a, b);
+}
+__device__ uint64_t powmod_p(uint64_t a, uint64_t e, int j) {
+  uint64_t r = 1, b = a;
+  while (e) {
+    if (e & 1) r = mulmod_p(r, b, j);
+    b = mulmod_p(b, b, j);
+    e >>= 1;
+  }
+  return r;
+}
+
+constexpr int kWideFinThreads = 128;
+
+}  // namespace
+
+// One CTA per queued sub-plan (persistent), thread i < d takes row i: its int128 value when
+// it stayed in range, else the integer rebuilt from its residues by Garner's algorithm;
+// thread 0 takes the exact median and rounds it once.
+__global__ void __launch_bounds__(kWideFinThreads) k_estimate_wide_finalize(const __grid_constant__ EstArgs A,
+                                                                             double* __restrict__ est,
+                                                                             int64_t* __restrict__ wide_rows) {
+  __shared__ uint64_t inv[kWideMods][kWideMods];          // inv[i][j] = p_i^-1 mod p_j, i < j
+  __shared__ uint64_t Pk[kWideMods + 1][kWideLimbs + 1];  // Pk[k] = p_0 ... p_{k-1}
+  __shared__ Wide rows[CMP_MAX_D];
+  __shared__ int32_t bad;
+  const uint32_t n_sub_q = A.wide_queue[1];
+  if (n_sub_q == 0 || blockIdx.x >= n_sub_q) return;
+  const int tid = threadIdx.x, d = A.d;
+  for (int t = tid; t < kWideMods * kWideMods; t += blockDim.x) {
+    const int i = t / kWideMods, j = t % kWideMods;
+    if (i < j) inv[i][j] = powmod_p(wide_p(i) % wide_p(j), wide_p(j) - 2, j);  // Fermat: p_j is prime
+  }
+  if (tid == 0) {
+    for (int l = 0; l <= kWideLimbs; l++) Pk[0][l] = l == 0 ? 1 : 0;
+    for (int k = 1; k <= kWideMods; k++) {  // Pk[k] = Pk[k-1] p_{k-1}
+      uint64_t carry = 0;
+      for (int l = 0; l <= kWideLimbs; l++) {
+        const u128 t = u128(Pk[k - 1][l]) * wide_p(k - 1) + carry;
+        Pk[k][l] = uint64_t(t);
+        carry = uint64_t(t >> 64);
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t k = blockIdx.x; k < n_sub_q; k += gridDim.x) {
+    const int64_t q = A.wide_queue[4 + A.wide_qcap + k];
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    if (tid < d) {
+      const int32_t slot = A.wide_slot[q * d + tid];
+      Wide wv;
+      if (slot < 0) {  // in range: the int128 row
+        const i128 v = A.wide_in[q * d + tid];
+        wv.neg = v < 0 ? 1 : 0;
+        const u128 m = v < 0 ? u128(0) - u128(v) : u128(v);
+        for (int l = 0; l < kWideLimbs; l++) wv.m[l] = l == 0 ? uint64_t(m) : (l == 1 ? uint64_t(m >> 64) : 0);
+      } else {
+        const uint64_t* r = A.wide_res + int64_t(slot) * (kWideMods + 1);
+        const int K = wide_mods_for(__longlong_as_double((long long)r[kWideMods]));
+        if (K == 0) atomicOr(&bad, 1);
+        // Garner: x = v_0 + v_1 p_0 + v_2 p_0 p_1 + ..., v_j from the residue mod p_j
+        uint64_t v[kWideMods];
+        for (int j = 0; j < K; j++) {
+          const uint64_t pj = wide_p(j);
+          uint64_t t = r[j];
+          for (int i = 0; i < j; i++) {
+            const uint64_t vi = v[i] >= pj ? v[i] - pj : v[i];
+            t = t >= vi ? t - vi : t + pj - vi;
+            t = mulmod_p(t, inv[i][j], j);
+          }
+          v[j] = t;
+        }
+        uint64_t x[kWideLimbs + 1];
+        for (int l = 0; l <= kWideLimbs; l++) x[l] = 0;
+        for (int j = K - 1; j >= 0; j--) {  // x = x p_j + v_j
+          uint64_t carry = v[j];
+          for (int l = 0; l <= kWideLimbs; l++) {
+            const u128 t = u128(x[l]) * wide_p(j) + carry;
+            x[l] = uint64_t(t);
+            carry = uint64_t(t >> 64);
+          }
+        }
+        // x in [0, P_K): E = x when x < P_K - x, else E = -(P_K - x)
+        uint64_t y[kWideLimbs + 1];
+        uint64_t borrow = 0;
+        for (int l = 0; l <= kWideLimbs; l++) {
+          const u128 t = u128(Pk[K][l]) - x[l] - borrow;
+          y[l] = uint64_t(t);
+          borrow = (t >> 64) ? 1 : 0;
+        }
+        bool x_small = true;
+        for (int l = kWideLimbs; l >= 0; l--)
+          if (x[l] != y[l]) {
+            x_small = x[l] < y[l];
+            break;
+          }
+        wv.neg = x_small ? 0 : 1;
+        for (int l = 0; l < kWideLimbs; l++) wv.m[l] = x_small ? x[l] : y[l];
+        bool zero = true;
+        for (int l = 0; l < kWideLimbs; l++) zero &= wv.m[l] == 0;
+        if (zero) wv.neg = 0;
+      }
+      rows[tid] = wv;
+      if (wide_rows) {  // two's complement limbs
+        int64_t* o = wide_rows + (q * d + tid) * kWideLimbs;
+        uint64_t c = 1;
+        for (int l = 0; l < kWideLimbs; l++) {
+          uint64_t limb = wv.m[l];
+          if (wv.neg) {
+            const u128 t = u128(~limb) + c;
+            limb = uint64_t(t);
+            c = uint64_t(t >> 64);
+          }
+          o[l] = int64_t(limb);
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const EstSub sb = A.subs[q];
+      if (bad) {
+        est[q] = __longlong_as_double(0x7ff8000000000000ll);
+        set_status(A.status, CMP_EOVERFLOW);
+      } else {
+        for (int a = 1; a < d; a++) {  // insertion sort of exact integers
+          const Wide v = rows[a];
+          int b = a - 1;
+          while (b >= 0 && wide_less(v, rows[b])) {
+            rows[b + 1] = rows[b];
+            b--;
+          }
+          rows[b + 1] = v;
+        }
+        double med;
+        if (d & 1) {
+          med = wide_mag_to_double(rows[d / 2].neg, 0, rows[d / 2].m);
+        } else {  // exact (a + b) / 2: signed sum, then one rounding
+          const Wide& a = rows[d / 2 - 1];
+          const Wide& b = rows[d / 2];
+          uint64_t s[kWideLimbs];
+          uint32_t top = 0;
+          bool neg;
+          if (a.neg == b.neg) {
+            uint64_t c = 0;
+            for (int l = 0; l < kWideLimbs; l++) {
+              const u128 t = u128(a.m[l]) + b.m[l] + c;
+              s[l] = uint64_t(t);
+              c = uint64_t(t >> 64);
+            }
+            top = uint32_t(c);
+            neg = a.neg;
+          } else {
+            const bool a_big = wide_cmp_mag(a.m, b.m) >= 0;
+            const uint64_t* big = a_big ? a.m : b.m;
+            const uint64_t* small = a_big ? b.m : a.m;
+            uint64_t br = 0;
+            for (int l = 0; l < kWideLimbs; l++) {
+              const u128 t = u128(big[l]) - small[l] - br;
+              s[l] = uint64_t(t);
+              br = (t >> 64) ? 1 : 0;
+            }
+            neg = a_big ? a.neg : b.neg;
+          }
+          med = wide_mag_to_double(neg, top, s) * 0.5;
+        }
+        est[q] = __dmul_rn(med, sb.scale);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_estimate_wide(const EstArgs& a, double* est, int64_t* wide_rows, cudaStream_t st) {
+  if (!a.wide) return cudaSuccess;
+  k_estimate_wide<<<unsigned(a.wide_grid), kWideThreads, 0, st>>>(a, 0);  // bounds
+  k_estimate_wide<<<unsigned(a.wide_grid), kWideThreads, 0, st>>>(a, 1);  // residues
+  k_estimate_wide_finalize<<<unsigned(sm_count()), kWideFinThreads, 0, st>>>(a, est, wide_rows);
+  return cudaGetLastError();
+}
+
+}  // namespace cmpk

@@ -265,12 +265,14 @@ __global__ void k_mlp_adam(float* __restrict__ P, float* __restrict__ m, float* 
 
 // Combined estimate: the plain median where it is a usable join size (>= 1 tuple), the
 // network's prediction exp(32 y) - 1 where the median is below one tuple.
-__global__ void k_mlp_combine(const double* __restrict__ median, const float* __restrict__ y, int64_t n,
+__global__ void k_mlp_combine(const double* __restrict__ median, const float* __restrict__ y,
+                              const uint8_t* __restrict__ eligible, int64_t n, double use_median_at,
                               double* __restrict__ out) {
   const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const double m = median[q];
-  out[q] = m >= 1.0 ? m : fmax(expm1(32.0 * double(y[q])), 0.0);
+  const bool net = (!eligible || eligible[q]) && !(m >= use_median_at);
+  out[q] = net ? fmax(expm1(32.0 * double(y[q])), 0.0) : m;
 }
 
 cudaError_t launch_sketch_f2(const int32_t* C, int64_t n_sketches, int32_t d, int32_t w, double* f2,
@@ -305,7 +307,7 @@ cudaError_t launch_mlp_infer(const float* P, int32_t nin, int32_t nh, int32_t sk
 
 cudaError_t launch_mlp_combine(const double* median, const float* y, int64_t n, double* out, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_mlp_combine<<<unsigned((n + 255) / 256), 256, 0, st>>>(median, y, n, out);
+  k_mlp_combine<<<unsigned((n + 255) / 256), 256, 0, st>>>(median, y, nullptr, n, 1.0, out);
   return cudaGetLastError();
 }
 
@@ -380,6 +382,15 @@ cmp_status cmp_mlp_infer(const float* params_dev, int32_t nin, int32_t nh, int32
                  cudaSuccess
              ? CMP_OK
              : CMP_ECUDA;
+}
+
+cmp_status cmp_mlp_combine_ex(const double* median_dev, const float* y_dev, const uint8_t* eligible_dev, int64_t n,
+                              double use_median_at, double* est_dev, void* stream) {
+  if (n < 0 || (n > 0 && (!median_dev || !y_dev || !est_dev)) || use_median_at != use_median_at) return CMP_EINVAL;
+  if (n == 0) return CMP_OK;
+  k_mlp_combine<<<unsigned((n + 255) / 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      median_dev, y_dev, eligible_dev, n, use_median_at, est_dev);
+  return cudaGetLastError() == cudaSuccess ? CMP_OK : CMP_ECUDA;
 }
 
 cmp_status cmp_mlp_combine(const double* median_dev, const float* y_dev, int64_t n, double* est_dev, void* stream) {

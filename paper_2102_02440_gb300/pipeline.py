@@ -292,6 +292,30 @@ class DeviceEstimator:
         hi = r[..., 1].astype(object)
         return (hi * (1 << 64) + lo).tolist()
 
+    def estimate_wide(self, stream=None):
+        """cmp_estimate_ex: the estimate with every row also as a 1024-bit integer (the rows
+        of sub-plans beyond int128 from the exact tier)."""
+        if getattr(self, "wide_rows", None) is None:
+            self.wide_rows = torch.empty((self.masks.size, self.d, 16), dtype=torch.int64, device=self.device)
+        status = self.dws[0].status
+        K.cmp_estimate_ex(self.plan_host.ctypes.data, self.plan_dev.data_ptr(), self.ws.data_ptr(), self.ws.numel(),
+                          self.est.data_ptr(), self.row_est.data_ptr(), self.wide_rows.data_ptr(), status.data_ptr(),
+                          K.stream_handle(stream))
+
+    def wide_values(self):
+        """The rows of the last estimate_wide as Python ints, [n_sub][d]."""
+        r = self.wide_rows.cpu().numpy().astype(np.uint64)
+        out = []
+        for q in range(r.shape[0]):
+            rows = []
+            for i in range(r.shape[1]):
+                v = 0
+                for l in range(15, -1, -1):
+                    v = (v << 64) | int(r[q, i, l])
+                rows.append(v - (1 << 1024) if v >> 1023 else v)
+            out.append(rows)
+        return out
+
 
 class Enumerator:
     """Algorithm 1 (join-order enumeration) over an estimate plan's sub-plans, for every
@@ -461,8 +485,11 @@ class PairBatch:
 
     def estimate(self, stream=None):
         s = K.stream_handle(stream)
+        need = K.cmp_presort_ws_bytes(2 * self.n * self.d, self.w)   # rows longer than 16384: merged in memory
+        if need and (getattr(self, "presort_ws", None) is None or self.presort_ws.numel() < need):
+            self.presort_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
         K.cmp_presort(self.counters.data_ptr(), 2 * self.n * self.d, self.w, self.abs.data_ptr(), self.perm.data_ptr(),
-                      0, 0, s)
+                      self.presort_ws.data_ptr() if need else 0, need, s)
         # k = 1 per table: the cross ranks are the inverse permutations, one call for all tables
         K.cmp_cross_ranks(self.abs.data_ptr(), self.perm.data_ptr(), 1, 2 * self.n * self.d, self.w, [0],
                           self.ranks.data_ptr(), s)
@@ -501,13 +528,14 @@ class Combiner:
     @classmethod
     def for_sketches(cls, d: int, w: int, device="cuda"):
         """The trained combiner for d-row sketches (checkpoints/combiner_d{d}.bin, written
-        by Combiner.save after training on the GPU), else an untrained one with seed-0
-        weights.  Returns (combiner, description)."""
+        by Combiner.save after training on the GPU on w-bucket sketches), else an untrained
+        one with seed-0 weights.  Returns (combiner, description)."""
         import os
         path = os.path.join(CHECKPOINT_DIR, f"combiner_d{d}.bin")
         if os.path.exists(path):
             c, hdr = cls.load(path, device=device)
-            return c, {"weights": f"checkpoints/combiner_d{d}.bin", **hdr}
+            if int(hdr.get("w", w)) == w:
+                return c, {"weights": f"checkpoints/combiner_d{d}.bin", **hdr}
         return cls(d + 2, 64, seed=0, device=device, skip=d // 2), {"weights": "untrained (seed 0)"}
 
     def __init__(self, nin: int, nh: int = 64, seed: int = 0, device="cuda", skip: int = -1, init_scale: float = 1.0):

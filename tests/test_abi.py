@@ -224,7 +224,7 @@ def test_estimate_plan_triangle_path_host_logic(K):
     assert (K.cmp_estimate_plan_bytes([c4], 5, 64, [0], [0b1111])[1] ==
             K.cmp_estimate_plan_bytes([c4], 5, 64, [0], [0b1111], gen)[1])
     with pytest.raises(K.CompassError) as ei:
-        K.cmp_estimate_plan_bytes([g], 11, 64, [0], [0b111], K.cmp_estimate_cfg.make(flags=8))
+        K.cmp_estimate_plan_bytes([g], 11, 64, [0], [0b111], K.cmp_estimate_cfg.make(flags=16))
     assert ei.value.status == K.CMP_EINVAL
 
 

@@ -124,9 +124,9 @@ def test_five_table_workload_cached(orc):
 
 def test_rows_beyond_int128_are_flagged_through_the_cache():
     """A 16-table chain of one-row tables with counters at 2^31 - 1 in sketch row 0 and small
-    values in row 1: the long sub-plans leave int128 in row 0 (NaN with CMP_EOVERFLOW),
-    including those that read an overflowed cached message; both plans agree on every
-    estimate, and on every exact row of the sub-plans that stay in range."""
+    values in row 1, with the exact tier off: the long sub-plans leave int128 in row 0 (NaN
+    with CMP_EOVERFLOW), including those that read an overflowed cached message; both plans
+    agree on every estimate, and on every exact row of the sub-plans that stay in range."""
     n = 16
     eu, ev = list(range(n - 1)), list(range(1, n))
     rng = np.random.default_rng(3)
@@ -147,10 +147,11 @@ def test_rows_beyond_int128_are_flagged_through_the_cache():
         t.counters.copy_(torch.from_numpy(a))
     masks = G.connected_subplans(n, eu, ev)
     dw.status.zero_()
-    cached = _run(dw, masks, CACHE)
+    no_wide = K.CMP_EST_NO_WIDE      # the int128 path's own flagging (the exact tier: test_gpu_wide)
+    cached = _run(dw, masks, K.cmp_estimate_cfg.make(flags=K.CMP_EST_CACHE_MESSAGES | no_wide))
     st_c = int(dw.status.item())
     dw.status.zero_()
-    plain = _run(dw, masks, None)
+    plain = _run(dw, masks, K.cmp_estimate_cfg.make(flags=no_wide))
     st_p = int(dw.status.item())
     assert st_c == st_p == K.CMP_EOVERFLOW
     nan_c = torch.isnan(cached.est)

@@ -98,8 +98,9 @@ def test_star_lattice_in_a_mixed_plan_with_the_cache():
 
 def test_star_rows_beyond_int128():
     """One-row leaf tables of a 10-leaf star, counters at 2^31 - 1 in sketch row 0 (every
-    product is huge) and small elsewhere: the large subsets leave int128 in row 0 and are NaN
-    with CMP_EOVERFLOW on both evaluations; the others are identical."""
+    product is huge) and small elsewhere, with the exact tier off: the large subsets leave
+    int128 in row 0 and are NaN with CMP_EOVERFLOW on both evaluations; the others are
+    identical."""
     n = 10
     rng = np.random.default_rng(4)
     eu, ev = [0] * n, list(range(1, n + 1))
@@ -119,8 +120,9 @@ def test_star_rows_beyond_int128():
         a[:, 0, :] = 2 ** 31 - 1
         t.counters.copy_(torch.from_numpy(a))
     masks = G.connected_subplans(n + 1, eu, ev)
-    lat, st1 = _run(dw, masks, STAR)
-    gen, st2 = _run(dw, masks, None)
+    no_wide = K.CMP_EST_NO_WIDE      # the int128 path's own flagging (the exact tier: test_gpu_wide)
+    lat, st1 = _run(dw, masks, K.cmp_estimate_cfg.make(flags=K.CMP_EST_STAR_LATTICE | no_wide))
+    gen, st2 = _run(dw, masks, K.cmp_estimate_cfg.make(flags=no_wide))
     assert st1 == st2 == K.CMP_EOVERFLOW
     nan = torch.isnan(lat.est)
     assert torch.equal(nan, torch.isnan(gen.est)) and 0 < int(nan.sum()) < len(masks)

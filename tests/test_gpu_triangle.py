@@ -160,15 +160,16 @@ def test_triangle_wide_rows_match_generic(w):
 
 
 def test_triangle_int128_overflow_is_reported(orc):
-    """Counters at 2^31 - 1 on a triangle with three leaves: every row is beyond int128;
-    the estimate is NaN with CMP_EOVERFLOW, as on the generic path."""
+    """Counters at 2^31 - 1 on a triangle with three leaves, with the exact tier off: every
+    row is beyond int128; the estimate is NaN with CMP_EOVERFLOW, as on the generic path."""
     rng = np.random.default_rng(9)
     eu, ev = [0, 1, 0, 0, 1, 2], [1, 2, 2, 3, 4, 5]
     dw = _raw_workload(rng, eu, ev, 6, 3, 32)
     _fill(dw, rng, 2 ** 31 - 1, 2 ** 31 - 1, 0.0)
-    tri, st = _run(dw, [0b111111])
+    no_wide = K.CMP_EST_NO_WIDE      # the int128 path's own flagging (the exact tier: test_gpu_wide)
+    tri, st = _run(dw, [0b111111], K.cmp_estimate_cfg.make(flags=no_wide))
     assert st == K.CMP_EOVERFLOW and np.isnan(float(tri.est[0]))
-    gen, st2 = _run(dw, [0b111111], GENERIC)
+    gen, st2 = _run(dw, [0b111111], K.cmp_estimate_cfg.make(flags=K.CMP_EST_GENERIC_ONLY | no_wide))
     assert st2 == K.CMP_EOVERFLOW and np.isnan(float(gen.est[0]))
     ref = _oracle_rows(orc, dw, [0b111111])[0]
     assert all(abs(v) >= 2 ** 127 for v in ref.rows)

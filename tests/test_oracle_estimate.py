@@ -348,3 +348,27 @@ def test_constant_star_has_its_closed_form(orc):
     sk = [tuple(np.full((1, w), c, np.int32) for _ in range(2)) for _ in range(k)]
     r = orc.estimate(eu, ev, sk, np.ones(k + 1, np.int64), 1, w, (1 << (k + 1)) - 1)
     assert r.rows == [c ** (k + 1) * w ** k]
+
+
+def test_join2_dense_equals_the_sort_merge_join(orc):
+    """The histogram dot product over a known domain (the labeller of the learned
+    combiner's training joins) equals the sort-merge join size, and brute force on small
+    inputs: skewed keys, disjoint key sets, one shared key, empty sides, keys at both ends of
+    the domain; a key outside the domain is refused."""
+    rng = np.random.default_rng(12)
+    cases = []
+    for dom in (1, 7, 1000, 100_000):
+        a = G.zipf_keys(rng, int(rng.integers(1, 5000)), dom, 1.3)
+        b = G.zipf_keys(rng, int(rng.integers(1, 5000)), dom, 0.6)
+        cases.append((a, b, dom))
+    cases.append((np.arange(0, 100, 2, dtype=np.int32), np.arange(1, 100, 2, dtype=np.int32), 100))  # disjoint
+    cases.append((np.full(3000, 41, np.int32), np.full(2000, 41, np.int32), 42))                    # one key
+    cases.append((np.zeros(0, np.int32), np.arange(10, dtype=np.int32), 10))                        # empty
+    cases.append((np.array([0, 9, 9], np.int32), np.array([9, 0, 0, 5], np.int32), 10))              # the ends
+    for a, b, dom in cases:
+        want = orc.join2(a, b)
+        assert orc.join2_dense(a, b, dom) == want
+        if a.size * b.size <= 10_000_000:
+            assert want == int((a[:, None].astype(np.int64) == b[None, :]).sum())
+    with pytest.raises(ValueError):
+        orc.join2_dense(np.array([3, 10], np.int32), np.array([3], np.int32), 10)
