@@ -790,15 +790,20 @@ def measure(a, wl, dev, world: int, rank: int, headline: bool):
         out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(wl)
     # our kernel launches per step: build (zeroing; clearing + counting with aggregated key
     # columns; the unique-key kernel; the row kernel when it has items; hashing of the counted
-    # keys), presort (one launch for w <= 16384, else chunks + 3 merges + split per 64 rows)
-    # and cross ranks, estimate (int64 items + int128 recompute for tree sub-plans, 3 triangle
-    # launches, finalize), combiner (4), enumeration (1)
+    # keys; the presence-bitmap kernel), presort (one launch for w <= 16384, else chunks + 3
+    # merges + split per 64 rows) and cross ranks, estimate (int64 items + int128 recompute for
+    # tree sub-plans, 3 triangle launches, finalize, the exact tier), combiner (4), enumeration (1)
     h = dw._plan[0][0] if dw._plan else None
     info = P.build_plan_info(dw)
-    n_rows_sorted = sum(t.k for t in dw.tables) * wl.d
-    presort_l = 1 if wl.w <= 16384 else 5 * ((n_rows_sorted + 63) // 64)
-    est_l = (2 if n_gen_sub > sum(1 for m in masks if bin(m).count("1") == 1) else 0) + (3 if n_tri_sub else 0) + 1
-    out["gpu_launches_per_step"] = info["launches"] + presort_l + 1 + est_l + 4 + 1
+    # presort and cross ranks of the tables the plan reads sorted, per run of consecutive tables
+    presort_l = 0
+    for _lo, _rlo, run in P.presort_runs(dw, only=est.sorted_tables()):
+        n_rows_sorted = sum(dw.tables[i].k for i in run) * wl.d
+        if n_rows_sorted:
+            presort_l += (1 if wl.w <= 16384 else 5 * ((n_rows_sorted + 63) // 64)) + 1
+    # (the exact tier: two passes and its finalize, which return at once when no row is queued)
+    est_l = (2 if n_gen_sub > sum(1 for m in masks if bin(m).count("1") == 1) else 0) + (3 if n_tri_sub else 0) + 1 + 3
+    out["gpu_launches_per_step"] = info["launches"] + presort_l + est_l + 4 + 1
     return out
 
 
@@ -855,6 +860,14 @@ def measure_batched(a, dev):
         with torch.cuda.graph(g_est, stream=st):
             plan.run(stream=st)
         ms_est_b = timed(lambda: (g_est.replay(), st.synchronize()))
+    # the same plan without the exact tier beyond int128 (its sub-plans beyond int128 NaN)
+    plan_nw = gb.plan(sg, sm, K.cmp_estimate_cfg.make(threads=256, ctas_per_sm=4, cond_chunk=16,
+                                                      flags=K.CMP_EST_CACHE_MESSAGES | K.CMP_EST_STAR_LATTICE |
+                                                      K.CMP_EST_NO_WIDE))
+    ms_est_nw = timed(plan_nw.run, 1)
+    n_nan_nw = int(torch.isnan(plan_nw.est).sum().item())
+    del plan_nw
+    gb.dw.status.zero_()
     rng = np.random.default_rng(0)
     samp = rng.choice(sm.size, min(2000, sm.size), replace=False)
     plans = [gb.plan(sg[q:q + 1], sm[q:q + 1]) for q in samp]
@@ -870,7 +883,8 @@ def measure_batched(a, dev):
                          "per_subplan_launches_per_s": samp.size / (ms_est_1 / 1e3),
                          "speedup": (sm.size / (ms_est_b / 1e3)) / (samp.size / (ms_est_1 / 1e3)),
                          "flags": "CMP_EST_CACHE_MESSAGES | CMP_EST_STAR_LATTICE, 256 threads x 4 CTAs/SM, chunk 16",
-                         "subplans_beyond_int128": n_nan}}
+                         "subplans_nan": n_nan,
+                         "without_exact_tier": {"ms": ms_est_nw, "subplans_beyond_int128": n_nan_nw}}}
 
 
 def run_ours(a):

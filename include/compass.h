@@ -139,7 +139,7 @@ typedef struct {
 /* ---------------------------------------------------------------------- general */
 
 /* Version of this interface (CMP_ABI_VERSION); bindings refuse a library that differs. */
-#define CMP_ABI_VERSION 6
+#define CMP_ABI_VERSION 7
 int32_t cmp_abi_version(void);
 const char* cmp_status_str(cmp_status s);
 
@@ -192,8 +192,14 @@ cmp_status cmp_sketch_build(const cmp_table* table, int32_t d, int32_t w, const 
  * (CMP_COL_UNIQUE, cfg->unique) are hashed once per surviving row by a kernel that keeps
  * one or more (sketch, row) pairs' counters in shared memory: int32, or two 16-bit halves
  * per word with every carry and borrow added to the global counter, so the counters stay
- * exact.  Launches: zeroing, then (when present) clearing + counting, the unique-key
- * kernel, the row kernel and the hashing of the counted keys.
+ * exact.  A unique column with a declared domain of at most 2^32 keys, at most four
+ * times the table's rows, in a table without predicates or sample, is instead marked in a
+ * presence bitmap over its domain by the counting pass and hashed in key order: every
+ * (sketch, row) pair walks runs of consecutive keys, advancing h's and xi's residues by
+ * finite differences (additions mod p, the same integers as evaluating the polynomials);
+ * a key outside the domain, or one seen twice, sends the column to the per-row path.
+ * Launches: zeroing, then (when present) clearing + counting, the unique-key kernel, the
+ * row kernel, the hashing of the counted keys and the presence-bitmap kernel.
  * cmp_build_plan_encode returns CMP_EWORKSPACE if plan_bytes is too small;
  * cmp_sketch_build_batched returns CMP_EWORKSPACE if ws_bytes is. */
 cmp_status cmp_build_plan_bytes(const cmp_table* tables, int32_t n_tables, int32_t d, int32_t w,
@@ -205,13 +211,14 @@ cmp_status cmp_sketch_build_batched(const void* plan_host, const void* plan_dev,
                                     void* ws_dev, size_t ws_bytes, int32_t* status_dev, void* stream);
 
 /* Counts of an encoded batched-build plan (host only, no GPU): tables, aggregated key
- * columns, unique-key slabs and items and that kernel's grid, the row kernel's grid, the
- * workspace, and the number of kernels one cmp_sketch_build_batched call enqueues.
+ * columns (presence bitmaps included), unique-key slabs and items and that kernel's grid,
+ * the row kernel's grid, the workspace, the number of kernels one cmp_sketch_build_batched
+ * call enqueues, and the presence-bitmap columns among the aggregated ones.
  * CMP_EINVAL for a NULL argument or a blob that is not a build plan. */
 typedef struct {
   int32_t n_tables, n_agg, n_unique_slabs, unique_grid;
   int64_t n_unique_items, row_grid, ws_bytes;
-  int32_t launches, reserved;
+  int32_t launches, n_presence;
 } cmp_build_plan_info;
 cmp_status cmp_build_plan_stats(const void* plan_host, cmp_build_plan_info* info);
 

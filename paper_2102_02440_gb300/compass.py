@@ -19,7 +19,7 @@ CMP_EST_GENERIC_ONLY = 1
 CMP_EST_CACHE_MESSAGES = 2
 CMP_EST_STAR_LATTICE = 4
 CMP_EST_NO_WIDE = 8
-CMP_ABI_VERSION = 6
+CMP_ABI_VERSION = 7
 CMP_PART_MAX_AXES = 4
 CMP_MAX_COLS, CMP_MAX_PREDS, CMP_MAX_SKETCHES, CMP_MAX_D = 32, 8, 16, 64
 
@@ -69,7 +69,7 @@ class cmp_build_cfg(C.Structure):
 class cmp_build_plan_info(C.Structure):
     _fields_ = [("n_tables", C.c_int32), ("n_agg", C.c_int32), ("n_unique_slabs", C.c_int32),
                 ("unique_grid", C.c_int32), ("n_unique_items", C.c_int64), ("row_grid", C.c_int64),
-                ("ws_bytes", C.c_int64), ("launches", C.c_int32), ("reserved", C.c_int32)]
+                ("ws_bytes", C.c_int64), ("launches", C.c_int32), ("n_presence", C.c_int32)]
 
 
 class cmp_part_estimate_cfg(C.Structure):

@@ -256,12 +256,22 @@ constexpr size_t kUniqSmemBudget = size_t(128) << 10;
 constexpr int32_t kUniqTileRows = 4096;
 constexpr int32_t kUniqThreadsHost = 512;
 
+// Presence bitmaps (dense kernel): a unique column with a declared domain in a table
+// without predicates or sample, whose domain is at most kDenseMaxFill times its rows (the
+// kernel steps through every key of the domain) and at most kDenseMaxSpan keys.
+constexpr int64_t kDenseMaxFill = 4;
+constexpr int64_t kDenseMaxSpan = int64_t(1) << 32;
+
 struct BuildPlanParts {
   BuildShape shape;
   std::vector<UniqSlab> uslabs;
   std::vector<UniqItem> uitems;
   std::vector<int32_t> u_cta_item;  // [u_grid + 1]
   int32_t u_pack16 = 0, u_words = 0;
+  std::vector<UniqSlab> dslabs;     // dense kernel
+  std::vector<UniqItem> ditems;
+  std::vector<int32_t> d_cta_item;  // [d_grid + 1]
+  int32_t d_words = 0, n_presence = 0;
   std::vector<uint32_t> uniq_mask;  // [table]
   std::vector<int32_t> surv_by;     // [table]
   std::vector<BuildItem> items;
@@ -317,10 +327,27 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
     const cmp_table& tb = tables[t];
     const bool agg_on = tb.n_sketches > 0 && tb.n_rows > 0 && s.dedupe &&
                         (agg_mode == 1 || (agg_mode == -1 && tb.n_rows >= kAggMinRows));
+    const bool unfiltered = tb.n_preds == 0 && !(tb.sample_rate > 0.0 && tb.sample_rate < 1.0);
     for (int k = 0; k < tb.n_sketches; k++) {
       const int c = tb.key_col[k];
       const cmp_col& col = tb.cols[c];
       if (uniq_mode >= 0 && uniq_fits && (col.flags & CMP_COL_UNIQUE)) {
+        const uint64_t span = (col.flags & CMP_COL_DOMAIN) ? uint64_t(col.dom_hi) - uint64_t(col.dom_lo) : 0;
+        if (unfiltered && span > 0 && span <= uint64_t(kDenseMaxSpan) &&
+            span <= uint64_t(kDenseMaxFill) * uint64_t(tb.n_rows)) {
+          if (P->col_agg[t][c] >= 0) continue;
+          AggCol a;  // presence bitmap over the declared domain
+          std::memset(&a, 0, sizeof(a));
+          a.table = t;
+          a.col = c;
+          a.cap = int64_t(span);
+          a.base = col.dom_lo;
+          a.mask = ~0ull;
+          a.kind = kAggPresence;
+          P->col_agg[t][c] = int32_t(P->aggs.size());
+          P->aggs.push_back(a);
+          continue;
+        }
         P->uniq_mask[t] |= 1u << c;
         continue;
       }
@@ -349,7 +376,9 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
   if (P->aggs.size() > size_t(n_tables) * CMP_MAX_SKETCHES) return CMP_EINVAL;
   for (AggCol& a : P->aggs) {
     a.off = int64_t(ws);
-    ws += al256(16 * size_t((a.cap + 3) / 4));  // whole int4 words: the zeroing kernel writes them
+    // whole int4 words: the zeroing kernel writes them
+    ws += a.kind == kAggPresence ? al256(sizeof(uint32_t) * size_t(presence_words(a.cap)))
+                                 : al256(16 * size_t((a.cap + 3) / 4));
   }
   P->ws_bytes = P->aggs.empty() ? 0 : ws;
   // unique-key slabs and their items: each CTA gets about the same number of tiles; the
@@ -477,12 +506,83 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
   P->hash_max_pairs = 1;
   for (AggCol& ac : P->aggs) {
     ac.hash_chunk0 = P->hash_total_chunks;
+    if (ac.kind == kAggPresence) continue;  // hashed by the dense kernel
     P->hash_total_chunks += (ac.cap + kHashChunk - 1) / kHashChunk;
     int32_t np = 0;
     for (int32_t k = 0; k < tables[ac.table].n_sketches; k++) np += tables[ac.table].key_col[k] == ac.col ? d : 0;
     P->hash_max_pairs = std::max(P->hash_max_pairs, np);
   }
   P->hash_grid = int32_t(std::min<int64_t>(P->hash_total_chunks, int64_t(sm_count()) * 2));  // resident: 2 per SM
+  // dense kernel: slabs of each presence column's pairs (as for the unique-key kernel);
+  // each slab's domain split into items of whole runs, about equal work (keys x pairs) per
+  // CTA, one CTA per SM; consecutive items of a CTA share a slab where they can
+  P->dslabs.clear();
+  P->ditems.clear();
+  P->d_cta_item.assign(1, 0);
+  P->d_words = 0;
+  P->n_presence = 0;
+  {
+    double total = 0;
+    for (int32_t ai = 0; ai < int32_t(P->aggs.size()); ai++) {
+      const AggCol& ac = P->aggs[ai];
+      if (ac.kind != kAggPresence) continue;
+      P->n_presence++;
+      const cmp_table& tb = tables[ac.table];
+      std::vector<int32_t> pairs;
+      for (int k = 0; k < tb.n_sketches; k++)
+        if (tb.key_col[k] == ac.col)
+          for (int i = 0; i < d; i++) pairs.push_back(k * d + i);
+      const int max_pps = P->u_pack16 ? 1
+                                       : int(std::max<size_t>(1, std::min<size_t>(kUniqMaxPairs,
+                                                                                  kUniqSmemBudget / (size_t(w) * 4))));
+      const int n_sl = int((pairs.size() + max_pps - 1) / max_pps);
+      const int pps = int((pairs.size() + n_sl - 1) / n_sl);
+      for (size_t b = 0; b < pairs.size(); b += pps) {
+        UniqSlab sl;
+        std::memset(&sl, 0, sizeof(sl));
+        sl.table = ac.table;
+        sl.col = ac.col;
+        sl.pad = ai;
+        sl.n_pairs = int32_t(std::min(pairs.size() - b, size_t(pps)));
+        for (int q = 0; q < sl.n_pairs; q++) sl.pair[q] = pairs[b + q];
+        P->d_words = std::max<int32_t>(P->d_words, P->u_pack16 ? int32_t((w + 1) / 2) : sl.n_pairs * w);
+        total += double(ac.cap) * sl.n_pairs;
+        P->dslabs.push_back(sl);
+      }
+    }
+    if (!P->dslabs.empty()) {
+      const int32_t G = sm_count();
+      const double per_cta = total / G;
+      // items: each slab's runs cut wherever a CTA's share of the total work ends
+      double acc = 0;  // work before the current item
+      int32_t cta = 0;
+      for (int32_t si = 0; si < int32_t(P->dslabs.size()); si++) {
+        const UniqSlab& sl = P->dslabs[si];
+        const int64_t runs = (P->aggs[sl.pad].cap + kDenseRun - 1) / kDenseRun;
+        const double wpr = double(kDenseRun) * sl.n_pairs;  // work per run
+        int64_t r = 0;
+        while (r < runs) {
+          // runs left in CTA `cta`'s share
+          const double room = double(cta + 1) * per_cta - acc;
+          int64_t take = cta == G - 1 ? runs - r : std::max<int64_t>(1, int64_t(room / wpr + 0.5));
+          take = std::min(take, runs - r);
+          UniqItem it;
+          it.slab = si;
+          it.count_surv = 0;
+          it.row_begin = r * kDenseRun;
+          it.row_end = (r + take) * kDenseRun;
+          P->ditems.push_back(it);
+          acc += double(take) * wpr;
+          r += take;
+          if (cta < G - 1 && acc >= double(cta + 1) * per_cta - 0.5 * wpr) {
+            P->d_cta_item.push_back(int32_t(P->ditems.size()));
+            cta++;
+          }
+        }
+      }
+      if (P->d_cta_item.back() != int32_t(P->ditems.size())) P->d_cta_item.push_back(int32_t(P->ditems.size()));
+    }
+  }
   const double target = double(sm_count()) * ctas_per_sm * 4.0;
   P->items.clear();
   P->cta_item.clear();
@@ -499,8 +599,11 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
     for (int64_t c = 0; c < n; c++) P->cta_item.push_back(int32_t(P->items.size()));
     P->items.push_back(it);
   }
-  // counting pass: one item per table with aggregated columns, its rows as chunks of 4
-  // tiles; a persistent grid of about one resident wave takes the chunks in order
+  // counting pass: one item per table with aggregated columns, its rows as chunks of a
+  // multiple of 4 tiles: about 16 chunks per CTA of the resident wave for the largest
+  // tables (a CTA's chunk hand-over is a block barrier and an atomic, so chunks are kept
+  // long), at most 64 tiles; a persistent grid of about one resident wave takes the chunks
+  // in order
   P->cnt_items.clear();
   P->cnt_total_chunks = 0;
   for (int32_t t = 0; t < n_tables; t++) {
@@ -510,8 +613,11 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
     CountItem ci;
     ci.table = t;
     ci.pad = 0;
+    const int64_t unit = 4 * int64_t(R);
+    const int64_t want = tables[t].n_rows / (int64_t(sm_count()) * 2 * 16);
+    ci.chunk_rows = unit * std::max<int64_t>(1, std::min<int64_t>(16, want / unit));
     ci.chunk_begin = P->cnt_total_chunks;
-    ci.n_chunks = (tables[t].n_rows + 4 * int64_t(R) - 1) / (4 * int64_t(R));
+    ci.n_chunks = (tables[t].n_rows + ci.chunk_rows - 1) / ci.chunk_rows;
     P->cnt_total_chunks += ci.n_chunks;
     P->cnt_items.push_back(ci);
   }
@@ -522,7 +628,8 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
     int max_ac = 0;
     for (int32_t t = 0; t < n_tables; t++) {
       int n = 0;
-      for (int32_t c = 0; c < CMP_MAX_COLS; c++) n += P->col_agg[t][c] >= 0;
+      for (int32_t c = 0; c < CMP_MAX_COLS; c++)
+        n += P->col_agg[t][c] >= 0 && P->aggs[P->col_agg[t][c]].kind == kAggCount;
       max_ac = std::max(max_ac, n);
     }
     P->cache_cols = std::min(max_ac, 4);
@@ -546,6 +653,9 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
   off += align16(sizeof(UniqSlab) * P->uslabs.size());
   off += align16(sizeof(UniqItem) * P->uitems.size());
   off += align16(sizeof(int32_t) * P->u_cta_item.size());
+  off += align16(sizeof(UniqSlab) * P->dslabs.size());
+  off += align16(sizeof(UniqItem) * P->ditems.size());
+  off += align16(sizeof(int32_t) * P->d_cta_item.size());
   P->bytes = off;
   return CMP_OK;
 }
@@ -609,6 +719,18 @@ extern "C" cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_t
   h.off_u_cta = int64_t(off);
   off += align16(sizeof(int32_t) * P.u_cta_item.size());
   h.u_grid = int32_t(P.u_cta_item.size()) - 1;
+  h.n_dslab = int64_t(P.dslabs.size());
+  h.off_dslab = int64_t(off);
+  off += align16(sizeof(UniqSlab) * P.dslabs.size());
+  h.n_ditems = int64_t(P.ditems.size());
+  h.off_ditems = int64_t(off);
+  off += align16(sizeof(UniqItem) * P.ditems.size());
+  h.off_d_cta = int64_t(off);
+  off += align16(sizeof(int32_t) * P.d_cta_item.size());
+  h.d_grid = int32_t(P.d_cta_item.size()) - 1;
+  h.d_pack16 = P.u_pack16;
+  h.d_words = P.d_words;
+  h.n_presence = P.n_presence;
   h.u_pack16 = P.u_pack16;
   h.u_words = P.u_words;
   h.u_tile_rows = kUniqTileRows;
@@ -643,6 +765,9 @@ extern "C" cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_t
   if (!P.uslabs.empty()) std::memcpy(base + h.off_uslab, P.uslabs.data(), sizeof(UniqSlab) * P.uslabs.size());
   if (!P.uitems.empty()) std::memcpy(base + h.off_uitems, P.uitems.data(), sizeof(UniqItem) * P.uitems.size());
   std::memcpy(base + h.off_u_cta, P.u_cta_item.data(), sizeof(int32_t) * P.u_cta_item.size());
+  if (!P.dslabs.empty()) std::memcpy(base + h.off_dslab, P.dslabs.data(), sizeof(UniqSlab) * P.dslabs.size());
+  if (!P.ditems.empty()) std::memcpy(base + h.off_ditems, P.ditems.data(), sizeof(UniqItem) * P.ditems.size());
+  std::memcpy(base + h.off_d_cta, P.d_cta_item.data(), sizeof(int32_t) * P.d_cta_item.size());
   std::memcpy(base, &h, sizeof(h));
   return CMP_OK;
 }
@@ -676,6 +801,12 @@ extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void
   a.n_uitems = h.n_uitems;
   a.u_pack16 = h.u_pack16;
   a.u_words = h.u_words;
+  a.dslab = reinterpret_cast<const UniqSlab*>(dev + h.off_dslab);
+  a.ditem = reinterpret_cast<const UniqItem*>(dev + h.off_ditems);
+  a.d_cta_item = reinterpret_cast<const int32_t*>(dev + h.off_d_cta);
+  a.n_ditems = h.n_ditems;
+  a.d_pack16 = h.d_pack16;
+  a.d_words = h.d_words;
   if (h.n_agg > 0) {
     a.agg = reinterpret_cast<const AggCol*>(dev + h.off_agg);
     a.n_agg = int32_t(h.n_agg);
@@ -696,7 +827,11 @@ extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void
   // one CTA of each per SM, the two overlap (memory-bound scan, integer-bound hashing)
   if (launch_uniq(a, h.u_grid, kUniqThreadsHost, h.u_tile_rows, cs) != cudaSuccess) return CMP_ECUDA;
   if (h.shape.grid > 0 && launch_build(a, h.shape, cs) != cudaSuccess) return CMP_ECUDA;
-  return launch_agg_hash(a, h.n_agg > 0 ? h.hash_grid : 0, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
+  const int32_t hash_grid = h.n_agg > 0 ? h.hash_grid : 0;
+  if (launch_agg_hash(a, hash_grid, cs) != cudaSuccess) return CMP_ECUDA;
+  // the presence-bitmap columns, beside the hashing of the counted keys when there is one
+  // (as its programmatic dependent: both only read what the counting pass wrote)
+  return launch_dense(a, h.n_ditems > 0 ? h.d_grid : 0, hash_grid > 0, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
 }
 
 
@@ -714,8 +849,10 @@ extern "C" cmp_status cmp_build_plan_stats(const void* plan_host, cmp_build_plan
   info->ws_bytes = h.ws_bytes;
   // zeroing; clearing (+ counting when it has chunks) and hashing of the counted keys; the
   // unique-key kernel; the row kernel
+  // unique-key kernel; the row kernel; the dense kernel
   info->launches = 1 + (h.n_agg > 0 ? 1 + (h.cnt_grid > 0 ? 1 : 0) + (h.hash_grid > 0 ? 1 : 0) : 0) +
-                   (h.n_uitems > 0 && h.u_grid > 0 ? 1 : 0) + (h.shape.grid > 0 ? 1 : 0);
-  info->reserved = 0;
+                   (h.n_uitems > 0 && h.u_grid > 0 ? 1 : 0) + (h.shape.grid > 0 ? 1 : 0) +
+                   (h.n_ditems > 0 && h.d_grid > 0 ? 1 : 0);
+  info->n_presence = h.n_presence;
   return CMP_OK;
 }

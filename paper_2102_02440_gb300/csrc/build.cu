@@ -340,14 +340,20 @@ cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t s
 __global__ void __launch_bounds__(256) k_agg_zero(const __grid_constant__ BuildArgs A) {
   const AggCol ac = A.agg[blockIdx.y];
   int4* c4 = reinterpret_cast<int4*>(A.ws + ac.off);
-  const int64_t n4 = (ac.cap + 3) / 4;
+  const int64_t n4 = ac.kind == kAggPresence ? presence_words(ac.cap) / 4 : (ac.cap + 3) / 4;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x)
     c4[i] = make_int4(0, 0, 0, 0);
 }
 
-// Counting pass of key aggregation.  Persistent CTAs take chunks of 4 tiles of a table's
-// rows in order from an atomic counter.  For every surviving row and every aggregated key
-// column of the table, the key's slot (key - base) & mask gets one count: in the CTA's
+// survivor offsets: a tile's (generic path) or two 256-entry buffers per warp (warp path)
+__host__ __device__ inline size_t agg_count_surv_entries(int32_t tile_rows, int32_t threads) {
+  return tile_rows > 16 * threads ? size_t(tile_rows) : size_t(16) * threads;
+}
+
+// Counting pass of key aggregation.  Persistent CTAs take chunks of whole tiles of a
+// table's rows (CountItem.chunk_rows) in order from an atomic counter.  For every surviving row and every aggregated key
+// column of the table, the key's slot (key - base) & mask gets one count (a presence
+// column: its bit is set; a bit found set already makes the column inactive): in the CTA's
 // direct-mapped shared-memory cache when its cache slot holds that slot index or is free
 // (the frequent keys of a skewed column settle there), else with one global atomic on the
 // count array.  Caches are added to the count arrays when the CTA moves to another table
@@ -363,9 +369,10 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
   __shared__ int32_t* acnt[CMP_MAX_SKETCHES];  // the current table's aggregated columns
   __shared__ int64_t abase[CMP_MAX_SKETCHES], acap[CMP_MAX_SKETCHES];
   __shared__ uint64_t amask[CMP_MAX_SKETCHES];
-  __shared__ int32_t acol[CMP_MAX_SKETCHES], aidx[CMP_MAX_SKETCHES];
+  __shared__ int32_t acol[CMP_MAX_SKETCHES], aidx[CMP_MAX_SKETCHES], akind[CMP_MAX_SKETCHES];
   __shared__ unsigned long long amax[CMP_MAX_SKETCHES], amin[CMP_MAX_SKETCHES];  // encoded
   __shared__ int32_t n_ac;
+  __shared__ uint32_t akeys;  // the current table's aggregated key columns (bit c: column c)
   __shared__ long long next_chunk;
   const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
   const int R = A.tile_rows, H = A.cnt_cache_slots, n_cache = A.cnt_cache_cols;
@@ -374,17 +381,20 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
   uint32_t* ccnt = ckey + size_t(H) * n_cache;          // [n_cache][H] its count so far
   unsigned char* sp = smem + align16(sizeof(uint32_t) * 2 * size_t(H) * n_cache);
   uint16_t* surv = reinterpret_cast<uint16_t*>(sp);
-  sp += align16(sizeof(uint16_t) * R);
+  sp += align16(sizeof(uint16_t) * agg_count_surv_entries(R, T));
   int32_t* sint = reinterpret_cast<int32_t*>(sp);
   constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // never a slot index: cap <= 2^31 - 1
   unsigned long long* work = reinterpret_cast<unsigned long long*>(A.ws) + 2 * int64_t(A.n_agg);
-  const int64_t CH = 4 * int64_t(R);  // rows per chunk
 
   // One surviving key of column a.  Returns false when the key lies outside the column's
   // declared domain (its counts are then discarded: the column keeps the per-row path).
   auto count_key = [&](int a, int64_t key) {
     const uint64_t off = uint64_t(key) - uint64_t(abase[a]);
     if (amask[a] == ~0ull && off >= uint64_t(acap[a])) return false;
+    if (akind[a] == kAggPresence) {  // off < cap <= 2^32
+      const uint32_t bit = 1u << (off & 31);
+      return (atomicOr(reinterpret_cast<uint32_t*>(acnt[a]) + (off >> 5), bit) & bit) == 0;
+    }
     const uint32_t x = uint32_t(off & amask[a]);  // < cap
     if (a < n_cache) {
       const size_t slot = size_t(a) * H + ((x * 0x9E3779B1u) >> hshift);
@@ -416,6 +426,48 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
       atomicMax(&amin[a], (unsigned long long)enc_min(mn));
     }
   };
+  // A counted column's parameters in registers (warp path), and its count of one key: the
+  // same steps as count_key for a count array.
+  struct CntCol {
+    int32_t* cnt;
+    uint32_t* ckey;  // its cache (nullptr: not cached)
+    uint32_t* ccnt;
+    uint64_t base, cap, mask;
+    bool declared;
+  };
+  auto cnt_col = [&](int a) {
+    CntCol cc;
+    cc.cnt = acnt[a];
+    cc.ckey = a < n_cache ? ckey + size_t(a) * H : nullptr;
+    cc.ccnt = a < n_cache ? ccnt + size_t(a) * H : nullptr;
+    cc.base = uint64_t(abase[a]);
+    cc.cap = uint64_t(acap[a]);
+    cc.mask = amask[a];
+    cc.declared = amask[a] == ~0ull;
+    return cc;
+  };
+  auto count_fast = [&](const CntCol& cc, int64_t key) {
+    const uint64_t off = uint64_t(key) - cc.base;
+    if (cc.declared && off >= cc.cap) return false;
+    const uint32_t x = uint32_t(off & cc.mask);
+    if (cc.ckey) {
+      const uint32_t slot = (x * 0x9E3779B1u) >> hshift;
+      const uint32_t cur = *reinterpret_cast<volatile uint32_t*>(cc.ckey + slot);
+      if (cur == x) {
+        atomicAdd(cc.ccnt + slot, 1u);
+        return true;
+      }
+      if (cur == kEmpty) {
+        const uint32_t prev = atomicCAS(cc.ckey + slot, kEmpty, x);
+        if (prev == kEmpty || prev == x) {
+          atomicAdd(cc.ccnt + slot, 1u);
+          return true;
+        }
+      }
+    }
+    atomicAdd(cc.cnt + x, 1);
+    return true;
+  };
   // adds the caches and key ranges of the current table to the global arrays (block-wide)
   auto flush = [&]() {
     __syncthreads();
@@ -432,34 +484,49 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
     __syncthreads();
   };
 
+  // the item of chunk c (items are in chunk order)
+  auto item_of = [&](int64_t c) {
+    int it = 0;
+    while (it + 1 < A.n_cnt_items && A.cnt_items[it + 1].chunk_begin <= c) it++;
+    return it;
+  };
+  // Memory-level parallelism: each warp prefetches into L2 the rows it reads next (bulk
+  // prefetches of whole row ranges, or the key sectors of its survivors): no registers or
+  // shared memory are held for data in flight.
   int item = -1;  // block-uniform
   for (;;) {
     if (tid == 0) next_chunk = (long long)atomicAdd(work, 1ull);
     __syncthreads();
     const int64_t c = next_chunk;
     if (c >= A.cnt_total_chunks) break;  // block-uniform
-    int it = 0;
-    while (it + 1 < A.n_cnt_items && A.cnt_items[it + 1].chunk_begin <= c) it++;
+    const int it = item_of(c);
     const CountItem ci = A.cnt_items[it];
     const DevTable* tb = A.tables + ci.table;
     if (it != item) {  // a new table: flush the caches, then set them up for its columns
       if (item >= 0) flush();
       if (tid == 0) {
         int n = 0;
-        for (int col = 0; col < tb->n_cols && n < CMP_MAX_SKETCHES; col++) {
-          const int ai = tb->agg[col];
-          if (ai < 0) continue;
-          const AggCol& ac = A.agg[ai];
-          acnt[n] = reinterpret_cast<int32_t*>(A.ws + ac.off);
-          abase[n] = ac.base;
-          acap[n] = ac.cap;
-          amask[n] = ac.mask;
-          acol[n] = col;
-          aidx[n] = ai;
-          amax[n] = 0;
-          amin[n] = 0;
-          n++;
-        }
+        uint32_t keys = 0;
+        for (int col = 0; col < tb->n_cols; col++)
+          if (tb->agg[col] >= 0) keys |= 1u << col;
+        akeys = keys;
+        // count arrays first (they take the hot-key caches), then presence bitmaps
+        for (int kind = kAggCount; kind <= kAggPresence; kind++)
+          for (int col = 0; col < tb->n_cols && n < CMP_MAX_SKETCHES; col++) {
+            const int ai = tb->agg[col];
+            if (ai < 0 || A.agg[ai].kind != kind) continue;
+            const AggCol& ac = A.agg[ai];
+            acnt[n] = reinterpret_cast<int32_t*>(A.ws + ac.off);
+            abase[n] = ac.base;
+            acap[n] = ac.cap;
+            amask[n] = ac.mask;
+            acol[n] = col;
+            aidx[n] = ai;
+            akind[n] = kind;
+            amax[n] = 0;
+            amin[n] = 0;
+            n++;
+          }
         n_ac = n;
       }
       for (int s = tid; s < H * n_cache; s += T) {
@@ -471,7 +538,7 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
     }
     const int nac = n_ac;
     const int64_t n_rows = tb->n_rows;
-    const int64_t r_begin = (c - ci.chunk_begin) * CH, r_end = min(n_rows, r_begin + CH);
+    const int64_t r_begin = (c - ci.chunk_begin) * ci.chunk_rows, r_end = min(n_rows, r_begin + ci.chunk_rows);
     const bool vec = tb->vec_ok != 0;
     if (!tb->filtered) {
       if (tid == 0 && r_end > r_begin)
@@ -484,6 +551,15 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
         int64_t mn = INT64_MAX, mx = INT64_MIN;
         bool ok = true;
         for (int64_t r = r_begin + 8 * int64_t(tid); r < r_end; r += 8 * int64_t(T)) {
+          if (lane == 0) {  // this warp's 256 rows of the next step (this column, else the next one's first)
+            const int64_t rw = r + 8 * int64_t(T);
+            if (rw < r_end) {
+              prefetch_rows(tb, 1u << acol[a], rw, min(r_end, rw + 256), 0, 1);
+            } else if (a + 1 < nac) {
+              const int64_t rn = r_begin + (rw - r_begin) % (8 * int64_t(T));
+              prefetch_rows(tb, 1u << acol[a + 1], rn, min(r_end, rn + 256), 0, 1);
+            }
+          }
           int64_t v[8];
           int nv = int(min(int64_t(8), r_end - r));
           if (vec && nv == 8) {
@@ -515,33 +591,44 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
       }
     } else if (vec && !tb->sample_keep && tb->n_preds >= 1 && tb->n_preds <= 2 && nac <= 2 &&
                tb->dtype[tb->pred[0].col] == CMP_I32 && tb->dtype[tb->pred[tb->n_preds - 1].col] == CMP_I32 &&
-               R >= 8 * T) {
-      // Warp-autonomous scan (no block barrier per tile): each warp takes 256 rows at a
-      // time, lane l the 16-byte groups at 4 l and 128 + 4 l, with both predicate columns'
-      // loads in flight together; the warp compacts its survivors' row offsets into its own
-      // 256-entry part of `surv`, then its lanes load every aggregated key of a survivor
-      // together and count them.
+               akind[0] == kAggCount && akind[nac - 1] == kAggCount) {
+      // Warp-autonomous scan in three stages (no block barrier inside the chunk).  Warp w
+      // takes the 256-row steps w, w + nwarps, ...; lane l the 16-byte groups at 4 l and 128 +
+      // 4 l of a step.  While it counts the survivors of step s (lane e holds the keys of
+      // survivor e, loaded during step s - 1), the predicate loads of step s + 1 (prefetched
+      // into L2 during step s - 1) are in flight; then it compacts step s + 1's survivors
+      // into its other 256-entry buffer and issues the loads of their keys, and bulk-
+      // prefetches the predicate rows of step s + 2.  Only the key sectors holding survivors
+      // are read.
       const int warp = tid >> 5, nwarps = T >> 5;
-      uint16_t* wbuf = surv + warp * 256;
-      const DevPred& q0 = tb->pred[0];
-      const DevPred& q1 = tb->pred[tb->n_preds - 1];
-      const int32_t* c0 = reinterpret_cast<const int32_t*>(tb->col[q0.col]);
-      const int32_t* c1 = reinterpret_cast<const int32_t*>(tb->col[q1.col]);
+      uint16_t* wb0 = surv + warp * 512;  // two 256-entry buffers: wb0 + 256 * buf
+      const PredReg q0 = pred_reg(tb->pred[0]);  // in registers for the whole chunk
+      const PredReg q1 = pred_reg(tb->pred[tb->n_preds - 1]);
+      const int32_t* c0 = reinterpret_cast<const int32_t*>(tb->col[tb->pred[0].col]);
+      const int32_t* c1 = reinterpret_cast<const int32_t*>(tb->col[tb->pred[tb->n_preds - 1].col]);
       const void* kb0 = tb->col[acol[0]];
       const void* kb1 = nac > 1 ? tb->col[acol[1]] : kb0;
       const int32_t kd0 = tb->dtype[acol[0]], kd1 = nac > 1 ? tb->dtype[acol[1]] : kd0;
       int64_t mn0 = INT64_MAX, mx0 = INT64_MIN, mn1 = INT64_MAX, mx1 = INT64_MIN;
       bool ok0 = true, ok1 = true;
       unsigned long long n_surv = 0;
-      // two 256-row steps per iteration (rows rb and rb + nwarps 256): the loads of both are
-      // in flight before either is evaluated
-      const int64_t step = int64_t(nwarps) * 256;
-      for (int64_t rb0 = r_begin + int64_t(warp) * 256; rb0 < r_end; rb0 += 2 * step) {
-        int4 v0[4], v1[4];
-        int nv[4];
+      const CntCol cc0 = cnt_col(0), cc1 = cnt_col(nac > 1 ? 1 : 0);
+      const int64_t stride = int64_t(nwarps) * 256;
+      const int64_t rb_first = r_begin + int64_t(warp) * 256;
+      // bulk L2 prefetch of the predicate rows of the step at rb (lanes 0 and 1)
+      auto prefetch_preds = [&](int64_t rb) {
+        if (lane < 2 && rb < r_end) {
+          const int32_t* col = lane == 0 ? c0 : c1;
+          l2_prefetch(col + rb, min(int64_t(256), r_end - rb) * 4);
+        }
+      };
+      int4 v0[2], v1[2];  // predicate values of the next step: groups 4 l and 128 + 4 l
+      int64_t pk0 = 0, pk1 = 0;  // keys of this lane's first survivor of the next step
+      int nv[2];
+      auto load_preds = [&](int64_t rb) {
 #pragma unroll
-        for (int g = 0; g < 4; g++) {
-          const int64_t r = rb0 + (g >> 1) * step + 128 * (g & 1) + 4 * lane;
+        for (int g = 0; g < 2; g++) {
+          const int64_t r = rb + 128 * g + 4 * lane;
           nv[g] = int(max(int64_t(0), min(int64_t(4), r_end - r)));
           if (nv[g] == 4) {
             v0[g] = __ldg(reinterpret_cast<const int4*>(c0 + r));
@@ -557,58 +644,93 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
             v1[g] = make_int4(t1[0], t1[1], t1[2], t1[3]);
           }
         }
+      };
+      // the survivors of the step at rb (predicates in v0, v1) into buffer wbuf; their key
+      // sectors are prefetched into L2.  Returns the count (warp-uniform).
+      const bool ranges = !q0.in && !q1.in;  // the common case: two range / point predicates
+      auto compact = [&](int64_t rb, uint16_t* wbuf) {
+        uint32_t m = 0;
 #pragma unroll
-        for (int half = 0; half < 2; half++) {
-          const int64_t rb = rb0 + half * step;
-          if (rb >= r_end) break;  // warp-uniform
-          uint32_t m = 0;
-#pragma unroll
-          for (int gg = 0; gg < 2; gg++) {
-            const int g = 2 * half + gg;
-            const int a0[4] = {v0[g].x, v0[g].y, v0[g].z, v0[g].w}, a1[4] = {v1[g].x, v1[g].y, v1[g].z, v1[g].w};
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-              if (j < nv[g] && pred_holds(q0, a0[j]) && pred_holds(q1, a1[j])) m |= 1u << (4 * gg + j);
-          }
-          const int c = __popc(m);
-          int incl = c;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-          }
-          const int total = __shfl_sync(0xffffffffu, incl, 31);
-          int pos = incl - c;
-#pragma unroll
-          for (int gg = 0; gg < 2; gg++)
+        for (int g = 0; g < 2; g++) {
+          const int a0[4] = {v0[g].x, v0[g].y, v0[g].z, v0[g].w}, a1[4] = {v1[g].x, v1[g].y, v1[g].z, v1[g].w};
+          if (ranges) {
 #pragma unroll
             for (int j = 0; j < 4; j++)
-              if ((m >> (4 * gg + j)) & 1u) wbuf[pos++] = uint16_t(128 * gg + 4 * lane + j);
-          __syncwarp();
-          n_surv += unsigned(total);
-          for (int e = lane; e < total; e += 32) {
-            const int64_t row = rb + wbuf[e];
-            const int64_t k0 = load1(kb0, kd0, row);
-            const int64_t k1 = nac > 1 ? load1(kb1, kd1, row) : 0;
-            mn0 = min(mn0, k0), mx0 = max(mx0, k0);
-            ok0 &= count_key(0, k0);
-            if (nac > 1) {
-              mn1 = min(mn1, k1), mx1 = max(mx1, k1);
-              ok1 &= count_key(1, k1);
-            }
+              m |= uint32_t(j < nv[g] && uint64_t(int64_t(a0[j])) - q0.lo < q0.span &&
+                            uint64_t(int64_t(a1[j])) - q1.lo < q1.span) << (4 * g + j);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+              if (j < nv[g] && reg_holds(q0, a0[j]) && reg_holds(q1, a1[j])) m |= 1u << (4 * g + j);
           }
-          __syncwarp();
         }
+        const int c = __popc(m);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int pos = incl - c;
+        while (m) {  // this lane's survivors, in row order
+          const int b = __ffs(m) - 1;
+          m &= m - 1;
+          wbuf[pos++] = uint16_t(128 * (b >> 2) + 4 * lane + (b & 3));
+        }
+        __syncwarp();
+        if (lane < total) {  // the keys of survivor `lane`, loaded now and counted next step
+          const int64_t row = rb + wbuf[lane];
+          pk0 = load1(kb0, kd0, row);
+          if (nac > 1) pk1 = load1(kb1, kd1, row);
+        }
+        return total;
+      };
+      // prologue: predicates of steps 0 and 1 prefetched, step 0 compacted
+      prefetch_preds(rb_first);
+      prefetch_preds(rb_first + stride);
+      int n_cur = 0;
+      if (rb_first < r_end) {
+        load_preds(rb_first);
+        n_cur = compact(rb_first, wb0);
+      }
+      int buf = 0;
+      for (int64_t rb = rb_first; rb < r_end; rb += stride) {  // warp-uniform
+        const int64_t rn = rb + stride;
+        prefetch_preds(rn + stride);
+        if (rn < r_end) load_preds(rn);  // in flight while step rb is counted
+        n_surv += unsigned(n_cur);
+        const uint16_t* cur = wb0 + 256 * buf;
+        auto count_row = [&](int64_t k0, int64_t k1) {
+          if (!cc0.declared) mn0 = min(mn0, k0), mx0 = max(mx0, k0);
+          ok0 &= count_fast(cc0, k0);
+          if (nac > 1) {
+            if (!cc1.declared) mn1 = min(mn1, k1), mx1 = max(mx1, k1);
+            ok1 &= count_fast(cc1, k1);
+          }
+        };
+        if (lane < n_cur) count_row(pk0, pk1);
+        for (int e = lane + 32; e < n_cur; e += 32) {  // beyond 32 survivors: loaded here
+          const int64_t row = rb + cur[e];
+          count_row(load1(kb0, kd0, row), nac > 1 ? load1(kb1, kd1, row) : 0);
+        }
+        __syncwarp();
+        buf ^= 1;
+        n_cur = rn < r_end ? compact(rn, wb0 + 256 * buf) : 0;
       }
       if (lane == 0 && n_surv) atomicAdd(reinterpret_cast<unsigned long long*>(tb->survivors), n_surv);
+      // a declared domain holds every surviving key unless one left it: its range is the domain
+      if (cc0.declared) mn0 = int64_t(cc0.base), mx0 = int64_t(cc0.base + cc0.cap - 1);
       if (!ok0) mn0 = INT64_MIN, mx0 = INT64_MAX;
       fold_range(0, mn0, mx0);
       if (nac > 1) {
+        if (cc1.declared) mn1 = int64_t(cc1.base), mx1 = int64_t(cc1.base + cc1.cap - 1);
         if (!ok1) mn1 = INT64_MIN, mx1 = INT64_MAX;
         fold_range(1, mn1, mx1);
       }
     } else {
       for (int64_t r0 = r_begin; r0 < r_end; r0 += R) {
+        if (tid < 32 && r0 + R < r_end) prefetch_rows(tb, akeys, r0 + R, min(r_end, r0 + 2 * int64_t(R)), tid, 32);
         const int rows_in_tile = int(min(int64_t(R), r_end - r0));
         const int n_surv = tile_survivors(tb, r0, rows_in_tile, R, vec, surv, sint);
         if (tid == 0 && n_surv)
@@ -653,6 +775,9 @@ size_t agg_hash_smem_bytes(int32_t max_pairs) {
 template <bool POW2>
 __global__ void __launch_bounds__(kHashThreads) k_agg_hash(const __grid_constant__ BuildArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
+  // the presence-bitmap kernel, launched next as a programmatic dependent, reads nothing
+  // this pass writes: let it start now
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ long long next_chunk;
   __shared__ int32_t n_pairs, active;
   __shared__ long long s_kmin, s_range;
@@ -773,9 +898,9 @@ cudaError_t launch_agg_hash(const BuildArgs& a, int32_t grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-size_t agg_count_smem_bytes(int32_t tile_rows, int32_t cache_slots, int32_t cache_cols) {
+size_t agg_count_smem_bytes(int32_t tile_rows, int32_t cache_slots, int32_t cache_cols, int32_t threads) {
   return align16(sizeof(uint32_t) * 2 * size_t(cache_slots) * size_t(cache_cols)) +
-         align16(sizeof(uint16_t) * tile_rows) + sizeof(int32_t) * 40;
+         align16(sizeof(uint16_t) * agg_count_surv_entries(tile_rows, threads)) + sizeof(int32_t) * 40;
 }
 
 cudaError_t launch_agg(const BuildArgs& a, int32_t tile_rows, int32_t cnt_threads, int32_t cnt_grid,
@@ -785,7 +910,7 @@ cudaError_t launch_agg(const BuildArgs& a, int32_t tile_rows, int32_t cnt_thread
   k_agg_zero<<<g, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || cnt_grid <= 0) return e;
-  const size_t smem = agg_count_smem_bytes(tile_rows, a.cnt_cache_slots, a.cnt_cache_cols);
+  const size_t smem = agg_count_smem_bytes(tile_rows, a.cnt_cache_slots, a.cnt_cache_cols, cnt_threads);
   e = cudaFuncSetAttribute(k_agg_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   // the whole shared memory of the SM, so that a CTA of the unique-key kernel (launched

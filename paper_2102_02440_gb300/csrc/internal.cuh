@@ -85,13 +85,17 @@ __device__ __forceinline__ KeyPow key_powers(uint64_t x) {
 // < 2^62 + 2^32 + 3 * 2^61 < 2^64.
 // SMALLX: the caller guarantees x < 2^31 (k.x.hi == 0), so the products with x.hi, which
 // are zero, are left out (same value, fewer multiplies).
-template <bool POW2, bool SMALLX = false>
-__device__ __forceinline__ uint32_t cw_bucket(const PairParam& q, const KeyPow& k, uint32_t w) {
+template <bool SMALLX = false>
+__device__ __forceinline__ uint64_t cw_bucket_residue(const PairParam& q, const KeyPow& k) {
   const uint64_t t0 = uint64_t(q.a_lo) * k.x.lo;
   const uint64_t t1 = SMALLX ? uint64_t(q.a_hi) * k.x.lo : uint64_t(q.a_lo) * k.x.hi + uint64_t(q.a_hi) * k.x.lo;
   const uint64_t t2 = SMALLX ? 0 : uint64_t(q.a_hi) * k.x.hi;
   const uint64_t s = t0 + (t1 >> 30) + ((t1 & kM30) << 31) + 2 * t2 + q.b;
-  const uint64_t r = canon61(fold61(s));
+  return canon61(fold61(s));
+}
+template <bool POW2, bool SMALLX = false>
+__device__ __forceinline__ uint32_t cw_bucket(const PairParam& q, const KeyPow& k, uint32_t w) {
+  const uint64_t r = cw_bucket_residue<SMALLX>(q, k);
   if (POW2) return uint32_t(r) & (w - 1);
   return uint32_t(r % w);
 }
@@ -100,7 +104,7 @@ __device__ __forceinline__ uint32_t cw_bucket(const PairParam& q, const KeyPow& 
 // are summed by limb position: S0 < 3 * 2^62, S1 < 6 * 2^61, S2 < 3 * 2^60, and
 // fold(S0) + (S1>>30) + ((S1&M30)<<31) + 2 S2 + c0 < 6 * 2^61 + 2^35 < 2^64.
 template <bool SMALLX = false>
-__device__ __forceinline__ int cw_sign(const PairParam& q, const KeyPow& k) {
+__device__ __forceinline__ uint64_t cw_sign_residue(const PairParam& q, const KeyPow& k) {
   const uint64_t S0 = uint64_t(q.c1_lo) * k.x.lo + uint64_t(q.c2_lo) * k.x2.lo + uint64_t(q.c3_lo) * k.x3.lo;
   const uint64_t S1 = (SMALLX ? 0 : uint64_t(q.c1_lo) * k.x.hi) + uint64_t(q.c1_hi) * k.x.lo +
                       uint64_t(q.c2_lo) * k.x2.hi + uint64_t(q.c2_hi) * k.x2.lo + uint64_t(q.c3_lo) * k.x3.hi +
@@ -108,8 +112,11 @@ __device__ __forceinline__ int cw_sign(const PairParam& q, const KeyPow& k) {
   const uint64_t S2 = (SMALLX ? 0 : uint64_t(q.c1_hi) * k.x.hi) + uint64_t(q.c2_hi) * k.x2.hi +
                       uint64_t(q.c3_hi) * k.x3.hi;
   const uint64_t v = fold61(S0) + (S1 >> 30) + ((S1 & kM30) << 31) + 2 * S2 + q.c0;
-  const uint64_t r = canon61(fold61(v));
-  return 1 - 2 * int(r & 1);
+  return canon61(fold61(v));
+}
+template <bool SMALLX = false>
+__device__ __forceinline__ int cw_sign(const PairParam& q, const KeyPow& k) {
+  return 1 - 2 * int(cw_sign_residue<SMALLX>(q, k) & 1);
 }
 
 // ---- Horner form (one (sketch, row) pair per key: no powers to share).  The same two
@@ -243,15 +250,25 @@ enum { kSurvRow = 0, kSurvCount = 1, kSurvUniq = 2 };
 // [n_agg] x (max, min) encoded as uint64 pairs, then the chunk counters of the counting
 // and hashing passes (two uint64; all zeroed before each build, 256-aligned area), then
 // each column's int32 count array at byte offset `off`.
+// A third kind, the presence bitmap, serves a unique key column with a declared domain in
+// a table without predicates: the counting pass sets bit (key - base) of a bitmap instead
+// of counting, and k_dense_hash walks the domain in key order.  A key outside the domain
+// or a bit already set (the column is not unique after all) makes the column inactive, so
+// that it keeps the per-row path.
+enum { kAggCount = 0, kAggPresence = 1 };
 struct AggCol {
   int32_t table, col;
-  int64_t cap;   // count slots
-  int64_t off;   // byte offset of the count array in the workspace
+  int64_t cap;   // count slots (presence: domain keys)
+  int64_t off;   // byte offset of the count array (presence: the bitmap) in the workspace
   int64_t base;  // key of slot 0 (declared domain) or 0
   uint64_t mask; // ~0 (declared domain) or cap - 1 (power of two)
   int64_t hash_chunk0;  // first chunk of this column in the hashing pass (kHashChunk slots each)
+  int32_t kind, pad;    // kAggCount / kAggPresence
 };
 constexpr int64_t kHashChunk = 16384;
+// Presence bitmaps are walked in runs of kDenseRun keys (8 words); a bitmap holds whole runs.
+constexpr int64_t kDenseRun = 256;
+__host__ __device__ inline int64_t presence_words(int64_t cap) { return (cap + kDenseRun - 1) / kDenseRun * (kDenseRun / 32); }
 
 // Order-preserving maps of an int64 to uint64, for atomicMax on the stats pairs (both
 // zero-initialised: an empty column decodes as max < min).
@@ -288,6 +305,8 @@ struct UniqItem {
   int32_t slab, count_surv;  // count_surv: this item adds its range's survivors to the table's count
   int64_t row_begin, row_end;
 };
+// k_dense_hash reuses both: a slab's pad is the AggCol index of its presence column, and an
+// item's [row_begin, row_end) is a range of domain offsets (key - base), whole runs.
 
 // One (table, slab of (sketch,row) pairs) handled by n_ctas consecutive CTAs walking tiles
 // of the table's rows (aggregated key columns are hashed by k_agg_hash instead).
@@ -300,11 +319,12 @@ struct BuildItem {
 };
 
 // Counting pass of key aggregation: the rows of one table as chunks [chunk_begin,
-// chunk_begin + n_chunks) of the pass's global chunk sequence (4 tiles each), handed out to
-// the persistent CTAs in order by an atomic counter.
+// chunk_begin + n_chunks) of the pass's global chunk sequence (chunk_rows each), handed out
+// to the persistent CTAs in order by an atomic counter.
 struct CountItem {
   int32_t table, pad;
   int64_t chunk_begin, n_chunks;
+  int64_t chunk_rows;  // a multiple of 4 tiles
 };
 
 struct BuildShape {
@@ -348,6 +368,12 @@ struct BuildArgs {
   int32_t u_pack16;  // 1: one pair per slab, counters as two 16-bit halves per word
   int32_t u_words;   // shared-memory counter words of a slab
   uint32_t m31, m4;  // 2^31 and 4 (multipliers of the Horner steps)
+  // dense (presence-bitmap) kernel: slabs, items and CTA map as for the unique-key kernel
+  const UniqSlab* dslab;
+  const UniqItem* ditem;
+  const int32_t* d_cta_item;
+  int64_t n_ditems;
+  int32_t d_pack16, d_words;
 };
 
 // Plan blob (host-encoded, device-read) for the batched build.
@@ -366,8 +392,10 @@ struct BuildPlanHdr {
   int32_t hash_max_pairs, hash_grid;
   int64_t n_uslab, off_uslab, n_uitems, off_uitems, off_u_cta;  // unique-key kernel
   int32_t u_grid, u_pack16, u_words, u_tile_rows;
+  int64_t n_dslab, off_dslab, n_ditems, off_ditems, off_d_cta;  // dense kernel
+  int32_t d_grid, d_pack16, d_words, n_presence;
 };
-constexpr int32_t kBuildPlanVersion = 7;
+constexpr int32_t kBuildPlanVersion = 8;
 struct ZeroSpan {
   void* ptr;
   int64_t bytes;
@@ -384,12 +412,14 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 // launchers implemented in the .cu files
 size_t build_smem_bytes(const BuildShape& s, int w);
 cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t st);
-size_t agg_count_smem_bytes(int32_t tile_rows, int32_t cache_slots, int32_t cache_cols);
+size_t agg_count_smem_bytes(int32_t tile_rows, int32_t cache_slots, int32_t cache_cols, int32_t threads);
 cudaError_t launch_agg(const BuildArgs& a, int32_t tile_rows, int32_t cnt_threads, int32_t cnt_grid, cudaStream_t st);
 size_t uniq_smem_bytes(int32_t words, int32_t tile_rows);
 cudaError_t launch_uniq(const BuildArgs& a, int32_t grid, int32_t threads, int32_t tile_rows, cudaStream_t st);
 cudaError_t launch_zero_spans(const ZeroSpan* spans_dev, int32_t n, cudaStream_t st);
 cudaError_t launch_agg_hash(const BuildArgs& a, int32_t grid, cudaStream_t st);
+size_t dense_smem_bytes(int32_t words);
+cudaError_t launch_dense(const BuildArgs& a, int32_t grid, bool pdl, cudaStream_t st);
 
 int sm_count();
 size_t smem_optin_bytes();

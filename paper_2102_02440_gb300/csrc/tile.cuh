@@ -12,6 +12,36 @@ __device__ __forceinline__ int64_t load1(const void* base, int32_t dtype, int64_
                           : int64_t(__ldg(reinterpret_cast<const long long*>(base) + row));
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (cp.async.bulk.prefetch: no registers, no shared
+// memory, no completion to wait for), shrunk to its 16-byte-aligned interior so that no
+// byte outside the range is touched; pieces of at most 32 KB.
+__device__ __forceinline__ void l2_prefetch(const void* p, int64_t bytes) {
+  if (bytes <= 0) return;
+  const size_t g = __cvta_generic_to_global(p);
+  size_t a = (g + 15) & ~size_t(15);
+  const size_t e = (g + size_t(bytes)) & ~size_t(15);
+  for (; a < e; a += 32768) {
+    const uint32_t n = uint32_t(e - a < 32768 ? e - a : 32768);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
+  }
+}
+
+// L2 prefetch of rows [r0, r1) (clamped to the table) of the columns a scan of table tb
+// reads: its predicate columns, then (when with_keys) the key columns selected by
+// key_cols (bit c: column c).  Thread `who` of `nwho` takes every nwho-th column.
+__device__ __forceinline__ void prefetch_rows(const DevTable* tb, uint32_t key_cols, int64_t r0, int64_t r1,
+                                              int who, int nwho) {
+  r1 = r1 < tb->n_rows ? r1 : tb->n_rows;
+  if (r0 >= r1) return;
+  const int np = tb->n_preds, nc = tb->n_cols;
+  for (int j = who; j < np + nc; j += nwho) {
+    const int c = j < np ? tb->pred[j].col : j - np;
+    if (j >= np && !((key_cols >> c) & 1u)) continue;
+    const int es = tb->dtype[c] == CMP_I32 ? 4 : 8;
+    l2_prefetch(static_cast<const char*>(tb->col[c]) + r0 * es, (r1 - r0) * es);
+  }
+}
+
 // 4 consecutive rows starting at `row` (row % 4 == 0); nvalid in 0..4.
 __device__ __forceinline__ void load4(const void* base, int32_t dtype, int64_t row, int nvalid, bool vec,
                                       int64_t v[4]) {
@@ -40,6 +70,30 @@ __device__ __forceinline__ void load4(const void* base, int32_t dtype, int64_t r
 __device__ __forceinline__ bool pred_holds(const DevPred& q, int64_t v) {
   if (q.op == CMP_RANGE) return q.lo <= v && v < q.hi;
   if (q.op == CMP_EQ) return v == q.lo;
+  if (v < 0 || v >= q.nbits) return false;
+  return (__ldg(q.bitmap + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// A predicate in registers: RANGE [lo, hi) and EQ (= [lo, lo + 1)) as one unsigned
+// comparison, v - lo < span in 64-bit arithmetic (span = 0: nothing holds); IN as its
+// bitmap.  The same truth value as pred_holds for every int64 v.
+struct PredReg {
+  uint64_t lo, span;
+  const uint32_t* bitmap;  // IN only
+  int64_t nbits;
+  int32_t in;
+};
+__device__ __forceinline__ PredReg pred_reg(const DevPred& q) {
+  PredReg r;
+  r.in = q.op != CMP_RANGE && q.op != CMP_EQ;
+  r.lo = uint64_t(q.lo);
+  r.span = q.op == CMP_EQ ? 1 : (q.op == CMP_RANGE && q.hi > q.lo ? uint64_t(q.hi) - uint64_t(q.lo) : 0);
+  r.bitmap = q.bitmap;
+  r.nbits = q.nbits;
+  return r;
+}
+__device__ __forceinline__ bool reg_holds(const PredReg& q, int64_t v) {
+  if (!q.in) return uint64_t(v) - q.lo < q.span;
   if (v < 0 || v >= q.nbits) return false;
   return (__ldg(q.bitmap + (v >> 5)) >> (v & 31)) & 1u;
 }

@@ -203,26 +203,65 @@ def _prep_tables(dw):
                 dw.ranks[i] = dw.ranks_all[:0]
 
 
-def _presort_tables(dw, s, offline: bool = False):
-    """cmp_presort of every sketch row of the online (or the offline) tables, then
-    cmp_cross_ranks_multi: one launch each over a contiguous range of the buffers."""
+def sorted_tables(n_tables: int, edge_u, edge_v, masks) -> set:
+    """Tables whose sorted sketch rows (presort, cross ranks) an estimate plan over `masks`
+    reads: the root of every multi-table sub-plan (its lowest table id) and every table
+    joined to two or more others in one.  A table that is only ever a leaf is read through
+    its counters alone, in its neighbour's sorted order."""
+    need = set()
+    for m in masks:
+        m = int(m)
+        if m & (m - 1) == 0:
+            continue  # one table: its survivor count
+        need.add((m & -m).bit_length() - 1)
+        deg = [0] * n_tables
+        for u, v in zip(edge_u, edge_v):
+            if (m >> u) & 1 and (m >> v) & 1:
+                deg[u] += 1
+                deg[v] += 1
+        need.update(t for t in range(n_tables) if deg[t] >= 2)
+    return need
+
+
+def presort_runs(dw, offline: bool = False, only=None) -> list:
+    """The runs of tables that _presort_tables sorts with one launch pair each: [(row
+    offset, rank offset, [tables])], tables consecutive in the buffers."""
     order = getattr(dw, "storage_order", list(range(len(dw.tables))))
     n_on = len(getattr(dw, "online", order))
     lo = sum(dw.tables[i].k for i in order[:n_on]) if offline else 0
     rlo = sum(dw.tables[i].k ** 2 for i in order[:n_on]) if offline else 0
     tabs = order[n_on:] if offline else order[:n_on]
-    total = sum(dw.tables[i].k for i in tabs)
-    if total == 0:
-        return
-    need = K.cmp_presort_ws_bytes(total * dw.d, dw.w)
-    ws = getattr(dw, "presort_ws", None)
-    if need and (ws is None or ws.numel() < need):
-        ws = dw.presort_ws = torch.empty(need, dtype=torch.uint8, device=dw.device)
-    K.cmp_presort(dw.counters_all[lo:].data_ptr(), total * dw.d, dw.w, dw.abs_all[lo:].data_ptr(),
-                  dw.perm_all[lo:].data_ptr(), ws.data_ptr() if need else 0, need, s)
-    K.cmp_cross_ranks_multi(dw.abs_all[lo:].data_ptr(), dw.perm_all[lo:].data_ptr(), [dw.tables[i].k for i in tabs],
-                            [e for i in tabs for e in dw.tables[i].edge_id], dw.d, dw.w, dw.ranks_all[rlo:].data_ptr(),
-                            s)
+    runs, cur = [], None  # [(row offset, rank offset, tables)]
+    for i in tabs:
+        if only is None or i in only:
+            if cur is None:
+                cur = (lo, rlo, [])
+                runs.append(cur)
+            cur[2].append(i)
+        else:
+            cur = None
+        lo += dw.tables[i].k
+        rlo += dw.tables[i].k ** 2
+    return runs
+
+
+def _presort_tables(dw, s, offline: bool = False, only=None):
+    """cmp_presort of every sketch row of the online (or the offline) tables (of those in
+    `only`, when given), then cmp_cross_ranks_multi: one launch each per run of tables
+    consecutive in the buffers."""
+    for lo, rlo, run in presort_runs(dw, offline, only):
+        total = sum(dw.tables[i].k for i in run)
+        if total == 0:
+            continue
+        need = K.cmp_presort_ws_bytes(total * dw.d, dw.w)
+        ws = getattr(dw, "presort_ws", None)
+        if need and (ws is None or ws.numel() < need):
+            ws = dw.presort_ws = torch.empty(need, dtype=torch.uint8, device=dw.device)
+        K.cmp_presort(dw.counters_all[lo:].data_ptr(), total * dw.d, dw.w, dw.abs_all[lo:].data_ptr(),
+                      dw.perm_all[lo:].data_ptr(), ws.data_ptr() if need else 0, need, s)
+        K.cmp_cross_ranks_multi(dw.abs_all[lo:].data_ptr(), dw.perm_all[lo:].data_ptr(),
+                                [dw.tables[i].k for i in run], [e for i in run for e in dw.tables[i].edge_id], dw.d,
+                                dw.w, dw.ranks_all[rlo:].data_ptr(), s)
 
 
 def _graph_struct(dw, g_tables, g_eu, g_ev, sketch_of, survivors_ptr, keep, sample_rates=None):
@@ -275,9 +314,14 @@ class DeviceEstimator:
         self.row_est = torch.empty((self.masks.size, self.d, 2), dtype=torch.int64, device=self.device)
 
     def presort(self, stream=None):
+        """Presort and cross ranks of the tables this plan reads sorted (sorted_tables)."""
         s = K.stream_handle(stream)
-        for dw in self.dws:
-            _presort_tables(dw, s)
+        for g, dw in enumerate(self.dws):
+            _presort_tables(dw, s, only=self.sorted_tables(g))
+
+    def sorted_tables(self, g: int = 0) -> set:
+        dw = self.dws[g]
+        return sorted_tables(len(dw.tables), dw.wl.edge_u, dw.wl.edge_v, self.masks[self.sub_graph == g])
 
     def estimate(self, stream=None, row_est=True):
         status = self.dws[0].status
@@ -509,12 +553,13 @@ class PairBatch:
 
 def build_plan_info(dw) -> dict:
     """Totals of cmp_build_plan_stats over a DeviceWorkload's encoded batched-build plans."""
-    out = {"launches": 0, "n_agg": 0, "n_unique_slabs": 0}
+    out = {"launches": 0, "n_agg": 0, "n_unique_slabs": 0, "n_presence": 0}
     for host, _dev, _wb in (dw._plans or []):
         info = K.cmp_build_plan_stats(host.ctypes.data)
         out["launches"] += int(info.launches)
         out["n_agg"] += int(info.n_agg)
         out["n_unique_slabs"] += int(info.n_unique_slabs)
+        out["n_presence"] += int(info.n_presence)
     return out
 
 

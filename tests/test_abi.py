@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(K):
 def test_status_strings(K):
     assert K.status_str(0) == "ok"
     assert "invalid" in K.status_str(-1)
-    assert K.lib().cmp_abi_version() == K.CMP_ABI_VERSION == 6
+    assert K.lib().cmp_abi_version() == K.CMP_ABI_VERSION == 7
 
 
 def test_hash_params_match_oracle_generator(K, orc):
@@ -133,6 +133,39 @@ def test_column_declarations_plan_host_logic(K):
     nb, _ = K.cmp_build_plan_bytes(uniq, 11, 1024, None)
     buf = np.zeros(nb, np.uint8)
     K.cmp_build_plan_encode(uniq, 11, 1024, 1, [0x2000], 0x4000, None, buf.ctypes.data, nb)
+
+
+def test_presence_columns_plan_host_logic(K):
+    """A unique column with a declared domain of at most four times its table's rows, in a
+    table without predicates or sample, becomes a presence bitmap: one bit per domain key
+    (whole 256-key runs) in the workspace, one more launch (the dense kernel), no unique-key
+    slab.  A predicate, a wider domain, no domain, or the unique paths switched off leave it
+    to the other paths."""
+    n = 1_000_000
+    flags = K.CMP_COL_UNIQUE | K.CMP_COL_DOMAIN
+
+    def stats(tabs, cfg=None, w=1024):
+        nb, wb = K.cmp_build_plan_bytes(tabs, 11, w, cfg)
+        buf = np.zeros(nb, np.uint8)
+        K.cmp_build_plan_encode(tabs, 11, w, 1, [0x2000] * len(tabs), 0x4000, cfg, buf.ctypes.data, nb)
+        return K.cmp_build_plan_stats(buf.ctypes.data), wb
+
+    dense, wb = stats([_desc(K, n_rows=n, flags=flags, dom=(5, 5 + 4 * n))])
+    assert dense.n_presence == 1 and dense.n_agg == 1 and dense.n_unique_slabs == 0
+    assert 4 * n // 8 <= wb < 4 * n // 8 + 4096
+    ragged, wb2 = stats([_desc(K, n_rows=n, flags=flags, dom=(-7, n - 7 + 1))])
+    assert ragged.n_presence == 1 and wb2 >= (n // 256 + 1) * 32
+    # zeroing, clearing, counting, the row kernel (the run-time fallback), the dense kernel
+    assert dense.launches == 5
+    packed, _ = stats([_desc(K, n_rows=n, flags=flags, dom=(0, n))], w=65536)
+    assert packed.n_presence == 1
+    rng = K.cmp_pred(0, K.CMP_RANGE, 0, 100, None, 0)
+    for t, cfg in ((_desc(K, n_rows=n, flags=flags, dom=(0, 4 * n + 1)), None),
+                   (_desc(K, n_rows=n, flags=flags, dom=(0, n), preds=(rng,)), None),
+                   (_desc(K, n_rows=n, flags=K.CMP_COL_UNIQUE), None),
+                   (_desc(K, n_rows=n, flags=flags, dom=(0, n)), K.cmp_build_cfg.make(unique=-1))):
+        st, _ = stats([t], cfg)
+        assert st.n_presence == 0
 
 
 def test_batched_plan_encoding_host_logic(K):

@@ -152,11 +152,14 @@ def test_five_table_declarations_equal_plain_build(orc):
         assert int(a.survivors[i].item()) == ref[1]
 
 
+@pytest.mark.parametrize("dom", [(0, 1), (-(1 << 62), 1 << 62)])
 @pytest.mark.parametrize("w", [65536, 40001, 4096])
-def test_unique_extreme_keys(orc, w):
+def test_unique_extreme_keys(orc, w, dom):
     """int64 keys at the ends of the field and of int64 (0, -1, p - 1, p, p + 1, -p,
     INT64_MIN, INT64_MAX, 2^31 - 1, 2^31, ...) in a unique column, mixed with random keys,
-    so that both the small-key and the general arithmetic run in the same warps."""
+    so that both the small-key and the general arithmetic run in the same warps.  With the
+    domain [0, 1) the column is a presence column whose keys leave the domain (the per-row
+    fallback); with the domain of 2^63 keys it goes to the unique-key kernel."""
     p = (1 << 61) - 1
     ext = [0, 1, -1, p - 1, p, p + 1, -p, -p - 1, 2 * p, 2 * p + 1, (1 << 31) - 1, 1 << 31, -(1 << 31),
            (1 << 62) + 3, -(1 << 63), (1 << 63) - 1, (1 << 63) - 2, -(1 << 63) + 1]
@@ -165,7 +168,7 @@ def test_unique_extreme_keys(orc, w):
     small = rng.permutation(100_000).astype(np.int64) + 10
     keys = np.concatenate([np.array(ext, np.int64), rand, small])
     rng.shuffle(keys)
-    t = G.Table("X", [keys], [], [0, 0], [0, 1], [("unique", 0, 1)])
+    t = G.Table("X", [keys], [], [0, 0], [0, 1], [("unique", dom[0], dom[1])])
     wl = G.Workload("extreme", [t], [0, 0], [0, 0], 5, w, 31, 1)
     ref = [orc.build_sketch(t, P.DeviceWorkload(wl).hash_u64, wl.d, wl.w)]
     _same(_build(wl, None), ref)
