@@ -769,9 +769,7 @@ def measure(a, wl, dev, world: int, rank: int, headline: bool):
             for k in range(min(a.warmup, 2) + a.steps):
                 flush.zero_()
                 e0.record(stream)
-                for tc, t in zip(host_cols, dw.tables):
-                    for hc, dc in zip(tc, t.cols):
-                        dc.copy_(hc, non_blocking=True)
+                dw.upload(host_cols, stream=stream)
                 if graph is not None:
                     graph.replay()
                 else:

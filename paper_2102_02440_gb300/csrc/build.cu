@@ -351,15 +351,16 @@ __host__ __device__ inline size_t agg_count_surv_entries(int32_t tile_rows, int3
 }
 
 // Counting pass of key aggregation.  Persistent CTAs take chunks of whole tiles of a
-// table's rows (CountItem.chunk_rows) in order from an atomic counter.  For every surviving row and every aggregated key
-// column of the table, the key's slot (key - base) & mask gets one count (a presence
-// column: its bit is set; a bit found set already makes the column inactive): in the CTA's
-// direct-mapped shared-memory cache when its cache slot holds that slot index or is free
-// (the frequent keys of a skewed column settle there), else with one global atomic on the
-// count array.  Caches are added to the count arrays when the CTA moves to another table
-// or ends.  The pass also records each column's smallest and largest surviving key
-// (thread-local, then warp and CTA reductions, then one global atomic pair per column and
-// table visit), and counts the table's survivors.
+// table's rows (CountItem.chunk_rows) in order from an atomic counter.  For every surviving
+// row and every aggregated key column of the table, the key's slot (key - base) & mask gets
+// one count (a presence column: its bit is set; a bit found set already makes the column
+// inactive): in the CTA's two-way set-associative shared-memory cache when a way of its set
+// holds that slot index or is free (the frequent keys of a skewed column settle there),
+// else with one global atomic on the count array.  Caches are added to the count arrays
+// when the CTA moves to another table or ends.  The pass also records each column's
+// smallest and largest surviving key (thread-local, then warp and CTA reductions, then one
+// global atomic pair per column and table visit; a declared domain stands for them), and
+// counts the table's survivors.
 __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ BuildArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   // The unique-key kernel, launched next as a programmatic dependent, reads nothing this
@@ -388,6 +389,27 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
 
   // One surviving key of column a.  Returns false when the key lies outside the column's
   // declared domain (its counts are then discarded: the column keeps the per-row path).
+  // The hot-key cache of one column: H / 2 sets of two (key, count) slots, a set chosen by a
+  // multiplicative hash of the slot index x.  x is counted in the way that holds it, else in
+  // an empty way it claims (compare-and-swap; a way once claimed keeps its key until the
+  // flush), else not at all (returns false: the caller counts it in the global array).
+  auto cache_count = [&](uint32_t* keys, uint32_t* cnts, uint32_t x) {
+    const uint32_t set2 = ((x * 0x9E3779B1u) >> (hshift + 1)) * 2;
+    const unsigned long long both = *reinterpret_cast<volatile unsigned long long*>(keys + set2);
+    const uint2 cur = make_uint2(uint32_t(both), uint32_t(both >> 32));
+    if (cur.x == x || cur.y == x) {
+      atomicAdd(cnts + set2 + (cur.x == x ? 0 : 1), 1u);
+      return true;
+    }
+    for (int way = cur.x == kEmpty ? 0 : (cur.y == kEmpty ? 1 : 2); way < 2; way++) {
+      const uint32_t prev = atomicCAS(keys + set2 + way, kEmpty, x);
+      if (prev == kEmpty || prev == x) {
+        atomicAdd(cnts + set2 + way, 1u);
+        return true;
+      }
+    }
+    return false;
+  };
   auto count_key = [&](int a, int64_t key) {
     const uint64_t off = uint64_t(key) - uint64_t(abase[a]);
     if (amask[a] == ~0ull && off >= uint64_t(acap[a])) return false;
@@ -396,21 +418,7 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
       return (atomicOr(reinterpret_cast<uint32_t*>(acnt[a]) + (off >> 5), bit) & bit) == 0;
     }
     const uint32_t x = uint32_t(off & amask[a]);  // < cap
-    if (a < n_cache) {
-      const size_t slot = size_t(a) * H + ((x * 0x9E3779B1u) >> hshift);
-      const uint32_t cur = *reinterpret_cast<volatile uint32_t*>(ckey + slot);
-      if (cur == x) {
-        atomicAdd(ccnt + slot, 1u);
-        return true;
-      }
-      if (cur == kEmpty) {
-        const uint32_t prev = atomicCAS(ckey + slot, kEmpty, x);
-        if (prev == kEmpty || prev == x) {
-          atomicAdd(ccnt + slot, 1u);
-          return true;
-        }
-      }
-    }
+    if (a < n_cache && cache_count(ckey + size_t(a) * H, ccnt + size_t(a) * H, x)) return true;
     atomicAdd(acnt[a] + x, 1);
     return true;
   };
@@ -450,21 +458,7 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
     const uint64_t off = uint64_t(key) - cc.base;
     if (cc.declared && off >= cc.cap) return false;
     const uint32_t x = uint32_t(off & cc.mask);
-    if (cc.ckey) {
-      const uint32_t slot = (x * 0x9E3779B1u) >> hshift;
-      const uint32_t cur = *reinterpret_cast<volatile uint32_t*>(cc.ckey + slot);
-      if (cur == x) {
-        atomicAdd(cc.ccnt + slot, 1u);
-        return true;
-      }
-      if (cur == kEmpty) {
-        const uint32_t prev = atomicCAS(cc.ckey + slot, kEmpty, x);
-        if (prev == kEmpty || prev == x) {
-          atomicAdd(cc.ccnt + slot, 1u);
-          return true;
-        }
-      }
-    }
+    if (cc.ckey && cache_count(cc.ckey, cc.ccnt, x)) return true;
     atomicAdd(cc.cnt + x, 1);
     return true;
   };
@@ -613,19 +607,45 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
       bool ok0 = true, ok1 = true;
       unsigned long long n_surv = 0;
       const CntCol cc0 = cnt_col(0), cc1 = cnt_col(nac > 1 ? 1 : 0);
+      // A cache miss is counted with a global atomic one step later (at most one per lane and
+      // column; a second one in the same step at once), its count-array line prefetched into
+      // L2 now: the atomic then finds the line in L2 instead of waiting for DRAM there.
+      uint32_t pend0 = kEmpty, pend1 = kEmpty;
+      auto count_deferred = [&](const CntCol& cc, int64_t key, uint32_t& pend) {
+        const uint64_t off = uint64_t(key) - cc.base;
+        if (cc.declared && off >= cc.cap) return false;
+        const uint32_t x = uint32_t(off & cc.mask);
+        if (cc.ckey && cache_count(cc.ckey, cc.ccnt, x)) return true;
+        if (pend == kEmpty) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(cc.cnt + x)));
+          pend = x;
+        } else {
+          atomicAdd(cc.cnt + x, 1);
+        }
+        return true;
+      };
       const int64_t stride = int64_t(nwarps) * 256;
       const int64_t rb_first = r_begin + int64_t(warp) * 256;
       // bulk L2 prefetch of the predicate rows of the step at rb (lanes 0 and 1)
+      // (rb is a multiple of 4 rows from the 16-byte aligned columns: a whole step is one
+      // aligned 1 KB prefetch per column; a partial last step is not prefetched)
       auto prefetch_preds = [&](int64_t rb) {
-        if (lane < 2 && rb < r_end) {
-          const int32_t* col = lane == 0 ? c0 : c1;
-          l2_prefetch(col + rb, min(int64_t(256), r_end - rb) * 4);
-        }
+        if (lane < 2 && rb + 256 <= r_end) l2_prefetch_exact((lane == 0 ? c0 : c1) + rb, 1024u);
       };
       int4 v0[2], v1[2];  // predicate values of the next step: groups 4 l and 128 + 4 l
       int64_t pk0 = 0, pk1 = 0;  // keys of this lane's first survivor of the next step
       int nv[2];
       auto load_preds = [&](int64_t rb) {
+        if (rb + 256 <= r_end) {  // a whole step (warp-uniform): no bounds per group
+#pragma unroll
+          for (int g = 0; g < 2; g++) {
+            const int64_t r = rb + 128 * g + 4 * lane;
+            nv[g] = 4;
+            v0[g] = __ldg(reinterpret_cast<const int4*>(c0 + r));
+            v1[g] = __ldg(reinterpret_cast<const int4*>(c1 + r));
+          }
+          return;
+        }
 #pragma unroll
         for (int g = 0; g < 2; g++) {
           const int64_t r = rb + 128 * g + 4 * lane;
@@ -648,6 +668,7 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
       // the survivors of the step at rb (predicates in v0, v1) into buffer wbuf; their key
       // sectors are prefetched into L2.  Returns the count (warp-uniform).
       const bool ranges = !q0.in && !q1.in;  // the common case: two range / point predicates
+      const PredI32 p0 = pred_i32(tb->pred[0]), p1 = pred_i32(tb->pred[tb->n_preds - 1]);
       auto compact = [&](int64_t rb, uint16_t* wbuf) {
         uint32_t m = 0;
 #pragma unroll
@@ -656,8 +677,7 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
           if (ranges) {
 #pragma unroll
             for (int j = 0; j < 4; j++)
-              m |= uint32_t(j < nv[g] && uint64_t(int64_t(a0[j])) - q0.lo < q0.span &&
-                            uint64_t(int64_t(a1[j])) - q1.lo < q1.span) << (4 * g + j);
+              m |= uint32_t(j < nv[g] && i32_holds(p0, a0[j]) && i32_holds(p1, a1[j])) << (4 * g + j);
           } else {
 #pragma unroll
             for (int j = 0; j < 4; j++)
@@ -701,12 +721,16 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
         if (rn < r_end) load_preds(rn);  // in flight while step rb is counted
         n_surv += unsigned(n_cur);
         const uint16_t* cur = wb0 + 256 * buf;
+        // the global atomics of last step's cache misses: their lines were prefetched then
+        if (pend0 != kEmpty) atomicAdd(cc0.cnt + pend0, 1);
+        if (pend1 != kEmpty) atomicAdd(cc1.cnt + pend1, 1);
+        pend0 = pend1 = kEmpty;
         auto count_row = [&](int64_t k0, int64_t k1) {
           if (!cc0.declared) mn0 = min(mn0, k0), mx0 = max(mx0, k0);
-          ok0 &= count_fast(cc0, k0);
+          ok0 &= count_deferred(cc0, k0, pend0);
           if (nac > 1) {
             if (!cc1.declared) mn1 = min(mn1, k1), mx1 = max(mx1, k1);
-            ok1 &= count_fast(cc1, k1);
+            ok1 &= count_deferred(cc1, k1, pend1);
           }
         };
         if (lane < n_cur) count_row(pk0, pk1);
@@ -718,6 +742,8 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
         buf ^= 1;
         n_cur = rn < r_end ? compact(rn, wb0 + 256 * buf) : 0;
       }
+      if (pend0 != kEmpty) atomicAdd(cc0.cnt + pend0, 1);
+      if (pend1 != kEmpty) atomicAdd(cc1.cnt + pend1, 1);
       if (lane == 0 && n_surv) atomicAdd(reinterpret_cast<unsigned long long*>(tb->survivors), n_surv);
       // a declared domain holds every surviving key unless one left it: its range is the domain
       if (cc0.declared) mn0 = int64_t(cc0.base), mx0 = int64_t(cc0.base + cc0.cap - 1);

@@ -36,8 +36,9 @@ constexpr int kDenseThreads = 512;
 constexpr int kRunWords = int(kDenseRun / 32);
 constexpr int kRuns = 2;  // runs per thread in flight: independent difference chains
 
-// Lazy residues: values v <= 2^61 + 1 with v = the residue (mod p).  The sum of two is
-// below 2^62 + 3 and one fold, (s mod 2^61) + (s >> 61), brings it back to <= 2^61 + 1.
+// Lazy residues: folded values v <= 2^61 + 3 with v = the residue (mod p).  A sum of
+// operands below 2^63 folds, (s mod 2^61) + (s >> 61), back to <= 2^61 + 3.  D2 is folded
+// every other step only: unfolded it stays below 2^62 + 7, and D1 + D2 below 2^63.
 __device__ __forceinline__ uint64_t add_lazy(uint64_t u, uint64_t v) { return fold61(u + v); }
 __device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b) { return a >= b ? a - b : a + kP61 - b; }
 
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_hash(const __grid_co
 #pragma unroll
             for (int u = 0; u < kRuns; u++) {
               if (m[u] & 1u) {
-                // residues: P or P - p (P <= p + 2); its parity flips with the subtraction
+                // residues: P or P - p (P <= p + 4 < 2p); its parity flips with the subtraction
                 const uint32_t geP = uint32_t((st[u].P + 1) >> 61), geB = uint32_t((st[u].B + 1) >> 61);
                 const int sg = 1 - 2 * int((uint32_t(st[u].P) ^ geP) & 1u);
                 uint32_t h;
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_hash(const __grid_co
               m[u] >>= 1;
               st[u].P = add_lazy(st[u].P, st[u].D1);
               st[u].D1 = add_lazy(st[u].D1, st[u].D2);
-              st[u].D2 = add_lazy(st[u].D2, D3[u]);
+              st[u].D2 = (b & 1) ? add_lazy(st[u].D2, D3[u]) : st[u].D2 + D3[u];
               st[u].B = add_lazy(st[u].B, a_step);
             }
           }

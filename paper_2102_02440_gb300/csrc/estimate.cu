@@ -221,6 +221,18 @@ __device__ __forceinline__ int rank_in(const uint32_t* __restrict__ a, int w, ui
   return lo;
 }
 
+// The same search in a shared-memory window (plain loads).
+__device__ __forceinline__ int rank_in_shared(const uint32_t* a, int n, uint32_t tau, bool strict) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const uint32_t v = a[mid];
+    if (strict ? v <= tau : v < tau) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // One CTA per (x, y, row): ranks of x's sorted magnitudes in y's, or x's inverse permutation.
 __global__ void k_cross_ranks(const __grid_constant__ CrossArgs A) {
   const int k = A.k, d = A.d, w = A.w;
@@ -252,23 +264,45 @@ struct CrossMultiArgs {
   int32_t edge[kCrossMultiTables][CMP_MAX_SKETCHES];
 };
 
-__global__ void k_cross_ranks_multi(const __grid_constant__ CrossMultiArgs A) {
-  const int64_t blk = blockIdx.x;
+// One CTA per (table, x, y, row, segment of kCrossSeg sorted positions of x).  x's sorted
+// magnitudes are ascending, so their ranks in y's are too: the segment's ranks lie between
+// the ranks of its first and last value, and that window of y's row is staged in shared
+// memory (when it fits; else the searches read y's row in global memory).
+constexpr int kCrossSeg = 2048;
+constexpr int kCrossWin = 4096;
+__global__ void __launch_bounds__(256) k_cross_ranks_multi(const __grid_constant__ CrossMultiArgs A) {
+  __shared__ uint32_t win[kCrossWin];
+  __shared__ int32_t s_lo, s_hi;
+  const int w = A.w, d = A.d;
+  const int64_t nseg = (w + kCrossSeg - 1) / kCrossSeg;
+  const int64_t blk = blockIdx.x / nseg;
+  const int r0 = int(blockIdx.x % nseg) * kCrossSeg, r1 = min(w, r0 + kCrossSeg);
   int t = 0;
   while (t + 1 < A.n && A.blk0[t + 1] <= blk) t++;
-  const int k = A.k[t], d = A.d, w = A.w;
+  const int k = A.k[t];
   const int64_t b = blk - A.blk0[t];
   const int row = int(b % d), y = int((b / d) % k), x = int(b / (int64_t(d) * k));
   int32_t* out = A.ranks + A.rank_off[t] + ((int64_t(x) * k + y) * d + row) * w;
   if (x == y) {
     const int32_t* perm = A.perm + (A.row_off[t] + int64_t(x) * d + row) * w;
-    for (int r = threadIdx.x; r < w; r += blockDim.x) out[__ldg(perm + r)] = r;
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) out[__ldg(perm + r)] = r;
     return;
   }
   const uint32_t* ax = A.abs + (A.row_off[t] + int64_t(x) * d + row) * w;
   const uint32_t* ay = A.abs + (A.row_off[t] + int64_t(y) * d + row) * w;
   const bool strict = A.edge[t][y] < A.edge[t][x];
-  for (int r = threadIdx.x; r < w; r += blockDim.x) out[r] = rank_in(ay, w, __ldg(ax + r), strict);
+  if (threadIdx.x == 0) s_lo = rank_in(ay, w, __ldg(ax + r0), strict);
+  if (threadIdx.x == 32) s_hi = rank_in(ay, w, __ldg(ax + r1 - 1), strict);
+  __syncthreads();
+  const int lo = s_lo, n = s_hi - lo;  // block-uniform
+  if (n <= kCrossWin) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) win[j] = __ldg(ay + lo + j);
+    __syncthreads();
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+      out[r] = lo + rank_in_shared(win, n, __ldg(ax + r), strict);
+  } else {
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) out[r] = rank_in(ay, w, __ldg(ax + r), strict);
+  }
 }
 
 cudaError_t launch_cross_ranks_multi(const uint32_t* abs, const int32_t* perm, int32_t n_tables, const int32_t* k,
@@ -297,7 +331,7 @@ cudaError_t launch_cross_ranks_multi(const uint32_t* abs, const int32_t* perm, i
     }
     a.blk0[a.n] = blk;
     if (blk > 0) {
-      k_cross_ranks_multi<<<unsigned(blk), 256, 0, st>>>(a);
+      k_cross_ranks_multi<<<unsigned(blk * ((w + kCrossSeg - 1) / kCrossSeg)), 256, 0, st>>>(a);
       const cudaError_t err = cudaGetLastError();
       if (err != cudaSuccess) return err;
     }

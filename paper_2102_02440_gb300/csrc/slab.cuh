@@ -38,8 +38,10 @@ __device__ __forceinline__ void counter_add(uint32_t* cs, int32_t* g, uint32_t h
   if (PACK16) {
     const uint32_t odd = h & 1u;
     uint32_t* wd = cs + (h >> 1);
-    const uint32_t old = atomicAdd(wd, uint32_t(sg) << (odd << 4));
-    if (((old & 0xFFFFu) - 1u) >= 0xFFFEu || ((old >> 16) - 1u) >= 0xFFFEu)
+    const uint32_t sh = odd << 4;
+    const uint32_t old = atomicAdd(wd, uint32_t(sg) << sh);
+    // only the updated half can wrap (the other one changes only through its carry)
+    if ((((old >> sh) & 0xFFFFu) - 1u) >= 0xFFFEu)
       pack16_wrap(wd, g + (h & ~1u), odd ? 0 : sg, odd ? sg : 0, old, (h | 1u) < w);
   } else {
     atomicAdd(reinterpret_cast<int32_t*>(cs) + h, sg);

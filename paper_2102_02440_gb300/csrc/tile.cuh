@@ -26,6 +26,12 @@ __device__ __forceinline__ void l2_prefetch(const void* p, int64_t bytes) {
   }
 }
 
+// One bulk L2 prefetch of [p, p + bytes): p 16-byte aligned, bytes a multiple of 16 and at
+// most 2^20 (the caller guarantees both).
+__device__ __forceinline__ void l2_prefetch_exact(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(bytes) : "memory");
+}
+
 // L2 prefetch of rows [r0, r1) (clamped to the table) of the columns a scan of table tb
 // reads: its predicate columns, then (when with_keys) the key columns selected by
 // key_cols (bit c: column c).  Thread `who` of `nwho` takes every nwho-th column.
@@ -72,6 +78,28 @@ __device__ __forceinline__ bool pred_holds(const DevPred& q, int64_t v) {
   if (q.op == CMP_EQ) return v == q.lo;
   if (v < 0 || v >= q.nbits) return false;
   return (__ldg(q.bitmap + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// A RANGE or EQ predicate on an int32 column as one 32-bit unsigned comparison: v holds iff
+// uint32(v - lo) < span, with [lo, lo + span) the predicate's interval clipped to int32;
+// all = every int32 value holds (an interval of 2^32 values), none when it is empty.
+struct PredI32 {
+  uint32_t lo, span;
+  int32_t all;
+};
+__device__ __forceinline__ PredI32 pred_i32(const DevPred& q) {
+  int64_t L = q.lo, H = q.op == CMP_EQ ? q.lo + 1 : q.hi;  // [L, H)
+  if (q.op == CMP_EQ && q.lo == INT64_MAX) H = INT64_MAX;  // no int32 value equals it anyway
+  L = L < INT32_MIN ? INT32_MIN : L;
+  H = H > int64_t(INT32_MAX) + 1 ? int64_t(INT32_MAX) + 1 : H;
+  PredI32 r;
+  r.all = L == INT32_MIN && H == int64_t(INT32_MAX) + 1;
+  r.lo = uint32_t(L);
+  r.span = H > L && !r.all ? uint32_t(H - L) : 0u;  // < 2^32 unless all
+  return r;
+}
+__device__ __forceinline__ bool i32_holds(const PredI32& q, int32_t v) {
+  return q.all || uint32_t(v) - q.lo < q.span;
 }
 
 // A predicate in registers: RANGE [lo, hi) and EQ (= [lo, lo + 1)) as one unsigned

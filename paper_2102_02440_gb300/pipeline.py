@@ -151,6 +151,30 @@ class DeviceWorkload:
         self._plan = self._plans[0] if len(self._plans) == 1 else None
         return sum(p[0].size for p in self._plans)
 
+    def upload(self, host_cols, n_streams: int = 4, stream=None):
+        """Copies every column from host memory (host_cols[t][c], ideally pinned, the shapes and
+        dtypes of the device columns) into the device columns the build reads, each column cut
+        into n_streams contiguous parts copied on as many side streams (the copy engines run
+        them side by side); `stream` (default: the current one) waits for all of them."""
+        main = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if getattr(self, "_up_streams", None) is None or len(self._up_streams) != n_streams:
+            self._up_streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
+            self._up_events = [torch.cuda.Event() for _ in range(n_streams)]
+        start = torch.cuda.Event()
+        start.record(main)
+        for i, st in enumerate(self._up_streams):
+            st.wait_event(start)
+            with torch.cuda.stream(st):
+                for hc, t in zip(host_cols, self.tables):
+                    for h, dcol in zip(hc, t.cols):
+                        n = dcol.numel()
+                        a, b = n * i // n_streams, n * (i + 1) // n_streams
+                        if b > a:
+                            dcol[a:b].copy_(h[a:b], non_blocking=True)
+            self._up_events[i].record(st)
+        for ev in self._up_events:
+            main.wait_event(ev)
+
     def build_batched(self, cfg=None, stream=None):
         if self._plans is None or (self._plan is None and len(self._plans) == 1):
             self.encode_batched(cfg)
