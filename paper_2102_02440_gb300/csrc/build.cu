@@ -158,9 +158,14 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
       const uint32_t h1 = cw_bucket<POW2, SMALLX>(q, k1, uint32_t(w));
       const int32_t v0 = cw_sign<SMALLX>(q, k0) * m0;
       const int32_t v1 = cw_sign<SMALLX>(q, k1) * m1;
-      int32_t* row = (GLOBAL ? gcnt : cnt) + size_t(pp) * w;
-      atomicAdd(row + h0, v0);
-      if (m1) atomicAdd(row + h1, v1);
+      int32_t* row = (GLOBAL ? gcnt : cnt) + size_t(pp) * w;  // L2 counters, or the CTA's shared ones
+      if (GLOBAL) {
+        red_add(row + h0, v0);
+        if (m1) red_add(row + h1, v1);
+      } else {
+        red_add_shared(row + h0, v0);
+        if (m1) red_add_shared(row + h1, v1);
+      }
     }
   };
   auto hash_entries = [&](int kc, int n_entries, const void* kbase, int32_t kdt, int64_t r0, bool from_map) {
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
             for (int probe = 0; probe < M; probe++) {
               const unsigned long long prev = atomicCAS(&mkey[slot], kEmptyKey, x);
               if (prev == kEmptyKey || prev == x) {
-                atomicAdd(&mcnt[slot], __popc(peers));
+                red_add_shared(&mcnt[slot], int32_t(__popc(peers)));
                 done = true;
                 break;
               }
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(1024) k_sketch_build(const __grid_constant__ B
     __syncthreads();
     for (int j = tid; j < npairs * w; j += T) {
       const int32_t v = cnt[j];
-      if (v) atomicAdd(gcnt + j, v);
+      if (v) red_add(gcnt + j, v);
     }
   }
   if (pair_begin == 0 && tid == 0 && my_survivors)
@@ -398,13 +403,13 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
     const unsigned long long both = *reinterpret_cast<volatile unsigned long long*>(keys + set2);
     const uint2 cur = make_uint2(uint32_t(both), uint32_t(both >> 32));
     if (cur.x == x || cur.y == x) {
-      atomicAdd(cnts + set2 + (cur.x == x ? 0 : 1), 1u);
+      red_add_shared(cnts + set2 + (cur.x == x ? 0 : 1), 1u);
       return true;
     }
     for (int way = cur.x == kEmpty ? 0 : (cur.y == kEmpty ? 1 : 2); way < 2; way++) {
       const uint32_t prev = atomicCAS(keys + set2 + way, kEmpty, x);
       if (prev == kEmpty || prev == x) {
-        atomicAdd(cnts + set2 + way, 1u);
+        red_add_shared(cnts + set2 + way, 1u);
         return true;
       }
     }
@@ -419,7 +424,7 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
     }
     const uint32_t x = uint32_t(off & amask[a]);  // < cap
     if (a < n_cache && cache_count(ckey + size_t(a) * H, ccnt + size_t(a) * H, x)) return true;
-    atomicAdd(acnt[a] + x, 1);
+    red_add(acnt[a] + x, 1);
     return true;
   };
   // thread-local key range of column a -> shared (warp-reduced first)
@@ -459,7 +464,7 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
     if (cc.declared && off >= cc.cap) return false;
     const uint32_t x = uint32_t(off & cc.mask);
     if (cc.ckey && cache_count(cc.ckey, cc.ccnt, x)) return true;
-    atomicAdd(cc.cnt + x, 1);
+    red_add(cc.cnt + x, 1);
     return true;
   };
   // adds the caches and key ranges of the current table to the global arrays (block-wide)
@@ -468,7 +473,7 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
     for (int a = 0; a < min(int(n_ac), n_cache); a++)
       for (int s = tid; s < H; s += T) {
         const uint32_t k = ckey[size_t(a) * H + s];
-        if (k != kEmpty) atomicAdd(acnt[a] + k, int32_t(ccnt[size_t(a) * H + s]));
+        if (k != kEmpty) red_add(acnt[a] + k, int32_t(ccnt[size_t(a) * H + s]));
       }
     if (tid < n_ac && amax[tid] != 0) {
       unsigned long long* st = reinterpret_cast<unsigned long long*>(A.ws) + 2 * int64_t(aidx[tid]);
@@ -620,7 +625,7 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
           asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(cc.cnt + x)));
           pend = x;
         } else {
-          atomicAdd(cc.cnt + x, 1);
+          red_add(cc.cnt + x, 1);
         }
         return true;
       };
@@ -722,8 +727,8 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
         n_surv += unsigned(n_cur);
         const uint16_t* cur = wb0 + 256 * buf;
         // the global atomics of last step's cache misses: their lines were prefetched then
-        if (pend0 != kEmpty) atomicAdd(cc0.cnt + pend0, 1);
-        if (pend1 != kEmpty) atomicAdd(cc1.cnt + pend1, 1);
+        if (pend0 != kEmpty) red_add(cc0.cnt + pend0, 1);
+        if (pend1 != kEmpty) red_add(cc1.cnt + pend1, 1);
         pend0 = pend1 = kEmpty;
         auto count_row = [&](int64_t k0, int64_t k1) {
           if (!cc0.declared) mn0 = min(mn0, k0), mx0 = max(mx0, k0);
@@ -742,8 +747,8 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
         buf ^= 1;
         n_cur = rn < r_end ? compact(rn, wb0 + 256 * buf) : 0;
       }
-      if (pend0 != kEmpty) atomicAdd(cc0.cnt + pend0, 1);
-      if (pend1 != kEmpty) atomicAdd(cc1.cnt + pend1, 1);
+      if (pend0 != kEmpty) red_add(cc0.cnt + pend0, 1);
+      if (pend1 != kEmpty) red_add(cc1.cnt + pend1, 1);
       if (lane == 0 && n_surv) atomicAdd(reinterpret_cast<unsigned long long*>(tb->survivors), n_surv);
       // a declared domain holds every surviving key unless one left it: its range is the domain
       if (cc0.declared) mn0 = int64_t(cc0.base), mx0 = int64_t(cc0.base + cc0.cap - 1);
@@ -876,8 +881,8 @@ __global__ void __launch_bounds__(kHashThreads) k_agg_hash(const __grid_constant
             int32_t* row = prow[p];
             const uint32_t h0 = cw_bucket<POW2, SX>(q, k0, w), h1 = cw_bucket<POW2, SX>(q, k1, w);
             const int32_t v0 = cw_sign<SX>(q, k0) * m0, v1 = cw_sign<SX>(q, k1) * m1;
-            if (m0) atomicAdd(row + h0, v0);
-            if (m1) atomicAdd(row + h1, v1);
+            if (m0) red_add(row + h0, v0);
+            if (m1) red_add(row + h1, v1);
           }
         };
         if (__all_sync(0xffffffffu, (k0.x.hi | k1.x.hi) == 0)) run(std::true_type{});

@@ -94,14 +94,14 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_hash(const __grid_co
       for (int j = tid; j < words; j += T) {
         const uint32_t v = cs[j];
         const int32_t lo = int32_t(v & 0xFFFFu) - int32_t(kHalfBias), hi = int32_t(v >> 16) - int32_t(kHalfBias);
-        if (lo) atomicAdd(g + 2 * j, lo);
-        if (hi && uint32_t(2 * j + 1) < w) atomicAdd(g + 2 * j + 1, hi);
+        if (lo) red_add(g + 2 * j, lo);
+        if (hi && uint32_t(2 * j + 1) < w) red_add(g + 2 * j + 1, hi);
         cs[j] = kWordBias;
       }
     } else {
       for (int j = tid; j < n_pairs * int(w); j += T) {
         const int32_t v = int32_t(cs[j]);
-        if (v) atomicAdd(grow[j / int(w)] + (j % int(w)), v);
+        if (v) red_add(grow[j / int(w)] + (j % int(w)), v);
         cs[j] = 0;
       }
     }
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_hash(const __grid_co
                 if (POW2) h = (uint32_t(st[u].B) + geB) & (w - 1);  // -p = 1 (mod w)
                 else h = uint32_t((geB ? st[u].B - kP61 : st[u].B) % w);
                 if (PACK16) counter_add<true>(c, g, h, sg, w);
-                else atomicAdd(reinterpret_cast<int32_t*>(c) + h, sg);
+                else red_add_shared(reinterpret_cast<int32_t*>(c) + h, sg);
               }
               m[u] >>= 1;
               st[u].P = add_lazy(st[u].P, st[u].D1);

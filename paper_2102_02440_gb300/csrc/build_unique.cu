@@ -59,14 +59,14 @@ __global__ void __launch_bounds__(kUniqThreads, 2) k_uniq_hash(const __grid_cons
       for (int j = tid; j < words; j += T) {
         const uint32_t v = cs[j];
         const int32_t lo = int32_t(v & 0xFFFFu) - int32_t(kHalfBias), hi = int32_t(v >> 16) - int32_t(kHalfBias);
-        if (lo) atomicAdd(g + 2 * j, lo);
-        if (hi && uint32_t(2 * j + 1) < w) atomicAdd(g + 2 * j + 1, hi);
+        if (lo) red_add(g + 2 * j, lo);
+        if (hi && uint32_t(2 * j + 1) < w) red_add(g + 2 * j + 1, hi);
         cs[j] = kWordBias;
       }
     } else {
       for (int j = tid; j < n_pairs * int(w); j += T) {
         const int32_t v = int32_t(cs[j]);
-        if (v) atomicAdd(grow[j / int(w)] + (j % int(w)), v);
+        if (v) red_add(grow[j / int(w)] + (j % int(w)), v);
         cs[j] = 0;
       }
     }
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kUniqThreads, 2) k_uniq_hash(const __grid_cons
             int32_t* c = reinterpret_cast<int32_t*>(cs) + size_t(p) * w;
 #pragma unroll
             for (int q = 0; q < KPT; q++)
-              if (q < nv) atomicAdd(c + h[q], sg[q]);
+              if (q < nv) red_add_shared(c + h[q], sg[q]);
           }
         }
       };

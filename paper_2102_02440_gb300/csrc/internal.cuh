@@ -402,6 +402,18 @@ struct ZeroSpan {
 };
 constexpr uint64_t kBuildPlanMagic = 0x434d504255494c44ull;  // "CMPBUILD"
 
+// Fire-and-forget atomic additions (PTX red, relaxed): the same update as atomicAdd, with
+// no result register, so no instruction waits for the reply.
+__device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
+  asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_shared(int32_t* p, int32_t v) {
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(uint32_t(__cvta_generic_to_shared(p))), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_shared(uint32_t* p, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(uint32_t(__cvta_generic_to_shared(p))), "r"(v) : "memory");
+}
+
 // device status helper: first error wins
 __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
   if (status) atomicCAS(status, 0, code);

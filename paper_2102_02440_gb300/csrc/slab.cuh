@@ -24,8 +24,8 @@ __device__ __noinline__ void pack16_wrap(uint32_t* word, int32_t* g2, int dl, in
     const int cl = lo > 0xFFFF ? 1 : (lo < 0 ? -1 : 0);
     const int hi = int(old >> 16) + dh + cl;
     const int ch = hi > 0xFFFF ? 1 : (hi < 0 ? -1 : 0);
-    if (cl) atomicAdd(g2, cl * 65536);
-    if (ch && has_hi) atomicAdd(g2 + 1, ch * 65536);
+    if (cl) red_add(g2, cl * 65536);
+    if (ch && has_hi) red_add(g2 + 1, ch * 65536);
     if (!cl) return;
     dl = 0;  // the carry (cl) reached the high half: take it back
     dh = -cl;
@@ -44,7 +44,7 @@ __device__ __forceinline__ void counter_add(uint32_t* cs, int32_t* g, uint32_t h
     if ((((old >> sh) & 0xFFFFu) - 1u) >= 0xFFFEu)
       pack16_wrap(wd, g + (h & ~1u), odd ? 0 : sg, odd ? sg : 0, old, (h | 1u) < w);
   } else {
-    atomicAdd(reinterpret_cast<int32_t*>(cs) + h, sg);
+    red_add_shared(reinterpret_cast<int32_t*>(cs) + h, sg);
   }
 }
 

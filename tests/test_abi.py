@@ -533,3 +533,18 @@ def test_estimate_plan_sample_rates(K):
         rates[1] = bad
         with pytest.raises(K.CompassError):
             K.cmp_estimate_plan_bytes([g], 5, 64, [0], [0b111])
+
+
+def test_sorted_tables_rule():
+    """Host rule of the tables whose sorted rows an estimate plan reads: the lowest table id
+    of every multi-table sub-plan and every table joined to two or more others in one."""
+    from paper_2102_02440_gb300 import datagen as G
+    from paper_2102_02440_gb300 import pipeline as P
+    chain = ([0, 1, 2, 3], [1, 2, 3, 4])
+    assert P.sorted_tables(5, *chain, G.connected_subplans(5, *chain)) == {0, 1, 2, 3}
+    star = ([0, 0, 0, 0], [1, 2, 3, 4])
+    assert P.sorted_tables(5, *star, G.connected_subplans(5, *star)) == {0}
+    back = ([4, 4, 4, 4], [0, 1, 2, 3])  # the centre has the highest id
+    assert P.sorted_tables(5, *back, [0b10001, 0b10010]) == {0, 1}
+    assert P.sorted_tables(5, *back, [0b10011]) == {0, 4}
+    assert P.sorted_tables(5, *back, [0b00001, 0b10000]) == set()  # single tables read no sketch

@@ -107,3 +107,30 @@ def test_cuda_graph_capture_and_replay(batch):
     for a, t in zip(ref_c, gb.dw.tables):
         assert torch.equal(a, t.counters)
     assert torch.equal(ref_e, plan.est)
+
+
+def test_upload_from_host_then_build_equals_resident_build():
+    """DeviceWorkload.upload (host columns copied on several streams, the caller's stream
+    waiting for all of them) followed by the batched build gives the same counters and
+    survivor counts as the build over the columns the workload uploaded itself; the columns
+    are overwritten with zeros first so that a missed part would show."""
+    rng = np.random.default_rng(8)
+    wl = G.random_graph_workload(rng, 5, 1, 1_000, 300_000, 5000, d=3, w=512, pred_prob=0.5, hash_seed=8)
+    dw = P.DeviceWorkload(wl)
+    dw.build_batched()
+    torch.cuda.synchronize()
+    ref = [t.counters.clone() for t in dw.tables]
+    ref_surv = dw.survivors.clone()
+    host = [[c.cpu().pin_memory() for c in t.cols] for t in dw.tables]
+    for t in dw.tables:
+        for c in t.cols:
+            c.zero_()
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        for n_streams in (1, 3, 4):
+            dw.upload(host, n_streams=n_streams, stream=st)
+            dw.build_batched(stream=st)
+            st.synchronize()
+            for t, r in zip(dw.tables, ref):
+                assert torch.equal(t.counters, r)
+            assert torch.equal(dw.survivors, ref_surv)

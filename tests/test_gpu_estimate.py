@@ -87,9 +87,21 @@ def test_random_graphs_all_connected_subplans(orc, name, w):
     dw.build()
     masks = G.connected_subplans(nt, eu, ev)
     est = P.DeviceEstimator(dw, masks)
+    # the plan reads only the sorted rows of P.sorted_tables: the others' presort and cross-rank
+    # buffers hold zeros (in-bounds, wrong) and must not change a row
+    for buf in (dw.abs_all, dw.perm_all, dw.ranks_all):
+        buf.zero_()
+    assert len(est.sorted_tables()) < nt or name in ("triangle", "parallel", "cycle4+tail")
     est.presort()
     est.estimate()
     _check(orc, dw, est, masks, brute=(w == 3 and len(eu) <= 5))
+    pairs = [m for m in masks if bin(m).count("1") <= 2]  # roots of the two-table sub-plans only
+    est2 = P.DeviceEstimator(dw, pairs)
+    for buf in (dw.abs_all, dw.perm_all, dw.ranks_all):
+        buf.zero_()
+    est2.presort()
+    est2.estimate()
+    _check(orc, dw, est2, pairs)
 
 
 @pytest.mark.parametrize("shape", [dict(threads=256, ctas_per_sm=4), dict(threads=256, ctas_per_sm=4, cond_chunk=16),
@@ -194,6 +206,42 @@ def test_rejections():
     dw2 = P.DeviceWorkload(wl2)
     dw2.build()
     P.DeviceEstimator(dw2, [0b111])          # one cycle: supported
+
+
+def test_cross_ranks_multi_windows_at_full_width():
+    """w = 65536: many 2048-position segments per row.  A sketch of widely spread magnitudes
+    against one of magnitudes 0..3 (many ties): some segments' windows in the other row are
+    empty, some hold most of the row (beyond the shared-memory window: the searches read the
+    row in global memory).  Every rank equals the definition (np.searchsorted, ties broken
+    by edge id) and the per-table kernel's."""
+    rng = np.random.default_rng(21)
+    d, w = 2, 65536
+    C = np.stack([rng.integers(-30000, 30001, size=(d, w)), rng.integers(-3, 4, size=(d, w))]).astype(np.int32)
+    Cd = torch.from_numpy(C).cuda()
+    a = torch.empty_like(Cd)
+    p = torch.empty_like(Cd)
+    need = K.cmp_presort_ws_bytes(2 * d, w)
+    ws = torch.empty(max(need, 16), dtype=torch.uint8, device="cuda")
+    K.cmp_presort(Cd.data_ptr(), 2 * d, w, a.data_ptr(), p.data_ptr(), ws.data_ptr(), need, K.stream_handle())
+    edges = [5, 2]
+    multi = torch.full((4, d, w), -7, dtype=torch.int32, device="cuda")
+    K.cmp_cross_ranks_multi(a.data_ptr(), p.data_ptr(), [2], edges, d, w, multi.data_ptr(), K.stream_handle())
+    one = torch.full((4, d, w), -9, dtype=torch.int32, device="cuda")
+    K.cmp_cross_ranks(a.data_ptr(), p.data_ptr(), 2, d, w, edges, one.data_ptr(), K.stream_handle())
+    torch.cuda.synchronize()
+    assert torch.equal(one, multi)
+    A = a.cpu().numpy().view(np.uint32).reshape(2, d, w)
+    R = multi.cpu().numpy().reshape(2, 2, d, w)
+    for x in range(2):
+        for y in range(2):
+            for i in range(d):
+                if x == y:
+                    inv = np.empty(w, np.int64)
+                    inv[p.cpu().numpy()[x, i]] = np.arange(w)
+                    assert np.array_equal(R[x, y, i], inv)
+                else:
+                    side = "right" if edges[y] < edges[x] else "left"
+                    assert np.array_equal(R[x, y, i], np.searchsorted(A[y, i], A[x, i], side=side))
 
 
 def test_cross_ranks_multi_equals_per_table():
