@@ -280,6 +280,8 @@ struct BuildPlanParts {
   std::vector<CountItem> cnt_items;
   int64_t cnt_total_chunks = 0;
   int32_t cnt_grid = 0;
+  int64_t cnt_split = 0;  // > 0: two launches, the tables with presence columns first
+  int32_t cnt_grid_b = 0;
   int64_t hash_total_chunks = 0;
   int32_t hash_max_pairs = 1, hash_grid = 0;
   std::vector<std::vector<int32_t>> col_agg;  // [table][col] AggCol index or -1
@@ -322,7 +324,7 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
   P->surv_by.assign(n_tables, kSurvRow);
   P->col_agg.assign(n_tables, std::vector<int32_t>(CMP_MAX_COLS, -1));
   P->aggs.clear();
-  size_t ws = al256(16 * size_t(n_tables) * CMP_MAX_SKETCHES + 16);  // stats + chunk counters (upper bound)
+  size_t ws = al256(16 * size_t(n_tables) * CMP_MAX_SKETCHES + 32);  // stats + chunk counters (upper bound)
   for (int32_t t = 0; t < n_tables; t++) {
     const cmp_table& tb = tables[t];
     const bool agg_on = tb.n_sketches > 0 && tb.n_rows > 0 && s.dedupe &&
@@ -604,12 +606,21 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
   // tables (a CTA's chunk hand-over is a block barrier and an atomic, so chunks are kept
   // long), at most 64 tiles; a persistent grid of about one resident wave takes the chunks
   // in order
+  // (tables with a presence column first, so that a split pass completes every bitmap in its
+  // first launch)
   P->cnt_items.clear();
   P->cnt_total_chunks = 0;
+  auto has_presence = [&](int32_t t) {
+    for (int32_t c = 0; c < CMP_MAX_COLS; c++)
+      if (P->col_agg[t][c] >= 0 && P->aggs[P->col_agg[t][c]].kind == kAggPresence) return true;
+    return false;
+  };
+  int64_t presence_chunks = 0;
+  for (int pass = 0; pass < 2; pass++)
   for (int32_t t = 0; t < n_tables; t++) {
     int ncol = 0;
     for (int32_t c = 0; c < CMP_MAX_COLS; c++) ncol += P->col_agg[t][c] >= 0;
-    if (!ncol) continue;
+    if (!ncol || has_presence(t) != (pass == 0)) continue;
     CountItem ci;
     ci.table = t;
     ci.pad = 0;
@@ -619,6 +630,7 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
     ci.chunk_begin = P->cnt_total_chunks;
     ci.n_chunks = (tables[t].n_rows + ci.chunk_rows - 1) / ci.chunk_rows;
     P->cnt_total_chunks += ci.n_chunks;
+    if (pass == 0) presence_chunks += ci.n_chunks;
     P->cnt_items.push_back(ci);
   }
   P->cnt_grid = 0;  // set below, once the unique-key items are known
@@ -640,6 +652,16 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
   // counting pass: 512-thread CTAs, two per SM; one per SM when the unique-key kernel runs
   // beside it
   P->cnt_grid = int32_t(std::min<int64_t>(P->cnt_total_chunks, int64_t(sm_count()) * (P->uitems.empty() ? 2 : 1)));
+  // split pass: when presence bitmaps and other counted tables are both present (and no
+  // unique-key kernel wants the place beside the counting pass), the bitmaps are counted
+  // first, then the rest with one CTA per SM and the dense kernel beside it
+  P->cnt_split = 0;
+  P->cnt_grid_b = 0;
+  if (!P->ditems.empty() && P->uitems.empty() && presence_chunks > 0 && presence_chunks < P->cnt_total_chunks) {
+    P->cnt_split = presence_chunks;
+    P->cnt_grid = int32_t(std::min<int64_t>(presence_chunks, int64_t(sm_count()) * 2));
+    P->cnt_grid_b = int32_t(std::min<int64_t>(P->cnt_total_chunks - presence_chunks, int64_t(sm_count())));
+  }
   s.grid = int32_t(P->cta_item.size());
   s.ctas_per_slab = 0;
   P->shape = s;
@@ -736,6 +758,8 @@ extern "C" cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_t
   h.u_tile_rows = kUniqTileRows;
   h.cnt_total_chunks = P.cnt_total_chunks;
   h.cnt_grid = P.cnt_grid;
+  h.cnt_split = P.cnt_split;
+  h.cnt_grid_b = P.cnt_grid_b;
   h.cnt_threads = 512;
   h.cnt_cache_slots = P.cache_slots;
   h.cnt_cache_cols = P.cache_cols;
@@ -820,18 +844,34 @@ extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void
     a.cnt_cache_cols = h.cnt_cache_cols;
     // the (max, min) key ranges start from zero (decoding as an empty column), so do the
     // chunk counters of the counting and hashing passes after them
-    if (cudaMemsetAsync(ws_dev, 0, 16 * size_t(h.n_agg) + 16, cs) != cudaSuccess) return CMP_ECUDA;
-    if (launch_agg(a, h.shape.tile_rows, h.cnt_threads, h.cnt_grid, cs) != cudaSuccess) return CMP_ECUDA;
+    if (cudaMemsetAsync(ws_dev, 0, 16 * size_t(h.n_agg) + 24, cs) != cudaSuccess) return CMP_ECUDA;
+    if (launch_agg_zero(a, cs) != cudaSuccess) return CMP_ECUDA;
   }
+  const int32_t hash_grid = h.n_agg > 0 ? h.hash_grid : 0;
+  const int32_t d_grid = h.n_ditems > 0 ? h.d_grid : 0;
+  if (h.cnt_split > 0) {
+    // the tables with presence columns, then the others with the dense kernel beside them
+    // (its programmatic dependent: one CTA of each per SM, a memory-bound scan beside an
+    // integer-bound walk; every bitmap is complete before the second launch starts)
+    if (launch_agg_count(a, h.shape.tile_rows, h.cnt_threads, h.cnt_grid, 0, 0, h.cnt_split, cs) != cudaSuccess ||
+        launch_agg_count(a, h.shape.tile_rows, h.cnt_threads, h.cnt_grid_b, 2, h.cnt_split, h.cnt_total_chunks, cs) !=
+            cudaSuccess ||
+        launch_dense(a, d_grid, true, kDenseThreadsBeside, cs) != cudaSuccess)
+      return CMP_ECUDA;
+    if (h.shape.grid > 0 && launch_build(a, h.shape, cs) != cudaSuccess) return CMP_ECUDA;
+    return launch_agg_hash(a, hash_grid, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
+  }
+  if (h.n_agg > 0 &&
+      launch_agg_count(a, h.shape.tile_rows, h.cnt_threads, h.cnt_grid, 0, 0, h.cnt_total_chunks, cs) != cudaSuccess)
+    return CMP_ECUDA;
   // the unique-key kernel right after the counting pass, as its programmatic dependent:
   // one CTA of each per SM, the two overlap (memory-bound scan, integer-bound hashing)
   if (launch_uniq(a, h.u_grid, kUniqThreadsHost, h.u_tile_rows, cs) != cudaSuccess) return CMP_ECUDA;
   if (h.shape.grid > 0 && launch_build(a, h.shape, cs) != cudaSuccess) return CMP_ECUDA;
-  const int32_t hash_grid = h.n_agg > 0 ? h.hash_grid : 0;
   if (launch_agg_hash(a, hash_grid, cs) != cudaSuccess) return CMP_ECUDA;
   // the presence-bitmap columns, beside the hashing of the counted keys when there is one
   // (as its programmatic dependent: both only read what the counting pass wrote)
-  return launch_dense(a, h.n_ditems > 0 ? h.d_grid : 0, hash_grid > 0, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
+  return launch_dense(a, d_grid, hash_grid > 0, kDenseThreadsAlone, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
 }
 
 
@@ -850,7 +890,7 @@ extern "C" cmp_status cmp_build_plan_stats(const void* plan_host, cmp_build_plan
   // zeroing; clearing (+ counting when it has chunks) and hashing of the counted keys; the
   // unique-key kernel; the row kernel
   // unique-key kernel; the row kernel; the dense kernel
-  info->launches = 1 + (h.n_agg > 0 ? 1 + (h.cnt_grid > 0 ? 1 : 0) + (h.hash_grid > 0 ? 1 : 0) : 0) +
+  info->launches = 1 + (h.n_agg > 0 ? 1 + (h.cnt_grid > 0 ? 1 : 0) + (h.cnt_split > 0 ? 1 : 0) + (h.hash_grid > 0 ? 1 : 0) : 0) +
                    (h.n_uitems > 0 && h.u_grid > 0 ? 1 : 0) + (h.shape.grid > 0 ? 1 : 0) +
                    (h.n_ditems > 0 && h.d_grid > 0 ? 1 : 0);
   info->n_presence = h.n_presence;

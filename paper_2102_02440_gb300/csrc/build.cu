@@ -390,7 +390,8 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
   sp += align16(sizeof(uint16_t) * agg_count_surv_entries(R, T));
   int32_t* sint = reinterpret_cast<int32_t*>(sp);
   constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // never a slot index: cap <= 2^31 - 1
-  unsigned long long* work = reinterpret_cast<unsigned long long*>(A.ws) + 2 * int64_t(A.n_agg);
+  // this launch's chunk counter: slot 0 (the only launch, or the first of two), 2 (the second)
+  unsigned long long* work = reinterpret_cast<unsigned long long*>(A.ws) + 2 * int64_t(A.n_agg) + A.cnt_work_slot;
 
   // One surviving key of column a.  Returns false when the key lies outside the column's
   // declared domain (its counts are then discarded: the column keeps the per-row path).
@@ -439,8 +440,7 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
       atomicMax(&amin[a], (unsigned long long)enc_min(mn));
     }
   };
-  // A counted column's parameters in registers (warp path), and its count of one key: the
-  // same steps as count_key for a count array.
+  // A counted column's parameters in registers (warp path).
   struct CntCol {
     int32_t* cnt;
     uint32_t* ckey;  // its cache (nullptr: not cached)
@@ -458,14 +458,6 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
     cc.mask = amask[a];
     cc.declared = amask[a] == ~0ull;
     return cc;
-  };
-  auto count_fast = [&](const CntCol& cc, int64_t key) {
-    const uint64_t off = uint64_t(key) - cc.base;
-    if (cc.declared && off >= cc.cap) return false;
-    const uint32_t x = uint32_t(off & cc.mask);
-    if (cc.ckey && cache_count(cc.ckey, cc.ccnt, x)) return true;
-    red_add(cc.cnt + x, 1);
-    return true;
   };
   // adds the caches and key ranges of the current table to the global arrays (block-wide)
   auto flush = [&]() {
@@ -494,10 +486,10 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
   // shared memory are held for data in flight.
   int item = -1;  // block-uniform
   for (;;) {
-    if (tid == 0) next_chunk = (long long)atomicAdd(work, 1ull);
+    if (tid == 0) next_chunk = A.cnt_chunk_begin + (long long)atomicAdd(work, 1ull);
     __syncthreads();
     const int64_t c = next_chunk;
-    if (c >= A.cnt_total_chunks) break;  // block-uniform
+    if (c >= A.cnt_chunk_end) break;  // block-uniform
     const int it = item_of(c);
     const CountItem ci = A.cnt_items[it];
     const DevTable* tb = A.tables + ci.table;
@@ -934,21 +926,30 @@ size_t agg_count_smem_bytes(int32_t tile_rows, int32_t cache_slots, int32_t cach
          align16(sizeof(uint16_t) * agg_count_surv_entries(tile_rows, threads)) + sizeof(int32_t) * 40;
 }
 
-cudaError_t launch_agg(const BuildArgs& a, int32_t tile_rows, int32_t cnt_threads, int32_t cnt_grid,
-                       cudaStream_t st) {
+cudaError_t launch_agg_zero(const BuildArgs& a, cudaStream_t st) {
   if (a.n_agg <= 0) return cudaSuccess;
   const dim3 g(unsigned(std::max(1, 8 * sm_count() / std::max(1, a.n_agg))), unsigned(a.n_agg));
   k_agg_zero<<<g, 256, 0, st>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || cnt_grid <= 0) return e;
+  return cudaGetLastError();
+}
+
+// One launch of the counting pass over chunks [chunk_begin, chunk_end), taken from chunk
+// counter `work_slot` of the workspace header (zeroed before the build).
+cudaError_t launch_agg_count(const BuildArgs& a, int32_t tile_rows, int32_t cnt_threads, int32_t cnt_grid,
+                             int32_t work_slot, int64_t chunk_begin, int64_t chunk_end, cudaStream_t st) {
+  if (a.n_agg <= 0 || cnt_grid <= 0 || chunk_end <= chunk_begin) return cudaSuccess;
   const size_t smem = agg_count_smem_bytes(tile_rows, a.cnt_cache_slots, a.cnt_cache_cols, cnt_threads);
-  e = cudaFuncSetAttribute(k_agg_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t e = cudaFuncSetAttribute(k_agg_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  // the whole shared memory of the SM, so that a CTA of the unique-key kernel (launched
-  // next, as a programmatic dependent) fits beside one of this pass
+  // the whole shared memory of the SM, so that a CTA of the unique-key or the dense kernel
+  // (launched next, as a programmatic dependent) fits beside one of this pass
   e = cudaFuncSetAttribute(k_agg_count, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  k_agg_count<<<unsigned(cnt_grid), cnt_threads, smem, st>>>(a);
+  BuildArgs b = a;
+  b.cnt_work_slot = work_slot;
+  b.cnt_chunk_begin = chunk_begin;
+  b.cnt_chunk_end = chunk_end;
+  k_agg_count<<<unsigned(cnt_grid), cnt_threads, smem, st>>>(b);
   return cudaGetLastError();
 }
 

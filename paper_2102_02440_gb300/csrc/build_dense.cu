@@ -32,7 +32,6 @@ namespace cmpk {
 
 namespace {
 
-constexpr int kDenseThreads = 512;
 constexpr int kRunWords = int(kDenseRun / 32);
 constexpr int kRuns = 2;  // runs per thread in flight: independent difference chains
 
@@ -72,8 +71,9 @@ __device__ __forceinline__ Diff diff_at(const PairParam& q, uint64_t x0, uint64_
 
 size_t dense_smem_bytes(int32_t words) { return align16(sizeof(uint32_t) * size_t(words)); }
 
-template <bool PACK16, bool POW2>
-__global__ void __launch_bounds__(kDenseThreads, 1) k_dense_hash(const __grid_constant__ BuildArgs A) {
+// THREADS: 512 alone on the SM, 256 beside a CTA of the counting pass (128 registers each)
+template <bool PACK16, bool POW2, int THREADS>
+__global__ void __launch_bounds__(THREADS, 512 / THREADS) k_dense_hash(const __grid_constant__ BuildArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ PairParam prm[kUniqMaxPairs];
   __shared__ int32_t* grow[kUniqMaxPairs];
@@ -208,20 +208,23 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_hash(const __grid_co
     }
   }
   if (cur >= 0 && s_active) flush();
-  // Launched as a programmatic dependent of the hashing of the counted keys: finish only
-  // after it has, so that the stream's later work also finds it complete.
+  // Launched as a programmatic dependent (of the hashing of the counted keys, or of the
+  // second launch of a split counting pass): finish only after it has, so that the stream's
+  // later work also finds it complete.
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-template <bool PK, bool P2>
+template <bool PK, bool P2, int TH>
 static cudaError_t launch_dense_t(const BuildArgs& a, int32_t grid, bool pdl, cudaStream_t st) {
-  auto k = k_dense_hash<PK, P2>;
+  auto k = k_dense_hash<PK, P2, TH>;
   const size_t smem = dense_smem_bytes(a.d_words);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(grid));
-  cfg.blockDim = dim3(unsigned(kDenseThreads));
+  cfg.blockDim = dim3(unsigned(TH));
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -233,14 +236,22 @@ static cudaError_t launch_dense_t(const BuildArgs& a, int32_t grid, bool pdl, cu
 }
 
 // pdl: launch as a programmatic dependent of the previous kernel on the stream, which must
-// then be the hashing of the counted keys (it lets dependents start once it runs, and it
-// starts only after the counting pass has completed); otherwise an ordinary launch.
-cudaError_t launch_dense(const BuildArgs& a, int32_t grid, bool pdl, cudaStream_t st) {
+// let dependents start only once every presence bitmap is complete: the hashing of the
+// counted keys (it starts after the whole counting pass), or the second launch of a split
+// counting pass (it starts after the first, which counts every table with a presence
+// column).  Otherwise an ordinary launch.  threads: kDenseThreadsAlone or
+// kDenseThreadsBeside.
+cudaError_t launch_dense(const BuildArgs& a, int32_t grid, bool pdl, int32_t threads, cudaStream_t st) {
   if (a.n_ditems <= 0 || grid <= 0) return cudaSuccess;
   const bool pow2 = (a.w & (a.w - 1)) == 0;
+  if (threads == kDenseThreadsBeside) {
+    if (a.d_pack16)
+      return pow2 ? launch_dense_t<true, true, 256>(a, grid, pdl, st) : launch_dense_t<true, false, 256>(a, grid, pdl, st);
+    return pow2 ? launch_dense_t<false, true, 256>(a, grid, pdl, st) : launch_dense_t<false, false, 256>(a, grid, pdl, st);
+  }
   if (a.d_pack16)
-    return pow2 ? launch_dense_t<true, true>(a, grid, pdl, st) : launch_dense_t<true, false>(a, grid, pdl, st);
-  return pow2 ? launch_dense_t<false, true>(a, grid, pdl, st) : launch_dense_t<false, false>(a, grid, pdl, st);
+    return pow2 ? launch_dense_t<true, true, 512>(a, grid, pdl, st) : launch_dense_t<true, false, 512>(a, grid, pdl, st);
+  return pow2 ? launch_dense_t<false, true, 512>(a, grid, pdl, st) : launch_dense_t<false, false, 512>(a, grid, pdl, st);
 }
 
 }  // namespace cmpk

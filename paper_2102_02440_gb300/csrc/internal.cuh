@@ -356,6 +356,8 @@ struct BuildArgs {
   unsigned char* ws;
   const CountItem* cnt_items;
   int32_t n_cnt_items;
+  int32_t cnt_work_slot;                      // chunk counter of this launch of the counting pass
+  int64_t cnt_chunk_begin, cnt_chunk_end;     // its chunks
   int32_t cnt_cache_slots, cnt_cache_cols;  // counting pass: hot-key cache slots per column, columns cached
   int64_t cnt_total_chunks;
   int64_t hash_total_chunks;  // hashing pass of the aggregated columns
@@ -394,8 +396,12 @@ struct BuildPlanHdr {
   int32_t u_grid, u_pack16, u_words, u_tile_rows;
   int64_t n_dslab, off_dslab, n_ditems, off_ditems, off_d_cta;  // dense kernel
   int32_t d_grid, d_pack16, d_words, n_presence;
+  // counting pass in two launches (cnt_split > 0): chunks [0, cnt_split) of the tables with
+  // presence columns first, then [cnt_split, total) with the dense kernel beside it
+  int64_t cnt_split;
+  int32_t cnt_grid_b, d_grid_split;
 };
-constexpr int32_t kBuildPlanVersion = 8;
+constexpr int32_t kBuildPlanVersion = 9;
 struct ZeroSpan {
   void* ptr;
   int64_t bytes;
@@ -425,13 +431,16 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 size_t build_smem_bytes(const BuildShape& s, int w);
 cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t st);
 size_t agg_count_smem_bytes(int32_t tile_rows, int32_t cache_slots, int32_t cache_cols, int32_t threads);
-cudaError_t launch_agg(const BuildArgs& a, int32_t tile_rows, int32_t cnt_threads, int32_t cnt_grid, cudaStream_t st);
+cudaError_t launch_agg_zero(const BuildArgs& a, cudaStream_t st);
+cudaError_t launch_agg_count(const BuildArgs& a, int32_t tile_rows, int32_t cnt_threads, int32_t cnt_grid,
+                             int32_t work_slot, int64_t chunk_begin, int64_t chunk_end, cudaStream_t st);
 size_t uniq_smem_bytes(int32_t words, int32_t tile_rows);
 cudaError_t launch_uniq(const BuildArgs& a, int32_t grid, int32_t threads, int32_t tile_rows, cudaStream_t st);
 cudaError_t launch_zero_spans(const ZeroSpan* spans_dev, int32_t n, cudaStream_t st);
 cudaError_t launch_agg_hash(const BuildArgs& a, int32_t grid, cudaStream_t st);
 size_t dense_smem_bytes(int32_t words);
-cudaError_t launch_dense(const BuildArgs& a, int32_t grid, bool pdl, cudaStream_t st);
+cudaError_t launch_dense(const BuildArgs& a, int32_t grid, bool pdl, int32_t threads, cudaStream_t st);
+constexpr int32_t kDenseThreadsAlone = 512, kDenseThreadsBeside = 256;
 
 int sm_count();
 size_t smem_optin_bytes();

@@ -134,3 +134,24 @@ def test_dense_beside_counted_and_unique_columns(orc):
         assert P.build_plan_info(off)["n_presence"] == 0
         for x, y in zip(dw.tables, off.tables):
             assert torch.equal(x.counters, y.counters)
+
+
+@pytest.mark.parametrize("w", [1024, 65536])
+def test_dense_beside_the_second_counting_launch(orc, w):
+    """Presence columns and counted columns without a unique-key kernel: the counting pass
+    runs in two launches (the presence tables first), the dense kernel beside the second
+    one (256 threads, one CTA per SM).  Counters equal the oracle's; the plan has one more
+    launch than the single pass."""
+    rng = np.random.default_rng(w + 5)
+    n = 300_000
+    pk = rng.permutation(n).astype(np.int64)
+    fk = G.zipf_keys(rng, 2_000_000, n, 1.2).astype(np.int64)
+    p = rng.integers(0, 1000, 2_000_000).astype(np.int32)
+    tabs = [G.Table("D", [pk], [], [0], [0], [("unique", 0, n)]),
+            G.Table("F", [fk, p], [G.Pred(1, G.RANGE, 0, 300)], [0], [0], [("domain", 0, n), None])]
+    wl = G.Workload("split", tabs, [0], [1], 4, w, 31, 2)
+    dw = _build(wl)
+    info = P.build_plan_info(dw)
+    assert info["n_presence"] == 1 and info["n_unique_slabs"] == 0
+    assert info["launches"] == 7  # zeroing, clearing, two counting launches, dense, row kernel, hashing
+    _check(orc, wl, dw)
