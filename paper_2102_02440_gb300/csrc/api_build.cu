@@ -379,7 +379,7 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
   for (AggCol& a : P->aggs) {
     a.off = int64_t(ws);
     // whole int4 words: the zeroing kernel writes them
-    ws += a.kind == kAggPresence ? al256(sizeof(uint32_t) * size_t(presence_words(a.cap)))
+    ws += a.kind == kAggPresence ? al256(sizeof(uint32_t) * size_t(presence_words(a.cap)) + sizeof(PresenceCheck))
                                  : al256(16 * size_t((a.cap + 3) / 4));
   }
   P->ws_bytes = P->aggs.empty() ? 0 : ws;
@@ -854,6 +854,7 @@ extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void
     // (its programmatic dependent: one CTA of each per SM, a memory-bound scan beside an
     // integer-bound walk; every bitmap is complete before the second launch starts)
     if (launch_agg_count(a, h.shape.tile_rows, h.cnt_threads, h.cnt_grid, 0, 0, h.cnt_split, cs) != cudaSuccess ||
+        launch_presence_check(a, cs) != cudaSuccess ||
         launch_agg_count(a, h.shape.tile_rows, h.cnt_threads, h.cnt_grid_b, 2, h.cnt_split, h.cnt_total_chunks, cs) !=
             cudaSuccess ||
         launch_dense(a, d_grid, true, kDenseThreadsBeside, cs) != cudaSuccess)
@@ -867,6 +868,7 @@ extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void
   // the unique-key kernel right after the counting pass, as its programmatic dependent:
   // one CTA of each per SM, the two overlap (memory-bound scan, integer-bound hashing)
   if (launch_uniq(a, h.u_grid, kUniqThreadsHost, h.u_tile_rows, cs) != cudaSuccess) return CMP_ECUDA;
+  if (launch_presence_check(a, cs) != cudaSuccess) return CMP_ECUDA;
   if (h.shape.grid > 0 && launch_build(a, h.shape, cs) != cudaSuccess) return CMP_ECUDA;
   if (launch_agg_hash(a, hash_grid, cs) != cudaSuccess) return CMP_ECUDA;
   // the presence-bitmap columns, beside the hashing of the counted keys when there is one
@@ -889,10 +891,10 @@ extern "C" cmp_status cmp_build_plan_stats(const void* plan_host, cmp_build_plan
   info->ws_bytes = h.ws_bytes;
   // zeroing; clearing (+ counting when it has chunks) and hashing of the counted keys; the
   // unique-key kernel; the row kernel
-  // unique-key kernel; the row kernel; the dense kernel
+  // unique-key kernel; the row kernel; the presence check and the dense kernel
   info->launches = 1 + (h.n_agg > 0 ? 1 + (h.cnt_grid > 0 ? 1 : 0) + (h.cnt_split > 0 ? 1 : 0) + (h.hash_grid > 0 ? 1 : 0) : 0) +
                    (h.n_uitems > 0 && h.u_grid > 0 ? 1 : 0) + (h.shape.grid > 0 ? 1 : 0) +
-                   (h.n_ditems > 0 && h.d_grid > 0 ? 1 : 0);
+                   (h.n_ditems > 0 && h.d_grid > 0 ? 2 : 0);  // the presence check and the dense kernel
   info->n_presence = h.n_presence;
   return CMP_OK;
 }

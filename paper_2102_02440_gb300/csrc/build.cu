@@ -345,7 +345,8 @@ cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t s
 __global__ void __launch_bounds__(256) k_agg_zero(const __grid_constant__ BuildArgs A) {
   const AggCol ac = A.agg[blockIdx.y];
   int4* c4 = reinterpret_cast<int4*>(A.ws + ac.off);
-  const int64_t n4 = ac.kind == kAggPresence ? presence_words(ac.cap) / 4 : (ac.cap + 3) / 4;
+  // (a presence bitmap: its whole runs, then the int4 holding its PresenceCheck)
+  const int64_t n4 = ac.kind == kAggPresence ? presence_words(ac.cap) / 4 + 1 : (ac.cap + 3) / 4;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x)
     c4[i] = make_int4(0, 0, 0, 0);
 }
@@ -419,9 +420,9 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
   auto count_key = [&](int a, int64_t key) {
     const uint64_t off = uint64_t(key) - uint64_t(abase[a]);
     if (amask[a] == ~0ull && off >= uint64_t(acap[a])) return false;
-    if (akind[a] == kAggPresence) {  // off < cap <= 2^32
-      const uint32_t bit = 1u << (off & 31);
-      return (atomicOr(reinterpret_cast<uint32_t*>(acnt[a]) + (off >> 5), bit) & bit) == 0;
+    if (akind[a] == kAggPresence) {  // off < cap <= 2^32; repeated keys are found by k_presence_check
+      red_or(reinterpret_cast<uint32_t*>(acnt[a]) + (off >> 5), 1u << (off & 31));
+      return true;
     }
     const uint32_t x = uint32_t(off & amask[a]);  // < cap
     if (a < n_cache && cache_count(ckey + size_t(a) * H, ccnt + size_t(a) * H, x)) return true;
@@ -788,7 +789,9 @@ __global__ void __launch_bounds__(512, 2) k_agg_count(const __grid_constant__ Bu
 // buffer and hashes 64 of them, two per lane, whenever it holds 64.
 constexpr int kHashThreads = 512;
 
-constexpr int kHashBuf = 96;  // entries buffered per warp: 64 hashed at a time, 31 carried over
+constexpr int kHashPer = 2;                    // entries per lane and batch: independent hash chains
+constexpr int kHashBatch = 32 * kHashPer;        // entries hashed at a time by a warp
+constexpr int kHashBuf = kHashBatch + 32;        // entries buffered per warp (31 carried over)
 
 size_t agg_hash_smem_bytes(int32_t max_pairs) {
   return align16(sizeof(PairParam) * size_t(max_pairs)) + align16(sizeof(int32_t*) * size_t(max_pairs)) +
@@ -860,24 +863,33 @@ __global__ void __launch_bounds__(kHashThreads) k_agg_hash(const __grid_constant
       const int np = n_pairs;
       const int64_t per = kHashChunk / nw;  // a multiple of 32
       const int64_t ws0 = min(range, s0 + warp * per), ws1 = min(range, ws0 + per);
-      // entries j0 and j1 of the warp's buffer (a negative index: nothing), two independent
-      // hash chains per lane sharing every parameter load
-      auto hash_batch = [&](int j0, int j1) {
-        const uint64_t x0 = j0 >= 0 ? bkey[j0] : 0, x1 = j1 >= 0 ? bkey[j1] : 0;
-        const int32_t m0 = j0 >= 0 ? bcnt[j0] : 0, m1 = j1 >= 0 ? bcnt[j1] : 0;
-        const KeyPow k0 = key_powers(x0), k1 = key_powers(x1);
+      // the first n entries of the warp's buffer, lane l taking l, l + 32, ...: kHashPer
+      // independent hash chains per lane sharing every parameter load
+      auto hash_batch = [&](int n) {
+        KeyPow k[kHashPer];
+        int32_t m[kHashPer];
+        uint32_t hi_or = 0;
+#pragma unroll
+        for (int e = 0; e < kHashPer; e++) {
+          const int j = lane + 32 * e;
+          m[e] = j < n ? bcnt[j] : 0;
+          k[e] = key_powers(j < n ? bkey[j] : 0);
+          hi_or |= k[e].x.hi;
+        }
         auto run = [&](auto smallx) {
           constexpr bool SX = decltype(smallx)::value;
           for (int p = 0; p < np; p++) {
             const PairParam q = prm[p];
             int32_t* row = prow[p];
-            const uint32_t h0 = cw_bucket<POW2, SX>(q, k0, w), h1 = cw_bucket<POW2, SX>(q, k1, w);
-            const int32_t v0 = cw_sign<SX>(q, k0) * m0, v1 = cw_sign<SX>(q, k1) * m1;
-            if (m0) red_add(row + h0, v0);
-            if (m1) red_add(row + h1, v1);
+#pragma unroll
+            for (int e = 0; e < kHashPer; e++) {
+              const uint32_t h = cw_bucket<POW2, SX>(q, k[e], w);
+              const int32_t v = cw_sign<SX>(q, k[e]) * m[e];
+              if (m[e]) red_add(row + h, v);
+            }
           }
         };
-        if (__all_sync(0xffffffffu, (k0.x.hi | k1.x.hi) == 0)) run(std::true_type{});
+        if (__all_sync(0xffffffffu, hi_or == 0)) run(std::true_type{});
         else run(std::false_type{});
       };
       int nb = 0;  // warp-uniform
@@ -892,18 +904,18 @@ __global__ void __launch_bounds__(kHashThreads) k_agg_hash(const __grid_constant
         }
         nb += __popc(nz);
         __syncwarp();
-        if (nb >= 64) {
-          hash_batch(lane, 32 + lane);
+        if (nb >= kHashBatch) {
+          hash_batch(kHashBatch);
           __syncwarp();
-          if (lane < nb - 64) {  // keep the overflow at the front
-            bkey[lane] = bkey[64 + lane];
-            bcnt[lane] = bcnt[64 + lane];
+          if (lane < nb - kHashBatch) {  // keep the overflow at the front
+            bkey[lane] = bkey[kHashBatch + lane];
+            bcnt[lane] = bcnt[kHashBatch + lane];
           }
-          nb -= 64;
+          nb -= kHashBatch;
           __syncwarp();
         }
       }
-      if (nb > 0) hash_batch(lane < nb ? lane : -1, 32 + lane < nb ? 32 + lane : -1);
+      if (nb > 0) hash_batch(nb);
     }
     __syncthreads();  // next_chunk and the parameters are rewritten next
   }
@@ -924,6 +936,50 @@ cudaError_t launch_agg_hash(const BuildArgs& a, int32_t grid, cudaStream_t st) {
 size_t agg_count_smem_bytes(int32_t tile_rows, int32_t cache_slots, int32_t cache_cols, int32_t threads) {
   return align16(sizeof(uint32_t) * 2 * size_t(cache_slots) * size_t(cache_cols)) +
          align16(sizeof(uint16_t) * agg_count_surv_entries(tile_rows, threads)) + sizeof(int32_t) * 40;
+}
+
+// After the counting pass: a presence column is valid only if its bitmap holds as many set
+// bits as its table has rows (the table has no predicates: every row survives); fewer bits
+// mean a key was seen twice, and the column's key range is then set to the whole int64
+// range, so that agg_active turns it down.  Each CTA adds the set bits of its part of the
+// bitmap; the CTA that finishes last (ticket) compares.  Grid: (CTAs per column, columns).
+__global__ void __launch_bounds__(256) k_presence_check(const __grid_constant__ BuildArgs A) {
+  __shared__ unsigned long long part[8];
+  __shared__ bool last;
+  const AggCol ac = A.agg[blockIdx.y];
+  if (ac.kind != kAggPresence) return;  // block-uniform
+  const int64_t words = presence_words(ac.cap);
+  const uint32_t* bm = reinterpret_cast<const uint32_t*>(A.ws + ac.off);
+  PresenceCheck* pc = reinterpret_cast<PresenceCheck*>(A.ws + ac.off + 4 * words);
+  unsigned long long n = 0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < words; i += int64_t(gridDim.x) * blockDim.x)
+    n += __popc(__ldg(bm + i));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int wi = 0; wi < int(blockDim.x >> 5); wi++) t += part[wi];
+    atomicAdd(&pc->bits, t);
+    __threadfence();  // this CTA's total before its ticket
+    last = atomicAdd(&pc->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  const unsigned long long total = *reinterpret_cast<volatile unsigned long long*>(&pc->bits);
+  if (total != (unsigned long long)A.tables[ac.table].n_rows) {
+    unsigned long long* st = reinterpret_cast<unsigned long long*>(A.ws) + 2 * int64_t(blockIdx.y);
+    atomicMax(st, (unsigned long long)enc_max(INT64_MAX));
+    atomicMax(st + 1, (unsigned long long)enc_min(INT64_MIN));
+  }
+}
+
+cudaError_t launch_presence_check(const BuildArgs& a, cudaStream_t st) {
+  if (a.n_agg <= 0 || a.n_ditems <= 0) return cudaSuccess;
+  k_presence_check<<<dim3(unsigned(std::max(1, sm_count())), unsigned(a.n_agg)), 256, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_agg_zero(const BuildArgs& a, cudaStream_t st) {

@@ -253,8 +253,10 @@ enum { kSurvRow = 0, kSurvCount = 1, kSurvUniq = 2 };
 // A third kind, the presence bitmap, serves a unique key column with a declared domain in
 // a table without predicates: the counting pass sets bit (key - base) of a bitmap instead
 // of counting, and k_dense_hash walks the domain in key order.  A key outside the domain
-// or a bit already set (the column is not unique after all) makes the column inactive, so
-// that it keeps the per-row path.
+// makes the column inactive, and so does a bitmap with fewer set bits than the table has
+// rows (a key seen twice: the column is not unique after all), checked by
+// k_presence_check; an inactive column keeps the per-row path.  After the bitmap's whole
+// runs, its allocation holds the check's set-bit total and CTA ticket (PresenceCheck).
 enum { kAggCount = 0, kAggPresence = 1 };
 struct AggCol {
   int32_t table, col;
@@ -269,6 +271,11 @@ constexpr int64_t kHashChunk = 16384;
 // Presence bitmaps are walked in runs of kDenseRun keys (8 words); a bitmap holds whole runs.
 constexpr int64_t kDenseRun = 256;
 __host__ __device__ inline int64_t presence_words(int64_t cap) { return (cap + kDenseRun - 1) / kDenseRun * (kDenseRun / 32); }
+struct PresenceCheck {
+  unsigned long long bits;  // set bits counted so far
+  unsigned int ticket;      // CTAs done
+  unsigned int pad;
+};
 
 // Order-preserving maps of an int64 to uint64, for atomicMax on the stats pairs (both
 // zero-initialised: an empty column decodes as max < min).
@@ -410,6 +417,9 @@ constexpr uint64_t kBuildPlanMagic = 0x434d504255494c44ull;  // "CMPBUILD"
 
 // Fire-and-forget atomic additions (PTX red, relaxed): the same update as atomicAdd, with
 // no result register, so no instruction waits for the reply.
+__device__ __forceinline__ void red_or(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(v) : "memory");
+}
 __device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
   asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(v) : "memory");
 }
@@ -432,6 +442,7 @@ size_t build_smem_bytes(const BuildShape& s, int w);
 cudaError_t launch_build(const BuildArgs& a, const BuildShape& s, cudaStream_t st);
 size_t agg_count_smem_bytes(int32_t tile_rows, int32_t cache_slots, int32_t cache_cols, int32_t threads);
 cudaError_t launch_agg_zero(const BuildArgs& a, cudaStream_t st);
+cudaError_t launch_presence_check(const BuildArgs& a, cudaStream_t st);
 cudaError_t launch_agg_count(const BuildArgs& a, int32_t tile_rows, int32_t cnt_threads, int32_t cnt_grid,
                              int32_t work_slot, int64_t chunk_begin, int64_t chunk_end, cudaStream_t st);
 size_t uniq_smem_bytes(int32_t words, int32_t tile_rows);

@@ -155,14 +155,15 @@ def test_presence_columns_plan_host_logic(K):
     assert 4 * n // 8 <= wb < 4 * n // 8 + 4096
     ragged, wb2 = stats([_desc(K, n_rows=n, flags=flags, dom=(-7, n - 7 + 1))])
     assert ragged.n_presence == 1 and wb2 >= (n // 256 + 1) * 32
-    # zeroing, clearing, counting, the row kernel (the run-time fallback), the dense kernel
-    assert dense.launches == 5
+    # zeroing, clearing, counting, the presence check, the row kernel (the run-time fallback), the
+    # dense kernel
+    assert dense.launches == 6
     packed, _ = stats([_desc(K, n_rows=n, flags=flags, dom=(0, n))], w=65536)
     assert packed.n_presence == 1
     # with a counted table beside it: the counting pass in two launches (presence first)
     fk = _desc(K, n_rows=4 * n, flags=K.CMP_COL_DOMAIN, dom=(0, n))
     split, _ = stats([fk, _desc(K, n_rows=n, flags=flags, dom=(0, n))])
-    assert split.n_presence == 1 and split.n_agg == 2 and split.launches == 7
+    assert split.n_presence == 1 and split.n_agg == 2 and split.launches == 8
     rng = K.cmp_pred(0, K.CMP_RANGE, 0, 100, None, 0)
     for t, cfg in ((_desc(K, n_rows=n, flags=flags, dom=(0, 4 * n + 1)), None),
                    (_desc(K, n_rows=n, flags=flags, dom=(0, n), preds=(rng,)), None),

@@ -153,5 +153,6 @@ def test_dense_beside_the_second_counting_launch(orc, w):
     dw = _build(wl)
     info = P.build_plan_info(dw)
     assert info["n_presence"] == 1 and info["n_unique_slabs"] == 0
-    assert info["launches"] == 7  # zeroing, clearing, two counting launches, dense, row kernel, hashing
+    # zeroing, clearing, two counting launches, the presence check, dense, row kernel, hashing
+    assert info["launches"] == 8
     _check(orc, wl, dw)
