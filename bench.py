@@ -721,8 +721,11 @@ def measure(a, wl, dev, world: int, rank: int, headline: bool):
     roof = {"bound": "hbm", "achieved": col_bytes / build_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
             "frac": col_bytes / build_s / 1e9 / hbm_peak, "traffic": _kernel_traffic(tkey),
             "peak_kind": peak_kind,
-            "kernel": "the batched build (one cmp_sketch_build_batched call: zeroing, key counting, unique-key "
-                      "hashing, row kernel, hashing of the counted keys)",
+            "kernel": "the batched build (one cmp_sketch_build_batched call: zeroing, key counting (two launches "
+                      "when presence bitmaps are built beside counted tables), presence check, unique-key "
+                      "hashing, presence-bitmap hashing, row kernel, hashing of the counted keys)",
+            "traffic_source": "profiles/counters.json (ncu DRAM bytes of every kernel of one build; the 1e9-row "
+                              "figure scaled x10 from its 10% case), null if a build source changed since",
             "algorithmic": f"{col_bytes} bytes: every referenced column read once ({rows} rows)",
             "alu": {"cw_evaluations": cw_evals, "tuple_updates": updates, "distinct_keys": distinct,
                     "achieved_evals_per_s": cw_evals / build_s,
