@@ -739,11 +739,13 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
     H->wide_max_slots = G.max_slots;
     H->wide_max_in = G.max_in;
     H->wide_max_suf = G.max_suf;
-    H->wide_grid = int32_t(sm_count()) * 4;
     H->wide_qcap = int32_t(std::min<int64_t>(int64_t(n_sub) * d, kWideQueueMax));
     H->wide_scratch_per_cta = int64_t(align16(
         sizeof(uint64_t) * size_t(int64_t(G.max_slots) * w + int64_t(G.max_suf) * (int64_t(w) + 1) +
                                   int64_t(std::max(G.max_in, 1)) * (int64_t(w) + 1))));
+    // its own grid: four CTAs per SM, as many as fit in kWideScratchBudget (at least one)
+    H->wide_grid = int32_t(std::max<int64_t>(
+        1, std::min<int64_t>(int64_t(sm_count()) * 4, kWideScratchBudget / std::max<int64_t>(H->wide_scratch_per_cta, 1))));
   }
   H->total_bytes = int64_t(off);
   H->max_suf = P->max_suf;
@@ -752,7 +754,7 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
   H->scratch_per_cta = int64_t(align16(sizeof(i128) * size_t(int64_t(P->max_slots) * w + int64_t(P->max_suf) * W1 +
                                                              int64_t(P->max_in) * W1) +
                                        sizeof(int32_t) * size_t(int64_t(P->max_rank) * w)));
-  H->ws_bytes = int64_t(est_ws_bytes(*H, H->grid, H->n_tri * d));
+  H->ws_bytes = int64_t(est_ws_bytes(*H, H->grid, H->n_tri * d, H->wide_grid));
   return CMP_OK;
 }
 
@@ -894,7 +896,7 @@ cmp_status cmp_estimate_ex(const void* plan_host, const void* plan_dev, void* ws
   if (H.n_sub > 0 && !est_dev) return CMP_EINVAL;
   if (ws_bytes < size_t(H.ws_bytes) || (H.ws_bytes > 0 && !ws_dev)) return CMP_EWORKSPACE;
   const EstArgs a = est_args(H, static_cast<const unsigned char*>(plan_dev), static_cast<unsigned char*>(ws_dev),
-                             H.grid, H.n_tri * H.d, status_dev);
+                             H.grid, H.n_tri * H.d, status_dev, H.wide_grid);
   return launch_estimate(a, H, est_dev, row_est_dev, reinterpret_cast<cudaStream_t>(stream), wide_rows_dev) ==
                  cudaSuccess
              ? CMP_OK

@@ -153,6 +153,9 @@ struct EstPlanHdr {
   int64_t wide_scratch_per_cta;
 };
 constexpr int32_t kWideQueueMax = 1 << 19;
+// scratch of the exact tier's own grid (its CTA areas reuse the estimate's scratch region and
+// extend it to this size when it is smaller)
+constexpr int64_t kWideScratchBudget = int64_t(256) << 20;
 constexpr uint64_t kEstPlanMagic = 0x434d504553544d54ull;  // "CMPESTMT"
 constexpr int32_t kEstPlanVersion = 6;
 
@@ -293,16 +296,19 @@ inline size_t est_fixed_bytes(const EstPlanHdr& H) {
          est_wide_bytes(H);
 }
 // The scratch region after the fixed part: `grid` per-CTA areas, then `tri_slots` triangle
-// rows; at least one CTA area of the exact tier's kernel.
-inline size_t est_scratch_bytes(const EstPlanHdr& H, int64_t grid, int64_t tri_slots) {
+// rows; the exact tier's kernel, which runs after every other one, reuses the region for
+// `wide_ctas` CTA areas of its own (at least one).
+inline size_t est_scratch_bytes(const EstPlanHdr& H, int64_t grid, int64_t tri_slots, int64_t wide_ctas) {
   const size_t main = size_t(H.scratch_per_cta) * size_t(grid) + size_t(H.tri_row_bytes) * size_t(tri_slots);
-  return H.wide && main < size_t(H.wide_scratch_per_cta) ? size_t(H.wide_scratch_per_cta) : main;
+  const size_t wide = H.wide ? size_t(H.wide_scratch_per_cta) * size_t(wide_ctas < 1 ? 1 : wide_ctas) : 0;
+  return main > wide ? main : wide;
 }
-inline size_t est_ws_bytes(const EstPlanHdr& H, int64_t grid, int64_t tri_slots) {
-  return est_fixed_bytes(H) + est_scratch_bytes(H, grid, tri_slots);
+inline size_t est_ws_bytes(const EstPlanHdr& H, int64_t grid, int64_t tri_slots, int64_t wide_ctas) {
+  return est_fixed_bytes(H) + est_scratch_bytes(H, grid, tri_slots, wide_ctas);
 }
+// wide_ctas: the exact tier's grid, the CTA areas est_scratch_bytes reserved for it (>= 1).
 inline EstArgs est_args(const EstPlanHdr& H, const unsigned char* pd, unsigned char* ws, int32_t grid,
-                        int64_t tri_slots, int32_t* status) {
+                        int64_t tri_slots, int32_t* status, int32_t wide_ctas) {
   EstArgs a;
   a.subs = reinterpret_cast<const EstSub*>(pd + H.off_subs);
   a.ops = reinterpret_cast<const EstOp*>(pd + H.off_ops);
@@ -349,10 +355,7 @@ inline EstArgs est_args(const EstPlanHdr& H, const unsigned char* pd, unsigned c
     a.wide_res = H.wide ? reinterpret_cast<uint64_t*>(ws + o_res) : nullptr;
     // the exact tier's kernel runs after every other one and reuses their scratch
     a.wide_scratch = H.wide ? ws + est_fixed_bytes(H) : nullptr;
-    if (H.wide && H.wide_scratch_per_cta > 0) {
-      const int64_t fit = int64_t(est_scratch_bytes(H, grid, tri_slots) / size_t(H.wide_scratch_per_cta));
-      a.wide_grid = int32_t(fit < 1 ? 1 : (fit < H.wide_grid ? fit : H.wide_grid));
-    }
+    if (H.wide && H.wide_scratch_per_cta > 0) a.wide_grid = wide_ctas < 1 ? 1 : wide_ctas;
   }
   a.scratch = ws + est_fixed_bytes(H);
   a.scratch_per_cta = H.scratch_per_cta;

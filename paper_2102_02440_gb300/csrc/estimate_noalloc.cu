@@ -57,13 +57,16 @@ extern "C" cmp_status cmp_estimate_noalloc(const void* plan_host, const void* pl
   if (per_cta) grid = std::max<int64_t>(1, std::min<int64_t>(grid, int64_t((cap - fixed - per_tri) / per_cta)));
   int64_t slots = 0;
   if (per_tri) slots = std::min<int64_t>(H.n_tri * H.d, int64_t((cap - fixed - per_cta * size_t(grid)) / per_tri));
-  if (est_ws_bytes(H, grid, slots) > cap || (per_tri && slots < 1)) return CMP_EWORKSPACE;
-  // (est_ws_bytes includes one CTA area of the exact tier's kernel, which shares the scratch)
+  // the exact tier's kernel reuses the scratch region: as many of its CTA areas as fit (at least one)
+  int64_t wide_ctas = 1;
+  if (H.wide && H.wide_scratch_per_cta > 0 && cap > fixed)
+    wide_ctas = std::max<int64_t>(1, std::min<int64_t>(H.wide_grid, int64_t((cap - fixed) / size_t(H.wide_scratch_per_cta))));
+  if (est_ws_bytes(H, grid, slots, wide_ctas) > cap || (per_tri && slots < 1)) return CMP_EWORKSPACE;
   void* ws_v = nullptr;
   const cmp_status st = workspace_address(&ws_v);
   if (st != CMP_OK) return st;
   const EstArgs a = est_args(H, static_cast<const unsigned char*>(plan_dev), static_cast<unsigned char*>(ws_v),
-                             int32_t(grid), slots, status_dev);
+                             int32_t(grid), slots, status_dev, int32_t(wide_ctas));
   return launch_estimate(a, H, est_dev, row_est_dev, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? CMP_OK
                                                                                                           : CMP_ECUDA;
 }

@@ -20,26 +20,50 @@ constexpr float kFeatScale = 1.0f / 32.0f;
 
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
+// Thread-block cluster helpers: this CTA's rank in its cluster, a barrier of every thread of
+// the cluster (release / acquire: shared-memory writes before it are visible after it), and
+// the address of a shared variable in another CTA of the cluster.
+__device__ __forceinline__ unsigned cluster_ctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+template <class T>
+__device__ __forceinline__ T* cluster_map_shared(T* p, unsigned rank) {
+  uint64_t out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<uint64_t>(p)), "r"(rank));
+  return reinterpret_cast<T*>(out);
+}
+
 // ---------------------------------------------------------------- self-join sizes
 // f2[s] = median over rows i of sum_j C[s][i][j]^2 (the Fast-AGMS self-join estimate of
-// Sec. 3.2 applied to one sketch), exact per row, rounded once.  One CTA per sketch; its
-// warps split the d rows into d * split contiguous parts (split = warps / d, at least 1),
-// each lane streaming its part with four independent accumulators.
+// Sec. 3.2 applied to one sketch), exact per row, rounded once.  One cluster of kF2Cluster
+// CTAs per sketch: CTA r of the cluster takes rows r, r + kF2Cluster, ..., its warps split
+// each of them into contiguous parts, each lane streaming its part with four independent
+// accumulators; after a cluster barrier the first CTA reads every row's exact sum from the
+// other CTAs' shared memory (distributed shared memory) and takes the median.
 constexpr int kF2Threads = 1024;
+constexpr int kF2Cluster = 8;
 
 __global__ void __launch_bounds__(kF2Threads) k_sketch_f2(const int32_t* __restrict__ C, int64_t n_sketches,
                                                           int32_t d, int32_t w, double* __restrict__ f2) {
   __shared__ u128 part[32];
-  __shared__ i128 rows[CMP_MAX_D];
+  __shared__ i128 rows[CMP_MAX_D];  // this CTA's rows (the others: unused)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int split = nw / d > 0 ? nw / d : 1;
-  const int units = d * split;
-  const int64_t len = (int64_t(w) + split - 1) / split;
-  for (int64_t s = blockIdx.x; s < n_sketches; s += gridDim.x) {
-    for (int u0 = 0; u0 < units; u0 += nw) {  // rounds of at most nw parts (one round unless d > warps)
+  const unsigned rank = cluster_ctarank();
+  const int64_t s = int64_t(blockIdx.x) / kF2Cluster;
+  const int my_rows = (d - int(rank) + kF2Cluster - 1) / kF2Cluster;  // rows rank, rank + kF2Cluster, ...
+  if (my_rows > 0) {
+    const int split = nw / my_rows > 0 ? nw / my_rows : 1;
+    const int units = my_rows * split;
+    const int64_t len = (int64_t(w) + split - 1) / split;
+    for (int u0 = 0; u0 < units; u0 += nw) {  // rounds of at most nw parts
       const int u = u0 + warp;
       if (u < units) {
-        const int i = u / split, p = u % split;
+        const int i = int(rank) + (u / split) * kF2Cluster, p = u % split;
         const int64_t b = int64_t(p) * len, e = b + len < w ? b + len : int64_t(w);
         const int32_t* src = C + (s * d + i) * int64_t(w);
         u128 a0 = 0, a1 = 0, a2 = 0, a3 = 0;  // each term < 2^62
@@ -68,29 +92,32 @@ __global__ void __launch_bounds__(kF2Threads) k_sketch_f2(const int32_t* __restr
       __syncthreads();
       if (threadIdx.x == 0) {
         for (int q = 0; q < nw && u0 + q < units; q++) {
-          const int uu = u0 + q, i = uu / split;
+          const int uu = u0 + q, i = int(rank) + (uu / split) * kF2Cluster;
           if (uu % split == 0) rows[i] = 0;
           rows[i] = i128(u128(rows[i]) + part[q]);
         }
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) {
-      for (int i = 1; i < d; i++) {  // insertion sort of exact integers
-        const i128 v = rows[i];
-        int j = i - 1;
-        while (j >= 0 && rows[j] > v) {
-          rows[j + 1] = rows[j];
-          j--;
-        }
-        rows[j + 1] = v;
-      }
-      const double r = (d & 1) ? i128_to_double(rows[d / 2])
-                               : 0.5 * mag_to_double(false, 0, u128(rows[d / 2 - 1]) + u128(rows[d / 2]));
-      f2[s] = r;
-    }
-    __syncthreads();
   }
+  cluster_sync_all();  // every row sum of the sketch is in its CTA's shared memory
+  if (rank == 0 && threadIdx.x == 0) {
+    i128 all[CMP_MAX_D];
+    for (int i = 0; i < d; i++) all[i] = *cluster_map_shared(&rows[i], unsigned(i % kF2Cluster));
+    for (int i = 1; i < d; i++) {  // insertion sort of exact integers
+      const i128 v = all[i];
+      int j = i - 1;
+      while (j >= 0 && all[j] > v) {
+        all[j + 1] = all[j];
+        j--;
+      }
+      all[j + 1] = v;
+    }
+    const double r = (d & 1) ? i128_to_double(all[d / 2])
+                             : 0.5 * mag_to_double(false, 0, u128(all[d / 2 - 1]) + u128(all[d / 2]));
+    f2[s] = r;
+  }
+  cluster_sync_all();  // the other CTAs' shared memory stays until the first has read it
 }
 
 // ---------------------------------------------------------------- features
@@ -278,9 +305,19 @@ __global__ void k_mlp_combine(const double* __restrict__ median, const float* __
 cudaError_t launch_sketch_f2(const int32_t* C, int64_t n_sketches, int32_t d, int32_t w, double* f2,
                              cudaStream_t st) {
   if (n_sketches <= 0) return cudaSuccess;
-  const int64_t grid = n_sketches < 8192 ? n_sketches : 8192;
-  k_sketch_f2<<<unsigned(grid), kF2Threads, 0, st>>>(C, n_sketches, d, w, f2);
-  return cudaGetLastError();
+  if (n_sketches > (int64_t(1) << 31) / kF2Cluster - 1) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(n_sketches * kF2Cluster));  // one cluster per sketch
+  cfg.blockDim = dim3(unsigned(kF2Threads));
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kF2Cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_sketch_f2, C, n_sketches, d, w, f2);
 }
 
 cudaError_t launch_mlp_features(const int64_t* row_est, int64_t n, int32_t d, const double* f2a, const double* f2b,

@@ -227,3 +227,23 @@ def test_features_indexed_equals_gathered():
     K.cmp_mlp_features_indexed(rows.data_ptr(), n, d, f2.data_ptr(), idx.data_ptr(), got.data_ptr(), K.stream_handle())
     torch.cuda.synchronize()
     assert torch.equal(ref, got)
+
+
+@pytest.mark.parametrize("d,w", [(1, 1), (3, 100), (8, 777), (15, 65536), (16, 4096), (64, 300)])
+def test_self_join_sizes_every_row_split(d, w):
+    """cmp_sketch_f2 with rows spread over the CTAs of a cluster (fewer rows than CTAs, one
+    each, several each, even d): the exact median of the exact row sums of squares, rounded
+    once, for counters up to +-(2^31 - 1)."""
+    rng = np.random.default_rng(d * 1000 + w)
+    n = 5
+    C = rng.integers(-(2 ** 31) + 1, 2 ** 31, size=(n, d, w), dtype=np.int64)
+    C[:, :, 0] = 2 ** 31 - 1
+    Cd = torch.from_numpy(C.astype(np.int32)).cuda()
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    K.cmp_sketch_f2(Cd.data_ptr(), n, d, w, out.data_ptr(), K.stream_handle())
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for s in range(n):
+        rows = sorted(sum(int(v) * int(v) for v in C[s, i]) for i in range(d))
+        want = float(rows[d // 2]) if d % 2 else float(rows[d // 2 - 1] + rows[d // 2]) / 2.0
+        assert got[s] == want, (s, got[s], want)
