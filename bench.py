@@ -63,7 +63,8 @@ def _args():
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of autotuned launch shapes: read if it has this workload's, else written")
     ap.add_argument("--case", default=None,
-                    choices=["estimate_small", "estimate_full", "build_f1", "build_five", "batched", "scale",
+                    choices=["estimate_small", "estimate_full", "build_f1", "build_five", "batched", "batched_full",
+                             "scale",
                              "partition", "offline_sample", "cached", "star17", "shapes"],
                     help="run one small profiling case instead of the benchmark (for ncu captures)")
     return ap.parse_args()
@@ -866,7 +867,13 @@ def measure_batched(a, dev):
                                                       flags=K.CMP_EST_CACHE_MESSAGES | K.CMP_EST_STAR_LATTICE |
                                                       K.CMP_EST_NO_WIDE))
     ms_est_nw = timed(plan_nw.run, 1)
-    n_nan_nw = int(torch.isnan(plan_nw.est).sum().item())
+    nan_nw = torch.isnan(plan_nw.est).cpu().numpy()
+    n_nan_nw = int(nan_nw.sum())
+    n_cyc_nw = 0  # of those, the sub-plans with a cycle (as many edges as tables, or more)
+    for q in np.flatnonzero(nan_nw):
+        g, m = graphs[sg[q]], int(sm[q])
+        inner = sum(1 for u, v in zip(g.edge_u, g.edge_v) if (m >> u) & 1 and (m >> v) & 1)
+        n_cyc_nw += int(inner >= bin(m).count("1"))
     del plan_nw
     gb.dw.status.zero_()
     rng = np.random.default_rng(0)
@@ -885,7 +892,8 @@ def measure_batched(a, dev):
                          "speedup": (sm.size / (ms_est_b / 1e3)) / (samp.size / (ms_est_1 / 1e3)),
                          "flags": "CMP_EST_CACHE_MESSAGES | CMP_EST_STAR_LATTICE, 256 threads x 4 CTAs/SM, chunk 16",
                          "subplans_nan": n_nan,
-                         "without_exact_tier": {"ms": ms_est_nw, "subplans_beyond_int128": n_nan_nw}}}
+                         "without_exact_tier": {"ms": ms_est_nw, "subplans_beyond_int128": n_nan_nw,
+                                                "of_which_cyclic": n_cyc_nw}}}
 
 
 def run_ours(a):
@@ -1443,6 +1451,10 @@ def main():
     a = _args()
     if a.case == "batched":
         run_batched(a)
+    elif a.case == "batched_full":  # the batched-enumeration extra of the benchmark line, alone
+        import torch
+        print(json.dumps({"case": "batched enumeration at full rows",
+                          **measure_batched(a, torch.device("cuda", 0))}), flush=True)
     elif a.case == "cached":
         run_cached(a)
     elif a.case == "shapes":

@@ -736,6 +736,9 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
       H->wide_n_items = n_gen;
     }
     const PlanOut& G = own ? *F : *P;
+    int64_t units = 0;  // every row of every sub-plan, once per conditioning chunk
+    for (const EstSub& sb : G.subs) units += int64_t(d) * std::max<int32_t>(1, sb.n_chunks);
+    H->wide_unit_cap = int32_t(std::min<int64_t>(std::max<int64_t>(units, 1), kWideUnitMax));
     H->wide_max_slots = G.max_slots;
     H->wide_max_in = G.max_in;
     H->wide_max_suf = G.max_suf;

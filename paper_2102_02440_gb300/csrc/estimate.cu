@@ -826,15 +826,24 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_estimate_finalize(const __
   }
   __syncthreads();
   // Exact tier: the rows beyond int128 of a sub-plan are queued and evaluated again modulo
-  // the primes; its other rows are kept as they are for the median.
+  // the primes, one unit per conditioning chunk of the row (its units are consecutive); its
+  // other rows are kept as they are for the median.
   if (A.wide && i < d && any_ovf) {
     int32_t slot = -1;
     if (ovf) {
       const uint32_t k = atomicAdd(A.wide_queue, 1u);
-      if (k < uint32_t(A.wide_qcap)) {
+      const uint32_t nch = uint32_t(max(1, A.wsubs[q].n_chunks));
+      const uint32_t cap = uint32_t(A.wide_unit_cap);
+      // no reservation once the units are used up (the counter cannot wrap)
+      const bool room = k < uint32_t(A.wide_qcap) && *reinterpret_cast<volatile uint32_t*>(A.wide_queue + 2) < cap;
+      const uint32_t u0 = room ? atomicAdd(A.wide_queue + 2, nch) : cap;
+      if (u0 < cap && nch <= cap - u0) {
         A.wide_queue[4 + k] = uint32_t(q * d + i);
+        A.wide_row_start[k] = int32_t(u0);
+        for (uint32_t c = 0; c < nch; c++) A.wide_units[u0 + c] = (uint64_t(k) << 32) | c;
         slot = int32_t(k);
       } else {
+        for (uint32_t c = u0; c < cap; c++) A.wide_units[c] = ~0ull;  // the part of the cap it took
         atomicOr(&lost, 1);
       }
     }

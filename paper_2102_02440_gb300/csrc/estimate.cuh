@@ -151,13 +151,15 @@ struct EstPlanHdr {
   int64_t wide_off_subs, wide_off_ops, wide_off_in, wide_off_items, wide_n_items;
   int32_t wide_max_slots, wide_max_in, wide_max_suf, wide_grid;
   int64_t wide_scratch_per_cta;
+  int32_t wide_unit_cap, pad2;  // (row, conditioning chunk) units the tier can take per call
 };
 constexpr int32_t kWideQueueMax = 1 << 19;
+constexpr int32_t kWideUnitMax = 1 << 20;
 // scratch of the exact tier's own grid (its CTA areas reuse the estimate's scratch region and
 // extend it to this size when it is smaller)
 constexpr int64_t kWideScratchBudget = int64_t(256) << 20;
 constexpr uint64_t kEstPlanMagic = 0x434d504553544d54ull;  // "CMPESTMT"
-constexpr int32_t kEstPlanVersion = 6;
+constexpr int32_t kEstPlanVersion = 7;
 
 // Exact tier beyond int128: a row is evaluated modulo kWideMods primes p_j = 2^62 - c_j
 // (exact ring arithmetic: the contraction is sums of products of the counters, and the
@@ -210,12 +212,14 @@ struct EstArgs {
   const EstIn* winputs;
   const EstItem* witems;
   int64_t wide_n_items;
-  int32_t wide_max_slots, wide_max_in, wide_max_suf, wide_grid, wide_qcap;
+  int32_t wide_max_slots, wide_max_in, wide_max_suf, wide_grid, wide_qcap, wide_unit_cap;
   int64_t wide_scratch_per_cta;
-  uint32_t* wide_queue;   // [0] rows queued, [1] sub-plans queued, [4..4+qcap) rows, then sub-plans
+  uint32_t* wide_queue;   // [0] rows queued, [1] sub-plans queued, [2] units taken, [4..4+qcap) rows, then sub-plans
   int32_t* wide_slot;     // [n_sub * d] queue slot of each row, -1 when it stays in int128
   i128* wide_in;          // [n_sub * d] the int128 rows of sub-plans in the queue
-  uint64_t* wide_res;     // [qcap][kWideMods + 1]: the row's residues, then its bound (double bits)
+  int32_t* wide_row_start;  // [qcap] first unit of each queued row (its chunks' units follow), -1: none
+  uint64_t* wide_units;   // [unit_cap] (queued row << 32 | conditioning chunk); row ~0u: none
+  uint64_t* wide_part;    // [unit_cap][kWideMods + 1]: the unit's residues, then its bound (double bits)
   void* wide_scratch;     // wide_grid areas of wide_scratch_per_cta bytes
 };
 
@@ -288,7 +292,9 @@ inline size_t est_wide_bytes(const EstPlanHdr& H) {
   if (!H.wide) return 0;
   const size_t rows = size_t(H.n_sub) * size_t(H.d);
   return align16(sizeof(uint32_t) * (4 + size_t(H.wide_qcap) + size_t(H.n_sub))) + align16(sizeof(int32_t) * rows) +
-         align16(sizeof(i128) * rows) + align16(sizeof(uint64_t) * size_t(H.wide_qcap) * (kWideMods + 1));
+         align16(sizeof(i128) * rows) + align16(sizeof(int32_t) * size_t(H.wide_qcap)) +
+         align16(sizeof(uint64_t) * size_t(H.wide_unit_cap)) +
+         align16(sizeof(uint64_t) * size_t(H.wide_unit_cap) * (kWideMods + 1));
 }
 inline size_t est_fixed_bytes(const EstPlanHdr& H) {
   return align16(sizeof(i128) * size_t(H.n_items)) + align16(sizeof(int32_t) * size_t(H.n_items)) +
@@ -342,17 +348,22 @@ inline EstArgs est_args(const EstPlanHdr& H, const unsigned char* pd, unsigned c
   a.wide_max_suf = H.wide_max_suf;
   a.wide_grid = 0;  // set below from the scratch region it shares
   a.wide_qcap = H.wide_qcap;
+  a.wide_unit_cap = H.wide_unit_cap;
   a.wide_scratch_per_cta = H.wide_scratch_per_cta;
   {
     const size_t o_wide = est_fixed_bytes(H) - est_wide_bytes(H);
     const size_t rows = size_t(H.n_sub) * size_t(H.d);
     const size_t o_slot = o_wide + align16(sizeof(uint32_t) * (4 + size_t(H.wide_qcap) + size_t(H.n_sub)));
     const size_t o_in = o_slot + align16(sizeof(int32_t) * rows);
-    const size_t o_res = o_in + align16(sizeof(i128) * rows);
+    const size_t o_start = o_in + align16(sizeof(i128) * rows);
+    const size_t o_units = o_start + align16(sizeof(int32_t) * size_t(H.wide_qcap));
+    const size_t o_part = o_units + align16(sizeof(uint64_t) * size_t(H.wide_unit_cap));
     a.wide_queue = H.wide ? reinterpret_cast<uint32_t*>(ws + o_wide) : nullptr;
     a.wide_slot = H.wide ? reinterpret_cast<int32_t*>(ws + o_slot) : nullptr;
     a.wide_in = H.wide ? reinterpret_cast<i128*>(ws + o_in) : nullptr;
-    a.wide_res = H.wide ? reinterpret_cast<uint64_t*>(ws + o_res) : nullptr;
+    a.wide_row_start = H.wide ? reinterpret_cast<int32_t*>(ws + o_start) : nullptr;
+    a.wide_units = H.wide ? reinterpret_cast<uint64_t*>(ws + o_units) : nullptr;
+    a.wide_part = H.wide ? reinterpret_cast<uint64_t*>(ws + o_part) : nullptr;
     // the exact tier's kernel runs after every other one and reuses their scratch
     a.wide_scratch = H.wide ? ws + est_fixed_bytes(H) : nullptr;
     if (H.wide && H.wide_scratch_per_cta > 0) a.wide_grid = wide_ctas < 1 ? 1 : wide_ctas;

@@ -6,10 +6,11 @@
 // min-abs selections of the merge decided by comparisons of presorted magnitudes only.  So
 // its value E is determined exactly by E mod p_j for primes p_j whose product P exceeds 2|E|,
 // and the same evaluation with absolute values in double, rounded upwards at every step, is
-// an upper bound on |E|.  A CTA evaluates one (queued row, modulus) unit over all of the row's
-// conditioning chunks; the finalize rebuilds E from its residues by Garner's algorithm when
-// the bound is below 2^kWideBits (< P / 2), takes the exact median over the d rows and rounds
-// it once to double.
+// an upper bound on |E|.  E is the sum of its conditioning values' terms (one term for a
+// tree), so a row is split into units, one per conditioning chunk: a CTA evaluates one
+// (unit, modulus) pair; the finalize sums the units' residues and bounds, rebuilds E by
+// Garner's algorithm when the bound is below 2^kWideBits (< P / 2), takes the exact median
+// over the d rows and rounds it once to double.
 #include <cuda_runtime.h>
 
 #include "est_arith.cuh"
@@ -131,9 +132,9 @@ __device__ __forceinline__ const int32_t* wrank_row(const EstIn& x, const EstIn&
 
 constexpr int kWideThreads = 256;
 
-// One row of sub-plan sb (its items [it0, it0 + n_chunks)) in arithmetic ar.
+// Conditioning chunk ch of one row of sub-plan sb (its item it0 + ch) in arithmetic ar.
 template <class M>
-__device__ typename M::V wide_row(const M& ar, const EstArgs& A, const EstSub& sb, int row, EstOp* sh_ops,
+__device__ typename M::V wide_row(const M& ar, const EstArgs& A, const EstSub& sb, int row, int ch, EstOp* sh_ops,
                                   EstIn* sh_in, typename M::V* sh, typename M::V* sh_val, uint32_t* sh_ac,
                                   unsigned char* cta) {
   using V = typename M::V;
@@ -168,9 +169,8 @@ __device__ typename M::V wide_row(const M& ar, const EstArgs& A, const EstSub& s
       if (sh_in[q].kind == kInCond) cond_s[n_cond++] = sh_in[q].s + ro;
   }
   V total = ar.zero();
-  const int64_t it0 = sb.item_begin + int64_t(row) * sb.n_chunks;
-  for (int ch = 0; ch < sb.n_chunks; ch++) {
-    const EstItem item = A.witems[it0 + ch];
+  {
+    const EstItem item = A.witems[sb.item_begin + int64_t(row) * sb.n_chunks + ch];
     for (int c = item.c0; c < item.c1; c++) {
       bool zero = false;
       for (int q = 0; q < n_cond; q++) zero |= __ldg(cond_s[q] + c) == 0;
@@ -303,9 +303,19 @@ __device__ __forceinline__ int wide_mods_for(double B) {
   return k < 1 ? 1 : (k > kWideMods ? 0 : k);
 }
 
-// Persistent over units of the queued rows: pass 0 computes every row's bound, pass 1 its
-// residues modulo the primes it needs (the others are skipped).
-__global__ void __launch_bounds__(kWideThreads) k_estimate_wide(const __grid_constant__ EstArgs A, int pass) {
+// A queued row's bound: the sum, rounded upwards in unit order, of its units' bounds.
+__device__ __forceinline__ double wide_row_bound(const EstArgs& A, uint32_t e) {
+  const uint32_t qr = A.wide_queue[4 + e];
+  const int nch = max(1, A.wsubs[qr / uint32_t(A.d)].n_chunks);
+  const uint64_t* part = A.wide_part + int64_t(A.wide_row_start[e]) * (kWideMods + 1);
+  double B = 0.0;
+  for (int c = 0; c < nch; c++) B = __dadd_ru(B, __longlong_as_double((long long)part[int64_t(c) * (kWideMods + 1) + kWideMods]));
+  return B;
+}
+
+// Persistent over the units of the queued rows: pass 0 computes every unit's bound, pass 1
+// its residues modulo the primes its row needs (the others are skipped).
+__global__ void __launch_bounds__(kWideThreads, 4) k_estimate_wide(const __grid_constant__ EstArgs A, int pass) {
   __shared__ EstOp sh_ops[kEstMaxOps];
   __shared__ EstIn sh_in[kEstMaxSubIn];
   __shared__ uint64_t sh_u[33];
@@ -313,16 +323,18 @@ __global__ void __launch_bounds__(kWideThreads) k_estimate_wide(const __grid_con
   __shared__ uint64_t sh_valu[CMP_MAX_SKETCHES];
   __shared__ double sh_vald[CMP_MAX_SKETCHES];
   __shared__ uint32_t sh_ac[CMP_MAX_SKETCHES];
-  const uint32_t n_rows = min(A.wide_queue[0], uint32_t(A.wide_qcap));
-  const int per_row = pass == 0 ? 1 : kWideMods;
-  const int64_t units = int64_t(n_rows) * per_row;
+  const uint32_t n_units = min(A.wide_queue[2], uint32_t(A.wide_unit_cap));
+  const int per_unit = pass == 0 ? 1 : kWideMods;
+  const int64_t jobs = int64_t(n_units) * per_unit;
   unsigned char* cta = static_cast<unsigned char*>(A.wide_scratch) + int64_t(blockIdx.x) * A.wide_scratch_per_cta;
-  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int64_t e = u / per_row;
-    const int j = pass == 0 ? kWideMods : int(u % per_row);
-    if (pass == 1 &&
-        j >= wide_mods_for(__longlong_as_double((long long)A.wide_res[e * (kWideMods + 1) + kWideMods])))
-      continue;  // block-uniform
+  for (int64_t g = blockIdx.x; g < jobs; g += gridDim.x) {
+    const int64_t u = g / per_unit;
+    const int j = pass == 0 ? kWideMods : int(g % per_unit);
+    const uint64_t ent = A.wide_units[u];
+    if (ent == ~0ull) continue;  // taken by a row that did not fit (its sub-plan is reported NaN)
+    const uint32_t e = uint32_t(ent >> 32);
+    const int ch = int(uint32_t(ent));
+    if (pass == 1 && j >= wide_mods_for(wide_row_bound(A, e))) continue;  // block-uniform
     const uint32_t qr = A.wide_queue[4 + e];
     const int64_t q = qr / uint32_t(A.d);
     const int row = int(qr % uint32_t(A.d));
@@ -345,13 +357,14 @@ __global__ void __launch_bounds__(kWideThreads) k_estimate_wide(const __grid_con
       __syncthreads();
       if (j < kWideMods) {
         const ModArith ar{wide_p(j), wide_c(j)};
-        result = wide_row(ar, A, sb, row, sh_ops, sh_in, sh_u, sh_valu, sh_ac, cta);
+        result = wide_row(ar, A, sb, row, ch, sh_ops, sh_in, sh_u, sh_valu, sh_ac, cta);
       } else {
         const BoundArith ar{};
-        result = uint64_t(__double_as_longlong(wide_row(ar, A, sb, row, sh_ops, sh_in, sh_d, sh_vald, sh_ac, cta)));
+        result =
+            uint64_t(__double_as_longlong(wide_row(ar, A, sb, row, ch, sh_ops, sh_in, sh_d, sh_vald, sh_ac, cta)));
       }
     }
-    if (threadIdx.x == 0) A.wide_res[e * (kWideMods + 1) + j] = result;
+    if (threadIdx.x == 0) A.wide_part[u * (kWideMods + 1) + j] = result;
     __syncthreads();
   }
 }
@@ -469,9 +482,21 @@ __global__ void __launch_bounds__(kWideFinThreads) k_estimate_wide_finalize(cons
         const u128 m = v < 0 ? u128(0) - u128(v) : u128(v);
         for (int l = 0; l < kWideLimbs; l++) wv.m[l] = l == 0 ? uint64_t(m) : (l == 1 ? uint64_t(m >> 64) : 0);
       } else {
-        const uint64_t* r = A.wide_res + int64_t(slot) * (kWideMods + 1);
-        const int K = wide_mods_for(__longlong_as_double((long long)r[kWideMods]));
+        const int K = wide_mods_for(wide_row_bound(A, uint32_t(slot)));
         if (K == 0) atomicOr(&bad, 1);
+        // the row's residues: its units' residues summed modulo each prime
+        const int nch = max(1, A.wsubs[q].n_chunks);
+        const uint64_t* part = A.wide_part + int64_t(A.wide_row_start[slot]) * (kWideMods + 1);
+        uint64_t r[kWideMods];
+        for (int j = 0; j < K; j++) {
+          const uint64_t pj = wide_p(j);
+          uint64_t s = 0;
+          for (int c = 0; c < nch; c++) {
+            s += part[int64_t(c) * (kWideMods + 1) + j];  // both < p_j < 2^62: no wrap
+            s = s >= pj ? s - pj : s;
+          }
+          r[j] = s;
+        }
         // Garner: x = v_0 + v_1 p_0 + v_2 p_0 p_1 + ..., v_j from the residue mod p_j
         uint64_t v[kWideMods];
         for (int j = 0; j < K; j++) {

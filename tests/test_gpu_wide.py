@@ -49,21 +49,21 @@ def _oracle(orc, dw, masks):
     return [orc.estimate(wl.edge_u, wl.edge_v, sk, surv, dw.d, dw.w, int(m)) for m in masks]
 
 
-def _run(dw, masks, flags=0):
+def _run(dw, masks, flags=0, cond_chunk=0):
     dw.status.zero_()
-    est = P.DeviceEstimator(dw, masks, cfg=K.cmp_estimate_cfg.make(flags=flags))
+    est = P.DeviceEstimator(dw, masks, cfg=K.cmp_estimate_cfg.make(flags=flags, cond_chunk=cond_chunk))
     est.presort()
     est.estimate_wide()
     torch.cuda.synchronize()
     return est, int(dw.status.item())
 
 
-def _check_exact(orc, dw, masks, flags_list):
+def _check_exact(orc, dw, masks, flags_list, cond_chunk=0):
     refs = _oracle(orc, dw, masks)
     beyond = sum(1 for r in refs if any(abs(v) >= 1 << 127 for v in r.rows))
     assert beyond > 0                                   # the tier has work to do
     for flags in flags_list:
-        est, st = _run(dw, masks, flags)
+        est, st = _run(dw, masks, flags, cond_chunk)
         assert st == 0, (flags, st)
         rows = est.wide_values()
         e = est.est.cpu().numpy()
@@ -131,6 +131,25 @@ def test_cancelling_signs_and_ties(orc):
     _fill(dw, f)
     masks = [m for m in G.connected_subplans(9, eu, ev) if bin(m).count("1") >= 5]
     _check_exact(orc, dw, masks, [0, K.CMP_EST_GENERIC_ONLY, K.CMP_EST_CACHE_MESSAGES])
+
+
+@pytest.mark.parametrize("cond_chunk", [1, 7, 64])
+def test_cycles_split_into_conditioning_chunks(orc, cond_chunk):
+    """A 5-cycle with a leaf and a 4-cycle, w = 100: each row of a cyclic sub-plan beyond
+    int128 is evaluated by the tier as one unit per conditioning chunk (100, 15 or 2 of
+    them, the last one ragged), whose residues and bounds are summed per row."""
+    eu, ev = [0, 1, 2, 3, 4, 0, 6, 7, 8, 9], [1, 2, 3, 4, 0, 5, 7, 8, 9, 6]
+    n = 10
+    dw = _one_row_tables(eu, ev, n, 3, 100)
+    rng = np.random.default_rng(cond_chunk)
+
+    def f(shape):
+        a = rng.choice(np.array([-(2 ** 31 - 1), 2 ** 31 - 1, 2 ** 31 - 5, 0, -9, 4]), size=shape)
+        return a
+    _fill(dw, f)
+    masks = [m for m in G.connected_subplans(n, eu, ev) if bin(m).count("1") >= 4]
+    assert 0b0000111111 in masks and 0b1111000000 in masks  # both cycles
+    _check_exact(orc, dw, masks, [0, K.CMP_EST_GENERIC_ONLY], cond_chunk=cond_chunk)
 
 
 def test_beyond_the_exact_tier_is_reported(orc):
