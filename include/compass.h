@@ -296,8 +296,10 @@ typedef struct {
  *     the first such on ties (the merge equation of Sec. 4.2, iterated).  For one edge
  *     this is the Fast-AGMS inner product of Sec. 3.2.  The estimate is the median of
  *     E_0..E_{d-1} (Sec. 3.2), exact, rounded once to double (even d: mean of the two
- *     middle values).  Sub-plans whose edges contain more than one independent cycle
- *     return CMP_EUNSUPPORTED from the plan step.
+ *     middle values).  A sub-plan with rho independent cycles (edges - tables + 1) is
+ *     evaluated by conditioning on the buckets of rho non-tree edges, w^rho tree
+ *     contractions per row; rho > 3, or w^rho > 2^31 - 1, returns CMP_EUNSUPPORTED from
+ *     the plan step.
  *   Sampled tables (sample_rate): the estimate (the median, or the selected count of a
  *     single table) is multiplied by the sub-plan's scale, the product over its tables in
  *     ascending order of 1 / rate (double, left to right), which makes the two-way

@@ -355,6 +355,9 @@ cmp_status emit_ops(const cmp_graph& g, int32_t gi, const std::vector<int>& es, 
         }
       } else {
         x.kind = kInCond;
+        x.slot = 0;  // ordinal among the conditioned edges (ascending edge id)
+        for (int e2 : ez)
+          if (e2 < e && !tree[e2]) x.slot++;
       }
       P->ins.push_back(x);
       op.k++;
@@ -457,7 +460,11 @@ cmp_status plan_sub(const cmp_graph& g, int32_t gi, uint64_t mask, int32_t d, in
   std::vector<int> cond;
   for (int e : es)
     if (!tree[e]) cond.push_back(e);
-  if (cond.size() > 1) return CMP_EUNSUPPORTED;  // more than one independent cycle
+  // every assignment of the conditioned edges' buckets: w^rho conditioning values (int32)
+  if (cond.size() > size_t(kEstMaxCond)) return CMP_EUNSUPPORTED;
+  int64_t n_cond_vals = 1;
+  for (size_t k = 0; k < cond.size(); k++) n_cond_vals *= w;
+  if (n_cond_vals > int64_t(INT32_MAX)) return CMP_EUNSUPPORTED;
   if (cond.size() == 1 && !(flags & CMP_EST_GENERIC_ONLY) && w <= kTriMaxW &&
       plan_triangle(g, es, tree, cond[0], mask, d, w, sub_index, P, &sb)) {
     P->subs.push_back(sb);
@@ -466,15 +473,16 @@ cmp_status plan_sub(const cmp_graph& g, int32_t gi, uint64_t mask, int32_t d, in
   const cmp_status st = emit_ops(g, gi, es, order, parent_edge, tree, root, -1, cond.empty() ? C : nullptr, P, &sb);
   if (st != CMP_OK) return st;
   sb.cond = cond.empty() ? 0 : 1;
-  sb.n_chunks = cond.empty() ? 1 : (w + chunk - 1) / chunk;
+  const int32_t nv = int32_t(n_cond_vals);
+  sb.n_chunks = cond.empty() ? 1 : int32_t((int64_t(nv) + chunk - 1) / chunk);
   P->subs.push_back(sb);
   for (int i = 0; i < d; i++)
     for (int ch = 0; ch < sb.n_chunks; ch++) {
       EstItem it;
       it.sub = sub_index;
       it.row = i;
-      it.c0 = cond.empty() ? 0 : ch * chunk;
-      it.c1 = cond.empty() ? 1 : std::min(w, (ch + 1) * chunk);
+      it.c0 = cond.empty() ? 0 : int32_t(int64_t(ch) * chunk);
+      it.c1 = cond.empty() ? 1 : int32_t(std::min<int64_t>(nv, int64_t(ch + 1) * chunk));
       P->items.push_back(it);
     }
   return CMP_OK;

@@ -396,7 +396,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_estimate_items(const __grid_cons
   __shared__ uint32_t sh_ac[kMaxIn];
   __shared__ EstOp sh_ops[kEstMaxOps];
   __shared__ EstIn sh_in[kEstMaxSubIn];
-  __shared__ const int32_t* sh_cond[2];
+  __shared__ const int32_t* sh_cond[2 * kEstMaxCond];  // each conditioned edge's two sketches
+  __shared__ int32_t sh_cond_k[2 * kEstMaxCond];       // and its ordinal
   __shared__ int32_t sh_ncond;
   // per conditioned operation (at most two per sub-plan), for every c of the chunk when
   // its other inputs are leaves: |s[c]| and the "attains the minimum" value
@@ -435,23 +436,30 @@ __global__ void __launch_bounds__(MAXT, MINB) k_estimate_items(const __grid_cons
       for (int q = 0; q < n_in; q++)
         if (sh_in[q].kind == kInCache && A.cache_ovf[int64_t(sh_in[q].slot) * A.d + item.row]) sh_flag[0] |= 1;
       int nc = 0;
-      for (int q = 0; q < n_in && nc < 2; q++)
-        if (sh_in[q].kind == kInCond) sh_cond[nc++] = sh_in[q].s + ro;
+      for (int q = 0; q < n_in && nc < 2 * kEstMaxCond; q++)
+        if (sh_in[q].kind == kInCond) {
+          sh_cond[nc] = sh_in[q].s + ro;
+          sh_cond_k[nc++] = sh_in[q].slot;
+        }
       sh_ncond = nc;
-      // conditioned operations whose other inputs are all leaves: precomputable per c
+      // operations with one conditioned input whose other inputs are all leaves: precomputable per c
       int np = 0;
       for (int o = 0; o < sb.n_ops && np < 2; o++) {
         const EstOp& op = sh_ops[o];
-        int ca = -1;
+        int ca = -1, n_ca = 0;
         bool leaves = true;
         for (int a = 0, l = 0; l < op.k; l++) {
           if (l == op.p) continue;
           const int kind = sh_in[op.in_begin + l].kind;
-          if (kind == kInCond) ca = a;
-          else leaves &= kind == kInLeaf;
+          if (kind == kInCond) {
+            ca = a;
+            n_ca++;
+          } else {
+            leaves &= kind == kInLeaf;
+          }
           a++;
         }
-        if (ca >= 0 && leaves) {
+        if (n_ca == 1 && leaves) {
           sh_pop[np] = o;
           sh_pa[np] = ca;
           np++;
@@ -484,7 +492,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_estimate_items(const __grid_cons
     if (pre_ok) {
       for (int c = item.c0 + tid; c < item.c1; c += T) {
         bool zero = false;
-        for (int q = 0; q < sh_ncond; q++) zero |= __ldg(sh_cond[q] + c) == 0;
+        for (int q = 0; q < sh_ncond; q++) zero |= __ldg(sh_cond[q] + cond_digit(c, sh_cond_k[q], w)) == 0;
         sh_skip[c - item.c0] = zero;
       }
       for (int t = tid; t < 2 * nchunk; t += T) {
@@ -495,9 +503,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_estimate_items(const __grid_cons
         const int p = op.p, m = op.k - (p >= 0 ? 1 : 0), a = sh_pa[k];
         const int la = a + (p >= 0 && a >= p ? 1 : 0);
         const EstIn& x = in[la];
-        const int32_t sv = __ldg(x.s + ro + c);
+        const int cx = cond_digit(c, x.slot, w);
+        const int32_t sv = __ldg(x.s + ro + cx);
         sh_cac[k][t % nchunk] = sv < 0 ? uint32_t(-int64_t(sv)) : uint32_t(sv);
-        const int rpos = __ldg(rank_row(x, x, A.d, item.row, w) + c);
+        const int rpos = __ldg(rank_row(x, x, A.d, item.row, w) + cx);
         i128 v = i128(sv);
         bool o1 = false;
         for (int b = 0; b < m && v != 0; b++) {  // the others are leaves: G is a cached suffix sum
@@ -519,7 +528,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_estimate_items(const __grid_cons
         if (sh_skip[c - item.c0]) continue;  // block-uniform
       } else {
         bool zero = false;
-        for (int q = 0; q < sh_ncond; q++) zero |= __ldg(sh_cond[q] + c) == 0;
+        for (int q = 0; q < sh_ncond; q++) zero |= __ldg(sh_cond[q] + cond_digit(c, sh_cond_k[q], w)) == 0;
         if (zero) continue;  // block-uniform
       }
       for (int o = 0; o < sb.n_ops; o++) {
@@ -577,7 +586,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_estimate_items(const __grid_cons
           if (tid < m) {
             const EstIn& x = in[tid + (p >= 0 && tid >= p ? 1 : 0)];
             if (x.kind == kInCond) {
-              const int32_t v = __ldg(x.s + ro + c);
+              const int32_t v = __ldg(x.s + ro + cond_digit(c, x.slot, w));
               sh_ac[tid] = v < 0 ? uint32_t(-int64_t(v)) : uint32_t(v);
             }
           }
@@ -587,10 +596,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_estimate_items(const __grid_cons
           const int la = tid + (p >= 0 && tid >= p ? 1 : 0);
           const EstIn& x = in[la];
           if (x.kind == kInCond) {
-            // its cross ranks are the cached ones at bucket c's sorted position
-            const int rpos = __ldg(rank_row(x, x, A.d, item.row, w) + c);
+            // its cross ranks are the cached ones at its bucket's sorted position
+            const int cx = cond_digit(c, x.slot, w);
+            const int rpos = __ldg(rank_row(x, x, A.d, item.row, w) + cx);
             const uint32_t tau = sh_ac[tid];
-            i128 v = i128(__ldg(x.s + ro + c));
+            i128 v = i128(__ldg(x.s + ro + cx));
             bool o1 = false;
             for (int b = 0; b < m; b++) {
               if (b == tid) continue;

@@ -12,6 +12,7 @@ enum { kInOutput = 0, kInLeaf = 1, kInSlot = 2, kInCond = 3, kInCache = 4 };
 constexpr int kEstMaxOps = 64;     // operations of one sub-plan (one per non-leaf table)
 constexpr int kEstMaxSubIn = 136;  // edge inputs of one sub-plan
 constexpr int kEstMaxLevels = 64;  // launch levels of cached subtree messages
+constexpr int kEstMaxCond = 3;     // independent cycles of one sub-plan (conditioned edges)
 
 // One edge of a table operation, in the table's ascending edge-id order.
 struct EstIn {
@@ -21,7 +22,8 @@ struct EstIn {
   const int32_t* msk;    // kInLeaf: the leaf neighbour's sketch on the edge, [d][w]
   const int32_t* rk;     // this table's cross ranks from this sketch: [k][d][w], indexed by the other sketch
   int32_t kind;          // kInOutput / kInLeaf / kInSlot / kInCond
-  int32_t slot;          // kInSlot: message slot written by the child's operation; kInCache: cached message
+  int32_t slot;          // kInSlot: message slot written by the child's operation; kInCache: cached message;
+                         // kInCond: the conditioned edge's ordinal (its digit of the conditioning index)
   int32_t suf;           // kInLeaf / kInSlot: suffix-sum array of the sub-plan (item-persistent)
   int32_t tslot;         // this sketch's index within its table (selects rows of another input's rk)
 };
@@ -82,6 +84,14 @@ inline size_t star_smem_bytes() {
 struct EstItem {
   int32_t sub, row, c0, c1;  // conditioning values [c0, c1); trees use [0, 1); triangle: columns [c0, c1)
 };
+
+// Digit k (base w) of a conditioning index: the bucket of the sub-plan's k-th conditioned
+// edge (ascending edge id) when the index runs over all w^rho assignments of its rho edges.
+__device__ __forceinline__ int cond_digit(int c, int k, int w) {
+  if (c < w) return k == 0 ? c : 0;
+  for (int i = 0; i < k; i++) c /= w;
+  return c % w;
+}
 
 // Triangle sub-plans: the only cycle is U-W-V with the conditioned edge U-V, and every
 // other table is a leaf joined to U, V or W.  Each node lists its edges (EstIn, ascending

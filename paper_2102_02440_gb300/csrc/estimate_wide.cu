@@ -159,21 +159,25 @@ __device__ typename M::V wide_row(const M& ar, const EstArgs& A, const EstSub& s
       block_scan_v(ar, sl, w, /*reverse=*/true, sh);
     }
   }
-  // conditioned edge: at most one (sub-plans with one independent cycle)
-  const int32_t* cond_s[2] = {nullptr, nullptr};
+  // conditioned edges: both sketches of each (one per independent cycle), with its ordinal
+  const int32_t* cond_s[2 * kEstMaxCond];
+  int cond_k[2 * kEstMaxCond];
   int n_cond = 0;
   {
     const EstOp last = sh_ops[sb.n_ops - 1];
     const int n_in = last.in_begin + last.k;
-    for (int q = 0; q < n_in && n_cond < 2; q++)
-      if (sh_in[q].kind == kInCond) cond_s[n_cond++] = sh_in[q].s + ro;
+    for (int q = 0; q < n_in && n_cond < 2 * kEstMaxCond; q++)
+      if (sh_in[q].kind == kInCond) {
+        cond_s[n_cond] = sh_in[q].s + ro;
+        cond_k[n_cond++] = sh_in[q].slot;
+      }
   }
   V total = ar.zero();
   {
     const EstItem item = A.witems[sb.item_begin + int64_t(row) * sb.n_chunks + ch];
     for (int c = item.c0; c < item.c1; c++) {
       bool zero = false;
-      for (int q = 0; q < n_cond; q++) zero |= __ldg(cond_s[q] + c) == 0;
+      for (int q = 0; q < n_cond; q++) zero |= __ldg(cond_s[q] + cond_digit(c, cond_k[q], w)) == 0;
       if (zero) continue;  // block-uniform: every merged entry through that table is 0
       for (int o = 0; o < sb.n_ops; o++) {
         const EstOp op = sh_ops[o];
@@ -195,7 +199,7 @@ __device__ typename M::V wide_row(const M& ar, const EstArgs& A, const EstSub& s
         if (tid < m) {
           const EstIn& x = in[tid + (p >= 0 && tid >= p ? 1 : 0)];
           if (x.kind == kInCond) {
-            const int32_t v = __ldg(x.s + ro + c);
+            const int32_t v = __ldg(x.s + ro + cond_digit(c, x.slot, w));
             sh_ac[tid] = v < 0 ? uint32_t(-int64_t(v)) : uint32_t(v);
           }
         }
@@ -204,9 +208,10 @@ __device__ typename M::V wide_row(const M& ar, const EstArgs& A, const EstSub& s
           const int la = tid + (p >= 0 && tid >= p ? 1 : 0);
           const EstIn& x = in[la];
           if (x.kind == kInCond) {
-            const int rpos = __ldg(wrank_row(x, x, A.d, row, w) + c);
+            const int cx = cond_digit(c, x.slot, w);
+            const int rpos = __ldg(wrank_row(x, x, A.d, row, w) + cx);
             const uint32_t tau = sh_ac[tid];
-            V v = ar.from(__ldg(x.s + ro + c));
+            V v = ar.from(__ldg(x.s + ro + cx));
             for (int b = 0; b < m; b++) {
               if (b == tid) continue;
               const int lb = b + (p >= 0 && b >= p ? 1 : 0);

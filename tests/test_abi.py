@@ -227,10 +227,16 @@ def test_estimate_plan_host_logic(K):
         K.cmp_estimate_plan_bytes([_graph(K, [0, 1], [1, 2], 3)], 11, 64, [0], [0b101])
     assert ei.value.status == K.CMP_EINVAL        # chain 0-1-2 without 1 is disconnected
     k4 = _graph(K, [0, 0, 0, 1, 1, 2], [1, 2, 3, 2, 3, 3], 4)
+    K.cmp_estimate_plan_bytes([k4], 5, 64, [0], [0b1111])   # three independent cycles: 64^3 values
     with pytest.raises(K.CompassError) as ei:
-        K.cmp_estimate_plan_bytes([k4], 5, 64, [0], [0b1111])
-    assert ei.value.status == K.CMP_EUNSUPPORTED  # three independent cycles
-    K.cmp_estimate_plan_bytes([k4], 5, 64, [0], [0b0111])   # one cycle
+        K.cmp_estimate_plan_bytes([k4], 5, 2048, [0], [0b1111])
+    assert ei.value.status == K.CMP_EUNSUPPORTED  # 2048^3 conditioning values exceed int32
+    K.cmp_estimate_plan_bytes([k4], 5, 2048, [0], [0b0111])   # one cycle
+    k5 = _graph(K, [0, 0, 0, 0, 1, 1, 1, 2, 2, 3], [1, 2, 3, 4, 2, 3, 4, 3, 4, 4], 5)
+    with pytest.raises(K.CompassError) as ei:
+        K.cmp_estimate_plan_bytes([k5], 5, 4, [0], [0b11111])
+    assert ei.value.status == K.CMP_EUNSUPPORTED  # six independent cycles (at most three)
+    K.cmp_estimate_plan_bytes([k5], 5, 4, [0], [0b01111])   # its K4: three
     for bad in ([0], [1 << 4], [0b10000]):
         with pytest.raises(K.CompassError):
             K.cmp_estimate_plan_bytes([k4], 5, 64, [0], bad)

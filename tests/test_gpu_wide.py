@@ -152,6 +152,23 @@ def test_cycles_split_into_conditioning_chunks(orc, cond_chunk):
     _check_exact(orc, dw, masks, [0, K.CMP_EST_GENERIC_ONLY], cond_chunk=cond_chunk)
 
 
+def test_multi_cycle_beyond_int128(orc):
+    """Two and three independent cycles (a 4-cycle with a chord and a tail, K4 beside it)
+    with counters near +-2^31: the rows leave int128 and the tier conditions on every
+    assignment of the non-tree edges, one unit per chunk."""
+    eu, ev = [0, 1, 2, 3, 0, 3, 5, 5, 5, 6, 6, 7], [1, 2, 3, 0, 2, 4, 6, 7, 8, 7, 8, 8]
+    n = 9
+    dw = _one_row_tables(eu, ev, n, 3, 12)
+    rng = np.random.default_rng(21)
+
+    def f(shape):
+        return rng.choice(np.array([-(2 ** 31 - 1), 2 ** 31 - 1, 2 ** 31 - 9, 0, -5, 3]), size=shape)
+    _fill(dw, f)
+    masks = [m for m in G.connected_subplans(n, eu, ev) if bin(m).count("1") >= 4]
+    assert 0b11111 in masks and 0b111100000 in masks
+    _check_exact(orc, dw, masks, [0, K.CMP_EST_GENERIC_ONLY], cond_chunk=10)
+
+
 def test_beyond_the_exact_tier_is_reported(orc):
     """A 34-table chain at 2^31 - 1 everywhere: its row exceeds 2^990 (the bound of the
     tier), so its estimate is NaN with CMP_EOVERFLOW; a 20-table part of it (about 2^620) is

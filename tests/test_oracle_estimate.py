@@ -95,6 +95,8 @@ GRAPHS = {
     "parallel": ([0, 0, 1], [1, 1, 2], 3),
     "tri+tail": ([0, 1, 2, 2], [1, 2, 0, 3], 4),
     "two_cycles": ([0, 1, 2, 0, 3], [1, 2, 0, 3, 1], 4),
+    "k4": ([0, 0, 0, 1, 1, 2], [1, 2, 3, 2, 3, 3], 4),          # three independent cycles
+    "triple_parallel": ([0, 0, 0, 1], [1, 1, 1, 2], 3),         # two, on one pair of tables
 }
 
 
