@@ -40,6 +40,7 @@ struct PlanOut {
   std::vector<StarFam> stars;
   std::vector<StarUnit> star_suf_units, star_lat_units;
   int64_t star_suf_words = 0, star_t_entries = 0, n_star_sub = 0;
+  std::vector<int32_t> star_q;  // per family (StarFam.q_off): leaf set -> sub-plan, -1: none
 };
 
 bool graph_ok(const cmp_graph& g) {
@@ -606,6 +607,8 @@ void plan_stars(const cmp_graph* graphs, int32_t n_sub, const int32_t* sub_graph
     F.m1 = std::min(F.k1, std::max(0, 12 - F.k2));  // at most 2^12 entries per unit
     F.suf_off = P->star_suf_words;
     F.t_off = P->star_t_entries;
+    F.q_off = int64_t(P->star_q.size());
+    P->star_q.resize(P->star_q.size() + (size_t(1) << K), -1);
     P->star_suf_words += int64_t(d) * K * (int64_t(w) + 1);
     P->star_t_entries += int64_t(d) * K * (int64_t(1) << k);
     for (int e : U) {
@@ -634,6 +637,8 @@ void plan_stars(const cmp_graph* graphs, int32_t n_sub, const int32_t* sub_graph
       for (int e : fm.edges[j]) bits |= 1u << int(std::lower_bound(U.begin(), U.end(), e) - U.begin());
       (*star_of)[fm.qs[j]] = fi;
       (*sbits_of)[fm.qs[j]] = bits;
+      int32_t& slot = P->star_q[size_t(F.q_off) + bits];
+      if (slot < 0) slot = fm.qs[j];  // a repeated leaf set keeps the first (the others: generic tier)
       P->n_star_sub++;
     }
   }
@@ -715,6 +720,9 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
   off += align16(sizeof(StarUnit) * size_t(H->n_star_units));
   H->star_suf_words = P->star_suf_words;
   H->star_t_entries = P->star_t_entries;
+  H->off_star_q = int64_t(off);
+  H->n_star_q = int64_t(P->star_q.size());
+  off += align16(sizeof(int32_t) * P->star_q.size());
   // exact tier beyond int128: the sub-plans on the generic path alone (the main arrays when
   // they already are), evaluated again modulo the primes for the rows found out of range
   H->wide = (shape.flags & CMP_EST_NO_WIDE) ? 0 : 1;
@@ -863,6 +871,7 @@ cmp_status cmp_estimate_plan_encode(const cmp_graph* graphs, int32_t n_graphs, i
   if (!P.star_lat_units.empty())
     std::memcpy(b + H.off_star_units + sizeof(StarUnit) * P.star_suf_units.size(), P.star_lat_units.data(),
                 sizeof(StarUnit) * P.star_lat_units.size());
+  if (!P.star_q.empty()) std::memcpy(b + H.off_star_q, P.star_q.data(), sizeof(int32_t) * P.star_q.size());
   if (!F.subs.empty()) {  // the exact tier's own generic plan
     std::memcpy(b + H.wide_off_subs, F.subs.data(), sizeof(EstSub) * F.subs.size());
     if (!F.ops.empty()) std::memcpy(b + H.wide_off_ops, F.ops.data(), sizeof(EstOp) * F.ops.size());

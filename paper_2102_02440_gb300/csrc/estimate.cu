@@ -842,7 +842,8 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_estimate_finalize(const __
     int32_t slot = -1;
     if (ovf) {
       const uint32_t k = atomicAdd(A.wide_queue, 1u);
-      const uint32_t nch = uint32_t(max(1, A.wsubs[q].n_chunks));
+      const bool lat = wide_star_row(A, q);
+      const uint32_t nch = uint32_t(wide_row_units(A, q));
       const uint32_t cap = uint32_t(A.wide_unit_cap);
       // no reservation once the units are used up (the counter cannot wrap)
       const bool room = k < uint32_t(A.wide_qcap) && *reinterpret_cast<volatile uint32_t*>(A.wide_queue + 2) < cap;
@@ -850,9 +851,14 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_estimate_finalize(const __
       if (u0 < cap && nch <= cap - u0) {
         A.wide_queue[4 + k] = uint32_t(q * d + i);
         A.wide_row_start[k] = int32_t(u0);
-        for (uint32_t c = 0; c < nch; c++) A.wide_units[u0 + c] = (uint64_t(k) << 32) | c;
+        for (uint32_t c = 0; c < nch; c++) A.wide_units[u0 + c] = (uint64_t(k) << 32) | (lat ? kUnitLattice : c);
+        if (lat) {  // its lattice sums start from 0 (residues) and 0.0 (bound)
+          for (int j = 0; j <= kWideMods; j++) A.wide_part[int64_t(u0) * (kWideMods + 1) + j] = 0;
+          atomicAdd(A.wide_star_cnt + int64_t(sb.star) * d + i, 1u);
+        }
         slot = int32_t(k);
       } else {
+        if (k < uint32_t(A.wide_qcap)) A.wide_row_start[k] = -1;
         for (uint32_t c = u0; c < cap; c++) A.wide_units[c] = ~0ull;  // the part of the cap it took
         atomicOr(&lost, 1);
       }
@@ -926,6 +932,13 @@ cudaError_t launch_estimate(const EstArgs& a, const EstPlanHdr& H, double* est, 
   }
   if (a.n_sub > 0) {
     if (a.wide && cudaMemsetAsync(a.wide_queue, 0, 4 * sizeof(uint32_t), st) != cudaSuccess) return cudaGetLastError();
+    if (a.wide && a.n_star > 0 &&  // the star-row counters and flags (three arrays, back to back)
+        cudaMemsetAsync(a.wide_star_cnt, 0,
+                        size_t(reinterpret_cast<unsigned char*>(a.wide_star_kmax) -
+                               reinterpret_cast<unsigned char*>(a.wide_star_cnt)) +
+                            sizeof(int32_t) * size_t(a.n_star) * size_t(a.d),
+                        st) != cudaSuccess)
+      return cudaGetLastError();
     k_estimate_finalize<<<unsigned(a.n_sub), kFinalizeThreads, 0, st>>>(a, est, row_est, wide_rows);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

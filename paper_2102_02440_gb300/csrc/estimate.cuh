@@ -66,6 +66,7 @@ struct StarFam {
   int32_t k1, k2, m1, pad;  // k1 + k2 = K - 1; a lattice unit covers 2^m1 A-side subsets
   int64_t suf_off;          // suffix sums: [d][K][w + 1] int64 at star_suf + suf_off
   int64_t t_off;            // lattice: [d][K][2^(K-1)] at star_t + t_off (and star_tf)
+  int64_t q_off;            // star_q + q_off: [2^K] the sub-plan of each leaf set, -1: none
 };
 struct StarUnit {
   int32_t fam, row, a, blk;  // suffix units: a = the leaf b whose suffix sums are built, blk = -1
@@ -154,6 +155,7 @@ struct EstPlanHdr {
   // star families (CMP_EST_STAR_LATTICE): families, units (suffix units first)
   int64_t n_star, off_star, n_star_units, n_star_suf_units, off_star_units;
   int64_t star_suf_words, star_t_entries;  // workspace: int64 suffix sums, lattice entries
+  int64_t off_star_q, n_star_q;            // the families' leaf-set -> sub-plan tables (int32)
   // exact tier beyond int128 (wide = 1): every sub-plan planned on the generic path alone
   // (its own arrays when the main plan uses other paths, else the main plan's), evaluated
   // modulo kWideMods primes for the rows found beyond int128, with a magnitude bound
@@ -169,7 +171,7 @@ constexpr int32_t kWideUnitMax = 1 << 20;
 // extend it to this size when it is smaller)
 constexpr int64_t kWideScratchBudget = int64_t(256) << 20;
 constexpr uint64_t kEstPlanMagic = 0x434d504553544d54ull;  // "CMPESTMT"
-constexpr int32_t kEstPlanVersion = 7;
+constexpr int32_t kEstPlanVersion = 8;
 
 // Exact tier beyond int128: a row is evaluated modulo kWideMods primes p_j = 2^62 - c_j
 // (exact ring arithmetic: the contraction is sums of products of the counters, and the
@@ -215,6 +217,7 @@ struct EstArgs {
   int64_t* star_suf;
   i128* star_t;
   uint8_t* star_tf;     // 1: the lattice entry left int128
+  const int32_t* star_q;  // leaf set -> sub-plan, per family (StarFam.q_off)
   // exact tier beyond int128
   int32_t wide;
   const EstSub* wsubs;
@@ -231,7 +234,28 @@ struct EstArgs {
   uint64_t* wide_units;   // [unit_cap] (queued row << 32 | conditioning chunk); row ~0u: none
   uint64_t* wide_part;    // [unit_cap][kWideMods + 1]: the unit's residues, then its bound (double bits)
   void* wide_scratch;     // wide_grid areas of wide_scratch_per_cta bytes
+  // star rows beyond int128 evaluated on their family's lattice in modular arithmetic, per
+  // (family, sketch row), [n_star * d] each: rows queued, 1 when the lattice evaluates them,
+  // the most primes one of them needs
+  uint32_t* wide_star_cnt;
+  int32_t* wide_star_on;
+  int32_t* wide_star_kmax;
 };
+
+// Unit entries of the exact tier: (queued row << 32) | low word; the low word is a
+// conditioning chunk, or kUnitLattice: a star row's single unit, which its family's lattice
+// fills (the residues summed over its leaves a of T_a(S \ {a}), the largest of their bounds).
+constexpr uint32_t kUnitLattice = 0x80000000u;
+
+// A star sub-plan whose leaf set maps to it in its family's table: its queued rows are
+// evaluated on the family's lattice in modular arithmetic when enough rows of the (family,
+// sketch row) are queued (else by the generic contraction).
+__device__ __forceinline__ bool wide_star_row(const EstArgs& A, int64_t q) {
+  const int32_t f = A.subs[q].star;
+  return f >= 0 && A.star_q[A.star[f].q_off + A.subs[q].sbits] == int32_t(q);
+}
+// Units of a queued row of sub-plan q: one per conditioning chunk of its generic plan.
+__device__ __forceinline__ int wide_row_units(const EstArgs& A, int64_t q) { return max(1, A.wsubs[q].n_chunks); }
 
 // Round-to-nearest-even of (neg ? -1 : 1) * (top * 2^128 + mag) to binary64, from the
 // definition: the top 53 significant bits, then half-ulp and sticky bits.
@@ -304,7 +328,8 @@ inline size_t est_wide_bytes(const EstPlanHdr& H) {
   return align16(sizeof(uint32_t) * (4 + size_t(H.wide_qcap) + size_t(H.n_sub))) + align16(sizeof(int32_t) * rows) +
          align16(sizeof(i128) * rows) + align16(sizeof(int32_t) * size_t(H.wide_qcap)) +
          align16(sizeof(uint64_t) * size_t(H.wide_unit_cap)) +
-         align16(sizeof(uint64_t) * size_t(H.wide_unit_cap) * (kWideMods + 1));
+         align16(sizeof(uint64_t) * size_t(H.wide_unit_cap) * (kWideMods + 1)) +
+         3 * align16(sizeof(int32_t) * size_t(H.n_star) * size_t(H.d));
 }
 inline size_t est_fixed_bytes(const EstPlanHdr& H) {
   return align16(sizeof(i128) * size_t(H.n_items)) + align16(sizeof(int32_t) * size_t(H.n_items)) +
@@ -340,6 +365,7 @@ inline EstArgs est_args(const EstPlanHdr& H, const unsigned char* pd, unsigned c
   const size_t o_star = o_cache + est_cache_bytes(H) + align16(sizeof(int32_t) * size_t(H.n_jobs) * size_t(H.d));
   a.star = reinterpret_cast<const StarFam*>(pd + H.off_star);
   a.star_units = reinterpret_cast<const StarUnit*>(pd + H.off_star_units);
+  a.star_q = reinterpret_cast<const int32_t*>(pd + H.off_star_q);
   a.n_star = H.n_star;
   a.n_star_units = H.n_star_units;
   a.n_star_suf_units = H.n_star_suf_units;
@@ -368,6 +394,11 @@ inline EstArgs est_args(const EstPlanHdr& H, const unsigned char* pd, unsigned c
     const size_t o_start = o_in + align16(sizeof(i128) * rows);
     const size_t o_units = o_start + align16(sizeof(int32_t) * size_t(H.wide_qcap));
     const size_t o_part = o_units + align16(sizeof(uint64_t) * size_t(H.wide_unit_cap));
+    const size_t o_scnt = o_part + align16(sizeof(uint64_t) * size_t(H.wide_unit_cap) * (kWideMods + 1));
+    const size_t fam_rows = align16(sizeof(int32_t) * size_t(H.n_star) * size_t(H.d));
+    a.wide_star_cnt = H.wide ? reinterpret_cast<uint32_t*>(ws + o_scnt) : nullptr;
+    a.wide_star_on = H.wide ? reinterpret_cast<int32_t*>(ws + o_scnt + fam_rows) : nullptr;
+    a.wide_star_kmax = H.wide ? reinterpret_cast<int32_t*>(ws + o_scnt + 2 * fam_rows) : nullptr;
     a.wide_queue = H.wide ? reinterpret_cast<uint32_t*>(ws + o_wide) : nullptr;
     a.wide_slot = H.wide ? reinterpret_cast<int32_t*>(ws + o_slot) : nullptr;
     a.wide_in = H.wide ? reinterpret_cast<i128*>(ws + o_in) : nullptr;

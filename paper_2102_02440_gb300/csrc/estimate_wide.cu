@@ -13,6 +13,8 @@
 // over the d rows and rounds it once to double.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "est_arith.cuh"
 
 namespace cmpk {
@@ -26,6 +28,7 @@ struct ModArith {
   uint64_t p, c;
   using V = uint64_t;
   __device__ __forceinline__ V zero() const { return 0; }
+  __device__ __forceinline__ V one() const { return 1; }
   __device__ __forceinline__ V reduce63(uint64_t u) const {  // u < 2^63
     uint64_t r = (u & ((1ull << 62) - 1)) + (u >> 62) * c;
     return r >= p ? r - p : r;
@@ -35,6 +38,7 @@ struct ModArith {
     const V m = reduce63(uint64_t(0) - uint64_t(v));  // |v| <= 2^63: below 2^63 + 1, reduce63 holds
     return m ? p - m : 0;
   }
+  __device__ __forceinline__ V from_wide(int64_t v) const { return from(v); }
   __device__ __forceinline__ V add(V a, V b) const {
     const uint64_t s = a + b;
     return s >= p ? s - p : s;
@@ -53,7 +57,11 @@ struct ModArith {
 struct BoundArith {
   using V = double;
   __device__ __forceinline__ V zero() const { return 0.0; }
-  __device__ __forceinline__ V from(int64_t v) const { return fabs(double(v)); }  // int32 counters: exact
+  __device__ __forceinline__ V one() const { return 1.0; }
+  __device__ __forceinline__ V from(int64_t v) const { return fabs(double(v)); }  // |v| < 2^53: exact
+  __device__ __forceinline__ V from_wide(int64_t v) const {                      // any int64: rounded up
+    return __ull2double_ru(v < 0 ? uint64_t(0) - uint64_t(v) : uint64_t(v));
+  }
   __device__ __forceinline__ V add(V a, V b) const { return __dadd_ru(a, b); }
   __device__ __forceinline__ V mul(V a, V b) const { return __dmul_ru(a, b); }
 };
@@ -308,11 +316,15 @@ __device__ __forceinline__ int wide_mods_for(double B) {
   return k < 1 ? 1 : (k > kWideMods ? 0 : k);
 }
 
-// A queued row's bound: the sum, rounded upwards in unit order, of its units' bounds.
+// A queued row's bound: the sum, rounded upwards in unit order, of its units' bounds; for a
+// star row on its lattice, |S| times the largest bound of its terms T_a(S \ {a}).
 __device__ __forceinline__ double wide_row_bound(const EstArgs& A, uint32_t e) {
   const uint32_t qr = A.wide_queue[4 + e];
-  const int nch = max(1, A.wsubs[qr / uint32_t(A.d)].n_chunks);
+  const int nch = wide_row_units(A, qr / uint32_t(A.d));
   const uint64_t* part = A.wide_part + int64_t(A.wide_row_start[e]) * (kWideMods + 1);
+  if (uint32_t(A.wide_units[A.wide_row_start[e]]) & kUnitLattice)
+    return __dmul_ru(__longlong_as_double((long long)part[kWideMods]),
+                     double(__popc(A.subs[qr / uint32_t(A.d)].sbits)));
   double B = 0.0;
   for (int c = 0; c < nch; c++) B = __dadd_ru(B, __longlong_as_double((long long)part[int64_t(c) * (kWideMods + 1) + kWideMods]));
   return B;
@@ -337,6 +349,7 @@ __global__ void __launch_bounds__(kWideThreads, 4) k_estimate_wide(const __grid_
     const int j = pass == 0 ? kWideMods : int(g % per_unit);
     const uint64_t ent = A.wide_units[u];
     if (ent == ~0ull) continue;  // taken by a row that did not fit (its sub-plan is reported NaN)
+    if (uint32_t(ent) & kUnitLattice) continue;  // filled by its star family's lattice
     const uint32_t e = uint32_t(ent >> 32);
     const int ch = int(uint32_t(ent));
     if (pass == 1 && j >= wide_mods_for(wide_row_bound(A, e))) continue;  // block-uniform
@@ -370,6 +383,205 @@ __global__ void __launch_bounds__(kWideThreads, 4) k_estimate_wide(const __grid_
       }
     }
     if (threadIdx.x == 0) A.wide_part[u * (kWideMods + 1) + j] = result;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- star rows on the lattice
+// A queued star row S of family f and sketch row i has E_i(S) = sum_{a in S} T_a(S \ {a})
+// (the family's lattice, estimate_star.cu).  When the (family, row) has enough queued rows
+// that one lattice per modulus costs less than their generic contractions (K 2^(K-1)
+// multiply-adds per sorted position against about |S|^2 / 4 gathered products per row,
+// weighted 3 for the gathers), the family's lattice is evaluated again modulo each prime the
+// rows need and as a magnitude bound, and every entry T_a(V) whose leaf set V + {a} is a
+// queued row is added to that row's unit: its residue modulo p_j (an exact modular sum,
+// whatever the order) and its bound (the unit keeps the largest; the row's bound is |S|
+// times it).  Otherwise the row's unit runs the generic contraction.
+
+// Per queued star row: the route of its (family, row), taken from the count of its rows.
+__global__ void k_star_route(const __grid_constant__ EstArgs A) {
+  const uint32_t n_rows = min(A.wide_queue[0], uint32_t(A.wide_qcap));
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_rows || A.wide_row_start[e] < 0) return;
+  const uint32_t qr = A.wide_queue[4 + e];
+  const int64_t q = qr / uint32_t(A.d);
+  const int row = int(qr % uint32_t(A.d));
+  if (!wide_star_row(A, q)) return;
+  const int32_t f = A.subs[q].star;
+  const int K = A.star[f].K;
+  const int64_t fr = int64_t(f) * A.d + row;
+  const uint64_t cnt = A.wide_star_cnt[fr];
+  if (cnt * uint64_t(3 * K) >= (uint64_t(1) << (K + 1))) {
+    A.wide_star_on[fr] = 1;
+    return;
+  }
+  A.wide_units[A.wide_row_start[e]] = uint64_t(e) << 32;  // chunk 0 of its generic (tree) plan
+}
+
+// Per queued star row on a lattice: the most primes a row of its (family, row) needs.
+__global__ void k_star_kmax(const __grid_constant__ EstArgs A) {
+  const uint32_t n_rows = min(A.wide_queue[0], uint32_t(A.wide_qcap));
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_rows || A.wide_row_start[e] < 0) return;
+  if (!(uint32_t(A.wide_units[A.wide_row_start[e]]) & kUnitLattice)) return;
+  const uint32_t qr = A.wide_queue[4 + e];
+  const int64_t q = qr / uint32_t(A.d);
+  atomicMax(A.wide_star_kmax + int64_t(A.subs[q].star) * A.d + int(qr % uint32_t(A.d)),
+            wide_mods_for(wide_row_bound(A, e)));
+}
+
+template <class M>
+__device__ __forceinline__ M star_arith(int j);
+template <>
+__device__ __forceinline__ ModArith star_arith<ModArith>(int j) {
+  return ModArith{wide_p(j), wide_c(j)};
+}
+template <>
+__device__ __forceinline__ BoundArith star_arith<BoundArith>(int) {
+  return BoundArith{};
+}
+
+// The lattice units of the families with rows on their lattice, in arithmetic M: pass 0 the
+// magnitude bounds (M = BoundArith), pass 1 the residues modulo the primes their rows need
+// (one unit per prime).  The layout of a unit follows k_star_lattice: 2^m1 A-side subsets
+// (the block's high bits fixed) times 2^k2 B-side subsets, entries split over the threads,
+// sorted positions in chunks of kStarR.
+template <class M>
+__global__ void __launch_bounds__(kStarThreads) k_star_wide(const __grid_constant__ EstArgs A, int pass) {
+  using V = typename M::V;
+  constexpr int R = kStarR, NB = 1 << kStarMaxK2;
+  __shared__ V Bs[R * NB];
+  __shared__ V As[R * 16];
+  __shared__ V red[kStarThreads];
+  __shared__ V fv[(CMP_MAX_SKETCHES - 1) * R];
+  __shared__ V wv[R];
+  const int tid = threadIdx.x, w = A.w, d = A.d;
+  const int per = pass == 0 ? 1 : kWideMods;
+  const int64_t n_lat = A.n_star_units - A.n_star_suf_units;
+  for (int64_t g = blockIdx.x; g < n_lat * per; g += gridDim.x) {
+    const StarUnit u = A.star_units[A.n_star_suf_units + g / per];
+    const int j = pass == 0 ? kWideMods : int(g % per);
+    const int64_t fr = int64_t(u.fam) * d + u.row;
+    if (!A.wide_star_on[fr]) continue;  // block-uniform
+    if (pass == 1 && j >= A.wide_star_kmax[fr]) continue;
+    const M ar = star_arith<M>(j);
+    const StarFam F = A.star[u.fam];
+    const int K = F.K, k = K - 1, k1 = F.k1, k2 = F.k2, m1 = F.m1;
+    const int NV2 = 1 << k2, E = 1 << (m1 + k2);
+    const int Ep = E < kStarThreads ? E : kStarThreads;
+    const int L = kStarThreads / Ep, J = E / Ep;
+    const int es = tid % Ep, lane = tid / Ep;
+    const int64_t ro = int64_t(u.row) * w;
+    const EstIn xa = A.inputs[F.in_begin + u.a];
+    const int64_t* suf0 = A.star_suf + F.suf_off + int64_t(u.row) * K * (int64_t(w) + 1);
+    V acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; q++) acc[q] = ar.zero();
+    for (int r0 = 0; r0 < w; r0 += R) {
+      // 1. the chunk's factors f[b][r] (position b of U \ {a}) and w[r]
+      for (int q = tid; q < (k + 1) * R; q += kStarThreads) {
+        const int b = q / R, rr = q % R, r = r0 + rr;
+        if (b < k) {
+          V f = ar.zero();
+          if (r < w) {
+            const int ub = b < u.a ? b : b + 1;
+            const EstIn& xb = A.inputs[F.in_begin + ub];
+            const int32_t pos = __ldg(xa.rk + (int64_t(xb.tslot) * d + u.row) * w + r);
+            f = ar.from(suf0[int64_t(ub) * (w + 1) + pos]);  // |suffix sum| < 2^51
+          }
+          fv[b * R + rr] = f;
+        } else {
+          V wr = ar.zero();
+          if (r < w) {
+            const int32_t jj = __ldg(xa.perm + ro + r);
+            wr = ar.from_wide(int64_t(__ldg(xa.s + ro + jj)) * int64_t(__ldg(xa.msk + ro + jj)));
+          }
+          wv[rr] = wr;
+        }
+      }
+      __syncthreads();
+      // 2. table roots: B[r][0] = 1, A[r][0] = w(r) times the factors of the block's bits
+      for (int rr = tid; rr < R; rr += kStarThreads) {
+        Bs[rr * NB] = ar.one();
+        V v = wv[rr];
+        for (int i = 0; i < k1 - m1; i++)
+          if ((u.blk >> i) & 1) v = ar.mul(v, fv[(m1 + i) * R + rr]);
+        As[rr * 16] = v;
+      }
+      __syncthreads();
+      // 3. doubling: entries [h, 2h) from [0, h) times the factor of bit jj
+      const int steps = k2 > m1 ? k2 : m1;
+      for (int jj = 0; jj < steps; jj++) {
+        const int h = 1 << jj;
+        if (jj < k2)
+          for (int q = tid; q < h * R; q += kStarThreads) {
+            const int rr = q / h, idx = h + q % h;
+            Bs[rr * NB + idx] = ar.mul(Bs[rr * NB + idx - h], fv[(k1 + jj) * R + rr]);
+          }
+        if (jj < m1)
+          for (int q = tid; q < h * R; q += kStarThreads) {
+            const int rr = q / h, idx = h + q % h;
+            As[rr * 16 + idx] = ar.mul(As[rr * 16 + idx - h], fv[jj * R + rr]);
+          }
+        __syncthreads();
+      }
+      // 4. multiply-add over the chunk's positions
+#pragma unroll
+      for (int q = 0; q < 16; q++) {
+        if (q >= J) break;
+        const int e = es + Ep * q;
+        const int v1 = e >> k2, v2 = e & (NV2 - 1);
+        V s = acc[q];
+        for (int rr = lane; rr < R; rr += L) s = ar.add(s, ar.mul(As[rr * 16 + v1], Bs[rr * NB + v2]));
+        acc[q] = s;
+      }
+      __syncthreads();
+    }
+    // 5. lanes of one entry (L > 1 means J = 1): their sum
+    if (L > 1) {
+      red[tid] = acc[0];
+      __syncthreads();
+      if (lane == 0) {
+        V s = ar.zero();
+        for (int l = 0; l < L; l++) s = ar.add(s, red[es + Ep * l]);
+        acc[0] = s;
+      }
+      __syncthreads();
+    }
+    // 6. each entry T_a(V) to the unit of the queued row V + {a}, if there is one
+    if (lane == 0) {
+      const uint32_t n_rows = min(A.wide_queue[0], uint32_t(A.wide_qcap));
+#pragma unroll
+      for (int q = 0; q < 16; q++) {
+        if (q >= J) break;
+        const int e = es + Ep * q;
+        const int v1 = e >> k2, v2 = e & (NV2 - 1);
+        const uint32_t Vb = uint32_t((u.blk << m1) | v1) | (uint32_t(v2) << k1);
+        const uint32_t low = (1u << u.a) - 1u;
+        const uint32_t S = ((Vb & ~low) << 1) | (1u << u.a) | (Vb & low);
+        const int32_t sq = A.star_q[F.q_off + S];
+        if (sq < 0) continue;
+        const int64_t rq = int64_t(sq) * d + u.row;
+        const int32_t slot = A.wide_slot[rq];  // stale unless the row was queued by this call:
+        if (slot < 0 || uint32_t(slot) >= n_rows || A.wide_row_start[slot] < 0 ||
+            A.wide_queue[4 + slot] != uint32_t(rq))
+          continue;  // the queue entry decides
+        const int64_t unit = A.wide_row_start[slot];
+        if (!(uint32_t(A.wide_units[unit]) & kUnitLattice)) continue;
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(A.wide_part + unit * (kWideMods + 1) + j);
+        if constexpr (std::is_same<V, double>::value) {
+          atomicMax(dst, (unsigned long long)__double_as_longlong(acc[q]));  // >= 0: bits order as values
+        } else {
+          const uint64_t p = wide_p(j);
+          unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(dst), seen;
+          do {  // (old + v) mod p; both below p < 2^62
+            seen = old;
+            const uint64_t s = uint64_t(seen) + acc[q];
+            old = atomicCAS(dst, seen, (unsigned long long)(s >= p ? s - p : s));
+          } while (old != seen);
+        }
+      }
+    }
     __syncthreads();
   }
 }
@@ -490,7 +702,7 @@ __global__ void __launch_bounds__(kWideFinThreads) k_estimate_wide_finalize(cons
         const int K = wide_mods_for(wide_row_bound(A, uint32_t(slot)));
         if (K == 0) atomicOr(&bad, 1);
         // the row's residues: its units' residues summed modulo each prime
-        const int nch = max(1, A.wsubs[q].n_chunks);
+        const int nch = wide_row_units(A, q);
         const uint64_t* part = A.wide_part + int64_t(A.wide_row_start[slot]) * (kWideMods + 1);
         uint64_t r[kWideMods];
         for (int j = 0; j < K; j++) {
@@ -616,7 +828,19 @@ __global__ void __launch_bounds__(kWideFinThreads) k_estimate_wide_finalize(cons
 
 cudaError_t launch_estimate_wide(const EstArgs& a, double* est, int64_t* wide_rows, cudaStream_t st) {
   if (!a.wide) return cudaSuccess;
+  // star rows on their families' lattices (only when the plan has lattice units)
+  const bool lat = a.n_star_units > a.n_star_suf_units;
+  const unsigned row_blocks = unsigned((a.wide_qcap + 255) / 256);
+  const unsigned lat_grid = unsigned(sm_count()) * 4;
+  if (lat) {
+    k_star_route<<<row_blocks, 256, 0, st>>>(a);
+    k_star_wide<BoundArith><<<lat_grid, kStarThreads, 0, st>>>(a, 0);
+  }
   k_estimate_wide<<<unsigned(a.wide_grid), kWideThreads, 0, st>>>(a, 0);  // bounds
+  if (lat) {
+    k_star_kmax<<<row_blocks, 256, 0, st>>>(a);
+    k_star_wide<ModArith><<<lat_grid, kStarThreads, 0, st>>>(a, 1);
+  }
   k_estimate_wide<<<unsigned(a.wide_grid), kWideThreads, 0, st>>>(a, 1);  // residues
   k_estimate_wide_finalize<<<unsigned(sm_count()), kWideFinThreads, 0, st>>>(a, est, wide_rows);
   return cudaGetLastError();

@@ -117,6 +117,29 @@ def test_triangle_beyond_int128(orc):
     _check_exact(orc, dw, [0b111111, 0b000111, 0b001111], [0, K.CMP_EST_GENERIC_ONLY])
 
 
+@pytest.mark.parametrize("huge", [[1, 2, 3], [1, 2, 3, 4], [1, 2, 3, 4, 5]])
+def test_star_rows_on_the_lattice_or_generic(orc, huge):
+    """A 10-leaf star (w = 8), sketch row 0 at 2^31 - 1 on the edges in `huge` and small
+    elsewhere: 1 to 5, 68 or 202 of its leaf subsets leave int128 in row 0.  With the star
+    lattice, below the break-even count those rows run the generic contraction; above it the
+    family's lattice runs again modulo each needed prime and as a bound, its entries summed
+    into the rows.  Rows equal the oracle's either way."""
+    n = 10
+    eu, ev = [0] * n, list(range(1, n + 1))
+    dw = _one_row_tables(eu, ev, n + 1, 3, 8)
+    rng = np.random.default_rng(4)
+    host = [rng.integers(1, 4, size=tuple(t.counters.shape)) for t in dw.tables]
+    for e in huge:
+        for end in range(2):
+            t, k = dw.wl.sketch_of(e, end)
+            host[t][k, 0, :] = 2 ** 31 - 1
+    dw.host_counters = [a.astype(np.int32) for a in host]
+    for t, a in zip(dw.tables, dw.host_counters):
+        t.counters.copy_(torch.from_numpy(a))
+    masks = G.connected_subplans(n + 1, eu, ev)
+    _check_exact(orc, dw, masks, [K.CMP_EST_STAR_LATTICE, 0])
+
+
 def test_cancelling_signs_and_ties(orc):
     """Random counters of both signs near +-2^31, with zeros and equal magnitudes (ties),
     on a cycle with a leaf and a chain: products far beyond int128 whose sums cancel; even d
