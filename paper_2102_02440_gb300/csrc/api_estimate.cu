@@ -762,9 +762,12 @@ cmp_status plan_all(const cmp_graph* graphs, int32_t n_graphs, int32_t d, int32_
     H->wide_scratch_per_cta = int64_t(align16(
         sizeof(uint64_t) * size_t(int64_t(G.max_slots) * w + int64_t(G.max_suf) * (int64_t(w) + 1) +
                                   int64_t(std::max(G.max_in, 1)) * (int64_t(w) + 1))));
-    // its own grid: four CTAs per SM, as many as fit in kWideScratchBudget (at least one)
+    // its own grid: kWideCtasPerSm CTAs per SM, as many as fit in kWideScratchBudget, and no
+    // more than its (unit, prime) jobs (at least one)
     H->wide_grid = int32_t(std::max<int64_t>(
-        1, std::min<int64_t>(int64_t(sm_count()) * 4, kWideScratchBudget / std::max<int64_t>(H->wide_scratch_per_cta, 1))));
+        1, std::min<int64_t>({int64_t(sm_count()) * kWideCtasPerSm,
+                              kWideScratchBudget / std::max<int64_t>(H->wide_scratch_per_cta, 1),
+                              int64_t(H->wide_unit_cap) * kWideMods})));
   }
   H->total_bytes = int64_t(off);
   H->max_suf = P->max_suf;

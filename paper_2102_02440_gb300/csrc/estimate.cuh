@@ -166,6 +166,7 @@ struct EstPlanHdr {
   int32_t wide_unit_cap, pad2;  // (row, conditioning chunk) units the tier can take per call
 };
 constexpr int32_t kWideQueueMax = 1 << 19;
+constexpr int32_t kWideCtasPerSm = 8;  // the tier's generic kernel: 128-thread CTAs, 8 per SM
 constexpr int32_t kWideUnitMax = 1 << 20;
 // scratch of the exact tier's own grid (its CTA areas reuse the estimate's scratch region and
 // extend it to this size when it is smaller)

@@ -13,6 +13,7 @@
 // over the d rows and rounds it once to double.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "est_arith.cuh"
@@ -42,6 +43,12 @@ struct ModArith {
   __device__ __forceinline__ V add(V a, V b) const {
     const uint64_t s = a + b;
     return s >= p ? s - p : s;
+  }
+  __device__ __forceinline__ V reduce128(u128 x) const {  // any x < 2^128 (e.g. 16 products)
+    const u128 H = x >> 62;                                              // < 2^66
+    const u128 y = H * c + (uint64_t(x) & ((1ull << 62) - 1));           // < 2^76 + 2^62
+    const uint64_t z = (uint64_t(y) & ((1ull << 62) - 1)) + uint64_t(y >> 62) * c;  // < 2^62 + 2^24
+    return z >= p ? z - p : z;
   }
   __device__ __forceinline__ V mul(V a, V b) const {
     const uint64_t lo = a * b, hi = __umul64hi(a, b);
@@ -138,7 +145,7 @@ __device__ __forceinline__ const int32_t* wrank_row(const EstIn& x, const EstIn&
   return x.rk + (int64_t(y.tslot) * d + row) * w;
 }
 
-constexpr int kWideThreads = 256;
+constexpr int kWideThreads = 128;  // latency-bound contractions: more small CTAs in flight
 
 // Conditioning chunk ch of one row of sub-plan sb (its item it0 + ch) in arithmetic ar.
 template <class M>
@@ -332,7 +339,7 @@ __device__ __forceinline__ double wide_row_bound(const EstArgs& A, uint32_t e) {
 
 // Persistent over the units of the queued rows: pass 0 computes every unit's bound, pass 1
 // its residues modulo the primes its row needs (the others are skipped).
-__global__ void __launch_bounds__(kWideThreads, 4) k_estimate_wide(const __grid_constant__ EstArgs A, int pass) {
+__global__ void __launch_bounds__(kWideThreads, kWideCtasPerSm) k_estimate_wide(const __grid_constant__ EstArgs A, int pass) {
   __shared__ EstOp sh_ops[kEstMaxOps];
   __shared__ EstIn sh_in[kEstMaxSubIn];
   __shared__ uint64_t sh_u[33];
@@ -525,15 +532,22 @@ __global__ void __launch_bounds__(kStarThreads) k_star_wide(const __grid_constan
           }
         __syncthreads();
       }
-      // 4. multiply-add over the chunk's positions
+      // 4. multiply-add over the chunk's positions (residues: the at most kStarR products of
+      //    a lane summed exactly in 128 bits, below 2^128, then reduced once)
 #pragma unroll
       for (int q = 0; q < 16; q++) {
         if (q >= J) break;
         const int e = es + Ep * q;
         const int v1 = e >> k2, v2 = e & (NV2 - 1);
-        V s = acc[q];
-        for (int rr = lane; rr < R; rr += L) s = ar.add(s, ar.mul(As[rr * 16 + v1], Bs[rr * NB + v2]));
-        acc[q] = s;
+        if constexpr (std::is_same<M, ModArith>::value) {
+          u128 s = 0;
+          for (int rr = lane; rr < R; rr += L) s += u128(As[rr * 16 + v1]) * Bs[rr * NB + v2];
+          acc[q] = ar.add(acc[q], ar.reduce128(s));
+        } else {
+          V s = acc[q];
+          for (int rr = lane; rr < R; rr += L) s = ar.add(s, ar.mul(As[rr * 16 + v1], Bs[rr * NB + v2]));
+          acc[q] = s;
+        }
       }
       __syncthreads();
     }
@@ -831,7 +845,8 @@ cudaError_t launch_estimate_wide(const EstArgs& a, double* est, int64_t* wide_ro
   // star rows on their families' lattices (only when the plan has lattice units)
   const bool lat = a.n_star_units > a.n_star_suf_units;
   const unsigned row_blocks = unsigned((a.wide_qcap + 255) / 256);
-  const unsigned lat_grid = unsigned(sm_count()) * 4;
+  const unsigned lat_grid =
+      unsigned(std::min<int64_t>(int64_t(sm_count()) * 4, (a.n_star_units - a.n_star_suf_units) * kWideMods));
   if (lat) {
     k_star_route<<<row_blocks, 256, 0, st>>>(a);
     k_star_wide<BoundArith><<<lat_grid, kStarThreads, 0, st>>>(a, 0);
