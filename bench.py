@@ -768,12 +768,14 @@ def measure(a, wl, dev, world: int, rank: int, headline: bool):
         h2d = sum(c.numel() * c.element_size() for tc in host_cols for c in tc)
         out_host = torch.empty(n_sub, dtype=torch.float64).pin_memory()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        tms = []
+        e_up = torch.cuda.Event(enable_timing=True)
+        tms, tups = [], []
         with torch.cuda.stream(stream):
             for k in range(min(a.warmup, 2) + a.steps):
                 flush.zero_()
                 e0.record(stream)
                 dw.upload(host_cols, stream=stream)
+                e_up.record(stream)
                 if graph is not None:
                     graph.replay()
                 else:
@@ -783,9 +785,12 @@ def measure(a, wl, dev, world: int, rank: int, headline: bool):
                 e1.synchronize()
                 if k >= min(a.warmup, 2):
                     tms.append(e0.elapsed_time(e1))
+                    tups.append(e0.elapsed_time(e_up))
         e2e_ms = _max_over_ranks(statistics.mean(tms), world)
+        up_ms = statistics.mean(tups)
         out["e2e"] = {"value": rows * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                      "d2h_bytes_per_step": int(out_host.numel() * 8), "ms_per_step": e2e_ms}
+                      "d2h_bytes_per_step": int(out_host.numel() * 8), "ms_per_step": e2e_ms,
+                      "h2d_ms": up_ms, "h2d_gbs": h2d / (up_ms / 1e3) / 1e9}
         del host_cols
     if headline and rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, masks)
