@@ -35,9 +35,12 @@ namespace {
 constexpr int kRunWords = int(kDenseRun / 32);
 constexpr int kRuns = 2;  // runs per thread in flight: independent difference chains
 
-// Lazy residues: folded values v <= 2^61 + 3 with v = the residue (mod p).  A sum of
-// operands below 2^63 folds, (s mod 2^61) + (s >> 61), back to <= 2^61 + 3.  D2 is folded
-// every other step only: unfolded it stays below 2^62 + 7, and D1 + D2 below 2^63.
+// Lazy residues: folded values v <= 2^61 + 3 with v = the residue (mod p).  A sum s below
+// 2^64 folds, (s mod 2^61) + (s >> 61), back to <= 2^61 + 7, and below 2^63 to <= 2^61 + 3.
+// D1 and D2 are folded at odd steps only (each 32-key word starts at an even step): after an
+// even step both are sums of two folded values, below 2^62 + 8, so at the odd step P + D1
+// stays below 2^63 and D1 + D2 below 2^63 + 16; P is folded at every step (its residue
+// gives the sign).
 __device__ __forceinline__ uint64_t add_lazy(uint64_t u, uint64_t v) { return fold61(u + v); }
 __device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b) { return a >= b ? a - b : a + kP61 - b; }
 
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_dense_hash(const __g
               }
               m[u] >>= 1;
               st[u].P = add_lazy(st[u].P, st[u].D1);
-              st[u].D1 = add_lazy(st[u].D1, st[u].D2);
+              st[u].D1 = (b & 1) ? add_lazy(st[u].D1, st[u].D2) : st[u].D1 + st[u].D2;
               st[u].D2 = (b & 1) ? add_lazy(st[u].D2, D3[u]) : st[u].D2 + D3[u];
               st[u].B = add_lazy(st[u].B, a_step);
             }
