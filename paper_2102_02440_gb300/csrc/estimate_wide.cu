@@ -587,12 +587,15 @@ __global__ void __launch_bounds__(kStarThreads) k_star_wide(const __grid_constan
           atomicMax(dst, (unsigned long long)__double_as_longlong(acc[q]));  // >= 0: bits order as values
         } else {
           const uint64_t p = wide_p(j);
-          unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(dst), seen;
-          do {  // (old + v) mod p; both below p < 2^62
+          unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(dst), seen = ~0ull;
+          // (old + v) mod p, both below p < 2^62; a failed exchange means another leaf's add
+          // landed (at most |S| - 1 of them), so the bound is never reached
+          for (int tries = 0; tries < 1024 && old != seen; tries++) {
             seen = old;
             const uint64_t s = uint64_t(seen) + acc[q];
             old = atomicCAS(dst, seen, (unsigned long long)(s >= p ? s - p : s));
-          } while (old != seen);
+          }
+          if (old != seen) set_status(A.status, CMP_ETIMEOUT);
         }
       }
     }
