@@ -312,15 +312,17 @@ typedef struct {
  *   row_est_dev  NULL or [n_sub][d][2] int64: each exact row estimate as a little-endian
  *                two's-complement int128 (low word first); unspecified for the rows of a
  *                sub-plan that has a row beyond int128 (see below)
- * Exact range.  Rows are evaluated in int128 (int64 storage where it suffices).  When a
- * row, or an intermediate value of its evaluation, leaves int128, every row of that
- * sub-plan is evaluated again, exactly, by a second tier: on the generic path, modulo 16
- * primes p_j = 2^62 - c_j, and in double on magnitudes rounded upwards (a bound B on |E|);
- * when B < 2^990 (below half the primes' product) the row is the unique integer with those
- * residues (Garner's algorithm), and est is its exact median rounded once.  est is NaN and
- * the status gets CMP_EOVERFLOW only when B >= 2^990, or when more than min(n_sub d, 2^19)
- * rows of one call need the tier.  Flag CMP_EST_NO_WIDE turns the tier off (rows beyond
- * int128 are then NaN with CMP_EOVERFLOW). */
+ * Exact range.  Rows are evaluated in int128 (int64 storage where it suffices).  A row whose
+ * value, or an intermediate value of its evaluation, leaves int128 is evaluated again,
+ * exactly, by a second tier (the sub-plan's other rows keep their int128 values): on the
+ * generic path, one unit per conditioning chunk, modulo 16 primes p_j = 2^62 - c_j, and in
+ * double on magnitudes rounded upwards (a bound B on |E|); when B < 2^990 (below half the
+ * primes' product) the row is the unique integer with those residues (Garner's algorithm),
+ * and est is the exact median of the rows rounded once.  est is NaN and the status gets
+ * CMP_EOVERFLOW only when B >= 2^990, or when more than min(n_sub d, 2^19) rows, or more
+ * than min(d x the plan's conditioning chunks, 2^20) units, of one call need the tier.
+ * Flag CMP_EST_NO_WIDE turns the tier off (rows beyond int128 are then NaN with
+ * CMP_EOVERFLOW). */
 /* Estimate launch shape; zero fields choose automatically.
  * Sub-plans whose only cycle is a triangle, with every other table a leaf of one of its
  * three tables, are evaluated by the triangle path: the conditioned sum regrouped as
@@ -350,7 +352,10 @@ typedef struct {
  * when K 2^(K-1) <= 2 sum_S |S|^2 over its requested stars (it is dense enough); other
  * sub-plans are planned as without the flag.  Rows that stay in int128 are the same exact
  * integers; a row where an intermediate value left int128 is passed to the exact tier
- * (cmp_estimate, "Exact range"), which evaluates it on the generic path. */
+ * (cmp_estimate, "Exact range").  When enough rows of one (family, sketch row) reach it
+ * (count x 3K >= 2^(K+1)), the tier evaluates the family's lattice again modulo each prime
+ * they need and as a magnitude bound, and sums each row's entries; otherwise it evaluates
+ * the rows on the generic path.  Either way the rows are the same exact integers. */
 #define CMP_EST_STAR_LATTICE 4
 #define CMP_EST_NO_WIDE 8
 typedef struct {
