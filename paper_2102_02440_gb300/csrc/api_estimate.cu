@@ -476,14 +476,23 @@ cmp_status plan_sub(const cmp_graph& g, int32_t gi, uint64_t mask, int32_t d, in
   sb.cond = cond.empty() ? 0 : 1;
   const int32_t nv = int32_t(n_cond_vals);
   sb.n_chunks = cond.empty() ? 1 : int32_t((int64_t(nv) + chunk - 1) / chunk);
+  // a wide tree whose only operation is a root with two or more inputs: its row is a sum over
+  // the root's sorted positions, split into kRootSplit chunks (one CTA each)
+  sb.split = cond.empty() && sb.n_ops == 1 && w >= kRootSplitMinW && P->ops[sb.op_begin].k >= 2 ? 1 : 0;
+  if (sb.split) sb.n_chunks = kRootSplit;
   P->subs.push_back(sb);
   for (int i = 0; i < d; i++)
     for (int ch = 0; ch < sb.n_chunks; ch++) {
       EstItem it;
       it.sub = sub_index;
       it.row = i;
-      it.c0 = cond.empty() ? 0 : int32_t(int64_t(ch) * chunk);
-      it.c1 = cond.empty() ? 1 : int32_t(std::min<int64_t>(nv, int64_t(ch + 1) * chunk));
+      if (sb.split) {
+        it.c0 = int32_t(int64_t(w) * ch / kRootSplit);
+        it.c1 = int32_t(int64_t(w) * (ch + 1) / kRootSplit);
+      } else {
+        it.c0 = cond.empty() ? 0 : int32_t(int64_t(ch) * chunk);
+        it.c1 = cond.empty() ? 1 : int32_t(std::min<int64_t>(nv, int64_t(ch + 1) * chunk));
+      }
       P->items.push_back(it);
     }
   return CMP_OK;

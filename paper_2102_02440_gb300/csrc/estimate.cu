@@ -523,7 +523,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_estimate_items(const __grid_cons
 
     i128 acc = 0;
     bool ovf = false;
-    for (int c = item.c0; c < item.c1; c++) {
+    // a split root: one pass, the root's sorted positions [r_lo, r_hi) of this item
+    const int c_end = sb.split ? item.c0 + 1 : item.c1;
+    const int r_lo = sb.split ? item.c0 : 0, r_hi = sb.split ? item.c1 : w;
+    for (int c = item.c0; c < c_end; c++) {
       if (pre_ok) {
         if (sh_skip[c - item.c0]) continue;  // block-uniform
       } else {
@@ -636,12 +639,13 @@ __global__ void __launch_bounds__(MAXT, MINB) k_estimate_items(const __grid_cons
           const i128* gm = x.kind == kInCache ? A.cache + (int64_t(x.slot) * A.d + item.row) * w : nullptr;
           S* pl = pre + int64_t(a) * W1;
           bool o2 = false, so2 = false;
-          for (int r0 = tid; r0 < w; r0 += kIlp * T) {
+          const int rb = p < 0 ? r_lo : 0, re = p < 0 ? r_hi : w;  // (a split sub-plan's op is its root)
+          for (int r0 = rb + tid; r0 < re; r0 += kIlp * T) {
             int jj[kIlp];
             bool ok[kIlp];
 #pragma unroll
             for (int u = 0; u < kIlp; u++) {
-              ok[u] = r0 + u * T < w;
+              ok[u] = r0 + u * T < re;
               jj[u] = ok[u] ? __ldg(perm + r0 + u * T) : 0;
             }
             int64_t sv[kIlp], mv[kIlp];

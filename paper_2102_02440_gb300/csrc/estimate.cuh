@@ -50,8 +50,11 @@ struct EstSub {
   int32_t job;        // >= 0: a cached subtree message (its index), not a sub-plan
   int32_t star;       // >= 0: a star of that family, its rows gathered from the family's lattice
   uint32_t sbits;     // star: its leaf edges, bit u = edge u of the family (ascending edge id)
-  int32_t pad;
+  int32_t split;      // 1: a tree whose only operation is the root; its chunks split the root's
+                      // sorted positions (item [c0, c1)), each recomputing the leaf suffix sums
 };
+constexpr int32_t kRootSplitMinW = 16384;  // widths from which such roots are split
+constexpr int32_t kRootSplit = 8;          // chunks of sorted positions per row
 
 // Star families (sub-plans whose only operation is the root joined to leaves, grouped by
 // graph and root).  For the family's K leaf edges U (ascending id), sketch row i and the

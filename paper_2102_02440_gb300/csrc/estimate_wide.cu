@@ -190,7 +190,10 @@ __device__ typename M::V wide_row(const M& ar, const EstArgs& A, const EstSub& s
   V total = ar.zero();
   {
     const EstItem item = A.witems[sb.item_begin + int64_t(row) * sb.n_chunks + ch];
-    for (int c = item.c0; c < item.c1; c++) {
+    // a split root: one pass over the root's sorted positions [r_lo, r_hi) of this chunk
+    const int c_end = sb.split ? item.c0 + 1 : item.c1;
+    const int r_lo = sb.split ? item.c0 : 0, r_hi = sb.split ? item.c1 : w;
+    for (int c = item.c0; c < c_end; c++) {
       bool zero = false;
       for (int q = 0; q < n_cond; q++) zero |= __ldg(cond_s[q] + cond_digit(c, cond_k[q], w)) == 0;
       if (zero) continue;  // block-uniform: every merged entry through that table is 0
@@ -255,7 +258,8 @@ __device__ typename M::V wide_row(const M& ar, const EstArgs& A, const EstSub& s
           const uint32_t* absa = x.abs + ro;
           const V* msg = x.kind == kInSlot ? slots + int64_t(x.slot) * w : nullptr;
           V* pl = pre + int64_t(a) * W1;
-          for (int r = tid; r < w; r += T) {
+          const int rb = p < 0 ? r_lo : 0, re = p < 0 ? r_hi : w;  // (a split sub-plan's op is its root)
+          for (int r = rb + tid; r < re; r += T) {
             const int j = __ldg(perm + r);
             V v = ar.mul(ar.from(__ldg(x.s + ro + j)), msg ? msg[j] : ar.from(__ldg(x.msk + ro + j)));
             for (int b = 0; b < m; b++) {

@@ -267,3 +267,31 @@ def test_cross_ranks_multi_equals_per_table():
             torch.cuda.synchronize()
             assert torch.equal(one, multi[roff:roff + k * k])
         off, roff, e = off + k, roff + k * k, e + k
+
+
+@pytest.mark.parametrize("w", [16384, 20011])
+def test_wide_star_roots_split_over_chunks(orc, w):
+    """At w >= 16384 a tree whose only operation is a root with two or more inputs (a star)
+    is split into chunks of the root's sorted positions, each recomputing the leaf suffix
+    sums; ragged chunk ends at w = 20011.  Its rows equal the oracle's, beside unsplit
+    sub-plans (pairs, a chain through the root) in the same plan."""
+    eu, ev, nt = [0, 0, 0, 3], [1, 2, 3, 4], 5
+    rng = np.random.default_rng(w)
+    tabs = []
+    for t in range(nt):
+        n = int(rng.integers(20_000, 200_000))
+        cols, kc, ei = [], [], []
+        for e in range(len(eu)):
+            if t in (eu[e], ev[e]):
+                cols.append(G.zipf_keys(rng, n, 50_000, float(rng.uniform(0.6, 1.3))))
+                kc.append(len(cols) - 1)
+                ei.append(e)
+        tabs.append(G.Table(f"T{t}", cols, [], kc, ei))
+    wl = G.Workload("star_wide", tabs, eu, ev, 3, w, 4711 + w, 0)
+    dw = P.DeviceWorkload(wl)
+    dw.build()
+    masks = [0b00111, 0b01011, 0b01111, 0b00011, 0b11001, 0b11111, 0b11000]
+    est = P.DeviceEstimator(dw, masks)
+    est.presort()
+    est.estimate()
+    _check(orc, dw, est, masks)

@@ -140,6 +140,20 @@ def test_star_rows_on_the_lattice_or_generic(orc, huge):
     _check_exact(orc, dw, masks, [K.CMP_EST_STAR_LATTICE, 0])
 
 
+def test_split_star_root_beyond_int128(orc):
+    """A three-leaf star at w = 16384 (its root split into chunks of sorted positions) with
+    counters near 2^31 - 1: every row leaves int128, and the exact tier evaluates it as one
+    unit per chunk."""
+    eu, ev = [0, 0, 0], [1, 2, 3]
+    dw = _one_row_tables(eu, ev, 4, 3, 16384)
+    rng = np.random.default_rng(8)
+
+    def f(shape):
+        return rng.choice(np.array([2 ** 31 - 1, -(2 ** 31 - 1), 2 ** 31 - 3, 0, 7]), size=shape)
+    _fill(dw, f)
+    _check_exact(orc, dw, [0b1111, 0b0111], [0, K.CMP_EST_GENERIC_ONLY])
+
+
 def test_cancelling_signs_and_ties(orc):
     """Random counters of both signs near +-2^31, with zeros and equal magnitudes (ties),
     on a cycle with a leaf and a chain: products far beyond int128 whose sums cancel; even d
