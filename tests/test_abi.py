@@ -559,3 +559,25 @@ def test_sorted_tables_rule():
     assert P.sorted_tables(5, *back, [0b10001, 0b10010]) == {0, 1}
     assert P.sorted_tables(5, *back, [0b10011]) == {0, 4}
     assert P.sorted_tables(5, *back, [0b00001, 0b10000]) == set()  # single tables read no sketch
+
+
+def test_estimate_plan_items_of_split_roots_and_cycle_ranks(K):
+    """Work items per sketch row: one for a tree; kRootSplit (8) for a tree whose only
+    operation is a root with two or more inputs once w >= 16384 (a star's sorted positions
+    in chunks), not for a two-table sub-plan; ceil(w^rho / chunk) for rho conditioned edges."""
+    d = 5
+    star = _graph(K, [0, 0, 0], [1, 2, 3], 4)
+    for w, per_star in ((8192, 1), (16384, 8), (65536, 8)):
+        st, _ = _plan_stats(K, [star], d, w, [0, 0, 0], [0b1111, 0b0111, 0b0011])
+        assert st.n_items == d * (2 * per_star + 1), (w, st.n_items)
+    chain = _graph(K, [0, 1], [1, 2], 3)   # rooted at table 0: two operations, never split
+    st, _ = _plan_stats(K, [chain], d, 65536, [0], [0b111])
+    assert st.n_items == d
+    k4 = _graph(K, [0, 0, 0, 1, 1, 2], [1, 2, 3, 2, 3, 3], 4)
+    for mask, rho in ((0b1111, 3), (0b0111, 1)):
+        cfg = K.cmp_estimate_cfg.make(cond_chunk=1000, flags=K.CMP_EST_GENERIC_ONLY)
+        pb, _ = K.cmp_estimate_plan_bytes([k4], d, 64, [0], [mask], cfg)
+        buf = np.zeros(pb, np.uint8)
+        K.cmp_estimate_plan_encode([k4], d, 64, [0], [mask], buf.ctypes.data, pb, cfg)
+        st = K.cmp_estimate_plan_stats(buf.ctypes.data)
+        assert st.n_items == d * -(-64 ** rho // 1000), (rho, st.n_items)
