@@ -281,6 +281,7 @@ struct BuildPlanParts {
   int64_t cnt_total_chunks = 0;
   int32_t cnt_grid = 0;
   int64_t cnt_split = 0;  // > 0: two launches, the tables with presence columns first
+  int32_t d_cut = 1024;   // split pass: the dense kernel's share beside the second counting launch
   int32_t cnt_grid_b = 0;
   int64_t hash_total_chunks = 0;
   int32_t hash_max_pairs = 1, hash_grid = 0;
@@ -657,10 +658,30 @@ static cmp_status plan_layout(const cmp_table* tables, int32_t n_tables, int32_t
   // first, then the rest with one CTA per SM and the dense kernel beside it
   P->cnt_split = 0;
   P->cnt_grid_b = 0;
+  P->d_cut = 1024;
   if (!P->ditems.empty() && P->uitems.empty() && presence_chunks > 0 && presence_chunks < P->cnt_total_chunks) {
     P->cnt_split = presence_chunks;
     P->cnt_grid = int32_t(std::min<int64_t>(presence_chunks, int64_t(sm_count()) * 2));
     P->cnt_grid_b = int32_t(std::min<int64_t>(P->cnt_total_chunks - presence_chunks, int64_t(sm_count())));
+    // The dense kernel's share beside the second counting launch: the part it walks while
+    // that launch scans (the rest runs after it, two warps per scheduler instead of one).  The
+    // scan's time is its columns' bytes at ~4.7 TB/s; the walk beside it advances at ~0.7 of
+    // its ~320 G key x row steps/s alone (GB300 measurements of the 1e9-row workload, whose
+    // best share, 0.75, this gives).
+    double bytes_b = 0, steps = 0;
+    for (const CountItem& ci : P->cnt_items) {
+      if (ci.chunk_begin < presence_chunks) continue;
+      const cmp_table& tb = tables[ci.table];
+      uint32_t used = 0;  // referenced columns: aggregated keys and predicates
+      for (int32_t c = 0; c < CMP_MAX_COLS; c++)
+        if (P->col_agg[ci.table][c] >= 0) used |= 1u << c;
+      for (int32_t p = 0; p < tb.n_preds; p++) used |= 1u << tb.preds[p].col;
+      for (int32_t c = 0; c < tb.n_cols && c < 32; c++)
+        if ((used >> c) & 1u) bytes_b += double(tb.n_rows) * (tb.cols[c].dtype == CMP_I64 ? 8.0 : 4.0);
+    }
+    for (const UniqSlab& sl : P->dslabs) steps += double(P->aggs[sl.pad].cap) * sl.n_pairs;
+    const double share = steps > 0 ? 0.7 * (bytes_b / 4.7e12) / (steps / 3.2e11) : 1.0;
+    P->d_cut = int32_t(std::max(1.0, std::min(1024.0, std::round(share * 1024.0))));
   }
   s.grid = int32_t(P->cta_item.size());
   s.ctas_per_slab = 0;
@@ -760,6 +781,7 @@ extern "C" cmp_status cmp_build_plan_encode(const cmp_table* tables, int32_t n_t
   h.cnt_grid = P.cnt_grid;
   h.cnt_split = P.cnt_split;
   h.cnt_grid_b = P.cnt_grid_b;
+  h.d_cut = P.d_cut;
   h.cnt_threads = 512;
   h.cnt_cache_slots = P.cache_slots;
   h.cnt_cache_cols = P.cache_cols;
@@ -856,9 +878,18 @@ extern "C" cmp_status cmp_sketch_build_batched(const void* plan_host, const void
     if (launch_agg_count(a, h.shape.tile_rows, h.cnt_threads, h.cnt_grid, 0, 0, h.cnt_split, cs) != cudaSuccess ||
         launch_presence_check(a, cs) != cudaSuccess ||
         launch_agg_count(a, h.shape.tile_rows, h.cnt_threads, h.cnt_grid_b, 2, h.cnt_split, h.cnt_total_chunks, cs) !=
-            cudaSuccess ||
-        launch_dense(a, d_grid, true, kDenseThreadsBeside, cs) != cudaSuccess)
+            cudaSuccess)
       return CMP_ECUDA;
+    // the dense kernel: its share beside the counting launch, then the rest with 512 threads
+    // (programmatic dependents both: the second takes each SM the first two leave)
+    BuildArgs b = a;
+    b.dense_part = h.d_cut < 1024 ? 1 : 0;
+    b.dense_cut = h.d_cut;
+    if (launch_dense(b, d_grid, true, kDenseThreadsBeside, cs) != cudaSuccess) return CMP_ECUDA;
+    if (h.d_cut < 1024) {
+      b.dense_part = 2;
+      if (launch_dense(b, d_grid, true, kDenseThreadsAlone, cs) != cudaSuccess) return CMP_ECUDA;
+    }
     if (h.shape.grid > 0 && launch_build(a, h.shape, cs) != cudaSuccess) return CMP_ECUDA;
     return launch_agg_hash(a, hash_grid, cs) == cudaSuccess ? CMP_OK : CMP_ECUDA;
   }
@@ -894,7 +925,8 @@ extern "C" cmp_status cmp_build_plan_stats(const void* plan_host, cmp_build_plan
   // unique-key kernel; the row kernel; the presence check and the dense kernel
   info->launches = 1 + (h.n_agg > 0 ? 1 + (h.cnt_grid > 0 ? 1 : 0) + (h.cnt_split > 0 ? 1 : 0) + (h.hash_grid > 0 ? 1 : 0) : 0) +
                    (h.n_uitems > 0 && h.u_grid > 0 ? 1 : 0) + (h.shape.grid > 0 ? 1 : 0) +
-                   (h.n_ditems > 0 && h.d_grid > 0 ? 2 : 0);  // the presence check and the dense kernel
+                   (h.n_ditems > 0 && h.d_grid > 0 ? 2 : 0) +  // the presence check and the dense kernel
+                   (h.n_ditems > 0 && h.d_grid > 0 && h.cnt_split > 0 && h.d_cut < 1024 ? 1 : 0);  // its second part
   info->n_presence = h.n_presence;
   return CMP_OK;
 }

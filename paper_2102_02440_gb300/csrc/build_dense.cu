@@ -83,6 +83,9 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_dense_hash(const __g
   __shared__ int32_t s_active;
   __shared__ long long s_lo, s_hi;  // domain offsets of the surviving keys: [s_lo, s_hi)
   const int tid = threadIdx.x, T = blockDim.x;
+  // the first part, beside the counting pass: the second part (512 threads, one CTA per SM)
+  // may take each SM as soon as both have left it
+  if (A.dense_part == 1) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const uint32_t w = uint32_t(A.w);
   uint32_t* cs = reinterpret_cast<uint32_t*>(smem);
   const int words = A.d_words;
@@ -141,7 +144,9 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_dense_hash(const __g
     if (lo >= hi) continue;
     const int64_t n_runs = (hi - lo + kDenseRun - 1) / kDenseRun;
     const uint32_t* bm = reinterpret_cast<const uint32_t*>(A.ws + ac.off);
-    for (int64_t r0 = tid; r0 < n_runs; r0 += int64_t(kRuns) * T) {
+    const int64_t cut = (n_runs * A.dense_cut + 1023) / 1024;  // this part's runs [run_lo, run_hi)
+    const int64_t run_lo = A.dense_part == 2 ? cut : 0, run_hi = A.dense_part == 1 ? cut : n_runs;
+    for (int64_t r0 = run_lo + tid; r0 < run_hi; r0 += int64_t(kRuns) * T) {
       // runs r0 and r0 + T of this item (when present): bitmap words and first keys
       uint32_t wd[kRuns][kRunWords];
       uint64_t x0[kRuns];
@@ -149,7 +154,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_dense_hash(const __g
 #pragma unroll
       for (int u = 0; u < kRuns; u++) {
         const int64_t r = r0 + int64_t(u) * T;
-        has[u] = r < n_runs;
+        has[u] = r < run_hi;
         const int64_t k0 = lo + r * kDenseRun;  // a multiple of kDenseRun: 32-byte aligned words
         if (has[u]) {
           const uint4* p4 = reinterpret_cast<const uint4*>(bm + k0 / 32);
@@ -211,9 +216,9 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_dense_hash(const __g
     }
   }
   if (cur >= 0 && s_active) flush();
-  // Launched as a programmatic dependent (of the hashing of the counted keys, or of the
-  // second launch of a split counting pass): finish only after it has, so that the stream's
-  // later work also finds it complete.
+  // Launched as a programmatic dependent (of the hashing of the counted keys, of the second
+  // launch of a split counting pass, or, the second part, of the first part): finish only
+  // after it has, so that the stream's later work also finds it complete.
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 

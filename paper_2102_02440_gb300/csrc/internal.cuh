@@ -383,6 +383,9 @@ struct BuildArgs {
   const int32_t* d_cta_item;
   int64_t n_ditems;
   int32_t d_pack16, d_words;
+  // the dense kernel's share of each item's runs: 0 all; 1 the first ceil(n d_cut / 1024);
+  // 2 the rest
+  int32_t dense_part, dense_cut;
 };
 
 // Plan blob (host-encoded, device-read) for the batched build.
@@ -406,9 +409,11 @@ struct BuildPlanHdr {
   // counting pass in two launches (cnt_split > 0): chunks [0, cnt_split) of the tables with
   // presence columns first, then [cnt_split, total) with the dense kernel beside it
   int64_t cnt_split;
-  int32_t cnt_grid_b, d_grid_split;
+  // split pass: the dense kernel walks the first d_cut / 1024 of each item's runs beside the
+  // second counting launch, the rest after it with 512 threads (d_cut = 1024: all beside)
+  int32_t cnt_grid_b, d_cut;
 };
-constexpr int32_t kBuildPlanVersion = 9;
+constexpr int32_t kBuildPlanVersion = 10;
 struct ZeroSpan {
   void* ptr;
   int64_t bytes;

@@ -160,10 +160,11 @@ def test_presence_columns_plan_host_logic(K):
     assert dense.launches == 6
     packed, _ = stats([_desc(K, n_rows=n, flags=flags, dom=(0, n))], w=65536)
     assert packed.n_presence == 1
-    # with a counted table beside it: the counting pass in two launches (presence first)
+    # with a counted table beside it: the counting pass in two launches (presence first), the
+    # dense kernel in two parts (its share beside the second counting launch, then the rest)
     fk = _desc(K, n_rows=4 * n, flags=K.CMP_COL_DOMAIN, dom=(0, n))
     split, _ = stats([fk, _desc(K, n_rows=n, flags=flags, dom=(0, n))])
-    assert split.n_presence == 1 and split.n_agg == 2 and split.launches == 8
+    assert split.n_presence == 1 and split.n_agg == 2 and split.launches == 9
     rng = K.cmp_pred(0, K.CMP_RANGE, 0, 100, None, 0)
     for t, cfg in ((_desc(K, n_rows=n, flags=flags, dom=(0, 4 * n + 1)), None),
                    (_desc(K, n_rows=n, flags=flags, dom=(0, n), preds=(rng,)), None),

@@ -139,9 +139,10 @@ def test_dense_beside_counted_and_unique_columns(orc):
 @pytest.mark.parametrize("w", [1024, 65536])
 def test_dense_beside_the_second_counting_launch(orc, w):
     """Presence columns and counted columns without a unique-key kernel: the counting pass
-    runs in two launches (the presence tables first), the dense kernel beside the second
-    one (256 threads, one CTA per SM).  Counters equal the oracle's; the plan has one more
-    launch than the single pass."""
+    runs in two launches (the presence tables first), the dense kernel's first part beside
+    the second one (256 threads, one CTA per SM) and the rest of each item's runs after it
+    (512 threads).  Counters equal the oracle's; the plan has two more launches than the
+    single pass."""
     rng = np.random.default_rng(w + 5)
     n = 300_000
     pk = rng.permutation(n).astype(np.int64)
@@ -153,6 +154,7 @@ def test_dense_beside_the_second_counting_launch(orc, w):
     dw = _build(wl)
     info = P.build_plan_info(dw)
     assert info["n_presence"] == 1 and info["n_unique_slabs"] == 0
-    # zeroing, clearing, two counting launches, the presence check, dense, row kernel, hashing
-    assert info["launches"] == 8
+    # zeroing, clearing, two counting launches, the presence check, dense in two parts, row
+    # kernel, hashing
+    assert info["launches"] == 9
     _check(orc, wl, dw)
