@@ -165,6 +165,11 @@ def test_presence_columns_plan_host_logic(K):
     fk = _desc(K, n_rows=4 * n, flags=K.CMP_COL_DOMAIN, dom=(0, n))
     split, _ = stats([fk, _desc(K, n_rows=n, flags=flags, dom=(0, n))])
     assert split.n_presence == 1 and split.n_agg == 2 and split.launches == 9
+    # a scan long enough to cover the whole walk (its bytes against the walk's key x row steps):
+    # the dense kernel stays in one part beside it
+    fk_long = _desc(K, n_rows=80 * n, flags=K.CMP_COL_DOMAIN, dom=(0, n))
+    whole, _ = stats([fk_long, _desc(K, n_rows=n, flags=flags, dom=(0, n))])
+    assert whole.n_presence == 1 and whole.launches == 8
     rng = K.cmp_pred(0, K.CMP_RANGE, 0, 100, None, 0)
     for t, cfg in ((_desc(K, n_rows=n, flags=flags, dom=(0, 4 * n + 1)), None),
                    (_desc(K, n_rows=n, flags=flags, dom=(0, n), preds=(rng,)), None),
